@@ -1,0 +1,320 @@
+"""FP64 CPU oracle of the 2-D PIC space-charge step (arXiv:2010.11540).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference legs of bench.py, never by the product package.  It
+shares no code with the CUDA path; the seeded inputs come from
+paper_2010_11540_gb300.synth, which the caller passes in as plain arrays.
+
+The particle loops are plain C (sc_oracle.c, built with -ffp-contract=off);
+the open-boundary convolution uses numpy's FFT as the library primitive
+(Hockney's zero-padded method, Sec. I reference [Hockney]); the tracking loop
+follows the PIC loop of Sec. I (deposit -> Poisson -> kick/push) with the kick
+of Sec. IV.
+
+Functions whose parity is pinned only against the oracle itself are marked
+"parity unpinned" in their docstrings (long-run statistics).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sc_oracle.c")
+_LIB = os.path.join(_HERE, "libsc_oracle.so")
+
+ONE_FX = 1 << 20  # fixed-point unit per axis
+Q_UNIT = float(1 << 40)  # one particle's total deposited charge
+
+DRIFT, QUAD, SEXT, BEND, RF, MARK = 0, 1, 2, 3, 4, 5
+
+
+def build(force=False):
+    """Compile the C oracle (gcc, -O2 -ffp-contract=off)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                               "-std=c11", "-D_DEFAULT_SOURCE", _SRC, "-o", _LIB, "-lm"])
+    return _LIB
+
+
+class _Beam(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in
+                ("gamma0", "beta0", "n_lambda", "r_p", "circumference", "mass_ev")]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_lp = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_deposit.restype = ctypes.c_int64
+        L.orc_deposit.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _lp]
+        L.orc_green_self.restype = ctypes.c_double
+        L.orc_green_self.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_green_cyclic.restype = None
+        L.orc_green_cyclic.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
+        L.orc_potential_direct.restype = None
+        L.orc_potential_direct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           _dp, _dp]
+        L.orc_fields.restype = None
+        L.orc_fields.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]
+        L.orc_kick.restype = None
+        L.orc_kick.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                               ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                               _dp, _dp, ctypes.c_double]
+        L.orc_push.restype = None
+        L.orc_push.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_void_p, ctypes.c_int,
+                               ctypes.POINTER(_Beam)]
+        L.orc_moments.restype = None
+        L.orc_moments.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _beam(b):
+    return _Beam(*(float(b[k]) for k in ("gamma0", "beta0", "n_lambda", "r_p", "circumference", "mass_ev")))
+
+
+# ---------------------------------------------------------------------------
+# Grid geometry (nodes x_i = xmin + i*hx, i = 0..nx-1)
+# ---------------------------------------------------------------------------
+class Geometry:
+    def __init__(self, nx, ny, xmin, xmax, ymin, ymax):
+        self.nx, self.ny = int(nx), int(ny)
+        self.xmin, self.xmax, self.ymin, self.ymax = map(float, (xmin, xmax, ymin, ymax))
+        self.hx = (self.xmax - self.xmin) / (self.nx - 1)
+        self.hy = (self.ymax - self.ymin) / (self.ny - 1)
+        self.inv_hx = 1.0 / self.hx
+        self.inv_hy = 1.0 / self.hy
+
+    @property
+    def node_x(self):
+        return self.xmin + np.arange(self.nx) * self.hx
+
+    @property
+    def node_y(self):
+        return self.ymin + np.arange(self.ny) * self.hy
+
+
+def deposit(g: Geometry, x, y):
+    """CIC deposit (Sec. IV-A) -> (Q int64 [ny, nx], n_out)."""
+    Q = np.zeros((g.ny, g.nx), dtype=np.int64)
+    n_out = lib().orc_deposit(len(x), _d(x), _d(y), g.nx, g.ny, g.xmin, g.ymin, g.inv_hx, g.inv_hy,
+                              Q.ctypes.data_as(_lp))
+    return Q, int(n_out)
+
+
+def green_self(hx, hy):
+    return lib().orc_green_self(hx, hy)
+
+
+def green_cyclic(g: Geometry):
+    G = np.zeros((2 * g.ny, 2 * g.nx))
+    lib().orc_green_cyclic(g.nx, g.ny, g.hx, g.hy, _d(G))
+    return G
+
+
+def normalise(Q, n_total):
+    """q = Q 2^-40 / N_mp: each macroparticle carries 1/N_mp of the line charge."""
+    return Q.astype(np.float64) / Q_UNIT / float(n_total)
+
+
+def potential_direct(g: Geometry, q):
+    """phi on nodes i=-1..nx, j=-1..ny by direct pairwise sum (small grids only)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    phi = np.zeros((g.ny + 2, g.nx + 2))
+    lib().orc_potential_direct(g.nx, g.ny, g.hx, g.hy, _d(q), _d(phi))
+    return phi
+
+
+def potential_fft(g: Geometry, q):
+    """phi on nodes i=-1..nx, j=-1..ny: Hockney's method, q zero-padded to the
+    doubled grid and cyclically convolved with G by FFT (numpy, float64)."""
+    Mx, My = 2 * g.nx, 2 * g.ny
+    qp = np.zeros((My, Mx))
+    qp[: g.ny, : g.nx] = q
+    G = green_cyclic(g)
+    phi = np.fft.irfft2(np.fft.rfft2(qp) * np.fft.rfft2(G), s=(My, Mx))
+    iy = np.r_[My - 1, np.arange(0, g.ny + 1)]
+    ix = np.r_[Mx - 1, np.arange(0, g.nx + 1)]
+    return np.ascontiguousarray(phi[np.ix_(iy, ix)])
+
+
+def fields(g: Geometry, phi_ext):
+    """E = -grad phi at the nodes by centred differences -> (Ex, Ey) [ny, nx]."""
+    phi_ext = np.ascontiguousarray(phi_ext, dtype=np.float64)
+    Ex = np.zeros((g.ny, g.nx))
+    Ey = np.zeros((g.ny, g.nx))
+    lib().orc_fields(g.nx, g.ny, g.hx, g.hy, _d(phi_ext), _d(Ex), _d(Ey))
+    return Ex, Ey
+
+
+def solve(g: Geometry, Q, n_total, method="fft"):
+    """Charge grid -> node fields (Ex, Ey), normalised per unit line charge."""
+    q = normalise(Q, n_total)
+    phi = potential_fft(g, q) if method == "fft" else potential_direct(g, q)
+    return fields(g, phi)
+
+
+def kick_strength(b):
+    """K = 2 r_p N_lambda / (beta0^2 gamma0^3) (Sec. IV kick eq. and Eq. pot2)."""
+    return 2.0 * b["r_p"] * b["n_lambda"] / (b["beta0"] ** 2 * b["gamma0"] ** 3)
+
+
+def kick(g: Geometry, st, Ex, Ey, kl):
+    lib().orc_kick(len(st["x"]), _d(st["x"]), _d(st["y"]), _d(st["px"]), _d(st["py"]), g.nx, g.ny,
+                   g.xmin, g.ymin, g.inv_hx, g.inv_hy, _d(np.ascontiguousarray(Ex)),
+                   _d(np.ascontiguousarray(Ey)), kl)
+
+
+def push(st, elems, b):
+    elems = np.ascontiguousarray(elems)
+    if len(elems) == 0:
+        return
+    bb = _beam(b)
+    lib().orc_push(len(st["x"]), _d(st["x"]), _d(st["px"]), _d(st["y"]), _d(st["py"]), _d(st["sigma"]),
+                   _d(st["psigma"]), elems.ctypes.data, len(elems), ctypes.byref(bb))
+
+
+def moments(st):
+    out = np.zeros(14)
+    lib().orc_moments(len(st["x"]), _d(st["x"]), _d(st["px"]), _d(st["y"]), _d(st["py"]), _d(st["sigma"]),
+                      _d(st["psigma"]), _d(out))
+    return out
+
+
+def emittances(st):
+    """rms emittances eps_u = sqrt(<uu><pp> - <up>^2) (Sec. V)."""
+    m = moments(st)
+    ex = np.sqrt(m[6] * m[8] - m[7] ** 2)
+    ey = np.sqrt(m[9] * m[11] - m[10] ** 2)
+    return ex, ey
+
+
+def copy_state(st):
+    return {k: np.array(v, dtype=np.float64, copy=True) for k, v in st.items()}
+
+
+# ---------------------------------------------------------------------------
+# Lattice: space-charge locations and the segments between them (Sec. V:
+# kicks at chosen locations, L = distance since the previous location).
+# ---------------------------------------------------------------------------
+def segments(lattice):
+    """-> (head, kicks): head = elements before the first marker; kicks = list of
+    (L_since_previous_marker, elements_after_this_marker_up_to_the_next)."""
+    lat = np.asarray(lattice)
+    marks = [i for i in range(len(lat)) if int(lat["type"][i]) == MARK]
+    s = np.concatenate([[0.0], np.cumsum(lat["length"])])
+    circ = float(s[-1])
+    if not marks:
+        return lat, []
+    head = lat[: marks[0]]
+    kicks = []
+    for k, m in enumerate(marks):
+        end = marks[k + 1] if k + 1 < len(marks) else len(lat)
+        prev = s[marks[k - 1]] if k > 0 else s[marks[-1]] - circ
+        kicks.append((float(s[m] - prev), lat[m + 1:end]))
+    return head, kicks
+
+
+def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None):
+    """Track `st` (modified in place) for n_turns with the PIC loop of Sec. I.
+    Each space-charge location: deposit -> solve -> kick (L since the previous
+    location) -> push to the next location.  Returns the number of kicks done.
+    `diag(turn, st)` is called at the start of every turn."""
+    head, kicks = segments(lattice)
+    K = kick_strength(b)
+    n = len(st["x"])
+    done = 0
+    for t in range(n_turns):
+        if diag is not None:
+            diag(t, st)
+        push(st, head, b)
+        for L, seg in kicks:
+            if max_kicks is not None and done >= max_kicks:
+                return done
+            Q, _ = deposit(g, st["x"], st["y"])
+            Ex, Ey = solve(g, Q, n, method)
+            kick(g, st, Ex, Ey, K * L)
+            push(st, seg, b)
+            done += 1
+    return done
+
+
+# ---------------------------------------------------------------------------
+# Linear optics diagnostics (Sec. V: beta from rms size, tunes from the
+# one-turn phase advance).
+# ---------------------------------------------------------------------------
+def one_turn_matrix(lattice, b, eps=1e-8, ps=0.0):
+    """4x4 transverse one-turn matrix at the given psigma by central differences
+    of the push (space charge off)."""
+    M = np.zeros((4, 4))
+    keys = ("x", "px", "y", "py")
+    for c in range(4):
+        st = {k: np.zeros(2) for k in ("x", "px", "y", "py", "sigma", "psigma")}
+        st["psigma"][:] = ps
+        st[keys[c]][0] = eps
+        st[keys[c]][1] = -eps
+        push(st, np.asarray(lattice), b)
+        for r in range(4):
+            M[r, c] = (st[keys[r]][0] - st[keys[r]][1]) / (2 * eps)
+    return M
+
+
+def twiss_from_matrix(M2):
+    """(mu, beta, alpha) of a 2x2 periodic matrix: cos mu = Tr/2."""
+    cmu = 0.5 * (M2[0, 0] + M2[1, 1])
+    smu = np.sign(M2[0, 1]) * np.sqrt(1.0 - cmu * cmu)
+    mu = np.arctan2(smu, cmu)
+    beta = M2[0, 1] / smu
+    alpha = (M2[0, 0] - M2[1, 1]) / (2.0 * smu)
+    return mu % (2 * np.pi), beta, alpha
+
+
+def bare_tunes(lattice, b):
+    M = one_turn_matrix(lattice, b)
+    qx = twiss_from_matrix(M[:2, :2])[0] / (2 * np.pi)
+    qy = twiss_from_matrix(M[2:, 2:])[0] / (2 * np.pi)
+    return qx, qy
+
+
+class PhaseAdvance:
+    """Per-particle tunes as the mean one-turn phase advance (Sec. V), in
+    normalised coordinates of the bare one-turn Twiss at the observation point.
+    Returns fractional tunes in [0, 1)."""
+
+    def __init__(self, beta_x, alpha_x, beta_y, alpha_y):
+        self.t = (beta_x, alpha_x, beta_y, alpha_y)
+        self.prev = None
+        self.acc = None
+        self.turns = 0
+
+    def _angles(self, st):
+        bx, ax, by, ay = self.t
+        X, PX = st["x"] / np.sqrt(bx), (ax * st["x"] + bx * st["px"]) / np.sqrt(bx)
+        Y, PY = st["y"] / np.sqrt(by), (ay * st["y"] + by * st["py"]) / np.sqrt(by)
+        return np.arctan2(-PX, X), np.arctan2(-PY, Y)
+
+    def __call__(self, turn, st):
+        ang = self._angles(st)
+        if self.prev is not None:
+            d = [np.mod(a - p, 2 * np.pi) for a, p in zip(ang, self.prev)]
+            self.acc = d if self.acc is None else [s + x for s, x in zip(self.acc, d)]
+            self.turns += 1
+        self.prev = ang
+
+    def tunes(self):
+        return [a / (2 * np.pi * self.turns) for a in self.acc]

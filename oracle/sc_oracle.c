@@ -1,0 +1,332 @@
+/*
+ * sc_oracle.c -- plain, slow, obviously-correct FP64 CPU reference of the
+ * 2-D particle-in-cell space-charge step (Kurimoto, "Particle Tracking with
+ * Space Charge Effects using GPU", arXiv:2010.11540).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or helper with the CUDA path.  Build with
+ * -ffp-contract=off so that every product and sum below is rounded exactly as
+ * written (no fused multiply-add).
+ *
+ * Contents, each following the passage cited at the function:
+ *   orc_deposit        Sec. IV-A, CIC charge-assignment equation (4 weights),
+ *                      in 2^-20 fixed point per axis, int64 accumulation.
+ *   orc_green_self     cell-averaged -ln r (self term of the open-boundary
+ *                      Green's function; the paper is silent, see DESIGN).
+ *   orc_green_cyclic   Hockney's zero-padded free-space Green's function
+ *                      G = -ln r laid out on the doubled (2nx x 2ny) grid.
+ *   orc_potential_direct  direct pairwise sum phi = sum G q (definition).
+ *   orc_fields         E = -grad phi by centred differences (Sec. IV-C, the
+ *                      field equation, with bilinear gather in place of the
+ *                      Bezier surface).
+ *   orc_kick           Sec. IV, transverse kick equation, bilinear gather.
+ *   orc_push           Sec. III: exact drift (III-A), thick chromatic
+ *                      quadrupole (III-B), thin sextupole (III-C, V of the
+ *                      H0+V split), linear sector dipole (H_approx with
+ *                      curvature), thin RF kick (Sec. V mentions RF cavities).
+ *   orc_moments        Sec. V: rms sizes / emittances from beam moments.
+ *
+ * Parity pins live in tests/test_oracle_*.py.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+typedef struct {
+  int32_t type, pad;
+  double length, k1, k2l, angle, volt, harmonic, lag;
+} orc_elem;
+
+typedef struct {
+  double gamma0, beta0, n_lambda, r_p, circumference, mass_ev;
+} orc_beam;
+
+enum { ORC_DRIFT = 0, ORC_QUAD = 1, ORC_SEXT = 2, ORC_BEND = 3, ORC_RF = 4, ORC_MARK = 5 };
+
+static const double ORC_ONE_FX = 1048576.0; /* 2^20 */
+
+/* ---------------------------------------------------------------------
+ * Charge deposition, Sec. IV-A (CIC equation).  Grid nodes are
+ * x_i = xmin + i*hx, i = 0..nx-1 (same for y); inv_hx = 1/hx is passed in.
+ * A particle with xi = (x - xmin)*inv_hx, eta = (y - ymin)*inv_hy lies in
+ * cell (i, j) = (floor xi, floor eta) with fractions fx = xi - i, fy = eta - j.
+ * It is inside iff 0 <= xi < nx-1 and 0 <= eta < ny-1; outside particles
+ * deposit nothing and are counted (return value).
+ * The paper's weights (x_{i+1}-x)(y_{j+1}-y)/(dx dy), ... are taken at 2^-20
+ * resolution per axis: ax = rint(fx*2^20), bx = 2^20 - ax, and Q (int64,
+ * Q[j*nx + i]) gets bx*by, ax*by, bx*ay, ax*ay at (i,j), (i+1,j), (i,j+1),
+ * (i+1,j+1).  Each particle adds exactly 2^40.  Q is accumulated, not zeroed.
+ * ------------------------------------------------------------------- */
+int64_t orc_deposit(int64_t n, const double *x, const double *y, int nx, int ny,
+                    double xmin, double ymin, double inv_hx, double inv_hy, int64_t *Q) {
+  int64_t n_out = 0;
+  for (int64_t p = 0; p < n; ++p) {
+    double xi = (x[p] - xmin) * inv_hx;
+    double eta = (y[p] - ymin) * inv_hy;
+    if (!(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) {
+      ++n_out;
+      continue;
+    }
+    double fi = floor(xi), fj = floor(eta);
+    int i = (int)fi, j = (int)fj;
+    double fx = xi - fi, fy = eta - fj;
+    int64_t ax = (int64_t)llrint(fx * ORC_ONE_FX);
+    int64_t ay = (int64_t)llrint(fy * ORC_ONE_FX);
+    int64_t bx = (int64_t)ORC_ONE_FX - ax;
+    int64_t by = (int64_t)ORC_ONE_FX - ay;
+    Q[(int64_t)j * nx + i] += bx * by;
+    Q[(int64_t)j * nx + i + 1] += ax * by;
+    Q[(int64_t)(j + 1) * nx + i] += bx * ay;
+    Q[(int64_t)(j + 1) * nx + i + 1] += ax * ay;
+  }
+  return n_out;
+}
+
+/* ---------------------------------------------------------------------
+ * Open-boundary Green's function of the 2-D Poisson equation (Sec. IV,
+ * Eq. poisson3D with u -> the free-space part; Hockney's method cited in
+ * Sec. I).  With potential normalised so that a unit line charge gives
+ * phi = -ln r, G(dx, dy) = -1/2 ln(dx^2 + dy^2).
+ * Self term G(0,0): mean of -ln r over the hx x hy cell centred on the node,
+ *   = -(1/(2ab)) * I(a,b), a = hx/2, b = hy/2,
+ *   I(a,b) = int_0^a int_0^b ln(x^2+y^2) dy dx
+ *          = ab(ln(a^2+b^2) - 3) + a^2 atan(b/a) + b^2 atan(a/b).
+ * ------------------------------------------------------------------- */
+double orc_green_self(double hx, double hy) {
+  double a = 0.5 * hx, b = 0.5 * hy;
+  double I = a * b * (log(a * a + b * b) - 3.0) + a * a * atan(b / a) + b * b * atan(a / b);
+  return -I / (2.0 * a * b);
+}
+
+static double orc_green_at(int di, int dj, double hx, double hy) {
+  if (di == 0 && dj == 0) return orc_green_self(hx, hy);
+  double dx = di * hx, dy = dj * hy;
+  return -0.5 * log(dx * dx + dy * dy);
+}
+
+/* G on the doubled grid, cyclic: index a in [0, 2nx) holds offset a for
+ * a <= nx and a - 2nx for a > nx (index nx holds offset nx, which equals
+ * offset -nx by symmetry); the same for b.  Layout Gc[b*(2nx) + a]. */
+void orc_green_cyclic(int nx, int ny, double hx, double hy, double *Gc) {
+  int Mx = 2 * nx, My = 2 * ny;
+  for (int b = 0; b < My; ++b) {
+    int dj = (b <= ny) ? b : b - My;
+    for (int a = 0; a < Mx; ++a) {
+      int di = (a <= nx) ? a : a - Mx;
+      Gc[(int64_t)b * Mx + a] = orc_green_at(di, dj, hx, hy);
+    }
+  }
+}
+
+/* Direct pairwise sum (the definition of the open-boundary convolution):
+ * phi(i, j) = sum_{k,l} G((i-k)hx, (j-l)hy) q[l*nx + k] for the extended node
+ * range i = -1..nx, j = -1..ny; output phi_ext[(j+1)*(nx+2) + (i+1)]. */
+void orc_potential_direct(int nx, int ny, double hx, double hy, const double *q, double *phi_ext) {
+  int ex = nx + 2;
+  for (int j = -1; j <= ny; ++j)
+    for (int i = -1; i <= nx; ++i) {
+      double s = 0.0;
+      for (int l = 0; l < ny; ++l)
+        for (int k = 0; k < nx; ++k) {
+          double ql = q[(int64_t)l * nx + k];
+          if (ql != 0.0) s += orc_green_at(i - k, j - l, hx, hy) * ql;
+        }
+      phi_ext[(int64_t)(j + 1) * ex + (i + 1)] = s;
+    }
+}
+
+/* E = -grad phi at the nx x ny nodes by centred differences, using the
+ * potential on the surrounding ring of nodes (i = -1, nx; j = -1, ny), which
+ * the open-boundary solution defines.  Ex[j*nx+i], Ey[j*nx+i]. */
+void orc_fields(int nx, int ny, double hx, double hy, const double *phi_ext, double *Ex, double *Ey) {
+  int ex = nx + 2;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      double pxp = phi_ext[(int64_t)(j + 1) * ex + (i + 2)];
+      double pxm = phi_ext[(int64_t)(j + 1) * ex + (i + 0)];
+      double pyp = phi_ext[(int64_t)(j + 2) * ex + (i + 1)];
+      double pym = phi_ext[(int64_t)(j + 0) * ex + (i + 1)];
+      Ex[(int64_t)j * nx + i] = -(pxp - pxm) / (2.0 * hx);
+      Ey[(int64_t)j * nx + i] = -(pyp - pym) / (2.0 * hy);
+    }
+}
+
+/* ---------------------------------------------------------------------
+ * Space-charge kick, Sec. IV (transverse kick equation):
+ *   dp = -(e lambda / (m gamma0^3 beta0^2 c^2)) grad u * L,
+ * with u normalised per unit line charge.  In the normalisation above this
+ * is dpx = K * L * Ex, dpy = K * L * Ey, K = 2 r_p N_lambda / (beta0^2 gamma0^3),
+ * and kl = K * L is passed in.  E at the particle is the bilinear
+ * interpolation of the node fields with the same cell and fractions as the
+ * deposit (float64 fractions).  Particles outside the grid get no kick.
+ * ------------------------------------------------------------------- */
+void orc_kick(int64_t n, const double *x, const double *y, double *px, double *py,
+              int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy,
+              const double *Ex, const double *Ey, double kl) {
+  for (int64_t p = 0; p < n; ++p) {
+    double xi = (x[p] - xmin) * inv_hx;
+    double eta = (y[p] - ymin) * inv_hy;
+    if (!(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) continue;
+    double fi = floor(xi), fj = floor(eta);
+    int i = (int)fi, j = (int)fj;
+    double fx = xi - fi, fy = eta - fj;
+    double w00 = (1.0 - fx) * (1.0 - fy), w10 = fx * (1.0 - fy);
+    double w01 = (1.0 - fx) * fy, w11 = fx * fy;
+    int64_t c = (int64_t)j * nx + i;
+    double ex = w00 * Ex[c] + w10 * Ex[c + 1] + w01 * Ex[c + nx] + w11 * Ex[c + nx + 1];
+    double ey = w00 * Ey[c] + w10 * Ey[c + 1] + w01 * Ey[c + nx] + w11 * Ey[c + nx + 1];
+    px[p] += kl * ex;
+    py[p] += kl * ey;
+  }
+}
+
+/* ---------------------------------------------------------------------
+ * Single-particle maps, Sec. III.  State (x, px, y, py, sg, ps) with
+ * px = Px/p0, sg = s - c beta0 t, ps = p_sigma.
+ * ------------------------------------------------------------------- */
+
+/* Exact drift (Sec. III-A: field-free motion solved without approximation).
+ * With (1+delta)^2 = 1 + 2 ps + beta0^2 ps^2 (Eq. BEND2) and
+ * pz = sqrt((1+delta)^2 - px^2 - py^2):
+ *   x += L px/pz,  y += L py/pz,  sg += L (1 - (1 + beta0^2 ps)/pz). */
+static void orc_drift(double *s, double L, double beta0) {
+  double px = s[1], py = s[3], ps = s[5];
+  double opd2 = 1.0 + 2.0 * ps + beta0 * beta0 * ps * ps;
+  double pz = sqrt(opd2 - px * px - py * py);
+  s[0] += L * px / pz;
+  s[2] += L * py / pz;
+  s[4] += L * (1.0 - (1.0 + beta0 * beta0 * ps) / pz);
+}
+
+/* Flow of H0 = (px^2+py^2)/2 (1-ps) + ps^2/(2 gamma0^2) over L (the k1 -> 0
+ * limit of the quadrupole below). */
+static void orc_h0_drift(double *s, double L, double gamma0) {
+  double px = s[1], py = s[3], ps = s[5];
+  s[0] += px * (1.0 - ps) * L;
+  s[2] += py * (1.0 - ps) * L;
+  s[4] += ps * L / (gamma0 * gamma0) - 0.5 * (px * px + py * py) * L;
+}
+
+/* One transverse plane of the thick quadrupole (Sec. III-B), focusing
+ * (foc = 1: cos/sin) or defocusing (foc = 0: cosh/sinh), with
+ * w = sqrt(|k1| (1 - ps)), a = sqrt((1-ps)/|k1|), b = sqrt(|k1|/(1-ps)):
+ *   focusing:   u = u0 cos wL + a pu0 sin wL,  pu = pu0 cos wL - b u0 sin wL
+ *   defocusing: u = u0 cosh wL + a pu0 sinh wL, pu = pu0 cosh wL + b u0 sinh wL
+ * Returns I = int_0^L pu(s)^2 ds in closed form (used by the sg equation). */
+static double orc_quad_plane(double *u, double *pu, double absk1, double ps, double L, int foc) {
+  double w = sqrt(absk1 * (1.0 - ps));
+  double a = sqrt((1.0 - ps) / absk1);
+  double b = sqrt(absk1 / (1.0 - ps));
+  double u0 = *u, p0 = *pu, I;
+  if (foc) {
+    double c = cos(w * L), s = sin(w * L);
+    *u = u0 * c + a * p0 * s;
+    *pu = p0 * c - b * u0 * s;
+    /* pu(s) = p0 cos(ws) - b u0 sin(ws) */
+    double icc = 0.5 * L + s * c / (2.0 * w);  /* int cos^2 */
+    double iss = 0.5 * L - s * c / (2.0 * w);  /* int sin^2 */
+    double isc = s * s / (2.0 * w);            /* int sin cos */
+    I = p0 * p0 * icc - 2.0 * p0 * b * u0 * isc + b * b * u0 * u0 * iss;
+  } else {
+    double c = cosh(w * L), s = sinh(w * L);
+    *u = u0 * c + a * p0 * s;
+    *pu = p0 * c + b * u0 * s;
+    /* pu(s) = p0 cosh(ws) + b u0 sinh(ws) */
+    double icc = 0.5 * L + s * c / (2.0 * w);   /* int cosh^2 */
+    double iss = -0.5 * L + s * c / (2.0 * w);  /* int sinh^2 */
+    double isc = s * s / (2.0 * w);             /* int sinh cosh */
+    I = p0 * p0 * icc + 2.0 * p0 * b * u0 * isc + b * b * u0 * u0 * iss;
+  }
+  return I;
+}
+
+/* Thick quadrupole, Sec. III-B: x/y maps as printed (k1 > 0 focuses x;
+ * k1 < 0 swaps the planes), and
+ *   sg(L) = sg(0) + ps L / gamma0^2 - 1/2 int_0^L (px^2 + py^2) ds. */
+static void orc_quad(double *s, double L, double k1, double gamma0) {
+  if (k1 == 0.0) { orc_h0_drift(s, L, gamma0); return; }
+  double ps = s[5], absk1 = fabs(k1);
+  double Ix = orc_quad_plane(&s[0], &s[1], absk1, ps, L, k1 > 0.0);
+  double Iy = orc_quad_plane(&s[2], &s[3], absk1, ps, L, k1 < 0.0);
+  s[4] += ps * L / (gamma0 * gamma0) - 0.5 * (Ix + Iy);
+}
+
+/* Thin sextupole: the V = k2 (x^3 - 3 x y^2)/6 step of Eq. Sym2 taken as
+ * one kick of integrated strength k2l:
+ *   px -= k2l/2 (x^2 - y^2),  py += k2l x y. */
+static void orc_sext(double *s, double k2l) {
+  double x = s[0], y = s[2];
+  s[1] -= 0.5 * k2l * (x * x - y * y);
+  s[3] += k2l * x * y;
+}
+
+/* Linear sector dipole from H_approx with curvature h = angle/L and the
+ * bending field's h^2 x^2/2 term (Sec. III, Eq. H):
+ *   H = (px^2+py^2)/2 + ps^2/(2 gamma0^2) - h x ps + h^2 x^2 / 2.
+ * With C = cos(hL), S = sin(hL):
+ *   x  = x0 C + px0 S/h + ps (1-C)/h
+ *   px = -x0 h S + px0 C + ps S
+ *   y  = y0 + py0 L,  py = py0
+ *   sg = sg0 + ps L/gamma0^2 - (x0 S + px0 (1-C)/h + ps (L - S/h)). */
+static void orc_bend(double *s, double L, double angle, double gamma0) {
+  if (angle == 0.0) { orc_h0_drift(s, L, gamma0); return; }
+  double h = angle / L, C = cos(angle), S = sin(angle);
+  double x0 = s[0], px0 = s[1], ps = s[5];
+  s[0] = x0 * C + px0 * S / h + ps * (1.0 - C) / h;
+  s[1] = -x0 * h * S + px0 * C + ps * S;
+  s[2] += s[3] * L;
+  s[4] += ps * L / (gamma0 * gamma0) - (x0 * S + px0 * (1.0 - C) / h + ps * (L - S / h));
+}
+
+/* Thin RF cavity: energy gain e V sin(lag - 2 pi h sg / C) per passage,
+ * ps += (V / (beta0^2 E0)) sin(lag - 2 pi h sg / C), E0 = gamma0 m c^2 [eV]. */
+static void orc_rf(double *s, const orc_elem *e, const orc_beam *bm) {
+  double e0 = bm->gamma0 * bm->mass_ev;
+  double phase = e->lag - 2.0 * M_PI * e->harmonic * s[4] / bm->circumference;
+  s[5] += e->volt / (bm->beta0 * bm->beta0 * e0) * sin(phase);
+}
+
+/* Push every particle through elements[0..n_elems) in order. */
+void orc_push(int64_t n, double *x, double *px, double *y, double *py, double *sg, double *ps,
+              const orc_elem *el, int n_elems, const orc_beam *bm) {
+  for (int64_t p = 0; p < n; ++p) {
+    double s[6] = {x[p], px[p], y[p], py[p], sg[p], ps[p]};
+    for (int k = 0; k < n_elems; ++k) {
+      const orc_elem *e = &el[k];
+      switch (e->type) {
+        case ORC_DRIFT: orc_drift(s, e->length, bm->beta0); break;
+        case ORC_QUAD: orc_quad(s, e->length, e->k1, bm->gamma0); break;
+        case ORC_SEXT: orc_sext(s, e->k2l); break;
+        case ORC_BEND: orc_bend(s, e->length, e->angle, bm->gamma0); break;
+        case ORC_RF: orc_rf(s, e, bm); break;
+        default: break; /* markers: no-op */
+      }
+    }
+    x[p] = s[0]; px[p] = s[1]; y[p] = s[2]; py[p] = s[3]; sg[p] = s[4]; ps[p] = s[5];
+  }
+}
+
+/* Beam moments for Sec. V diagnostics: out[0..6) = means of
+ * (x, px, y, py, sg, ps); out[6..) = central second moments
+ * <xx>, <x px>, <px px>, <yy>, <y py>, <py py>, <sg sg>, <ps ps>. */
+void orc_moments(int64_t n, const double *x, const double *px, const double *y, const double *py,
+                 const double *sg, const double *ps, double *out) {
+  const double *a[6] = {x, px, y, py, sg, ps};
+  double m[6] = {0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < 6; ++c) {
+    double t = 0.0;
+    for (int64_t p = 0; p < n; ++p) t += a[c][p];
+    m[c] = t / (double)n;
+    out[c] = m[c];
+  }
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t p = 0; p < n; ++p) {
+    double dx = x[p] - m[0], dpx = px[p] - m[1], dy = y[p] - m[2], dpy = py[p] - m[3];
+    double ds = sg[p] - m[4], dps = ps[p] - m[5];
+    s[0] += dx * dx; s[1] += dx * dpx; s[2] += dpx * dpx;
+    s[3] += dy * dy; s[4] += dy * dpy; s[5] += dpy * dpy;
+    s[6] += ds * ds; s[7] += dps * dps;
+  }
+  for (int c = 0; c < 8; ++c) out[6 + c] = s[c] / (double)n;
+}

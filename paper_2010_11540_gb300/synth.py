@@ -1,0 +1,186 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module draws random numbers and lays out plain data (particle arrays,
+element tables, grid extents, beam constants).  It holds none of the
+space-charge method's arithmetic: no deposition, no field, no transfer map.
+
+Workloads stand in for the paper's J-PARC Main Ring runs (Sec. V, Table II:
+2e5 macroparticles, ~100x100 grids, ~1 m between space-charge locations),
+whose lattice is not available; they are synthetic FODO rings.
+
+Element table layout (one 64-byte record per element, the C-ABI `sc_element`):
+    type:int32, pad:int32, length, k1, k2l, angle, volt, harmonic, lag (float64)
+Element type codes are part of the C-ABI (include/sc.h):
+    0 drift (exact, Sec. III-A), 1 thick quadrupole (Sec. III-B),
+    2 thin sextupole (Sec. III-C, single-kick limit), 3 sector dipole (Sec. III-A),
+    4 thin RF cavity (Sec. V), 5 space-charge location marker (Sec. IV, kick eq.).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# ---- element table -------------------------------------------------------
+DRIFT, QUAD, SEXT, BEND, RF, MARK = 0, 1, 2, 3, 4, 5
+
+ELEMENT_DTYPE = np.dtype(
+    [
+        ("type", "<i4"),
+        ("pad", "<i4"),
+        ("length", "<f8"),
+        ("k1", "<f8"),
+        ("k2l", "<f8"),
+        ("angle", "<f8"),
+        ("volt", "<f8"),
+        ("harmonic", "<f8"),
+        ("lag", "<f8"),
+    ],
+    align=True,
+)
+assert ELEMENT_DTYPE.itemsize == 64
+
+# ---- physical constants (CODATA 2018) ------------------------------------
+PROTON_MASS_EV = 938.27208816e6
+CLASSICAL_PROTON_RADIUS = 2.8179403262e-15 / 1836.15267343  # m: r_e / (m_p/m_e)
+# The paper prints r_p ~ 1.547e-18 m next to its tune-spread formula (Sec. V);
+# the CODATA value above is used everywhere except the test that reproduces
+# the paper's printed -0.45.
+PAPER_PROTON_RADIUS = 1.547e-18
+
+
+def elem(type_, length=0.0, k1=0.0, k2l=0.0, angle=0.0, volt=0.0, harmonic=0.0, lag=0.0):
+    """One element record as a tuple in ELEMENT_DTYPE order."""
+    return (type_, 0, length, k1, k2l, angle, volt, harmonic, lag)
+
+
+def table(elems) -> np.ndarray:
+    return np.array(list(elems), dtype=ELEMENT_DTYPE)
+
+
+def kinematics(kinetic_ev: float, mass_ev: float = PROTON_MASS_EV):
+    """gamma0, beta0 of the reference particle from its kinetic energy."""
+    gamma0 = 1.0 + kinetic_ev / mass_ev
+    beta0 = float(np.sqrt(1.0 - 1.0 / (gamma0 * gamma0)))
+    return gamma0, beta0
+
+
+def beam(kinetic_ev=3.0e9, n_lambda=5.0e9, circumference=0.0, r_p=CLASSICAL_PROTON_RADIUS):
+    """Beam constants as a plain dict (the C-ABI `sc_beam` fields)."""
+    g, b = kinematics(kinetic_ev)
+    return dict(gamma0=g, beta0=b, n_lambda=n_lambda, r_p=r_p,
+                circumference=circumference, mass_ev=PROTON_MASS_EV)
+
+
+# ---- particles -----------------------------------------------------------
+def _truncated_normal(rng, n, sigma, cut):
+    out = rng.standard_normal(n)
+    bad = np.abs(out) > cut
+    while bad.any():
+        out[bad] = rng.standard_normal(int(bad.sum()))
+        bad = np.abs(out) > cut
+    return out * sigma
+
+
+def gaussian_bunch(n, seed, sig_x, sig_y, sig_px, sig_py, sig_psigma=1e-3,
+                   z_half=10.0, trunc=4.0, sig_z=None, z_trunc=4.0):
+    """6-D particle arrays (x, px, y, py, sigma, psigma), float64, C-contiguous.
+
+    Transverse: independent Gaussians, each truncated at `trunc` sigma (redraw).
+    Longitudinal: sigma uniform on [-z_half, z_half], or Gaussian with rms
+    `sig_z` truncated at `z_trunc` sigma when `sig_z` is given.
+    Momentum: psigma Gaussian with rms `sig_psigma` (psigma equals dp/p to
+    first order, Sec. III).
+    Random numbers: numpy Philox counter-based generator keyed by `seed`.
+    """
+    rng = np.random.Generator(np.random.Philox(key=int(seed)))
+    x = _truncated_normal(rng, n, sig_x, trunc)
+    px = _truncated_normal(rng, n, sig_px, trunc)
+    y = _truncated_normal(rng, n, sig_y, trunc)
+    py = _truncated_normal(rng, n, sig_py, trunc)
+    if sig_z is None:
+        sg = rng.uniform(-z_half, z_half, n)
+    else:
+        sg = _truncated_normal(rng, n, sig_z, z_trunc)
+    ps = rng.standard_normal(n) * sig_psigma
+    return {k: np.ascontiguousarray(v, dtype=np.float64)
+            for k, v in zip(("x", "px", "y", "py", "sigma", "psigma"), (x, px, y, py, sg, ps))}
+
+
+def uniform_disk(n, seed, radius, cx=0.0, cy=0.0):
+    """Round uniform (KV-like transverse projection) beam of given radius."""
+    rng = np.random.Generator(np.random.Philox(key=int(seed)))
+    r = radius * np.sqrt(rng.uniform(0.0, 1.0, n))
+    t = rng.uniform(0.0, 2.0 * np.pi, n)
+    return cx + r * np.cos(t), cy + r * np.sin(t)
+
+
+def uniform_points(n, seed, lo, hi):
+    rng = np.random.Generator(np.random.Philox(key=int(seed)))
+    return rng.uniform(lo, hi, n), rng.uniform(lo, hi, n)
+
+
+# ---- lattices --------------------------------------------------------------
+def fodo_c1():
+    """24 identical FODO cells: QF(0.5 m, k1=+0.5) D(5) QD(0.5 m, k1=-0.5) D(5),
+    a space-charge location after each drift (48 per turn, 5.5 m apart)."""
+    cell = [elem(QUAD, 0.5, k1=0.5), elem(DRIFT, 5.0), elem(MARK),
+            elem(QUAD, 0.5, k1=-0.5), elem(DRIFT, 5.0), elem(MARK)]
+    return table(cell * 24)
+
+
+# Quadrupole gradients of the 72-cell ring, matched to bare tunes
+# (22.40, 20.75) at psigma = 0 by oracle/match_ring.py (Newton on the
+# one-turn matrix trace).
+C2_K1F = 0.14154544140329006
+C2_K1D = -0.13573619989395166
+C2_K2L = 0.5 * 0.2  # k2 = 0.5 m^-3 over 0.2 m
+
+
+def ring_c2_cell(k1f=C2_K1F, k1d=C2_K1D, k2l=C2_K2L):
+    """One 24 m cell: three 8 m segments, each opened by a space-charge location.
+    QF at [0,1] m, QD at [12,13] m, thin SF/SD next to them."""
+    return [
+        elem(MARK), elem(QUAD, 1.0, k1=k1f), elem(DRIFT, 1.0), elem(SEXT, k2l=+k2l), elem(DRIFT, 6.0),
+        elem(MARK), elem(DRIFT, 4.0), elem(QUAD, 1.0, k1=k1d), elem(DRIFT, 1.0), elem(SEXT, k2l=-k2l),
+        elem(DRIFT, 2.0),
+        elem(MARK), elem(DRIFT, 8.0),
+    ]
+
+
+def ring_c2(k1f=C2_K1F, k1d=C2_K1D, k2l=C2_K2L, n_cells=72):
+    """72-cell ring (3-fold symmetric: 3 x 24 identical cells), 216 SC locations."""
+    return table(ring_c2_cell(k1f, k1d, k2l) * n_cells)
+
+
+# ---- workload presets ------------------------------------------------------
+def grid_extent(sig_x, sig_y, n_sigma=5.0):
+    return (-n_sigma * sig_x, n_sigma * sig_x, -n_sigma * sig_y, n_sigma * sig_y)
+
+
+CONFIGS = {
+    # 2e4 particles, 64x64, 24-cell FODO, 48 kicks/turn, 10 turns
+    "c1": dict(n=20000, sig_x=2e-3, sig_y=2e-3, sig_px=2e-4, sig_py=2e-4, grid=64,
+               lattice="c1", n_lambda=1e11 / 20.0, turns=10),
+    # 1e6 particles, 128x128, 72-cell ring, 216 kicks/turn
+    "c2": dict(n=1000000, sig_x=4e-3, sig_y=3e-3, sig_px=2e-4, sig_py=2e-4, grid=128,
+               lattice="c2", n_lambda=1e11 / 20.0, turns=1000),
+    # 4e6 particles, 256x256, same ring
+    "c3": dict(n=4000000, sig_x=4e-3, sig_y=3e-3, sig_px=2e-4, sig_py=2e-4, grid=256,
+               lattice="c2", n_lambda=1e11 / 20.0, turns=100),
+}
+
+
+def lattice(name):
+    return {"c1": fodo_c1, "c2": ring_c2}[name]()
+
+
+def workload(name, seed=12345, n=None):
+    """(particles, beam dict, grid (nx, ny, xmin, xmax, ymin, ymax), lattice table)."""
+    c = CONFIGS[name]
+    n = c["n"] if n is None else n
+    parts = gaussian_bunch(n, seed, c["sig_x"], c["sig_y"], c["sig_px"], c["sig_py"])
+    lat = lattice(c["lattice"])
+    circ = float(lat["length"].sum())
+    b = beam(n_lambda=c["n_lambda"], circumference=circ)
+    g = c["grid"]
+    grid = (g, g) + grid_extent(c["sig_x"], c["sig_y"])
+    return parts, b, grid, lat

@@ -1,0 +1,169 @@
+"""Pins of the oracle's single-particle maps (Sec. III) against the
+Hamiltonians they come from: each map must equal a fine RK4 integration of
+Hamilton's equations of its Hamiltonian (Eq. H: exact form for the drift,
+H_approx for the quadrupole and the linear dipole), with the vector field
+taken by complex-step differentiation of H itself, and each map must be
+symplectic (M^T J M = J for its 6-D Jacobian)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_11540_gb300 import synth
+
+B = synth.beam(circumference=100.0)
+G0, B0 = B["gamma0"], B["beta0"]
+
+
+def h_drift(z):
+    x, px, y, py, sg, ps = z
+    return ps - np.sqrt(1 + 2 * ps + B0**2 * ps**2 - px**2 - py**2)
+
+
+def h_quad(k1):
+    def H(z):
+        x, px, y, py, sg, ps = z
+        return (px**2 + py**2) / 2 + ps**2 / (2 * G0**2) - (px**2 + py**2) / 2 * ps + k1 / 2 * (x**2 - y**2)
+    return H
+
+
+def h_bend(h):
+    def H(z):
+        x, px, y, py, sg, ps = z
+        return (px**2 + py**2) / 2 + ps**2 / (2 * G0**2) - h * x * ps + h * h * x * x / 2
+    return H
+
+
+def vector_field(H, z):
+    """dz/ds = J grad H, gradient by complex step."""
+    grad = np.zeros(6)
+    for k in range(6):
+        zc = z.astype(complex)
+        zc[k] += 1e-30j
+        grad[k] = H(zc).imag / 1e-30
+    # (x,px),(y,py),(sg,ps) conjugate pairs: dq/ds = dH/dp, dp/ds = -dH/dq
+    return np.array([grad[1], -grad[0], grad[3], -grad[2], grad[5], -grad[4]])
+
+
+def rk4(H, z, L, n=2000):
+    h = L / n
+    for _ in range(n):
+        k1 = vector_field(H, z)
+        k2 = vector_field(H, z + 0.5 * h * k1)
+        k3 = vector_field(H, z + 0.5 * h * k2)
+        k4 = vector_field(H, z + h * k3)
+        z = z + h / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+    return z
+
+
+def apply(elems, z):
+    st = {k: np.array([v]) for k, v in zip(("x", "px", "y", "py", "sigma", "psigma"), z)}
+    oracle.push(st, synth.table(elems), B)
+    return np.array([st[k][0] for k in ("x", "px", "y", "py", "sigma", "psigma")])
+
+
+Z0 = np.array([2e-3, -3e-4, -1.5e-3, 2e-4, 0.3, 2.5e-3])
+
+
+@pytest.mark.parametrize("case", ["drift", "qf", "qd", "bend"])
+def test_map_equals_hamiltonian_flow(case):
+    L = 1.3
+    if case == "drift":
+        e, H = synth.elem(synth.DRIFT, L), h_drift
+    elif case == "qf":
+        e, H = synth.elem(synth.QUAD, L, k1=0.8), h_quad(0.8)
+    elif case == "qd":
+        e, H = synth.elem(synth.QUAD, L, k1=-0.6), h_quad(-0.6)
+    else:
+        e, H = synth.elem(synth.BEND, L, angle=0.2), h_bend(0.2 / L)
+    got = apply([e], Z0)
+    want = rk4(H, Z0.copy(), L)
+    scale = np.array([1e-3, 1e-4, 1e-3, 1e-4, 1e-3, 1e-3])
+    assert np.max(np.abs(got - want) / scale) < 1e-9
+
+
+def jacobian(elems, z, eps=1e-6):
+    M = np.zeros((6, 6))
+    for c in range(6):
+        dz = np.zeros(6)
+        dz[c] = eps
+        M[:, c] = (apply(elems, z + dz) - apply(elems, z - dz)) / (2 * eps)
+    return M
+
+
+J = np.zeros((6, 6))
+for _k in range(3):
+    J[2 * _k, 2 * _k + 1] = 1.0
+    J[2 * _k + 1, 2 * _k] = -1.0
+
+
+@pytest.mark.parametrize("e", [
+    synth.elem(synth.DRIFT, 2.0),
+    synth.elem(synth.QUAD, 0.7, k1=1.1),
+    synth.elem(synth.QUAD, 0.7, k1=-0.9),
+    synth.elem(synth.QUAD, 0.7, k1=0.0),
+    synth.elem(synth.SEXT, k2l=3.0),
+    synth.elem(synth.BEND, 1.5, angle=0.1),
+    synth.elem(synth.RF, volt=2e5, harmonic=9.0, lag=0.3),
+])
+def test_symplectic(e):
+    M = jacobian([e], Z0)
+    assert np.max(np.abs(M.T @ J @ M - J)) < 1e-7
+    assert abs(np.linalg.det(M) - 1.0) < 1e-7
+
+
+def test_quad_tends_to_h0_drift():
+    a = apply([synth.elem(synth.QUAD, 1.0, k1=1e-13)], Z0)
+    b = apply([synth.elem(synth.QUAD, 1.0, k1=0.0)], Z0)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_sextupole_kick_values():
+    """Thin kick of V = k2 (x^3 - 3 x y^2)/6: dpx = -k2l/2 (x^2-y^2), dpy = k2l x y."""
+    z = apply([synth.elem(synth.SEXT, k2l=2.0)], Z0)
+    x, y = Z0[0], Z0[2]
+    assert z[1] - Z0[1] == pytest.approx(-(x * x - y * y), rel=1e-12)
+    assert z[3] - Z0[3] == pytest.approx(2.0 * x * y, rel=1e-12)
+
+
+def test_bare_tune_trace_vs_tracked_phase_advance():
+    """Tune from cos mu = Tr(M)/2 equals the tracked mean phase advance of a
+    small-amplitude particle (Sec. V tune definition)."""
+    lat = synth.fodo_c1()
+    b = synth.beam(circumference=264.0)
+    M = oracle.one_turn_matrix(lat, b)
+    mux, bx, ax = oracle.twiss_from_matrix(M[:2, :2])
+    muy, by, ay = oracle.twiss_from_matrix(M[2:, 2:])
+    st = {k: np.zeros(3) for k in ("x", "px", "y", "py", "sigma", "psigma")}
+    st["x"][:] = [1e-6, 2e-6, -1e-6]
+    st["y"][:] = [1e-6, -3e-6, 2e-6]
+    pa = oracle.PhaseAdvance(bx, ax, by, ay)
+    for t in range(60):
+        pa(t, st)
+        oracle.push(st, lat, b)
+    qx, qy = pa.tunes()
+    assert np.allclose(qx, mux / (2 * np.pi), atol=1e-9)
+    assert np.allclose(qy, muy / (2 * np.pi), atol=1e-9)
+
+
+def test_rms_size_gives_beta():
+    """Sec. V: for a matched Gaussian, sigma(s)^2 / eps = beta(s), with beta
+    propagated from the start by the transfer matrix."""
+    lat = synth.fodo_c1()
+    b = synth.beam(circumference=264.0)
+    M = oracle.one_turn_matrix(lat, b)
+    _, bx, ax = oracle.twiss_from_matrix(M[:2, :2])
+    eps = 4e-7
+    n = 200000
+    rng = np.random.default_rng(3)
+    u, v = rng.standard_normal(n), rng.standard_normal(n)
+    x = np.sqrt(eps * bx) * u
+    px = np.sqrt(eps / bx) * (v - ax * u)
+    st = {"x": x, "px": px, "y": np.zeros(n), "py": np.zeros(n), "sigma": np.zeros(n), "psigma": np.zeros(n)}
+    part = lat[:2]  # QF + drift
+    oracle.push(st, part, b)
+    Mp = oracle.one_turn_matrix(part, b)[:2, :2]
+    g0 = (1 + ax * ax) / bx
+    b1 = Mp[0, 0] ** 2 * bx - 2 * Mp[0, 0] * Mp[0, 1] * ax + Mp[0, 1] ** 2 * g0
+    eps_meas = oracle.emittances(st)[0]
+    assert np.var(st["x"]) / eps_meas == pytest.approx(b1, rel=0.01)  # sampling error ~ 1/sqrt(n)
+    assert eps_meas == pytest.approx(eps, rel=0.01)
