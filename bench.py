@@ -1,0 +1,306 @@
+"""Throughput of the 2-D PIC space-charge step on one GB300.
+
+Metric: particle-SC-kicks/s = particles x space-charge kicks / time, one kick
+being deposit + open-boundary solve + gather/kick + push to the next
+space-charge location.  Workload (default): 1e6 macroparticles, 128x128 grid
+(256x256 padded), the synthetic 72-cell FODO ring with 216 kicks per turn.
+One bench step = one turn (216 kicks) through sc_track_turns.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|tf32x3]
+  python bench.py --impl reference      # the FP64 CPU oracle, bounded sample
+
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-SC-kicks/s at 1e6 particles,128² grid; batched split-TF32 vs plain FP64"
+UNIT = "particle-kicks/s"
+WORKLOAD = ("c2: 1e6 macroparticles (4D Gaussian, sigma_x=4 mm, sigma_y=3 mm, 0.2 mrad, 4-sigma cut), "
+            "128x128 grid over +-5 sigma (256x256 padded open-boundary solve), 72-cell FODO ring with "
+            "2 thin-sextupole families, bare tunes (22.40, 20.75), 216 SC kicks/turn")
+
+# FP64 flops per particle and element/kick, counted from the kernel's formulas
+# (multiply, add and fused multiply-add = 2); see the roofline section of the design doc.
+FP64_FLOPS = {"kick": 26, "deposit": 6, "drift": 22, "quad": 70, "sext": 7, "bend": 40, "rf": 30}
+NOMINAL_FP64_TFLOPS = 1.25  # GB300 dense FP64 (profiling recipe table)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--cpu-kicks", type=int, default=24, help="oracle sample size in kicks")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- helpers
+def segment_flops(lat):
+    """FP64 flops per particle per turn from the element mix, and kicks/turn."""
+    from paper_2010_11540_gb300 import synth
+    t = lat["type"]
+    n_k = int((t == synth.MARK).sum())
+    per = {synth.DRIFT: "drift", synth.QUAD: "quad", synth.SEXT: "sext", synth.BEND: "bend", synth.RF: "rf"}
+    f = n_k * (FP64_FLOPS["kick"] + FP64_FLOPS["deposit"])
+    for code, name in per.items():
+        f += int((t == code).sum()) * FP64_FLOPS[name]
+    return f, n_k
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(config, n_kicks):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample:
+    the full particle set through the first n_kicks kicks of turn 1."""
+    import oracle
+    from paper_2010_11540_gb300 import synth
+    parts, b, grid, lat = synth.workload(config)
+    g = oracle.Geometry(*grid)
+    st = oracle.copy_state(parts)
+    oracle.lib()
+    t0 = time.perf_counter()
+    done = oracle.track(g, st, b, lat, 1, max_kicks=n_kicks)
+    dt = time.perf_counter() - t0
+    n = len(parts["x"])
+    return {"value": n * done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{config} full particle set ({n}), first {done} SC kicks of turn 1, {dt:.1f} s"}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    kicks = max(1, args.cpu_kicks // 4)
+    for _ in range(args.warmup):
+        cpu_baseline(args.config, 1)
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.config, kicks))
+    wall = time.perf_counter() - t0
+    value = statistics.mean(v["value"] for v in vals)
+    cb = dict(vals[0])
+    cb["value"] = value
+    cb["sample"] = f"each step: {cb['sample']}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "step": f"{kicks} SC kicks on the CPU oracle"},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_2010_11540_gb300 import build, sc, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    sc.load()
+    stream = torch.cuda.Stream()
+    parts, b, grid, lat = synth.workload(args.config, seed=12345 + rank)
+    n = len(parts["x"])
+    keys = ("x", "px", "y", "py", "sigma", "psigma")
+    dev = {k: torch.from_numpy(parts[k]).cuda() for k in keys}
+    g = sc.create_grid(*grid, precision=args.precision, stream=stream)
+    flops_turn, n_kicks = segment_flops(lat)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sc.track_turns(g, dev, b, lat, 1)
+        stream.synchronize()
+        # ---------------- timed region: K turns, L2 flushed between turns
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        clocks = ClockSampler(local)
+        clocks.start()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            sc.track_turns(g, dev, b, lat, 1)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t_wall
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(c) for a, c in ev]
+    ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * n_kicks * args.steps / (ms * 1e-3)
+
+    # ---------------- dominant kernel (kick + push + fused deposit), timed alone per segment
+    head, kicks = _segments(lat, synth)
+    kp_ms = []
+    with torch.cuda.stream(stream):
+        for rep in range(2):
+            for L, seg in kicks[:3]:
+                for _ in range(8):
+                    sc.solve(g)
+                    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    sc.kick_push(g, dev, b, L, seg, next_grid=g)
+                    c.record(stream)
+                    if rep == 1:
+                        kp_ms.append((a, c, seg))
+        stream.synchronize()
+    times = [a.elapsed_time(c) for a, c, _ in kp_ms]
+    seg_flops = []
+    for _, _, seg in kp_ms:
+        f = FP64_FLOPS["kick"] + FP64_FLOPS["deposit"]
+        for e in seg:
+            f += FP64_FLOPS[{0: "drift", 1: "quad", 2: "sext", 3: "bend", 4: "rf"}.get(int(e["type"]), "kick")] \
+                if int(e["type"]) != synth.MARK else 0
+        seg_flops.append(f)
+    kp_avg_ms = statistics.mean(times)
+    achieved = statistics.mean(seg_flops) * n / (kp_avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "kick_push_kernel (gather+kick, push, fused CIC deposit)",
+                "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "peak_source": "nominal GB300 dense FP64 1.25 TFLOP/s (profiling recipe); probe measured 1.19",
+                "avg_launch_ms": kp_avg_ms, "fp64_flops_per_particle_kick": statistics.mean(seg_flops)}
+
+    # ---------------- end to end: host buffers through the public API
+    pinned = {k: torch.from_numpy(parts[k].copy()).pin_memory() for k in keys}
+    e2e_steps = max(2, args.steps // 2)
+    with torch.cuda.stream(stream):
+        sc.track_turns_host(g, pinned, b, lat, 1, device_state=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            sc.track_turns_host(g, pinned, b, lat, 1, device_state=dev)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e = {"value": n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
+           "d2h_bytes_per_step": 6 * 8 * n}
+
+    solve_kernels = 3 if args.precision == "fp64" else 3
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one turn = 216 SC kicks via sc_track_turns (CUDA graph)",
+                       "solve": "fp64 FFT convolution" if args.precision == "fp64" else
+                       "tf32x3 DFT GEMMs on tcgen05", "particles": n, "grid": [g.nx, g.ny],
+                       "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "gpu_launches": args.steps * n_kicks * (solve_kernels + 1),
+            "wall_s_timed": wall}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_kicks)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _segments(lat, synth):
+    marks = [i for i in range(len(lat)) if int(lat["type"][i]) == synth.MARK]
+    s = np.concatenate([[0.0], np.cumsum(lat["length"])])
+    out = []
+    for k, m in enumerate(marks):
+        end = marks[k + 1] if k + 1 < len(marks) else len(lat)
+        prev = s[marks[k - 1]] if k > 0 else s[marks[-1]] - s[-1]
+        out.append((float(s[m] - prev), lat[m + 1:end]))
+    return lat[: marks[0]], out
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

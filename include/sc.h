@@ -1,0 +1,155 @@
+/*
+ * sc.h -- C-ABI of libsc, the GB300 (sm_103a) 2-D particle-in-cell
+ * space-charge step for proton-ring tracking (arXiv:2010.11540).
+ *
+ * The calls follow the paper's PIC loop (Sec. I: assign charge to the grid,
+ * solve Poisson's equation, move particles in the field) with the space-charge
+ * kick of Sec. IV and the single-particle maps of Sec. III.
+ *
+ * Conventions
+ *  - Every call returns sc_status: SC_OK (0) or a negative error code.  No
+ *    C++ exception crosses this boundary.  sc_last_error() returns a text for
+ *    the most recent failure of the calling thread.
+ *  - Device pointers are plain CUDA device addresses on the current device.
+ *    Particle arrays are owned by the caller; libsc never frees them.  Grids
+ *    own their device buffers (charge, fields, Green's-function spectra,
+ *    scratch, captured graphs) and release them in sc_destroy_grid().
+ *  - All work on a grid is enqueued on the CUDA stream given to
+ *    sc_create_grid() (NULL = legacy default stream) and is asynchronous,
+ *    except the calls documented as synchronous (sc_grid_read,
+ *    sc_grid_write_charge, sc_track_turns when diag != NULL).  Errors raised
+ *    inside kernels surface at the next synchronous call.
+ *  - Particle state is SoA float64: x [m], px = Px/p0, y [m], py = Py/p0,
+ *    sigma = s - c beta0 t [m], psigma (Sec. III, Eq. H).
+ */
+#ifndef SC_H
+#define SC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int sc_status;
+
+#define SC_OK 0
+#define SC_ERR_ARG (-1)         /* bad argument (null, size, geometry)        */
+#define SC_ERR_CUDA (-2)        /* a CUDA runtime call failed                 */
+#define SC_ERR_OOM (-3)         /* device allocation failed                   */
+#define SC_ERR_OVERFLOW (-4)    /* more particles than the int64 charge grid can hold */
+#define SC_ERR_TIMEOUT (-5)     /* a bounded device wait ran out              */
+#define SC_ERR_NAN (-6)         /* non-finite particle state seen             */
+#define SC_ERR_UNSUPPORTED (-7) /* grid size / precision not supported        */
+
+/* Poisson-solve arithmetic (sc_create_grid `precision`). */
+#define SC_SOLVE_FP64 0   /* float64 FFT convolution (the plain form)           */
+#define SC_SOLVE_TF32X3 1 /* DFT as tcgen05 GEMMs, 3-term split TF32, FP32 acc. */
+
+/* Element types (sc_element.type). */
+#define SC_DRIFT 0 /* exact drift, Sec. III-A                                  */
+#define SC_QUAD 1  /* thick quadrupole with chromatic factor, Sec. III-B       */
+#define SC_SEXT 2  /* thin sextupole kick (V-step of Eq. Sym2), Sec. III-C     */
+#define SC_BEND 3  /* linear sector dipole from H_approx, Sec. III             */
+#define SC_RF 4    /* thin RF cavity                                           */
+#define SC_MARK 5  /* space-charge location (kick point), Sec. V               */
+
+/* Largest macroparticle count one grid may hold: each particle deposits
+ * exactly 2^40 fixed-point units, so 2^23 particles fill an int64. */
+#define SC_MAX_PARTICLES_PER_GRID (1LL << 23)
+
+typedef struct sc_grid sc_grid; /* opaque */
+
+/* Caller-owned particle arrays (device pointers, n float64 each). */
+typedef struct {
+  double *x, *px, *y, *py, *sigma, *psigma;
+  int64_t n;
+} sc_particles;
+
+/* Reference-particle and beam constants.
+ * gamma0, beta0: reference Lorentz factors; n_lambda: line density [protons/m]
+ * used by the transverse kick; r_p: classical proton radius [m];
+ * circumference [m] and mass_ev (m c^2 [eV]) are used by SC_RF only. */
+typedef struct {
+  double gamma0, beta0, n_lambda, r_p, circumference, mass_ev;
+} sc_beam;
+
+/* One lattice element, 64 bytes.
+ * length [m] (0 for thin elements); k1 [m^-2] (SC_QUAD; >0 focuses x);
+ * k2l [m^-2] integrated sextupole strength (SC_SEXT); angle [rad] (SC_BEND);
+ * volt [V], harmonic, lag [rad] (SC_RF: dpsigma = volt/(beta0^2 E0) *
+ * sin(lag - 2 pi harmonic sigma / circumference)). */
+typedef struct {
+  int32_t type;
+  int32_t pad;
+  double length, k1, k2l, angle, volt, harmonic, lag;
+} sc_element;
+
+/* Create a transverse grid of nx x ny nodes at x_i = xmin + i hx,
+ * hx = (xmax - xmin)/(nx - 1) (same for y), with the open-boundary
+ * (Hockney zero-padded) Poisson solver of the given precision.  Builds the
+ * Green's-function spectra on the device (synchronous on `stream`).
+ * nx, ny: 8..512 and powers of two for SC_SOLVE_FP64; multiples of 32 in
+ * 32..256 for SC_SOLVE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
+ * SC_ERR_OOM, SC_ERR_CUDA.  *out is set only on success. */
+sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
+                         double ymax, int precision, void *stream);
+
+/* Release a grid and everything it owns (synchronises its stream). NULL ok. */
+sc_status sc_destroy_grid(sc_grid *g);
+
+/* CIC charge deposition, Sec. IV-A: zero the grid's int64 charge Q, then add
+ * each particle's four fixed-point weights (2^-20 per axis, 2^40 per
+ * particle).  Particles outside [xmin, xmax) x [ymin, ymax) (and non-finite
+ * ones) deposit nothing and are counted (sc_grid_read's n_out).
+ * Errors: SC_ERR_ARG, SC_ERR_OVERFLOW (n > SC_MAX_PARTICLES_PER_GRID). */
+sc_status sc_deposit(sc_grid *g, const sc_particles *p);
+
+/* Open-boundary Poisson solve (Sec. IV, Eq. poisson3D, free-space part):
+ * phi = G * q with G = -ln r, q = Q 2^-40 / N (N = particle count of the last
+ * deposit), and node fields E = -grad phi by centred differences; stored as
+ * interleaved (Ex, Ey) float64 per node, in units of 1/m per unit line charge. */
+sc_status sc_solve(sc_grid *g);
+
+/* Fused space-charge step for one location (Sec. IV kick, Sec. III maps):
+ * for every particle, gather E of grid g bilinearly at (x, y), kick
+ * px += K L_sc Ex, py += K L_sc Ey with K = 2 r_p n_lambda / (beta0^2 gamma0^3)
+ * (no kick when L_sc == 0 or the particle is outside g), push through
+ * elems[0..n_elems) (host array, copied at the call), and, when next != NULL,
+ * deposit the new positions into `next` as sc_deposit does (next may be g).
+ * Errors: SC_ERR_ARG, SC_ERR_OVERFLOW. */
+sc_status sc_kick_push(sc_grid *g, const sc_particles *p, const sc_beam *b, double L_sc,
+                       const sc_element *elems, int n_elems, sc_grid *next);
+
+/* Track n_turns turns of the ring `lattice` (host array of n_elems elements;
+ * SC_MARK entries are the space-charge locations, the kick length being the
+ * path length since the previous marker, cyclically).  Each marker runs
+ * deposit -> solve -> kick, then the elements up to the next marker are
+ * pushed; elements before the first marker are pushed without a kick.  One
+ * turn is captured once as a CUDA graph and replayed.  When diag != NULL
+ * (host, n_turns x 14 doubles) the beam moments at the start of every turn
+ * are written there: means of (x, px, y, py, sigma, psigma), then central
+ * <xx>, <x px>, <px px>, <yy>, <y py>, <py py>, <sigma sigma>,
+ * <psigma psigma>; the call is then synchronous.
+ * Errors: SC_ERR_ARG, SC_ERR_OVERFLOW, SC_ERR_CUDA. */
+sc_status sc_track_turns(sc_grid *g, const sc_particles *p, const sc_beam *b,
+                         const sc_element *lattice, int n_elems, int n_turns, double *diag);
+
+/* Synchronous copy-out of a grid's state into host arrays (each may be NULL):
+ * Q (nx*ny int64, row-major [j][i]), Ex and Ey (nx*ny float64), and n_out =
+ * particles found outside the grid by deposits since the grid was created. */
+sc_status sc_grid_read(sc_grid *g, int64_t *Q, double *Ex, double *Ey, int64_t *n_out);
+
+/* Synchronous upload of a charge grid Q (host, nx*ny int64) and the particle
+ * count N used to normalise it, e.g. to solve a given charge. */
+sc_status sc_grid_write_charge(sc_grid *g, const int64_t *Q, int64_t n_particles);
+
+/* Text of the last error on the calling thread (always NUL-terminated). */
+sc_status sc_last_error(char *buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SC_H */

@@ -1,0 +1,439 @@
+// C-ABI of libsc (include/sc.h): grid lifecycle, the PIC-loop calls of
+// Sec. I (deposit, solve, kick + push) and the turn driver that captures one
+// turn of the ring as a CUDA graph and replays it.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sc_internal.cuh"
+
+namespace sc {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+sc_status set_error(sc_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+sc_status cuda_error(cudaError_t e, const char* what) {
+  char buf[512];
+  std::snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  if (e == cudaErrorMemoryAllocation) return set_error(SC_ERR_OOM, buf);
+  return set_error(SC_ERR_CUDA, buf);
+}
+
+// Captured turn of a ring for one (grid, particles, beam, lattice) set.
+struct TrackPlan {
+  std::vector<unsigned char> key;
+  sc_element* d_elems = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  bool has_head = false;
+  bool diag = false;
+  int n_kicks = 0;
+  double* partial = nullptr;   // moments partial sums
+  double** d_base = nullptr;   // device cell holding the diag output pointer
+  int* d_turn = nullptr;       // device turn counter
+  double* d_diag = nullptr;    // [cap][14]
+  int diag_cap = 0;
+};
+
+namespace {
+
+void destroy_plan(TrackPlan* t) {
+  if (!t) return;
+  if (t->exec) cudaGraphExecDestroy(t->exec);
+  if (t->graph) cudaGraphDestroy(t->graph);
+  cudaFree(t->d_elems);
+  cudaFree(t->partial);
+  cudaFree(t->d_base);
+  cudaFree(t->d_turn);
+  cudaFree(t->d_diag);
+  delete t;
+}
+
+sc_status check_particles(const sc_particles* p) {
+  if (!p) return set_error(SC_ERR_ARG, "particles is NULL");
+  if (p->n < 0) return set_error(SC_ERR_ARG, "negative particle count");
+  if (p->n > 0 && (!p->x || !p->px || !p->y || !p->py || !p->sigma || !p->psigma))
+    return set_error(SC_ERR_ARG, "particle array pointer is NULL");
+  if (p->n > SC_MAX_PARTICLES_PER_GRID)
+    return set_error(SC_ERR_OVERFLOW, "more than 2^23 particles on one grid would overflow the int64 charge");
+  return SC_OK;
+}
+
+void fill_beam(KPParams& P, const sc_beam* b) {
+  P.beta0_sq = b->beta0 * b->beta0;
+  P.inv_gamma0_sq = 1.0 / (b->gamma0 * b->gamma0);
+  const double e0 = b->gamma0 * b->mass_ev;
+  P.rf_scale = (e0 > 0.0) ? 1.0 / (P.beta0_sq * e0) : 0.0;
+  P.two_pi_over_c = (b->circumference > 0.0) ? 2.0 * M_PI / b->circumference : 0.0;
+}
+
+// K = 2 r_p N_lambda / (beta0^2 gamma0^3): the transverse kick of Sec. IV per
+// unit length and unit normalised field.
+double kick_strength(const sc_beam* b) {
+  return 2.0 * b->r_p * b->n_lambda / (b->beta0 * b->beta0 * b->gamma0 * b->gamma0 * b->gamma0);
+}
+
+KPParams base_params(const sc_particles* p, const sc_beam* b) {
+  KPParams P;
+  std::memset(&P, 0, sizeof P);
+  P.x = p->x;
+  P.px = p->px;
+  P.y = p->y;
+  P.py = p->py;
+  P.sg = p->sigma;
+  P.ps = p->psigma;
+  P.n = p->n;
+  fill_beam(P, b);
+  return P;
+}
+
+void set_kick(KPParams& P, const sc_grid* g, double kl) {
+  P.do_kick = (kl != 0.0);
+  P.gk = g->geom;
+  P.E = g->E;
+  P.kl = kl;
+}
+
+void set_deposit(KPParams& P, sc_grid* d) {
+  P.do_deposit = 1;
+  P.gd = d->geom;
+  P.Q = d->Q;
+  P.n_out = d->n_out;
+}
+
+sc_status solve_dispatch(sc_grid* g) {
+  if (g->precision == SC_SOLVE_TF32X3) return tf32_solve(g);
+  return fft64_solve(g);
+}
+
+sc_status stage_elements(sc_grid* g, const sc_element* elems, int n) {
+  if (n <= 0) return SC_OK;
+  if (n > g->el_stage_cap) {
+    cudaFree(g->el_stage);
+    g->el_stage = nullptr;
+    g->el_stage_cap = 0;
+    SC_CUDA(cudaMalloc(&g->el_stage, (size_t)n * sizeof(sc_element)));
+    g->el_stage_cap = n;
+  }
+  SC_CUDA(cudaMemcpyAsync(g->el_stage, elems, (size_t)n * sizeof(sc_element), cudaMemcpyHostToDevice, g->stream));
+  return SC_OK;
+}
+
+}  // namespace
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+sc_status sc_last_error(char* buf, size_t n) {
+  if (!buf || n == 0) return SC_ERR_ARG;
+  std::snprintf(buf, n, "%s", g_last_error.c_str());
+  return SC_OK;
+}
+
+sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                         int precision, void* stream) {
+  if (!out) return set_error(SC_ERR_ARG, "out is NULL");
+  if (nx < 2 || ny < 2) return set_error(SC_ERR_ARG, "grid needs at least 2x2 nodes");
+  if (!(xmax > xmin) || !(ymax > ymin) || !std::isfinite(xmin) || !std::isfinite(xmax) || !std::isfinite(ymin) ||
+      !std::isfinite(ymax))
+    return set_error(SC_ERR_ARG, "grid extent must be finite with xmax > xmin, ymax > ymin");
+  if (precision != SC_SOLVE_FP64 && precision != SC_SOLVE_TF32X3)
+    return set_error(SC_ERR_UNSUPPORTED, "unknown solve precision");
+  sc_grid* g = new (std::nothrow) sc_grid();
+  if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
+  std::memset(g, 0, sizeof *g);
+  g->nx = nx;
+  g->ny = ny;
+  g->precision = precision;
+  g->xmin = xmin;
+  g->xmax = xmax;
+  g->ymin = ymin;
+  g->ymax = ymax;
+  g->hx = (xmax - xmin) / (nx - 1);
+  g->hy = (ymax - ymin) / (ny - 1);
+  g->geom.nx = nx;
+  g->geom.ny = ny;
+  g->geom.xmin = xmin;
+  g->geom.ymin = ymin;
+  g->geom.inv_hx = 1.0 / g->hx;
+  g->geom.inv_hy = 1.0 / g->hy;
+  g->geom.xlast = (double)(nx - 1);
+  g->geom.ylast = (double)(ny - 1);
+  sc_status st = SC_OK;
+  cudaError_t e = cudaGetDevice(&g->device);
+  if (e != cudaSuccess) {
+    st = cuda_error(e, "cudaGetDevice");
+    delete g;
+    return st;
+  }
+  if (stream) {
+    g->stream = (cudaStream_t)stream;
+  } else {
+    // Graph capture needs a non-legacy stream; this one still orders with the legacy default stream.
+    e = cudaStreamCreate(&g->stream);
+    if (e != cudaSuccess) {
+      st = cuda_error(e, "cudaStreamCreate");
+      delete g;
+      return st;
+    }
+    g->own_stream = true;
+  }
+  const size_t cells = (size_t)nx * ny;
+  if ((e = cudaMalloc(&g->Q, cells * 8)) != cudaSuccess || (e = cudaMalloc(&g->E, cells * sizeof(double2))) != cudaSuccess ||
+      (e = cudaMalloc(&g->n_out, 8)) != cudaSuccess) {
+    st = cuda_error(e, "cudaMalloc(grid)");
+    sc_destroy_grid(g);
+    return st;
+  }
+  cudaMemsetAsync(g->Q, 0, cells * 8, g->stream);
+  cudaMemsetAsync(g->E, 0, cells * sizeof(double2), g->stream);
+  cudaMemsetAsync(g->n_out, 0, 8, g->stream);
+  const bool tile = deposit_uses_tile(g);
+  g->dep_blocks = deposit_blocks_for(tile ? (int)(cells * 8) : 0, tile);
+  g->kp_blocks = kick_push_blocks_for(tile ? (int)(cells * 8) : 0, tile);
+  g->kp_blocks_plain = kick_push_blocks_for(0, false);
+  st = (precision == SC_SOLVE_TF32X3) ? tf32_create(g) : fft64_create(g);
+  if (st == SC_OK) {
+    e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) st = cuda_error(e, "sc_create_grid");
+  }
+  if (st != SC_OK) {
+    sc_destroy_grid(g);
+    return st;
+  }
+  *out = g;
+  return SC_OK;
+}
+
+sc_status sc_destroy_grid(sc_grid* g) {
+  if (!g) return SC_OK;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  destroy_plan(g->track);
+  if (g->precision == SC_SOLVE_TF32X3)
+    tf32_destroy(g);
+  else
+    fft64_destroy(g);
+  cudaFree(g->Q);
+  cudaFree(g->E);
+  cudaFree(g->n_out);
+  cudaFree(g->el_stage);
+  if (g->own_stream) cudaStreamDestroy(g->stream);
+  delete g;
+  return SC_OK;
+}
+
+sc_status sc_deposit(sc_grid* g, const sc_particles* p) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  sc_status st = check_particles(p);
+  if (st) return st;
+  SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * 8, g->stream));
+  g->n_particles = p->n;
+  if (p->n == 0) return SC_OK;
+  return launch_deposit(g, p);
+}
+
+sc_status sc_solve(sc_grid* g) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  return solve_dispatch(g);
+}
+
+sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, double L_sc, const sc_element* elems,
+                       int n_elems, sc_grid* next) {
+  if (!g || !b) return set_error(SC_ERR_ARG, "grid or beam is NULL");
+  if (n_elems < 0 || (n_elems > 0 && !elems)) return set_error(SC_ERR_ARG, "bad element list");
+  if (!std::isfinite(L_sc)) return set_error(SC_ERR_ARG, "L_sc must be finite");
+  sc_status st = check_particles(p);
+  if (st) return st;
+  for (int k = 0; k < n_elems; ++k)
+    if (elems[k].type < SC_DRIFT || elems[k].type > SC_MARK) return set_error(SC_ERR_ARG, "unknown element type");
+  if ((st = stage_elements(g, elems, n_elems))) return st;
+  if (next) {
+    SC_CUDA(cudaMemsetAsync(next->Q, 0, (size_t)next->nx * next->ny * 8, g->stream));
+    next->n_particles = p->n;
+  }
+  if (p->n == 0) return SC_OK;
+  KPParams P = base_params(p, b);
+  set_kick(P, g, kick_strength(b) * L_sc);
+  if (next) set_deposit(P, next);
+  P.el = g->el_stage;
+  P.n_elem = n_elems;
+  return launch_kick_push(P, next, next ? next->kp_blocks : g->kp_blocks_plain, g->stream);
+}
+
+sc_status sc_grid_read(sc_grid* g, int64_t* Q, double* Ex, double* Ey, int64_t* n_out) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  const size_t cells = (size_t)g->nx * g->ny;
+  if (Q) SC_CUDA(cudaMemcpy(Q, g->Q, cells * 8, cudaMemcpyDeviceToHost));
+  if (Ex || Ey) {
+    std::vector<double2> E(cells);
+    SC_CUDA(cudaMemcpy(E.data(), g->E, cells * sizeof(double2), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < cells; ++c) {
+      if (Ex) Ex[c] = E[c].x;
+      if (Ey) Ey[c] = E[c].y;
+    }
+  }
+  if (n_out) {
+    unsigned long long v = 0;
+    SC_CUDA(cudaMemcpy(&v, g->n_out, 8, cudaMemcpyDeviceToHost));
+    *n_out = (int64_t)v;
+  }
+  return SC_OK;
+}
+
+sc_status sc_grid_write_charge(sc_grid* g, const int64_t* Q, int64_t n_particles) {
+  if (!g || !Q) return set_error(SC_ERR_ARG, "grid or Q is NULL");
+  if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  SC_CUDA(cudaMemcpy(g->Q, Q, (size_t)g->nx * g->ny * 8, cudaMemcpyHostToDevice));
+  g->n_particles = n_particles;
+  return SC_OK;
+}
+
+sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, const sc_element* lattice, int n_elems,
+                         int n_turns, double* diag) {
+  if (!g || !b) return set_error(SC_ERR_ARG, "grid or beam is NULL");
+  if (n_turns < 0 || n_elems < 0 || (n_elems > 0 && !lattice)) return set_error(SC_ERR_ARG, "bad lattice/turns");
+  sc_status st = check_particles(p);
+  if (st) return st;
+  for (int k = 0; k < n_elems; ++k)
+    if (lattice[k].type < SC_DRIFT || lattice[k].type > SC_MARK) return set_error(SC_ERR_ARG, "unknown element type");
+  if (n_turns == 0 || p->n == 0) return SC_OK;
+
+  // ---- key of the captured plan ------------------------------------------------
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* v, size_t n) {
+    const unsigned char* c = (const unsigned char*)v;
+    key.insert(key.end(), c, c + n);
+  };
+  put(p, sizeof *p);
+  put(b, sizeof *b);
+  put(&n_elems, sizeof n_elems);
+  if (n_elems) put(lattice, (size_t)n_elems * sizeof(sc_element));
+  const int want_diag = diag != nullptr;
+  put(&want_diag, sizeof want_diag);
+
+  TrackPlan* T = g->track;
+  if (!T || T->key != key) {
+    destroy_plan(T);
+    g->track = nullptr;
+    T = new (std::nothrow) TrackPlan();
+    if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
+    T->key = key;
+    T->diag = want_diag;
+    g->track = T;
+    // ---- segments: head (before the first marker) and one per marker -----------
+    std::vector<int> marks;
+    std::vector<double> s(n_elems + 1, 0.0);
+    for (int k = 0; k < n_elems; ++k) {
+      s[k + 1] = s[k] + lattice[k].length;
+      if (lattice[k].type == SC_MARK) marks.push_back(k);
+    }
+    const double circ = s[n_elems];
+    T->n_kicks = (int)marks.size();
+    T->has_head = marks.empty() ? true : marks[0] > 0;
+    if (n_elems) SC_CUDA(cudaMalloc(&T->d_elems, (size_t)n_elems * sizeof(sc_element)));
+    if (n_elems)
+      SC_CUDA(cudaMemcpy(T->d_elems, lattice, (size_t)n_elems * sizeof(sc_element), cudaMemcpyHostToDevice));
+    if (want_diag) {
+      SC_CUDA(cudaMalloc(&T->partial, (size_t)moments_blocks() * 14 * sizeof(double)));
+      SC_CUDA(cudaMalloc(&T->d_base, sizeof(double*)));
+      SC_CUDA(cudaMalloc(&T->d_turn, sizeof(int)));
+    }
+    g->n_particles = p->n;
+    const double K = kick_strength(b);
+    // ---- capture one turn ------------------------------------------------------
+    SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    sc_status cst = SC_OK;
+    if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, g->stream);
+    const size_t qbytes = (size_t)g->nx * g->ny * 8;
+    if (!cst && T->has_head) {
+      KPParams P = base_params(p, b);
+      P.el = T->d_elems;
+      P.n_elem = marks.empty() ? n_elems : marks[0];
+      if (!marks.empty()) {
+        set_deposit(P, g);
+        if (cudaMemsetAsync(g->Q, 0, qbytes, g->stream) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "memset");
+      }
+      if (!cst) cst = launch_kick_push(P, marks.empty() ? nullptr : g, marks.empty() ? g->kp_blocks_plain : g->kp_blocks, g->stream);
+    }
+    for (size_t k = 0; !cst && k < marks.size(); ++k) {
+      const int m = marks[k];
+      const int end = (k + 1 < marks.size()) ? marks[k + 1] : n_elems;
+      const double prev = (k > 0) ? s[marks[k - 1]] : s[marks.back()] - circ;
+      cst = solve_dispatch(g);
+      if (cst) break;
+      KPParams P = base_params(p, b);
+      set_kick(P, g, K * (s[m] - prev));
+      P.el = T->d_elems + m + 1;
+      P.n_elem = end - m - 1;
+      const bool dep = (k + 1 < marks.size()) || !T->has_head;
+      if (dep) {
+        set_deposit(P, g);
+        if (cudaMemsetAsync(g->Q, 0, qbytes, g->stream) != cudaSuccess) {
+          cst = set_error(SC_ERR_CUDA, "memset");
+          break;
+        }
+      }
+      cst = launch_kick_push(P, dep ? g : nullptr, dep ? g->kp_blocks : g->kp_blocks_plain, g->stream);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+    if (cst) {
+      if (graph) cudaGraphDestroy(graph);
+      destroy_plan(T);
+      g->track = nullptr;
+      return cst;
+    }
+    if (ce != cudaSuccess) {
+      destroy_plan(T);
+      g->track = nullptr;
+      return cuda_error(ce, "cudaStreamEndCapture");
+    }
+    T->graph = graph;
+    ce = cudaGraphInstantiate(&T->exec, graph, 0);
+    if (ce != cudaSuccess) {
+      destroy_plan(T);
+      g->track = nullptr;
+      return cuda_error(ce, "cudaGraphInstantiate");
+    }
+  }
+
+  // ---- run -------------------------------------------------------------------------
+  if (T->diag) {
+    if (n_turns > T->diag_cap) {
+      cudaFree(T->d_diag);
+      T->d_diag = nullptr;
+      SC_CUDA(cudaMalloc(&T->d_diag, (size_t)n_turns * 14 * sizeof(double)));
+      T->diag_cap = n_turns;
+    }
+    SC_CUDA(cudaMemcpyAsync(T->d_base, &T->d_diag, sizeof(double*), cudaMemcpyHostToDevice, g->stream));
+    SC_CUDA(cudaMemsetAsync(T->d_turn, 0, sizeof(int), g->stream));
+  }
+  g->n_particles = p->n;
+  if (!T->has_head && T->n_kicks > 0) {
+    // charge at the first space-charge location of the first turn
+    SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * 8, g->stream));
+    if ((st = launch_deposit(g, p))) return st;
+  }
+  for (int t = 0; t < n_turns; ++t) SC_CUDA(cudaGraphLaunch(T->exec, g->stream));
+  if (T->diag) {
+    SC_CUDA(cudaMemcpyAsync(diag, T->d_diag, (size_t)n_turns * 14 * sizeof(double), cudaMemcpyDeviceToHost,
+                            g->stream));
+    SC_CUDA(cudaStreamSynchronize(g->stream));
+  }
+  return SC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// Stand-alone CIC charge deposition (Sec. IV-A): per-block shared-memory
+// int64 tile, flushed once per block into the global grid.
+#include "cic.cuh"
+
+namespace sc {
+
+namespace {
+
+constexpr int kDepThreads = 512;
+
+template <bool TILE>
+__global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __restrict__ x,
+                                                               const double* __restrict__ y, int64_t n,
+                                                               GridGeom g, unsigned long long* Q,
+                                                               unsigned long long* n_out) {
+  extern __shared__ unsigned long long tile[];
+  const int cells = g.nx * g.ny;
+  if (TILE) {
+    tile_zero(tile, cells);
+    __syncthreads();
+  }
+  unsigned long long* dst = TILE ? tile : Q;
+  unsigned int out = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    Cell c;
+    if (locate(g, __ldg(x + p), __ldg(y + p), c))
+      deposit4(dst, g.nx, c);
+    else
+      ++out;
+  }
+  count_out(out, n_out);
+  if (TILE) {
+    __syncthreads();
+    tile_flush(tile, Q, cells);
+  }
+}
+
+}  // namespace
+
+bool deposit_uses_tile(const sc_grid* g) { return (size_t)g->nx * g->ny * 8 <= 200 * 1024; }
+
+sc_status launch_deposit(sc_grid* g, const sc_particles* p) {
+  const bool tile = deposit_uses_tile(g);
+  const int smem = tile ? g->nx * g->ny * 8 : 0;
+  int blocks = g->dep_blocks;
+  const int64_t need = (p->n + kDepThreads - 1) / kDepThreads;
+  if (need < blocks) blocks = (int)(need > 0 ? need : 1);
+  if (tile)
+    deposit_kernel<true><<<blocks, kDepThreads, smem, g->stream>>>(p->x, p->y, p->n, g->geom, g->Q, g->n_out);
+  else
+    deposit_kernel<false><<<blocks, kDepThreads, 0, g->stream>>>(p->x, p->y, p->n, g->geom, g->Q, g->n_out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+int deposit_blocks_for(int smem_bytes, bool tile) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (tile) {
+    cudaFuncSetAttribute(deposit_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, deposit_kernel<true>, kDepThreads, smem_bytes);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, deposit_kernel<false>, kDepThreads, 0);
+  }
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+}  // namespace sc

@@ -1,0 +1,86 @@
+// Beam moments for the per-turn diagnostics (Sec. V: rms sizes -> beta,
+// emittances).  Two launches with a fixed grid so that the float64 sums are
+// reduced in the same order every time (deterministic).
+#include "sc_internal.cuh"
+
+namespace sc {
+
+namespace {
+
+constexpr int kMomThreads = 256;
+constexpr int kMomBlocks = 304;  // fixed: 2 per SM on a 152-SM GB300
+constexpr int kNM = 14;
+
+__global__ void __launch_bounds__(kMomThreads) moments_partial(const double* __restrict__ x,
+                                                                const double* __restrict__ px,
+                                                                const double* __restrict__ y,
+                                                                const double* __restrict__ py,
+                                                                const double* __restrict__ sg,
+                                                                const double* __restrict__ ps, int64_t n,
+                                                                double* __restrict__ partial) {
+  double s[kNM];
+#pragma unroll
+  for (int c = 0; c < kNM; ++c) s[c] = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const double a = x[p], b = px[p], c = y[p], d = py[p], e = sg[p], f = ps[p];
+    s[0] += a; s[1] += b; s[2] += c; s[3] += d; s[4] += e; s[5] += f;
+    s[6] += a * a; s[7] += a * b; s[8] += b * b;
+    s[9] += c * c; s[10] += c * d; s[11] += d * d;
+    s[12] += e * e; s[13] += f * f;
+  }
+  __shared__ double red[kMomThreads / 32][kNM];
+#pragma unroll
+  for (int c = 0; c < kNM; ++c) {
+    double v = s[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][c] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNM) {
+    double v = 0.0;
+    for (int w = 0; w < kMomThreads / 32; ++w) v += red[w][threadIdx.x];
+    partial[(size_t)blockIdx.x * kNM + threadIdx.x] = v;
+  }
+}
+
+// out = base_ptr[0] + 14 * (*turn): means, then central second moments; bumps *turn.
+__global__ void moments_final(const double* __restrict__ partial, int n_blocks, int64_t n, double* const* base_ptr,
+                              int* turn) {
+  __shared__ double tot[kNM];
+  if (threadIdx.x < kNM) {
+    double v = 0.0;
+    for (int b = 0; b < n_blocks; ++b) v += partial[(size_t)b * kNM + threadIdx.x];
+    tot[threadIdx.x] = v / (double)n;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* out = *base_ptr + (size_t)kNM * (*turn);
+    const double* m = tot;
+    for (int c = 0; c < 6; ++c) out[c] = m[c];
+    out[6] = m[6] - m[0] * m[0];
+    out[7] = m[7] - m[0] * m[1];
+    out[8] = m[8] - m[1] * m[1];
+    out[9] = m[9] - m[2] * m[2];
+    out[10] = m[10] - m[2] * m[3];
+    out[11] = m[11] - m[3] * m[3];
+    out[12] = m[12] - m[4] * m[4];
+    out[13] = m[13] - m[5] * m[5];
+    *turn += 1;
+  }
+}
+
+}  // namespace
+
+int moments_blocks() { return kMomBlocks; }
+
+sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
+                         cudaStream_t s) {
+  moments_partial<<<n_blocks, kMomThreads, 0, s>>>(p->x, p->px, p->y, p->py, p->sigma, p->psigma, p->n, partial);
+  moments_final<<<1, 32, 0, s>>>(partial, n_blocks, p->n, base_ptr, turn);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
+}  // namespace sc

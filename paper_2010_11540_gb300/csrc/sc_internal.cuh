@@ -1,0 +1,120 @@
+// Internal declarations shared by the libsc translation units (CUDA path only).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "sc.h"
+
+namespace sc {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local last error, status codes of sc.h)
+// ---------------------------------------------------------------------------
+sc_status set_error(sc_status code, const std::string& msg);
+sc_status cuda_error(cudaError_t e, const char* what);
+
+#define SC_CUDA(call)                                    \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return sc::cuda_error(_e, #call); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Grid geometry as the kernels see it.  Nodes x_i = xmin + i*hx.
+// ---------------------------------------------------------------------------
+struct GridGeom {
+  int nx, ny;
+  double xmin, ymin, inv_hx, inv_hy;
+  double xlast, ylast;  // (double)(nx-1), (double)(ny-1): exclusive upper bounds of xi, eta
+};
+
+// Kick/push/deposit launch parameters, passed by value (constant bank).
+
+struct KPParams {
+  double *x, *px, *y, *py, *sg, *ps;
+  int64_t n;
+  // gather + kick
+  GridGeom gk;
+  const double2* E;  // (Ex, Ey) per node of the kick grid
+  double kl;         // K * L_sc
+  int do_kick;
+  // deposit
+  int do_deposit;
+  GridGeom gd;
+  unsigned long long* Q;      // int64 charge of the deposit grid
+  unsigned long long* n_out;  // running count of particles outside the deposit grid
+  // beam constants
+  double beta0_sq, inv_gamma0_sq, rf_scale, two_pi_over_c;
+  const sc_element* el;  // device array of the segment's elements
+  int n_elem;
+};
+
+// Solve scratch and spectra for the float64 FFT form.
+struct Fft64Plan {
+  int M;                 // 2 * n (padded length), per axis: Mx, My
+  double2* twx;          // Mx/2 twiddles exp(-2 pi i t / Mx)
+  double2* twy;          // My/2 twiddles
+  double2* F1;           // row transforms  [ny][nx+1]
+  double2* Hx;           // column results for Ex [ny][nx+1]
+  double2* Hy;           // column results for Ey [ny][nx+1]
+  double* Sx;            // imaginary part of the Ex kernel spectrum [My][nx+1]
+  double* Sy;            // imaginary part of the Ey kernel spectrum [My][nx+1]
+};
+
+struct Tf32Plan;  // tensor-core DFT-GEMM form (solve_tf32.cu)
+
+struct TrackPlan;  // captured turn graph (api.cu)
+
+}  // namespace sc
+
+struct sc_grid {
+  int nx, ny, precision;
+  double xmin, xmax, ymin, ymax, hx, hy;
+  sc::GridGeom geom;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  unsigned long long* Q;      // [ny*nx] int64 charge (2^40 per particle)
+  double2* E;                 // [ny*nx] (Ex, Ey)
+  unsigned long long* n_out;  // device counter
+  int64_t n_particles;        // particle count of the last deposit (normalises Q)
+  sc::Fft64Plan fft;
+  sc::Tf32Plan* tf32;
+  sc::TrackPlan* track;
+  int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
+  int kp_blocks_plain;         // kick/push without a deposit
+  sc_element* el_stage;        // device staging for sc_kick_push's elements
+  int el_stage_cap;
+};
+
+namespace sc {
+
+// deposit.cu
+sc_status launch_deposit(sc_grid* g, const sc_particles* p);
+// kick_push.cu
+// blocks: dep->kp_blocks when depositing into dep, else the kick grid's kp_blocks_plain.
+sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s);
+bool deposit_uses_tile(const sc_grid* g);
+int deposit_blocks_for(int smem_bytes, bool tile);
+int kick_push_blocks_for(int smem_bytes, bool tile);
+// solve_fft64.cu
+sc_status fft64_create(sc_grid* g);
+void fft64_destroy(sc_grid* g);
+sc_status fft64_solve(sc_grid* g);
+// solve_tf32.cu
+sc_status tf32_create(sc_grid* g);
+void tf32_destroy(sc_grid* g);
+sc_status tf32_solve(sc_grid* g);
+// diag.cu
+sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
+                         cudaStream_t s);
+int moments_blocks();
+
+// Build the cyclic difference-kernel fields Dx, Dy on the doubled grid, float64
+// host arrays [My][Mx] (used by both solve forms).
+void build_field_kernels(const sc_grid* g, double* Dx, double* Dy);
+
+}  // namespace sc

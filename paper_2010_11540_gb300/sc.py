@@ -1,0 +1,211 @@
+"""Thin Python binding of libsc's C-ABI (include/sc.h): argument marshalling only.
+
+Every step of the space-charge path runs in libsc's CUDA kernels; this module
+converts torch tensors / numpy arrays into the C structs and raises on error
+codes.  There is no CPU fallback: if libsc.so is missing or no GPU is present
+the calls fail loudly.
+
+Names follow the C-ABI: create_grid, deposit, solve, kick_push, track_turns,
+grid_read, grid_write_charge.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import synth
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsc.so")
+
+SC_OK = 0
+ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVERFLOW",
+          -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
+PRECISION = {"fp64": 0, "tf32x3": 1}
+EXPORTS = ("sc_create_grid", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
+           "sc_grid_read", "sc_grid_write_charge", "sc_last_error")
+
+
+class ScError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("px", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("py", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("psigma", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
+class Beam(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("gamma0", "beta0", "n_lambda", "r_p", "circumference", "mass_ev")]
+
+
+_lib = None
+
+
+def load():
+    """Load libsc.so (built by paper_2010_11540_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libsc.so not built ({LIB_PATH}); run paper_2010_11540_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+    L.sc_create_grid.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    L.sc_destroy_grid.argtypes = [vp]
+    L.sc_deposit.argtypes = [vp, ctypes.POINTER(Particles)]
+    L.sc_solve.argtypes = [vp]
+    L.sc_kick_push.argtypes = [vp, ctypes.POINTER(Particles), ctypes.POINTER(Beam), ctypes.c_double, vp,
+                               ctypes.c_int, vp]
+    L.sc_track_turns.argtypes = [vp, ctypes.POINTER(Particles), ctypes.POINTER(Beam), vp, ctypes.c_int,
+                                 ctypes.c_int, dp]
+    L.sc_grid_read.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64)]
+    L.sc_grid_write_charge.argtypes = [vp, vp, i64]
+    L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+    for name in EXPORTS:
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != SC_OK:
+        buf = ctypes.create_string_buffer(1024)
+        load().sc_last_error(buf, 1024)
+        raise ScError(code, buf.value.decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Grid:
+    """An sc_grid: nx x ny nodes over [xmin, xmax] x [ymin, ymax] with its solver."""
+
+    def __init__(self, nx, ny, xmin, xmax, ymin, ymax, precision="fp64", stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.extent = (float(xmin), float(xmax), float(ymin), float(ymax))
+        self.precision = precision
+        h = ctypes.c_void_p()
+        _check(load().sc_create_grid(ctypes.byref(h), self.nx, self.ny, *self.extent, PRECISION[precision],
+                                     _stream_handle(stream)))
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().sc_destroy_grid(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def create_grid(nx, ny, xmin, xmax, ymin, ymax, precision="fp64", stream=None) -> Grid:
+    return Grid(nx, ny, xmin, xmax, ymin, ymax, precision, stream)
+
+
+def particles(state) -> Particles:
+    """sc_particles from a dict of six CUDA float64 contiguous tensors of equal length."""
+    keys = ("x", "px", "y", "py", "sigma", "psigma")
+    ts = [state[k] for k in keys]
+    n = int(ts[0].numel())
+    for t in ts:
+        if not (t.is_cuda and t.dtype.is_floating_point and t.element_size() == 8 and t.is_contiguous()):
+            raise ValueError("particle arrays must be contiguous CUDA float64 tensors")
+        if t.numel() != n:
+            raise ValueError("particle arrays differ in length")
+    return Particles(*(t.data_ptr() for t in ts), n)
+
+
+def beam(b: dict) -> Beam:
+    return Beam(*(float(b[k]) for k in ("gamma0", "beta0", "n_lambda", "r_p", "circumference", "mass_ev")))
+
+
+def _elements(elems):
+    if elems is None or len(elems) == 0:
+        return None, 0, None
+    arr = np.ascontiguousarray(elems, dtype=synth.ELEMENT_DTYPE)
+    return arr.ctypes.data, len(arr), arr
+
+
+def deposit(grid: Grid, state):
+    p = particles(state)
+    _check(load().sc_deposit(grid.handle, ctypes.byref(p)))
+
+
+def solve(grid: Grid):
+    _check(load().sc_solve(grid.handle))
+
+
+def kick_push(grid: Grid, state, b: dict, L_sc: float, elems=None, next_grid: Grid | None = None):
+    p = particles(state)
+    bb = beam(b)
+    ptr, n, keep = _elements(elems)
+    _check(load().sc_kick_push(grid.handle, ctypes.byref(p), ctypes.byref(bb), float(L_sc), ptr, n,
+                               next_grid.handle if next_grid is not None else None))
+
+
+def track_turns(grid: Grid, state, b: dict, lattice, n_turns: int, diag: bool = False):
+    p = particles(state)
+    bb = beam(b)
+    ptr, n, keep = _elements(lattice)
+    out = np.zeros((n_turns, 14)) if diag else None
+    _check(load().sc_track_turns(grid.handle, ctypes.byref(p), ctypes.byref(bb), ptr, n, int(n_turns),
+                                 out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if diag else None))
+    return out
+
+
+def grid_read(grid: Grid):
+    """-> (Q int64 [ny, nx], Ex [ny, nx], Ey [ny, nx], n_out)"""
+    Q = np.zeros((grid.ny, grid.nx), dtype=np.int64)
+    Ex = np.zeros((grid.ny, grid.nx))
+    Ey = np.zeros((grid.ny, grid.nx))
+    n_out = ctypes.c_int64(0)
+    _check(load().sc_grid_read(grid.handle, Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data, ctypes.byref(n_out)))
+    return Q, Ex, Ey, int(n_out.value)
+
+
+def grid_write_charge(grid: Grid, Q, n_particles: int):
+    Q = np.ascontiguousarray(Q, dtype=np.int64)
+    assert Q.shape == (grid.ny, grid.nx)
+    _check(load().sc_grid_write_charge(grid.handle, Q.ctypes.data, int(n_particles)))
+
+
+def track_turns_host(grid: Grid, host_state, b: dict, lattice, n_turns: int, device_state=None, stream=None):
+    """Track a bunch held in host memory: copy the six arrays to the device,
+    run sc_track_turns, copy them back (in place).  `host_state` values are
+    numpy float64 arrays (pinned torch CPU tensors also accepted);
+    `device_state` may hold preallocated CUDA tensors to reuse."""
+    import torch
+
+    keys = ("x", "px", "y", "py", "sigma", "psigma")
+    if device_state is None:
+        device_state = {k: torch.empty(len(host_state[k]), dtype=torch.float64, device="cuda") for k in keys}
+    for k in keys:
+        src = host_state[k]
+        src = torch.from_numpy(src) if isinstance(src, np.ndarray) else src
+        device_state[k].copy_(src, non_blocking=True)
+    track_turns(grid, device_state, b, lattice, n_turns)
+    for k in keys:
+        dst = host_state[k]
+        dst = torch.from_numpy(dst) if isinstance(dst, np.ndarray) else dst
+        dst.copy_(device_state[k], non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return host_state

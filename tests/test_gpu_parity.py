@@ -1,0 +1,190 @@
+"""GPU (libsc, sm_103a) vs the FP64 CPU oracle on the same seeded inputs,
+through the C-ABI.  Tolerances: charge grid bit-exact; float64 fields 1e-12
+relative L2; single-step and one-turn coordinates 1e-10 relative (per
+coordinate, to its rms)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_11540_gb300 import build, sc, synth
+from gpu_helpers import KEYS, rel_l2, rel_state_err, to_gpu, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    sc.load()
+
+
+def grid_pair(geom_args, precision="fp64"):
+    return sc.create_grid(*geom_args, precision=precision), oracle.Geometry(*geom_args)
+
+
+# ------------------------------------------------------------------ deposit
+@pytest.mark.parametrize("n,grid", [
+    (20000, (64, 64, -0.01, 0.01, -0.01, 0.01)),     # c1 size
+    (12345, (32, 16, -0.012, 0.009, -0.007, 0.008)),  # ragged count, non-square, beam past the edge
+    (1, (8, 8, -1.0, 1.0, -1.0, 1.0)),
+])
+def test_deposit_bit_exact(n, grid):
+    parts = synth.gaussian_bunch(n, 12345 + n, 3e-3, 2.5e-3, 1e-4, 1e-4)
+    g, og = grid_pair(grid)
+    sc.deposit(g, to_gpu(parts))
+    Q, _, _, n_out = sc.grid_read(g)
+    Qo, n_out_o = oracle.deposit(og, parts["x"], parts["y"])
+    assert np.array_equal(Q, Qo)
+    assert n_out == n_out_o
+
+
+def test_deposit_bit_exact_full_size():
+    """1e6 particles on 128x128 (the bench workload's grid)."""
+    parts, b, grid, lat = synth.workload("c2")
+    g, og = grid_pair(grid)
+    sc.deposit(g, to_gpu(parts))
+    Q, _, _, n_out = sc.grid_read(g)
+    Qo, n_out_o = oracle.deposit(og, parts["x"], parts["y"])
+    assert np.array_equal(Q, Qo) and n_out == n_out_o
+    assert Q.sum() == (len(parts["x"]) - n_out) * (1 << 40)
+
+
+def test_deposit_edge_cases():
+    g, og = grid_pair((8, 8, 0.0, 7.0, 0.0, 7.0))
+    x = np.array([7.0, -1e-12, 3.0, np.nan, 6.999999, 3.0, 3.0, 0.0])
+    y = np.array([3.0, 3.0, 7.0, 1.0, 6.999999, np.inf, 0.0, 0.0])
+    st = {k: np.zeros(len(x)) for k in KEYS}
+    st["x"], st["y"] = x, y
+    sc.deposit(g, to_gpu(st))
+    Q, _, _, n_out = sc.grid_read(g)
+    Qo, n_out_o = oracle.deposit(og, x, y)
+    assert np.array_equal(Q, Qo) and n_out == n_out_o == 5
+    # empty deposit zeroes the grid
+    sc.deposit(g, to_gpu({k: np.zeros(0) for k in KEYS}))
+    assert not sc.grid_read(g)[0].any()
+
+
+def test_overflow_rejected():
+    import torch
+    g = sc.create_grid(8, 8, 0.0, 1.0, 0.0, 1.0)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p = sc.Particles(*(t.data_ptr(),) * 6, (1 << 23) + 1)
+    import ctypes
+    code = sc.load().sc_deposit(g.handle, ctypes.byref(p))
+    assert code == -4
+
+
+# ------------------------------------------------------------------ solve
+@pytest.mark.parametrize("grid", [(64, 64, -0.01, 0.01, -0.01, 0.01), (32, 16, -0.012, 0.009, -0.007, 0.008),
+                                  (128, 128, -0.02, 0.02, -0.015, 0.015)])
+def test_solve_fp64_matches_oracle(grid):
+    parts = synth.gaussian_bunch(200000, 77, 4e-3, 3e-3, 1e-4, 1e-4)
+    g, og = grid_pair(grid)
+    Qo, _ = oracle.deposit(og, parts["x"], parts["y"])
+    sc.grid_write_charge(g, Qo, len(parts["x"]))
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    Exo, Eyo = oracle.solve(og, Qo, len(parts["x"]))
+    assert rel_l2(Ex, Exo) < 1e-12 and rel_l2(Ey, Eyo) < 1e-12
+
+
+def test_solve_point_charge_corner():
+    """A charge in a corner node exercises the wrap-around of the doubled grid."""
+    grid = (16, 16, 0.0, 1.0, 0.0, 1.0)
+    g, og = grid_pair(grid)
+    Q = np.zeros((16, 16), dtype=np.int64)
+    Q[0, 0] = 1 << 40
+    Q[15, 15] = 3 << 40
+    sc.grid_write_charge(g, Q, 4)
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    Exo, Eyo = oracle.solve(og, Q, 4)
+    assert rel_l2(Ex, Exo) < 1e-12 and rel_l2(Ey, Eyo) < 1e-12
+
+
+# ------------------------------------------------------------------ kick + push
+def _one_step(parts, b, grid, elems, L, n_next=True):
+    g, og = grid_pair(grid)
+    st = to_gpu(parts)
+    sc.deposit(g, st)
+    sc.solve(g)
+    sc.kick_push(g, st, b, L, elems, next_grid=g if n_next else None)
+    got = to_host(st)
+    Qg = sc.grid_read(g)[0]
+    ref = oracle.copy_state(parts)
+    Qo, _ = oracle.deposit(og, ref["x"], ref["y"])
+    Ex, Ey = oracle.solve(og, Qo, len(ref["x"]))
+    oracle.kick(og, ref, Ex, Ey, oracle.kick_strength(b) * L)
+    oracle.push(ref, elems, b)
+    return got, ref, Qg, og
+
+
+@pytest.mark.parametrize("n", [20000, 4099])
+def test_kick_push_c2_segments(n):
+    parts, b, grid, lat = synth.workload("c2", n=n)
+    b = dict(b, n_lambda=5e11)  # strong space charge so the kick is visible
+    head, kicks = oracle.segments(lat)
+    for L, seg in kicks[:3]:
+        got, ref, Qg, og = _one_step(parts, b, grid, seg, L)
+        err = rel_state_err(got, ref)
+        assert max(err.values()) < 1e-10, err
+        Qn, _ = oracle.deposit(og, got["x"], got["y"])
+        assert np.array_equal(Qg, Qn)  # fused deposit of the pushed state
+
+
+def test_kick_push_every_element_type():
+    parts, b, grid, lat = synth.workload("c1", n=5000)
+    b = dict(b, circumference=264.0)
+    elems = synth.table([
+        synth.elem(synth.DRIFT, 2.0), synth.elem(synth.QUAD, 0.7, k1=1.1), synth.elem(synth.QUAD, 0.7, k1=-0.9),
+        synth.elem(synth.QUAD, 0.3, k1=0.0), synth.elem(synth.SEXT, k2l=3.0),
+        synth.elem(synth.BEND, 1.5, angle=0.1), synth.elem(synth.BEND, 1.0, angle=0.0),
+        synth.elem(synth.RF, volt=2e5, harmonic=9.0, lag=0.3), synth.elem(synth.MARK),
+    ])
+    got, ref, _, _ = _one_step(parts, b, grid, elems, 5.5)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+
+
+# ------------------------------------------------------------------ tracking
+def test_track_c1_full():
+    """Config c1 in full: 2e4 particles, 64x64, 48 kicks/turn, 10 turns."""
+    parts, b, grid, lat = synth.workload("c1")
+    g, og = grid_pair(grid)
+    st = to_gpu(parts)
+    diag = sc.track_turns(g, st, b, lat, 10, diag=True)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    mom = []
+    oracle.track(og, ref, b, lat, 10, diag=lambda t, s: mom.append(oracle.moments(s)))
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+    mom = np.array(mom)
+    assert np.max(np.abs(diag - mom) / (np.abs(mom) + 1e-30)) < 1e-9
+
+
+def test_track_graph_replay_consistent():
+    """Two calls of 1 turn equal one call of 2 turns (captured graph reused)."""
+    parts, b, grid, lat = synth.workload("c1", n=3000)
+    g = sc.create_grid(*grid)
+    a = to_gpu(parts)
+    sc.track_turns(g, a, b, lat, 1)
+    sc.track_turns(g, a, b, lat, 1)
+    g2 = sc.create_grid(*grid)
+    c = to_gpu(parts)
+    sc.track_turns(g2, c, b, lat, 2)
+    for k in KEYS:
+        assert np.array_equal(a[k].cpu().numpy(), c[k].cpu().numpy())
+
+
+def test_track_c2_one_turn_full_size():
+    """The bench workload (1e6 particles, 128x128, 216 kicks) for one turn."""
+    parts, b, grid, lat = synth.workload("c2")
+    g, og = grid_pair(grid)
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(og, ref, b, lat, 1)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
