@@ -31,16 +31,19 @@ sc_status cuda_error(cudaError_t e, const char* what) {
 // Captured turn of a ring for one (grid, particles, beam, lattice) set.
 struct TrackPlan {
   std::vector<unsigned char> key;
-  sc_element* d_elems = nullptr;
+  DevElem* d_elems = nullptr;  // compiled lattice (segments longer than KP_INLINE read it)
+  int* cell = nullptr;         // cell cache [n]
+  double2* frac = nullptr;     // fraction cache [n]
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool has_head = false;
   bool diag = false;
   int n_kicks = 0;
-  double* partial = nullptr;   // moments partial sums
-  double** d_base = nullptr;   // device cell holding the diag output pointer
-  int* d_turn = nullptr;       // device turn counter
-  double* d_diag = nullptr;    // [cap][14]
+  KPParams prologue{};        // deposit at the first marker (lattices that start with one)
+  double* partial = nullptr;  // moments partial sums
+  double** d_base = nullptr;  // device cell holding the diag output pointer
+  int* d_turn = nullptr;      // device turn counter
+  double* d_diag = nullptr;   // [cap][14]
   int diag_cap = 0;
 };
 
@@ -51,6 +54,8 @@ void destroy_plan(TrackPlan* t) {
   if (t->exec) cudaGraphExecDestroy(t->exec);
   if (t->graph) cudaGraphDestroy(t->graph);
   cudaFree(t->d_elems);
+  cudaFree(t->cell);
+  cudaFree(t->frac);
   cudaFree(t->partial);
   cudaFree(t->d_base);
   cudaFree(t->d_turn);
@@ -68,12 +73,27 @@ sc_status check_particles(const sc_particles* p) {
   return SC_OK;
 }
 
-void fill_beam(KPParams& P, const sc_beam* b) {
-  P.beta0_sq = b->beta0 * b->beta0;
-  P.inv_gamma0_sq = 1.0 / (b->gamma0 * b->gamma0);
-  const double e0 = b->gamma0 * b->mass_ev;
-  P.rf_scale = (e0 > 0.0) ? 1.0 / (P.beta0_sq * e0) : 0.0;
-  P.two_pi_over_c = (b->circumference > 0.0) ? 2.0 * M_PI / b->circumference : 0.0;
+sc_status check_beam(const sc_beam* b) {
+  if (!b) return set_error(SC_ERR_ARG, "beam is NULL");
+  if (!(b->gamma0 >= 1.0) || !(b->beta0 > 0.0 && b->beta0 < 1.0) || !std::isfinite(b->n_lambda) ||
+      !std::isfinite(b->r_p))
+    return set_error(SC_ERR_ARG, "beam constants out of range (gamma0 >= 1, 0 < beta0 < 1, finite n_lambda, r_p)");
+  return SC_OK;
+}
+
+sc_status check_elements(const sc_element* e, int n) {
+  if (n < 0 || (n > 0 && !e)) return set_error(SC_ERR_ARG, "bad element list");
+  for (int k = 0; k < n; ++k) {
+    if (e[k].type < SC_DRIFT || e[k].type > SC_MARK) return set_error(SC_ERR_ARG, "unknown element type");
+    if (!std::isfinite(e[k].length) || e[k].length < 0.0) return set_error(SC_ERR_ARG, "bad element length");
+  }
+  return SC_OK;
+}
+
+bool any_quad(const sc_element* e, int n) {
+  for (int k = 0; k < n; ++k)
+    if (e[k].type == SC_QUAD) return true;
+  return false;
 }
 
 // K = 2 r_p N_lambda / (beta0^2 gamma0^3): the transverse kick of Sec. IV per
@@ -92,7 +112,8 @@ KPParams base_params(const sc_particles* p, const sc_beam* b) {
   P.sg = p->sigma;
   P.ps = p->psigma;
   P.n = p->n;
-  fill_beam(P, b);
+  P.beta0_sq = b->beta0 * b->beta0;
+  P.inv_gamma0_sq = 1.0 / (b->gamma0 * b->gamma0);
   return P;
 }
 
@@ -110,22 +131,22 @@ void set_deposit(KPParams& P, sc_grid* d) {
   P.n_out = d->n_out;
 }
 
+// Elements of a segment: inline in the launch parameters when they fit,
+// else the device array `dev` (compiled already) at the same offset.
+void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, const DevElem* dev) {
+  P.n_elem = n;
+  P.has_quad = any_quad(host, n);
+  if (n <= KP_INLINE) {
+    compile_elements(host, n, b, P.inl);
+    P.el = nullptr;
+  } else {
+    P.el = dev;
+  }
+}
+
 sc_status solve_dispatch(sc_grid* g) {
   if (g->precision == SC_SOLVE_TF32X3) return tf32_solve(g);
   return fft64_solve(g);
-}
-
-sc_status stage_elements(sc_grid* g, const sc_element* elems, int n) {
-  if (n <= 0) return SC_OK;
-  if (n > g->el_stage_cap) {
-    cudaFree(g->el_stage);
-    g->el_stage = nullptr;
-    g->el_stage_cap = 0;
-    SC_CUDA(cudaMalloc(&g->el_stage, (size_t)n * sizeof(sc_element)));
-    g->el_stage_cap = n;
-  }
-  SC_CUDA(cudaMemcpyAsync(g->el_stage, elems, (size_t)n * sizeof(sc_element), cudaMemcpyHostToDevice, g->stream));
-  return SC_OK;
 }
 
 }  // namespace
@@ -144,7 +165,7 @@ sc_status sc_last_error(char* buf, size_t n) {
 sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
                          int precision, void* stream) {
   if (!out) return set_error(SC_ERR_ARG, "out is NULL");
-  if (nx < 2 || ny < 2) return set_error(SC_ERR_ARG, "grid needs at least 2x2 nodes");
+  if (nx < 2 || ny < 2 || nx > 4096 || ny > 4096) return set_error(SC_ERR_ARG, "grid needs 2..4096 nodes per axis");
   if (!(xmax > xmin) || !(ymax > ymin) || !std::isfinite(xmin) || !std::isfinite(xmax) || !std::isfinite(ymin) ||
       !std::isfinite(ymax))
     return set_error(SC_ERR_ARG, "grid extent must be finite with xmax > xmin, ymax > ymin");
@@ -152,7 +173,6 @@ sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax
     return set_error(SC_ERR_UNSUPPORTED, "unknown solve precision");
   sc_grid* g = new (std::nothrow) sc_grid();
   if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
-  std::memset(g, 0, sizeof *g);
   g->nx = nx;
   g->ny = ny;
   g->precision = precision;
@@ -250,14 +270,10 @@ sc_status sc_solve(sc_grid* g) {
 
 sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, double L_sc, const sc_element* elems,
                        int n_elems, sc_grid* next) {
-  if (!g || !b) return set_error(SC_ERR_ARG, "grid or beam is NULL");
-  if (n_elems < 0 || (n_elems > 0 && !elems)) return set_error(SC_ERR_ARG, "bad element list");
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   if (!std::isfinite(L_sc)) return set_error(SC_ERR_ARG, "L_sc must be finite");
-  sc_status st = check_particles(p);
-  if (st) return st;
-  for (int k = 0; k < n_elems; ++k)
-    if (elems[k].type < SC_DRIFT || elems[k].type > SC_MARK) return set_error(SC_ERR_ARG, "unknown element type");
-  if ((st = stage_elements(g, elems, n_elems))) return st;
+  sc_status st;
+  if ((st = check_beam(b)) || (st = check_particles(p)) || (st = check_elements(elems, n_elems))) return st;
   if (next) {
     SC_CUDA(cudaMemsetAsync(next->Q, 0, (size_t)next->nx * next->ny * 8, g->stream));
     next->n_particles = p->n;
@@ -266,8 +282,21 @@ sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, doub
   KPParams P = base_params(p, b);
   set_kick(P, g, kick_strength(b) * L_sc);
   if (next) set_deposit(P, next);
-  P.el = g->el_stage;
-  P.n_elem = n_elems;
+  if (n_elems > KP_INLINE) {
+    // long segment: compiled copy in device memory (synchronous upload)
+    std::vector<DevElem> dev(n_elems);
+    compile_elements(elems, n_elems, b, dev.data());
+    SC_CUDA(cudaStreamSynchronize(g->stream));
+    if (n_elems > g->el_stage_cap) {
+      cudaFree(g->el_stage);
+      g->el_stage = nullptr;
+      g->el_stage_cap = 0;
+      SC_CUDA(cudaMalloc(&g->el_stage, (size_t)n_elems * sizeof(DevElem)));
+      g->el_stage_cap = n_elems;
+    }
+    SC_CUDA(cudaMemcpy(g->el_stage, dev.data(), (size_t)n_elems * sizeof(DevElem), cudaMemcpyHostToDevice));
+  }
+  set_elements(P, elems, n_elems, b, g->el_stage);
   return launch_kick_push(P, next, next ? next->kp_blocks : g->kp_blocks_plain, g->stream);
 }
 
@@ -303,12 +332,10 @@ sc_status sc_grid_write_charge(sc_grid* g, const int64_t* Q, int64_t n_particles
 
 sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, const sc_element* lattice, int n_elems,
                          int n_turns, double* diag) {
-  if (!g || !b) return set_error(SC_ERR_ARG, "grid or beam is NULL");
-  if (n_turns < 0 || n_elems < 0 || (n_elems > 0 && !lattice)) return set_error(SC_ERR_ARG, "bad lattice/turns");
-  sc_status st = check_particles(p);
-  if (st) return st;
-  for (int k = 0; k < n_elems; ++k)
-    if (lattice[k].type < SC_DRIFT || lattice[k].type > SC_MARK) return set_error(SC_ERR_ARG, "unknown element type");
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
+  sc_status st;
+  if ((st = check_beam(b)) || (st = check_particles(p)) || (st = check_elements(lattice, n_elems))) return st;
   if (n_turns == 0 || p->n == 0) return SC_OK;
 
   // ---- key of the captured plan ------------------------------------------------
@@ -343,9 +370,14 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     const double circ = s[n_elems];
     T->n_kicks = (int)marks.size();
     T->has_head = marks.empty() ? true : marks[0] > 0;
-    if (n_elems) SC_CUDA(cudaMalloc(&T->d_elems, (size_t)n_elems * sizeof(sc_element)));
-    if (n_elems)
-      SC_CUDA(cudaMemcpy(T->d_elems, lattice, (size_t)n_elems * sizeof(sc_element), cudaMemcpyHostToDevice));
+    std::vector<DevElem> dev(n_elems > 0 ? n_elems : 1);
+    compile_elements(lattice, n_elems, b, dev.data());
+    SC_CUDA(cudaMalloc(&T->d_elems, dev.size() * sizeof(DevElem)));
+    SC_CUDA(cudaMemcpy(T->d_elems, dev.data(), dev.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
+    if (!marks.empty()) {
+      SC_CUDA(cudaMalloc(&T->cell, (size_t)p->n * sizeof(int)));
+      SC_CUDA(cudaMalloc(&T->frac, (size_t)p->n * sizeof(double2)));
+    }
     if (want_diag) {
       SC_CUDA(cudaMalloc(&T->partial, (size_t)moments_blocks() * 14 * sizeof(double)));
       SC_CUDA(cudaMalloc(&T->d_base, sizeof(double*)));
@@ -353,20 +385,29 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     }
     g->n_particles = p->n;
     const double K = kick_strength(b);
+    const size_t qbytes = (size_t)g->nx * g->ny * 8;
+    // prologue: charge (and cell cache) at the first marker for lattices that open with one
+    T->prologue = base_params(p, b);
+    set_deposit(T->prologue, g);
+    T->prologue.cell = T->cell;
+    T->prologue.frac = T->frac;
     // ---- capture one turn ------------------------------------------------------
     SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     sc_status cst = SC_OK;
     if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, g->stream);
-    const size_t qbytes = (size_t)g->nx * g->ny * 8;
     if (!cst && T->has_head) {
       KPParams P = base_params(p, b);
-      P.el = T->d_elems;
-      P.n_elem = marks.empty() ? n_elems : marks[0];
+      const int nh = marks.empty() ? n_elems : marks[0];
+      set_elements(P, lattice, nh, b, T->d_elems);
       if (!marks.empty()) {
         set_deposit(P, g);
+        P.cell = T->cell;
+        P.frac = T->frac;
         if (cudaMemsetAsync(g->Q, 0, qbytes, g->stream) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "memset");
       }
-      if (!cst) cst = launch_kick_push(P, marks.empty() ? nullptr : g, marks.empty() ? g->kp_blocks_plain : g->kp_blocks, g->stream);
+      if (!cst)
+        cst = launch_kick_push(P, marks.empty() ? nullptr : g, marks.empty() ? g->kp_blocks_plain : g->kp_blocks,
+                               g->stream);
     }
     for (size_t k = 0; !cst && k < marks.size(); ++k) {
       const int m = marks[k];
@@ -376,8 +417,10 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       if (cst) break;
       KPParams P = base_params(p, b);
       set_kick(P, g, K * (s[m] - prev));
-      P.el = T->d_elems + m + 1;
-      P.n_elem = end - m - 1;
+      set_elements(P, lattice + m + 1, end - m - 1, b, T->d_elems + m + 1);
+      // the cell cache is valid at every marker: the previous launch deposited on this grid
+      P.cell = T->cell;
+      P.frac = T->frac;
       const bool dep = (k + 1 < marks.size()) || !T->has_head;
       if (dep) {
         set_deposit(P, g);
@@ -413,6 +456,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   // ---- run -------------------------------------------------------------------------
   if (T->diag) {
     if (n_turns > T->diag_cap) {
+      SC_CUDA(cudaStreamSynchronize(g->stream));
       cudaFree(T->d_diag);
       T->d_diag = nullptr;
       SC_CUDA(cudaMalloc(&T->d_diag, (size_t)n_turns * 14 * sizeof(double)));
@@ -425,7 +469,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   if (!T->has_head && T->n_kicks > 0) {
     // charge at the first space-charge location of the first turn
     SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * 8, g->stream));
-    if ((st = launch_deposit(g, p))) return st;
+    if ((st = launch_kick_push(T->prologue, g, g->kp_blocks, g->stream))) return st;
   }
   for (int t = 0; t < n_turns; ++t) SC_CUDA(cudaGraphLaunch(T->exec, g->stream));
   if (T->diag) {

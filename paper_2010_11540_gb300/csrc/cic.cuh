@@ -5,35 +5,35 @@
 
 namespace sc {
 
-struct Cell {
-  int i, j;
-  double fx, fy;
-};
-
-// Cell (i, j) and fractions of a particle: xi = (x - xmin) * inv_hx rounded
-// twice (no fused multiply-add, so every platform takes the same integer
-// decision), i = floor(xi), fx = xi - i (exact).  Inside iff
-// 0 <= xi < nx-1 and 0 <= eta < ny-1; NaN/inf are outside.
-__device__ __forceinline__ bool locate(const GridGeom& g, double x, double y, Cell& c) {
+// Cell and fractions of a particle: xi = (x - xmin) * inv_hx rounded twice
+// (no fused multiply-add, so every platform takes the same integer decision),
+// i = floor(xi), fx = xi - i (exact).  Inside iff 0 <= xi < nx-1 and
+// 0 <= eta < ny-1; non-finite coordinates are outside.  The range test is
+// done on the integer floor (0 <= i <= nx-2 is the same condition for finite
+// xi; out-of-range values saturate), and finiteness on the exponent bits, so
+// that only the subtract, multiply, floor-convert, back-convert and subtract
+// of each axis use the FP64 pipe.  Returns the cell index j*nx+i or -1.
+__device__ __forceinline__ int locate(const GridGeom& g, double x, double y, double& fx, double& fy) {
+  const bool finite = ((__double2hiint(x) & 0x7ff00000) != 0x7ff00000) &&
+                      ((__double2hiint(y) & 0x7ff00000) != 0x7ff00000);
   const double xi = __dmul_rn(__dsub_rn(x, g.xmin), g.inv_hx);
   const double eta = __dmul_rn(__dsub_rn(y, g.ymin), g.inv_hy);
-  if (!(xi >= 0.0 && xi < g.xlast && eta >= 0.0 && eta < g.ylast)) return false;
-  const double fi = floor(xi), fj = floor(eta);
-  c.i = (int)fi;
-  c.j = (int)fj;
-  c.fx = __dsub_rn(xi, fi);
-  c.fy = __dsub_rn(eta, fj);
-  return true;
+  const int i = __double2int_rd(xi);
+  const int j = __double2int_rd(eta);
+  fx = __dsub_rn(xi, (double)i);
+  fy = __dsub_rn(eta, (double)j);
+  const bool inside = finite && (unsigned)i < (unsigned)(g.nx - 1) && (unsigned)j < (unsigned)(g.ny - 1);
+  return inside ? j * g.nx + i : -1;
 }
 
 // The four CIC weights in 2^-20 fixed point per axis: a = rint(f 2^20)
 // (round half to even), b = 2^20 - a; the products sum to exactly 2^40.
 // dst is either a shared-memory tile or the global grid (same [j][i] layout).
-__device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, const Cell& c) {
-  const long long ax = __double2ll_rn(__dmul_rn(c.fx, 1048576.0));
-  const long long ay = __double2ll_rn(__dmul_rn(c.fy, 1048576.0));
+__device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int cell, double fx, double fy) {
+  const long long ax = __double2ll_rn(__dmul_rn(fx, 1048576.0));
+  const long long ay = __double2ll_rn(__dmul_rn(fy, 1048576.0));
   const long long bx = 1048576LL - ax, by = 1048576LL - ay;
-  unsigned long long* q = dst + (size_t)c.j * nx + c.i;
+  unsigned long long* q = dst + cell;
   atomicAdd(q, (unsigned long long)(bx * by));
   atomicAdd(q + 1, (unsigned long long)(ax * by));
   atomicAdd(q + nx, (unsigned long long)(bx * ay));

@@ -23,9 +23,10 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __re
   unsigned int out = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
-    Cell c;
-    if (locate(g, __ldg(x + p), __ldg(y + p), c))
-      deposit4(dst, g.nx, c);
+    double fx, fy;
+    const int cell = locate(g, __ldg(x + p), __ldg(y + p), fx, fy);
+    if (cell >= 0)
+      deposit4(dst, g.nx, cell, fx, fy);
     else
       ++out;
   }

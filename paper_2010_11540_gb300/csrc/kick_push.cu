@@ -3,6 +3,8 @@
 // and CIC deposit of the new positions (Sec. IV-A) into a per-block
 // shared-memory int64 tile flushed once per block.  One thread per particle,
 // persistent grid-stride loop over SoA float64 state.
+#include <cmath>
+
 #include "cic.cuh"
 #include "maps.cuh"
 
@@ -12,8 +14,10 @@ namespace {
 
 constexpr int kKPThreads = 512;
 
-template <bool TILE>
-__global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const KPParams P) {
+// TILE: deposit into a shared-memory tile (grid fits); CACHE: the cell cache
+// P.cell / P.frac is valid for the gather and is refreshed by the deposit.
+template <bool TILE, bool CACHE>
+__global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
   const int cells = P.gd.nx * P.gd.ny;
   if (TILE) {
@@ -21,32 +25,47 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const KPParams P)
     __syncthreads();
   }
   unsigned long long* dst = TILE ? tile : P.Q;
-  const BeamK bk{P.beta0_sq, P.inv_gamma0_sq, P.rf_scale, P.two_pi_over_c};
   unsigned int out = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n; p += stride) {
     State s{P.x[p], P.px[p], P.y[p], P.py[p], P.sg[p], P.ps[p]};
     if (P.do_kick) {
-      Cell c;
-      if (locate(P.gk, s.x, s.y, c)) {
-        const double2* e = P.E + (size_t)c.j * P.gk.nx + c.i;
+      double fx, fy;
+      int cell;
+      if (CACHE) {
+        cell = P.cell[p];
+        const double2 f = P.frac[p];
+        fx = f.x;
+        fy = f.y;
+      } else {
+        cell = locate(P.gk, s.x, s.y, fx, fy);
+      }
+      if (cell >= 0) {
+        const double2* e = P.E + cell;
         const double2 e00 = __ldg(e), e10 = __ldg(e + 1);
         const double2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
-        const double gx = 1.0 - c.fx, gy = 1.0 - c.fy;
-        const double w00 = gx * gy, w10 = c.fx * gy, w01 = gx * c.fy, w11 = c.fx * c.fy;
-        const double ex = w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x;
-        const double ey = w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y;
-        s.px = fma(P.kl, ex, s.px);
-        s.py = fma(P.kl, ey, s.py);
+        // bilinear interpolation with the gather weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy
+        const double ax = fma(fx, e10.x - e00.x, e00.x), bx = fma(fx, e11.x - e01.x, e01.x);
+        const double ay = fma(fx, e10.y - e00.y, e00.y), by = fma(fx, e11.y - e01.y, e01.y);
+        s.px = fma(P.kl, fma(fy, bx - ax, ax), s.px);
+        s.py = fma(P.kl, fma(fy, by - ay, ay), s.py);
       }
     }
-    push_elements(s, P.el, P.n_elem, bk);
+    if (P.el)
+      push_elements(s, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, P.has_quad != 0);
+    else
+      push_elements(s, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, P.has_quad != 0);
     if (P.do_deposit) {
-      Cell c;
-      if (locate(P.gd, s.x, s.y, c))
-        deposit4(dst, P.gd.nx, c);
+      double fx, fy;
+      const int cell = locate(P.gd, s.x, s.y, fx, fy);
+      if (cell >= 0)
+        deposit4(dst, P.gd.nx, cell, fx, fy);
       else
         ++out;
+      if (CACHE) {
+        P.cell[p] = cell;
+        P.frac[p] = make_double2(fx, fy);
+      }
     }
     P.x[p] = s.x;
     P.px[p] = s.px;
@@ -64,33 +83,107 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const KPParams P)
   }
 }
 
-}  // namespace
-
-int kick_push_blocks_for(int smem_bytes, bool tile) {
+template <bool TILE, bool CACHE>
+int blocks_for(int smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (tile) {
-    cudaFuncSetAttribute(kick_push_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<true>, kKPThreads, smem_bytes);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<false>, kKPThreads, 0);
-  }
-  if (per < 1) per = 1;
-  return sms * per;
+  if (TILE) cudaFuncSetAttribute(kick_push_kernel<TILE, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<TILE, CACHE>, kKPThreads, smem);
+  return sms * (per < 1 ? 1 : per);
 }
 
-// dep: the deposit grid (NULL when P.do_deposit == 0).
+}  // namespace
+
+int kick_push_blocks_for(int smem_bytes, bool tile) {
+  // the cached and uncached variants have the same shared memory; size on the larger register count
+  if (tile) {
+    const int a = blocks_for<true, false>(smem_bytes), b = blocks_for<true, true>(smem_bytes);
+    return a < b ? a : b;
+  }
+  const int a = blocks_for<false, false>(0), b = blocks_for<false, true>(0);
+  return a < b ? a : b;
+}
+
 sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s) {
   const bool tile = P.do_deposit && dep && deposit_uses_tile(dep);
+  const bool cache = P.cell != nullptr;
   const int64_t need = (P.n + kKPThreads - 1) / kKPThreads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
-  if (tile)
-    kick_push_kernel<true><<<blocks, kKPThreads, dep->nx * dep->ny * 8, s>>>(P);
+  const int smem = tile ? dep->nx * dep->ny * 8 : 0;
+  if (tile && cache)
+    kick_push_kernel<true, true><<<blocks, kKPThreads, smem, s>>>(P);
+  else if (tile)
+    kick_push_kernel<true, false><<<blocks, kKPThreads, smem, s>>>(P);
+  else if (cache)
+    kick_push_kernel<false, true><<<blocks, kKPThreads, 0, s>>>(P);
   else
-    kick_push_kernel<false><<<blocks, kKPThreads, 0, s>>>(P);
+    kick_push_kernel<false, false><<<blocks, kKPThreads, 0, s>>>(P);
   SC_CUDA(cudaGetLastError());
   return SC_OK;
+}
+
+// Per-element constants in float64 on the host (libm), in the layouts that
+// maps.cuh documents for each element type.
+void compile_elements(const sc_element* in, int n, const sc_beam* b, DevElem* out) {
+  const double beta0_sq = b->beta0 * b->beta0;
+  const double e0 = b->gamma0 * b->mass_ev;
+  for (int i = 0; i < n; ++i) {
+    const sc_element& e = in[i];
+    DevElem& d = out[i];
+    d = DevElem{};
+    d.type = e.type;
+    switch (e.type) {
+      case SC_DRIFT:
+        d.p[0] = e.length;
+        break;
+      case SC_QUAD: {
+        d.p[0] = e.length;
+        if (e.k1 == 0.0) {
+          d.flags = QF_ZERO;
+          break;
+        }
+        const double sqk = std::sqrt(std::fabs(e.k1));
+        const double th0 = sqk * e.length;
+        d.flags = e.k1 > 0.0 ? QF_FOCUS_X : QF_FOCUS_Y;
+        d.p[1] = th0;
+        d.p[2] = std::cos(th0);
+        d.p[3] = std::sin(th0);
+        d.p[4] = std::cosh(th0);
+        d.p[5] = std::sinh(th0);
+        d.p[6] = sqk;
+        d.p[7] = 1.0 / sqk;
+        d.p[8] = e.k1;
+        break;
+      }
+      case SC_SEXT:
+        d.p[0] = 0.5 * e.k2l;
+        d.p[1] = e.k2l;
+        break;
+      case SC_BEND: {
+        d.p[0] = e.length;
+        if (e.angle == 0.0 || e.length == 0.0) {
+          d.flags = 1;
+          break;
+        }
+        const double h = e.angle / e.length, C = std::cos(e.angle), S = std::sin(e.angle);
+        d.p[1] = C;
+        d.p[2] = S;
+        d.p[3] = S / h;
+        d.p[4] = (1.0 - C) / h;
+        d.p[5] = h * S;
+        d.p[6] = e.length - S / h;
+        break;
+      }
+      case SC_RF:
+        d.p[0] = (e0 > 0.0) ? e.volt / (beta0_sq * e0) : 0.0;
+        d.p[1] = (b->circumference > 0.0) ? 2.0 * M_PI * e.harmonic / b->circumference : 0.0;
+        d.p[2] = e.lag;
+        break;
+      default:
+        break;
+    }
+  }
 }
 
 }  // namespace sc

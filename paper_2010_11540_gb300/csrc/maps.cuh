@@ -1,133 +1,188 @@
 // Single-particle transfer maps of Sec. III in float64, one particle per
-// thread.  State: (x, px, y, py, sg, ps) with px = Px/p0, sg = s - c beta0 t.
+// thread, arranged to spend few instructions on the FP64 pipe (the GB300's
+// scarcest unit: every FP64 add, multiply, fma, compare, floor and
+// conversion takes one of its two issue slots per SM clock).
+//
+// State: (x, px, y, py, sg, ps) with px = Px/p0, sg = s - c beta0 t.
+// Per-particle quantities that depend on ps alone are computed once per
+// launch (ps changes only in RF cavities, after which they are refreshed).
 #pragma once
 
 #include "sc_internal.cuh"
 
 namespace sc {
 
+enum : int { QF_ZERO = 0, QF_FOCUS_X = 1, QF_FOCUS_Y = 2 };
+
+// Largest chromatic phase shift |Delta| = |theta0 (sqrt(1-ps) - 1)| handled by
+// the angle-addition series (truncation below 1e-18); beyond it the library
+// sin/cos/sinh/cosh are used.
+constexpr double kMaxDelta = 0.02;
+
 struct State {
   double x, px, y, py, sg, ps;
 };
 
-struct BeamK {
-  double beta0_sq, inv_gamma0_sq, rf_scale, two_pi_over_c;
+struct PsConst {
+  double opd2;  // (1+delta)^2 = 1 + 2 ps + beta0^2 ps^2        (Eq. BEND2)
+  double opb;   // 1 + beta0^2 ps = (1+delta) d(delta)/d(ps)
+  double opm;   // 1 - ps, the quadrupole's chromatic factor     (Sec. III-B)
+  double s1;    // sqrt(1 - ps)
+  double r;     // 1/sqrt(1 - ps)
+  double qi;    // 1/(4 (1 - ps))
 };
 
-// Exact field-free drift (Sec. III-A, uniform field solved without the
-// approximate Hamiltonian).  (1+delta)^2 = 1 + 2 ps + beta0^2 ps^2 (Eq. BEND2),
-// 1/pz = ((1+delta)^2 - px^2 - py^2)^(-1/2):
-//   x += L px/pz, y += L py/pz, sg += L (1 - (1 + beta0^2 ps)/pz).
-__device__ __forceinline__ void map_drift(State& s, double L, const BeamK& b) {
-  const double opd2 = fma(b.beta0_sq * s.ps, s.ps, fma(2.0, s.ps, 1.0));
-  const double rpz = rsqrt(opd2 - s.px * s.px - s.py * s.py);
+__device__ __forceinline__ void ps_const(PsConst& k, double ps, double beta0_sq, bool quads) {
+  k.opd2 = fma(beta0_sq * ps, ps, fma(2.0, ps, 1.0));
+  k.opb = fma(beta0_sq, ps, 1.0);
+  k.opm = 1.0 - ps;
+  if (quads) {
+    k.r = rsqrt(k.opm);
+    k.s1 = k.opm * k.r;
+    k.qi = 0.25 * k.r * k.r;
+  } else {
+    k.r = k.s1 = k.qi = 0.0;
+  }
+}
+
+// Exact drift (Sec. III-A): with pz = sqrt((1+delta)^2 - px^2 - py^2),
+// x += L px/pz, y += L py/pz, sg += L (1 - (1 + beta0^2 ps)/pz).
+// e.p[0] = L.
+__device__ __forceinline__ void map_drift(State& s, const DevElem& e, const PsConst& k) {
+  const double L = e.p[0];
+  const double rpz = rsqrt(fma(-s.py, s.py, fma(-s.px, s.px, k.opd2)));
   const double Lr = L * rpz;
   s.x = fma(Lr, s.px, s.x);
   s.y = fma(Lr, s.py, s.y);
-  s.sg += L - Lr * fma(b.beta0_sq, s.ps, 1.0);
+  s.sg += fma(-Lr, k.opb, L);
 }
 
-// Flow of H0 (k1 -> 0 limit of the quadrupole): straight line with the
-// chromatic factor (1 - ps).
-__device__ __forceinline__ void map_h0(State& s, double L, const BeamK& b) {
-  const double f = (1.0 - s.ps) * L;
-  s.x = fma(f, s.px, s.x);
-  s.y = fma(f, s.py, s.y);
-  s.sg += s.ps * L * b.inv_gamma0_sq - 0.5 * L * (s.px * s.px + s.py * s.py);
-}
-
-// One plane of the thick quadrupole (Sec. III-B), w = sqrt(|k1|(1-ps)),
-// a = sqrt((1-ps)/|k1|) = (1-ps)/w, bq = sqrt(|k1|/(1-ps)) = w/(1-ps).
-// Focusing: u' = u c + a pu s, pu' = pu c - bq u s (c, s = cos, sin wL);
-// defocusing: cosh/sinh and + sign.  Returns int_0^L pu(s)^2 ds.
-template <bool FOC>
-__device__ __forceinline__ double quad_plane(double& u, double& pu, double w, double a, double bq, double L) {
-  double c, s;
-  if (FOC) {
-    sincos(w * L, &s, &c);
-  } else {
-    s = sinh(w * L);
-    c = cosh(w * L);
-  }
-  const double u0 = u, p0 = pu;
-  const double sc2w = s * c / (2.0 * w);
-  const double s2w = s * s / (2.0 * w);
-  if (FOC) {
-    u = fma(u0, c, a * p0 * s);
-    pu = fma(p0, c, -bq * u0 * s);
-    const double icc = 0.5 * L + sc2w, iss = 0.5 * L - sc2w;
-    return p0 * p0 * icc - 2.0 * p0 * bq * u0 * s2w + bq * bq * u0 * u0 * iss;
-  } else {
-    u = fma(u0, c, a * p0 * s);
-    pu = fma(p0, c, bq * u0 * s);
-    const double icc = 0.5 * L + sc2w, iss = -0.5 * L + sc2w;
-    return p0 * p0 * icc + 2.0 * p0 * bq * u0 * s2w + bq * bq * u0 * u0 * iss;
-  }
-}
-
-// Thick quadrupole: planes as above (k1 > 0 focuses x), and
-// sg += ps L / gamma0^2 - 1/2 (int px^2 + int py^2).
-__device__ __forceinline__ void map_quad(State& s, double L, double k1, const BeamK& b) {
-  if (k1 == 0.0) {
-    map_h0(s, L, b);
+// Thick quadrupole (Sec. III-B) for H_approx with K1 = k1:
+//   w = sqrt(|k1| (1-ps)), a = sqrt((1-ps)/|k1|) = s1/sqk, bq = sqrt(|k1|/(1-ps)) = sqk r
+//   focusing plane:   u = u0 cos wL + a pu0 sin wL,  pu = pu0 cos wL - bq u0 sin wL
+//   defocusing plane: u = u0 cosh wL + a pu0 sinh wL, pu = pu0 cosh wL + bq u0 sinh wL
+// wL = theta0 s1 = theta0 + Delta, theta0 = sqk L; cos/sin/cosh/sinh of
+// theta0 come from the host, those of the small Delta from their Taylor
+// series, combined by the addition theorems.
+// sg: d sg/ds = ps/gamma0^2 - (px^2+py^2)/2.  Each plane conserves
+// h_u = ((1-ps) pu^2 + k_u u^2)/2 (k_x = k1, k_y = -k1) and
+// d(u pu)/ds = (1-ps) pu^2 - k_u u^2, so
+//   int_0^L pu^2 ds = (h_u L + [u pu]_0^L / 2) / (1-ps),
+// which gives sg += ps L/gamma0^2 - (L S2 + D) / (4 (1-ps)) with
+// S2 = (1-ps)(px0^2+py0^2) + k1 (x0^2 - y0^2), D = [x px + y py]_0^L.
+// e.p = {L, theta0, cos theta0, sin theta0, cosh theta0, sinh theta0, sqk, 1/sqk, k1},
+// e.flags = QF_*; the L/gamma0^2 term is e.p[0] * inv_gamma0_sq.
+__device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
+  const double L = e.p[0];
+  if (e.flags == QF_ZERO) {  // flow of H0: straight line with the chromatic factor
+    const double f = k.opm * L;
+    const double pp = fma(s.px, s.px, s.py * s.py);
+    s.x = fma(f, s.px, s.x);
+    s.y = fma(f, s.py, s.y);
+    s.sg = fma(-0.5 * L, pp, fma(s.ps, L * inv_gamma0_sq, s.sg));
     return;
   }
-  const double ak = fabs(k1);
-  const double opm = 1.0 - s.ps;
-  const double w = sqrt(ak * opm);
-  const double a = opm / w;
-  const double bq = w / opm;
-  double Ix, Iy;
-  if (k1 > 0.0) {
-    Ix = quad_plane<true>(s.x, s.px, w, a, bq, L);
-    Iy = quad_plane<false>(s.y, s.py, w, a, bq, L);
+  const double th0 = e.p[1];
+  const double delta = fma(th0, k.s1, -th0);
+  double c, sn, ch, sh;
+  if (fabs(delta) <= kMaxDelta) {
+    const double d2 = delta * delta;
+    double p = fma(d2, -1.0 / 5040.0, 1.0 / 120.0);
+    p = fma(d2, p, -1.0 / 6.0) * d2;
+    const double sd = fma(delta, p, delta);  // sin(delta)
+    double q = fma(d2, -1.0 / 720.0, 1.0 / 24.0);
+    const double cm = fma(d2, q, -0.5) * d2;  // cos(delta) - 1
+    double ph = fma(d2, 1.0 / 5040.0, 1.0 / 120.0);
+    ph = fma(d2, ph, 1.0 / 6.0) * d2;
+    const double shd = fma(delta, ph, delta);  // sinh(delta)
+    double qh = fma(d2, 1.0 / 720.0, 1.0 / 24.0);
+    const double chm = fma(d2, qh, 0.5) * d2;  // cosh(delta) - 1
+    const double c0 = e.p[2], s0 = e.p[3], ch0 = e.p[4], sh0 = e.p[5];
+    c = fma(-s0, sd, fma(c0, cm, c0));
+    sn = fma(c0, sd, fma(s0, cm, s0));
+    ch = fma(sh0, shd, fma(ch0, chm, ch0));
+    sh = fma(ch0, shd, fma(sh0, chm, sh0));
   } else {
-    Ix = quad_plane<false>(s.x, s.px, w, a, bq, L);
-    Iy = quad_plane<true>(s.y, s.py, w, a, bq, L);
+    const double th = th0 * k.s1;
+    sincos(th, &sn, &c);
+    ch = cosh(th);
+    sh = sinh(th);
   }
-  s.sg += s.ps * L * b.inv_gamma0_sq - 0.5 * (Ix + Iy);
+  const double a = k.s1 * e.p[7];
+  const double bq = e.p[6] * k.r;
+  const double x0 = s.x, px0 = s.px, y0 = s.y, py0 = s.py;
+  const double S2 = fma(e.p[8], fma(x0, x0, -y0 * y0), k.opm * fma(px0, px0, py0 * py0));
+  const double D0 = fma(x0, px0, y0 * py0);
+  // focusing plane on trig (c, sn), defocusing on hyperbolic (ch, sh)
+  double cx, sx_a, sx_b, cy, sy_a, sy_b;
+  if (e.flags == QF_FOCUS_X) {
+    cx = c;  sx_a = a * sn;  sx_b = -bq * sn;
+    cy = ch; sy_a = a * sh;  sy_b = bq * sh;
+  } else {
+    cx = ch; sx_a = a * sh;  sx_b = bq * sh;
+    cy = c;  sy_a = a * sn;  sy_b = -bq * sn;
+  }
+  s.x = fma(cx, x0, sx_a * px0);
+  s.px = fma(cx, px0, sx_b * x0);
+  s.y = fma(cy, y0, sy_a * py0);
+  s.py = fma(cy, py0, sy_b * y0);
+  const double D = fma(s.x, s.px, s.y * s.py) - D0;
+  s.sg = fma(-fma(L, S2, D), k.qi, fma(s.ps, L * inv_gamma0_sq, s.sg));
 }
 
-// Thin sextupole (V-step of Eq. Sym2): px -= k2l/2 (x^2 - y^2), py += k2l x y.
-__device__ __forceinline__ void map_sext(State& s, double k2l) {
-  s.px -= 0.5 * k2l * (s.x - s.y) * (s.x + s.y);
-  s.py = fma(k2l * s.x, s.y, s.py);
+// Thin sextupole (the V step of Eq. Sym2): px -= k2l/2 (x^2 - y^2), py += k2l x y.
+// e.p = {k2l/2, k2l}.
+__device__ __forceinline__ void map_sext(State& s, const DevElem& e) {
+  s.px = fma(-e.p[0], (s.x - s.y) * (s.x + s.y), s.px);
+  s.py = fma(e.p[1] * s.x, s.y, s.py);
 }
 
-// Linear sector dipole from H_approx with curvature h = angle/L (Sec. III,
-// Eq. H including the bending field's h^2 x^2/2).
-__device__ __forceinline__ void map_bend(State& s, double L, double angle, const BeamK& b) {
-  if (angle == 0.0) {
-    map_h0(s, L, b);
+// Linear sector dipole from H_approx with curvature h (Sec. III, Eq. H plus
+// the bending field's h^2 x^2 / 2):
+//   x = C x0 + (S/h) px0 + ((1-C)/h) ps,  px = -hS x0 + C px0 + S ps,
+//   y += L py, sg += ps L/gamma0^2 - (S x0 + ((1-C)/h) px0 + (L - S/h) ps).
+// e.p = {L, C, S, S/h, (1-C)/h, h S, L - S/h}; angle 0: e.flags = 1 (H0 flow).
+__device__ __forceinline__ void map_bend(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
+  const double L = e.p[0];
+  if (e.flags == 1) {
+    const double f = k.opm * L;
+    const double pp = fma(s.px, s.px, s.py * s.py);
+    s.x = fma(f, s.px, s.x);
+    s.y = fma(f, s.py, s.y);
+    s.sg = fma(-0.5 * L, pp, fma(s.ps, L * inv_gamma0_sq, s.sg));
     return;
   }
-  const double h = angle / L;
-  double S, C;
-  sincos(angle, &S, &C);
+  const double C = e.p[1], S = e.p[2], Soh = e.p[3], Cm = e.p[4], hS = e.p[5], LS = e.p[6];
   const double x0 = s.x, px0 = s.px, ps = s.ps;
-  s.x = x0 * C + px0 * S / h + ps * (1.0 - C) / h;
-  s.px = -x0 * h * S + px0 * C + ps * S;
-  s.y = fma(s.py, L, s.y);
-  s.sg += ps * L * b.inv_gamma0_sq - (x0 * S + px0 * (1.0 - C) / h + ps * (L - S / h));
+  s.x = fma(C, x0, fma(Soh, px0, Cm * ps));
+  s.px = fma(-hS, x0, fma(C, px0, S * ps));
+  s.y = fma(L, s.py, s.y);
+  s.sg = fma(ps, L * inv_gamma0_sq, s.sg) - fma(S, x0, fma(Cm, px0, LS * ps));
 }
 
-// Thin RF cavity: ps += volt / (beta0^2 E0) sin(lag - 2 pi h sg / C).
-__device__ __forceinline__ void map_rf(State& s, double volt, double harmonic, double lag, const BeamK& b) {
-  s.ps += volt * b.rf_scale * sin(lag - b.two_pi_over_c * harmonic * s.sg);
+// Thin RF cavity: ps += V/(beta0^2 E0) sin(lag - 2 pi h sg / C).
+// e.p = {V/(beta0^2 E0), 2 pi h / C, lag}.
+__device__ __forceinline__ void map_rf(State& s, const DevElem& e) {
+  s.ps = fma(e.p[0], sin(fma(-e.p[1], s.sg, e.p[2])), s.ps);
 }
 
-__device__ __forceinline__ void push_elements(State& s, const sc_element* __restrict__ el, int n_elem,
-                                              const BeamK& b) {
+// quads: the segment holds a quadrupole (then the square roots of 1-ps are needed).
+__device__ __forceinline__ void push_elements(State& s, const DevElem* __restrict__ el, int n_elem,
+                                              double beta0_sq, double inv_gamma0_sq, bool quads) {
+  PsConst k;
+  ps_const(k, s.ps, beta0_sq, quads);
 #pragma unroll 1
-  for (int k = 0; k < n_elem; ++k) {
-    const int type = __ldg(&el[k].type);
-    const double L = __ldg(&el[k].length);
-    switch (type) {
-      case SC_DRIFT: map_drift(s, L, b); break;
-      case SC_QUAD: map_quad(s, L, __ldg(&el[k].k1), b); break;
-      case SC_SEXT: map_sext(s, __ldg(&el[k].k2l)); break;
-      case SC_BEND: map_bend(s, L, __ldg(&el[k].angle), b); break;
-      case SC_RF: map_rf(s, __ldg(&el[k].volt), __ldg(&el[k].harmonic), __ldg(&el[k].lag), b); break;
+  for (int i = 0; i < n_elem; ++i) {
+    const DevElem e = el[i];
+    switch (e.type) {
+      case SC_DRIFT: map_drift(s, e, k); break;
+      case SC_QUAD: map_quad(s, e, k, inv_gamma0_sq); break;
+      case SC_SEXT: map_sext(s, e); break;
+      case SC_BEND: map_bend(s, e, k, inv_gamma0_sq); break;
+      case SC_RF:
+        map_rf(s, e);
+        ps_const(k, s.ps, beta0_sq, quads);
+        break;
       default: break;
     }
   }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "sc.h"
 
@@ -31,8 +32,18 @@ struct GridGeom {
   double xlast, ylast;  // (double)(nx-1), (double)(ny-1): exclusive upper bounds of xi, eta
 };
 
-// Kick/push/deposit launch parameters, passed by value (constant bank).
+// Element compiled for the kernels: the user's sc_element plus per-element
+// constants precomputed on the host in float64 (see compile_elements).
+struct DevElem {
+  int type;
+  int flags;
+  double p[9];
+};
 
+// Segments up to this many elements travel inside the launch parameters.
+constexpr int KP_INLINE = 12;
+
+// Kick/push/deposit launch parameters, passed by value (constant bank).
 struct KPParams {
   double *x, *px, *y, *py, *sg, *ps;
   int64_t n;
@@ -41,16 +52,26 @@ struct KPParams {
   const double2* E;  // (Ex, Ey) per node of the kick grid
   double kl;         // K * L_sc
   int do_kick;
+  // Cell cache: the deposit of the previous step located every particle on
+  // the same grid at the same position; the gather reuses it.  cell = j*nx+i
+  // or -1 (outside), frac = (fx, fy).  NULL: locate again.
+  int* cell;
+  double2* frac;
   // deposit
   int do_deposit;
   GridGeom gd;
   unsigned long long* Q;      // int64 charge of the deposit grid
   unsigned long long* n_out;  // running count of particles outside the deposit grid
   // beam constants
-  double beta0_sq, inv_gamma0_sq, rf_scale, two_pi_over_c;
-  const sc_element* el;  // device array of the segment's elements
+  double beta0_sq, inv_gamma0_sq;
+  const DevElem* el;  // device array of the segment's compiled elements, or NULL: use inl
   int n_elem;
+  int has_quad;       // the segment holds an SC_QUAD
+  DevElem inl[KP_INLINE];
 };
+
+// Host: compile n user elements into out (float64 constants per element).
+void compile_elements(const sc_element* in, int n, const sc_beam* b, DevElem* out);
 
 // Solve scratch and spectra for the float64 FFT form.
 struct Fft64Plan {
@@ -86,7 +107,7 @@ struct sc_grid {
   sc::TrackPlan* track;
   int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
   int kp_blocks_plain;         // kick/push without a deposit
-  sc_element* el_stage;        // device staging for sc_kick_push's elements
+  sc::DevElem* el_stage;       // device copy of sc_kick_push's last long segment
   int el_stage_cap;
 };
 

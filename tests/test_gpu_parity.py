@@ -188,3 +188,28 @@ def test_track_c2_one_turn_full_size():
     oracle.track(og, ref, b, lat, 1)
     err = rel_state_err(got, ref)
     assert max(err.values()) < 1e-10, err
+
+
+def test_kick_push_long_segment():
+    """More elements than fit in the launch parameters (device-array path)."""
+    parts, b, grid, lat = synth.workload("c1", n=3000)
+    b = dict(b, circumference=264.0)
+    cell = [synth.elem(synth.QUAD, 0.4, k1=0.9), synth.elem(synth.DRIFT, 1.0), synth.elem(synth.SEXT, k2l=0.5),
+            synth.elem(synth.QUAD, 0.4, k1=-0.9), synth.elem(synth.DRIFT, 1.0), synth.elem(synth.BEND, 0.8, angle=0.02)]
+    elems = synth.table(cell * 6)
+    got, ref, _, _ = _one_step(parts, b, grid, elems, 2.0)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+
+
+def test_quads_large_momentum_offsets():
+    """psigma up to +-0.3 drives the chromatic phase shift of the quadrupole
+    past the series range into the library-trig branch."""
+    parts, b, grid, lat = synth.workload("c1", n=4096)
+    rng = np.random.default_rng(5)
+    parts["psigma"] = rng.uniform(-0.3, 0.3, 4096)
+    elems = synth.table([synth.elem(synth.QUAD, 1.0, k1=0.8), synth.elem(synth.QUAD, 1.0, k1=-1.3),
+                         synth.elem(synth.QUAD, 0.5, k1=0.0), synth.elem(synth.DRIFT, 3.0)])
+    got, ref, _, _ = _one_step(parts, b, grid, elems, 0.0)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
