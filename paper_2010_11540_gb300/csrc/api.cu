@@ -318,6 +318,7 @@ sc_status sc_grid_read(sc_grid* g, int64_t* Q, double* Ex, double* Ey, int64_t* 
     SC_CUDA(cudaMemcpy(&v, g->n_out, 8, cudaMemcpyDeviceToHost));
     *n_out = (int64_t)v;
   }
+  if (tf32_error(g)) return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
   return SC_OK;
 }
 

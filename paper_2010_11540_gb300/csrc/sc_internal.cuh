@@ -129,6 +129,7 @@ sc_status fft64_solve(sc_grid* g);
 sc_status tf32_create(sc_grid* g);
 void tf32_destroy(sc_grid* g);
 sc_status tf32_solve(sc_grid* g);
+int tf32_error(sc_grid* g);  // 1 when a tensor-core solve gave up on a bounded wait
 // diag.cu
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
                          cudaStream_t s);

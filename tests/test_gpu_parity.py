@@ -213,3 +213,62 @@ def test_quads_large_momentum_offsets():
     got, ref, _, _ = _one_step(parts, b, grid, elems, 0.0)
     err = rel_state_err(got, ref)
     assert max(err.values()) < 1e-10, err
+
+
+# ------------------------------------------------------------------ split-TF32 tensor-core solve
+@pytest.mark.parametrize("n", [128, 256])
+def test_solve_tf32_fields_within_1e5(n):
+    parts = synth.gaussian_bunch(1000000, 31 + n, 4e-3, 3e-3, 1e-4, 1e-4)
+    grid = (n, n, -0.02, 0.02, -0.015, 0.015)
+    g = sc.create_grid(*grid, precision="tf32x3")
+    og = oracle.Geometry(*grid)
+    Qo, _ = oracle.deposit(og, parts["x"], parts["y"])
+    sc.grid_write_charge(g, Qo, len(parts["x"]))
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    Exo, Eyo = oracle.solve(og, Qo, len(parts["x"]))
+    assert rel_l2(Ex, Exo) < 1e-5 and rel_l2(Ey, Eyo) < 1e-5, (rel_l2(Ex, Exo), rel_l2(Ey, Eyo))
+    # a second solve on the same grid gives the same fields (no state leaks between solves)
+    sc.solve(g)
+    _, Ex2, Ey2, _ = sc.grid_read(g)
+    assert np.array_equal(Ex, Ex2) and np.array_equal(Ey, Ey2)
+
+
+def test_solve_tf32_point_charges():
+    """Sparse charge in the corners: the worst case for relative field error."""
+    grid = (128, 128, 0.0, 1.0, 0.0, 1.0)
+    g = sc.create_grid(*grid, precision="tf32x3")
+    og = oracle.Geometry(*grid)
+    Q = np.zeros((128, 128), dtype=np.int64)
+    Q[0, 0] = 1 << 40
+    Q[127, 127] = 3 << 40
+    Q[64, 3] = 2 << 40
+    sc.grid_write_charge(g, Q, 6)
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    Exo, Eyo = oracle.solve(og, Q, 6)
+    assert rel_l2(Ex, Exo) < 1e-5 and rel_l2(Ey, Eyo) < 1e-5, (rel_l2(Ex, Exo), rel_l2(Ey, Eyo))
+
+
+def test_tf32_unsupported_size():
+    with pytest.raises(sc.ScError) as e:
+        sc.create_grid(64, 64, -1.0, 1.0, -1.0, 1.0, precision="tf32x3")
+    assert e.value.code == -7
+
+
+def test_track_tf32_statistics():
+    """Split-precision form: one turn of the bench ring at 2e5 particles; rms
+    emittances and the per-coordinate rms agree with the oracle within 1e-3."""
+    parts, b, grid, lat = synth.workload("c2", n=200000)
+    b = dict(b, n_lambda=5e11)
+    g, og = grid_pair(grid, precision="tf32x3")
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(og, ref, b, lat, 1)
+    eg, eo = oracle.emittances(got), oracle.emittances(ref)
+    for a, c in zip(eg, eo):
+        assert abs(a / c - 1) < 1e-3
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-4, err
