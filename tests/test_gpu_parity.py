@@ -257,10 +257,10 @@ def test_tf32_unsupported_size():
 
 
 def test_track_tf32_statistics():
-    """Split-precision form: one turn of the bench ring at 2e5 particles; rms
-    emittances and the per-coordinate rms agree with the oracle within 1e-3."""
+    """Split-precision form: one turn of the bench ring at 2e5 particles at the
+    workload's line density: rms emittances within 1e-3 of the oracle, and every
+    coordinate within 1e-5 of its rms (the 1e-5 field error, propagated)."""
     parts, b, grid, lat = synth.workload("c2", n=200000)
-    b = dict(b, n_lambda=5e11)
     g, og = grid_pair(grid, precision="tf32x3")
     st = to_gpu(parts)
     sc.track_turns(g, st, b, lat, 1)
@@ -271,4 +271,4 @@ def test_track_tf32_statistics():
     for a, c in zip(eg, eo):
         assert abs(a / c - 1) < 1e-3
     err = rel_state_err(got, ref)
-    assert max(err.values()) < 1e-4, err
+    assert max(err.values()) < 1e-5, err
