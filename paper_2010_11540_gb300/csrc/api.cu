@@ -144,9 +144,9 @@ void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, 
   }
 }
 
-sc_status solve_dispatch(sc_grid* g) {
-  if (g->precision == SC_SOLVE_TF32X3) return tf32_solve(g);
-  return fft64_solve(g);
+sc_status solve_dispatch(sc_grid* g, bool zero_q) {
+  if (g->precision == SC_SOLVE_TF32X3) return tf32_solve(g, zero_q);
+  return fft64_solve(g, zero_q);
 }
 
 }  // namespace
@@ -265,7 +265,7 @@ sc_status sc_deposit(sc_grid* g, const sc_particles* p) {
 
 sc_status sc_solve(sc_grid* g) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
-  return solve_dispatch(g);
+  return solve_dispatch(g, false);
 }
 
 sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, double L_sc, const sc_element* elems,
@@ -386,7 +386,6 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     }
     g->n_particles = p->n;
     const double K = kick_strength(b);
-    const size_t qbytes = (size_t)g->nx * g->ny * 8;
     // prologue: charge (and cell cache) at the first marker for lattices that open with one
     T->prologue = base_params(p, b);
     set_deposit(T->prologue, g);
@@ -401,10 +400,10 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       const int nh = marks.empty() ? n_elems : marks[0];
       set_elements(P, lattice, nh, b, T->d_elems);
       if (!marks.empty()) {
+        // the turn's last solve cleared the charge (and the prologue did before the first turn)
         set_deposit(P, g);
         P.cell = T->cell;
         P.frac = T->frac;
-        if (cudaMemsetAsync(g->Q, 0, qbytes, g->stream) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "memset");
       }
       if (!cst)
         cst = launch_kick_push(P, marks.empty() ? nullptr : g, marks.empty() ? g->kp_blocks_plain : g->kp_blocks,
@@ -414,7 +413,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       const int m = marks[k];
       const int end = (k + 1 < marks.size()) ? marks[k + 1] : n_elems;
       const double prev = (k > 0) ? s[marks[k - 1]] : s[marks.back()] - circ;
-      cst = solve_dispatch(g);
+      // the solve clears the charge after reading it, ready for this marker's deposit
+      cst = solve_dispatch(g, true);
       if (cst) break;
       KPParams P = base_params(p, b);
       set_kick(P, g, K * (s[m] - prev));
@@ -423,13 +423,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       P.cell = T->cell;
       P.frac = T->frac;
       const bool dep = (k + 1 < marks.size()) || !T->has_head;
-      if (dep) {
-        set_deposit(P, g);
-        if (cudaMemsetAsync(g->Q, 0, qbytes, g->stream) != cudaSuccess) {
-          cst = set_error(SC_ERR_CUDA, "memset");
-          break;
-        }
-      }
+      if (dep) set_deposit(P, g);
       cst = launch_kick_push(P, dep ? g : nullptr, dep ? g->kp_blocks : g->kp_blocks_plain, g->stream);
     }
     cudaGraph_t graph = nullptr;

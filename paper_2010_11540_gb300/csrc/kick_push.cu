@@ -20,10 +20,9 @@ template <bool TILE, bool CACHE>
 __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
   const int cells = P.gd.nx * P.gd.ny;
-  if (TILE) {
-    tile_zero(tile, cells);
-    __syncthreads();
-  }
+  if (TILE) tile_zero(tile, cells);
+  pdl_wait();  // fields, charge grid and particles of the previous kernels
+  if (TILE) __syncthreads();
   unsigned long long* dst = TILE ? tile : P.Q;
   unsigned int out = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -74,6 +73,7 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
     P.sg[p] = s.sg;
     P.ps[p] = s.ps;
   }
+  pdl_allow();
   if (P.do_deposit) {
     count_out(out, P.n_out);
     if (TILE) {
@@ -111,15 +111,9 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
   const int64_t need = (P.n + kKPThreads - 1) / kKPThreads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
   const int smem = tile ? dep->nx * dep->ny * 8 : 0;
-  if (tile && cache)
-    kick_push_kernel<true, true><<<blocks, kKPThreads, smem, s>>>(P);
-  else if (tile)
-    kick_push_kernel<true, false><<<blocks, kKPThreads, smem, s>>>(P);
-  else if (cache)
-    kick_push_kernel<false, true><<<blocks, kKPThreads, 0, s>>>(P);
-  else
-    kick_push_kernel<false, false><<<blocks, kKPThreads, 0, s>>>(P);
-  SC_CUDA(cudaGetLastError());
+  auto k = tile ? (cache ? kick_push_kernel<true, true> : kick_push_kernel<true, false>)
+                : (cache ? kick_push_kernel<false, true> : kick_push_kernel<false, false>);
+  SC_CUDA(launch_pdl(k, dim3(blocks), dim3(kKPThreads), (size_t)smem, s, P));
   return SC_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sc.h"
@@ -22,6 +23,31 @@ sc_status cuda_error(cudaError_t e, const char* what);
     cudaError_t _e = (call);                             \
     if (_e != cudaSuccess) return sc::cuda_error(_e, #call); \
   } while (0)
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch: kernels of a turn are launched so that the
+// next one may start its prologue while the previous one finishes; each kernel
+// calls pdl_wait() before touching anything the previous kernels wrote, and
+// pdl_allow() once its dependents may be scheduled.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---------------------------------------------------------------------------
 // Grid geometry as the kernels see it.  Nodes x_i = xmin + i*hx.
@@ -124,11 +150,12 @@ int kick_push_blocks_for(int smem_bytes, bool tile);
 // solve_fft64.cu
 sc_status fft64_create(sc_grid* g);
 void fft64_destroy(sc_grid* g);
-sc_status fft64_solve(sc_grid* g);
+// zero_q: also clear the charge grid once it has been read (for the next deposit)
+sc_status fft64_solve(sc_grid* g, bool zero_q);
 // solve_tf32.cu
 sc_status tf32_create(sc_grid* g);
 void tf32_destroy(sc_grid* g);
-sc_status tf32_solve(sc_grid* g);
+sc_status tf32_solve(sc_grid* g, bool zero_q);
 int tf32_error(sc_grid* g);  // 1 when a tensor-core solve gave up on a bounded wait
 // diag.cu
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,

@@ -53,19 +53,24 @@ __global__ void fft64_rows_fwd(const unsigned long long* __restrict__ Q, int nx,
   extern __shared__ double2 sm[];
   const int Mx = 2 * nx, j = blockIdx.x, t = threadIdx.x;
   double2 *a = sm, *b = sm + Mx;
+  pdl_wait();
   a[t] = make_double2((double)(long long)Q[(size_t)j * nx + t] * scale, 0.0);
   a[t + nx] = make_double2(0.0, 0.0);
   __syncthreads();
   const double2* r = fft_smem<false>(a, b, Mx, twx);
+  pdl_allow();
   for (int p = t; p <= nx; p += nx) F1[(size_t)j * (nx + 1) + p] = r[p];
 }
 
 __global__ void fft64_columns(const double2* __restrict__ F1, int nx, int ny, const double* __restrict__ Sx,
                               const double* __restrict__ Sy, double2* __restrict__ Hx, double2* __restrict__ Hy,
-                              const double2* __restrict__ twy) {
+                              const double2* __restrict__ twy, unsigned long long* Qzero) {
   extern __shared__ double2 sm[];
   const int My = 2 * ny, p = blockIdx.x, t = threadIdx.x;
   double2 *A = sm, *B = sm + My, *C = sm + 2 * My, *D = sm + 3 * My;
+  pdl_wait();
+  if (Qzero)  // the row transform has read the charge: clear it for the next deposit
+    for (int c = blockIdx.x * blockDim.x + t; c < nx * ny; c += gridDim.x * blockDim.x) Qzero[c] = 0ull;
   A[t] = F1[(size_t)t * (nx + 1) + p];
   A[t + ny] = make_double2(0.0, 0.0);
   __syncthreads();
@@ -80,6 +85,7 @@ __global__ void fft64_columns(const double2* __restrict__ F1, int nx, int ny, co
   __syncthreads();
   const double2* rx = fft_smem<true>(C, freebuf, My, twy);
   const double2* ry = fft_smem<true>(D, R, My, twy);
+  pdl_allow();
   Hx[(size_t)t * (nx + 1) + p] = rx[t];
   Hy[(size_t)t * (nx + 1) + p] = ry[t];
 }
@@ -91,6 +97,7 @@ __global__ void fft64_rows_inv(const double2* __restrict__ Hx, const double2* __
   double2 *A = sm, *B = sm + Mx, *C = sm + 2 * Mx, *D = sm + 3 * Mx;
   const double2* hx = Hx + (size_t)j * (nx + 1);
   const double2* hy = Hy + (size_t)j * (nx + 1);
+  pdl_wait();
   // p = t (<= nx) straight from the half spectrum; p = t + nx from Hermitian symmetry
   A[t] = hx[t];
   C[t] = hy[t];
@@ -108,6 +115,7 @@ __global__ void fft64_rows_inv(const double2* __restrict__ Hx, const double2* __
   __syncthreads();
   const double2* rx = fft_smem<true>(A, B, Mx, twx);
   const double2* ry = fft_smem<true>(C, D, Mx, twx);
+  pdl_allow();
   E[(size_t)j * nx + t] = make_double2(rx[t].x * inv_norm, ry[t].x * inv_norm);
 }
 
@@ -235,15 +243,17 @@ void fft64_destroy(sc_grid* g) {
   f = Fft64Plan{};
 }
 
-sc_status fft64_solve(sc_grid* g) {
+sc_status fft64_solve(sc_grid* g, bool zero_q) {
   const int nx = g->nx, ny = g->ny, Mx = 2 * nx, My = 2 * ny;
   Fft64Plan& f = g->fft;
   const double scale = 1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1);
-  fft64_rows_fwd<<<ny, nx, 2 * Mx * sizeof(double2), g->stream>>>(g->Q, nx, scale, f.F1, f.twx);
-  fft64_columns<<<nx + 1, ny, 4 * My * sizeof(double2), g->stream>>>(f.F1, nx, ny, f.Sx, f.Sy, f.Hx, f.Hy, f.twy);
-  fft64_rows_inv<<<ny, nx, 4 * Mx * sizeof(double2), g->stream>>>(f.Hx, f.Hy, nx, 1.0 / ((double)Mx * (double)My),
-                                                                   g->E, f.twx);
-  SC_CUDA(cudaGetLastError());
+  SC_CUDA(launch_pdl(fft64_rows_fwd, dim3(ny), dim3(nx), 2 * Mx * sizeof(double2), g->stream,
+                     (const unsigned long long*)g->Q, nx, scale, f.F1, (const double2*)f.twx));
+  SC_CUDA(launch_pdl(fft64_columns, dim3(nx + 1), dim3(ny), 4 * My * sizeof(double2), g->stream,
+                     (const double2*)f.F1, nx, ny, (const double*)f.Sx, (const double*)f.Sy, f.Hx, f.Hy,
+                     (const double2*)f.twy, zero_q ? g->Q : (unsigned long long*)nullptr));
+  SC_CUDA(launch_pdl(fft64_rows_inv, dim3(ny), dim3(nx), 4 * Mx * sizeof(double2), g->stream, (const double2*)f.Hx,
+                     (const double2*)f.Hy, nx, 1.0 / ((double)Mx * (double)My), g->E, (const double2*)f.twx));
   return SC_OK;
 }
 

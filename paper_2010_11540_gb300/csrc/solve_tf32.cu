@@ -140,11 +140,13 @@ struct GemmArgs {
   CUtensorMap tA_hi, tA_lo, tB_hi, tB_lo;  // tB_* unused for P1
   int k_chunks;   // K / KC
   int n_tiles;    // N tiles per M block
-  int a_half;     // row offset of the second M sub-tile (MT = 2)
   int nx, ny, My, Npad;
   // P1: charge input
   const unsigned long long* Q;
   double scale;
+  // P2A: charge grid to clear for the next deposit (NULL: leave it)
+  unsigned long long* Qzero;
+  int qcells;
   // outputs / epilogue inputs
   float *out_hi, *out_lo;  // next phase's operand (P1: B2, P2A: B3, P2B: A3)
   int out_ld;              // its row length (K of the next phase)
@@ -153,20 +155,35 @@ struct GemmArgs {
   int* err;                // set to 1 when a bounded wait ran out
 };
 
-template <int PH, int MT>
+// Which operand is a constant DFT matrix (loadable before the grid dependency
+// resolves) and which is the previous kernel's output.
+template <int PH>
+struct Roles {
+  static constexpr bool CONST_A = (PH != P3);
+  static constexpr bool TMA_B = (PH != P1);
+};
+
+template <int PH>
 struct Smem {
-  static constexpr int A_TILE = TM * 128;                  // bytes of one 128-row x 32-elt tile
-  static constexpr int B_TILE = NT * 128;                  // 2 KB
-  static constexpr int STAGE = 2 * MT * A_TILE + (PH == P1 ? 0 : 2 * B_TILE);
-  static constexpr int STAGES = (MT == 2) ? 3 : 4;
-  static constexpr int B_RESIDENT_MAX_CHUNKS = 8;          // P1: q tiles for K up to 256
+  static constexpr int A_TILE = TM * 128;  // bytes of one 128-row x 32-element tile
+  static constexpr int B_TILE = NT * 128;  // 2 KB
+  static constexpr int STAGE = 2 * A_TILE + (Roles<PH>::TMA_B ? 2 * B_TILE : 0);
+  static constexpr int STAGES = (PH == P1) ? 4 : 5;
+  static constexpr int B_RESIDENT_MAX_CHUNKS = 8;  // P1: charge tiles for K up to 256
   static constexpr int RESIDENT = (PH == P1) ? 2 * B_RESIDENT_MAX_CHUNKS * B_TILE : 0;
   static constexpr int BYTES = STAGES * STAGE + RESIDENT + 1024 /*align slack*/;
 };
 
-template <int PH, int MT>
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)m) : "memory");
+}
+
+// One CTA: a 128-row x NT-column tile of C = A B^T over the whole K, with the
+// three split products accumulated in one TMEM accumulator.
+template <int PH>
 __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ GemmArgs g) {
-  using L = Smem<PH, MT>;
+  using L = Smem<PH>;
+  using R = Roles<PH>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[L::STAGES], empty_bar[L::STAGES], accum_bar;
@@ -175,9 +192,21 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mb = blockIdx.x / g.n_tiles, nb = blockIdx.x % g.n_tiles;
-  const int n0 = nb * NT;
+  const int n0 = nb * NT, a_row = mb * TM;
   unsigned char* stage_base = smem;
   unsigned char* resident = smem + L::STAGES * L::STAGE;
+  const int pre = g.k_chunks < L::STAGES ? g.k_chunks : L::STAGES;
+
+  auto load_a = [&](int kc, int st) {
+    unsigned char* sb = stage_base + st * L::STAGE;
+    tma_load_2d(sb, &g.tA_hi, &full_bar[st], kc * KC, a_row);
+    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], kc * KC, a_row);
+  };
+  auto load_b = [&](int kc, int st) {
+    unsigned char* bb = stage_base + st * L::STAGE + 2 * L::A_TILE;
+    tma_load_2d(bb, &g.tB_hi, &full_bar[st], kc * KC, n0);
+    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], kc * KC, n0);
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < L::STAGES; ++s) {
@@ -187,137 +216,156 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     mbar_init(&accum_bar, 1);
     abort_s = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    prefetch_map(&g.tA_hi);
+    prefetch_map(&g.tA_lo);
+    if (R::TMA_B) {
+      prefetch_map(&g.tB_hi);
+      prefetch_map(&g.tB_lo);
+    }
   }
   if (warp == 2) tmem_alloc(&tmem_base_s, 32);
-
-  if (PH == P1) {
-    // B operand = normalised charge rows j = n0 .. n0+NT-1, all K = nx, split hi/lo, swizzled
-    for (int e = threadIdx.x; e < NT * g.nx; e += kThreads) {
-      const int r = e / g.nx, i = e % g.nx;
-      const double qv = (double)(long long)g.Q[(size_t)(n0 + r) * g.nx + i] * g.scale;
-      const float hi = tf32_round((float)qv);
-      const float lo = tf32_round((float)(qv - (double)hi));
-      const int kc = i / KC, k = i % KC;
-      *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
-      *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
-    }
-    fence_proxy_async();
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
 
+  // constant operand of the first stages: independent of the previous kernel
+  if (threadIdx.x == 0) {
+    for (int kc = 0; kc < pre; ++kc) {
+      mbar_expect_tx(&full_bar[kc], (uint32_t)L::STAGE);
+      if (R::CONST_A)
+        load_a(kc, kc);
+      else
+        load_b(kc, kc);
+    }
+  }
+  pdl_wait();
+  if (PH == P2A && g.Qzero) {
+    // every reader of the charge (the row transform) has finished: clear it for the next deposit
+    for (int c = blockIdx.x * kThreads + threadIdx.x; c < g.qcells; c += gridDim.x * kThreads) g.Qzero[c] = 0ull;
+  }
+  if (PH == P1) {
+    // B operand = normalised charge rows j = n0 .. n0+NT-1, all K = nx, split hi/lo, swizzled.
+    // All loads of a thread are issued before any is used.
+    constexpr int PER = NT * 256 / kThreads;  // upper bound of elements per thread (nx <= 256)
+    long long v[PER];
+    const int total = NT * g.nx;
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * kThreads;
+      v[u] = (e < total) ? (long long)g.Q[(size_t)(n0 + e / g.nx) * g.nx + (e % g.nx)] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + u * kThreads;
+      if (e < total) {
+        const int r = e / g.nx, i = e % g.nx;
+        const double qv = (double)v[u] * g.scale;
+        const float hi = tf32_round((float)qv);
+        const float lo = tf32_round((float)(qv - (double)hi));
+        const int kc = i / KC, k = i % KC;
+        *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
+        *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+      }
+    }
+    fence_proxy_async();
+  }
+  __syncthreads();
+
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer
-    const uint32_t bytes = (uint32_t)L::STAGE;
-    for (int kc = 0; kc < g.k_chunks; ++kc) {
+    // ---- TMA producer: the data operand of the prefetched stages, then whole stages
+    for (int kc = 0; kc < pre; ++kc) {
+      if (R::CONST_A) {
+        if (R::TMA_B) load_b(kc, kc);
+      } else {
+        load_a(kc, kc);
+      }
+    }
+    for (int kc = pre; kc < g.k_chunks; ++kc) {
       const int st = kc % L::STAGES;
-      if (kc >= L::STAGES && !mbar_wait(&empty_bar[st], ((kc / L::STAGES) - 1) & 1)) {
+      if (!mbar_wait(&empty_bar[st], ((kc / L::STAGES) - 1) & 1)) {
         abort_s = 1;
         break;
       }
-      unsigned char* sb = stage_base + st * L::STAGE;
-      mbar_expect_tx(&full_bar[st], bytes);
-      for (int s = 0; s < MT; ++s) {
-        const int arow = mb * TM + s * g.a_half;
-        tma_load_2d(sb + (2 * s) * L::A_TILE, &g.tA_hi, &full_bar[st], kc * KC, arow);
-        tma_load_2d(sb + (2 * s + 1) * L::A_TILE, &g.tA_lo, &full_bar[st], kc * KC, arow);
-      }
-      if (PH != P1) {
-        unsigned char* bb = sb + 2 * MT * L::A_TILE;
-        tma_load_2d(bb, &g.tB_hi, &full_bar[st], kc * KC, n0);
-        tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], kc * KC, n0);
-      }
+      mbar_expect_tx(&full_bar[st], (uint32_t)L::STAGE);
+      load_a(kc, st);
+      if (R::TMA_B) load_b(kc, st);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    bool ok = true;
     for (int kc = 0; kc < g.k_chunks; ++kc) {
       const int st = kc % L::STAGES;
       if (!mbar_wait(&full_bar[st], (kc / L::STAGES) & 1)) {
-        ok = false;
         abort_s = 1;
         break;
       }
       tc_fence_after();
       unsigned char* sb = stage_base + st * L::STAGE;
-      const unsigned char* bh = (PH == P1) ? resident + (2 * kc) * L::B_TILE : sb + 2 * MT * L::A_TILE;
+      const unsigned char* bh = (PH == P1) ? resident + (2 * kc) * L::B_TILE : sb + 2 * L::A_TILE;
       const unsigned char* bl = bh + L::B_TILE;
       const uint64_t dbh = desc_sw128(smem_u32(bh)), dbl = desc_sw128(smem_u32(bl));
-      for (int s = 0; s < MT; ++s) {
-        const uint64_t dah = desc_sw128(smem_u32(sb + (2 * s) * L::A_TILE));
-        const uint64_t dal = desc_sw128(smem_u32(sb + (2 * s + 1) * L::A_TILE));
-        const uint32_t d = tmem + s * NT;
+      const uint64_t dah = desc_sw128(smem_u32(sb)), dal = desc_sw128(smem_u32(sb + L::A_TILE));
 #pragma unroll
-        for (int kk = 0; kk < KC / 8; ++kk) {
-          const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
-          mma_tf32(d, dah + o, dbh + o, kIdesc, (kc > 0 || kk > 0) ? 1u : 0u);
-          mma_tf32(d, dah + o, dbl + o, kIdesc, 1u);
-          mma_tf32(d, dal + o, dbh + o, kIdesc, 1u);
-        }
+      for (int kk = 0; kk < KC / 8; ++kk) {
+        const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
+        mma_tf32(tmem, dah + o, dbh + o, kIdesc, (kc > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, dah + o, dbl + o, kIdesc, 1u);
+        mma_tf32(tmem, dal + o, dbh + o, kIdesc, 1u);
       }
       mma_commit(&empty_bar[st]);
     }
     // always: the accumulator barrier completes once every MMA issued so far has
     // finished, so TMEM is never freed under an MMA in flight
     mma_commit(&accum_bar);
-    (void)ok;
   }
   __syncwarp();
+  pdl_allow();
 
   // ---- epilogue: all four warps; warp w owns TMEM lanes / tile rows 32w .. 32w+31
-  bool have = mbar_wait(&accum_bar, 0);
-  if (!have || abort_s) {
-    if (threadIdx.x == 0) atomicExch(g.err, 1);
-  }
+  const bool have = mbar_wait(&accum_bar, 0);
+  if ((!have || abort_s) && threadIdx.x == 0) atomicExch(g.err, 1);
   tc_fence_after();
   const int t = warp * 32 + lane;
-  float acc[MT][NT];
-  if (have) {
-#pragma unroll
-    for (int s = 0; s < MT; ++s) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + s * NT, acc[s]);
-  }
+  const int r = a_row + t;  // row of C
+  float acc[NT];
+  if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), acc);
   if (have && !abort_s) {
     if (PH == P1) {
       // row c of R1T: Re F1(j, p = c) for c <= nx, Im F1(j, p = c - nx) above
-      const int c = mb * TM + t;
-      const int p = (c <= g.nx) ? c : c - g.nx;
-      const int half = (c <= g.nx) ? 0 : 1;
+      const int p = (r <= g.nx) ? r : r - g.nx;
+      const int half = (r <= g.nx) ? 0 : 1;
       float* dh = g.out_hi + (size_t)p * g.out_ld + half * g.ny + n0;
       float* dl = g.out_lo + (size_t)p * g.out_ld + half * g.ny + n0;
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) split(acc[0][cc], dh[cc], dl[cc]);
+      for (int cc = 0; cc < NT; ++cc) split(acc[cc], dh[cc], dl[cc]);
     } else if (PH == P2A) {
-      // (Re F, Im F) at k = mb*128 + t for columns p = n0 + cc; H_f = i S_f F
-      const int k = mb * TM + t;
+      // row r < My: Re F(k = r, p) -> Im H_f = S_f Re F (column My + k of B3)
+      // row r >= My: Im F(k = r - My, p) -> Re H_f = -S_f Im F (column k)
+      const bool re = r < g.My;
+      const int k = re ? r : r - g.My;
+      const int col = re ? g.My + k : k;
+      const float sgn = re ? 1.f : -1.f;
 #pragma unroll
       for (int cc = 0; cc < NT; ++cc) {
         const int p = n0 + cc;
-        const float re = acc[0][cc], im = acc[1][cc];
-        const float sx = g.Sx[(size_t)k * g.Npad + p], sy = g.Sy[(size_t)k * g.Npad + p];
-        const size_t rx = (size_t)p * g.out_ld, ry = (size_t)(g.Npad + p) * g.out_ld;
-        split(-sx * im, g.out_hi[rx + k], g.out_lo[rx + k]);
-        split(sx * re, g.out_hi[rx + g.My + k], g.out_lo[rx + g.My + k]);
-        split(-sy * im, g.out_hi[ry + k], g.out_lo[ry + k]);
-        split(sy * re, g.out_hi[ry + g.My + k], g.out_lo[ry + g.My + k]);
+        const float f = sgn * acc[cc];
+        const size_t rx = (size_t)p * g.out_ld + col, ry = (size_t)(g.Npad + p) * g.out_ld + col;
+        split(g.Sx[(size_t)k * g.Npad + p] * f, g.out_hi[rx], g.out_lo[rx]);
+        split(g.Sy[(size_t)k * g.Npad + p] * f, g.out_hi[ry], g.out_lo[ry]);
       }
     } else if (PH == P2B) {
-      // (Re G_f, Im G_f)(j', p) at j' = mb*128 + t, columns n = f*Npad + p
-      const int jr = mb * TM + t;
+      // row r: part (Re G, Im G) = r / ny at j' = r % ny; columns n = f*Npad + p
+      const int part = r / g.ny, jr = r % g.ny;
       const int f = n0 / g.Npad, p0 = n0 % g.Npad;  // NT divides Npad: one field per tile
-      const size_t row = (size_t)(f * g.ny + jr) * g.out_ld;
+      const size_t o = (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p0;
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) {
-        split(acc[0][cc], g.out_hi[row + p0 + cc], g.out_lo[row + p0 + cc]);
-        split(acc[1][cc], g.out_hi[row + g.Npad + p0 + cc], g.out_lo[row + g.Npad + p0 + cc]);
-      }
+      for (int cc = 0; cc < NT; ++cc) split(acc[cc], g.out_hi[o + cc], g.out_lo[o + cc]);
     } else {
-      // (Ex, Ey)(j, i) at j = mb*128 + t, i = n0 + cc
-      const int j = mb * TM + t;
-      double2* e = g.E + (size_t)j * g.nx + n0;
+      // row r: field f = r / ny (Ex, Ey) at j = r % ny; columns i = n0 + cc
+      const int f = r / g.ny, j = r % g.ny;
+      double* e = (double*)(g.E + (size_t)j * g.nx + n0) + f;
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) e[cc] = make_double2((double)acc[0][cc], (double)acc[1][cc]);
+      for (int cc = 0; cc < NT; ++cc) e[2 * cc] = (double)acc[cc];
     }
   }
   tc_fence_before();
@@ -421,10 +469,15 @@ void free_mat(Mat& m) {
   m = Mat{};
 }
 
-template <int PH, int MT>
+template <int PH>
 sc_status set_smem_attr() {
-  SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PH, MT>::BYTES));
+  SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PH>::BYTES));
   return SC_OK;
+}
+
+template <int PH>
+cudaError_t launch_phase(int grid, const GemmArgs& a, cudaStream_t s) {
+  return launch_pdl(dft_gemm<PH>, dim3(grid), dim3(kThreads), Smem<PH>::BYTES, s, a);
 }
 
 void host_fft(std::complex<double>* a, int n, int stride) {
@@ -542,7 +595,6 @@ sc_status tf32_create(sc_grid* g) {
     return st;
   T->a1.k_chunks = nx / KC;
   T->a1.n_tiles = ny / NT;
-  T->a1.a_half = 0;
   T->a1.Q = g->Q;
   T->a1.out_hi = T->B2.hi;
   T->a1.out_lo = T->B2.lo;
@@ -557,13 +609,14 @@ sc_status tf32_create(sc_grid* g) {
     return st;
   T->a2a.k_chunks = 2 * ny / KC;
   T->a2a.n_tiles = Npad / NT;
-  T->a2a.a_half = My;
+  T->a2a.Qzero = nullptr;
+  T->a2a.qcells = nx * ny;
   T->a2a.Sx = T->Sx;
   T->a2a.Sy = T->Sy;
   T->a2a.out_hi = T->B3.hi;
   T->a2a.out_lo = T->B3.lo;
   T->a2a.out_ld = 2 * My;
-  T->grid2a = (My / TM) * T->a2a.n_tiles;
+  T->grid2a = (2 * My / TM) * T->a2a.n_tiles;
   // P2B: C[r][(f,p)] = W2i B3^T: M = 2ny as (Re, Im) pairs, N = 2 Npad, K = 2My
   base(T->a2b);
   if ((st = make_map(&T->a2b.tA_hi, T->W2i.hi, 2 * ny, 2 * My, TM)) ||
@@ -573,11 +626,10 @@ sc_status tf32_create(sc_grid* g) {
     return st;
   T->a2b.k_chunks = 2 * My / KC;
   T->a2b.n_tiles = 2 * Npad / NT;
-  T->a2b.a_half = ny;
   T->a2b.out_hi = T->A3.hi;
   T->a2b.out_lo = T->A3.lo;
   T->a2b.out_ld = 2 * Npad;
-  T->grid2b = (ny / TM) * T->a2b.n_tiles;
+  T->grid2b = (2 * ny / TM) * T->a2b.n_tiles;
   // P3: C[(f,j)][i] = A3 B4^T: M = 2ny as (Ex, Ey) pairs, N = nx, K = 2 Npad
   base(T->a3);
   if ((st = make_map(&T->a3.tA_hi, T->A3.hi, 2 * ny, 2 * Npad, TM)) ||
@@ -587,11 +639,10 @@ sc_status tf32_create(sc_grid* g) {
     return st;
   T->a3.k_chunks = 2 * Npad / KC;
   T->a3.n_tiles = nx / NT;
-  T->a3.a_half = ny;
   T->a3.E = g->E;
-  T->grid3 = (ny / TM) * T->a3.n_tiles;
-  if ((st = set_smem_attr<P1, 1>()) || (st = set_smem_attr<P2A, 2>()) || (st = set_smem_attr<P2B, 2>()) ||
-      (st = set_smem_attr<P3, 2>()))
+  T->grid3 = (2 * ny / TM) * T->a3.n_tiles;
+  if ((st = set_smem_attr<P1>()) || (st = set_smem_attr<P2A>()) || (st = set_smem_attr<P2B>()) ||
+      (st = set_smem_attr<P3>()))
     return st;
   return SC_OK;
 }
@@ -613,15 +664,15 @@ void tf32_destroy(sc_grid* g) {
   g->tf32 = nullptr;
 }
 
-sc_status tf32_solve(sc_grid* g) {
+sc_status tf32_solve(sc_grid* g, bool zero_q) {
   Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_ARG, "grid has no TF32 solver");
   T->a1.scale = 1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1);
-  dft_gemm<P1, 1><<<T->grid1, kThreads, Smem<P1, 1>::BYTES, g->stream>>>(T->a1);
-  dft_gemm<P2A, 2><<<T->grid2a, kThreads, Smem<P2A, 2>::BYTES, g->stream>>>(T->a2a);
-  dft_gemm<P2B, 2><<<T->grid2b, kThreads, Smem<P2B, 2>::BYTES, g->stream>>>(T->a2b);
-  dft_gemm<P3, 2><<<T->grid3, kThreads, Smem<P3, 2>::BYTES, g->stream>>>(T->a3);
-  SC_CUDA(cudaGetLastError());
+  T->a2a.Qzero = zero_q ? g->Q : nullptr;
+  SC_CUDA(launch_phase<P1>(T->grid1, T->a1, g->stream));
+  SC_CUDA(launch_phase<P2A>(T->grid2a, T->a2a, g->stream));
+  SC_CUDA(launch_phase<P2B>(T->grid2b, T->a2b, g->stream));
+  SC_CUDA(launch_phase<P3>(T->grid3, T->a3, g->stream));
   return SC_OK;
 }
 
