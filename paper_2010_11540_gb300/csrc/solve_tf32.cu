@@ -143,14 +143,14 @@ struct GemmArgs {
   int nx, ny, My, Npad;
   // P1: charge input
   const unsigned long long* Q;
-  double scale;
+  float scale;
   // P2A: charge grid to clear for the next deposit (NULL: leave it)
   unsigned long long* Qzero;
   int qcells;
   // outputs / epilogue inputs
   float *out_hi, *out_lo;  // next phase's operand (P1: B2, P2A: B3, P2B: A3)
   int out_ld;              // its row length (K of the next phase)
-  const float *Sx, *Sy;    // P2A: spectra [My][Npad]
+  const float *Sx, *Sy;    // P2A: spectra [Npad][My]
   double2* E;              // P3: fields
   int* err;                // set to 1 when a bounded wait ran out
 };
@@ -174,13 +174,31 @@ struct Smem {
   static constexpr int BYTES = STAGES * STAGE + RESIDENT + 1024 /*align slack*/;
 };
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// float at the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ float ld_dsmem(const float* local, uint32_t rank) {
+  uint32_t ra;
+  float v;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+  return v;
+}
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)m) : "memory");
 }
 
-// One CTA: a 128-row x NT-column tile of C = A B^T over the whole K, with the
-// three split products accumulated in one TMEM accumulator.
-template <int PH>
+// One cluster of SK CTAs: a 128-row x NT-column tile of C = A B^T, the K
+// chunks split evenly across the SK CTAs; each accumulates its three split
+// products in TMEM, the partial tiles are summed through distributed shared
+// memory and each CTA finishes NT/SK of the columns.
+template <int PH, int SK>
 __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ GemmArgs g) {
   using L = Smem<PH>;
   using R = Roles<PH>;
@@ -191,21 +209,24 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   __shared__ volatile int abort_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int mb = blockIdx.x / g.n_tiles, nb = blockIdx.x % g.n_tiles;
+  const int rank = (SK > 1) ? (int)cluster_rank() : 0;
+  const int tile = blockIdx.x / SK;
+  const int mb = tile / g.n_tiles, nb = tile % g.n_tiles;
   const int n0 = nb * NT, a_row = mb * TM;
   unsigned char* stage_base = smem;
   unsigned char* resident = smem + L::STAGES * L::STAGE;
-  const int pre = g.k_chunks < L::STAGES ? g.k_chunks : L::STAGES;
+  const int kpc = g.k_chunks / SK, kc0 = rank * kpc;  // this CTA's K chunks: kc0 .. kc0+kpc-1
+  const int pre = kpc < L::STAGES ? kpc : L::STAGES;
 
-  auto load_a = [&](int kc, int st) {
+  auto load_a = [&](int lk, int st) {
     unsigned char* sb = stage_base + st * L::STAGE;
-    tma_load_2d(sb, &g.tA_hi, &full_bar[st], kc * KC, a_row);
-    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], kc * KC, a_row);
+    tma_load_2d(sb, &g.tA_hi, &full_bar[st], (kc0 + lk) * KC, a_row);
+    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], (kc0 + lk) * KC, a_row);
   };
-  auto load_b = [&](int kc, int st) {
+  auto load_b = [&](int lk, int st) {
     unsigned char* bb = stage_base + st * L::STAGE + 2 * L::A_TILE;
-    tma_load_2d(bb, &g.tB_hi, &full_bar[st], kc * KC, n0);
-    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], kc * KC, n0);
+    tma_load_2d(bb, &g.tB_hi, &full_bar[st], (kc0 + lk) * KC, n0);
+    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], (kc0 + lk) * KC, n0);
   };
 
   if (threadIdx.x == 0) {
@@ -260,9 +281,10 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const int e = threadIdx.x + u * kThreads;
       if (e < total) {
         const int r = e / g.nx, i = e % g.nx;
-        const double qv = (double)v[u] * g.scale;
-        const float hi = tf32_round((float)qv);
-        const float lo = tf32_round((float)(qv - (double)hi));
+        // int64 -> float through its 32-bit halves (no FP64 instruction)
+        const float qv = fmaf(__int2float_rn((int)(v[u] >> 32)), 4294967296.f, __uint2float_rn((unsigned)v[u])) * g.scale;
+        float hi, lo;
+        split(qv, hi, lo);
         const int kc = i / KC, k = i % KC;
         *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
         *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
@@ -281,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
         load_a(kc, kc);
       }
     }
-    for (int kc = pre; kc < g.k_chunks; ++kc) {
+    for (int kc = pre; kc < kpc; ++kc) {
       const int st = kc % L::STAGES;
       if (!mbar_wait(&empty_bar[st], ((kc / L::STAGES) - 1) & 1)) {
         abort_s = 1;
@@ -293,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    for (int kc = 0; kc < g.k_chunks; ++kc) {
+    for (int kc = 0; kc < kpc; ++kc) {
       const int st = kc % L::STAGES;
       if (!mbar_wait(&full_bar[st], (kc / L::STAGES) & 1)) {
         abort_s = 1;
@@ -301,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       }
       tc_fence_after();
       unsigned char* sb = stage_base + st * L::STAGE;
-      const unsigned char* bh = (PH == P1) ? resident + (2 * kc) * L::B_TILE : sb + 2 * L::A_TILE;
+      const unsigned char* bh = (PH == P1) ? resident + (2 * (kc0 + kc)) * L::B_TILE : sb + 2 * L::A_TILE;
       const unsigned char* bl = bh + L::B_TILE;
       const uint64_t dbh = desc_sw128(smem_u32(bh)), dbl = desc_sw128(smem_u32(bl));
       const uint64_t dah = desc_sw128(smem_u32(sb)), dal = desc_sw128(smem_u32(sb + L::A_TILE));
@@ -329,15 +351,36 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   const int r = a_row + t;  // row of C
   float acc[NT];
   if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), acc);
+  constexpr int CW = NT / SK;  // columns finished by this CTA
+  const int c0 = rank * CW;
+  if (SK > 1) {
+    // partial tiles -> shared memory (the stages are idle now), summed across the cluster
+    float* red = (float*)stage_base;
+#pragma unroll
+    for (int cc = 0; cc < NT; ++cc) red[t * NT + cc] = have ? acc[cc] : 0.f;
+    cluster_sync();
+#pragma unroll
+    for (int cc = 0; cc < CW; ++cc) {
+      float v = 0.f;
+      for (int q = 0; q < SK; ++q) v += ld_dsmem(&red[t * NT + c0 + cc], (uint32_t)q);
+      acc[c0 + cc] = v;
+    }
+  }
   if (have && !abort_s) {
     if (PH == P1) {
       // row c of R1T: Re F1(j, p = c) for c <= nx, Im F1(j, p = c - nx) above
       const int p = (r <= g.nx) ? r : r - g.nx;
       const int half = (r <= g.nx) ? 0 : 1;
-      float* dh = g.out_hi + (size_t)p * g.out_ld + half * g.ny + n0;
-      float* dl = g.out_lo + (size_t)p * g.out_ld + half * g.ny + n0;
+      float4* dh = (float4*)(g.out_hi + (size_t)p * g.out_ld + half * g.ny + n0 + c0);
+      float4* dl = (float4*)(g.out_lo + (size_t)p * g.out_ld + half * g.ny + n0 + c0);
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) split(acc[cc], dh[cc], dl[cc]);
+      for (int q4 = 0; q4 < CW / 4; ++q4) {
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split(acc[c0 + 4 * q4 + u], h[u], l[u]);
+        dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
+        dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
+      }
     } else if (PH == P2A) {
       // row r < My: Re F(k = r, p) -> Im H_f = S_f Re F (column My + k of B3)
       // row r >= My: Im F(k = r - My, p) -> Re H_f = -S_f Im F (column k)
@@ -346,28 +389,37 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const int col = re ? g.My + k : k;
       const float sgn = re ? 1.f : -1.f;
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) {
+      for (int cc = c0; cc < c0 + CW; ++cc) {
         const int p = n0 + cc;
         const float f = sgn * acc[cc];
         const size_t rx = (size_t)p * g.out_ld + col, ry = (size_t)(g.Npad + p) * g.out_ld + col;
-        split(g.Sx[(size_t)k * g.Npad + p] * f, g.out_hi[rx], g.out_lo[rx]);
-        split(g.Sy[(size_t)k * g.Npad + p] * f, g.out_hi[ry], g.out_lo[ry]);
+        split(g.Sx[(size_t)p * g.My + k] * f, g.out_hi[rx], g.out_lo[rx]);
+        split(g.Sy[(size_t)p * g.My + k] * f, g.out_hi[ry], g.out_lo[ry]);
       }
     } else if (PH == P2B) {
       // row r: part (Re G, Im G) = r / ny at j' = r % ny; columns n = f*Npad + p
       const int part = r / g.ny, jr = r % g.ny;
       const int f = n0 / g.Npad, p0 = n0 % g.Npad;  // NT divides Npad: one field per tile
-      const size_t o = (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p0;
+      const size_t o = (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p0 + c0;
+      float4* dh = (float4*)(g.out_hi + o);
+      float4* dl = (float4*)(g.out_lo + o);
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) split(acc[cc], g.out_hi[o + cc], g.out_lo[o + cc]);
+      for (int q4 = 0; q4 < CW / 4; ++q4) {
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split(acc[c0 + 4 * q4 + u], h[u], l[u]);
+        dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
+        dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
+      }
     } else {
       // row r: field f = r / ny (Ex, Ey) at j = r % ny; columns i = n0 + cc
       const int f = r / g.ny, j = r % g.ny;
       double* e = (double*)(g.E + (size_t)j * g.nx + n0) + f;
 #pragma unroll
-      for (int cc = 0; cc < NT; ++cc) e[2 * cc] = (double)acc[cc];
+      for (int cc = c0; cc < c0 + CW; ++cc) e[2 * cc] = (double)acc[cc];
     }
   }
+  if (SK > 1) cluster_sync();  // keep this CTA's partial tile alive until every rank has read it
   tc_fence_before();
   __syncthreads();
   if (warp == 2) {
@@ -433,7 +485,8 @@ struct Tf32Plan {
   int Mx, My, Npad;
   Mat B1, W2f, W2i, B4;      // constants
   Mat B2, B3, A3;            // intermediates (next phase operands)
-  float *Sx, *Sy;            // [My][Npad]
+  float *Sx, *Sy;            // [Npad][My]
+  int K3;                    // row length of A3 and B4 (2 Npad rounded up to whole split-K chunks)
   int* err;
   GemmArgs a1, a2a, a2b, a3;
   int grid1, grid2a, grid2b, grid3;
@@ -469,15 +522,34 @@ void free_mat(Mat& m) {
   m = Mat{};
 }
 
-template <int PH>
+// Split-K cluster size per phase (K chunks per CTA: P1 nx/32, P2A 2ny/64, P2B 2My/128, P3 K3/64).
+constexpr int SK1 = 1, SK2A = 2, SK2B = 4, SK3 = 2;
+
+template <int PH, int SK>
 sc_status set_smem_attr() {
-  SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PH>::BYTES));
+  SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PH>::BYTES));
+  if (SK > 1) SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH, SK>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
   return SC_OK;
 }
 
-template <int PH>
-cudaError_t launch_phase(int grid, const GemmArgs& a, cudaStream_t s) {
-  return launch_pdl(dft_gemm<PH>, dim3(grid), dim3(kThreads), Smem<PH>::BYTES, s, a);
+// tiles x SK CTAs, clusters of SK along x, programmatic dependent launch.
+template <int PH, int SK>
+cudaError_t launch_phase(int tiles, const GemmArgs& a, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(tiles * SK);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = Smem<PH>::BYTES;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = SK;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, dft_gemm<PH, SK>, a);
 }
 
 void host_fft(std::complex<double>* a, int n, int stride) {
@@ -513,9 +585,11 @@ sc_status tf32_create(sc_grid* g) {
   if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
   g->tf32 = T;
   const int Mx = 2 * nx, My = 2 * ny, Npad = ((nx + 1 + NT - 1) / NT) * NT;
+  const int K3 = ((2 * Npad + KC * SK3 - 1) / (KC * SK3)) * (KC * SK3);
   T->Mx = Mx;
   T->My = My;
   T->Npad = Npad;
+  T->K3 = K3;
   const double tp = 2.0 * M_PI;
 
   // P1: B1 [2nx][nx]
@@ -541,14 +615,14 @@ sc_status tf32_create(sc_grid* g) {
       const bool re_row = r < ny, re_col = c < My;
       W2i[(size_t)r * 2 * My + c] = re_row ? (re_col ? C : -S) : (re_col ? S : C);
     }
-  // P3: B4 [nx][2 Npad]
-  std::vector<double> B4((size_t)nx * 2 * Npad, 0.0);
+  // P3: B4 [nx][K3]
+  std::vector<double> B4((size_t)nx * K3, 0.0);
   const double nrm = 1.0 / ((double)Mx * (double)My);
   for (int i = 0; i < nx; ++i)
     for (int p = 0; p <= nx; ++p) {
       const double w = (p == 0 || p == nx) ? 1.0 : 2.0;
-      B4[(size_t)i * 2 * Npad + p] = w * std::cos(tp * (double)p * i / Mx) * nrm;
-      B4[(size_t)i * 2 * Npad + Npad + p] = -w * std::sin(tp * (double)p * i / Mx) * nrm;
+      B4[(size_t)i * K3 + p] = w * std::cos(tp * (double)p * i / Mx) * nrm;
+      B4[(size_t)i * K3 + Npad + p] = -w * std::sin(tp * (double)p * i / Mx) * nrm;
     }
   // spectra of the field kernels (imaginary parts), [My][Npad]
   std::vector<double> Dx((size_t)Mx * My), Dy((size_t)Mx * My);
@@ -562,17 +636,18 @@ sc_status tf32_create(sc_grid* g) {
     host_fft(cx.data() + c, My, Mx);
     host_fft(cy.data() + c, My, Mx);
   }
+  // [p][k]: the P2A epilogue reads consecutive k across a warp
   std::vector<float> Sx((size_t)My * Npad, 0.f), Sy((size_t)My * Npad, 0.f);
   for (int k = 0; k < My; ++k)
     for (int p = 0; p <= nx; ++p) {
-      Sx[(size_t)k * Npad + p] = (float)cx[(size_t)k * Mx + p].imag();
-      Sy[(size_t)k * Npad + p] = (float)cy[(size_t)k * Mx + p].imag();
+      Sx[(size_t)p * My + k] = (float)cx[(size_t)k * Mx + p].imag();
+      Sy[(size_t)p * My + k] = (float)cy[(size_t)k * Mx + p].imag();
     }
 
   if ((st = upload(T->B1, B1, 2 * nx, nx)) || (st = upload(T->W2f, W2f, 2 * My, 2 * ny)) ||
-      (st = upload(T->W2i, W2i, 2 * ny, 2 * My)) || (st = upload(T->B4, B4, nx, 2 * Npad)) ||
+      (st = upload(T->W2i, W2i, 2 * ny, 2 * My)) || (st = upload(T->B4, B4, nx, K3)) ||
       (st = alloc_zero(T->B2, Npad, 2 * ny)) || (st = alloc_zero(T->B3, 2 * Npad, 2 * My)) ||
-      (st = alloc_zero(T->A3, 2 * ny, 2 * Npad)))
+      (st = alloc_zero(T->A3, 2 * ny, K3)))
     return st;
   SC_CUDA(cudaMalloc(&T->Sx, Sx.size() * 4));
   SC_CUDA(cudaMalloc(&T->Sy, Sy.size() * 4));
@@ -628,21 +703,19 @@ sc_status tf32_create(sc_grid* g) {
   T->a2b.n_tiles = 2 * Npad / NT;
   T->a2b.out_hi = T->A3.hi;
   T->a2b.out_lo = T->A3.lo;
-  T->a2b.out_ld = 2 * Npad;
+  T->a2b.out_ld = K3;
   T->grid2b = (2 * ny / TM) * T->a2b.n_tiles;
   // P3: C[(f,j)][i] = A3 B4^T: M = 2ny as (Ex, Ey) pairs, N = nx, K = 2 Npad
   base(T->a3);
-  if ((st = make_map(&T->a3.tA_hi, T->A3.hi, 2 * ny, 2 * Npad, TM)) ||
-      (st = make_map(&T->a3.tA_lo, T->A3.lo, 2 * ny, 2 * Npad, TM)) ||
-      (st = make_map(&T->a3.tB_hi, T->B4.hi, nx, 2 * Npad, NT)) ||
-      (st = make_map(&T->a3.tB_lo, T->B4.lo, nx, 2 * Npad, NT)))
+  if ((st = make_map(&T->a3.tA_hi, T->A3.hi, 2 * ny, K3, TM)) || (st = make_map(&T->a3.tA_lo, T->A3.lo, 2 * ny, K3, TM)) ||
+      (st = make_map(&T->a3.tB_hi, T->B4.hi, nx, K3, NT)) || (st = make_map(&T->a3.tB_lo, T->B4.lo, nx, K3, NT)))
     return st;
-  T->a3.k_chunks = 2 * Npad / KC;
+  T->a3.k_chunks = K3 / KC;
   T->a3.n_tiles = nx / NT;
   T->a3.E = g->E;
   T->grid3 = (2 * ny / TM) * T->a3.n_tiles;
-  if ((st = set_smem_attr<P1>()) || (st = set_smem_attr<P2A>()) || (st = set_smem_attr<P2B>()) ||
-      (st = set_smem_attr<P3>()))
+  if ((st = set_smem_attr<P1, SK1>()) || (st = set_smem_attr<P2A, SK2A>()) || (st = set_smem_attr<P2B, SK2B>()) ||
+      (st = set_smem_attr<P3, SK3>()))
     return st;
   return SC_OK;
 }
@@ -667,12 +740,12 @@ void tf32_destroy(sc_grid* g) {
 sc_status tf32_solve(sc_grid* g, bool zero_q) {
   Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_ARG, "grid has no TF32 solver");
-  T->a1.scale = 1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1);
+  T->a1.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
   T->a2a.Qzero = zero_q ? g->Q : nullptr;
-  SC_CUDA(launch_phase<P1>(T->grid1, T->a1, g->stream));
-  SC_CUDA(launch_phase<P2A>(T->grid2a, T->a2a, g->stream));
-  SC_CUDA(launch_phase<P2B>(T->grid2b, T->a2b, g->stream));
-  SC_CUDA(launch_phase<P3>(T->grid3, T->a3, g->stream));
+  SC_CUDA((launch_phase<P1, SK1>(T->grid1, T->a1, g->stream)));
+  SC_CUDA((launch_phase<P2A, SK2A>(T->grid2a, T->a2a, g->stream)));
+  SC_CUDA((launch_phase<P2B, SK2B>(T->grid2b, T->a2b, g->stream)));
+  SC_CUDA((launch_phase<P3, SK3>(T->grid3, T->a3, g->stream)));
   return SC_OK;
 }
 
