@@ -16,6 +16,7 @@
 //   P3  E[(f,j)][i] = A3[(f,j)][(re|im, p)] B4[i][(re|im, p)]   Hermitian
 //       inverse row DFT with weights 1 (p = 0, nx) or 2 and 1/(Mx My).
 // Supported: nx = ny in {128, 256} (M tiles of 128 rows).
+#include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -174,22 +175,7 @@ struct Smem {
   static constexpr int BYTES = STAGES * STAGE + RESIDENT + 1024 /*align slack*/;
 };
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-// float at the same shared-memory offset in CTA `rank` of the cluster
-__device__ __forceinline__ float ld_dsmem(const float* local, uint32_t rank) {
-  uint32_t ra;
-  float v;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
-  return v;
-}
+namespace cg = cooperative_groups;
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)m) : "memory");
 }
@@ -209,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   __shared__ volatile int abort_s;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rank = (SK > 1) ? (int)cluster_rank() : 0;
+  const int rank = (SK > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int tile = blockIdx.x / SK;
   const int mb = tile / g.n_tiles, nb = tile % g.n_tiles;
   const int n0 = nb * NT, a_row = mb * TM;
@@ -267,27 +253,32 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   }
   if (PH == P1) {
     // B operand = normalised charge rows j = n0 .. n0+NT-1, all K = nx, split hi/lo, swizzled.
-    // All loads of a thread are issued before any is used.
-    constexpr int PER = NT * 256 / kThreads;  // upper bound of elements per thread (nx <= 256)
-    long long v[PER];
-    const int total = NT * g.nx;
+    // 16-byte loads, all issued before any is used.
+    constexpr int PER2 = NT * 256 / 2 / kThreads;  // pairs per thread for nx <= 256
+    const int pairs = NT * g.nx / 2;
+    const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx);
+    longlong2 v[PER2];
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
+    for (int u = 0; u < PER2; ++u) {
       const int e = threadIdx.x + u * kThreads;
-      v[u] = (e < total) ? (long long)g.Q[(size_t)(n0 + e / g.nx) * g.nx + (e % g.nx)] : 0;
+      v[u] = (e < pairs) ? q2[e] : make_longlong2(0, 0);
     }
 #pragma unroll
-    for (int u = 0; u < PER; ++u) {
+    for (int u = 0; u < PER2; ++u) {
       const int e = threadIdx.x + u * kThreads;
-      if (e < total) {
-        const int r = e / g.nx, i = e % g.nx;
-        // int64 -> float through its 32-bit halves (no FP64 instruction)
-        const float qv = fmaf(__int2float_rn((int)(v[u] >> 32)), 4294967296.f, __uint2float_rn((unsigned)v[u])) * g.scale;
-        float hi, lo;
-        split(qv, hi, lo);
-        const int kc = i / KC, k = i % KC;
-        *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
-        *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+      if (e < pairs) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long qi = h ? v[u].y : v[u].x;
+          const int el = 2 * e + h, r = el / g.nx, i = el % g.nx;
+          // int64 -> float through its 32-bit halves (no FP64 instruction)
+          const float qv = fmaf(__int2float_rn((int)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * g.scale;
+          float hi, lo;
+          split(qv, hi, lo);
+          const int kc = i / KC, k = i % KC;
+          *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
+          *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+        }
       }
     }
     fence_proxy_async();
@@ -355,15 +346,34 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   const int c0 = rank * CW;
   if (SK > 1) {
     // partial tiles -> shared memory (the stages are idle now), summed across the cluster
-    float* red = (float*)stage_base;
+    cg::cluster_group cl = cg::this_cluster();
+    float4* red = (float4*)stage_base;
 #pragma unroll
-    for (int cc = 0; cc < NT; ++cc) red[t * NT + cc] = have ? acc[cc] : 0.f;
-    cluster_sync();
+    for (int q4 = 0; q4 < NT / 4; ++q4)
+      red[t * (NT / 4) + q4] = have ? make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3])
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    cl.sync();
+    float4 part[SK][CW / 4];
 #pragma unroll
-    for (int cc = 0; cc < CW; ++cc) {
-      float v = 0.f;
-      for (int q = 0; q < SK; ++q) v += ld_dsmem(&red[t * NT + c0 + cc], (uint32_t)q);
-      acc[c0 + cc] = v;
+    for (int q = 0; q < SK; ++q) {
+      const float4* rem = cl.map_shared_rank(red, q);
+#pragma unroll
+      for (int q4 = 0; q4 < CW / 4; ++q4) part[q][q4] = rem[t * (NT / 4) + c0 / 4 + q4];
+    }
+#pragma unroll
+    for (int q4 = 0; q4 < CW / 4; ++q4) {
+      float4 v = part[0][q4];
+#pragma unroll
+      for (int q = 1; q < SK; ++q) {
+        v.x += part[q][q4].x;
+        v.y += part[q][q4].y;
+        v.z += part[q][q4].z;
+        v.w += part[q][q4].w;
+      }
+      acc[c0 + 4 * q4] = v.x;
+      acc[c0 + 4 * q4 + 1] = v.y;
+      acc[c0 + 4 * q4 + 2] = v.z;
+      acc[c0 + 4 * q4 + 3] = v.w;
     }
   }
   if (have && !abort_s) {
@@ -419,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       for (int cc = c0; cc < c0 + CW; ++cc) e[2 * cc] = (double)acc[cc];
     }
   }
-  if (SK > 1) cluster_sync();  // keep this CTA's partial tile alive until every rank has read it
+  if (SK > 1) cg::this_cluster().sync();  // keep this CTA's partial tile alive until every rank has read it
   tc_fence_before();
   __syncthreads();
   if (warp == 2) {
