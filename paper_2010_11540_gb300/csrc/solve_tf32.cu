@@ -398,13 +398,20 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const int k = re ? r : r - g.My;
       const int col = re ? g.My + k : k;
       const float sgn = re ? 1.f : -1.f;
+      // all spectrum loads first (the stores below could alias them for the compiler)
+      float sx[CW], sy[CW];
 #pragma unroll
-      for (int cc = c0; cc < c0 + CW; ++cc) {
-        const int p = n0 + cc;
-        const float f = sgn * acc[cc];
+      for (int cc = 0; cc < CW; ++cc) {
+        sx[cc] = __ldg(g.Sx + (size_t)(n0 + c0 + cc) * g.My + k);
+        sy[cc] = __ldg(g.Sy + (size_t)(n0 + c0 + cc) * g.My + k);
+      }
+#pragma unroll
+      for (int cc = 0; cc < CW; ++cc) {
+        const int p = n0 + c0 + cc;
+        const float f = sgn * acc[c0 + cc];
         const size_t rx = (size_t)p * g.out_ld + col, ry = (size_t)(g.Npad + p) * g.out_ld + col;
-        split(g.Sx[(size_t)p * g.My + k] * f, g.out_hi[rx], g.out_lo[rx]);
-        split(g.Sy[(size_t)p * g.My + k] * f, g.out_hi[ry], g.out_lo[ry]);
+        split(sx[cc] * f, g.out_hi[rx], g.out_lo[rx]);
+        split(sy[cc] * f, g.out_hi[ry], g.out_lo[ry]);
       }
     } else if (PH == P2B) {
       // row r: part (Re G, Im G) = r / ny at j' = r % ny; columns n = f*Npad + p
