@@ -34,6 +34,7 @@ struct TrackPlan {
   DevElem* d_elems = nullptr;  // compiled lattice (segments longer than KP_INLINE read it)
   int* cell = nullptr;         // cell cache [n]
   double2* frac = nullptr;     // fraction cache [n]
+  double* psc = nullptr;       // per-particle ps-dependent quantities [5][n]
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool has_head = false;
@@ -56,6 +57,7 @@ void destroy_plan(TrackPlan* t) {
   cudaFree(t->d_elems);
   cudaFree(t->cell);
   cudaFree(t->frac);
+  cudaFree(t->psc);
   cudaFree(t->partial);
   cudaFree(t->d_base);
   cudaFree(t->d_turn);
@@ -379,6 +381,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       SC_CUDA(cudaMalloc(&T->cell, (size_t)p->n * sizeof(int)));
       SC_CUDA(cudaMalloc(&T->frac, (size_t)p->n * sizeof(double2)));
     }
+    SC_CUDA(cudaMalloc(&T->psc, (size_t)p->n * 5 * sizeof(double)));
     if (want_diag) {
       SC_CUDA(cudaMalloc(&T->partial, (size_t)moments_blocks() * 14 * sizeof(double)));
       SC_CUDA(cudaMalloc(&T->d_base, sizeof(double*)));
@@ -386,17 +389,24 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     }
     g->n_particles = p->n;
     const double K = kick_strength(b);
-    // prologue: charge (and cell cache) at the first marker for lattices that open with one
+    // prologue of every call: the ps-dependent quantities of each particle, and
+    // for lattices that open with a marker the charge (and cell cache) there
     T->prologue = base_params(p, b);
-    set_deposit(T->prologue, g);
-    T->prologue.cell = T->cell;
-    T->prologue.frac = T->frac;
+    T->prologue.psc = T->psc;
+    T->prologue.psc_mode = 2;
+    if (!T->has_head && T->n_kicks > 0) {
+      set_deposit(T->prologue, g);
+      T->prologue.cell = T->cell;
+      T->prologue.frac = T->frac;
+    }
     // ---- capture one turn ------------------------------------------------------
     SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     sc_status cst = SC_OK;
     if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, g->stream);
     if (!cst && T->has_head) {
       KPParams P = base_params(p, b);
+      P.psc = T->psc;
+      P.psc_mode = 1;
       const int nh = marks.empty() ? n_elems : marks[0];
       set_elements(P, lattice, nh, b, T->d_elems);
       if (!marks.empty()) {
@@ -417,6 +427,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       cst = solve_dispatch(g, true);
       if (cst) break;
       KPParams P = base_params(p, b);
+      P.psc = T->psc;
+      P.psc_mode = 1;
       set_kick(P, g, K * (s[m] - prev));
       set_elements(P, lattice + m + 1, end - m - 1, b, T->d_elems + m + 1);
       // the cell cache is valid at every marker: the previous launch deposited on this grid
@@ -465,6 +477,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     // charge at the first space-charge location of the first turn
     SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * 8, g->stream));
     if ((st = launch_kick_push(T->prologue, g, g->kp_blocks, g->stream))) return st;
+  } else {
+    if ((st = launch_kick_push(T->prologue, nullptr, g->kp_blocks_plain, g->stream))) return st;
   }
   for (int t = 0; t < n_turns; ++t) SC_CUDA(cudaGraphLaunch(T->exec, g->stream));
   if (T->diag) {

@@ -15,8 +15,9 @@ namespace {
 constexpr int kKPThreads = 512;
 
 // TILE: deposit into a shared-memory tile (grid fits); CACHE: the cell cache
-// P.cell / P.frac is valid for the gather and is refreshed by the deposit.
-template <bool TILE, bool CACHE>
+// P.cell / P.frac is valid for the gather and is refreshed by the deposit;
+// PSC: mode of the per-particle ps-quantity arrays (see KPParams).
+template <bool TILE, bool CACHE, int PSC>
 __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
   const int cells = P.gd.nx * P.gd.ny;
@@ -50,10 +51,29 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
         s.py = fma(P.kl, fma(fy, by - ay, ay), s.py);
       }
     }
-    if (P.el)
-      push_elements(s, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, P.has_quad != 0);
-    else
-      push_elements(s, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, P.has_quad != 0);
+    PsConst k;
+    if (PSC == 1) {
+      const size_t n = (size_t)P.n;
+      k.opd2 = P.psc[p];
+      k.opb = P.psc[n + p];
+      k.s1 = P.psc[2 * n + p];
+      k.r = P.psc[3 * n + p];
+      k.qi = P.psc[4 * n + p];
+      k.opm = 1.0 - s.ps;
+    } else {
+      ps_const(k, s.ps, P.beta0_sq, PSC == 2 || P.has_quad != 0);
+    }
+    const bool quads = PSC != 0 || P.has_quad != 0;
+    const bool changed = P.el ? push_elements(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads)
+                              : push_elements(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads);
+    if (PSC == 2 || (PSC == 1 && changed)) {
+      const size_t n = (size_t)P.n;
+      P.psc[p] = k.opd2;
+      P.psc[n + p] = k.opb;
+      P.psc[2 * n + p] = k.s1;
+      P.psc[3 * n + p] = k.r;
+      P.psc[4 * n + p] = k.qi;
+    }
     if (P.do_deposit) {
       double fx, fy;
       const int cell = locate(P.gd, s.x, s.y, fx, fy);
@@ -83,26 +103,36 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
   }
 }
 
-template <bool TILE, bool CACHE>
+template <bool TILE, bool CACHE, int PSC>
 int blocks_for(int smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (TILE) cudaFuncSetAttribute(kick_push_kernel<TILE, CACHE>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<TILE, CACHE>, kKPThreads, smem);
+  if (TILE)
+    cudaFuncSetAttribute(kick_push_kernel<TILE, CACHE, PSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<TILE, CACHE, PSC>, kKPThreads, smem);
   return sms * (per < 1 ? 1 : per);
+}
+
+template <bool TILE>
+int min_blocks(int smem) {
+  int b = blocks_for<TILE, false, 0>(smem);
+  const int c[5] = {blocks_for<TILE, false, 1>(smem), blocks_for<TILE, false, 2>(smem), blocks_for<TILE, true, 0>(smem),
+                    blocks_for<TILE, true, 1>(smem), blocks_for<TILE, true, 2>(smem)};
+  for (int v : c) b = v < b ? v : b;
+  return b;
+}
+
+template <bool TILE, bool CACHE>
+decltype(&kick_push_kernel<TILE, CACHE, 0>) pick_psc(int mode) {
+  return mode == 1 ? kick_push_kernel<TILE, CACHE, 1> : mode == 2 ? kick_push_kernel<TILE, CACHE, 2> : kick_push_kernel<TILE, CACHE, 0>;
 }
 
 }  // namespace
 
 int kick_push_blocks_for(int smem_bytes, bool tile) {
-  // the cached and uncached variants have the same shared memory; size on the larger register count
-  if (tile) {
-    const int a = blocks_for<true, false>(smem_bytes), b = blocks_for<true, true>(smem_bytes);
-    return a < b ? a : b;
-  }
-  const int a = blocks_for<false, false>(0), b = blocks_for<false, true>(0);
-  return a < b ? a : b;
+  // all variants share the shared memory size; size the grid on the largest register count
+  return tile ? min_blocks<true>(smem_bytes) : min_blocks<false>(0);
 }
 
 sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s) {
@@ -111,8 +141,9 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
   const int64_t need = (P.n + kKPThreads - 1) / kKPThreads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
   const int smem = tile ? dep->nx * dep->ny * 8 : 0;
-  auto k = tile ? (cache ? kick_push_kernel<true, true> : kick_push_kernel<true, false>)
-                : (cache ? kick_push_kernel<false, true> : kick_push_kernel<false, false>);
+  const int m = P.psc ? P.psc_mode : 0;
+  auto k = tile ? (cache ? pick_psc<true, true>(m) : pick_psc<true, false>(m))
+                : (cache ? pick_psc<false, true>(m) : pick_psc<false, false>(m));
   SC_CUDA(launch_pdl(k, dim3(blocks), dim3(kKPThreads), (size_t)smem, s, P));
   return SC_OK;
 }

@@ -15,9 +15,10 @@ namespace sc {
 enum : int { QF_ZERO = 0, QF_FOCUS_X = 1, QF_FOCUS_Y = 2 };
 
 // Largest chromatic phase shift |Delta| = |theta0 (sqrt(1-ps) - 1)| handled by
-// the angle-addition series (truncation below 1e-18); beyond it the library
+// the angle-addition series: with terms up to Delta^5 (sin) and Delta^4 (cos),
+// the truncation is below 2e-18 for |Delta| <= 2^-8; beyond it the library
 // sin/cos/sinh/cosh are used.
-constexpr double kMaxDelta = 0.02;
+constexpr double kMaxDelta = 0.00390625;
 
 struct State {
   double x, px, y, py, sg, ps;
@@ -87,16 +88,10 @@ __device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsCon
   double c, sn, ch, sh;
   if (fabs(delta) <= kMaxDelta) {
     const double d2 = delta * delta;
-    double p = fma(d2, -1.0 / 5040.0, 1.0 / 120.0);
-    p = fma(d2, p, -1.0 / 6.0) * d2;
-    const double sd = fma(delta, p, delta);  // sin(delta)
-    double q = fma(d2, -1.0 / 720.0, 1.0 / 24.0);
-    const double cm = fma(d2, q, -0.5) * d2;  // cos(delta) - 1
-    double ph = fma(d2, 1.0 / 5040.0, 1.0 / 120.0);
-    ph = fma(d2, ph, 1.0 / 6.0) * d2;
-    const double shd = fma(delta, ph, delta);  // sinh(delta)
-    double qh = fma(d2, 1.0 / 720.0, 1.0 / 24.0);
-    const double chm = fma(d2, qh, 0.5) * d2;  // cosh(delta) - 1
+    const double sd = fma(delta, fma(d2, 1.0 / 120.0, -1.0 / 6.0) * d2, delta);   // sin(delta)
+    const double cm = fma(d2, 1.0 / 24.0, -0.5) * d2;                             // cos(delta) - 1
+    const double shd = fma(delta, fma(d2, 1.0 / 120.0, 1.0 / 6.0) * d2, delta);   // sinh(delta)
+    const double chm = fma(d2, 1.0 / 24.0, 0.5) * d2;                             // cosh(delta) - 1
     const double c0 = e.p[2], s0 = e.p[3], ch0 = e.p[4], sh0 = e.p[5];
     c = fma(-s0, sd, fma(c0, cm, c0));
     sn = fma(c0, sd, fma(s0, cm, s0));
@@ -166,11 +161,12 @@ __device__ __forceinline__ void map_rf(State& s, const DevElem& e) {
   s.ps = fma(e.p[0], sin(fma(-e.p[1], s.sg, e.p[2])), s.ps);
 }
 
-// quads: the segment holds a quadrupole (then the square roots of 1-ps are needed).
-__device__ __forceinline__ void push_elements(State& s, const DevElem* __restrict__ el, int n_elem,
+// Push through n_elem elements with the ps-dependent quantities k (valid on
+// entry).  quads: refresh k's square roots after an RF cavity.  Returns true
+// when an RF cavity changed ps (k then holds the new values).
+__device__ __forceinline__ bool push_elements(State& s, PsConst& k, const DevElem* __restrict__ el, int n_elem,
                                               double beta0_sq, double inv_gamma0_sq, bool quads) {
-  PsConst k;
-  ps_const(k, s.ps, beta0_sq, quads);
+  bool changed = false;
 #pragma unroll 1
   for (int i = 0; i < n_elem; ++i) {
     const DevElem e = el[i];
@@ -182,10 +178,12 @@ __device__ __forceinline__ void push_elements(State& s, const DevElem* __restric
       case SC_RF:
         map_rf(s, e);
         ps_const(k, s.ps, beta0_sq, quads);
+        changed = true;
         break;
       default: break;
     }
   }
+  return changed;
 }
 
 }  // namespace sc

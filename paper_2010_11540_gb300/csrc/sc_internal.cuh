@@ -93,6 +93,11 @@ struct KPParams {
   const DevElem* el;  // device array of the segment's compiled elements, or NULL: use inl
   int n_elem;
   int has_quad;       // the segment holds an SC_QUAD
+  // Per-particle ps-dependent quantities, 5 arrays of n: (1+delta)^2,
+  // 1 + beta0^2 ps, sqrt(1-ps), 1/sqrt(1-ps), 1/(4(1-ps)).  psc_mode 0: none
+  // (computed in registers), 1: read (rewritten after an RF cavity), 2: compute and write.
+  double* psc;
+  int psc_mode;
   DevElem inl[KP_INLINE];
 };
 

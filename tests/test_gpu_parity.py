@@ -278,3 +278,37 @@ def test_track_tf32_statistics():
         d = got[k] - ref[k]
         assert np.sqrt(np.mean(d * d)) < 1e-5 * scale, k
         assert np.max(np.abs(d)) < 1e-2 * scale, k
+
+
+def test_track_with_rf_and_head():
+    """An RF cavity inside a segment changes psigma mid-push (the per-particle
+    psigma-dependent quantities must follow), with elements before the first
+    space-charge marker: 3 turns against the oracle."""
+    parts, b, grid, lat = synth.workload("c1", n=5000)
+    rows = list(lat)
+    rf = synth.table([synth.elem(synth.RF, volt=4e6, harmonic=4.0, lag=0.0)])[0]
+    lat2 = synth.table([tuple(rows[0]), tuple(rf)] + [tuple(r) for r in rows[1:]])
+    b = dict(b, circumference=float(lat2["length"].sum()))
+    g, og = grid_pair(grid)
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat2, 3)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(og, ref, b, lat2, 3)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+    assert np.abs(got["psigma"] - parts["psigma"]).max() > 1e-6  # the cavity did act
+
+
+def test_track_without_space_charge_markers():
+    parts, b, grid, lat = synth.workload("c1", n=3000)
+    lat2 = lat[lat["type"] != synth.MARK]
+    g = sc.create_grid(*grid)
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat2, 2)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.push(ref, lat2, b)
+    oracle.push(ref, lat2, b)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
