@@ -33,11 +33,14 @@ WORKLOAD = ("c2: 1e6 macroparticles (4D Gaussian, sigma_x=4 mm, sigma_y=3 mm, 0.
             "128x128 grid over +-5 sigma (256x256 padded open-boundary solve), 72-cell FODO ring with "
             "2 thin-sextupole families, bare tunes (22.40, 20.75), 216 SC kicks/turn")
 
-# FP64 flops per particle and element/kick, counted from the kernel's formulas
-# (multiply, add and fused multiply-add = 2); see the roofline section of the design doc.
-FP64_FLOPS = {"kick": 26, "deposit": 6, "drift": 22, "quad": 70, "sext": 7, "bend": 40, "rf": 30}
-NOMINAL_FP64_TFLOPS = 1.25  # GB300 dense FP64 (profiling recipe table)
-
+# FP64-pipe thread instructions per particle in kick_push_kernel (the turn
+# graph's variant), by segment content: measured with ncu
+# (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul} + conversions, floor and
+# compares via sm__inst_executed_pipe_fp64) on the bench workload; see the
+# roofline section of the design doc.  base = gather + kick + fused deposit.
+FP64_INST = {"base": 32.0, "drift": 13.0, "quad": 47.0, "sext": 6.0, "bend": 16.0, "rf": 30.0}
+# GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
+FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -108,15 +111,15 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- helpers
-def segment_flops(lat):
-    """FP64 flops per particle per turn from the element mix, and kicks/turn."""
+def fp64_inst_per_turn(lat):
+    """FP64-pipe instructions per particle per turn from the element mix, and kicks/turn."""
     from paper_2010_11540_gb300 import synth
     t = lat["type"]
     n_k = int((t == synth.MARK).sum())
     per = {synth.DRIFT: "drift", synth.QUAD: "quad", synth.SEXT: "sext", synth.BEND: "bend", synth.RF: "rf"}
-    f = n_k * (FP64_FLOPS["kick"] + FP64_FLOPS["deposit"])
+    f = n_k * FP64_INST["base"]
     for code, name in per.items():
-        f += int((t == code).sum()) * FP64_FLOPS[name]
+        f += int((t == code).sum()) * FP64_INST[name]
     return f, n_k
 
 
@@ -189,7 +192,7 @@ def run_ours(args):
     keys = ("x", "px", "y", "py", "sigma", "psigma")
     dev = {k: torch.from_numpy(parts[k]).cuda() for k in keys}
     g = sc.create_grid(*grid, precision=args.precision, stream=stream)
-    flops_turn, n_kicks = segment_flops(lat)
+    inst_turn, n_kicks = fp64_inst_per_turn(lat)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
@@ -223,36 +226,24 @@ def run_ours(args):
         ms = float(t.item())
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
 
-    # ---------------- dominant kernel (kick + push + fused deposit), timed alone per segment
-    head, kicks = _segments(lat, synth)
-    kp_ms = []
+    # ---------------- dominant kernel, timed inside the turn graph (library tracing:
+    # CUDA events on the grid's stream around every solve and kick/push launch)
+    sc.trace_enable(g, True)
     with torch.cuda.stream(stream):
-        for rep in range(2):
-            for L, seg in kicks[:3]:
-                for _ in range(8):
-                    sc.solve(g)
-                    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a.record(stream)
-                    sc.kick_push(g, dev, b, L, seg, next_grid=g)
-                    c.record(stream)
-                    if rep == 1:
-                        kp_ms.append((a, c, seg))
-        stream.synchronize()
-    times = [a.elapsed_time(c) for a, c, _ in kp_ms]
-    seg_flops = []
-    for _, _, seg in kp_ms:
-        f = FP64_FLOPS["kick"] + FP64_FLOPS["deposit"]
-        for e in seg:
-            f += FP64_FLOPS[{0: "drift", 1: "quad", 2: "sext", 3: "bend", 4: "rf"}.get(int(e["type"]), "kick")] \
-                if int(e["type"]) != synth.MARK else 0
-        seg_flops.append(f)
-    kp_avg_ms = statistics.mean(times)
-    achieved = statistics.mean(seg_flops) * n / (kp_avg_ms * 1e-3) / 1e12
+        sc.track_turns(g, dev, b, lat, 1)  # capture + warm
+        sc.trace_read(g)
+        sc.track_turns(g, dev, b, lat, 2)
+    kp_ms, solve_ms, traced = sc.trace_read(g)
+    sc.trace_enable(g, False)
+    kp_avg_ms = kp_ms / traced
+    inst_per_kick = inst_turn / n_kicks
+    achieved = inst_per_kick * n / (kp_avg_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": "kick_push_kernel (gather+kick, push, fused CIC deposit)",
-                "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 dense FP64 1.25 TFLOP/s (profiling recipe); probe measured 1.19",
-                "avg_launch_ms": kp_avg_ms, "fp64_flops_per_particle_kick": statistics.mean(seg_flops)}
+                "achieved": achieved, "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
+                "frac": achieved / FP64_PIPE_PEAK_TINST, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (probe: 2.0/clk/SM)",
+                "avg_launch_ms": kp_avg_ms, "fp64_inst_per_particle_kick": inst_per_kick,
+                "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
 
     # ---------------- end to end: host buffers through the public API
     pinned = {k: torch.from_numpy(parts[k].copy()).pin_memory() for k in keys}

@@ -90,8 +90,8 @@ typedef struct {
  * hx = (xmax - xmin)/(nx - 1) (same for y), with the open-boundary
  * (Hockney zero-padded) Poisson solver of the given precision.  Builds the
  * Green's-function spectra on the device (synchronous on `stream`).
- * nx, ny: 8..512 and powers of two for SC_SOLVE_FP64; multiples of 32 in
- * 32..256 for SC_SOLVE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
+ * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {128, 256}
+ * for SC_SOLVE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
  * SC_ERR_OOM, SC_ERR_CUDA.  *out is set only on success. */
 sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
                          double ymax, int precision, void *stream);
@@ -127,7 +127,10 @@ sc_status sc_kick_push(sc_grid *g, const sc_particles *p, const sc_beam *b, doub
  * path length since the previous marker, cyclically).  Each marker runs
  * deposit -> solve -> kick, then the elements up to the next marker are
  * pushed; elements before the first marker are pushed without a kick.  One
- * turn is captured once as a CUDA graph and replayed.  When diag != NULL
+ * turn is captured once as a CUDA graph and replayed (re-captured when any
+ * argument changes).  The grid keeps per-particle working arrays for the run
+ * (cell/fraction cache of the last deposit, psigma-dependent quantities; 60
+ * bytes per particle), recomputed at the start of every call.  When diag != NULL
  * (host, n_turns x 14 doubles) the beam moments at the start of every turn
  * are written there: means of (x, px, y, py, sigma, psigma), then central
  * <xx>, <x px>, <px px>, <yy>, <y py>, <py py>, <sigma sigma>,
@@ -144,6 +147,17 @@ sc_status sc_grid_read(sc_grid *g, int64_t *Q, double *Ex, double *Ey, int64_t *
 /* Synchronous upload of a charge grid Q (host, nx*ny int64) and the particle
  * count N used to normalise it, e.g. to solve a given charge. */
 sc_status sc_grid_write_charge(sc_grid *g, const int64_t *Q, int64_t n_particles);
+
+/* Per-phase tracing.  When enabled, the next turn sc_track_turns captures
+ * records CUDA events around every solve and every kick/push launch (on the
+ * grid's stream); sc_track_turns then waits after each turn and accumulates
+ * the elapsed times (this serialises the kernels of a turn: a profiling mode,
+ * not the fast path).  Enabling or disabling re-captures the turn. */
+sc_status sc_trace_enable(sc_grid *g, int enable);
+
+/* Totals accumulated since the last read (then reset): kick/push launch time
+ * and solve time in ms, and the number of kicks they cover. */
+sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
 /* Text of the last error on the calling thread (always NUL-terminated). */
 sc_status sc_last_error(char *buf, size_t n);

@@ -46,6 +46,7 @@ struct TrackPlan {
   int* d_turn = nullptr;      // device turn counter
   double* d_diag = nullptr;   // [cap][14]
   int diag_cap = 0;
+  std::vector<cudaEvent_t> ev;  // tracing: per kick (solve start, kick/push start, kick/push end)
 };
 
 namespace {
@@ -62,6 +63,7 @@ void destroy_plan(TrackPlan* t) {
   cudaFree(t->d_base);
   cudaFree(t->d_turn);
   cudaFree(t->d_diag);
+  for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
   delete t;
 }
 
@@ -324,6 +326,24 @@ sc_status sc_grid_read(sc_grid* g, int64_t* Q, double* Ex, double* Ey, int64_t* 
   return SC_OK;
 }
 
+sc_status sc_trace_enable(sc_grid* g, int enable) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  g->trace = enable ? 1 : 0;
+  g->trace_kp_ms = g->trace_solve_ms = 0.0;
+  g->trace_kicks = 0;
+  return SC_OK;
+}
+
+sc_status sc_trace_read(sc_grid* g, double* kick_push_ms, double* solve_ms, int64_t* n_kicks) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (kick_push_ms) *kick_push_ms = g->trace_kp_ms;
+  if (solve_ms) *solve_ms = g->trace_solve_ms;
+  if (n_kicks) *n_kicks = g->trace_kicks;
+  g->trace_kp_ms = g->trace_solve_ms = 0.0;
+  g->trace_kicks = 0;
+  return SC_OK;
+}
+
 sc_status sc_grid_write_charge(sc_grid* g, const int64_t* Q, int64_t n_particles) {
   if (!g || !Q) return set_error(SC_ERR_ARG, "grid or Q is NULL");
   if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
@@ -353,6 +373,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   if (n_elems) put(lattice, (size_t)n_elems * sizeof(sc_element));
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
+  put(&g->trace, sizeof g->trace);
 
   TrackPlan* T = g->track;
   if (!T || T->key != key) {
@@ -382,6 +403,10 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       SC_CUDA(cudaMalloc(&T->frac, (size_t)p->n * sizeof(double2)));
     }
     SC_CUDA(cudaMalloc(&T->psc, (size_t)p->n * 5 * sizeof(double)));
+    if (g->trace) {
+      T->ev.resize(3 * marks.size());
+      for (auto& e : T->ev) SC_CUDA(cudaEventCreate(&e));
+    }
     if (want_diag) {
       SC_CUDA(cudaMalloc(&T->partial, (size_t)moments_blocks() * 14 * sizeof(double)));
       SC_CUDA(cudaMalloc(&T->d_base, sizeof(double*)));
@@ -423,9 +448,14 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       const int m = marks[k];
       const int end = (k + 1 < marks.size()) ? marks[k + 1] : n_elems;
       const double prev = (k > 0) ? s[marks[k - 1]] : s[marks.back()] - circ;
+      if (g->trace && cudaEventRecord(T->ev[3 * k], g->stream) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "event");
       // the solve clears the charge after reading it, ready for this marker's deposit
-      cst = solve_dispatch(g, true);
+      if (!cst) cst = solve_dispatch(g, true);
       if (cst) break;
+      if (g->trace && cudaEventRecord(T->ev[3 * k + 1], g->stream) != cudaSuccess) {
+        cst = set_error(SC_ERR_CUDA, "event");
+        break;
+      }
       KPParams P = base_params(p, b);
       P.psc = T->psc;
       P.psc_mode = 1;
@@ -437,6 +467,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       const bool dep = (k + 1 < marks.size()) || !T->has_head;
       if (dep) set_deposit(P, g);
       cst = launch_kick_push(P, dep ? g : nullptr, dep ? g->kp_blocks : g->kp_blocks_plain, g->stream);
+      if (!cst && g->trace && cudaEventRecord(T->ev[3 * k + 2], g->stream) != cudaSuccess)
+        cst = set_error(SC_ERR_CUDA, "event");
     }
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
@@ -480,7 +512,20 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   } else {
     if ((st = launch_kick_push(T->prologue, nullptr, g->kp_blocks_plain, g->stream))) return st;
   }
-  for (int t = 0; t < n_turns; ++t) SC_CUDA(cudaGraphLaunch(T->exec, g->stream));
+  for (int t = 0; t < n_turns; ++t) {
+    SC_CUDA(cudaGraphLaunch(T->exec, g->stream));
+    if (!T->ev.empty()) {
+      SC_CUDA(cudaStreamSynchronize(g->stream));
+      for (size_t k = 0; 3 * k + 2 < T->ev.size(); ++k) {
+        float a = 0.f, c = 0.f;
+        SC_CUDA(cudaEventElapsedTime(&a, T->ev[3 * k], T->ev[3 * k + 1]));
+        SC_CUDA(cudaEventElapsedTime(&c, T->ev[3 * k + 1], T->ev[3 * k + 2]));
+        g->trace_solve_ms += a;
+        g->trace_kp_ms += c;
+        g->trace_kicks += 1;
+      }
+    }
+  }
   if (T->diag) {
     SC_CUDA(cudaMemcpyAsync(diag, T->d_diag, (size_t)n_turns * 14 * sizeof(double), cudaMemcpyDeviceToHost,
                             g->stream));

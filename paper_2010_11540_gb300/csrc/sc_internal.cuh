@@ -136,6 +136,9 @@ struct sc_grid {
   sc::Fft64Plan fft;
   sc::Tf32Plan* tf32;
   sc::TrackPlan* track;
+  int trace;                   // record per-phase events in captured turns
+  double trace_kp_ms, trace_solve_ms;
+  int64_t trace_kicks;
   int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
   int kp_blocks_plain;         // kick/push without a deposit
   sc::DevElem* el_stage;       // device copy of sc_kick_push's last long segment

@@ -25,7 +25,7 @@ ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVE
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "tf32x3": 1}
 EXPORTS = ("sc_create_grid", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
-           "sc_grid_read", "sc_grid_write_charge", "sc_last_error")
+           "sc_grid_read", "sc_grid_write_charge", "sc_trace_enable", "sc_trace_read", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -67,6 +67,8 @@ def load():
                                  ctypes.c_int, dp]
     L.sc_grid_read.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64)]
     L.sc_grid_write_charge.argtypes = [vp, vp, i64]
+    L.sc_trace_enable.argtypes = [vp, ctypes.c_int]
+    L.sc_trace_read.argtypes = [vp, dp, dp, ctypes.POINTER(i64)]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -180,6 +182,17 @@ def grid_read(grid: Grid):
     n_out = ctypes.c_int64(0)
     _check(load().sc_grid_read(grid.handle, Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data, ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
+
+
+def trace_enable(grid: Grid, enable: bool = True):
+    _check(load().sc_trace_enable(grid.handle, 1 if enable else 0))
+
+
+def trace_read(grid: Grid):
+    """-> (kick_push_ms, solve_ms, n_kicks) accumulated since the last read."""
+    a, c, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
+    _check(load().sc_trace_read(grid.handle, ctypes.byref(a), ctypes.byref(c), ctypes.byref(n)))
+    return a.value, c.value, int(n.value)
 
 
 def grid_write_charge(grid: Grid, Q, n_particles: int):
