@@ -448,11 +448,11 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       const int m = marks[k];
       const int end = (k + 1 < marks.size()) ? marks[k + 1] : n_elems;
       const double prev = (k > 0) ? s[marks[k - 1]] : s[marks.back()] - circ;
-      if (g->trace && cudaEventRecord(T->ev[3 * k], g->stream) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "event");
+      if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k], g->stream, cudaEventRecordExternal) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "event");
       // the solve clears the charge after reading it, ready for this marker's deposit
       if (!cst) cst = solve_dispatch(g, true);
       if (cst) break;
-      if (g->trace && cudaEventRecord(T->ev[3 * k + 1], g->stream) != cudaSuccess) {
+      if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k + 1], g->stream, cudaEventRecordExternal) != cudaSuccess) {
         cst = set_error(SC_ERR_CUDA, "event");
         break;
       }
@@ -467,7 +467,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       const bool dep = (k + 1 < marks.size()) || !T->has_head;
       if (dep) set_deposit(P, g);
       cst = launch_kick_push(P, dep ? g : nullptr, dep ? g->kp_blocks : g->kp_blocks_plain, g->stream);
-      if (!cst && g->trace && cudaEventRecord(T->ev[3 * k + 2], g->stream) != cudaSuccess)
+      if (!cst && g->trace && cudaEventRecordWithFlags(T->ev[3 * k + 2], g->stream, cudaEventRecordExternal) != cudaSuccess)
         cst = set_error(SC_ERR_CUDA, "event");
     }
     cudaGraph_t graph = nullptr;

@@ -312,3 +312,22 @@ def test_track_without_space_charge_markers():
     oracle.push(ref, lat2, b)
     err = rel_state_err(got, ref)
     assert max(err.values()) < 1e-10, err
+
+
+def test_trace_accumulates_phase_times():
+    parts, b, grid, lat = synth.workload("c1", n=4096)
+    g = sc.create_grid(*grid)
+    st = to_gpu(parts)
+    sc.trace_enable(g, True)
+    sc.track_turns(g, st, b, lat, 2)
+    kp, sv, n = sc.trace_read(g)
+    assert n == 2 * 48 and kp > 0 and sv > 0
+    assert sc.trace_read(g)[2] == 0  # reading resets
+    sc.trace_enable(g, False)
+    a = to_host(st)
+    # traced tracking gives the same state as untraced
+    g2 = sc.create_grid(*grid)
+    st2 = to_gpu(parts)
+    sc.track_turns(g2, st2, b, lat, 2)
+    c = to_host(st2)
+    assert all(np.array_equal(a[k], c[k]) for k in KEYS)
