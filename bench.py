@@ -38,7 +38,7 @@ WORKLOAD = ("c2: 1e6 macroparticles (4D Gaussian, sigma_x=4 mm, sigma_y=3 mm, 0.
 # (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul} + conversions, floor and
 # compares via sm__inst_executed_pipe_fp64) on the bench workload; see the
 # roofline section of the design doc.  base = gather + kick + fused deposit.
-FP64_INST = {"base": 32.0, "drift": 13.0, "quad": 47.0, "sext": 6.0, "bend": 16.0, "rf": 30.0}
+FP64_INST = {"base": 27.5, "drift": 12.2, "quad": 51.5, "sext": 5.0, "bend": 16.0, "rf": 30.0}
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 

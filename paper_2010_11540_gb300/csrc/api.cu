@@ -33,7 +33,8 @@ struct TrackPlan {
   std::vector<unsigned char> key;
   DevElem* d_elems = nullptr;  // compiled lattice (segments longer than KP_INLINE read it)
   int* cell = nullptr;         // cell cache [n]
-  double2* frac = nullptr;     // fraction cache [n]
+  double2* frac = nullptr;     // float64 fraction cache [n] (float64 fields)
+  int2* fix = nullptr;         // fixed-point fraction cache [n] (float32 fields)
   double* psc = nullptr;       // per-particle ps-dependent quantities [5][n]
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -58,6 +59,7 @@ void destroy_plan(TrackPlan* t) {
   cudaFree(t->d_elems);
   cudaFree(t->cell);
   cudaFree(t->frac);
+  cudaFree(t->fix);
   cudaFree(t->psc);
   cudaFree(t->partial);
   cudaFree(t->d_base);
@@ -125,10 +127,14 @@ void set_kick(KPParams& P, const sc_grid* g, double kl) {
   P.do_kick = (kl != 0.0);
   P.gk = g->geom;
   P.E = g->E;
+  P.E32 = (const float2*)g->E;
+  P.field32 = g->field32;
   P.kl = kl;
 }
 
+// The cell cache a deposit writes follows the deposit grid's field precision.
 void set_deposit(KPParams& P, sc_grid* d) {
+  P.field32 = d->field32;
   P.do_deposit = 1;
   P.gd = d->geom;
   P.Q = d->Q;
@@ -180,6 +186,7 @@ sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax
   g->nx = nx;
   g->ny = ny;
   g->precision = precision;
+  g->field32 = (precision == SC_SOLVE_TF32X3);
   g->xmin = xmin;
   g->xmax = xmax;
   g->ymin = ymin;
@@ -309,7 +316,14 @@ sc_status sc_grid_read(sc_grid* g, int64_t* Q, double* Ex, double* Ey, int64_t* 
   SC_CUDA(cudaStreamSynchronize(g->stream));
   const size_t cells = (size_t)g->nx * g->ny;
   if (Q) SC_CUDA(cudaMemcpy(Q, g->Q, cells * 8, cudaMemcpyDeviceToHost));
-  if (Ex || Ey) {
+  if ((Ex || Ey) && g->field32) {
+    std::vector<float2> E(cells);
+    SC_CUDA(cudaMemcpy(E.data(), g->E, cells * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < cells; ++c) {
+      if (Ex) Ex[c] = E[c].x;
+      if (Ey) Ey[c] = E[c].y;
+    }
+  } else if (Ex || Ey) {
     std::vector<double2> E(cells);
     SC_CUDA(cudaMemcpy(E.data(), g->E, cells * sizeof(double2), cudaMemcpyDeviceToHost));
     for (size_t c = 0; c < cells; ++c) {
@@ -400,7 +414,10 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     SC_CUDA(cudaMemcpy(T->d_elems, dev.data(), dev.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
     if (!marks.empty()) {
       SC_CUDA(cudaMalloc(&T->cell, (size_t)p->n * sizeof(int)));
-      SC_CUDA(cudaMalloc(&T->frac, (size_t)p->n * sizeof(double2)));
+      if (g->field32)
+        SC_CUDA(cudaMalloc(&T->fix, (size_t)p->n * sizeof(int2)));
+      else
+        SC_CUDA(cudaMalloc(&T->frac, (size_t)p->n * sizeof(double2)));
     }
     SC_CUDA(cudaMalloc(&T->psc, (size_t)p->n * 5 * sizeof(double)));
     if (g->trace) {
@@ -423,6 +440,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       set_deposit(T->prologue, g);
       T->prologue.cell = T->cell;
       T->prologue.frac = T->frac;
+      T->prologue.fix = T->fix;
     }
     // ---- capture one turn ------------------------------------------------------
     SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
@@ -439,6 +457,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
         set_deposit(P, g);
         P.cell = T->cell;
         P.frac = T->frac;
+        P.fix = T->fix;
       }
       if (!cst)
         cst = launch_kick_push(P, marks.empty() ? nullptr : g, marks.empty() ? g->kp_blocks_plain : g->kp_blocks,
@@ -464,6 +483,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       // the cell cache is valid at every marker: the previous launch deposited on this grid
       P.cell = T->cell;
       P.frac = T->frac;
+      P.fix = T->fix;
       const bool dep = (k + 1 < marks.size()) || !T->has_head;
       if (dep) set_deposit(P, g);
       cst = launch_kick_push(P, dep ? g : nullptr, dep ? g->kp_blocks : g->kp_blocks_plain, g->stream);

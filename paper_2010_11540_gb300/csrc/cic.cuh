@@ -29,7 +29,8 @@ __device__ __forceinline__ int locate(const GridGeom& g, double x, double y, dou
 // The four CIC weights in 2^-20 fixed point per axis: a = rint(f 2^20)
 // (round half to even), b = 2^20 - a; the products sum to exactly 2^40.
 // dst is either a shared-memory tile or the global grid (same [j][i] layout).
-__device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int cell, double fx, double fy) {
+// Returns the fixed-point fractions (ax, ay).
+__device__ __forceinline__ int2 deposit4(unsigned long long* dst, int nx, int cell, double fx, double fy) {
   const long long ax = __double2ll_rn(__dmul_rn(fx, 1048576.0));
   const long long ay = __double2ll_rn(__dmul_rn(fy, 1048576.0));
   const long long bx = 1048576LL - ax, by = 1048576LL - ay;
@@ -38,6 +39,7 @@ __device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int ce
   atomicAdd(q + 1, (unsigned long long)(ax * by));
   atomicAdd(q + nx, (unsigned long long)(bx * ay));
   atomicAdd(q + nx + 1, (unsigned long long)(ax * ay));
+  return make_int2((int)ax, (int)ay);
 }
 
 // Zero a shared-memory tile of `cells` int64 bins (whole block).

@@ -15,9 +15,11 @@ namespace {
 constexpr int kKPThreads = 512;
 
 // TILE: deposit into a shared-memory tile (grid fits); CACHE: the cell cache
-// P.cell / P.frac is valid for the gather and is refreshed by the deposit;
-// PSC: mode of the per-particle ps-quantity arrays (see KPParams).
-template <bool TILE, bool CACHE, int PSC>
+// of the previous deposit is valid for the gather and is refreshed by this
+// deposit; F32: float32 fields and gather (the split-precision solve's fields
+// carry float32 accuracy; the fractions are then the deposit's own fixed-point
+// weights), else float64 fields and fractions.
+template <bool TILE, bool CACHE, bool F32>
 __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
   const int cells = P.gd.nx * P.gd.ny;
@@ -25,35 +27,60 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
   pdl_wait();  // fields, charge grid and particles of the previous kernels
   if (TILE) __syncthreads();
   unsigned long long* dst = TILE ? tile : P.Q;
+  const int psc_mode = P.psc ? P.psc_mode : 0;
+  const size_t n = (size_t)P.n;
   unsigned int out = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P.n; p += stride) {
     State s{P.x[p], P.px[p], P.y[p], P.py[p], P.sg[p], P.ps[p]};
     if (P.do_kick) {
-      double fx, fy;
       int cell;
-      if (CACHE) {
-        cell = P.cell[p];
-        const double2 f = P.frac[p];
-        fx = f.x;
-        fy = f.y;
+      if (F32) {
+        float fx, fy;
+        if (CACHE) {
+          cell = P.cell[p];
+          const int2 a = P.fix[p];
+          fx = (float)a.x * (1.0f / 1048576.0f);
+          fy = (float)a.y * (1.0f / 1048576.0f);
+        } else {
+          double dx, dy;
+          cell = locate(P.gk, s.x, s.y, dx, dy);
+          fx = (float)dx;
+          fy = (float)dy;
+        }
+        if (cell >= 0) {
+          const float2* e = P.E32 + cell;
+          const float2 e00 = __ldg(e), e10 = __ldg(e + 1);
+          const float2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
+          const float ax = fmaf(fx, e10.x - e00.x, e00.x), bx = fmaf(fx, e11.x - e01.x, e01.x);
+          const float ay = fmaf(fx, e10.y - e00.y, e00.y), by = fmaf(fx, e11.y - e01.y, e01.y);
+          s.px = fma(P.kl, (double)fmaf(fy, bx - ax, ax), s.px);
+          s.py = fma(P.kl, (double)fmaf(fy, by - ay, ay), s.py);
+        }
       } else {
-        cell = locate(P.gk, s.x, s.y, fx, fy);
-      }
-      if (cell >= 0) {
-        const double2* e = P.E + cell;
-        const double2 e00 = __ldg(e), e10 = __ldg(e + 1);
-        const double2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
-        // bilinear interpolation with the gather weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy
-        const double ax = fma(fx, e10.x - e00.x, e00.x), bx = fma(fx, e11.x - e01.x, e01.x);
-        const double ay = fma(fx, e10.y - e00.y, e00.y), by = fma(fx, e11.y - e01.y, e01.y);
-        s.px = fma(P.kl, fma(fy, bx - ax, ax), s.px);
-        s.py = fma(P.kl, fma(fy, by - ay, ay), s.py);
+        double fx, fy;
+        if (CACHE) {
+          cell = P.cell[p];
+          const double2 f = P.frac[p];
+          fx = f.x;
+          fy = f.y;
+        } else {
+          cell = locate(P.gk, s.x, s.y, fx, fy);
+        }
+        if (cell >= 0) {
+          const double2* e = P.E + cell;
+          const double2 e00 = __ldg(e), e10 = __ldg(e + 1);
+          const double2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
+          // bilinear interpolation with the gather weights (1-fx)(1-fy), fx(1-fy), (1-fx)fy, fx fy
+          const double ax = fma(fx, e10.x - e00.x, e00.x), bx = fma(fx, e11.x - e01.x, e01.x);
+          const double ay = fma(fx, e10.y - e00.y, e00.y), by = fma(fx, e11.y - e01.y, e01.y);
+          s.px = fma(P.kl, fma(fy, bx - ax, ax), s.px);
+          s.py = fma(P.kl, fma(fy, by - ay, ay), s.py);
+        }
       }
     }
     PsConst k;
-    if (PSC == 1) {
-      const size_t n = (size_t)P.n;
+    if (psc_mode == 1) {
       k.opd2 = P.psc[p];
       k.opb = P.psc[n + p];
       k.s1 = P.psc[2 * n + p];
@@ -61,13 +88,12 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
       k.qi = P.psc[4 * n + p];
       k.opm = 1.0 - s.ps;
     } else {
-      ps_const(k, s.ps, P.beta0_sq, PSC == 2 || P.has_quad != 0);
+      ps_const(k, s.ps, P.beta0_sq, psc_mode == 2 || P.has_quad != 0);
     }
-    const bool quads = PSC != 0 || P.has_quad != 0;
+    const bool quads = psc_mode != 0 || P.has_quad != 0;
     const bool changed = P.el ? push_elements(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads)
                               : push_elements(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads);
-    if (PSC == 2 || (PSC == 1 && changed)) {
-      const size_t n = (size_t)P.n;
+    if (psc_mode == 2 || (psc_mode == 1 && changed)) {
       P.psc[p] = k.opd2;
       P.psc[n + p] = k.opb;
       P.psc[2 * n + p] = k.s1;
@@ -77,13 +103,17 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
     if (P.do_deposit) {
       double fx, fy;
       const int cell = locate(P.gd, s.x, s.y, fx, fy);
+      int2 a = make_int2(0, 0);
       if (cell >= 0)
-        deposit4(dst, P.gd.nx, cell, fx, fy);
+        a = deposit4(dst, P.gd.nx, cell, fx, fy);
       else
         ++out;
       if (CACHE) {
         P.cell[p] = cell;
-        P.frac[p] = make_double2(fx, fy);
+        if (F32)
+          P.fix[p] = a;
+        else
+          P.frac[p] = make_double2(fx, fy);
       }
     }
     P.x[p] = s.x;
@@ -103,29 +133,24 @@ __global__ void __launch_bounds__(kKPThreads) kick_push_kernel(const __grid_cons
   }
 }
 
-template <bool TILE, bool CACHE, int PSC>
+template <bool TILE, bool CACHE, bool F32>
 int blocks_for(int smem) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (TILE)
-    cudaFuncSetAttribute(kick_push_kernel<TILE, CACHE, PSC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<TILE, CACHE, PSC>, kKPThreads, smem);
+    cudaFuncSetAttribute(kick_push_kernel<TILE, CACHE, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<TILE, CACHE, F32>, kKPThreads, smem);
   return sms * (per < 1 ? 1 : per);
 }
 
 template <bool TILE>
 int min_blocks(int smem) {
-  int b = blocks_for<TILE, false, 0>(smem);
-  const int c[5] = {blocks_for<TILE, false, 1>(smem), blocks_for<TILE, false, 2>(smem), blocks_for<TILE, true, 0>(smem),
-                    blocks_for<TILE, true, 1>(smem), blocks_for<TILE, true, 2>(smem)};
+  const int c[4] = {blocks_for<TILE, false, false>(smem), blocks_for<TILE, false, true>(smem),
+                    blocks_for<TILE, true, false>(smem), blocks_for<TILE, true, true>(smem)};
+  int b = c[0];
   for (int v : c) b = v < b ? v : b;
   return b;
-}
-
-template <bool TILE, bool CACHE>
-decltype(&kick_push_kernel<TILE, CACHE, 0>) pick_psc(int mode) {
-  return mode == 1 ? kick_push_kernel<TILE, CACHE, 1> : mode == 2 ? kick_push_kernel<TILE, CACHE, 2> : kick_push_kernel<TILE, CACHE, 0>;
 }
 
 }  // namespace
@@ -138,12 +163,17 @@ int kick_push_blocks_for(int smem_bytes, bool tile) {
 sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s) {
   const bool tile = P.do_deposit && dep && deposit_uses_tile(dep);
   const bool cache = P.cell != nullptr;
+  const bool f32 = P.field32 != 0;
   const int64_t need = (P.n + kKPThreads - 1) / kKPThreads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
   const int smem = tile ? dep->nx * dep->ny * 8 : 0;
-  const int m = P.psc ? P.psc_mode : 0;
-  auto k = tile ? (cache ? pick_psc<true, true>(m) : pick_psc<true, false>(m))
-                : (cache ? pick_psc<false, true>(m) : pick_psc<false, false>(m));
+  decltype(&kick_push_kernel<true, true, true>) k;
+  if (tile)
+    k = cache ? (f32 ? kick_push_kernel<true, true, true> : kick_push_kernel<true, true, false>)
+              : (f32 ? kick_push_kernel<true, false, true> : kick_push_kernel<true, false, false>);
+  else
+    k = cache ? (f32 ? kick_push_kernel<false, true, true> : kick_push_kernel<false, true, false>)
+              : (f32 ? kick_push_kernel<false, false, true> : kick_push_kernel<false, false, false>);
   SC_CUDA(launch_pdl(k, dim3(blocks), dim3(kKPThreads), (size_t)smem, s, P));
   return SC_OK;
 }

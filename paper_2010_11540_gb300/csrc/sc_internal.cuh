@@ -82,7 +82,11 @@ struct KPParams {
   // the same grid at the same position; the gather reuses it.  cell = j*nx+i
   // or -1 (outside), frac = (fx, fy).  NULL: locate again.
   int* cell;
-  double2* frac;
+  double2* frac;   // float64 fractions (float64 fields)
+  int2* fix;       // fixed-point fractions (ax, ay) of the deposit (float32 fields)
+  // float32 fields: E32 holds (Ex, Ey) as float2 and the gather runs in float32
+  int field32;
+  const float2* E32;
   // deposit
   int do_deposit;
   GridGeom gd;
@@ -130,7 +134,8 @@ struct sc_grid {
   bool own_stream;
   int device;
   unsigned long long* Q;      // [ny*nx] int64 charge (2^40 per particle)
-  double2* E;                 // [ny*nx] (Ex, Ey)
+  double2* E;                 // [ny*nx] (Ex, Ey); float32 pairs in the first half when field32
+  int field32;                // the solve writes float32 fields (SC_SOLVE_TF32X3)
   unsigned long long* n_out;  // device counter
   int64_t n_particles;        // particle count of the last deposit (normalises Q)
   sc::Fft64Plan fft;

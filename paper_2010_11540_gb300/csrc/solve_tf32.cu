@@ -152,7 +152,7 @@ struct GemmArgs {
   float *out_hi, *out_lo;  // next phase's operand (P1: B2, P2A: B3, P2B: A3)
   int out_ld;              // its row length (K of the next phase)
   const float *Sx, *Sy;    // P2A: spectra [Npad][My]
-  double2* E;              // P3: fields
+  float2* E;               // P3: fields, float32 (Ex, Ey) per node
   int* err;                // set to 1 when a bounded wait ran out
 };
 
@@ -429,11 +429,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
         dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
       }
     } else {
-      // row r: field f = r / ny (Ex, Ey) at j = r % ny; columns i = n0 + cc
+      // row r: field f = r / ny (Ex, Ey) at j = r % ny; columns i = n0 + cc; float32 (Ex, Ey) pairs
       const int f = r / g.ny, j = r % g.ny;
-      double* e = (double*)(g.E + (size_t)j * g.nx + n0) + f;
+      float* e = (float*)g.E + 2 * ((size_t)j * g.nx + n0) + f;
 #pragma unroll
-      for (int cc = c0; cc < c0 + CW; ++cc) e[2 * cc] = (double)acc[cc];
+      for (int cc = c0; cc < c0 + CW; ++cc) e[2 * cc] = acc[cc];
     }
   }
   if (SK > 1) cg::this_cluster().sync();  // keep this CTA's partial tile alive until every rank has read it
@@ -729,7 +729,7 @@ sc_status tf32_create(sc_grid* g) {
     return st;
   T->a3.k_chunks = K3 / KC;
   T->a3.n_tiles = nx / NT;
-  T->a3.E = g->E;
+  T->a3.E = (float2*)g->E;
   T->grid3 = (2 * ny / TM) * T->a3.n_tiles;
   if ((st = set_smem_attr<P1, SK1>()) || (st = set_smem_attr<P2A, SK2A>()) || (st = set_smem_attr<P2B, SK2B>()) ||
       (st = set_smem_attr<P3, SK3>()))
