@@ -39,6 +39,8 @@ WORKLOAD = ("c2: 1e6 macroparticles (4D Gaussian, sigma_x=4 mm, sigma_y=3 mm, 0.
 # compares via sm__inst_executed_pipe_fp64) on the bench workload; see the
 # roofline section of the design doc.  base = gather + kick + fused deposit.
 FP64_INST = {"base": 27.5, "drift": 12.2, "quad": 51.5, "sext": 5.0, "bend": 16.0, "rf": 30.0}
+# split-TF32 form: float32 gather (two float->double conversions + two fma for the kick)
+FP64_INST_BASE_F32 = 17.5
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -48,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "tf32x3"])
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3"],
+                    help="solve form of the headline number; the other form is timed beside it")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other solve form")
     ap.add_argument("--config", default="c2")
     ap.add_argument("--cpu-kicks", type=int, default=24, help="oracle sample size in kicks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -111,13 +115,13 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- helpers
-def fp64_inst_per_turn(lat):
+def fp64_inst_per_turn(lat, precision):
     """FP64-pipe instructions per particle per turn from the element mix, and kicks/turn."""
     from paper_2010_11540_gb300 import synth
     t = lat["type"]
     n_k = int((t == synth.MARK).sum())
     per = {synth.DRIFT: "drift", synth.QUAD: "quad", synth.SEXT: "sext", synth.BEND: "bend", synth.RF: "rf"}
-    f = n_k * FP64_INST["base"]
+    f = n_k * (FP64_INST["base"] if precision == "fp64" else FP64_INST_BASE_F32)
     for code, name in per.items():
         f += int((t == code).sum()) * FP64_INST[name]
     return f, n_k
@@ -190,41 +194,53 @@ def run_ours(args):
     parts, b, grid, lat = synth.workload(args.config, seed=12345 + rank)
     n = len(parts["x"])
     keys = ("x", "px", "y", "py", "sigma", "psigma")
-    dev = {k: torch.from_numpy(parts[k]).cuda() for k in keys}
-    g = sc.create_grid(*grid, precision=args.precision, stream=stream)
-    inst_turn, n_kicks = fp64_inst_per_turn(lat)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            sc.track_turns(g, dev, b, lat, 1)
-        stream.synchronize()
-        # ---------------- timed region: K turns, L2 flushed between turns
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        clocks = ClockSampler(local)
-        clocks.start()
+    def timed_turns(precision):
+        """Warm-up turns, then exactly args.steps timed turns, L2 flushed between
+        turns; returns (grid, device state, total ms (max over ranks), wall s, clocks)."""
+        dev = {k: torch.from_numpy(parts[k]).cuda() for k in keys}
+        g = sc.create_grid(*grid, precision=precision, stream=stream)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                sc.track_turns(g, dev, b, lat, 1)
+            stream.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            clocks = ClockSampler(local)
+            clocks.start()
+            if world > 1:
+                torch.distributed.barrier()
+            torch.cuda.synchronize()
+            t_wall = time.perf_counter()
+            for s in range(args.steps):
+                flush.zero_()
+                ev[s][0].record(stream)
+                sc.track_turns(g, dev, b, lat, 1)
+                ev[s][1].record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t_wall
+            if world > 1:
+                torch.distributed.barrier()
+            clk = clocks.stop()
+        ms = sum(a.elapsed_time(c) for a, c in ev)
         if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        t_wall = time.perf_counter()
-        for s in range(args.steps):
-            flush.zero_()
-            ev[s][0].record(stream)
-            sc.track_turns(g, dev, b, lat, 1)
-            ev[s][1].record(stream)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t_wall
-        if world > 1:
-            torch.distributed.barrier()
-        clk = clocks.stop()
-        step_ms = [a.elapsed_time(c) for a, c in ev]
-    ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return g, dev, ms, wall, clk
+
+    inst_turn, n_kicks = fp64_inst_per_turn(lat, args.precision)
+    g, dev, ms, wall, clk = timed_turns(args.precision)
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
+    compare = None
+    if not args.no_compare:
+        other = "fp64" if args.precision == "tf32x3" else "tf32x3"
+        g2, _, ms2, _, clk2 = timed_turns(other)
+        compare = {"precision": other, "value": world * n * n_kicks * args.steps / (ms2 * 1e-3),
+                   "ms_per_step": ms2 / args.steps, "clocks": clk2}
+        g2.close()
 
     # ---------------- dominant kernel, timed inside the turn graph (library tracing:
     # CUDA events on the grid's stream around every solve and kick/push launch)
@@ -259,7 +275,7 @@ def run_ours(args):
     e2e = {"value": n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
            "d2h_bytes_per_step": 6 * 8 * n}
 
-    solve_kernels = 3 if args.precision == "fp64" else 3
+    solve_kernels = 3 if args.precision == "fp64" else 4
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -267,7 +283,7 @@ def run_ours(args):
                        "solve": "fp64 FFT convolution" if args.precision == "fp64" else
                        "tf32x3 DFT GEMMs on tcgen05", "particles": n, "grid": [g.nx, g.ny],
                        "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "e2e": e2e, "clocks": clk,
+            "roofline": roofline, "e2e": e2e, "clocks": clk, "compare_form": compare,
             "gpu_launches": args.steps * n_kicks * (solve_kernels + 1),
             "wall_s_timed": wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -276,17 +292,6 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
-
-
-def _segments(lat, synth):
-    marks = [i for i in range(len(lat)) if int(lat["type"][i]) == synth.MARK]
-    s = np.concatenate([[0.0], np.cumsum(lat["length"])])
-    out = []
-    for k, m in enumerate(marks):
-        end = marks[k + 1] if k + 1 < len(marks) else len(lat)
-        prev = s[marks[k - 1]] if k > 0 else s[marks[-1]] - s[-1]
-        out.append((float(s[m] - prev), lat[m + 1:end]))
-    return lat[: marks[0]], out
 
 
 if __name__ == "__main__":
