@@ -159,6 +159,28 @@ sc_status sc_trace_enable(sc_grid *g, int enable);
  * and solve time in ms, and the number of kicks they cover. */
 sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
+/* Largest particle count sc_moments_noalloc accepts (its partial sums are
+ * reduced in float64 by a fixed 304-block grid; counts are bounded like a
+ * grid's). */
+#define SC_MOMENTS_NOALLOC_MAX_N SC_MAX_PARTICLES_PER_GRID
+
+/* Beam moments that allocate nothing: the paper has no counterpart; this
+ * entry point exists for callers that cannot allocate device memory while
+ * they run (an arena that owns the whole device, an allocator that must not be
+ * re-entered, a real-time loop where cudaMalloc/cudaFree may synchronise).
+ * Writes 14 doubles to the device pointer `out` on `stream` (asynchronous):
+ * means of (x, px, y, py, sigma, psigma), then the central moments <xx>,
+ * <x px>, <px px>, <yy>, <y py>, <py py>, <sigma sigma>, <psigma psigma> — the
+ * same numbers as sc_track_turns' per-turn diagnostics.  Scratch: a
+ * file-scope device array of 304 x 14 doubles (34 KB), held by every GPU that
+ * loads the library until the process exits.  The first call on a device
+ * looks up that array's address (make it before any stream capture); calls
+ * that overlap on the GPU share the array and race.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * Errors: SC_ERR_ARG (NULL, n <= 0), SC_ERR_OVERFLOW (n > SC_MOMENTS_NOALLOC_MAX_N),
+ * SC_ERR_CUDA. */
+sc_status sc_moments_noalloc(const sc_particles *p, double *out, void *stream);
+
 /* Text of the last error on the calling thread (always NUL-terminated). */
 sc_status sc_last_error(char *buf, size_t n);
 

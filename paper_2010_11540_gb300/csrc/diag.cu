@@ -1,6 +1,8 @@
 // Beam moments for the per-turn diagnostics (Sec. V: rms sizes -> beta,
 // emittances).  Two launches with a fixed grid so that the float64 sums are
 // reduced in the same order every time (deterministic).
+#include <atomic>
+
 #include "sc_internal.cuh"
 
 namespace sc {
@@ -84,3 +86,86 @@ sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, d
 }
 
 }  // namespace sc
+
+// ---------------------------------------------------------------------------
+// Beam moments without any device allocation.
+//
+// For callers that cannot allocate device memory while they run: code inside
+// a memory pool or arena that owns all of the device's memory, code running in
+// a process whose allocator must not be re-entered (callbacks, signal-driven
+// monitors), or a real-time loop where cudaMalloc/cudaFree (which can
+// synchronise the device) are not allowed.  The block partial sums live in a
+// file-scope device array instead of a caller- or library-allocated buffer.
+//
+// Every GPU that loads the library's device code holds the array (34 KB) until
+// the process exits.  The first call on a device looks up its device
+// address (cudaGetSymbolAddress) with that device current; make that first
+// call before any stream capture.  Every call writes all kMomBlocks partial
+// rows before they are read, so nothing needs clearing between calls; calls
+// that overlap on the GPU (different streams, or different host threads on the
+// same device) share the array and race.
+// ---------------------------------------------------------------------------
+namespace sc {
+namespace {
+
+constexpr int kMaxDevices = 64;
+static __device__ __align__(256) double g_noalloc_partial[kMomBlocks * kNM];
+
+__global__ void moments_final_to(const double* __restrict__ partial, int n_blocks, int64_t n, double* out) {
+  __shared__ double tot[kNM];
+  if (threadIdx.x < kNM) {
+    double v = 0.0;
+    for (int b = 0; b < n_blocks; ++b) v += partial[(size_t)b * kNM + threadIdx.x];
+    tot[threadIdx.x] = v / (double)n;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* m = tot;
+    for (int c = 0; c < 6; ++c) out[c] = m[c];
+    out[6] = m[6] - m[0] * m[0];
+    out[7] = m[7] - m[0] * m[1];
+    out[8] = m[8] - m[1] * m[1];
+    out[9] = m[9] - m[2] * m[2];
+    out[10] = m[10] - m[2] * m[3];
+    out[11] = m[11] - m[3] * m[3];
+    out[12] = m[12] - m[4] * m[4];
+    out[13] = m[13] - m[5] * m[5];
+  }
+}
+
+std::atomic<double*> g_noalloc_addr[kMaxDevices];
+
+// Device address of g_noalloc_partial on the current device (looked up once).
+sc_status noalloc_scratch(double** out) {
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(SC_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  double* a = g_noalloc_addr[dev].load();
+  if (!a) {
+    SC_CUDA(cudaGetSymbolAddress((void**)&a, g_noalloc_partial));
+    g_noalloc_addr[dev].store(a);
+  }
+  *out = a;
+  return SC_OK;
+}
+
+}  // namespace
+}  // namespace sc
+
+extern "C" sc_status sc_moments_noalloc(const sc_particles* p, double* out, void* stream) {
+  using namespace sc;
+  if (!p || !out) return set_error(SC_ERR_ARG, "particles or out is NULL");
+  if (p->n <= 0) return set_error(SC_ERR_ARG, "sc_moments_noalloc needs at least one particle");
+  if (p->n > SC_MOMENTS_NOALLOC_MAX_N)
+    return set_error(SC_ERR_OVERFLOW, "sc_moments_noalloc: more than SC_MOMENTS_NOALLOC_MAX_N particles");
+  if (!p->x || !p->px || !p->y || !p->py || !p->sigma || !p->psigma)
+    return set_error(SC_ERR_ARG, "particle array pointer is NULL");
+  double* scratch = nullptr;
+  sc_status st = noalloc_scratch(&scratch);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  moments_partial<<<kMomBlocks, kMomThreads, 0, s>>>(p->x, p->px, p->y, p->py, p->sigma, p->psigma, p->n, scratch);
+  moments_final_to<<<1, 32, 0, s>>>(scratch, kMomBlocks, p->n, out);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}

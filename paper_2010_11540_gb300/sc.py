@@ -25,7 +25,8 @@ ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVE
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "tf32x3": 1}
 EXPORTS = ("sc_create_grid", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
-           "sc_grid_read", "sc_grid_write_charge", "sc_trace_enable", "sc_trace_read", "sc_last_error")
+           "sc_grid_read", "sc_grid_write_charge", "sc_trace_enable", "sc_trace_read", "sc_moments_noalloc",
+           "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -69,6 +70,7 @@ def load():
     L.sc_grid_write_charge.argtypes = [vp, vp, i64]
     L.sc_trace_enable.argtypes = [vp, ctypes.c_int]
     L.sc_trace_read.argtypes = [vp, dp, dp, ctypes.POINTER(i64)]
+    L.sc_moments_noalloc.argtypes = [ctypes.POINTER(Particles), vp, vp]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -193,6 +195,14 @@ def trace_read(grid: Grid):
     a, c, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
     _check(load().sc_trace_read(grid.handle, ctypes.byref(a), ctypes.byref(c), ctypes.byref(n)))
     return a.value, c.value, int(n.value)
+
+
+def moments_noalloc(state, out, stream=None):
+    """Beam moments into the 14-element CUDA float64 tensor `out`, through the
+    entry point that allocates no device memory (sc_moments_noalloc)."""
+    p = particles(state)
+    _check(load().sc_moments_noalloc(ctypes.byref(p), out.data_ptr(), _stream_handle(stream)))
+    return out
 
 
 def grid_write_charge(grid: Grid, Q, n_particles: int):
