@@ -148,6 +148,18 @@ sc_status sc_grid_read(sc_grid *g, int64_t *Q, double *Ex, double *Ey, int64_t *
  * count N used to normalise it, e.g. to solve a given charge. */
 sc_status sc_grid_write_charge(sc_grid *g, const int64_t *Q, int64_t n_particles);
 
+/* Per-particle tunes, Sec. V (the betatron tune of a particle is its one-turn
+ * phase advance).  Arms grid g: every turn sc_track_turns then runs ends with
+ * the phase advance of each particle of p in the normalised coordinates of the
+ * bare Twiss functions at the turn start, twiss = {beta_x, alpha_x, beta_y,
+ * alpha_y} (host array), accumulated in acc (device, caller-owned, 4 n
+ * doubles: phases x, phases y, summed advances x, summed advances y, each
+ * advance taken mod 2 pi).  This call records the initial phases and zeroes the
+ * sums (asynchronous, on the grid's stream).  After T tracked turns, the
+ * fractional tunes are sums / (2 pi T).  acc == NULL disarms.
+ * Errors: SC_ERR_ARG. */
+sc_status sc_tune_setup(sc_grid *g, const sc_particles *p, const double *twiss, double *acc);
+
 /* Per-phase tracing.  When enabled, the next turn sc_track_turns captures
  * records CUDA events around every solve and every kick/push launch (on the
  * grid's stream); sc_track_turns then waits after each turn and accumulates

@@ -340,6 +340,23 @@ sc_status sc_grid_read(sc_grid* g, int64_t* Q, double* Ex, double* Ey, int64_t* 
   return SC_OK;
 }
 
+sc_status sc_tune_setup(sc_grid* g, const sc_particles* p, const double* twiss, double* acc) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (!acc) {
+    g->tune_acc = nullptr;
+    return SC_OK;
+  }
+  sc_status st = check_particles(p);
+  if (st) return st;
+  if (!twiss || !(twiss[0] > 0.0) || !(twiss[2] > 0.0) || !std::isfinite(twiss[1]) || !std::isfinite(twiss[3]))
+    return set_error(SC_ERR_ARG, "twiss needs beta_x > 0, alpha_x, beta_y > 0, alpha_y");
+  for (int k = 0; k < 4; ++k) g->tune_twiss[k] = twiss[k];
+  g->tune_acc = acc;
+  if (p->n == 0) return SC_OK;
+  SC_CUDA(cudaMemsetAsync(acc + 2 * p->n, 0, (size_t)p->n * 2 * sizeof(double), g->stream));
+  return launch_phase_advance(p, g->tune_twiss, acc, 0, g->stream);
+}
+
 sc_status sc_trace_enable(sc_grid* g, int enable) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   g->trace = enable ? 1 : 0;
@@ -388,6 +405,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
   put(&g->trace, sizeof g->trace);
+  put(&g->tune_acc, sizeof g->tune_acc);
+  put(g->tune_twiss, sizeof g->tune_twiss);
 
   TrackPlan* T = g->track;
   if (!T || T->key != key) {
@@ -490,6 +509,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       if (!cst && g->trace && cudaEventRecordWithFlags(T->ev[3 * k + 2], g->stream, cudaEventRecordExternal) != cudaSuccess)
         cst = set_error(SC_ERR_CUDA, "event");
     }
+    // per-particle phase advance over the turn (state at the end of the turn = start of the next)
+    if (!cst && g->tune_acc) cst = launch_phase_advance(p, g->tune_twiss, g->tune_acc, 1, g->stream);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
     if (cst) {

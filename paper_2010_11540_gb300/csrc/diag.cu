@@ -77,6 +77,40 @@ __global__ void moments_final(const double* __restrict__ partial, int n_blocks, 
 
 int moments_blocks() { return kMomBlocks; }
 
+// Per-particle betatron phase, Sec. V (tunes as the one-turn phase advance):
+// in normalised coordinates of the bare Twiss (beta, alpha) at the turn start,
+// U = u / sqrt(beta), PU = (alpha u + beta pu) / sqrt(beta), the phase is
+// atan2(-PU, U).  acc (4 arrays of n): previous phase x, previous phase y,
+// accumulated advance x, accumulated advance y; each call adds
+// (phase - previous) mod 2 pi when `accumulate`, and stores the phase.
+__global__ void phase_advance(const double* __restrict__ x, const double* __restrict__ px,
+                              const double* __restrict__ y, const double* __restrict__ py, int64_t n, double bx,
+                              double ax, double by, double ay, double* acc, int accumulate) {
+  const double rbx = rsqrt(bx), rby = rsqrt(by);
+  const double two_pi = 6.283185307179586;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const double tx = atan2(-(ax * x[p] + bx * px[p]) * rbx, x[p] * rbx);
+    const double ty = atan2(-(ay * y[p] + by * py[p]) * rby, y[p] * rby);
+    if (accumulate) {
+      double dx = fmod(tx - acc[p], two_pi), dy = fmod(ty - acc[n + p], two_pi);
+      if (dx < 0.0) dx += two_pi;
+      if (dy < 0.0) dy += two_pi;
+      acc[2 * n + p] += dx;
+      acc[3 * n + p] += dy;
+    }
+    acc[p] = tx;
+    acc[n + p] = ty;
+  }
+}
+
+sc_status launch_phase_advance(const sc_particles* p, const double* twiss, double* acc, int accumulate,
+                               cudaStream_t s) {
+  phase_advance<<<kMomBlocks, kMomThreads, 0, s>>>(p->x, p->px, p->y, p->py, p->n, twiss[0], twiss[1], twiss[2],
+                                                   twiss[3], acc, accumulate);
+  SC_CUDA(cudaGetLastError());
+  return SC_OK;
+}
+
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
                          cudaStream_t s) {
   moments_partial<<<n_blocks, kMomThreads, 0, s>>>(p->x, p->px, p->y, p->py, p->sigma, p->psigma, p->n, partial);

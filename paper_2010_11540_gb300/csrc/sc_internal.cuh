@@ -142,6 +142,8 @@ struct sc_grid {
   sc::Tf32Plan* tf32;
   sc::TrackPlan* track;
   int trace;                   // record per-phase events in captured turns
+  double* tune_acc;            // per-particle phase accumulators (caller-owned, 4 n) or NULL
+  double tune_twiss[4];        // bare beta_x, alpha_x, beta_y, alpha_y at the turn start
   double trace_kp_ms, trace_solve_ms;
   int64_t trace_kicks;
   int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
@@ -174,6 +176,8 @@ int tf32_error(sc_grid* g);  // 1 when a tensor-core solve gave up on a bounded 
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
                          cudaStream_t s);
 int moments_blocks();
+sc_status launch_phase_advance(const sc_particles* p, const double* twiss, double* acc, int accumulate,
+                               cudaStream_t s);
 
 // Build the cyclic difference-kernel fields Dx, Dy on the doubled grid, float64
 // host arrays [My][Mx] (used by both solve forms).

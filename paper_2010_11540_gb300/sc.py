@@ -25,7 +25,8 @@ ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVE
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "tf32x3": 1}
 EXPORTS = ("sc_create_grid", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
-           "sc_grid_read", "sc_grid_write_charge", "sc_trace_enable", "sc_trace_read", "sc_moments_noalloc",
+           "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
+           "sc_moments_noalloc",
            "sc_last_error")
 
 
@@ -68,6 +69,7 @@ def load():
                                  ctypes.c_int, dp]
     L.sc_grid_read.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64)]
     L.sc_grid_write_charge.argtypes = [vp, vp, i64]
+    L.sc_tune_setup.argtypes = [vp, ctypes.POINTER(Particles), dp, vp]
     L.sc_trace_enable.argtypes = [vp, ctypes.c_int]
     L.sc_trace_read.argtypes = [vp, dp, dp, ctypes.POINTER(i64)]
     L.sc_moments_noalloc.argtypes = [ctypes.POINTER(Particles), vp, vp]
@@ -184,6 +186,21 @@ def grid_read(grid: Grid):
     n_out = ctypes.c_int64(0)
     _check(load().sc_grid_read(grid.handle, Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data, ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
+
+
+def tune_setup(grid: Grid, state, twiss, acc):
+    """Arm per-particle tune accumulation (sc_tune_setup); acc: CUDA float64
+    tensor of 4 n elements (None disarms).  twiss = (beta_x, alpha_x, beta_y, alpha_y)."""
+    p = particles(state)
+    tw = (ctypes.c_double * 4)(*[float(v) for v in twiss])
+    _check(load().sc_tune_setup(grid.handle, ctypes.byref(p), tw, acc.data_ptr() if acc is not None else None))
+
+
+def tunes(acc, n, turns):
+    """Fractional tunes (qx, qy) per particle from a tune accumulator after `turns` turns."""
+    import math
+    a = acc.view(4, n)
+    return (a[2] / (2 * math.pi * turns)).cpu().numpy(), (a[3] / (2 * math.pi * turns)).cpu().numpy()
 
 
 def trace_enable(grid: Grid, enable: bool = True):

@@ -331,3 +331,65 @@ def test_trace_accumulates_phase_times():
     sc.track_turns(g2, st2, b, lat, 2)
     c = to_host(st2)
     assert all(np.array_equal(a[k], c[k]) for k in KEYS)
+
+
+# ------------------------------------------------------------------ 256x256 grids (no shared-memory tile)
+def test_deposit_bit_exact_256():
+    """4e6 particles on a 256x256 grid: the 512 KB int64 grid exceeds a block's
+    shared memory, so the deposit accumulates straight into global memory."""
+    parts = synth.gaussian_bunch(4000000, 99, 4e-3, 3e-3, 2e-4, 2e-4)
+    grid = (256, 256) + synth.grid_extent(4e-3, 3e-3)
+    g, og = grid_pair(grid)
+    sc.deposit(g, to_gpu(parts))
+    Q, _, _, n_out = sc.grid_read(g)
+    Qo, n_out_o = oracle.deposit(og, parts["x"], parts["y"])
+    assert np.array_equal(Q, Qo) and n_out == n_out_o
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_track_256_one_turn(precision):
+    """c3-sized grid (256x256) with 5e5 particles, one turn of the c2 ring."""
+    parts, b, _, lat = synth.workload("c2", n=500000)
+    grid = (256, 256) + synth.grid_extent(4e-3, 3e-3)
+    g, og = grid_pair(grid, precision=precision)
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(og, ref, b, lat, 1)
+    if precision == "fp64":
+        err = rel_state_err(got, ref)
+        assert max(err.values()) < 1e-10, err
+    else:
+        for k in KEYS:
+            scale = np.sqrt(np.mean(ref[k] ** 2))
+            d = got[k] - ref[k]
+            assert np.sqrt(np.mean(d * d)) < 1e-5 * scale, k
+
+
+def test_tunes_match_oracle_phase_advance():
+    """Per-particle tunes (Sec. V: one-turn phase advance) accumulated on the GPU
+    over 8 turns with space charge equal the oracle's, and without space charge
+    equal the bare tune from the one-turn matrix."""
+    import torch
+    parts, b, grid, lat = synth.workload("c1", n=4096)
+    M = oracle.one_turn_matrix(lat, b)
+    mux, bx, ax = oracle.twiss_from_matrix(M[:2, :2])
+    muy, by, ay = oracle.twiss_from_matrix(M[2:, 2:])
+    for n_lambda in (b["n_lambda"], 0.0):
+        bb = dict(b, n_lambda=n_lambda)
+        g, og = grid_pair(grid)
+        st = to_gpu(parts)
+        acc = torch.zeros(4 * 4096, dtype=torch.float64, device="cuda")
+        sc.tune_setup(g, st, (bx, ax, by, ay), acc)
+        sc.track_turns(g, st, bb, lat, 8)
+        qx, qy = sc.tunes(acc, 4096, 8)
+        pa = oracle.PhaseAdvance(bx, ax, by, ay)
+        ref = oracle.copy_state(parts)
+        oracle.track(og, ref, bb, lat, 8, diag=pa)
+        pa(8, ref)
+        rqx, rqy = pa.tunes()
+        assert np.mean(np.abs(qx - rqx) < 1e-9) > 0.999 and np.mean(np.abs(qy - rqy) < 1e-9) > 0.999
+        if n_lambda == 0.0:
+            # chromatic spread only: mean tune = bare tune to the psigma spread
+            assert abs(np.median(qx) - mux / (2 * np.pi)) < 2e-3
