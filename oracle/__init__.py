@@ -47,16 +47,24 @@ class _Beam(ctypes.Structure):
 
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
-_lp = ctypes.POINTER(ctypes.c_int64)
+_lp = ctypes.POINTER(ctypes.c_uint64)
 
 
 def lib():
     global _lib
     if _lib is None:
         L = ctypes.CDLL(build())
-        L.orc_deposit.restype = ctypes.c_int64
+        L.orc_deposit.restype = ctypes.c_uint64
         L.orc_deposit.argtypes = [ctypes.c_int64, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, _lp]
+        L.orc_deposit_sliced.restype = ctypes.c_uint64
+        L.orc_deposit_sliced.argtypes = [ctypes.c_int64, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_double, ctypes.c_double, _lp]
+        L.orc_kick_sliced.restype = None
+        L.orc_kick_sliced.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, ctypes.c_double]
         L.orc_green_self.restype = ctypes.c_double
         L.orc_green_self.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_green_cyclic.restype = None
@@ -109,9 +117,40 @@ class Geometry:
         return self.ymin + np.arange(self.ny) * self.hy
 
 
+class Slices:
+    """Longitudinal slicing: nz bins of sigma over [zmin, zmax) (the line density
+    lambda(z) of Sec. IV as a histogram of sigma), each bin with its own grid."""
+
+    def __init__(self, nz, zmin, zmax):
+        self.nz, self.zmin, self.zmax = int(nz), float(zmin), float(zmax)
+        self.dz = (self.zmax - self.zmin) / self.nz
+        self.inv_dz = 1.0 / self.dz
+
+
+def deposit_sliced(g: Geometry, zs: Slices, x, y, sg):
+    """CIC deposit per slice -> (Q uint64 [nz, ny, nx], n_out)."""
+    Q = np.zeros((zs.nz, g.ny, g.nx), dtype=np.uint64)
+    n_out = lib().orc_deposit_sliced(len(x), _d(x), _d(y), _d(sg), g.nx, g.ny, g.xmin, g.ymin, g.inv_hx, g.inv_hy,
+                                     zs.nz, zs.zmin, zs.inv_dz, Q.ctypes.data_as(_lp))
+    return Q, int(n_out)
+
+
+def kick_sliced(g: Geometry, zs: Slices, st, Ex, Ey, kl):
+    lib().orc_kick_sliced(len(st["x"]), _d(st["x"]), _d(st["y"]), _d(st["sigma"]), _d(st["px"]), _d(st["py"]),
+                          g.nx, g.ny, g.xmin, g.ymin, g.inv_hx, g.inv_hy, zs.nz, zs.zmin, zs.inv_dz,
+                          _d(np.ascontiguousarray(Ex)), _d(np.ascontiguousarray(Ey)), kl)
+
+
+def solve_sliced(g: Geometry, Q, n_total, method="fft"):
+    """Per-slice fields (Ex, Ey) [nz, ny, nx], each slice's charge normalised by
+    the total macroparticle count."""
+    out = [solve(g, Q[k], n_total, method) for k in range(Q.shape[0])]
+    return np.stack([e[0] for e in out]), np.stack([e[1] for e in out])
+
+
 def deposit(g: Geometry, x, y):
-    """CIC deposit (Sec. IV-A) -> (Q int64 [ny, nx], n_out)."""
-    Q = np.zeros((g.ny, g.nx), dtype=np.int64)
+    """CIC deposit (Sec. IV-A) -> (Q uint64 [ny, nx], n_out)."""
+    Q = np.zeros((g.ny, g.nx), dtype=np.uint64)
     n_out = lib().orc_deposit(len(x), _d(x), _d(y), g.nx, g.ny, g.xmin, g.ymin, g.inv_hx, g.inv_hy,
                               Q.ctypes.data_as(_lp))
     return Q, int(n_out)
@@ -230,11 +269,13 @@ def segments(lattice):
     return head, kicks
 
 
-def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None):
+def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None, slices=None):
     """Track `st` (modified in place) for n_turns with the PIC loop of Sec. I.
     Each space-charge location: deposit -> solve -> kick (L since the previous
     location) -> push to the next location.  Returns the number of kicks done.
-    `diag(turn, st)` is called at the start of every turn."""
+    `diag(turn, st)` is called at the start of every turn.  With `slices`
+    (a Slices), every slice has its own grid and b["n_lambda"] is the line
+    density of a slice that held the whole bunch (N / dz)."""
     head, kicks = segments(lattice)
     K = kick_strength(b)
     n = len(st["x"])
@@ -246,9 +287,14 @@ def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kic
         for L, seg in kicks:
             if max_kicks is not None and done >= max_kicks:
                 return done
-            Q, _ = deposit(g, st["x"], st["y"])
-            Ex, Ey = solve(g, Q, n, method)
-            kick(g, st, Ex, Ey, K * L)
+            if slices is None:
+                Q, _ = deposit(g, st["x"], st["y"])
+                Ex, Ey = solve(g, Q, n, method)
+                kick(g, st, Ex, Ey, K * L)
+            else:
+                Q, _ = deposit_sliced(g, slices, st["x"], st["y"], st["sigma"])
+                Ex, Ey = solve_sliced(g, Q, n, method)
+                kick_sliced(g, slices, st, Ex, Ey, K * L)
             push(st, seg, b)
             done += 1
     return done

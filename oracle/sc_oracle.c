@@ -11,7 +11,10 @@
  *
  * Contents, each following the passage cited at the function:
  *   orc_deposit        Sec. IV-A, CIC charge-assignment equation (4 weights),
- *                      in 2^-20 fixed point per axis, int64 accumulation.
+ *                      in 2^-20 fixed point per axis, uint64 accumulation;
+ *                      optionally into one of nz longitudinal slices by sigma
+ *                      (the line density lambda(z) of Sec. IV as a histogram
+ *                      of sigma, each bin with its own transverse grid).
  *   orc_green_self     cell-averaged -ln r (self term of the open-boundary
  *                      Green's function; the paper is silent, see DESIGN).
  *   orc_green_cyclic   Hockney's zero-padded free-space Green's function
@@ -54,33 +57,51 @@ static const double ORC_ONE_FX = 1048576.0; /* 2^20 */
  * It is inside iff 0 <= xi < nx-1 and 0 <= eta < ny-1; outside particles
  * deposit nothing and are counted (return value).
  * The paper's weights (x_{i+1}-x)(y_{j+1}-y)/(dx dy), ... are taken at 2^-20
- * resolution per axis: ax = rint(fx*2^20), bx = 2^20 - ax, and Q (int64,
+ * resolution per axis: ax = rint(fx*2^20), bx = 2^20 - ax, and Q (uint64,
  * Q[j*nx + i]) gets bx*by, ax*by, bx*ay, ax*ay at (i,j), (i+1,j), (i,j+1),
  * (i+1,j+1).  Each particle adds exactly 2^40.  Q is accumulated, not zeroed.
  * ------------------------------------------------------------------- */
-int64_t orc_deposit(int64_t n, const double *x, const double *y, int nx, int ny,
-                    double xmin, double ymin, double inv_hx, double inv_hy, int64_t *Q) {
-  int64_t n_out = 0;
+/* Slice of a particle: zeta = (sg - zmin)*inv_dz (two roundings), slice
+ * k = floor(zeta), valid iff 0 <= zeta < nz.  nz == 1 means no slicing
+ * (every particle is in slice 0). */
+static int orc_slice(double sg, int nz, double zmin, double inv_dz) {
+  if (nz <= 1) return 0;
+  double zeta = (sg - zmin) * inv_dz;
+  if (!(zeta >= 0.0 && zeta < (double)nz)) return -1;
+  return (int)floor(zeta);
+}
+
+uint64_t orc_deposit_sliced(int64_t n, const double *x, const double *y, const double *sg, int nx, int ny,
+                            double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin,
+                            double inv_dz, uint64_t *Q) {
+  uint64_t n_out = 0;
   for (int64_t p = 0; p < n; ++p) {
+    int k = orc_slice(sg ? sg[p] : 0.0, nz, zmin, inv_dz);
     double xi = (x[p] - xmin) * inv_hx;
     double eta = (y[p] - ymin) * inv_hy;
-    if (!(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) {
+    if (k < 0 || !(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) {
       ++n_out;
       continue;
     }
     double fi = floor(xi), fj = floor(eta);
     int i = (int)fi, j = (int)fj;
     double fx = xi - fi, fy = eta - fj;
-    int64_t ax = (int64_t)llrint(fx * ORC_ONE_FX);
-    int64_t ay = (int64_t)llrint(fy * ORC_ONE_FX);
-    int64_t bx = (int64_t)ORC_ONE_FX - ax;
-    int64_t by = (int64_t)ORC_ONE_FX - ay;
-    Q[(int64_t)j * nx + i] += bx * by;
-    Q[(int64_t)j * nx + i + 1] += ax * by;
-    Q[(int64_t)(j + 1) * nx + i] += bx * ay;
-    Q[(int64_t)(j + 1) * nx + i + 1] += ax * ay;
+    uint64_t ax = (uint64_t)llrint(fx * ORC_ONE_FX);
+    uint64_t ay = (uint64_t)llrint(fy * ORC_ONE_FX);
+    uint64_t bx = (uint64_t)ORC_ONE_FX - ax;
+    uint64_t by = (uint64_t)ORC_ONE_FX - ay;
+    uint64_t *q = Q + (int64_t)k * nx * ny;
+    q[(int64_t)j * nx + i] += bx * by;
+    q[(int64_t)j * nx + i + 1] += ax * by;
+    q[(int64_t)(j + 1) * nx + i] += bx * ay;
+    q[(int64_t)(j + 1) * nx + i + 1] += ax * ay;
   }
   return n_out;
+}
+
+uint64_t orc_deposit(int64_t n, const double *x, const double *y, int nx, int ny, double xmin, double ymin,
+                     double inv_hx, double inv_hy, uint64_t *Q) {
+  return orc_deposit_sliced(n, x, y, 0, nx, ny, xmin, ymin, inv_hx, inv_hy, 1, 0.0, 0.0, Q);
 }
 
 /* ---------------------------------------------------------------------
@@ -153,7 +174,8 @@ void orc_fields(int nx, int ny, double hx, double hy, const double *phi_ext, dou
 }
 
 /* ---------------------------------------------------------------------
- * Space-charge kick, Sec. IV (transverse kick equation):
+ * Space-charge kick, Sec. IV (transverse kick equation), optionally per
+ * longitudinal slice (E arrays then hold nz grids):
  *   dp = -(e lambda / (m gamma0^3 beta0^2 c^2)) grad u * L,
  * with u normalised per unit line charge.  In the normalisation above this
  * is dpx = K * L * Ex, dpy = K * L * Ey, K = 2 r_p N_lambda / (beta0^2 gamma0^3),
@@ -161,24 +183,30 @@ void orc_fields(int nx, int ny, double hx, double hy, const double *phi_ext, dou
  * interpolation of the node fields with the same cell and fractions as the
  * deposit (float64 fractions).  Particles outside the grid get no kick.
  * ------------------------------------------------------------------- */
-void orc_kick(int64_t n, const double *x, const double *y, double *px, double *py,
-              int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy,
-              const double *Ex, const double *Ey, double kl) {
+void orc_kick_sliced(int64_t n, const double *x, const double *y, const double *sg, double *px, double *py,
+                     int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin,
+                     double inv_dz, const double *Ex, const double *Ey, double kl) {
   for (int64_t p = 0; p < n; ++p) {
+    int k = orc_slice(sg ? sg[p] : 0.0, nz, zmin, inv_dz);
     double xi = (x[p] - xmin) * inv_hx;
     double eta = (y[p] - ymin) * inv_hy;
-    if (!(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) continue;
+    if (k < 0 || !(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) continue;
     double fi = floor(xi), fj = floor(eta);
     int i = (int)fi, j = (int)fj;
     double fx = xi - fi, fy = eta - fj;
     double w00 = (1.0 - fx) * (1.0 - fy), w10 = fx * (1.0 - fy);
     double w01 = (1.0 - fx) * fy, w11 = fx * fy;
-    int64_t c = (int64_t)j * nx + i;
+    int64_t c = (int64_t)k * nx * ny + (int64_t)j * nx + i;
     double ex = w00 * Ex[c] + w10 * Ex[c + 1] + w01 * Ex[c + nx] + w11 * Ex[c + nx + 1];
     double ey = w00 * Ey[c] + w10 * Ey[c + 1] + w01 * Ey[c + nx] + w11 * Ey[c + nx + 1];
     px[p] += kl * ex;
     py[p] += kl * ey;
   }
+}
+
+void orc_kick(int64_t n, const double *x, const double *y, double *px, double *py, int nx, int ny, double xmin,
+              double ymin, double inv_hx, double inv_hy, const double *Ex, const double *Ey, double kl) {
+  orc_kick_sliced(n, x, y, 0, px, py, nx, ny, xmin, ymin, inv_hx, inv_hy, 1, 0.0, 0.0, Ex, Ey, kl);
 }
 
 /* ---------------------------------------------------------------------

@@ -33,12 +33,12 @@ def _worker(rank, world, port, split, out_path):
     lo = 0 if rank == 0 else split
     hi = split if rank == 0 else len(parts["x"])
     Q, n_out = oracle.deposit(g, np.ascontiguousarray(parts["x"][lo:hi]), np.ascontiguousarray(parts["y"][lo:hi]))
-    t = torch.from_numpy(Q.copy())
+    t = torch.from_numpy(Q.view(np.int64).copy())  # uint64 sums modulo 2^64 are the same bits
     c = torch.tensor([n_out], dtype=torch.int64)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     dist.all_reduce(c, op=dist.ReduceOp.SUM)
     if rank == 0:
-        np.save(out_path, np.concatenate([t.numpy().ravel(), c.numpy()]))
+        np.save(out_path, np.concatenate([t.numpy().view(np.uint64).ravel(), c.numpy().astype(np.uint64)]))
     dist.destroy_process_group()
 
 
