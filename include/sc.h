@@ -55,9 +55,10 @@ typedef int sc_status;
 #define SC_RF 4    /* thin RF cavity                                           */
 #define SC_MARK 5  /* space-charge location (kick point), Sec. V               */
 
-/* Largest macroparticle count one grid may hold: each particle deposits
- * exactly 2^40 fixed-point units, so 2^23 particles fill an int64. */
-#define SC_MAX_PARTICLES_PER_GRID (1LL << 23)
+/* Largest macroparticle count per call: each particle deposits exactly 2^40
+ * fixed-point units into an unsigned 64-bit grid, which holds fewer than 2^24
+ * particles' worth even if all of them land in one cell (or one slice). */
+#define SC_MAX_PARTICLES_PER_GRID ((1LL << 24) - 1)
 
 typedef struct sc_grid sc_grid; /* opaque */
 
@@ -96,10 +97,27 @@ typedef struct {
 sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
                          double ymax, int precision, void *stream);
 
+/* Longitudinally sliced grid (2.5-D): the line density lambda(z) of Sec. IV
+ * as a histogram of sigma with n_slices bins over [zmin, zmax), each bin with
+ * its own nx x ny transverse grid of the given extent.  A particle belongs to
+ * slice k = floor((sigma - zmin) * (1 / dz)), dz = (zmax - zmin) / n_slices; particles outside
+ * [zmin, zmax) are outside the grid.  Every call then works on all slices:
+ * deposits fill each particle's slice, one solve call solves every slice
+ * (batched launches), the kick gathers from the particle's slice.  Each
+ * slice's charge is normalised by the total particle count N, so sc_beam's
+ * n_lambda is the line density of a slice holding the whole bunch (N_ppb / dz).
+ * Deposits are fastest with particles sorted by sigma.  Charge and field
+ * arrays of sc_grid_read / sc_grid_write_charge then hold n_slices grids,
+ * slice-major.  1 <= n_slices <= 1024 and nx*ny*n_slices <= 2^28, else
+ * SC_ERR_ARG; other arguments and errors as sc_create_grid. */
+sc_status sc_create_grid_sliced(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
+                                double ymax, int n_slices, double zmin, double zmax, int precision,
+                                void *stream);
+
 /* Release a grid and everything it owns (synchronises its stream). NULL ok. */
 sc_status sc_destroy_grid(sc_grid *g);
 
-/* CIC charge deposition, Sec. IV-A: zero the grid's int64 charge Q, then add
+/* CIC charge deposition, Sec. IV-A: zero the grid's uint64 charge Q, then add
  * each particle's four fixed-point weights (2^-20 per axis, 2^40 per
  * particle).  Particles outside [xmin, xmax) x [ymin, ymax) (and non-finite
  * ones) deposit nothing and are counted (sc_grid_read's n_out).
@@ -140,13 +158,14 @@ sc_status sc_track_turns(sc_grid *g, const sc_particles *p, const sc_beam *b,
                          const sc_element *lattice, int n_elems, int n_turns, double *diag);
 
 /* Synchronous copy-out of a grid's state into host arrays (each may be NULL):
- * Q (nx*ny int64, row-major [j][i]), Ex and Ey (nx*ny float64), and n_out =
- * particles found outside the grid by deposits since the grid was created. */
-sc_status sc_grid_read(sc_grid *g, int64_t *Q, double *Ex, double *Ey, int64_t *n_out);
+ * Q (n_slices*ny*nx uint64, row-major [k][j][i]), Ex and Ey (same layout,
+ * float64), and n_out = particles found outside the grid by deposits since
+ * the grid was created. */
+sc_status sc_grid_read(sc_grid *g, uint64_t *Q, double *Ex, double *Ey, int64_t *n_out);
 
-/* Synchronous upload of a charge grid Q (host, nx*ny int64) and the particle
- * count N used to normalise it, e.g. to solve a given charge. */
-sc_status sc_grid_write_charge(sc_grid *g, const int64_t *Q, int64_t n_particles);
+/* Synchronous upload of a charge grid Q (host, n_slices*ny*nx uint64) and the
+ * particle count N used to normalise it, e.g. to solve a given charge. */
+sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particles);
 
 /* Per-particle tunes, Sec. V (the betatron tune of a particle is its one-turn
  * phase advance).  Arms grid g: every turn sc_track_turns then runs ends with

@@ -75,7 +75,7 @@ sc_status check_particles(const sc_particles* p) {
   if (p->n > 0 && (!p->x || !p->px || !p->y || !p->py || !p->sigma || !p->psigma))
     return set_error(SC_ERR_ARG, "particle array pointer is NULL");
   if (p->n > SC_MAX_PARTICLES_PER_GRID)
-    return set_error(SC_ERR_OVERFLOW, "more than 2^23 particles on one grid would overflow the int64 charge");
+    return set_error(SC_ERR_OVERFLOW, "2^24 or more particles on one grid could overflow the 64-bit charge");
   return SC_OK;
 }
 
@@ -174,8 +174,18 @@ sc_status sc_last_error(char* buf, size_t n) {
 
 sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
                          int precision, void* stream) {
+  return sc_create_grid_sliced(out, nx, ny, xmin, xmax, ymin, ymax, 1, 0.0, 0.0, precision, stream);
+}
+
+sc_status sc_create_grid_sliced(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                                int n_slices, double zmin, double zmax, int precision, void* stream) {
   if (!out) return set_error(SC_ERR_ARG, "out is NULL");
+  if (n_slices < 1 || n_slices > 1024) return set_error(SC_ERR_ARG, "n_slices must be in 1..1024");
+  if (n_slices > 1 && (!(zmax > zmin) || !std::isfinite(zmin) || !std::isfinite(zmax)))
+    return set_error(SC_ERR_ARG, "slice range must be finite with zmax > zmin");
   if (nx < 2 || ny < 2 || nx > 4096 || ny > 4096) return set_error(SC_ERR_ARG, "grid needs 2..4096 nodes per axis");
+  if ((int64_t)nx * ny * n_slices > (1LL << 28))  // cell indices stay 32-bit
+    return set_error(SC_ERR_ARG, "more than 2^28 nodes over all slices");
   if (!(xmax > xmin) || !(ymax > ymin) || !std::isfinite(xmin) || !std::isfinite(xmax) || !std::isfinite(ymin) ||
       !std::isfinite(ymax))
     return set_error(SC_ERR_ARG, "grid extent must be finite with xmax > xmin, ymax > ymin");
@@ -185,6 +195,9 @@ sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax
   if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
   g->nx = nx;
   g->ny = ny;
+  g->nz = n_slices;
+  g->zmin = zmin;
+  g->zmax = zmax;
   g->precision = precision;
   g->field32 = (precision == SC_SOLVE_TF32X3);
   g->xmin = xmin;
@@ -201,6 +214,9 @@ sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax
   g->geom.inv_hy = 1.0 / g->hy;
   g->geom.xlast = (double)(nx - 1);
   g->geom.ylast = (double)(ny - 1);
+  g->geom.nz = n_slices;
+  g->geom.zmin = zmin;
+  g->geom.inv_dz = n_slices > 1 ? 1.0 / ((zmax - zmin) / (double)n_slices) : 0.0;  // 1 / dz
   sc_status st = SC_OK;
   cudaError_t e = cudaGetDevice(&g->device);
   if (e != cudaSuccess) {
@@ -220,7 +236,7 @@ sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax
     }
     g->own_stream = true;
   }
-  const size_t cells = (size_t)nx * ny;
+  const size_t cells = (size_t)nx * ny * n_slices;  // all slices
   if ((e = cudaMalloc(&g->Q, cells * 8)) != cudaSuccess || (e = cudaMalloc(&g->E, cells * sizeof(double2))) != cudaSuccess ||
       (e = cudaMalloc(&g->n_out, 8)) != cudaSuccess) {
     st = cuda_error(e, "cudaMalloc(grid)");
@@ -231,8 +247,9 @@ sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax
   cudaMemsetAsync(g->E, 0, cells * sizeof(double2), g->stream);
   cudaMemsetAsync(g->n_out, 0, 8, g->stream);
   const bool tile = deposit_uses_tile(g);
-  g->dep_blocks = deposit_blocks_for(tile ? (int)(cells * 8) : 0, tile);
-  g->kp_blocks = kick_push_blocks_for(tile ? (int)(cells * 8) : 0, tile);
+  const int tile_bytes = nx * ny * 8;  // one slice
+  g->dep_blocks = deposit_blocks_for(tile ? tile_bytes : 0, tile);
+  g->kp_blocks = kick_push_blocks_for(tile ? tile_bytes : 0, tile);
   g->kp_blocks_plain = kick_push_blocks_for(0, false);
   st = (precision == SC_SOLVE_TF32X3) ? tf32_create(g) : fft64_create(g);
   if (st == SC_OK) {
@@ -268,7 +285,7 @@ sc_status sc_deposit(sc_grid* g, const sc_particles* p) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   sc_status st = check_particles(p);
   if (st) return st;
-  SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * 8, g->stream));
+  SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nz * 8, g->stream));
   g->n_particles = p->n;
   if (p->n == 0) return SC_OK;
   return launch_deposit(g, p);
@@ -286,7 +303,7 @@ sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, doub
   sc_status st;
   if ((st = check_beam(b)) || (st = check_particles(p)) || (st = check_elements(elems, n_elems))) return st;
   if (next) {
-    SC_CUDA(cudaMemsetAsync(next->Q, 0, (size_t)next->nx * next->ny * 8, g->stream));
+    SC_CUDA(cudaMemsetAsync(next->Q, 0, (size_t)next->nx * next->ny * next->nz * 8, g->stream));
     next->n_particles = p->n;
   }
   if (p->n == 0) return SC_OK;
@@ -311,10 +328,10 @@ sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, doub
   return launch_kick_push(P, next, next ? next->kp_blocks : g->kp_blocks_plain, g->stream);
 }
 
-sc_status sc_grid_read(sc_grid* g, int64_t* Q, double* Ex, double* Ey, int64_t* n_out) {
+sc_status sc_grid_read(sc_grid* g, uint64_t* Q, double* Ex, double* Ey, int64_t* n_out) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   SC_CUDA(cudaStreamSynchronize(g->stream));
-  const size_t cells = (size_t)g->nx * g->ny;
+  const size_t cells = (size_t)g->nx * g->ny * g->nz;
   if (Q) SC_CUDA(cudaMemcpy(Q, g->Q, cells * 8, cudaMemcpyDeviceToHost));
   if ((Ex || Ey) && g->field32) {
     std::vector<float2> E(cells);
@@ -375,11 +392,11 @@ sc_status sc_trace_read(sc_grid* g, double* kick_push_ms, double* solve_ms, int6
   return SC_OK;
 }
 
-sc_status sc_grid_write_charge(sc_grid* g, const int64_t* Q, int64_t n_particles) {
+sc_status sc_grid_write_charge(sc_grid* g, const uint64_t* Q, int64_t n_particles) {
   if (!g || !Q) return set_error(SC_ERR_ARG, "grid or Q is NULL");
   if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
   SC_CUDA(cudaStreamSynchronize(g->stream));
-  SC_CUDA(cudaMemcpy(g->Q, Q, (size_t)g->nx * g->ny * 8, cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(g->Q, Q, (size_t)g->nx * g->ny * g->nz * 8, cudaMemcpyHostToDevice));
   g->n_particles = n_particles;
   return SC_OK;
 }
@@ -548,7 +565,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   g->n_particles = p->n;
   if (!T->has_head && T->n_kicks > 0) {
     // charge at the first space-charge location of the first turn
-    SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * 8, g->stream));
+    SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nz * 8, g->stream));
     if ((st = launch_kick_push(T->prologue, g, g->kp_blocks, g->stream))) return st;
   } else {
     if ((st = launch_kick_push(T->prologue, nullptr, g->kp_blocks_plain, g->stream))) return st;

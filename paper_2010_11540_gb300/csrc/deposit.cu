@@ -10,30 +10,36 @@ constexpr int kDepThreads = 512;
 
 template <bool TILE>
 __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __restrict__ x,
-                                                               const double* __restrict__ y, int64_t n,
+                                                               const double* __restrict__ y,
+                                                               const double* __restrict__ sg, int64_t n,
                                                                GridGeom g, unsigned long long* Q,
                                                                unsigned long long* n_out) {
   extern __shared__ unsigned long long tile[];
+  __shared__ int tile_k;
   const int cells = g.nx * g.ny;
   if (TILE) {
     tile_zero(tile, cells);
+    if (threadIdx.x == 0) tile_k = g.nz > 1 ? -1 : 0;
     __syncthreads();
   }
-  unsigned long long* dst = TILE ? tile : Q;
   unsigned int out = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+  // one contiguous chunk per block (a sigma-sorted bunch keeps a block in one slice)
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t p_end = min(n, (int64_t)(blockIdx.x + 1) * chunk);
+  for (int64_t p = (int64_t)blockIdx.x * chunk + threadIdx.x; p < p_end; p += blockDim.x) {
     double fx, fy;
-    const int cell = locate(g, __ldg(x + p), __ldg(y + p), fx, fy);
-    if (cell >= 0)
-      deposit4(dst, g.nx, cell, fx, fy);
-    else
+    const int cell = locate(g, __ldg(x + p), __ldg(y + p), __ldg(sg + p), fx, fy);
+    if (cell < 0)
       ++out;
+    else if (TILE)
+      deposit_tiled(tile, &tile_k, Q, g, cell, fx, fy);
+    else
+      deposit4(Q, g.nx, cell, fx, fy);
   }
   count_out(out, n_out);
   if (TILE) {
     __syncthreads();
-    tile_flush(tile, Q, cells);
+    if (tile_k >= 0) tile_flush(tile, Q + (size_t)tile_k * cells, cells);
   }
 }
 
@@ -48,9 +54,9 @@ sc_status launch_deposit(sc_grid* g, const sc_particles* p) {
   const int64_t need = (p->n + kDepThreads - 1) / kDepThreads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
   if (tile)
-    deposit_kernel<true><<<blocks, kDepThreads, smem, g->stream>>>(p->x, p->y, p->n, g->geom, g->Q, g->n_out);
+    deposit_kernel<true><<<blocks, kDepThreads, smem, g->stream>>>(p->x, p->y, p->sigma, p->n, g->geom, g->Q, g->n_out);
   else
-    deposit_kernel<false><<<blocks, kDepThreads, 0, g->stream>>>(p->x, p->y, p->n, g->geom, g->Q, g->n_out);
+    deposit_kernel<false><<<blocks, kDepThreads, 0, g->stream>>>(p->x, p->y, p->sigma, p->n, g->geom, g->Q, g->n_out);
   SC_CUDA(cudaGetLastError());
   return SC_OK;
 }

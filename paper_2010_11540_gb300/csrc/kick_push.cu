@@ -29,23 +29,29 @@ constexpr int kp_max_threads() {
 template <bool TILE, bool CACHE, bool F32>
 __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
+  __shared__ int tile_k;  // slice held by the tile (-1: not yet claimed)
   const int cells = P.gd.nx * P.gd.ny;
-  if (TILE) tile_zero(tile, cells);
+  if (TILE) {
+    tile_zero(tile, cells);
+    if (threadIdx.x == 0) tile_k = P.gd.nz > 1 ? -1 : 0;
+  }
   pdl_wait();  // fields, charge grid and particles of the previous kernels
   if (TILE) __syncthreads();
-  unsigned long long* dst = TILE ? tile : P.Q;
   const int psc_mode = P.psc ? P.psc_mode : 0;
   const size_t n = (size_t)P.n;
   unsigned int out = 0;
   // Traversal (measured on the c2 workload): the float32-field variant gives
   // each block one contiguous, equal chunk (every SM finishes together); the
   // float64-field variant, whose plan arrays take more of L2, sweeps all
-  // blocks over a common window (grid stride).  Consecutive threads take
-  // consecutive particles either way.
-  const int64_t chunk = F32 ? (P.n + gridDim.x - 1) / gridDim.x : 0;
-  const int64_t p_begin = F32 ? (int64_t)blockIdx.x * chunk : (int64_t)blockIdx.x * blockDim.x;
-  const int64_t p_end = F32 ? min(P.n, (int64_t)(blockIdx.x + 1) * chunk) : P.n;
-  const int64_t p_step = F32 ? (int64_t)blockDim.x : (int64_t)gridDim.x * blockDim.x;
+  // blocks over a common window (grid stride);
+  // consecutive threads take consecutive particles either way.  Sliced grids
+  // always use chunks, so that a block's particles (sorted by sigma) stay in
+  // the slice its tile holds.
+  const bool chunked = F32 || P.gd.nz > 1;
+  const int64_t chunk = chunked ? (P.n + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t p_begin = chunked ? (int64_t)blockIdx.x * chunk : (int64_t)blockIdx.x * blockDim.x;
+  const int64_t p_end = chunked ? min(P.n, (int64_t)(blockIdx.x + 1) * chunk) : P.n;
+  const int64_t p_step = chunked ? (int64_t)blockDim.x : (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = p_begin + threadIdx.x; p < p_end; p += p_step) {
     State s{P.x[p], P.px[p], P.y[p], P.py[p], P.sg[p], P.ps[p]};
     if (P.do_kick) {
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
           fy = (float)a.y * (1.0f / 1048576.0f);
         } else {
           double dx, dy;
-          cell = locate(P.gk, s.x, s.y, dx, dy);
+          cell = locate(P.gk, s.x, s.y, s.sg, dx, dy);
           fx = (float)dx;
           fy = (float)dy;
         }
@@ -80,7 +86,7 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
           fx = f.x;
           fy = f.y;
         } else {
-          cell = locate(P.gk, s.x, s.y, fx, fy);
+          cell = locate(P.gk, s.x, s.y, s.sg, fx, fy);
         }
         if (cell >= 0) {
           const double2* e = P.E + cell;
@@ -117,10 +123,10 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
     }
     if (P.do_deposit) {
       double fx, fy;
-      const int cell = locate(P.gd, s.x, s.y, fx, fy);
+      const int cell = locate(P.gd, s.x, s.y, s.sg, fx, fy);
       int2 a = make_int2(0, 0);
       if (cell >= 0)
-        a = deposit4(dst, P.gd.nx, cell, fx, fy);
+        a = TILE ? deposit_tiled(tile, &tile_k, P.Q, P.gd, cell, fx, fy) : deposit4(P.Q, P.gd.nx, cell, fx, fy);
       else
         ++out;
       if (CACHE) {
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
     count_out(out, P.n_out);
     if (TILE) {
       __syncthreads();
-      tile_flush(tile, P.Q, cells);
+      if (tile_k >= 0) tile_flush(tile, P.Q + (size_t)tile_k * cells, cells);
     }
   }
 }

@@ -56,6 +56,10 @@ struct GridGeom {
   int nx, ny;
   double xmin, ymin, inv_hx, inv_hy;
   double xlast, ylast;  // (double)(nx-1), (double)(ny-1): exclusive upper bounds of xi, eta
+  // longitudinal slices (nz == 1: none): slice k = floor((sigma - zmin) * inv_dz), 0 <= k < nz;
+  // cell indices then carry the slice offset k * nx * ny
+  int nz;
+  double zmin, inv_dz;
 };
 
 // Element compiled for the kernels: the user's sc_element plus per-element
@@ -127,7 +131,8 @@ struct TrackPlan;  // captured turn graph (api.cu)
 }  // namespace sc
 
 struct sc_grid {
-  int nx, ny, precision;
+  int nx, ny, nz, precision;   // nz: longitudinal slices, each with its own nx x ny grid
+  double zmin, zmax;
   double xmin, xmax, ymin, ymax, hx, hy;
   sc::GridGeom geom;
   cudaStream_t stream;

@@ -52,9 +52,12 @@ __global__ void fft64_rows_fwd(const unsigned long long* __restrict__ Q, int nx,
                                double2* __restrict__ F1, const double2* __restrict__ twx) {
   extern __shared__ double2 sm[];
   const int Mx = 2 * nx, j = blockIdx.x, t = threadIdx.x;
+  // slice blockIdx.y: its charge grid and its row transforms
+  Q += (size_t)blockIdx.y * gridDim.x * nx;
+  F1 += (size_t)blockIdx.y * gridDim.x * (nx + 1);
   double2 *a = sm, *b = sm + Mx;
   pdl_wait();
-  a[t] = make_double2((double)(long long)Q[(size_t)j * nx + t] * scale, 0.0);
+  a[t] = make_double2((double)Q[(size_t)j * nx + t] * scale, 0.0);
   a[t + nx] = make_double2(0.0, 0.0);
   __syncthreads();
   const double2* r = fft_smem<false>(a, b, Mx, twx);
@@ -68,9 +71,17 @@ __global__ void fft64_columns(const double2* __restrict__ F1, int nx, int ny, co
   extern __shared__ double2 sm[];
   const int My = 2 * ny, p = blockIdx.x, t = threadIdx.x;
   double2 *A = sm, *B = sm + My, *C = sm + 2 * My, *D = sm + 3 * My;
+  const size_t so = (size_t)blockIdx.y * ny * (nx + 1);  // slice blockIdx.y
+  F1 += so;
+  Hx += so;
+  Hy += so;
   pdl_wait();
-  if (Qzero)  // the row transform has read the charge: clear it for the next deposit
-    for (int c = blockIdx.x * blockDim.x + t; c < nx * ny; c += gridDim.x * blockDim.x) Qzero[c] = 0ull;
+  if (Qzero) {  // the row transform has read every slice's charge: clear it for the next deposit
+    const int64_t total = (int64_t)gridDim.y * nx * ny;
+    for (int64_t c = ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + t; c < total;
+         c += (int64_t)gridDim.x * gridDim.y * blockDim.x)
+      Qzero[c] = 0ull;
+  }
   A[t] = F1[(size_t)t * (nx + 1) + p];
   A[t + ny] = make_double2(0.0, 0.0);
   __syncthreads();
@@ -95,8 +106,10 @@ __global__ void fft64_rows_inv(const double2* __restrict__ Hx, const double2* __
   extern __shared__ double2 sm[];
   const int Mx = 2 * nx, j = blockIdx.x, t = threadIdx.x;
   double2 *A = sm, *B = sm + Mx, *C = sm + 2 * Mx, *D = sm + 3 * Mx;
-  const double2* hx = Hx + (size_t)j * (nx + 1);
-  const double2* hy = Hy + (size_t)j * (nx + 1);
+  const size_t so = (size_t)blockIdx.y * gridDim.x * (nx + 1);  // slice blockIdx.y
+  E += (size_t)blockIdx.y * gridDim.x * nx;
+  const double2* hx = Hx + so + (size_t)j * (nx + 1);
+  const double2* hy = Hy + so + (size_t)j * (nx + 1);
   pdl_wait();
   // p = t (<= nx) straight from the half spectrum; p = t + nx from Hermitian symmetry
   A[t] = hx[t];
@@ -210,7 +223,7 @@ sc_status fft64_create(sc_grid* g) {
       Sy[(size_t)k * (nx + 1) + p] = cy[(size_t)k * Mx + p].imag();
     }
   const auto twx = twiddles(Mx), twy = twiddles(My);
-  const size_t half = (size_t)ny * (nx + 1) * sizeof(double2);
+  const size_t half = (size_t)g->nz * ny * (nx + 1) * sizeof(double2);  // one set per slice
   if (cudaMalloc(&f.twx, twx.size() * sizeof(double2)) != cudaSuccess ||
       cudaMalloc(&f.twy, twy.size() * sizeof(double2)) != cudaSuccess || cudaMalloc(&f.F1, half) != cudaSuccess ||
       cudaMalloc(&f.Hx, half) != cudaSuccess || cudaMalloc(&f.Hy, half) != cudaSuccess ||
@@ -247,12 +260,13 @@ sc_status fft64_solve(sc_grid* g, bool zero_q) {
   const int nx = g->nx, ny = g->ny, Mx = 2 * nx, My = 2 * ny;
   Fft64Plan& f = g->fft;
   const double scale = 1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1);
-  SC_CUDA(launch_pdl(fft64_rows_fwd, dim3(ny), dim3(nx), 2 * Mx * sizeof(double2), g->stream,
+  const unsigned nz = (unsigned)g->nz;
+  SC_CUDA(launch_pdl(fft64_rows_fwd, dim3(ny, nz), dim3(nx), 2 * Mx * sizeof(double2), g->stream,
                      (const unsigned long long*)g->Q, nx, scale, f.F1, (const double2*)f.twx));
-  SC_CUDA(launch_pdl(fft64_columns, dim3(nx + 1), dim3(ny), 4 * My * sizeof(double2), g->stream,
+  SC_CUDA(launch_pdl(fft64_columns, dim3(nx + 1, nz), dim3(ny), 4 * My * sizeof(double2), g->stream,
                      (const double2*)f.F1, nx, ny, (const double*)f.Sx, (const double*)f.Sy, f.Hx, f.Hy,
                      (const double2*)f.twy, zero_q ? g->Q : (unsigned long long*)nullptr));
-  SC_CUDA(launch_pdl(fft64_rows_inv, dim3(ny), dim3(nx), 4 * Mx * sizeof(double2), g->stream, (const double2*)f.Hx,
+  SC_CUDA(launch_pdl(fft64_rows_inv, dim3(ny, nz), dim3(nx), 4 * Mx * sizeof(double2), g->stream, (const double2*)f.Hx,
                      (const double2*)f.Hy, nx, 1.0 / ((double)Mx * (double)My), g->E, (const double2*)f.twx));
   return SC_OK;
 }

@@ -154,6 +154,10 @@ struct GemmArgs {
   const float *Sx, *Sy;    // P2A: spectra [Npad][My]
   float2* E;               // P3: fields, float32 (Ex, Ey) per node
   int* err;                // set to 1 when a bounded wait ran out
+  // longitudinal slices (blockIdx.y): rows per slice of the data operands and
+  // elements per slice of the inputs / outputs
+  int a_slice_rows, b_slice_rows;
+  long long out_slice, q_slice, e_slice;
 };
 
 // Which operand is a constant DFT matrix (loadable before the grid dependency
@@ -199,6 +203,9 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   const int tile = blockIdx.x / SK;
   const int mb = tile / g.n_tiles, nb = tile % g.n_tiles;
   const int n0 = nb * NT, a_row = mb * TM;
+  const int slice = blockIdx.y;
+  const int a_row_g = a_row + slice * g.a_slice_rows;  // row of the (stacked) A tensor
+  const int n0_g = n0 + slice * g.b_slice_rows;        // row of the (stacked) B tensor
   unsigned char* stage_base = smem;
   unsigned char* resident = smem + L::STAGES * L::STAGE;
   const int kpc = g.k_chunks / SK, kc0 = rank * kpc;  // this CTA's K chunks: kc0 .. kc0+kpc-1
@@ -206,13 +213,13 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 
   auto load_a = [&](int lk, int st) {
     unsigned char* sb = stage_base + st * L::STAGE;
-    tma_load_2d(sb, &g.tA_hi, &full_bar[st], (kc0 + lk) * KC, a_row);
-    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], (kc0 + lk) * KC, a_row);
+    tma_load_2d(sb, &g.tA_hi, &full_bar[st], (kc0 + lk) * KC, a_row_g);
+    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], (kc0 + lk) * KC, a_row_g);
   };
   auto load_b = [&](int lk, int st) {
     unsigned char* bb = stage_base + st * L::STAGE + 2 * L::A_TILE;
-    tma_load_2d(bb, &g.tB_hi, &full_bar[st], (kc0 + lk) * KC, n0);
-    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], (kc0 + lk) * KC, n0);
+    tma_load_2d(bb, &g.tB_hi, &full_bar[st], (kc0 + lk) * KC, n0_g);
+    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], (kc0 + lk) * KC, n0_g);
   };
 
   if (threadIdx.x == 0) {
@@ -249,14 +256,16 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   pdl_wait();
   if (PH == P2A && g.Qzero) {
     // every reader of the charge (the row transform) has finished: clear it for the next deposit
-    for (int c = blockIdx.x * kThreads + threadIdx.x; c < g.qcells; c += gridDim.x * kThreads) g.Qzero[c] = 0ull;
+    for (long long c = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * kThreads + threadIdx.x; c < g.qcells;
+         c += (long long)gridDim.x * gridDim.y * kThreads)
+      g.Qzero[c] = 0ull;
   }
   if (PH == P1) {
     // B operand = normalised charge rows j = n0 .. n0+NT-1, all K = nx, split hi/lo, swizzled.
     // 16-byte loads, all issued before any is used.
     constexpr int PER2 = NT * 256 / 2 / kThreads;  // pairs per thread for nx <= 256
     const int pairs = NT * g.nx / 2;
-    const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx);
+    const longlong2* q2 = (const longlong2*)(g.Q + slice * g.q_slice + (size_t)n0 * g.nx);
     longlong2 v[PER2];
 #pragma unroll
     for (int u = 0; u < PER2; ++u) {
@@ -269,10 +278,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       if (e < pairs) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const long long qi = h ? v[u].y : v[u].x;
+          const unsigned long long qi = (unsigned long long)(h ? v[u].y : v[u].x);
           const int el = 2 * e + h, r = el / g.nx, i = el % g.nx;
-          // int64 -> float through its 32-bit halves (no FP64 instruction)
-          const float qv = fmaf(__int2float_rn((int)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * g.scale;
+          // uint64 -> float through its 32-bit halves (no FP64 instruction)
+          const float qv =
+              fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * g.scale;
           float hi, lo;
           split(qv, hi, lo);
           const int kc = i / KC, k = i % KC;
@@ -381,8 +391,9 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       // row c of R1T: Re F1(j, p = c) for c <= nx, Im F1(j, p = c - nx) above
       const int p = (r <= g.nx) ? r : r - g.nx;
       const int half = (r <= g.nx) ? 0 : 1;
-      float4* dh = (float4*)(g.out_hi + (size_t)p * g.out_ld + half * g.ny + n0 + c0);
-      float4* dl = (float4*)(g.out_lo + (size_t)p * g.out_ld + half * g.ny + n0 + c0);
+      const size_t ob = slice * g.out_slice + (size_t)p * g.out_ld + half * g.ny + n0 + c0;
+      float4* dh = (float4*)(g.out_hi + ob);
+      float4* dl = (float4*)(g.out_lo + ob);
 #pragma unroll
       for (int q4 = 0; q4 < CW / 4; ++q4) {
         float h[4], l[4];
@@ -409,7 +420,8 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       for (int cc = 0; cc < CW; ++cc) {
         const int p = n0 + c0 + cc;
         const float f = sgn * acc[c0 + cc];
-        const size_t rx = (size_t)p * g.out_ld + col, ry = (size_t)(g.Npad + p) * g.out_ld + col;
+        const size_t rx = slice * g.out_slice + (size_t)p * g.out_ld + col;
+        const size_t ry = slice * g.out_slice + (size_t)(g.Npad + p) * g.out_ld + col;
         split(sx[cc] * f, g.out_hi[rx], g.out_lo[rx]);
         split(sy[cc] * f, g.out_hi[ry], g.out_lo[ry]);
       }
@@ -417,7 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       // row r: part (Re G, Im G) = r / ny at j' = r % ny; columns n = f*Npad + p
       const int part = r / g.ny, jr = r % g.ny;
       const int f = n0 / g.Npad, p0 = n0 % g.Npad;  // NT divides Npad: one field per tile
-      const size_t o = (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p0 + c0;
+      const size_t o = slice * g.out_slice + (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p0 + c0;
       float4* dh = (float4*)(g.out_hi + o);
       float4* dl = (float4*)(g.out_lo + o);
 #pragma unroll
@@ -431,7 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     } else {
       // row r: field f = r / ny (Ex, Ey) at j = r % ny; columns i = n0 + cc; float32 (Ex, Ey) pairs
       const int f = r / g.ny, j = r % g.ny;
-      float* e = (float*)g.E + 2 * ((size_t)j * g.nx + n0) + f;
+      float* e = (float*)g.E + 2 * (slice * g.e_slice + (size_t)j * g.nx + n0) + f;
 #pragma unroll
       for (int cc = c0; cc < c0 + CW; ++cc) e[2 * cc] = acc[cc];
     }
@@ -551,9 +563,9 @@ sc_status set_smem_attr() {
 
 // tiles x SK CTAs, clusters of SK along x, programmatic dependent launch.
 template <int PH, int SK>
-cudaError_t launch_phase(int tiles, const GemmArgs& a, cudaStream_t s) {
+cudaError_t launch_phase(int tiles, int slices, const GemmArgs& a, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(tiles * SK);
+  cfg.gridDim = dim3(tiles * SK, slices);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = Smem<PH>::BYTES;
   cfg.stream = s;
@@ -593,7 +605,7 @@ void host_fft(std::complex<double>* a, int n, int stride) {
 }  // namespace
 
 sc_status tf32_create(sc_grid* g) {
-  const int nx = g->nx, ny = g->ny;
+  const int nx = g->nx, ny = g->ny, nz = g->nz;
   if (nx != ny || (nx != 128 && nx != 256))
     return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_TF32X3 needs nx = ny in {128, 256}");
   sc_status st = get_encoder();
@@ -663,8 +675,8 @@ sc_status tf32_create(sc_grid* g) {
 
   if ((st = upload(T->B1, B1, 2 * nx, nx)) || (st = upload(T->W2f, W2f, 2 * My, 2 * ny)) ||
       (st = upload(T->W2i, W2i, 2 * ny, 2 * My)) || (st = upload(T->B4, B4, nx, K3)) ||
-      (st = alloc_zero(T->B2, Npad, 2 * ny)) || (st = alloc_zero(T->B3, 2 * Npad, 2 * My)) ||
-      (st = alloc_zero(T->A3, 2 * ny, K3)))
+      (st = alloc_zero(T->B2, nz * Npad, 2 * ny)) || (st = alloc_zero(T->B3, nz * 2 * Npad, 2 * My)) ||
+      (st = alloc_zero(T->A3, nz * 2 * ny, K3)))
     return st;
   SC_CUDA(cudaMalloc(&T->Sx, Sx.size() * 4));
   SC_CUDA(cudaMalloc(&T->Sy, Sy.size() * 4));
@@ -680,6 +692,8 @@ sc_status tf32_create(sc_grid* g) {
     a.My = My;
     a.Npad = Npad;
     a.err = T->err;
+    a.q_slice = (long long)nx * ny;
+    a.e_slice = (long long)nx * ny;
   };
   // P1: C[c][j] = B1 q^T: M = 2nx (c), N = ny (j), K = nx
   base(T->a1);
@@ -691,43 +705,50 @@ sc_status tf32_create(sc_grid* g) {
   T->a1.out_hi = T->B2.hi;
   T->a1.out_lo = T->B2.lo;
   T->a1.out_ld = 2 * ny;
+  T->a1.out_slice = (long long)Npad * 2 * ny;
   T->grid1 = (2 * nx / TM) * T->a1.n_tiles;
   // P2A: C[r][p] = W2f B2^T: M = 2My as (Re, Im) pairs of 128 rows, N = Npad, K = 2ny
   base(T->a2a);
   if ((st = make_map(&T->a2a.tA_hi, T->W2f.hi, 2 * My, 2 * ny, TM)) ||
       (st = make_map(&T->a2a.tA_lo, T->W2f.lo, 2 * My, 2 * ny, TM)) ||
-      (st = make_map(&T->a2a.tB_hi, T->B2.hi, Npad, 2 * ny, NT)) ||
-      (st = make_map(&T->a2a.tB_lo, T->B2.lo, Npad, 2 * ny, NT)))
+      (st = make_map(&T->a2a.tB_hi, T->B2.hi, nz * Npad, 2 * ny, NT)) ||
+      (st = make_map(&T->a2a.tB_lo, T->B2.lo, nz * Npad, 2 * ny, NT)))
     return st;
   T->a2a.k_chunks = 2 * ny / KC;
   T->a2a.n_tiles = Npad / NT;
   T->a2a.Qzero = nullptr;
-  T->a2a.qcells = nx * ny;
+  T->a2a.qcells = nz * nx * ny;
   T->a2a.Sx = T->Sx;
   T->a2a.Sy = T->Sy;
   T->a2a.out_hi = T->B3.hi;
   T->a2a.out_lo = T->B3.lo;
   T->a2a.out_ld = 2 * My;
+  T->a2a.b_slice_rows = Npad;
+  T->a2a.out_slice = (long long)2 * Npad * 2 * My;
   T->grid2a = (2 * My / TM) * T->a2a.n_tiles;
   // P2B: C[r][(f,p)] = W2i B3^T: M = 2ny as (Re, Im) pairs, N = 2 Npad, K = 2My
   base(T->a2b);
   if ((st = make_map(&T->a2b.tA_hi, T->W2i.hi, 2 * ny, 2 * My, TM)) ||
       (st = make_map(&T->a2b.tA_lo, T->W2i.lo, 2 * ny, 2 * My, TM)) ||
-      (st = make_map(&T->a2b.tB_hi, T->B3.hi, 2 * Npad, 2 * My, NT)) ||
-      (st = make_map(&T->a2b.tB_lo, T->B3.lo, 2 * Npad, 2 * My, NT)))
+      (st = make_map(&T->a2b.tB_hi, T->B3.hi, nz * 2 * Npad, 2 * My, NT)) ||
+      (st = make_map(&T->a2b.tB_lo, T->B3.lo, nz * 2 * Npad, 2 * My, NT)))
     return st;
   T->a2b.k_chunks = 2 * My / KC;
   T->a2b.n_tiles = 2 * Npad / NT;
   T->a2b.out_hi = T->A3.hi;
   T->a2b.out_lo = T->A3.lo;
   T->a2b.out_ld = K3;
+  T->a2b.b_slice_rows = 2 * Npad;
+  T->a2b.out_slice = (long long)2 * ny * K3;
   T->grid2b = (2 * ny / TM) * T->a2b.n_tiles;
   // P3: C[(f,j)][i] = A3 B4^T: M = 2ny as (Ex, Ey) pairs, N = nx, K = 2 Npad
   base(T->a3);
-  if ((st = make_map(&T->a3.tA_hi, T->A3.hi, 2 * ny, K3, TM)) || (st = make_map(&T->a3.tA_lo, T->A3.lo, 2 * ny, K3, TM)) ||
+  if ((st = make_map(&T->a3.tA_hi, T->A3.hi, nz * 2 * ny, K3, TM)) ||
+      (st = make_map(&T->a3.tA_lo, T->A3.lo, nz * 2 * ny, K3, TM)) ||
       (st = make_map(&T->a3.tB_hi, T->B4.hi, nx, K3, NT)) || (st = make_map(&T->a3.tB_lo, T->B4.lo, nx, K3, NT)))
     return st;
   T->a3.k_chunks = K3 / KC;
+  T->a3.a_slice_rows = 2 * ny;
   T->a3.n_tiles = nx / NT;
   T->a3.E = (float2*)g->E;
   T->grid3 = (2 * ny / TM) * T->a3.n_tiles;
@@ -759,10 +780,10 @@ sc_status tf32_solve(sc_grid* g, bool zero_q) {
   if (!T) return set_error(SC_ERR_ARG, "grid has no TF32 solver");
   T->a1.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
   T->a2a.Qzero = zero_q ? g->Q : nullptr;
-  SC_CUDA((launch_phase<P1, SK1>(T->grid1, T->a1, g->stream)));
-  SC_CUDA((launch_phase<P2A, SK2A>(T->grid2a, T->a2a, g->stream)));
-  SC_CUDA((launch_phase<P2B, SK2B>(T->grid2b, T->a2b, g->stream)));
-  SC_CUDA((launch_phase<P3, SK3>(T->grid3, T->a3, g->stream)));
+  SC_CUDA((launch_phase<P1, SK1>(T->grid1, g->nz, T->a1, g->stream)));
+  SC_CUDA((launch_phase<P2A, SK2A>(T->grid2a, g->nz, T->a2a, g->stream)));
+  SC_CUDA((launch_phase<P2B, SK2B>(T->grid2b, g->nz, T->a2b, g->stream)));
+  SC_CUDA((launch_phase<P3, SK3>(T->grid3, g->nz, T->a3, g->stream)));
   return SC_OK;
 }
 

@@ -24,7 +24,7 @@ SC_OK = 0
 ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVERFLOW",
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
 PRECISION = {"fp64": 0, "tf32x3": 1}
-EXPORTS = ("sc_create_grid", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
+EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
            "sc_moments_noalloc",
            "sc_last_error")
@@ -60,6 +60,9 @@ def load():
     vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
     L.sc_create_grid.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    L.sc_create_grid_sliced.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     L.sc_destroy_grid.argtypes = [vp]
     L.sc_deposit.argtypes = [vp, ctypes.POINTER(Particles)]
     L.sc_solve.argtypes = [vp]
@@ -98,13 +101,20 @@ def _stream_handle(stream):
 class Grid:
     """An sc_grid: nx x ny nodes over [xmin, xmax] x [ymin, ymax] with its solver."""
 
-    def __init__(self, nx, ny, xmin, xmax, ymin, ymax, precision="fp64", stream=None):
+    def __init__(self, nx, ny, xmin, xmax, ymin, ymax, precision="fp64", stream=None, slices=None):
+        """slices = (n_slices, zmin, zmax) for a longitudinally sliced grid."""
         self.nx, self.ny = int(nx), int(ny)
         self.extent = (float(xmin), float(xmax), float(ymin), float(ymax))
         self.precision = precision
+        self.nz = 1 if slices is None else int(slices[0])
         h = ctypes.c_void_p()
-        _check(load().sc_create_grid(ctypes.byref(h), self.nx, self.ny, *self.extent, PRECISION[precision],
-                                     _stream_handle(stream)))
+        if slices is None:
+            _check(load().sc_create_grid(ctypes.byref(h), self.nx, self.ny, *self.extent, PRECISION[precision],
+                                         _stream_handle(stream)))
+        else:
+            _check(load().sc_create_grid_sliced(ctypes.byref(h), self.nx, self.ny, *self.extent, self.nz,
+                                                float(slices[1]), float(slices[2]), PRECISION[precision],
+                                                _stream_handle(stream)))
         self._h = h
 
     @property
@@ -123,8 +133,8 @@ class Grid:
             pass
 
 
-def create_grid(nx, ny, xmin, xmax, ymin, ymax, precision="fp64", stream=None) -> Grid:
-    return Grid(nx, ny, xmin, xmax, ymin, ymax, precision, stream)
+def create_grid(nx, ny, xmin, xmax, ymin, ymax, precision="fp64", stream=None, slices=None) -> Grid:
+    return Grid(nx, ny, xmin, xmax, ymin, ymax, precision, stream, slices)
 
 
 def particles(state) -> Particles:
@@ -179,10 +189,11 @@ def track_turns(grid: Grid, state, b: dict, lattice, n_turns: int, diag: bool = 
 
 
 def grid_read(grid: Grid):
-    """-> (Q int64 [ny, nx], Ex [ny, nx], Ey [ny, nx], n_out)"""
-    Q = np.zeros((grid.ny, grid.nx), dtype=np.int64)
-    Ex = np.zeros((grid.ny, grid.nx))
-    Ey = np.zeros((grid.ny, grid.nx))
+    """-> (Q uint64, Ex, Ey, n_out); arrays [ny, nx], or [n_slices, ny, nx] for sliced grids"""
+    shape = (grid.ny, grid.nx) if grid.nz == 1 else (grid.nz, grid.ny, grid.nx)
+    Q = np.zeros(shape, dtype=np.uint64)
+    Ex = np.zeros(shape)
+    Ey = np.zeros(shape)
     n_out = ctypes.c_int64(0)
     _check(load().sc_grid_read(grid.handle, Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data, ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
@@ -223,8 +234,8 @@ def moments_noalloc(state, out, stream=None):
 
 
 def grid_write_charge(grid: Grid, Q, n_particles: int):
-    Q = np.ascontiguousarray(Q, dtype=np.int64)
-    assert Q.shape == (grid.ny, grid.nx)
+    Q = np.ascontiguousarray(Q, dtype=np.uint64)
+    assert Q.size == grid.nz * grid.ny * grid.nx
     _check(load().sc_grid_write_charge(grid.handle, Q.ctypes.data, int(n_particles)))
 
 

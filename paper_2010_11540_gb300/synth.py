@@ -166,6 +166,11 @@ CONFIGS = {
     # 4e6 particles, 256x256, same ring
     "c3": dict(n=4000000, sig_x=4e-3, sig_y=3e-3, sig_px=2e-4, sig_py=2e-4, grid=256,
                lattice="c2", n_lambda=1e11 / 20.0, turns=100),
+    # 1e7 particles, Gaussian bunch (sigma_z = 15 m, cut at 4 sigma_z) in 32
+    # slices of its own 128x128 grid over +-4 sigma_z; n_ppb protons per bunch
+    # (scan 0.5e13 .. 2e13); sorted by sigma (the layout the sliced deposit prefers)
+    "c5": dict(n=10000000, sig_x=4e-3, sig_y=3e-3, sig_px=2e-4, sig_py=2e-4, grid=128,
+               lattice="c2", sig_z=15.0, n_slices=32, n_ppb=1.0e13, turns=500),
 }
 
 
@@ -173,14 +178,33 @@ def lattice(name):
     return {"c1": fodo_c1, "c2": ring_c2}[name]()
 
 
+def sort_by_sigma(parts):
+    order = np.argsort(parts["sigma"], kind="stable")
+    return {k: np.ascontiguousarray(v[order]) for k, v in parts.items()}
+
+
+def slices(name):
+    """(n_slices, zmin, zmax) of a sliced workload."""
+    c = CONFIGS[name]
+    return c["n_slices"], -4.0 * c["sig_z"], 4.0 * c["sig_z"]
+
+
 def workload(name, seed=12345, n=None):
-    """(particles, beam dict, grid (nx, ny, xmin, xmax, ymin, ymax), lattice table)."""
+    """(particles, beam dict, grid (nx, ny, xmin, xmax, ymin, ymax), lattice table).
+    For sliced workloads n_lambda is n_ppb / dz (a slice holding the whole bunch)."""
     c = CONFIGS[name]
     n = c["n"] if n is None else n
-    parts = gaussian_bunch(n, seed, c["sig_x"], c["sig_y"], c["sig_px"], c["sig_py"])
+    parts = gaussian_bunch(n, seed, c["sig_x"], c["sig_y"], c["sig_px"], c["sig_py"], sig_z=c.get("sig_z"))
+    if "n_slices" in c:
+        parts = sort_by_sigma(parts)
     lat = lattice(c["lattice"])
     circ = float(lat["length"].sum())
-    b = beam(n_lambda=c["n_lambda"], circumference=circ)
+    if "n_slices" in c:
+        nz, z0, z1 = slices(name)
+        n_lambda = c["n_ppb"] / ((z1 - z0) / nz)
+    else:
+        n_lambda = c["n_lambda"]
+    b = beam(n_lambda=n_lambda, circumference=circ)
     g = c["grid"]
     grid = (g, g) + grid_extent(c["sig_x"], c["sig_y"])
     return parts, b, grid, lat

@@ -44,7 +44,7 @@ def test_noalloc_moments_rejects_bad_sizes():
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
     out = torch.zeros(14, dtype=torch.float64, device="cuda")
     L = sc.load()
-    too_many = sc.Particles(*(t.data_ptr(),) * 6, (1 << 23) + 1)
+    too_many = sc.Particles(*(t.data_ptr(),) * 6, 1 << 24)
     assert L.sc_moments_noalloc(ctypes.byref(too_many), out.data_ptr(), None) == -4
     empty = sc.Particles(*(t.data_ptr(),) * 6, 0)
     assert L.sc_moments_noalloc(ctypes.byref(empty), out.data_ptr(), None) == -1
