@@ -91,7 +91,7 @@ typedef struct {
  * hx = (xmax - xmin)/(nx - 1) (same for y), with the open-boundary
  * (Hockney zero-padded) Poisson solver of the given precision.  Builds the
  * Green's-function spectra on the device (synchronous on `stream`).
- * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {128, 256}
+ * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {64, 128, 256}
  * for SC_SOLVE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
  * SC_ERR_OOM, SC_ERR_CUDA.  *out is set only on success. */
 sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
@@ -189,6 +189,61 @@ sc_status sc_trace_enable(sc_grid *g, int enable);
 /* Totals accumulated since the last read (then reset): kick/push launch time
  * and solve time in ms, and the number of kicks they cover. */
 sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
+
+/* ---- Batches of independent bunches --------------------------------------
+ * Many bunches (working points of a tune scan, bunches of a train, intensity
+ * scans), each with its own particles, beam, lattice and transverse grid,
+ * tracked together: per space-charge location one batched solve per grid
+ * class (bunches whose grids have the same nodes and extent share the solver
+ * constants and are solved by one set of launches, one stacked grid each) and
+ * ONE kick/push/deposit launch for all bunches, whose blocks are split over
+ * the bunches in proportion to their particle counts.  A whole turn of all
+ * bunches is captured as one CUDA graph.  The physics per bunch is exactly
+ * sc_track_turns on a grid of that bunch's own: each bunch's charge is
+ * normalised by its own particle count and kicked with its own N_lambda. */
+typedef struct {
+  int nx, ny; /* as sc_create_grid */
+  double xmin, xmax, ymin, ymax;
+} sc_grid_spec;
+
+typedef struct {
+  sc_particles particles;     /* caller-owned device arrays of this bunch */
+  sc_beam beam;
+  const sc_element *lattice;  /* host array, as sc_track_turns */
+  int n_elems;
+} sc_bunch;
+
+typedef struct sc_batch sc_batch; /* opaque */
+
+/* Create a batch of n_bunches grids (grids[b] is bunch b's) with the solver
+ * of the given precision on `stream` (NULL: a stream of its own).  Grids must
+ * meet sc_create_grid's rules; 1 <= n_bunches <= 4096.  Errors as
+ * sc_create_grid.  *out is set only on success. */
+sc_status sc_create_batch(sc_batch **out, const sc_grid_spec *grids, int n_bunches, int precision,
+                          void *stream);
+
+/* Release a batch (synchronises its stream).  NULL ok. */
+sc_status sc_destroy_batch(sc_batch *B);
+
+/* Track bunches[0 .. n_bunches-1] (the batch's count) n_turns turns, as
+ * sc_track_turns does for each bunch alone.  Every lattice must hold the same
+ * number of SC_MARK elements and either all or none start with one; the
+ * elements between markers may differ (different working points).  The
+ * captured turn is kept while the bunches (pointers, counts, beams, lattices)
+ * stay the same.  diag: NULL, or host [n_turns][n_bunches][14] receiving each
+ * bunch's moments at the start of every turn (layout of sc_track_turns).
+ * Errors: SC_ERR_ARG (NULL, mismatched markers), SC_ERR_OVERFLOW (a bunch over
+ * SC_MAX_PARTICLES_PER_GRID), SC_ERR_CUDA, SC_ERR_OOM. */
+sc_status sc_batch_track_turns(sc_batch *B, const sc_bunch *bunches, int n_turns, double *diag);
+
+/* Synchronous copy-out of bunch b's grid state, as sc_grid_read. */
+sc_status sc_batch_read(sc_batch *B, int b, uint64_t *Q, double *Ex, double *Ey, int64_t *n_out);
+
+/* Tracing of batched turns, as sc_trace_enable / sc_trace_read (kick/push
+ * time is the batched launch covering every bunch; solve time covers every
+ * grid class). */
+sc_status sc_batch_trace_enable(sc_batch *B, int enable);
+sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
 /* Largest particle count sc_moments_noalloc accepts (its partial sums are
  * reduced in float64 by a fixed 304-block grid; counts are bounded like a

@@ -69,6 +69,8 @@ void destroy_plan(TrackPlan* t) {
   delete t;
 }
 
+}  // namespace
+
 sc_status check_particles(const sc_particles* p) {
   if (!p) return set_error(SC_ERR_ARG, "particles is NULL");
   if (p->n < 0) return set_error(SC_ERR_ARG, "negative particle count");
@@ -96,7 +98,7 @@ sc_status check_elements(const sc_element* e, int n) {
   return SC_OK;
 }
 
-bool any_quad(const sc_element* e, int n) {
+static bool any_quad(const sc_element* e, int n) {
   for (int k = 0; k < n; ++k)
     if (e[k].type == SC_QUAD) return true;
   return false;
@@ -159,32 +161,15 @@ sc_status solve_dispatch(sc_grid* g, bool zero_q) {
   return fft64_solve(g, zero_q);
 }
 
-}  // namespace
-}  // namespace sc
-
-using namespace sc;
-
-extern "C" {
-
-sc_status sc_last_error(char* buf, size_t n) {
-  if (!buf || n == 0) return SC_ERR_ARG;
-  std::snprintf(buf, n, "%s", g_last_error.c_str());
-  return SC_OK;
-}
-
-sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
-                         int precision, void* stream) {
-  return sc_create_grid_sliced(out, nx, ny, xmin, xmax, ymin, ymax, 1, 0.0, 0.0, precision, stream);
-}
-
-sc_status sc_create_grid_sliced(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
-                                int n_slices, double zmin, double zmax, int precision, void* stream) {
+sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                      int n_slices, double zmin, double zmax, int nstack, int precision, void* stream) {
   if (!out) return set_error(SC_ERR_ARG, "out is NULL");
   if (n_slices < 1 || n_slices > 1024) return set_error(SC_ERR_ARG, "n_slices must be in 1..1024");
   if (n_slices > 1 && (!(zmax > zmin) || !std::isfinite(zmin) || !std::isfinite(zmax)))
     return set_error(SC_ERR_ARG, "slice range must be finite with zmax > zmin");
+  if (nstack < 1 || (n_slices > 1 && nstack != n_slices)) return set_error(SC_ERR_ARG, "bad stacked grid count");
   if (nx < 2 || ny < 2 || nx > 4096 || ny > 4096) return set_error(SC_ERR_ARG, "grid needs 2..4096 nodes per axis");
-  if ((int64_t)nx * ny * n_slices > (1LL << 28))  // cell indices stay 32-bit
+  if ((int64_t)nx * ny * nstack > (1LL << 28))  // cell indices stay 32-bit
     return set_error(SC_ERR_ARG, "more than 2^28 nodes over all slices");
   if (!(xmax > xmin) || !(ymax > ymin) || !std::isfinite(xmin) || !std::isfinite(xmax) || !std::isfinite(ymin) ||
       !std::isfinite(ymax))
@@ -196,6 +181,7 @@ sc_status sc_create_grid_sliced(sc_grid** out, int nx, int ny, double xmin, doub
   g->nx = nx;
   g->ny = ny;
   g->nz = n_slices;
+  g->nstack = nstack;
   g->zmin = zmin;
   g->zmax = zmax;
   g->precision = precision;
@@ -236,16 +222,16 @@ sc_status sc_create_grid_sliced(sc_grid** out, int nx, int ny, double xmin, doub
     }
     g->own_stream = true;
   }
-  const size_t cells = (size_t)nx * ny * n_slices;  // all slices
+  const size_t cells = (size_t)nx * ny * nstack;  // all stacked grids
   if ((e = cudaMalloc(&g->Q, cells * 8)) != cudaSuccess || (e = cudaMalloc(&g->E, cells * sizeof(double2))) != cudaSuccess ||
-      (e = cudaMalloc(&g->n_out, 8)) != cudaSuccess) {
+      (e = cudaMalloc(&g->n_out, 8 * (size_t)nstack)) != cudaSuccess) {
     st = cuda_error(e, "cudaMalloc(grid)");
     sc_destroy_grid(g);
     return st;
   }
   cudaMemsetAsync(g->Q, 0, cells * 8, g->stream);
   cudaMemsetAsync(g->E, 0, cells * sizeof(double2), g->stream);
-  cudaMemsetAsync(g->n_out, 0, 8, g->stream);
+  cudaMemsetAsync(g->n_out, 0, 8 * (size_t)nstack, g->stream);
   const bool tile = deposit_uses_tile(g);
   const int tile_bytes = nx * ny * 8;  // one slice
   g->dep_blocks = deposit_blocks_for(tile ? tile_bytes : 0, tile);
@@ -264,6 +250,29 @@ sc_status sc_create_grid_sliced(sc_grid** out, int nx, int ny, double xmin, doub
   return SC_OK;
 }
 
+}  // namespace sc
+
+using namespace sc;
+
+extern "C" {
+
+sc_status sc_last_error(char* buf, size_t n) {
+  if (!buf || n == 0) return SC_ERR_ARG;
+  std::snprintf(buf, n, "%s", g_last_error.c_str());
+  return SC_OK;
+}
+
+sc_status sc_create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                         int precision, void* stream) {
+  return sc_create_grid_sliced(out, nx, ny, xmin, xmax, ymin, ymax, 1, 0.0, 0.0, precision, stream);
+}
+
+sc_status sc_create_grid_sliced(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                                int n_slices, double zmin, double zmax, int precision, void* stream) {
+  return create_grid(out, nx, ny, xmin, xmax, ymin, ymax, n_slices, zmin, zmax, n_slices < 1 ? 1 : n_slices,
+                     precision, stream);
+}
+
 sc_status sc_destroy_grid(sc_grid* g) {
   if (!g) return SC_OK;
   if (g->stream) cudaStreamSynchronize(g->stream);
@@ -275,6 +284,7 @@ sc_status sc_destroy_grid(sc_grid* g) {
   cudaFree(g->Q);
   cudaFree(g->E);
   cudaFree(g->n_out);
+  cudaFree(g->stack_scale);
   cudaFree(g->el_stage);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   delete g;
@@ -285,7 +295,7 @@ sc_status sc_deposit(sc_grid* g, const sc_particles* p) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   sc_status st = check_particles(p);
   if (st) return st;
-  SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nz * 8, g->stream));
+  SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nstack * 8, g->stream));
   g->n_particles = p->n;
   if (p->n == 0) return SC_OK;
   return launch_deposit(g, p);
@@ -303,7 +313,7 @@ sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, doub
   sc_status st;
   if ((st = check_beam(b)) || (st = check_particles(p)) || (st = check_elements(elems, n_elems))) return st;
   if (next) {
-    SC_CUDA(cudaMemsetAsync(next->Q, 0, (size_t)next->nx * next->ny * next->nz * 8, g->stream));
+    SC_CUDA(cudaMemsetAsync(next->Q, 0, (size_t)next->nx * next->ny * next->nstack * 8, g->stream));
     next->n_particles = p->n;
   }
   if (p->n == 0) return SC_OK;
@@ -331,7 +341,7 @@ sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, doub
 sc_status sc_grid_read(sc_grid* g, uint64_t* Q, double* Ex, double* Ey, int64_t* n_out) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   SC_CUDA(cudaStreamSynchronize(g->stream));
-  const size_t cells = (size_t)g->nx * g->ny * g->nz;
+  const size_t cells = (size_t)g->nx * g->ny * g->nstack;
   if (Q) SC_CUDA(cudaMemcpy(Q, g->Q, cells * 8, cudaMemcpyDeviceToHost));
   if ((Ex || Ey) && g->field32) {
     std::vector<float2> E(cells);
@@ -396,7 +406,7 @@ sc_status sc_grid_write_charge(sc_grid* g, const uint64_t* Q, int64_t n_particle
   if (!g || !Q) return set_error(SC_ERR_ARG, "grid or Q is NULL");
   if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
   SC_CUDA(cudaStreamSynchronize(g->stream));
-  SC_CUDA(cudaMemcpy(g->Q, Q, (size_t)g->nx * g->ny * g->nz * 8, cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(g->Q, Q, (size_t)g->nx * g->ny * g->nstack * 8, cudaMemcpyHostToDevice));
   g->n_particles = n_particles;
   return SC_OK;
 }
@@ -481,7 +491,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     // ---- capture one turn ------------------------------------------------------
     SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     sc_status cst = SC_OK;
-    if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, g->stream);
+    if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, 14, g->stream);
     if (!cst && T->has_head) {
       KPParams P = base_params(p, b);
       P.psc = T->psc;
@@ -565,7 +575,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   g->n_particles = p->n;
   if (!T->has_head && T->n_kicks > 0) {
     // charge at the first space-charge location of the first turn
-    SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nz * 8, g->stream));
+    SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nstack * 8, g->stream));
     if ((st = launch_kick_push(T->prologue, g, g->kp_blocks, g->stream))) return st;
   } else {
     if ((st = launch_kick_push(T->prologue, nullptr, g->kp_blocks_plain, g->stream))) return st;

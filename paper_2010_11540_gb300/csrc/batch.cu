@@ -1,0 +1,519 @@
+// Batches of independent bunches: each bunch has its own particles, beam,
+// lattice (working point) and transverse grid; per space-charge location the
+// bunches' grids are solved class by class (grids with the same nodes and
+// extent are stacked and solved by one set of launches) and ONE kick/push/
+// deposit launch serves every bunch.  The per-bunch physics is that of
+// sc_track_turns (Sec. I PIC loop, Sec. IV kick, Sec. III maps).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sc_internal.cuh"
+
+namespace sc {
+namespace {
+
+// Waves of resident blocks a batched launch is cut into: more waves balance
+// bunches of uneven size better, fewer flush fewer deposit tiles.
+constexpr int kWaves = 4;
+
+struct BatchPlan {
+  std::vector<unsigned char> key;
+  int n_bunches = 0;
+  bool has_head = false, diag = false;
+  int n_kicks = 0;
+  // per bunch
+  std::vector<DevElem*> d_elems;
+  std::vector<int*> cell;
+  std::vector<double2*> frac;
+  std::vector<int2*> fix;
+  std::vector<double*> psc;
+  // launch descriptors: [launch][bunch]; launch 0 = prologue, 1 = head (if any), then one per marker
+  KPParams* d_descs = nullptr;
+  int n_launches = 0;
+  std::vector<char> launch_cache;  // CACHE flag per launch
+  int4* d_blocks = nullptr;
+  int n_blocks = 0;
+  int tile_cells = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double* partial = nullptr;
+  double** d_base = nullptr;  // [bunch]
+  int* d_turn = nullptr;      // [bunch]
+  double* d_diag = nullptr;
+  int diag_cap = 0;
+  std::vector<cudaEvent_t> ev;
+};
+
+void destroy_batch_plan(BatchPlan* t) {
+  if (!t) return;
+  if (t->exec) cudaGraphExecDestroy(t->exec);
+  if (t->graph) cudaGraphDestroy(t->graph);
+  for (auto* p : t->d_elems) cudaFree(p);
+  for (auto* p : t->cell) cudaFree(p);
+  for (auto* p : t->frac) cudaFree(p);
+  for (auto* p : t->fix) cudaFree(p);
+  for (auto* p : t->psc) cudaFree(p);
+  cudaFree(t->d_descs);
+  cudaFree(t->d_blocks);
+  cudaFree(t->partial);
+  cudaFree(t->d_base);
+  cudaFree(t->d_turn);
+  cudaFree(t->d_diag);
+  for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
+  delete t;
+}
+
+}  // namespace
+}  // namespace sc
+
+struct sc_batch {
+  int n_bunches = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<sc_grid*> cls;   // grid classes (stacked grids)
+  std::vector<int> cls_of;     // bunch -> class
+  std::vector<int> idx;        // bunch -> stacked grid within its class
+  sc::BatchPlan* plan = nullptr;
+  int trace = 0;
+  double trace_kp_ms = 0.0, trace_solve_ms = 0.0;
+  int64_t trace_kicks = 0;
+};
+
+using namespace sc;
+
+namespace {
+
+bool same_spec(const sc_grid_spec& a, const sc_grid_spec& b) {
+  return a.nx == b.nx && a.ny == b.ny && a.xmin == b.xmin && a.xmax == b.xmax && a.ymin == b.ymin && a.ymax == b.ymax;
+}
+
+size_t cells_of(const sc_grid* g) { return (size_t)g->nx * g->ny; }
+
+// Bunch b's view of its class grid: fields, charge and out-of-grid counter of
+// its own stacked grid.
+void bunch_kick(const sc_batch* B, int b, KPParams& P, double kl) {
+  const sc_grid* g = B->cls[B->cls_of[b]];
+  set_kick(P, g, kl);
+  const size_t off = (size_t)B->idx[b] * cells_of(g);
+  P.E = g->E + off;
+  P.E32 = (const float2*)g->E + off;
+}
+
+void bunch_deposit(const sc_batch* B, int b, KPParams& P) {
+  sc_grid* g = B->cls[B->cls_of[b]];
+  set_deposit(P, g);
+  P.Q = g->Q + (size_t)B->idx[b] * cells_of(g);
+  P.n_out = g->n_out + B->idx[b];
+}
+
+// Blocks of one batched launch: the smallest chunk for which the bunches'
+// chunks fit kWaves waves of resident blocks; bunch by bunch, chunk by chunk.
+std::vector<int4> partition(const std::vector<int64_t>& n, int resident) {
+  const int target = kWaves * (resident > 0 ? resident : 1);
+  int64_t total = 0;
+  for (int64_t v : n) total += v;
+  auto count = [&](int64_t chunk) {
+    int64_t c = 0;
+    for (int64_t v : n) c += (v + chunk - 1) / chunk;
+    return c;
+  };
+  int64_t lo = 1, hi = std::max<int64_t>(1, total);
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (count(mid) <= target)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  std::vector<int4> blocks;
+  for (size_t b = 0; b < n.size(); ++b) {
+    const int k = (int)((n[b] + lo - 1) / lo);
+    for (int c = 0; c < k; ++c) blocks.push_back(make_int4((int)b, c, k, 0));
+  }
+  return blocks;
+}
+
+}  // namespace
+
+extern "C" {
+
+sc_status sc_create_batch(sc_batch** out, const sc_grid_spec* grids, int n_bunches, int precision, void* stream) {
+  if (!out || !grids) return set_error(SC_ERR_ARG, "out or grids is NULL");
+  if (n_bunches < 1 || n_bunches > 4096) return set_error(SC_ERR_ARG, "n_bunches must be in 1..4096");
+  sc_batch* B = new (std::nothrow) sc_batch();
+  if (!B) return set_error(SC_ERR_OOM, "host allocation failed");
+  B->n_bunches = n_bunches;
+  B->precision = precision;
+  if (stream) {
+    B->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreate(&B->stream);
+    if (e != cudaSuccess) {
+      delete B;
+      return cuda_error(e, "cudaStreamCreate");
+    }
+    B->own_stream = true;
+  }
+  std::vector<sc_grid_spec> spec;  // per class
+  std::vector<int> count;
+  B->cls_of.resize(n_bunches);
+  B->idx.resize(n_bunches);
+  for (int b = 0; b < n_bunches; ++b) {
+    int c = 0;
+    while (c < (int)spec.size() && !same_spec(spec[c], grids[b])) ++c;
+    if (c == (int)spec.size()) {
+      spec.push_back(grids[b]);
+      count.push_back(0);
+    }
+    B->cls_of[b] = c;
+    B->idx[b] = count[c]++;
+  }
+  for (size_t c = 0; c < spec.size(); ++c) {
+    const sc_grid_spec& s = spec[c];
+    sc_grid* g = nullptr;
+    sc_status st = create_grid(&g, s.nx, s.ny, s.xmin, s.xmax, s.ymin, s.ymax, 1, 0.0, 0.0, count[c], precision,
+                               B->stream);
+    if (st == SC_OK) {
+      const size_t bytes = (size_t)count[c] * (precision == SC_SOLVE_TF32X3 ? sizeof(float) : sizeof(double));
+      cudaError_t e = cudaMalloc(&g->stack_scale, bytes);
+      if (e != cudaSuccess) {
+        sc_destroy_grid(g);
+        st = cuda_error(e, "cudaMalloc(stack_scale)");
+      }
+    }
+    if (st != SC_OK) {
+      sc_destroy_batch(B);
+      return st;
+    }
+    B->cls.push_back(g);
+  }
+  *out = B;
+  return SC_OK;
+}
+
+sc_status sc_destroy_batch(sc_batch* B) {
+  if (!B) return SC_OK;
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  destroy_batch_plan(B->plan);
+  for (sc_grid* g : B->cls) sc_destroy_grid(g);
+  if (B->own_stream) cudaStreamDestroy(B->stream);
+  delete B;
+  return SC_OK;
+}
+
+sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns, double* diag) {
+  if (!B || !bunches) return set_error(SC_ERR_ARG, "batch or bunches is NULL");
+  if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
+  const int nb = B->n_bunches;
+  sc_status st;
+  // markers of every lattice
+  std::vector<std::vector<int>> marks(nb);
+  for (int b = 0; b < nb; ++b) {
+    const sc_bunch& u = bunches[b];
+    if ((st = check_beam(&u.beam)) || (st = check_particles(&u.particles)) ||
+        (st = check_elements(u.lattice, u.n_elems)))
+      return st;
+    for (int k = 0; k < u.n_elems; ++k)
+      if (u.lattice[k].type == SC_MARK) marks[b].push_back(k);
+    const bool head = marks[b].empty() || marks[b][0] > 0;
+    const bool head0 = marks[0].empty() || marks[0][0] > 0;
+    if (marks[b].size() != marks[0].size() || head != head0)
+      return set_error(SC_ERR_ARG, "every lattice of a batch needs the same SC markers (count, and one at the start or none)");
+  }
+  if (n_turns == 0) return SC_OK;
+
+  // ---- key of the captured plan ------------------------------------------------
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* v, size_t n) {
+    const unsigned char* c = (const unsigned char*)v;
+    key.insert(key.end(), c, c + n);
+  };
+  for (int b = 0; b < nb; ++b) {
+    put(&bunches[b].particles, sizeof(sc_particles));
+    put(&bunches[b].beam, sizeof(sc_beam));
+    put(&bunches[b].n_elems, sizeof(int));
+    if (bunches[b].n_elems) put(bunches[b].lattice, (size_t)bunches[b].n_elems * sizeof(sc_element));
+  }
+  const int want_diag = diag != nullptr;
+  put(&want_diag, sizeof want_diag);
+  put(&B->trace, sizeof B->trace);
+
+  const bool f32 = B->precision == SC_SOLVE_TF32X3;
+  BatchPlan* T = B->plan;
+  if (!T || T->key != key) {
+    destroy_batch_plan(T);
+    B->plan = nullptr;
+    T = new (std::nothrow) BatchPlan();
+    if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
+    B->plan = T;
+    T->key = key;
+    T->diag = want_diag;
+    T->n_bunches = nb;
+    const int n_marks = (int)marks[0].size();
+    T->n_kicks = n_marks;
+    T->has_head = marks[0].empty() || marks[0][0] > 0;
+    T->d_elems.assign(nb, nullptr);
+    T->cell.assign(nb, nullptr);
+    T->frac.assign(nb, nullptr);
+    T->fix.assign(nb, nullptr);
+    T->psc.assign(nb, nullptr);
+    std::vector<int64_t> counts(nb);
+    for (int b = 0; b < nb; ++b) {
+      const sc_bunch& u = bunches[b];
+      const int64_t n = u.particles.n;
+      counts[b] = n;
+      std::vector<DevElem> dev(u.n_elems > 0 ? u.n_elems : 1);
+      compile_elements(u.lattice, u.n_elems, &u.beam, dev.data());
+      SC_CUDA(cudaMalloc(&T->d_elems[b], dev.size() * sizeof(DevElem)));
+      SC_CUDA(cudaMemcpy(T->d_elems[b], dev.data(), dev.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
+      const size_t m = (size_t)(n > 0 ? n : 1);
+      if (n_marks > 0) {
+        SC_CUDA(cudaMalloc(&T->cell[b], m * sizeof(int)));
+        if (f32)
+          SC_CUDA(cudaMalloc(&T->fix[b], m * sizeof(int2)));
+        else
+          SC_CUDA(cudaMalloc(&T->frac[b], m * sizeof(double2)));
+      }
+      SC_CUDA(cudaMalloc(&T->psc[b], m * 5 * sizeof(double)));
+    }
+    // per-bunch charge normalisation 2^-40 / N_b, class by class
+    for (size_t c = 0; c < B->cls.size(); ++c) {
+      sc_grid* g = B->cls[c];
+      std::vector<double> sd(g->nstack, 0.0);
+      for (int b = 0; b < nb; ++b)
+        if (B->cls_of[b] == (int)c) sd[B->idx[b]] = 1.0 / 1099511627776.0 / (double)(counts[b] > 0 ? counts[b] : 1);
+      if (f32) {
+        std::vector<float> sf(sd.begin(), sd.end());
+        SC_CUDA(cudaMemcpy(g->stack_scale, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice));
+      } else {
+        SC_CUDA(cudaMemcpy(g->stack_scale, sd.data(), sd.size() * sizeof(double), cudaMemcpyHostToDevice));
+      }
+    }
+    // blocks of the batched launch: the shared-memory tile holds the largest class grid that fits
+    int tile_cells = 0;
+    for (sc_grid* g : B->cls)
+      if (deposit_uses_tile(g)) tile_cells = std::max(tile_cells, (int)cells_of(g));
+    T->tile_cells = tile_cells;
+    const std::vector<int4> blocks = partition(counts, kick_push_batched_resident(tile_cells * 8, f32, true));
+    T->n_blocks = (int)blocks.size();
+    if (T->n_blocks > 0) {
+      SC_CUDA(cudaMalloc(&T->d_blocks, blocks.size() * sizeof(int4)));
+      SC_CUDA(cudaMemcpy(T->d_blocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    // ---- descriptors: prologue, head, one per marker ------------------------------
+    T->n_launches = 1 + (T->has_head ? 1 : 0) + n_marks;
+    std::vector<KPParams> descs((size_t)T->n_launches * nb);
+    T->launch_cache.assign(T->n_launches, 0);
+    for (int b = 0; b < nb; ++b) {
+      const sc_bunch& u = bunches[b];
+      const sc_particles* p = &u.particles;
+      const sc_beam* bm = &u.beam;
+      const std::vector<int>& mk = marks[b];
+      std::vector<double> s(u.n_elems + 1, 0.0);
+      for (int k = 0; k < u.n_elems; ++k) s[k + 1] = s[k] + u.lattice[k].length;
+      const double circ = s[u.n_elems];
+      const double K = kick_strength(bm);
+      int L = 0;
+      // prologue: the ps-dependent quantities, and the first deposit for lattices opening with a marker
+      KPParams& P0 = descs[(size_t)L * nb + b];
+      P0 = base_params(p, bm);
+      P0.psc = T->psc[b];
+      P0.psc_mode = 2;
+      if (!T->has_head && n_marks > 0) {
+        bunch_deposit(B, b, P0);
+        P0.cell = T->cell[b];
+        P0.frac = T->frac[b];
+        P0.fix = T->fix[b];
+      }
+      T->launch_cache[L] = P0.cell != nullptr;
+      ++L;
+      if (T->has_head) {
+        KPParams& P = descs[(size_t)L * nb + b];
+        P = base_params(p, bm);
+        P.psc = T->psc[b];
+        P.psc_mode = 1;
+        const int nh = mk.empty() ? u.n_elems : mk[0];
+        set_elements(P, u.lattice, nh, bm, T->d_elems[b]);
+        if (!mk.empty()) {
+          bunch_deposit(B, b, P);
+          P.cell = T->cell[b];
+          P.frac = T->frac[b];
+          P.fix = T->fix[b];
+        }
+        T->launch_cache[L] = P.cell != nullptr;
+        ++L;
+      }
+      for (int k = 0; k < n_marks; ++k, ++L) {
+        const int m = mk[k];
+        const int end = (k + 1 < n_marks) ? mk[k + 1] : u.n_elems;
+        const double prev = (k > 0) ? s[mk[k - 1]] : s[mk.back()] - circ;
+        KPParams& P = descs[(size_t)L * nb + b];
+        P = base_params(p, bm);
+        P.psc = T->psc[b];
+        P.psc_mode = 1;
+        bunch_kick(B, b, P, K * (s[m] - prev));
+        set_elements(P, u.lattice + m + 1, end - m - 1, bm, T->d_elems[b] + m + 1);
+        P.cell = T->cell[b];
+        P.frac = T->frac[b];
+        P.fix = T->fix[b];
+        if ((k + 1 < n_marks) || !T->has_head) bunch_deposit(B, b, P);
+        T->launch_cache[L] = 1;
+      }
+    }
+    SC_CUDA(cudaMalloc(&T->d_descs, descs.size() * sizeof(KPParams)));
+    SC_CUDA(cudaMemcpy(T->d_descs, descs.data(), descs.size() * sizeof(KPParams), cudaMemcpyHostToDevice));
+    if (B->trace) {
+      T->ev.resize(3 * (size_t)n_marks);
+      for (auto& e : T->ev) SC_CUDA(cudaEventCreate(&e));
+    }
+    if (want_diag) {
+      SC_CUDA(cudaMalloc(&T->partial, (size_t)moments_blocks() * 14 * sizeof(double)));
+      SC_CUDA(cudaMalloc(&T->d_base, (size_t)nb * sizeof(double*)));
+      SC_CUDA(cudaMalloc(&T->d_turn, (size_t)nb * sizeof(int)));
+    }
+    for (sc_grid* g : B->cls) g->n_particles = 1;  // normalisation comes from stack_scale
+
+    // ---- capture one turn of every bunch -----------------------------------------
+    cudaStream_t S = B->stream;
+    SC_CUDA(cudaStreamBeginCapture(S, cudaStreamCaptureModeThreadLocal));
+    sc_status cst = SC_OK;
+    for (int b = 0; !cst && want_diag && b < nb; ++b)
+      if (bunches[b].particles.n > 0)
+        cst = launch_moments(&bunches[b].particles, T->partial, moments_blocks(), T->d_base + b, T->d_turn + b,
+                             14 * nb, S);
+    int L = 1;
+    const bool any = T->n_blocks > 0;  // some bunch holds particles
+    if (T->has_head) {
+      if (!cst && any)
+        cst = launch_kick_push_batched(T->d_descs + (size_t)L * nb, T->d_blocks, T->n_blocks, T->tile_cells, f32,
+                                       T->launch_cache[L] != 0, S);
+      ++L;
+    }
+    for (int k = 0; !cst && k < n_marks; ++k, ++L) {
+      if (B->trace && cudaEventRecordWithFlags(T->ev[3 * k], S, cudaEventRecordExternal) != cudaSuccess)
+        cst = set_error(SC_ERR_CUDA, "event");
+      // every class: solve, then clear the charge for this marker's deposit
+      for (size_t c = 0; !cst && c < B->cls.size(); ++c) cst = solve_dispatch(B->cls[c], true);
+      if (!cst && B->trace && cudaEventRecordWithFlags(T->ev[3 * k + 1], S, cudaEventRecordExternal) != cudaSuccess)
+        cst = set_error(SC_ERR_CUDA, "event");
+      if (!cst && any)
+        cst = launch_kick_push_batched(T->d_descs + (size_t)L * nb, T->d_blocks, T->n_blocks, T->tile_cells, f32,
+                                       T->launch_cache[L] != 0, S);
+      if (!cst && B->trace && cudaEventRecordWithFlags(T->ev[3 * k + 2], S, cudaEventRecordExternal) != cudaSuccess)
+        cst = set_error(SC_ERR_CUDA, "event");
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(S, &graph);
+    if (cst || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      destroy_batch_plan(T);
+      B->plan = nullptr;
+      return cst ? cst : cuda_error(ce, "cudaStreamEndCapture");
+    }
+    T->graph = graph;
+    ce = cudaGraphInstantiate(&T->exec, graph, 0);
+    if (ce != cudaSuccess) {
+      destroy_batch_plan(T);
+      B->plan = nullptr;
+      return cuda_error(ce, "cudaGraphInstantiate");
+    }
+  }
+
+  // ---- run -------------------------------------------------------------------------
+  cudaStream_t S = B->stream;
+  if (T->diag) {
+    if (n_turns > T->diag_cap) {
+      SC_CUDA(cudaStreamSynchronize(S));
+      cudaFree(T->d_diag);
+      T->d_diag = nullptr;
+      SC_CUDA(cudaMalloc(&T->d_diag, (size_t)n_turns * nb * 14 * sizeof(double)));
+      T->diag_cap = n_turns;
+    }
+    std::vector<double*> base(nb);
+    for (int b = 0; b < nb; ++b) base[b] = T->d_diag + (size_t)14 * b;
+    SC_CUDA(cudaMemcpy(T->d_base, base.data(), nb * sizeof(double*), cudaMemcpyHostToDevice));
+    SC_CUDA(cudaMemsetAsync(T->d_turn, 0, nb * sizeof(int), S));
+    SC_CUDA(cudaMemsetAsync(T->d_diag, 0, (size_t)n_turns * nb * 14 * sizeof(double), S));
+  }
+  if (T->n_blocks > 0) {
+    if (!T->has_head && T->n_kicks > 0)
+      for (sc_grid* g : B->cls) SC_CUDA(cudaMemsetAsync(g->Q, 0, cells_of(g) * g->nstack * 8, S));
+    if ((st = launch_kick_push_batched(T->d_descs, T->d_blocks, T->n_blocks, T->tile_cells, f32,
+                                       T->launch_cache[0] != 0, S)))
+      return st;
+  }
+  for (int t = 0; t < n_turns; ++t) {
+    SC_CUDA(cudaGraphLaunch(T->exec, S));
+    if (!T->ev.empty()) {
+      SC_CUDA(cudaStreamSynchronize(S));
+      for (size_t k = 0; 3 * k + 2 < T->ev.size(); ++k) {
+        float a = 0.f, c = 0.f;
+        SC_CUDA(cudaEventElapsedTime(&a, T->ev[3 * k], T->ev[3 * k + 1]));
+        SC_CUDA(cudaEventElapsedTime(&c, T->ev[3 * k + 1], T->ev[3 * k + 2]));
+        B->trace_solve_ms += a;
+        B->trace_kp_ms += c;
+        B->trace_kicks += 1;
+      }
+    }
+  }
+  if (T->diag) {
+    SC_CUDA(cudaMemcpyAsync(diag, T->d_diag, (size_t)n_turns * nb * 14 * sizeof(double), cudaMemcpyDeviceToHost, S));
+    SC_CUDA(cudaStreamSynchronize(S));
+  }
+  return SC_OK;
+}
+
+sc_status sc_batch_read(sc_batch* B, int b, uint64_t* Q, double* Ex, double* Ey, int64_t* n_out) {
+  if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
+  if (b < 0 || b >= B->n_bunches) return set_error(SC_ERR_ARG, "bunch index out of range");
+  SC_CUDA(cudaStreamSynchronize(B->stream));
+  sc_grid* g = B->cls[B->cls_of[b]];
+  const size_t cells = cells_of(g), off = (size_t)B->idx[b] * cells;
+  if (Q) SC_CUDA(cudaMemcpy(Q, g->Q + off, cells * 8, cudaMemcpyDeviceToHost));
+  if ((Ex || Ey) && g->field32) {
+    std::vector<float2> E(cells);
+    SC_CUDA(cudaMemcpy(E.data(), (const float2*)g->E + off, cells * sizeof(float2), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < cells; ++c) {
+      if (Ex) Ex[c] = E[c].x;
+      if (Ey) Ey[c] = E[c].y;
+    }
+  } else if (Ex || Ey) {
+    std::vector<double2> E(cells);
+    SC_CUDA(cudaMemcpy(E.data(), g->E + off, cells * sizeof(double2), cudaMemcpyDeviceToHost));
+    for (size_t c = 0; c < cells; ++c) {
+      if (Ex) Ex[c] = E[c].x;
+      if (Ey) Ey[c] = E[c].y;
+    }
+  }
+  if (n_out) {
+    unsigned long long v = 0;
+    SC_CUDA(cudaMemcpy(&v, g->n_out + B->idx[b], 8, cudaMemcpyDeviceToHost));
+    *n_out = (int64_t)v;
+  }
+  for (sc_grid* c : B->cls)
+    if (tf32_error(c)) return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
+  return SC_OK;
+}
+
+sc_status sc_batch_trace_enable(sc_batch* B, int enable) {
+  if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
+  B->trace = enable ? 1 : 0;
+  B->trace_kp_ms = B->trace_solve_ms = 0.0;
+  B->trace_kicks = 0;
+  return SC_OK;
+}
+
+sc_status sc_batch_trace_read(sc_batch* B, double* kick_push_ms, double* solve_ms, int64_t* n_kicks) {
+  if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
+  if (kick_push_ms) *kick_push_ms = B->trace_kp_ms;
+  if (solve_ms) *solve_ms = B->trace_solve_ms;
+  if (n_kicks) *n_kicks = B->trace_kicks;
+  B->trace_kp_ms = B->trace_solve_ms = 0.0;
+  B->trace_kicks = 0;
+  return SC_OK;
+}
+
+}  // extern "C"

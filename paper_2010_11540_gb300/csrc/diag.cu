@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(kMomThreads) moments_partial(const double* __r
   }
 }
 
-// out = base_ptr[0] + 14 * (*turn): means, then central second moments; bumps *turn.
+// out = base_ptr[0] + stride * (*turn): means, then central second moments; bumps *turn.
 __global__ void moments_final(const double* __restrict__ partial, int n_blocks, int64_t n, double* const* base_ptr,
-                              int* turn) {
+                              int* turn, int stride) {
   __shared__ double tot[kNM];
   if (threadIdx.x < kNM) {
     double v = 0.0;
@@ -58,7 +58,7 @@ __global__ void moments_final(const double* __restrict__ partial, int n_blocks, 
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double* out = *base_ptr + (size_t)kNM * (*turn);
+    double* out = *base_ptr + (size_t)stride * (*turn);
     const double* m = tot;
     for (int c = 0; c < 6; ++c) out[c] = m[c];
     out[6] = m[6] - m[0] * m[0];
@@ -112,9 +112,9 @@ sc_status launch_phase_advance(const sc_particles* p, const double* twiss, doubl
 }
 
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
-                         cudaStream_t s) {
+                         int stride, cudaStream_t s) {
   moments_partial<<<n_blocks, kMomThreads, 0, s>>>(p->x, p->px, p->y, p->py, p->sigma, p->psigma, p->n, partial);
-  moments_final<<<1, 32, 0, s>>>(partial, n_blocks, p->n, base_ptr, turn);
+  moments_final<<<1, 32, 0, s>>>(partial, n_blocks, p->n, base_ptr, turn, stride);
   SC_CUDA(cudaGetLastError());
   return SC_OK;
 }

@@ -21,37 +21,20 @@ constexpr int kp_max_threads() {
   return F32 ? 768 : 640;
 }
 
-// TILE: deposit into a shared-memory tile (grid fits); CACHE: the cell cache
-// of the previous deposit is valid for the gather and is refreshed by this
+// One block's share of a space-charge location: particles p_begin, p_begin +
+// p_step, ... below p_end.  use_tile: deposit into the block's shared-memory
+// tile (zeroed by the caller), flushed at the end; CACHE: the cell cache of
+// the previous deposit is valid for the gather and is refreshed by this
 // deposit; F32: float32 fields and gather (the split-precision solve's fields
 // carry float32 accuracy; the fractions are then the deposit's own fixed-point
 // weights), else float64 fields and fractions.
-template <bool TILE, bool CACHE, bool F32>
-__global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const __grid_constant__ KPParams P) {
-  extern __shared__ unsigned long long tile[];
-  __shared__ int tile_k;  // slice held by the tile (-1: not yet claimed)
+template <bool CACHE, bool F32>
+__device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile, unsigned long long* tile,
+                                                int* tile_k, int64_t p_begin, int64_t p_end, int64_t p_step) {
   const int cells = P.gd.nx * P.gd.ny;
-  if (TILE) {
-    tile_zero(tile, cells);
-    if (threadIdx.x == 0) tile_k = P.gd.nz > 1 ? -1 : 0;
-  }
-  pdl_wait();  // fields, charge grid and particles of the previous kernels
-  if (TILE) __syncthreads();
   const int psc_mode = P.psc ? P.psc_mode : 0;
   const size_t n = (size_t)P.n;
   unsigned int out = 0;
-  // Traversal (measured on the c2 workload): the float32-field variant gives
-  // each block one contiguous, equal chunk (every SM finishes together); the
-  // float64-field variant, whose plan arrays take more of L2, sweeps all
-  // blocks over a common window (grid stride);
-  // consecutive threads take consecutive particles either way.  Sliced grids
-  // always use chunks, so that a block's particles (sorted by sigma) stay in
-  // the slice its tile holds.
-  const bool chunked = F32 || P.gd.nz > 1;
-  const int64_t chunk = chunked ? (P.n + gridDim.x - 1) / gridDim.x : 0;
-  const int64_t p_begin = chunked ? (int64_t)blockIdx.x * chunk : (int64_t)blockIdx.x * blockDim.x;
-  const int64_t p_end = chunked ? min(P.n, (int64_t)(blockIdx.x + 1) * chunk) : P.n;
-  const int64_t p_step = chunked ? (int64_t)blockDim.x : (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = p_begin + threadIdx.x; p < p_end; p += p_step) {
     State s{P.x[p], P.px[p], P.y[p], P.py[p], P.sg[p], P.ps[p]};
     if (P.do_kick) {
@@ -126,7 +109,7 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
       const int cell = locate(P.gd, s.x, s.y, s.sg, fx, fy);
       int2 a = make_int2(0, 0);
       if (cell >= 0)
-        a = TILE ? deposit_tiled(tile, &tile_k, P.Q, P.gd, cell, fx, fy) : deposit4(P.Q, P.gd.nx, cell, fx, fy);
+        a = use_tile ? deposit_tiled(tile, tile_k, P.Q, P.gd, cell, fx, fy) : deposit4(P.Q, P.gd.nx, cell, fx, fy);
       else
         ++out;
       if (CACHE) {
@@ -147,11 +130,68 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
   pdl_allow();
   if (P.do_deposit) {
     count_out(out, P.n_out);
-    if (TILE) {
+    if (use_tile) {
       __syncthreads();
-      if (tile_k >= 0) tile_flush(tile, P.Q + (size_t)tile_k * cells, cells);
+      if (*tile_k >= 0) tile_flush(tile, P.Q + (size_t)*tile_k * cells, cells);
     }
   }
+}
+
+// One grid, one location.  TILE: the deposit grid fits the shared-memory tile.
+template <bool TILE, bool CACHE, bool F32>
+__global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const __grid_constant__ KPParams P) {
+  extern __shared__ unsigned long long tile[];
+  __shared__ int tile_k;  // slice held by the tile (-1: not yet claimed)
+  if (TILE) {
+    tile_zero(tile, P.gd.nx * P.gd.ny);
+    if (threadIdx.x == 0) tile_k = P.gd.nz > 1 ? -1 : 0;
+  }
+  pdl_wait();  // fields, charge grid and particles of the previous kernels
+  if (TILE) __syncthreads();
+  // Traversal (measured on the c2 workload): the float32-field variant gives
+  // each block one contiguous, equal chunk (every SM finishes together); the
+  // float64-field variant, whose plan arrays take more of L2, sweeps all
+  // blocks over a common window (grid stride);
+  // consecutive threads take consecutive particles either way.  Sliced grids
+  // always use chunks, so that a block's particles (sorted by sigma) stay in
+  // the slice its tile holds.
+  const bool chunked = F32 || P.gd.nz > 1;
+  const int64_t chunk = chunked ? (P.n + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t p_begin = chunked ? (int64_t)blockIdx.x * chunk : (int64_t)blockIdx.x * blockDim.x;
+  const int64_t p_end = chunked ? min(P.n, (int64_t)(blockIdx.x + 1) * chunk) : P.n;
+  const int64_t p_step = chunked ? (int64_t)blockDim.x : (int64_t)gridDim.x * blockDim.x;
+  kick_push_range<CACHE, F32>(P, TILE, tile, &tile_k, p_begin, p_end, p_step);
+}
+
+// Many bunches, one location each, one launch.  Block b works for bunch
+// blocks[b].x (its descriptor descs[bunch], copied to shared memory) on the
+// contiguous chunk blocks[b].y of blocks[b].z equal chunks of that bunch.
+// The bunch's deposit uses the tile when its grid fits tile_cells.
+template <bool CACHE, bool F32>
+__global__ void __launch_bounds__(kp_max_threads<F32>())
+    kick_push_batched(const KPParams* __restrict__ descs, const int4* __restrict__ blocks, int tile_cells) {
+  extern __shared__ unsigned long long tile[];
+  __shared__ int tile_k;
+  __shared__ KPParams sP;
+  const int4 bt = blocks[blockIdx.x];
+  {
+    // the descriptor is plain data: copy it as 8-byte words
+    const unsigned long long* src = (const unsigned long long*)(descs + bt.x);
+    unsigned long long* dst = (unsigned long long*)&sP;
+    for (int w = threadIdx.x; w < (int)(sizeof(KPParams) / 8); w += blockDim.x) dst[w] = src[w];
+  }
+  __syncthreads();
+  const bool use_tile = sP.do_deposit && sP.gd.nx * sP.gd.ny <= tile_cells;
+  if (use_tile) {
+    tile_zero(tile, sP.gd.nx * sP.gd.ny);
+    if (threadIdx.x == 0) tile_k = sP.gd.nz > 1 ? -1 : 0;
+  }
+  pdl_wait();
+  __syncthreads();
+  const int64_t chunk = (sP.n + bt.z - 1) / bt.z;
+  const int64_t p_begin = (int64_t)bt.y * chunk;
+  const int64_t p_end = min(sP.n, p_begin + chunk);
+  kick_push_range<CACHE, F32>(sP, use_tile, tile, &tile_k, p_begin, p_end, blockDim.x);
 }
 
 template <bool TILE, bool CACHE, bool F32>
@@ -198,6 +238,30 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
     k = cache ? (f32 ? kick_push_kernel<false, true, true> : kick_push_kernel<false, true, false>)
               : (f32 ? kick_push_kernel<false, false, true> : kick_push_kernel<false, false, false>);
   SC_CUDA(launch_pdl(k, dim3(blocks), dim3(threads), (size_t)smem, s, P));
+  return SC_OK;
+}
+
+int kick_push_batched_threads(bool f32) { return f32 ? kp_max_threads<true>() : kp_max_threads<false>(); }
+
+int kick_push_batched_resident(int smem_bytes, bool f32, bool cache) {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  decltype(&kick_push_batched<true, true>) ks[4] = {kick_push_batched<false, false>, kick_push_batched<false, true>,
+                                                     kick_push_batched<true, false>, kick_push_batched<true, true>};
+  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  auto k = ks[(cache ? 2 : 0) + (f32 ? 1 : 0)];
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kick_push_batched_threads(f32), smem_bytes);
+  return sms * (per < 1 ? 1 : per);
+}
+
+sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
+                                   bool cache, cudaStream_t s) {
+  auto k = cache ? (f32 ? kick_push_batched<true, true> : kick_push_batched<true, false>)
+                 : (f32 ? kick_push_batched<false, true> : kick_push_batched<false, false>);
+  // (the shared-memory limit was raised by kick_push_batched_resident, called before any launch)
+  SC_CUDA(launch_pdl(k, dim3(n_blocks), dim3(kick_push_batched_threads(f32)), (size_t)tile_cells * 8, s, descs,
+                     blocks, tile_cells));
   return SC_OK;
 }
 

@@ -132,16 +132,23 @@ struct TrackPlan;  // captured turn graph (api.cu)
 
 struct sc_grid {
   int nx, ny, nz, precision;   // nz: longitudinal slices, each with its own nx x ny grid
+  // Transverse grids stored back to back and solved by one batched solve: nz
+  // for a sliced grid, the bunch count for the grid class of a batch.
+  int nstack;
+  // Per stacked grid normalisation of the charge (2^-40 / N of that grid),
+  // device float64 (FP64 form) or float32 (split form) array of nstack, or
+  // NULL: every stacked grid is normalised by n_particles.
+  void* stack_scale;
   double zmin, zmax;
   double xmin, xmax, ymin, ymax, hx, hy;
   sc::GridGeom geom;
   cudaStream_t stream;
   bool own_stream;
   int device;
-  unsigned long long* Q;      // [ny*nx] int64 charge (2^40 per particle)
-  double2* E;                 // [ny*nx] (Ex, Ey); float32 pairs in the first half when field32
+  unsigned long long* Q;      // [nstack][ny][nx] uint64 charge (2^40 per particle)
+  double2* E;                 // [nstack][ny][nx] (Ex, Ey); float32 pairs in the first half when field32
   int field32;                // the solve writes float32 fields (SC_SOLVE_TF32X3)
-  unsigned long long* n_out;  // device counter
+  unsigned long long* n_out;  // device counter (one per stacked grid in a batch class)
   int64_t n_particles;        // particle count of the last deposit (normalises Q)
   sc::Fft64Plan fft;
   sc::Tf32Plan* tf32;
@@ -164,6 +171,11 @@ sc_status launch_deposit(sc_grid* g, const sc_particles* p);
 // kick_push.cu
 // blocks: dep->kp_blocks when depositing into dep, else the kick grid's kp_blocks_plain.
 sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s);
+// Batched form: descs[bunch] per bunch, blocks[b] = (bunch, chunk, chunks of that bunch, 0) per block;
+// deposits of grids with at most tile_cells nodes go through the shared-memory tile.
+sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
+                                   bool cache, cudaStream_t s);
+int kick_push_batched_resident(int smem_bytes, bool f32, bool cache);  // resident blocks on the device
 bool deposit_uses_tile(const sc_grid* g);
 int deposit_blocks_for(int smem_bytes, bool tile);
 int kick_push_blocks_for(int smem_bytes, bool tile);
@@ -178,11 +190,27 @@ void tf32_destroy(sc_grid* g);
 sc_status tf32_solve(sc_grid* g, bool zero_q);
 int tf32_error(sc_grid* g);  // 1 when a tensor-core solve gave up on a bounded wait
 // diag.cu
+// out = *base_ptr + stride * (*turn) receives the 14 moments; bumps *turn
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,
-                         cudaStream_t s);
+                         int stride, cudaStream_t s);
 int moments_blocks();
 sc_status launch_phase_advance(const sc_particles* p, const double* twiss, double* acc, int accumulate,
                                cudaStream_t s);
+
+// api.cu helpers shared with batch.cu
+sc_status check_particles(const sc_particles* p);
+sc_status check_beam(const sc_beam* b);
+sc_status check_elements(const sc_element* e, int n);
+double kick_strength(const sc_beam* b);
+KPParams base_params(const sc_particles* p, const sc_beam* b);
+void set_kick(KPParams& P, const sc_grid* g, double kl);
+void set_deposit(KPParams& P, sc_grid* d);
+void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, const DevElem* dev);
+sc_status solve_dispatch(sc_grid* g, bool zero_q);
+// Grid construction shared by sc_create_grid_sliced and batches: nstack stacked
+// grids; n_slices > 1 slices them by sigma (then nstack == n_slices).
+sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,
+                      int n_slices, double zmin, double zmax, int nstack, int precision, void* stream);
 
 // Build the cyclic difference-kernel fields Dx, Dy on the doubled grid, float64
 // host arrays [My][Mx] (used by both solve forms).

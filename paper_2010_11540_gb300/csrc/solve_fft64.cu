@@ -49,6 +49,7 @@ __device__ double2* fft_smem(double2* a, double2* b, int M, const double2* __res
 }
 
 __global__ void fft64_rows_fwd(const unsigned long long* __restrict__ Q, int nx, double scale,
+                               const double* __restrict__ stack_scale,
                                double2* __restrict__ F1, const double2* __restrict__ twx) {
   extern __shared__ double2 sm[];
   const int Mx = 2 * nx, j = blockIdx.x, t = threadIdx.x;
@@ -57,6 +58,7 @@ __global__ void fft64_rows_fwd(const unsigned long long* __restrict__ Q, int nx,
   F1 += (size_t)blockIdx.y * gridDim.x * (nx + 1);
   double2 *a = sm, *b = sm + Mx;
   pdl_wait();
+  if (stack_scale) scale = stack_scale[blockIdx.y];  // per stacked grid (bunches of a batch)
   a[t] = make_double2((double)Q[(size_t)j * nx + t] * scale, 0.0);
   a[t + nx] = make_double2(0.0, 0.0);
   __syncthreads();
@@ -223,7 +225,7 @@ sc_status fft64_create(sc_grid* g) {
       Sy[(size_t)k * (nx + 1) + p] = cy[(size_t)k * Mx + p].imag();
     }
   const auto twx = twiddles(Mx), twy = twiddles(My);
-  const size_t half = (size_t)g->nz * ny * (nx + 1) * sizeof(double2);  // one set per slice
+  const size_t half = (size_t)g->nstack * ny * (nx + 1) * sizeof(double2);  // one set per stacked grid
   if (cudaMalloc(&f.twx, twx.size() * sizeof(double2)) != cudaSuccess ||
       cudaMalloc(&f.twy, twy.size() * sizeof(double2)) != cudaSuccess || cudaMalloc(&f.F1, half) != cudaSuccess ||
       cudaMalloc(&f.Hx, half) != cudaSuccess || cudaMalloc(&f.Hy, half) != cudaSuccess ||
@@ -260,9 +262,10 @@ sc_status fft64_solve(sc_grid* g, bool zero_q) {
   const int nx = g->nx, ny = g->ny, Mx = 2 * nx, My = 2 * ny;
   Fft64Plan& f = g->fft;
   const double scale = 1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1);
-  const unsigned nz = (unsigned)g->nz;
+  const unsigned nz = (unsigned)g->nstack;
   SC_CUDA(launch_pdl(fft64_rows_fwd, dim3(ny, nz), dim3(nx), 2 * Mx * sizeof(double2), g->stream,
-                     (const unsigned long long*)g->Q, nx, scale, f.F1, (const double2*)f.twx));
+                     (const unsigned long long*)g->Q, nx, scale, (const double*)g->stack_scale, f.F1,
+                     (const double2*)f.twx));
   SC_CUDA(launch_pdl(fft64_columns, dim3(nx + 1, nz), dim3(ny), 4 * My * sizeof(double2), g->stream,
                      (const double2*)f.F1, nx, ny, (const double*)f.Sx, (const double*)f.Sy, f.Hx, f.Hy,
                      (const double2*)f.twy, zero_q ? g->Q : (unsigned long long*)nullptr));

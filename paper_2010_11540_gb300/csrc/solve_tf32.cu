@@ -145,6 +145,7 @@ struct GemmArgs {
   // P1: charge input
   const unsigned long long* Q;
   float scale;
+  const float* stack_scale;  // per stacked grid (bunches of a batch), or NULL: scale
   // P2A: charge grid to clear for the next deposit (NULL: leave it)
   unsigned long long* Qzero;
   int qcells;
@@ -266,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     constexpr int PER2 = NT * 256 / 2 / kThreads;  // pairs per thread for nx <= 256
     const int pairs = NT * g.nx / 2;
     const longlong2* q2 = (const longlong2*)(g.Q + slice * g.q_slice + (size_t)n0 * g.nx);
+    const float qscale = g.stack_scale ? g.stack_scale[slice] : g.scale;
     longlong2 v[PER2];
 #pragma unroll
     for (int u = 0; u < PER2; ++u) {
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
           const int el = 2 * e + h, r = el / g.nx, i = el % g.nx;
           // uint64 -> float through its 32-bit halves (no FP64 instruction)
           const float qv =
-              fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * g.scale;
+              fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * qscale;
           float hi, lo;
           split(qv, hi, lo);
           const int kc = i / KC, k = i % KC;
@@ -605,9 +607,9 @@ void host_fft(std::complex<double>* a, int n, int stride) {
 }  // namespace
 
 sc_status tf32_create(sc_grid* g) {
-  const int nx = g->nx, ny = g->ny, nz = g->nz;
-  if (nx != ny || (nx != 128 && nx != 256))
-    return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_TF32X3 needs nx = ny in {128, 256}");
+  const int nx = g->nx, ny = g->ny, nz = g->nstack;
+  if (nx != ny || (nx != 64 && nx != 128 && nx != 256))
+    return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_TF32X3 needs nx = ny in {64, 128, 256}");
   sc_status st = get_encoder();
   if (st) return st;
   Tf32Plan* T = new (std::nothrow) Tf32Plan();
@@ -779,11 +781,12 @@ sc_status tf32_solve(sc_grid* g, bool zero_q) {
   Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_ARG, "grid has no TF32 solver");
   T->a1.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
+  T->a1.stack_scale = (const float*)g->stack_scale;
   T->a2a.Qzero = zero_q ? g->Q : nullptr;
-  SC_CUDA((launch_phase<P1, SK1>(T->grid1, g->nz, T->a1, g->stream)));
-  SC_CUDA((launch_phase<P2A, SK2A>(T->grid2a, g->nz, T->a2a, g->stream)));
-  SC_CUDA((launch_phase<P2B, SK2B>(T->grid2b, g->nz, T->a2b, g->stream)));
-  SC_CUDA((launch_phase<P3, SK3>(T->grid3, g->nz, T->a3, g->stream)));
+  SC_CUDA((launch_phase<P1, SK1>(T->grid1, g->nstack, T->a1, g->stream)));
+  SC_CUDA((launch_phase<P2A, SK2A>(T->grid2a, g->nstack, T->a2a, g->stream)));
+  SC_CUDA((launch_phase<P2B, SK2B>(T->grid2b, g->nstack, T->a2b, g->stream)));
+  SC_CUDA((launch_phase<P3, SK3>(T->grid3, g->nstack, T->a3, g->stream)));
   return SC_OK;
 }
 

@@ -26,7 +26,8 @@ ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVE
 PRECISION = {"fp64": 0, "tf32x3": 1}
 EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
-           "sc_moments_noalloc",
+           "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
+           "sc_batch_trace_enable", "sc_batch_trace_read",
            "sc_last_error")
 
 
@@ -44,6 +45,15 @@ class Particles(ctypes.Structure):
 
 class Beam(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("gamma0", "beta0", "n_lambda", "r_p", "circumference", "mass_ev")]
+
+
+class GridSpec(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int)] + [
+        (k, ctypes.c_double) for k in ("xmin", "xmax", "ymin", "ymax")]
+
+
+class Bunch(ctypes.Structure):
+    _fields_ = [("particles", Particles), ("beam", Beam), ("lattice", ctypes.c_void_p), ("n_elems", ctypes.c_int)]
 
 
 _lib = None
@@ -76,6 +86,12 @@ def load():
     L.sc_trace_enable.argtypes = [vp, ctypes.c_int]
     L.sc_trace_read.argtypes = [vp, dp, dp, ctypes.POINTER(i64)]
     L.sc_moments_noalloc.argtypes = [ctypes.POINTER(Particles), vp, vp]
+    L.sc_create_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(GridSpec), ctypes.c_int, ctypes.c_int, vp]
+    L.sc_destroy_batch.argtypes = [vp]
+    L.sc_batch_track_turns.argtypes = [vp, ctypes.POINTER(Bunch), ctypes.c_int, dp]
+    L.sc_batch_read.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(i64)]
+    L.sc_batch_trace_enable.argtypes = [vp, ctypes.c_int]
+    L.sc_batch_trace_read.argtypes = [vp, dp, dp, ctypes.POINTER(i64)]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -260,3 +276,77 @@ def track_turns_host(grid: Grid, host_state, b: dict, lattice, n_turns: int, dev
         dst.copy_(device_state[k], non_blocking=True)
     torch.cuda.current_stream().synchronize()
     return host_state
+
+
+# ---------------------------------------------------------------- batches of bunches
+class Batch:
+    """An sc_batch: one grid per bunch, grids = [(nx, ny, xmin, xmax, ymin, ymax), ...]."""
+
+    def __init__(self, grids, precision="fp64", stream=None):
+        self.grids = [tuple(g) for g in grids]
+        arr = (GridSpec * len(self.grids))(*[GridSpec(int(g[0]), int(g[1]), *map(float, g[2:])) for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(load().sc_create_batch(ctypes.byref(h), arr, len(self.grids), PRECISION[precision],
+                                      _stream_handle(stream)))
+        self._h = h
+        self.precision = precision
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __len__(self):
+        return len(self.grids)
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().sc_destroy_batch(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+
+def create_batch(grids, precision="fp64", stream=None) -> Batch:
+    return Batch(grids, precision, stream)
+
+
+def batch_track_turns(batch: Batch, states, beams, lattices, n_turns: int, diag: bool = False):
+    """Track every bunch n_turns turns (sc_batch_track_turns); states, beams and
+    lattices are per-bunch lists.  diag -> [n_turns, n_bunches, 14]."""
+    nb = len(batch)
+    if not (len(states) == len(beams) == len(lattices) == nb):
+        raise ValueError("one state, beam and lattice per bunch")
+    keep = []
+    arr = (Bunch * nb)()
+    for b in range(nb):
+        ptr, n, k = _elements(lattices[b])
+        keep.append(k)
+        arr[b] = Bunch(particles(states[b]), beam(beams[b]), ptr, n)
+    out = np.zeros((n_turns, nb, 14)) if diag else None
+    _check(load().sc_batch_track_turns(batch.handle, arr, int(n_turns),
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if diag else None))
+    return out
+
+
+def batch_read(batch: Batch, b: int):
+    """-> (Q uint64 [ny, nx], Ex, Ey, n_out) of bunch b's grid."""
+    nx, ny = batch.grids[b][0], batch.grids[b][1]
+    Q = np.zeros((ny, nx), dtype=np.uint64)
+    Ex = np.zeros((ny, nx))
+    Ey = np.zeros((ny, nx))
+    n_out = ctypes.c_int64(0)
+    _check(load().sc_batch_read(batch.handle, int(b), Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data,
+                                ctypes.byref(n_out)))
+    return Q, Ex, Ey, int(n_out.value)
+
+
+def batch_trace_enable(batch: Batch, enable: bool = True):
+    _check(load().sc_batch_trace_enable(batch.handle, 1 if enable else 0))
+
+
+def batch_trace_read(batch: Batch):
+    """-> (kick_push_ms, solve_ms, n_kicks) accumulated since the last read."""
+    a, c, n = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_int64(0)
+    _check(load().sc_batch_trace_read(batch.handle, ctypes.byref(a), ctypes.byref(c), ctypes.byref(n)))
+    return a.value, c.value, int(n.value)

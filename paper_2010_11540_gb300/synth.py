@@ -174,8 +174,105 @@ CONFIGS = {
 }
 
 
+# c4: 8 x 8 working points (Qx, Qy) = (22.40, 20.75) + (dqx, dqy), dqx and dqy
+# in 8 equal steps over [-0.1, 0.1] (row-major: dqx outer), as (k1F, k1D) of
+# the c2 ring; matched on the bare one-turn trace by `python -m oracle.match_ring --scan`.
+C4_WORKING_POINTS = [
+    (0.14111251691365673, -0.13528782290733868),  # (22.3000, 20.6500)
+    (0.1411244595147973, -0.1354025965324823),  # (22.3000, 20.6786)
+    (0.14113638556241373, -0.1355172960540812),  # (22.3000, 20.7071)
+    (0.14114829501187626, -0.13563192078266814),  # (22.3000, 20.7357)
+    (0.14116018781875456, -0.1357464700292751),  # (22.3000, 20.7643)
+    (0.14117206393881762, -0.13586094310543687),  # (22.3000, 20.7929)
+    (0.14118392332803284, -0.13597533932319486),  # (22.3000, 20.8214)
+    (0.14119576594256567, -0.13608965799510062),  # (22.3000, 20.8500)
+    (0.1412246072383412, -0.13530145143623215),  # (22.3286, 20.6500)
+    (0.14123650067254964, -0.13541617589794486),  # (22.3286, 20.6786)
+    (0.1412483776302314, -0.13553082633304672),  # (22.3286, 20.7071)
+    (0.14126023806689691, -0.1356454020522107),  # (22.3286, 20.7357)
+    (0.14127208193825505, -0.13575990236660795),  # (22.3286, 20.7643)
+    (0.1412839092002132, -0.1358743265879119),  # (22.3286, 20.7929)
+    (0.14129571980887634, -0.13598867402830156),  # (22.3286, 20.8214)
+    (0.1413075137205467, -0.1361029440004653),  # (22.3286, 20.8500)
+    (0.1413365793575812, -0.13531505592871587),  # (22.3571, 20.6500)
+    (0.14134842372146947, -0.1354297313236655),  # (22.3571, 20.6786)
+    (0.14136025168560162, -0.1355443327687113),  # (22.3571, 20.7071)
+    (0.1413720632056282, -0.13565885957466622),  # (22.3571, 20.7357)
+    (0.14138385823739755, -0.13577331105284113),  # (22.3571, 20.7643)
+    (0.1413956367369555, -0.13588768651504796),  # (22.3571, 20.7929)
+    (0.1414073986605448, -0.13600198527360352),  # (22.3571, 20.8214)
+    (0.14141914396460453, -0.13611620664133303),  # (22.3571, 20.8500)
+    (0.14144843261138837, -0.13532863634556808),  # (22.3857, 20.6500)
+    (0.14146022800164954, -0.13544326277050348),  # (22.3857, 20.6786)
+    (0.1414720070686985, -0.1355578153220152),  # (22.3857, 20.7071)
+    (0.14148376976832597, -0.13567229331105674),  # (22.3857, 20.7357)
+    (0.14149551605651997, -0.13578669604907845),  # (22.3857, 20.7643)
+    (0.141507245889465, -0.1359010228480311),  # (22.3857, 20.7929)
+    (0.1415189592235416, -0.13601527302036948),  # (22.3857, 20.8214)
+    (0.14153065601532586, -0.13612944587905576),  # (22.3857, 20.8500)
+    (0.1415601663405168, -0.13534219264777203),  # (22.4143, 20.6500)
+    (0.1415719128539242, -0.13545677019952196),  # (22.4143, 20.6786)
+    (0.14158364312043706, -0.13557127395410212),  # (22.4143, 20.7071)
+    (0.14159535709598642, -0.13568570322260667),  # (22.4143, 20.7357)
+    (0.14160705473670002, -0.13580005731662576),  # (22.4143, 20.7643)
+    (0.1416187359989011, -0.13591433554824886),  # (22.4143, 20.7929)
+    (0.14163040083910816, -0.13602853723006872),  # (22.4143, 20.8214)
+    (0.1416420492140344, -0.1361426616751851),  # (22.4143, 20.8500)
+    (0.1416717798864663, -0.1353557247965145),  # (22.4429, 20.6500)
+    (0.14168347761987302, -0.13547025357198722),  # (22.4429, 20.6786)
+    (0.14169515918247674, -0.1355847086263183),  # (22.4429, 20.7071)
+    (0.14170682453034938, -0.1356990892707426),  # (22.4429, 20.7357)
+    (0.14171847361975815, -0.13581339481698998),  # (22.4429, 20.7643)
+    (0.14173010640716543, -0.13592762457728902),  # (22.4429, 20.7929)
+    (0.14174172284922773, -0.13604177786437063),  # (22.4429, 20.8214)
+    (0.1417533229027955, -0.1361558539914719),  # (22.4429, 20.8500)
+    (0.14178327259148568, -0.13536923275318566),  # (22.4714, 20.6500)
+    (0.1417949216418237, -0.13548371284936822),  # (22.4714, 20.6786)
+    (0.14180655459722488, -0.13559811930021182),  # (22.4714, 20.7071)
+    (0.1418181714139017, -0.13571245141709198),  # (22.4714, 20.7357)
+    (0.14182977204826155, -0.13582670851187859),  # (22.4714, 20.7643)
+    (0.1418413564569056, -0.13594088989693928),  # (22.4714, 20.7929)
+    (0.14185292459662857, -0.13605499488514347),  # (22.4714, 20.8214)
+    (0.1418644764244185, -0.13616902278986537),  # (22.4714, 20.8500)
+    (0.14189464379857594, -0.13538271647937763),  # (22.5000, 20.6500)
+    (0.14190624426285564, -0.13549714799333532),  # (22.5000, 20.6786)
+    (0.14191782870783945, -0.13561150593753157),  # (22.5000, 20.7071)
+    (0.14192939708988075, -0.13572578962348272),  # (22.5000, 20.7357)
+    (0.14194094936552676, -0.1358399983631987),  # (22.5000, 20.7643)
+    (0.1419524854915179, -0.13595413146918653),  # (22.5000, 20.7929)
+    (0.14196400542478743, -0.1360681882544539),  # (22.5000, 20.8214)
+    (0.1419755091224605, -0.1361821680325128),  # (22.5000, 20.8500)
+]
+
+
 def lattice(name):
     return {"c1": fodo_c1, "c2": ring_c2}[name]()
+
+
+def c4_grid_size(n):
+    """Grid nodes per axis for a bunch of n macroparticles."""
+    return 64 if n < 100000 else (128 if n < 500000 else 256)
+
+
+def c4_bunches(seed=12345, n_bunches=64, n_min=1e4, n_max=2e6, scale=1.0):
+    """Batching workload: n_bunches independent bunches, counts log-uniform in
+    [n_min, n_max] (times `scale`), bunch b seeded with seed + b and tracked at
+    working point b of C4_WORKING_POINTS (cyclic); each with the c2 distribution,
+    line density and grid extent, and a grid of c4_grid_size(count) nodes.
+    -> list of (particles, beam dict, grid, lattice table)."""
+    rng = np.random.Generator(np.random.Philox(key=seed))
+    counts = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_bunches))
+    c = CONFIGS["c2"]
+    out = []
+    for b in range(n_bunches):
+        n = max(1, int(round(counts[b] * scale)))
+        parts = gaussian_bunch(n, seed + b, c["sig_x"], c["sig_y"], c["sig_px"], c["sig_py"])
+        k1f, k1d = C4_WORKING_POINTS[b % len(C4_WORKING_POINTS)]
+        lat = ring_c2(k1f=k1f, k1d=k1d)
+        bm = beam(n_lambda=c["n_lambda"], circumference=float(lat["length"].sum()))
+        g = c4_grid_size(int(round(counts[b])))
+        out.append((parts, bm, (g, g) + grid_extent(c["sig_x"], c["sig_y"]), lat))
+    return out
 
 
 def sort_by_sigma(parts):

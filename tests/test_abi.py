@@ -45,6 +45,46 @@ def test_struct_layouts():
     assert ctypes.sizeof(sc.Particles) == 56
     assert ctypes.sizeof(sc.Beam) == 48
     assert synth.ELEMENT_DTYPE.itemsize == 64
+    assert ctypes.sizeof(sc.GridSpec) == 40
+    assert ctypes.sizeof(sc.Bunch) == 120
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """sizeof / offsetof of the public structs as a C compiler sees sc.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stddef.h>
+#include <stdio.h>
+#include "sc.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sc_particles), sizeof(sc_beam), sizeof(sc_element),
+         sizeof(sc_grid_spec), sizeof(sc_bunch), offsetof(sc_bunch, beam), offsetof(sc_bunch, lattice),
+         offsetof(sc_element, length));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == [ctypes.sizeof(sc.Particles), ctypes.sizeof(sc.Beam), synth.ELEMENT_DTYPE.itemsize,
+                   ctypes.sizeof(sc.GridSpec), ctypes.sizeof(sc.Bunch), sc.Bunch.beam.offset,
+                   sc.Bunch.lattice.offset, synth.ELEMENT_DTYPE.fields["length"][1]]
+
+
+def test_batch_argument_errors_without_gpu(lib):
+    """sc_create_batch rejects bad arguments before touching the device."""
+    h = ctypes.c_void_p()
+    spec = (sc.GridSpec * 1)(sc.GridSpec(64, 64, -1.0, 1.0, -1.0, 1.0))
+    assert lib.sc_create_batch(None, spec, 1, 0, None) == -1
+    assert lib.sc_create_batch(ctypes.byref(h), spec, 0, 0, None) == -1
+    assert lib.sc_create_batch(ctypes.byref(h), None, 1, 0, None) == -1
+    assert lib.sc_batch_track_turns(None, None, 1, None) == -1
+    assert lib.sc_destroy_batch(None) == 0
 
 
 def test_last_error_without_gpu(lib):

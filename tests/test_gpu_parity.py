@@ -216,7 +216,7 @@ def test_quads_large_momentum_offsets():
 
 
 # ------------------------------------------------------------------ split-TF32 tensor-core solve
-@pytest.mark.parametrize("n", [128, 256])
+@pytest.mark.parametrize("n", [64, 128, 256])
 def test_solve_tf32_fields_within_1e5(n):
     parts = synth.gaussian_bunch(1000000, 31 + n, 4e-3, 3e-3, 1e-4, 1e-4)
     grid = (n, n, -0.02, 0.02, -0.015, 0.015)
@@ -250,9 +250,10 @@ def test_solve_tf32_point_charges():
     assert rel_l2(Ex, Exo) < 1e-5 and rel_l2(Ey, Eyo) < 1e-5, (rel_l2(Ex, Exo), rel_l2(Ey, Eyo))
 
 
-def test_tf32_unsupported_size():
+@pytest.mark.parametrize("nx,ny", [(32, 32), (512, 512), (128, 64)])
+def test_tf32_unsupported_size(nx, ny):
     with pytest.raises(sc.ScError) as e:
-        sc.create_grid(64, 64, -1.0, 1.0, -1.0, 1.0, precision="tf32x3")
+        sc.create_grid(nx, ny, -1.0, 1.0, -1.0, 1.0, precision="tf32x3")
     assert e.value.code == -7
 
 
