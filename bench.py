@@ -32,6 +32,15 @@ UNIT = "particle-kicks/s"
 WORKLOAD = ("c2: 1e6 macroparticles (4D Gaussian, sigma_x=4 mm, sigma_y=3 mm, 0.2 mrad, 4-sigma cut), "
             "128x128 grid over +-5 sigma (256x256 padded open-boundary solve), 72-cell FODO ring with "
             "2 thin-sextupole families, bare tunes (22.40, 20.75), 216 SC kicks/turn")
+WORKLOADS = {
+    "c1": "c1: 2e4 macroparticles (sigma 2 mm), 64x64 grid, 24-cell FODO ring, 48 SC kicks/turn",
+    "c2": WORKLOAD,
+    "c3": "c3: 4e6 macroparticles, 256x256 grid (512x512 padded), the c2 ring, 216 SC kicks/turn",
+    "c4": ("c4: 64 independent bunches, counts log-uniform 1e4-2e6 (2.37e7 total), grids 64^2/128^2/256^2 by "
+           "count, 8x8 working points of the c2 ring, 216 SC kicks/turn"),
+    "c5": ("c5: 1e7 macroparticles, Gaussian bunch sigma_z = 15 m cut at 4 sigma_z, sorted by sigma, 32 slices "
+           "over +-4 sigma_z each with its own 128x128 grid, 1e13 protons, the c2 ring, 216 SC kicks/turn"),
+}
 
 # FP64-pipe thread instructions per particle in kick_push_kernel (the turn
 # graph's variant), by segment content: measured with ncu
@@ -41,6 +50,8 @@ WORKLOAD = ("c2: 1e6 macroparticles (4D Gaussian, sigma_x=4 mm, sigma_y=3 mm, 0.
 FP64_INST = {"base": 27.5, "drift": 12.2, "quad": 51.5, "sext": 5.0, "bend": 16.0, "rf": 30.0}
 # split-TF32 form: float32 gather (two float->double conversions + two fma for the kick)
 FP64_INST_BASE_F32 = 17.5
+# sliced grids: the slice index (one subtract, one multiply, one floor conversion) per locate
+FP64_INST_SLICE = 3.0
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -136,19 +147,29 @@ def measured_peaks():
 
 def cpu_baseline(config, n_kicks):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample:
-    the full particle set through the first n_kicks kicks of turn 1."""
+    the full particle set (c4: its largest bunch) through the first n_kicks
+    kicks of turn 1."""
     import oracle
     from paper_2010_11540_gb300 import synth
-    parts, b, grid, lat = synth.workload(config)
+    slices = None
+    if config == "c4":
+        bunches = synth.c4_bunches()
+        parts, b, grid, lat = max(bunches, key=lambda u: len(u[0]["x"]))
+        what = "c4 largest bunch"
+    else:
+        parts, b, grid, lat = synth.workload(config)
+        what = f"{config} full particle set"
+        if "n_slices" in synth.CONFIGS[config]:
+            slices = oracle.Slices(*synth.slices(config))
     g = oracle.Geometry(*grid)
     st = oracle.copy_state(parts)
     oracle.lib()
     t0 = time.perf_counter()
-    done = oracle.track(g, st, b, lat, 1, max_kicks=n_kicks)
+    done = oracle.track(g, st, b, lat, 1, max_kicks=n_kicks, slices=slices)
     dt = time.perf_counter() - t0
     n = len(parts["x"])
     return {"value": n * done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{config} full particle set ({n}), first {done} SC kicks of turn 1, {dt:.1f} s"}
+            "sample": f"{what} ({n}), first {done} SC kicks of turn 1, {dt:.1f} s"}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -171,13 +192,118 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "step": f"{kicks} SC kicks on the CPU oracle"},
+            "data": "synthetic", "config": {"workload": WORKLOADS.get(args.config, args.config),
+                                            "step": f"{kicks} SC kicks on the CPU oracle"},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # --------------------------------------------------------------------------- our arm
+KEYS = ("x", "px", "y", "py", "sigma", "psigma")
+
+
+class SingleRun:
+    """One bunch on one grid (c1-c3), or one bunch on a sliced grid (c5): sc_track_turns."""
+
+    kernel = "kick_push_kernel (gather+kick, push, fused CIC deposit)"
+
+    def __init__(self, config, rank, stream):
+        from paper_2010_11540_gb300 import synth
+        self.parts, self.b, self.grid, self.lat = synth.workload(config, seed=12345 + rank)
+        self.slices = synth.slices(config) if "n_slices" in synth.CONFIGS[config] else None
+        self.n = len(self.parts["x"])
+        self.stream = stream
+        self.n_classes = 1
+
+    def make(self, precision):
+        import torch
+        from paper_2010_11540_gb300 import sc
+        dev = {k: torch.from_numpy(self.parts[k]).cuda() for k in KEYS}
+        return sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices), dev
+
+    def turns(self, h, n):
+        from paper_2010_11540_gb300 import sc
+        sc.track_turns(h[0], h[1], self.b, self.lat, n)
+
+    def trace(self, h, on):
+        from paper_2010_11540_gb300 import sc
+        sc.trace_enable(h[0], on)
+
+    def trace_read(self, h):
+        from paper_2010_11540_gb300 import sc
+        return sc.trace_read(h[0])
+
+    def pinned(self):
+        import torch
+        return {k: torch.from_numpy(self.parts[k].copy()).pin_memory() for k in KEYS}
+
+    def host_turn(self, h, pinned):
+        from paper_2010_11540_gb300 import sc
+        sc.track_turns_host(h[0], pinned, self.b, self.lat, 1, device_state=h[1])
+
+    def close(self, h):
+        h[0].close()
+
+    def grid_desc(self):
+        d = {"grid": [self.grid[0], self.grid[1]]}
+        if self.slices:
+            d["slices"] = list(self.slices)
+        return d
+
+
+class BatchRun:
+    """Many bunches in one batch (c4): sc_batch_track_turns."""
+
+    kernel = "kick_push_batched (all bunches: gather+kick, push, fused CIC deposit)"
+
+    def __init__(self, config, rank, stream):
+        from paper_2010_11540_gb300 import synth
+        self.bunches = synth.c4_bunches(seed=12345 + 1000 * rank)
+        self.n = sum(len(p["x"]) for p, _, _, _ in self.bunches)
+        self.lat = self.bunches[0][3]
+        self.stream = stream
+        self.grids = [g for _, _, g, _ in self.bunches]
+        self.beams = [b for _, b, _, _ in self.bunches]
+        self.lats = [l for _, _, _, l in self.bunches]
+        self.n_classes = len(set(self.grids))
+
+    def make(self, precision):
+        import torch
+        from paper_2010_11540_gb300 import sc
+        devs = [{k: torch.from_numpy(p[k]).cuda() for k in KEYS} for p, _, _, _ in self.bunches]
+        return sc.create_batch(self.grids, precision=precision, stream=self.stream), devs
+
+    def turns(self, h, n):
+        from paper_2010_11540_gb300 import sc
+        sc.batch_track_turns(h[0], h[1], self.beams, self.lats, n)
+
+    def trace(self, h, on):
+        from paper_2010_11540_gb300 import sc
+        sc.batch_trace_enable(h[0], on)
+
+    def trace_read(self, h):
+        from paper_2010_11540_gb300 import sc
+        return sc.batch_trace_read(h[0])
+
+    def pinned(self):
+        import torch
+        return [{k: torch.from_numpy(p[k].copy()).pin_memory() for k in KEYS} for p, _, _, _ in self.bunches]
+
+    def host_turn(self, h, pinned):
+        from paper_2010_11540_gb300 import sc
+        sc.batch_track_turns_host(h[0], pinned, self.beams, self.lats, 1, device_states=h[1])
+
+    def close(self, h):
+        pass
+
+    def grid_desc(self):
+        sizes = sorted({g[0] for g in self.grids})
+        return {"bunches": len(self.bunches), "grids": {f"{s}x{s}": sum(1 for g in self.grids if g[0] == s)
+                                                        for s in sizes},
+                "working_points": "8x8 tune scan +-0.1 around (22.40, 20.75)"}
+
+
 def run_ours(args):
     import torch
 
@@ -191,20 +317,18 @@ def run_ours(args):
     build.build()
     sc.load()
     stream = torch.cuda.Stream()
-    parts, b, grid, lat = synth.workload(args.config, seed=12345 + rank)
-    n = len(parts["x"])
-    keys = ("x", "px", "y", "py", "sigma", "psigma")
+    W = (BatchRun if args.config == "c4" else SingleRun)(args.config, rank, stream)
+    n = W.n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
 
     def timed_turns(precision):
         """Warm-up turns, then exactly args.steps timed turns, L2 flushed between
-        turns; returns (grid, device state, total ms (max over ranks), wall s, clocks)."""
-        dev = {k: torch.from_numpy(parts[k]).cuda() for k in keys}
-        g = sc.create_grid(*grid, precision=precision, stream=stream)
+        turns; returns (handle, total ms (max over ranks), wall s, clocks)."""
+        h = W.make(precision)
         with torch.cuda.stream(stream):
             for _ in range(args.warmup):
-                sc.track_turns(g, dev, b, lat, 1)
+                W.turns(h, 1)
             stream.synchronize()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.steps)]
@@ -217,7 +341,7 @@ def run_ours(args):
             for s in range(args.steps):
                 flush.zero_()
                 ev[s][0].record(stream)
-                sc.track_turns(g, dev, b, lat, 1)
+                W.turns(h, 1)
                 ev[s][1].record(stream)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t_wall
@@ -229,32 +353,35 @@ def run_ours(args):
             t = torch.tensor([ms], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
-        return g, dev, ms, wall, clk
+        return h, ms, wall, clk
 
-    inst_turn, n_kicks = fp64_inst_per_turn(lat, args.precision)
-    g, dev, ms, wall, clk = timed_turns(args.precision)
+    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, args.precision)
+    if getattr(W, "slices", None):
+        inst_turn += n_kicks * FP64_INST_SLICE
+    h, ms, wall, clk = timed_turns(args.precision)
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
     compare = None
     if not args.no_compare:
         other = "fp64" if args.precision == "tf32x3" else "tf32x3"
-        g2, _, ms2, _, clk2 = timed_turns(other)
+        h2, ms2, _, clk2 = timed_turns(other)
         compare = {"precision": other, "value": world * n * n_kicks * args.steps / (ms2 * 1e-3),
                    "ms_per_step": ms2 / args.steps, "clocks": clk2}
-        g2.close()
+        W.close(h2)
+        del h2
 
     # ---------------- dominant kernel, timed inside the turn graph (library tracing:
     # CUDA events on the grid's stream around every solve and kick/push launch)
-    sc.trace_enable(g, True)
+    W.trace(h, True)
     with torch.cuda.stream(stream):
-        sc.track_turns(g, dev, b, lat, 1)  # capture + warm
-        sc.trace_read(g)
-        sc.track_turns(g, dev, b, lat, 2)
-    kp_ms, solve_ms, traced = sc.trace_read(g)
-    sc.trace_enable(g, False)
+        W.turns(h, 1)  # capture + warm
+        W.trace_read(h)
+        W.turns(h, 2)
+    kp_ms, solve_ms, traced = W.trace_read(h)
+    W.trace(h, False)
     kp_avg_ms = kp_ms / traced
     inst_per_kick = inst_turn / n_kicks
     achieved = inst_per_kick * n / (kp_avg_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "kernel": "kick_push_kernel (gather+kick, push, fused CIC deposit)",
+    roofline = {"bound": "alu", "kernel": W.kernel,
                 "achieved": achieved, "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
                 "frac": achieved / FP64_PIPE_PEAK_TINST, "traffic": None,
                 "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (probe: 2.0/clk/SM)",
@@ -262,29 +389,31 @@ def run_ours(args):
                 "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
 
     # ---------------- end to end: host buffers through the public API
-    pinned = {k: torch.from_numpy(parts[k].copy()).pin_memory() for k in keys}
+    pinned = W.pinned()
     e2e_steps = max(2, args.steps // 2)
     with torch.cuda.stream(stream):
-        sc.track_turns_host(g, pinned, b, lat, 1, device_state=dev)
+        W.host_turn(h, pinned)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            sc.track_turns_host(g, pinned, b, lat, 1, device_state=dev)
+            W.host_turn(h, pinned)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e = {"value": n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
+    e2e = {"value": world * n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
            "d2h_bytes_per_step": 6 * 8 * n}
 
     solve_kernels = 3 if args.precision == "fp64" else 4
+    config = {"workload": WORKLOADS.get(args.config, args.config),
+              "step": f"one turn = {n_kicks} SC kicks via "
+                      f"{'sc_batch_track_turns' if args.config == 'c4' else 'sc_track_turns'} (CUDA graph)",
+              "solve": "fp64 FFT convolution" if args.precision == "fp64" else "tf32x3 DFT GEMMs on tcgen05",
+              "particles": n, **W.grid_desc(),
+              "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one turn = 216 SC kicks via sc_track_turns (CUDA graph)",
-                       "solve": "fp64 FFT convolution" if args.precision == "fp64" else
-                       "tf32x3 DFT GEMMs on tcgen05", "particles": n, "grid": [g.nx, g.ny],
-                       "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"},
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
             "roofline": roofline, "e2e": e2e, "clocks": clk, "compare_form": compare,
-            "gpu_launches": args.steps * n_kicks * (solve_kernels + 1),
+            "gpu_launches": args.steps * n_kicks * (W.n_classes * solve_kernels + 1),
             "wall_s_timed": wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_kicks)

@@ -190,6 +190,20 @@ sc_status sc_trace_enable(sc_grid *g, int enable);
  * and solve time in ms, and the number of kicks they cover. */
 sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
+/* Tiling of the split-TF32 solve (SC_SOLVE_TF32X3).  Each of its four GEMM
+ * phases (row DFT, column DFT, inverse column DFT, inverse row DFT) has a few
+ * kernel variants (tile width, split-K cluster size, pipeline depth); the
+ * fastest for the grid (and its stacked slices) is chosen by timing them all
+ * when the grid is created.  sc_get_solver_tiling reads the four variant
+ * indices and, if desc != NULL, describes them in desc (n bytes, always
+ * NUL-terminated); sc_set_solver_tiling forces them (an entry of -1 keeps
+ * that phase's variant), e.g. to compare grids bit for bit.  Variants differ
+ * only in the summation order of the FP32 accumulation.  Errors:
+ * SC_ERR_UNSUPPORTED (not a split-TF32 grid), SC_ERR_ARG (index out of range
+ * or a variant that does not fit the grid). */
+sc_status sc_get_solver_tiling(sc_grid *g, int *choice, char *desc, size_t n);
+sc_status sc_set_solver_tiling(sc_grid *g, const int *choice);
+
 /* ---- Batches of independent bunches --------------------------------------
  * Many bunches (working points of a tune scan, bunches of a train, intensity
  * scans), each with its own particles, beam, lattice and transverse grid,
@@ -243,6 +257,8 @@ sc_status sc_batch_read(sc_batch *B, int b, uint64_t *Q, double *Ex, double *Ey,
  * time is the batched launch covering every bunch; solve time covers every
  * grid class). */
 sc_status sc_batch_trace_enable(sc_batch *B, int enable);
+/* sc_set_solver_tiling for every grid class of the batch (split-TF32 batches). */
+sc_status sc_batch_set_solver_tiling(sc_batch *B, const int *choice);
 sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
 /* Largest particle count sc_moments_noalloc accepts (its partial sums are

@@ -384,6 +384,28 @@ sc_status sc_tune_setup(sc_grid* g, const sc_particles* p, const double* twiss, 
   return launch_phase_advance(p, g->tune_twiss, acc, 0, g->stream);
 }
 
+sc_status sc_get_solver_tiling(sc_grid* g, int* choice, char* desc, size_t n) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  std::string d;
+  sc_status st = tf32_get_tiling(g, choice, desc ? &d : nullptr);
+  if (st) return st;
+  if (desc && n > 0) {
+    std::strncpy(desc, d.c_str(), n - 1);
+    desc[n - 1] = '\0';
+  }
+  return SC_OK;
+}
+
+sc_status sc_set_solver_tiling(sc_grid* g, const int* choice) {
+  if (!g || !choice) return set_error(SC_ERR_ARG, "grid or choice is NULL");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->track) {  // captured turns hold the old launches
+    destroy_plan(g->track);
+    g->track = nullptr;
+  }
+  return tf32_set_tiling(g, choice);
+}
+
 sc_status sc_trace_enable(sc_grid* g, int enable) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   g->trace = enable ? 1 : 0;

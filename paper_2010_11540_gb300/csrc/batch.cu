@@ -498,6 +498,18 @@ sc_status sc_batch_read(sc_batch* B, int b, uint64_t* Q, double* Ex, double* Ey,
   return SC_OK;
 }
 
+sc_status sc_batch_set_solver_tiling(sc_batch* B, const int* choice) {
+  if (!B || !choice) return set_error(SC_ERR_ARG, "batch or choice is NULL");
+  SC_CUDA(cudaStreamSynchronize(B->stream));
+  destroy_batch_plan(B->plan);  // captured turns hold the old launches
+  B->plan = nullptr;
+  for (sc_grid* g : B->cls) {
+    sc_status st = sc_set_solver_tiling(g, choice);
+    if (st) return st;
+  }
+  return SC_OK;
+}
+
 sc_status sc_batch_trace_enable(sc_batch* B, int enable) {
   if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
   B->trace = enable ? 1 : 0;

@@ -15,7 +15,9 @@
 //       DFT, kept for j' < ny: r < ny: Re G_f(j', p), r = ny+j': Im G_f
 //   P3  E[(f,j)][i] = A3[(f,j)][(re|im, p)] B4[i][(re|im, p)]   Hermitian
 //       inverse row DFT with weights 1 (p = 0, nx) or 2 and 1/(Mx My).
-// Supported: nx = ny in {128, 256} (M tiles of 128 rows).
+// Supported: nx = ny in {64, 128, 256} (M tiles of 128 rows).  Tile width
+// (N columns per CTA), split-K cluster size and pipeline depth are chosen per
+// phase by timing the candidates when a grid is created.
 #include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -32,7 +34,6 @@ namespace sc {
 namespace {
 
 constexpr int KC = 32;          // fp32 elements per K chunk (one 128-byte swizzle row)
-constexpr int NT = 16;          // N columns per CTA tile
 constexpr int TM = 128;         // rows per MMA / M tile
 constexpr int kThreads = 128;   // 4 warps: TMA producer, MMA issuer, TMEM owner, all do the epilogue
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier waits (~2 s of SM clock), then error + bail out
@@ -118,8 +119,6 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   d |= (uint64_t)2 << 61;
   return d;
 }
-// Instruction descriptor: D f32, A = B = tf32, both K-major, M = 128, N = NT.
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
@@ -140,25 +139,25 @@ __device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
 struct GemmArgs {
   CUtensorMap tA_hi, tA_lo, tB_hi, tB_lo;  // tB_* unused for P1
   int k_chunks;   // K / KC
-  int n_tiles;    // N tiles per M block
+  int m_tiles;    // M tiles (TM rows each) of the whole, possibly stacked, GEMM
+  int n_tiles;    // N tiles (NT columns each)
+  int n_total;    // valid columns (the last tile may run past them)
   int nx, ny, My, Npad;
-  // P1: charge input
+  // P1: charge input (stacked grids back to back: row n of the GEMM's N is Q row n)
   const unsigned long long* Q;
   float scale;
   const float* stack_scale;  // per stacked grid (bunches of a batch), or NULL: scale
   // P2A: charge grid to clear for the next deposit (NULL: leave it)
   unsigned long long* Qzero;
-  int qcells;
+  long long qcells;
   // outputs / epilogue inputs
   float *out_hi, *out_lo;  // next phase's operand (P1: B2, P2A: B3, P2B: A3)
   int out_ld;              // its row length (K of the next phase)
+  long long out_slice;     // its elements per stacked grid
   const float *Sx, *Sy;    // P2A: spectra [Npad][My]
   float2* E;               // P3: fields, float32 (Ex, Ey) per node
+  long long e_slice;       // P3: nodes per stacked grid
   int* err;                // set to 1 when a bounded wait ran out
-  // longitudinal slices (blockIdx.y): rows per slice of the data operands and
-  // elements per slice of the inputs / outputs
-  int a_slice_rows, b_slice_rows;
-  long long out_slice, q_slice, e_slice;
 };
 
 // Which operand is a constant DFT matrix (loadable before the grid dependency
@@ -169,16 +168,23 @@ struct Roles {
   static constexpr bool TMA_B = (PH != P1);
 };
 
-template <int PH>
+template <int PH, int NT, int STAGES_>
 struct Smem {
   static constexpr int A_TILE = TM * 128;  // bytes of one 128-row x 32-element tile
-  static constexpr int B_TILE = NT * 128;  // 2 KB
+  static constexpr int B_TILE = NT * 128;
   static constexpr int STAGE = 2 * A_TILE + (Roles<PH>::TMA_B ? 2 * B_TILE : 0);
-  static constexpr int STAGES = (PH == P1) ? 4 : 5;
+  static constexpr int STAGES = STAGES_;
   static constexpr int B_RESIDENT_MAX_CHUNKS = 8;  // P1: charge tiles for K up to 256
   static constexpr int RESIDENT = (PH == P1) ? 2 * B_RESIDENT_MAX_CHUNKS * B_TILE : 0;
   static constexpr int BYTES = STAGES * STAGE + RESIDENT + 1024 /*align slack*/;
+  static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
+
+// Instruction descriptor: D f32, A = B = tf32, both K-major, M = 128, N = NT.
+template <int NT>
+__host__ __device__ constexpr uint32_t idesc() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
 
 namespace cg = cooperative_groups;
 __device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
@@ -188,11 +194,15 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
 // One cluster of SK CTAs: a 128-row x NT-column tile of C = A B^T, the K
 // chunks split evenly across the SK CTAs; each accumulates its three split
 // products in TMEM, the partial tiles are summed through distributed shared
-// memory and each CTA finishes NT/SK of the columns.
-template <int PH, int SK>
+// memory and each CTA finishes NT/SK of the columns.  Stacked grids (slices,
+// bunches of a batch) extend the data operand: their rows follow one another,
+// so one launch covers all of them; tiles are ordered so that consecutive
+// CTAs share the data operand's tile (the constant one stays in L2).
+template <int PH, int SK, int NT, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ GemmArgs g) {
-  using L = Smem<PH>;
+  using L = Smem<PH, NT, STAGES>;
   using R = Roles<PH>;
+  constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[L::STAGES], empty_bar[L::STAGES], accum_bar;
@@ -202,11 +212,10 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int rank = (SK > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int tile = blockIdx.x / SK;
-  const int mb = tile / g.n_tiles, nb = tile % g.n_tiles;
+  // data operand outer: B (P1, P2A, P2B) or A (P3)
+  const int mb = R::CONST_A ? tile % g.m_tiles : tile / g.n_tiles;
+  const int nb = R::CONST_A ? tile / g.m_tiles : tile % g.n_tiles;
   const int n0 = nb * NT, a_row = mb * TM;
-  const int slice = blockIdx.y;
-  const int a_row_g = a_row + slice * g.a_slice_rows;  // row of the (stacked) A tensor
-  const int n0_g = n0 + slice * g.b_slice_rows;        // row of the (stacked) B tensor
   unsigned char* stage_base = smem;
   unsigned char* resident = smem + L::STAGES * L::STAGE;
   const int kpc = g.k_chunks / SK, kc0 = rank * kpc;  // this CTA's K chunks: kc0 .. kc0+kpc-1
@@ -214,13 +223,13 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 
   auto load_a = [&](int lk, int st) {
     unsigned char* sb = stage_base + st * L::STAGE;
-    tma_load_2d(sb, &g.tA_hi, &full_bar[st], (kc0 + lk) * KC, a_row_g);
-    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], (kc0 + lk) * KC, a_row_g);
+    tma_load_2d(sb, &g.tA_hi, &full_bar[st], (kc0 + lk) * KC, a_row);
+    tma_load_2d(sb + L::A_TILE, &g.tA_lo, &full_bar[st], (kc0 + lk) * KC, a_row);
   };
   auto load_b = [&](int lk, int st) {
     unsigned char* bb = stage_base + st * L::STAGE + 2 * L::A_TILE;
-    tma_load_2d(bb, &g.tB_hi, &full_bar[st], (kc0 + lk) * KC, n0_g);
-    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], (kc0 + lk) * KC, n0_g);
+    tma_load_2d(bb, &g.tB_hi, &full_bar[st], (kc0 + lk) * KC, n0);
+    tma_load_2d(bb + L::B_TILE, &g.tB_lo, &full_bar[st], (kc0 + lk) * KC, n0);
   };
 
   if (threadIdx.x == 0) {
@@ -238,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       prefetch_map(&g.tB_lo);
     }
   }
-  if (warp == 2) tmem_alloc(&tmem_base_s, 32);
+  if (warp == 2) tmem_alloc(&tmem_base_s, TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -257,39 +266,41 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   pdl_wait();
   if (PH == P2A && g.Qzero) {
     // every reader of the charge (the row transform) has finished: clear it for the next deposit
-    for (long long c = ((long long)blockIdx.y * gridDim.x + blockIdx.x) * kThreads + threadIdx.x; c < g.qcells;
-         c += (long long)gridDim.x * gridDim.y * kThreads)
+    for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < g.qcells;
+         c += (long long)gridDim.x * kThreads)
       g.Qzero[c] = 0ull;
   }
   if (PH == P1) {
-    // B operand = normalised charge rows j = n0 .. n0+NT-1, all K = nx, split hi/lo, swizzled.
-    // 16-byte loads, all issued before any is used.
-    constexpr int PER2 = NT * 256 / 2 / kThreads;  // pairs per thread for nx <= 256
+    // B operand = normalised charge rows n0 .. n0+NT-1 (NT divides ny: one stacked grid per
+    // tile), all K = nx, split hi/lo, swizzled; 16-byte loads, issued in groups of 8.
     const int pairs = NT * g.nx / 2;
-    const longlong2* q2 = (const longlong2*)(g.Q + slice * g.q_slice + (size_t)n0 * g.nx);
-    const float qscale = g.stack_scale ? g.stack_scale[slice] : g.scale;
-    longlong2 v[PER2];
+    const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx);
+    const float qscale = g.stack_scale ? g.stack_scale[n0 / g.ny] : g.scale;
+    constexpr int G = 8;
+    for (int e0 = threadIdx.x; e0 < pairs; e0 += G * kThreads) {
+      longlong2 v[G];
 #pragma unroll
-    for (int u = 0; u < PER2; ++u) {
-      const int e = threadIdx.x + u * kThreads;
-      v[u] = (e < pairs) ? q2[e] : make_longlong2(0, 0);
-    }
+      for (int u = 0; u < G; ++u) {
+        const int e = e0 + u * kThreads;
+        v[u] = (e < pairs) ? q2[e] : make_longlong2(0, 0);
+      }
 #pragma unroll
-    for (int u = 0; u < PER2; ++u) {
-      const int e = threadIdx.x + u * kThreads;
-      if (e < pairs) {
+      for (int u = 0; u < G; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e < pairs) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const unsigned long long qi = (unsigned long long)(h ? v[u].y : v[u].x);
-          const int el = 2 * e + h, r = el / g.nx, i = el % g.nx;
-          // uint64 -> float through its 32-bit halves (no FP64 instruction)
-          const float qv =
-              fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * qscale;
-          float hi, lo;
-          split(qv, hi, lo);
-          const int kc = i / KC, k = i % KC;
-          *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
-          *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+          for (int h = 0; h < 2; ++h) {
+            const unsigned long long qi = (unsigned long long)(h ? v[u].y : v[u].x);
+            const int el = 2 * e + h, r = el / g.nx, i = el % g.nx;
+            // uint64 -> float through its 32-bit halves (no FP64 instruction)
+            const float qv =
+                fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * qscale;
+            float hi, lo;
+            split(qv, hi, lo);
+            const int kc = i / KC, k = i % KC;
+            *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
+            *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+          }
         }
       }
     }
@@ -333,9 +344,9 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 #pragma unroll
       for (int kk = 0; kk < KC / 8; ++kk) {
         const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
-        mma_tf32(tmem, dah + o, dbh + o, kIdesc, (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah + o, dbl + o, kIdesc, 1u);
-        mma_tf32(tmem, dal + o, dbh + o, kIdesc, 1u);
+        mma_tf32(tmem, dah + o, dbh + o, idesc<NT>(), (kc > 0 || kk > 0) ? 1u : 0u);
+        mma_tf32(tmem, dah + o, dbl + o, idesc<NT>(), 1u);
+        mma_tf32(tmem, dal + o, dbh + o, idesc<NT>(), 1u);
       }
       mma_commit(&empty_bar[st]);
     }
@@ -347,60 +358,34 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   pdl_allow();
 
   // ---- epilogue: all four warps; warp w owns TMEM lanes / tile rows 32w .. 32w+31
-  const bool have = mbar_wait(&accum_bar, 0);
+  // warp-uniform decisions (tcgen05.ld is a warp-collective instruction)
+  const bool have = __all_sync(0xffffffffu, mbar_wait(&accum_bar, 0));
   if ((!have || abort_s) && threadIdx.x == 0) atomicExch(g.err, 1);
   tc_fence_after();
   const int t = warp * 32 + lane;
   const int r = a_row + t;  // row of C
-  float acc[NT];
-  if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), acc);
-  constexpr int CW = NT / SK;  // columns finished by this CTA
+  const bool ok = __all_sync(0xffffffffu, have && !abort_s);
+  constexpr int CW = NT / SK;             // columns finished by this CTA
+  constexpr int CH = CW < 16 ? CW : 16;   // columns per epilogue chunk
+  static_assert(CW % 4 == 0, "whole float4 column groups");
   const int c0 = rank * CW;
-  if (SK > 1) {
-    // partial tiles -> shared memory (the stages are idle now), summed across the cluster
-    cg::cluster_group cl = cg::this_cluster();
-    float4* red = (float4*)stage_base;
-#pragma unroll
-    for (int q4 = 0; q4 < NT / 4; ++q4)
-      red[t * (NT / 4) + q4] = have ? make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3])
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-    cl.sync();
-    float4 part[SK][CW / 4];
-#pragma unroll
-    for (int q = 0; q < SK; ++q) {
-      const float4* rem = cl.map_shared_rank(red, q);
-#pragma unroll
-      for (int q4 = 0; q4 < CW / 4; ++q4) part[q][q4] = rem[t * (NT / 4) + c0 / 4 + q4];
-    }
-#pragma unroll
-    for (int q4 = 0; q4 < CW / 4; ++q4) {
-      float4 v = part[0][q4];
-#pragma unroll
-      for (int q = 1; q < SK; ++q) {
-        v.x += part[q][q4].x;
-        v.y += part[q][q4].y;
-        v.z += part[q][q4].z;
-        v.w += part[q][q4].w;
-      }
-      acc[c0 + 4 * q4] = v.x;
-      acc[c0 + 4 * q4 + 1] = v.y;
-      acc[c0 + 4 * q4 + 2] = v.z;
-      acc[c0 + 4 * q4 + 3] = v.w;
-    }
-  }
-  if (have && !abort_s) {
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+
+  // Finish columns cb .. cb+CH-1 of the tile (values in acc) for this phase.
+  auto finish = [&](const float* acc, int cb) {
     if (PH == P1) {
-      // row c of R1T: Re F1(j, p = c) for c <= nx, Im F1(j, p = c - nx) above
+      // row c of R1T: Re F1(j, p = c) for c <= nx, Im F1(j, p = c - nx) above; column = charge row
       const int p = (r <= g.nx) ? r : r - g.nx;
       const int half = (r <= g.nx) ? 0 : 1;
-      const size_t ob = slice * g.out_slice + (size_t)p * g.out_ld + half * g.ny + n0 + c0;
+      const int slice = n0 / g.ny, j = n0 - slice * g.ny + cb;
+      const size_t ob = (size_t)slice * g.out_slice + (size_t)p * g.out_ld + half * g.ny + j;
       float4* dh = (float4*)(g.out_hi + ob);
       float4* dl = (float4*)(g.out_lo + ob);
 #pragma unroll
-      for (int q4 = 0; q4 < CW / 4; ++q4) {
+      for (int q4 = 0; q4 < CH / 4; ++q4) {
         float h[4], l[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) split(acc[c0 + 4 * q4 + u], h[u], l[u]);
+        for (int u = 0; u < 4; ++u) split(acc[4 * q4 + u], h[u], l[u]);
         dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
         dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
       }
@@ -412,50 +397,103 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const int col = re ? g.My + k : k;
       const float sgn = re ? 1.f : -1.f;
       // all spectrum loads first (the stores below could alias them for the compiler)
-      float sx[CW], sy[CW];
+      float sx[CH], sy[CH];
+      int sl[CH], pp[CH];
 #pragma unroll
-      for (int cc = 0; cc < CW; ++cc) {
-        sx[cc] = __ldg(g.Sx + (size_t)(n0 + c0 + cc) * g.My + k);
-        sy[cc] = __ldg(g.Sy + (size_t)(n0 + c0 + cc) * g.My + k);
+      for (int u = 0; u < CH; ++u) {
+        const int n = n0 + cb + u;  // stacked column: grid n / Npad, p = n % Npad
+        sl[u] = n / g.Npad;
+        pp[u] = n - sl[u] * g.Npad;
+        const bool in = n < g.n_total;
+        sx[u] = in ? __ldg(g.Sx + (size_t)pp[u] * g.My + k) : 0.f;
+        sy[u] = in ? __ldg(g.Sy + (size_t)pp[u] * g.My + k) : 0.f;
       }
 #pragma unroll
-      for (int cc = 0; cc < CW; ++cc) {
-        const int p = n0 + c0 + cc;
-        const float f = sgn * acc[c0 + cc];
-        const size_t rx = slice * g.out_slice + (size_t)p * g.out_ld + col;
-        const size_t ry = slice * g.out_slice + (size_t)(g.Npad + p) * g.out_ld + col;
-        split(sx[cc] * f, g.out_hi[rx], g.out_lo[rx]);
-        split(sy[cc] * f, g.out_hi[ry], g.out_lo[ry]);
+      for (int u = 0; u < CH; ++u) {
+        if (n0 + cb + u >= g.n_total) continue;
+        const float f = sgn * acc[u];
+        const size_t base = (size_t)sl[u] * g.out_slice;
+        const size_t rx = base + (size_t)pp[u] * g.out_ld + col;
+        const size_t ry = base + (size_t)(g.Npad + pp[u]) * g.out_ld + col;
+        split(sx[u] * f, g.out_hi[rx], g.out_lo[rx]);
+        split(sy[u] * f, g.out_hi[ry], g.out_lo[ry]);
       }
     } else if (PH == P2B) {
-      // row r: part (Re G, Im G) = r / ny at j' = r % ny; columns n = f*Npad + p
+      // row r: part (Re G, Im G) = r / ny at j' = r % ny; stacked column n: grid n / (2 Npad),
+      // field f and p within it (4-column groups never straddle: Npad is a multiple of 16)
       const int part = r / g.ny, jr = r % g.ny;
-      const int f = n0 / g.Npad, p0 = n0 % g.Npad;  // NT divides Npad: one field per tile
-      const size_t o = slice * g.out_slice + (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p0 + c0;
-      float4* dh = (float4*)(g.out_hi + o);
-      float4* dl = (float4*)(g.out_lo + o);
 #pragma unroll
-      for (int q4 = 0; q4 < CW / 4; ++q4) {
+      for (int q4 = 0; q4 < CH / 4; ++q4) {
+        const int n = n0 + cb + 4 * q4;
+        if (n >= g.n_total) continue;
+        const int slice = n / (2 * g.Npad), rem = n - slice * 2 * g.Npad;
+        const int f = rem / g.Npad, p = rem - f * g.Npad;
+        const size_t o = (size_t)slice * g.out_slice + (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p;
         float h[4], l[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) split(acc[c0 + 4 * q4 + u], h[u], l[u]);
-        dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
-        dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
+        for (int u = 0; u < 4; ++u) split(acc[4 * q4 + u], h[u], l[u]);
+        *(float4*)(g.out_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+        *(float4*)(g.out_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
       }
     } else {
-      // row r: field f = r / ny (Ex, Ey) at j = r % ny; columns i = n0 + cc; float32 (Ex, Ey) pairs
-      const int f = r / g.ny, j = r % g.ny;
-      float* e = (float*)g.E + 2 * (slice * g.e_slice + (size_t)j * g.nx + n0) + f;
+      // stacked row r: grid r / (2 ny); within it field f = (r % 2ny) / ny (Ex, Ey) at j;
+      // columns i = n0 + cb + u; float32 (Ex, Ey) pairs
+      const int slice = r / (2 * g.ny), rr = r - slice * 2 * g.ny;
+      const int f = rr / g.ny, j = rr % g.ny;
+      float* e = (float*)g.E + 2 * ((size_t)slice * g.e_slice + (size_t)j * g.nx + n0 + cb) + f;
 #pragma unroll
-      for (int cc = c0; cc < c0 + CW; ++cc) e[2 * cc] = acc[cc];
+      for (int u = 0; u < CH; ++u) e[2 * u] = acc[u];
+    }
+  };
+
+  if (SK > 1) {
+    // partial tiles -> shared memory (the stages are idle now), summed across the cluster
+    static_assert(SK == 1 || kThreads * NT * 4 <= L::STAGES * L::STAGE, "reduction buffer fits the stages");
+    cg::cluster_group cl = cg::this_cluster();
+    float4* red = (float4*)stage_base;
+#pragma unroll
+    for (int c16 = 0; c16 < NT / 16; ++c16) {
+      float v[16];
+      if (have) tmem_ld16(trow + c16 * 16, v);
+#pragma unroll
+      for (int q4 = 0; q4 < 4; ++q4)
+        red[t * (NT / 4) + c16 * 4 + q4] =
+            have ? make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    cl.sync();
+#pragma unroll
+    for (int cb = c0; cb < c0 + CW; cb += CH) {
+      float acc[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) acc[u] = 0.f;
+#pragma unroll
+      for (int q = 0; q < SK; ++q) {
+        const float4* rem = cl.map_shared_rank(red, q);
+#pragma unroll
+        for (int q4 = 0; q4 < CH / 4; ++q4) {
+          const float4 w = rem[t * (NT / 4) + cb / 4 + q4];
+          acc[4 * q4] += w.x;
+          acc[4 * q4 + 1] += w.y;
+          acc[4 * q4 + 2] += w.z;
+          acc[4 * q4 + 3] += w.w;
+        }
+      }
+      if (ok) finish(acc, cb);
+    }
+    cl.sync();  // keep this CTA's partial tile alive until every rank has read it
+  } else if (ok) {
+#pragma unroll
+    for (int c16 = 0; c16 < NT / 16; ++c16) {
+      float acc[16];
+      tmem_ld16(trow + c16 * 16, acc);
+      finish(acc, c16 * 16);
     }
   }
-  if (SK > 1) cg::this_cluster().sync();  // keep this CTA's partial tile alive until every rank has read it
   tc_fence_before();
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    tmem_dealloc(tmem, 32);
+    tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
@@ -512,6 +550,13 @@ struct Mat {
 
 }  // namespace
 
+// One phase of the solve as launched: kernel variant, its arguments, its grid.
+struct PhaseRun {
+  int variant = -1;  // index into the phase's candidate list
+  GemmArgs a;
+  int grid = 0;
+};
+
 struct Tf32Plan {
   int Mx, My, Npad;
   Mat B1, W2f, W2i, B4;      // constants
@@ -519,8 +564,8 @@ struct Tf32Plan {
   float *Sx, *Sy;            // [Npad][My]
   int K3;                    // row length of A3 and B4 (2 Npad rounded up to whole split-K chunks)
   int* err;
-  GemmArgs a1, a2a, a2b, a3;
-  int grid1, grid2a, grid2b, grid3;
+  PhaseRun run[4];           // P1, P2A, P2B, P3
+  float tuned_us[4];         // time of the chosen variant when tuned (0: forced)
 };
 
 namespace {
@@ -553,34 +598,62 @@ void free_mat(Mat& m) {
   m = Mat{};
 }
 
-// Split-K cluster size per phase (K chunks per CTA: P1 nx/32, P2A 2ny/64, P2B 2My/128, P3 K3/64).
-constexpr int SK1 = 1, SK2A = 2, SK2B = 4, SK3 = 2;
+// ------------------------------------------------------------------ kernel variants
+struct Variant {
+  int sk, nt, stages, smem;
+  const void* fn;
+};
 
-template <int PH, int SK>
-sc_status set_smem_attr() {
-  SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH, SK>, cudaFuncAttributeMaxDynamicSharedMemorySize, Smem<PH>::BYTES));
-  if (SK > 1) SC_CUDA(cudaFuncSetAttribute(dft_gemm<PH, SK>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
+template <int PH, int SK, int NT, int ST>
+Variant variant() {
+  return Variant{SK, NT, ST, Smem<PH, NT, ST>::BYTES, (const void*)dft_gemm<PH, SK, NT, ST>};
+}
+
+// Candidates per phase (split-K cluster size SK, tile width NT, pipeline
+// stages), timed against each other when a grid is created.  Wide tiles load
+// each constant-operand tile once for many columns (stacked grids); narrow,
+// K-split tiles give a single small grid enough CTAs.
+const std::vector<Variant>& variants(int ph) {
+  static const std::vector<Variant> v[4] = {
+      {variant<P1, 1, 16, 4>(), variant<P1, 1, 32, 4>(), variant<P1, 1, 64, 2>()},
+      {variant<P2A, 2, 16, 5>(), variant<P2A, 1, 32, 4>(), variant<P2A, 2, 32, 4>(), variant<P2A, 1, 64, 4>(),
+       variant<P2A, 1, 128, 3>()},
+      {variant<P2B, 4, 16, 5>(), variant<P2B, 2, 32, 4>(), variant<P2B, 1, 64, 4>(), variant<P2B, 2, 64, 4>(),
+       variant<P2B, 1, 128, 3>()},
+      {variant<P3, 2, 16, 5>(), variant<P3, 1, 32, 4>(), variant<P3, 2, 32, 4>(), variant<P3, 1, 64, 4>()}};
+  return v[ph];
+}
+
+sc_status set_attrs(const Variant& v) {
+  SC_CUDA(cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem));
+  if (v.sk > 1) SC_CUDA(cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
   return SC_OK;
 }
 
-// tiles x SK CTAs, clusters of SK along x, programmatic dependent launch.
-template <int PH, int SK>
-cudaError_t launch_phase(int tiles, int slices, const GemmArgs& a, cudaStream_t s) {
+// CTAs (tiles x SK), clusters of SK along x, optionally programmatic dependent launch.
+cudaError_t launch_run(int ph, const PhaseRun& r, cudaStream_t s, bool pdl) {
+  const Variant& v = variants(ph)[r.variant];
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(tiles * SK, slices);
+  cfg.gridDim = dim3(r.grid);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = Smem<PH>::BYTES;
+  cfg.dynamicSmemBytes = v.smem;
   cfg.stream = s;
   cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  at[1].id = cudaLaunchAttributeClusterDimension;
-  at[1].val.clusterDim.x = SK;
-  at[1].val.clusterDim.y = 1;
-  at[1].val.clusterDim.z = 1;
+  int na = 0;
+  at[na].id = cudaLaunchAttributeClusterDimension;
+  at[na].val.clusterDim.x = v.sk;
+  at[na].val.clusterDim.y = 1;
+  at[na].val.clusterDim.z = 1;
+  ++na;
+  if (pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = at;
-  cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, dft_gemm<PH, SK>, a);
+  cfg.numAttrs = na;
+  void* args[1] = {(void*)&r.a};
+  return cudaLaunchKernelExC(&cfg, v.fn, args);
 }
 
 void host_fft(std::complex<double>* a, int n, int stride) {
@@ -606,6 +679,130 @@ void host_fft(std::complex<double>* a, int n, int stride) {
 
 }  // namespace
 
+// Arguments of phase ph for candidate k on grid g (tensor maps with the
+// variant's tile width); SC_ERR_ARG when the variant does not fit the grid.
+sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
+  Tf32Plan* T = g->tf32;
+  const Variant& v = variants(ph)[k];
+  const int nx = g->nx, ny = g->ny, nz = g->nstack, My = T->My, Npad = T->Npad, K3 = T->K3;
+  GemmArgs& a = out.a;
+  std::memset(&a, 0, sizeof a);
+  a.nx = nx;
+  a.ny = ny;
+  a.My = My;
+  a.Npad = Npad;
+  a.err = T->err;
+  int M = 0;
+  sc_status st = SC_OK;
+  switch (ph) {
+    case P1:  // C[c][(s,j)] = B1 q^T: M = 2nx (c), N = nz ny (j of every stacked grid), K = nx
+      if (ny % v.nt) return set_error(SC_ERR_ARG, "tile wider than a grid's rows");
+      if ((st = make_map(&a.tA_hi, T->B1.hi, 2 * nx, nx, TM)) || (st = make_map(&a.tA_lo, T->B1.lo, 2 * nx, nx, TM)))
+        return st;
+      M = 2 * nx;
+      a.k_chunks = nx / KC;
+      a.n_total = nz * ny;
+      a.Q = g->Q;
+      a.out_hi = T->B2.hi;
+      a.out_lo = T->B2.lo;
+      a.out_ld = 2 * ny;
+      a.out_slice = (long long)Npad * 2 * ny;
+      break;
+    case P2A:  // C[r][(s,p)] = W2f B2^T: M = 2My as (Re, Im) halves, N = nz Npad, K = 2ny
+      if ((st = make_map(&a.tA_hi, T->W2f.hi, 2 * My, 2 * ny, TM)) ||
+          (st = make_map(&a.tA_lo, T->W2f.lo, 2 * My, 2 * ny, TM)) ||
+          (st = make_map(&a.tB_hi, T->B2.hi, nz * Npad, 2 * ny, v.nt)) ||
+          (st = make_map(&a.tB_lo, T->B2.lo, nz * Npad, 2 * ny, v.nt)))
+        return st;
+      M = 2 * My;
+      a.k_chunks = 2 * ny / KC;
+      a.n_total = nz * Npad;
+      a.qcells = (long long)nz * nx * ny;
+      a.Sx = T->Sx;
+      a.Sy = T->Sy;
+      a.out_hi = T->B3.hi;
+      a.out_lo = T->B3.lo;
+      a.out_ld = 2 * My;
+      a.out_slice = (long long)2 * Npad * 2 * My;
+      break;
+    case P2B:  // C[r][(s,f,p)] = W2i B3^T: M = 2ny as (Re, Im) halves, N = nz 2 Npad, K = 2My
+      if ((st = make_map(&a.tA_hi, T->W2i.hi, 2 * ny, 2 * My, TM)) ||
+          (st = make_map(&a.tA_lo, T->W2i.lo, 2 * ny, 2 * My, TM)) ||
+          (st = make_map(&a.tB_hi, T->B3.hi, nz * 2 * Npad, 2 * My, v.nt)) ||
+          (st = make_map(&a.tB_lo, T->B3.lo, nz * 2 * Npad, 2 * My, v.nt)))
+        return st;
+      M = 2 * ny;
+      a.k_chunks = 2 * My / KC;
+      a.n_total = nz * 2 * Npad;
+      a.out_hi = T->A3.hi;
+      a.out_lo = T->A3.lo;
+      a.out_ld = K3;
+      a.out_slice = (long long)2 * ny * K3;
+      break;
+    default:  // P3: C[(s,f,j)][i] = A3 B4^T: M = nz 2ny as (Ex, Ey) halves per grid, N = nx, K = K3
+      if (nx % v.nt) return set_error(SC_ERR_ARG, "tile wider than a grid's columns");
+      if ((st = make_map(&a.tA_hi, T->A3.hi, nz * 2 * ny, K3, TM)) ||
+          (st = make_map(&a.tA_lo, T->A3.lo, nz * 2 * ny, K3, TM)) ||
+          (st = make_map(&a.tB_hi, T->B4.hi, nx, K3, v.nt)) || (st = make_map(&a.tB_lo, T->B4.lo, nx, K3, v.nt)))
+        return st;
+      M = nz * 2 * ny;
+      a.k_chunks = K3 / KC;
+      a.n_total = nx;
+      a.E = (float2*)g->E;
+      a.e_slice = (long long)nx * ny;
+      break;
+  }
+  if (a.k_chunks % v.sk) return set_error(SC_ERR_ARG, "K chunks do not split evenly over the cluster");
+  a.m_tiles = M / TM;
+  a.n_tiles = (a.n_total + v.nt - 1) / v.nt;
+  const long long grid = (long long)a.m_tiles * a.n_tiles * v.sk;
+  if (grid > (1LL << 30)) return set_error(SC_ERR_ARG, "too many tiles");
+  out.grid = (int)grid;
+  out.variant = k;
+  return set_attrs(v);
+}
+
+// Time every candidate of every phase on this grid (zero inputs; the time of a
+// dense contraction does not depend on the values) and keep the fastest.
+sc_status tf32_tune(sc_grid* g) {
+  Tf32Plan* T = g->tf32;
+  cudaEvent_t e0, e1;
+  SC_CUDA(cudaEventCreate(&e0));
+  SC_CUDA(cudaEventCreate(&e1));
+  sc_status st = SC_OK;
+  for (int ph = 0; ph < 4 && !st; ++ph) {
+    float best = 1e30f;
+    for (int k = 0; k < (int)variants(ph).size() && !st; ++k) {
+      PhaseRun r;
+      if (make_run(g, ph, k, r) != SC_OK) continue;  // does not fit this grid
+      r.a.scale = 1.f;
+      cudaError_t e = launch_run(ph, r, g->stream, false);  // warm-up
+      float ms = 0.f;
+      constexpr int reps = 3;
+      if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
+      for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch_run(ph, r, g->stream, false);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = cuda_error(e, "tuning the split-TF32 solve");
+        break;
+      }
+      const float us = 1e3f * ms / reps;
+      if (us < best) {
+        best = us;
+        T->run[ph] = r;
+        T->tuned_us[ph] = us;
+      }
+    }
+    if (!st && T->run[ph].variant < 0) st = set_error(SC_ERR_UNSUPPORTED, "no solve tiling fits this grid");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!st && tf32_error(g)) st = set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
+  return st;
+}
+
 sc_status tf32_create(sc_grid* g) {
   const int nx = g->nx, ny = g->ny, nz = g->nstack;
   if (nx != ny || (nx != 64 && nx != 128 && nx != 256))
@@ -615,8 +812,9 @@ sc_status tf32_create(sc_grid* g) {
   Tf32Plan* T = new (std::nothrow) Tf32Plan();
   if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
   g->tf32 = T;
-  const int Mx = 2 * nx, My = 2 * ny, Npad = ((nx + 1 + NT - 1) / NT) * NT;
-  const int K3 = ((2 * Npad + KC * SK3 - 1) / (KC * SK3)) * (KC * SK3);
+  // half-spectrum columns p = 0..nx, padded to a multiple of 16 (whole float4 groups per field)
+  const int Mx = 2 * nx, My = 2 * ny, Npad = ((nx + 1 + 15) / 16) * 16;
+  const int K3 = ((2 * Npad + 2 * KC - 1) / (2 * KC)) * (2 * KC);  // whole chunks for split-K up to 2
   T->Mx = Mx;
   T->My = My;
   T->Npad = Npad;
@@ -687,76 +885,7 @@ sc_status tf32_create(sc_grid* g) {
   SC_CUDA(cudaMalloc(&T->err, sizeof(int)));
   SC_CUDA(cudaMemset(T->err, 0, sizeof(int)));
 
-  auto base = [&](GemmArgs& a) {
-    std::memset(&a, 0, sizeof a);
-    a.nx = nx;
-    a.ny = ny;
-    a.My = My;
-    a.Npad = Npad;
-    a.err = T->err;
-    a.q_slice = (long long)nx * ny;
-    a.e_slice = (long long)nx * ny;
-  };
-  // P1: C[c][j] = B1 q^T: M = 2nx (c), N = ny (j), K = nx
-  base(T->a1);
-  if ((st = make_map(&T->a1.tA_hi, T->B1.hi, 2 * nx, nx, TM)) || (st = make_map(&T->a1.tA_lo, T->B1.lo, 2 * nx, nx, TM)))
-    return st;
-  T->a1.k_chunks = nx / KC;
-  T->a1.n_tiles = ny / NT;
-  T->a1.Q = g->Q;
-  T->a1.out_hi = T->B2.hi;
-  T->a1.out_lo = T->B2.lo;
-  T->a1.out_ld = 2 * ny;
-  T->a1.out_slice = (long long)Npad * 2 * ny;
-  T->grid1 = (2 * nx / TM) * T->a1.n_tiles;
-  // P2A: C[r][p] = W2f B2^T: M = 2My as (Re, Im) pairs of 128 rows, N = Npad, K = 2ny
-  base(T->a2a);
-  if ((st = make_map(&T->a2a.tA_hi, T->W2f.hi, 2 * My, 2 * ny, TM)) ||
-      (st = make_map(&T->a2a.tA_lo, T->W2f.lo, 2 * My, 2 * ny, TM)) ||
-      (st = make_map(&T->a2a.tB_hi, T->B2.hi, nz * Npad, 2 * ny, NT)) ||
-      (st = make_map(&T->a2a.tB_lo, T->B2.lo, nz * Npad, 2 * ny, NT)))
-    return st;
-  T->a2a.k_chunks = 2 * ny / KC;
-  T->a2a.n_tiles = Npad / NT;
-  T->a2a.Qzero = nullptr;
-  T->a2a.qcells = nz * nx * ny;
-  T->a2a.Sx = T->Sx;
-  T->a2a.Sy = T->Sy;
-  T->a2a.out_hi = T->B3.hi;
-  T->a2a.out_lo = T->B3.lo;
-  T->a2a.out_ld = 2 * My;
-  T->a2a.b_slice_rows = Npad;
-  T->a2a.out_slice = (long long)2 * Npad * 2 * My;
-  T->grid2a = (2 * My / TM) * T->a2a.n_tiles;
-  // P2B: C[r][(f,p)] = W2i B3^T: M = 2ny as (Re, Im) pairs, N = 2 Npad, K = 2My
-  base(T->a2b);
-  if ((st = make_map(&T->a2b.tA_hi, T->W2i.hi, 2 * ny, 2 * My, TM)) ||
-      (st = make_map(&T->a2b.tA_lo, T->W2i.lo, 2 * ny, 2 * My, TM)) ||
-      (st = make_map(&T->a2b.tB_hi, T->B3.hi, nz * 2 * Npad, 2 * My, NT)) ||
-      (st = make_map(&T->a2b.tB_lo, T->B3.lo, nz * 2 * Npad, 2 * My, NT)))
-    return st;
-  T->a2b.k_chunks = 2 * My / KC;
-  T->a2b.n_tiles = 2 * Npad / NT;
-  T->a2b.out_hi = T->A3.hi;
-  T->a2b.out_lo = T->A3.lo;
-  T->a2b.out_ld = K3;
-  T->a2b.b_slice_rows = 2 * Npad;
-  T->a2b.out_slice = (long long)2 * ny * K3;
-  T->grid2b = (2 * ny / TM) * T->a2b.n_tiles;
-  // P3: C[(f,j)][i] = A3 B4^T: M = 2ny as (Ex, Ey) pairs, N = nx, K = 2 Npad
-  base(T->a3);
-  if ((st = make_map(&T->a3.tA_hi, T->A3.hi, nz * 2 * ny, K3, TM)) ||
-      (st = make_map(&T->a3.tA_lo, T->A3.lo, nz * 2 * ny, K3, TM)) ||
-      (st = make_map(&T->a3.tB_hi, T->B4.hi, nx, K3, NT)) || (st = make_map(&T->a3.tB_lo, T->B4.lo, nx, K3, NT)))
-    return st;
-  T->a3.k_chunks = K3 / KC;
-  T->a3.a_slice_rows = 2 * ny;
-  T->a3.n_tiles = nx / NT;
-  T->a3.E = (float2*)g->E;
-  T->grid3 = (2 * ny / TM) * T->a3.n_tiles;
-  if ((st = set_smem_attr<P1, SK1>()) || (st = set_smem_attr<P2A, SK2A>()) || (st = set_smem_attr<P2B, SK2B>()) ||
-      (st = set_smem_attr<P3, SK3>()))
-    return st;
+  if ((st = tf32_tune(g)) != SC_OK) return st;
   return SC_OK;
 }
 
@@ -780,13 +909,11 @@ void tf32_destroy(sc_grid* g) {
 sc_status tf32_solve(sc_grid* g, bool zero_q) {
   Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_ARG, "grid has no TF32 solver");
-  T->a1.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
-  T->a1.stack_scale = (const float*)g->stack_scale;
-  T->a2a.Qzero = zero_q ? g->Q : nullptr;
-  SC_CUDA((launch_phase<P1, SK1>(T->grid1, g->nstack, T->a1, g->stream)));
-  SC_CUDA((launch_phase<P2A, SK2A>(T->grid2a, g->nstack, T->a2a, g->stream)));
-  SC_CUDA((launch_phase<P2B, SK2B>(T->grid2b, g->nstack, T->a2b, g->stream)));
-  SC_CUDA((launch_phase<P3, SK3>(T->grid3, g->nstack, T->a3, g->stream)));
+  PhaseRun& r1 = T->run[P1];
+  r1.a.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
+  r1.a.stack_scale = (const float*)g->stack_scale;
+  T->run[P2A].a.Qzero = zero_q ? g->Q : nullptr;
+  for (int ph = P1; ph <= P3; ++ph) SC_CUDA(launch_run(ph, T->run[ph], g->stream, true));
   return SC_OK;
 }
 
@@ -795,6 +922,41 @@ int tf32_error(sc_grid* g) {
   int e = 0;
   cudaMemcpy(&e, g->tf32->err, sizeof(int), cudaMemcpyDeviceToHost);
   return e;
+}
+
+int tf32_variant_count(int ph) { return (int)variants(ph).size(); }
+
+sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc) {
+  const Tf32Plan* T = g->tf32;
+  if (!T) return set_error(SC_ERR_UNSUPPORTED, "the grid has no split-TF32 solve");
+  static const char* names[4] = {"row DFT", "column DFT", "inverse column DFT", "inverse row DFT"};
+  for (int ph = 0; ph < 4; ++ph) {
+    const int k = T->run[ph].variant;
+    if (choice) choice[ph] = k;
+    if (desc) {
+      const Variant& v = variants(ph)[k];
+      char b[160];
+      std::snprintf(b, sizeof b, "%s%s: %d columns x split-K %d, %d stages, %d CTAs (%.1f us)", ph ? "; " : "",
+                    names[ph], v.nt, v.sk, v.stages, T->run[ph].grid, T->tuned_us[ph]);
+      *desc += b;
+    }
+  }
+  return SC_OK;
+}
+
+sc_status tf32_set_tiling(sc_grid* g, const int* choice) {
+  Tf32Plan* T = g->tf32;
+  if (!T) return set_error(SC_ERR_UNSUPPORTED, "the grid has no split-TF32 solve");
+  for (int ph = 0; ph < 4; ++ph) {
+    if (choice[ph] < 0) continue;
+    if (choice[ph] >= (int)variants(ph).size()) return set_error(SC_ERR_ARG, "tiling variant index out of range");
+    PhaseRun r;
+    sc_status st = make_run(g, ph, choice[ph], r);
+    if (st) return st;
+    T->run[ph] = r;
+    T->tuned_us[ph] = 0.f;
+  }
+  return SC_OK;
 }
 
 }  // namespace sc

@@ -27,7 +27,8 @@ PRECISION = {"fp64": 0, "tf32x3": 1}
 EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
-           "sc_batch_trace_enable", "sc_batch_trace_read",
+           "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
+           "sc_batch_set_solver_tiling",
            "sc_last_error")
 
 
@@ -92,6 +93,9 @@ def load():
     L.sc_batch_read.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(i64)]
     L.sc_batch_trace_enable.argtypes = [vp, ctypes.c_int]
     L.sc_batch_trace_read.argtypes = [vp, dp, dp, ctypes.POINTER(i64)]
+    L.sc_get_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p, ctypes.c_size_t]
+    L.sc_set_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.sc_batch_set_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -241,6 +245,19 @@ def trace_read(grid: Grid):
     return a.value, c.value, int(n.value)
 
 
+def get_solver_tiling(grid: Grid):
+    """-> ([variant index per phase], description) of a split-TF32 grid."""
+    c = (ctypes.c_int * 4)()
+    buf = ctypes.create_string_buffer(1024)
+    _check(load().sc_get_solver_tiling(grid.handle, c, buf, 1024))
+    return list(c), buf.value.decode()
+
+
+def set_solver_tiling(grid: Grid, choice):
+    """Force the split-TF32 solve's kernel variant per phase (-1 keeps one)."""
+    _check(load().sc_set_solver_tiling(grid.handle, (ctypes.c_int * 4)(*[int(v) for v in choice])))
+
+
 def moments_noalloc(state, out, stream=None):
     """Beam moments into the 14-element CUDA float64 tensor `out`, through the
     entry point that allocates no device memory (sc_moments_noalloc)."""
@@ -329,6 +346,28 @@ def batch_track_turns(batch: Batch, states, beams, lattices, n_turns: int, diag:
     return out
 
 
+def batch_track_turns_host(batch: Batch, host_states, beams, lattices, n_turns: int, device_states=None):
+    """Track bunches held in host memory: copy each bunch's six arrays to the
+    device, run sc_batch_track_turns, copy them back (in place)."""
+    import torch
+
+    keys = ("x", "px", "y", "py", "sigma", "psigma")
+    if device_states is None:
+        device_states = [{k: torch.empty(len(h[k]), dtype=torch.float64, device="cuda") for k in keys}
+                         for h in host_states]
+    for h, d in zip(host_states, device_states):
+        for k in keys:
+            src = torch.from_numpy(h[k]) if isinstance(h[k], np.ndarray) else h[k]
+            d[k].copy_(src, non_blocking=True)
+    batch_track_turns(batch, device_states, beams, lattices, n_turns)
+    for h, d in zip(host_states, device_states):
+        for k in keys:
+            dst = torch.from_numpy(h[k]) if isinstance(h[k], np.ndarray) else h[k]
+            dst.copy_(d[k], non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return host_states
+
+
 def batch_read(batch: Batch, b: int):
     """-> (Q uint64 [ny, nx], Ex, Ey, n_out) of bunch b's grid."""
     nx, ny = batch.grids[b][0], batch.grids[b][1]
@@ -339,6 +378,10 @@ def batch_read(batch: Batch, b: int):
     _check(load().sc_batch_read(batch.handle, int(b), Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data,
                                 ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
+
+
+def batch_set_solver_tiling(batch: Batch, choice):
+    _check(load().sc_batch_set_solver_tiling(batch.handle, (ctypes.c_int * 4)(*[int(v) for v in choice])))
 
 
 def batch_trace_enable(batch: Batch, enable: bool = True):

@@ -234,6 +234,48 @@ def test_solve_tf32_fields_within_1e5(n):
     assert np.array_equal(Ex, Ex2) and np.array_equal(Ey, Ey2)
 
 
+# candidates per phase of the split-TF32 solve (row DFT, column DFT, inverse column DFT, inverse row DFT)
+TILING_VARIANTS = (3, 5, 5, 4)
+
+
+@pytest.mark.parametrize("n,nz", [(64, 1), (128, 1), (256, 1), (128, 3), (64, 5)])
+def test_solve_tf32_every_tiling(n, nz):
+    """Every kernel variant the tuner may pick, phase by phase, on single and
+    stacked (sliced) grids: fields within 1e-5 of the oracle; variants that do
+    not fit the grid are refused."""
+    parts = synth.gaussian_bunch(200000, 5 + n + nz, 4e-3, 3e-3, 1e-4, 1e-4, sig_z=15.0)
+    grid = (n, n, -0.02, 0.02, -0.015, 0.015)
+    sl = None if nz == 1 else (nz, -60.0, 60.0)
+    g = sc.create_grid(*grid, precision="tf32x3", slices=sl)
+    og = oracle.Geometry(*grid)
+    if sl is None:
+        Qo, _ = oracle.deposit(og, parts["x"], parts["y"])
+        Exo, Eyo = oracle.solve(og, Qo, len(parts["x"]))
+    else:
+        Qo, _ = oracle.deposit_sliced(og, oracle.Slices(*sl), parts["x"], parts["y"], parts["sigma"])
+        Exo, Eyo = oracle.solve_sliced(og, Qo, len(parts["x"]))
+    tuned, desc = sc.get_solver_tiling(g)
+    assert all(0 <= v < c for v, c in zip(tuned, TILING_VARIANTS)) and "columns" in desc
+    tried = 0
+    for ph in range(4):
+        for k in range(TILING_VARIANTS[ph]):
+            choice = list(tuned)
+            choice[ph] = k
+            try:
+                sc.set_solver_tiling(g, choice)
+            except sc.ScError as e:
+                assert e.code == -1  # does not fit this grid
+                continue
+            tried += 1
+            sc.grid_write_charge(g, Qo, len(parts["x"]))
+            sc.solve(g)
+            _, Ex, Ey, _ = sc.grid_read(g)
+            assert rel_l2(Ex, Exo) < 1e-5 and rel_l2(Ey, Eyo) < 1e-5, (ph, k, rel_l2(Ex, Exo))
+    assert tried >= 12
+    with pytest.raises(sc.ScError):
+        sc.set_solver_tiling(g, [99, -1, -1, -1])
+
+
 def test_solve_tf32_point_charges():
     """Sparse charge in the corners: the worst case for relative field error."""
     grid = (128, 128, 0.0, 1.0, 0.0, 1.0)
