@@ -43,15 +43,14 @@ WORKLOADS = {
 }
 
 # FP64-pipe thread instructions per particle in kick_push_kernel (the turn
-# graph's variant), by segment content: measured with ncu
-# (smsp__sass_thread_inst_executed_op_{dfma,dadd,dmul} + conversions, floor and
-# compares via sm__inst_executed_pipe_fp64) on the bench workload; see the
-# roofline section of the design doc.  base = gather + kick + fused deposit.
-FP64_INST = {"base": 27.5, "drift": 12.2, "quad": 51.5, "sext": 5.0, "bend": 16.0, "rf": 30.0}
-# split-TF32 form: float32 gather (two float->double conversions + two fma for the kick)
-FP64_INST_BASE_F32 = 17.5
-# sliced grids: the slice index (one subtract, one multiply, one floor conversion) per locate
-FP64_INST_SLICE = 3.0
+# graph's variant), by segment content, from ncu's
+# sm__thread_inst_executed_pipe_fp64_pred_on per launch on the three segment
+# types of the bench ring (1e6 particles); base = gather + kick + fused deposit.
+FP64_INST = {"base": 18.1, "drift": 12.1, "quad": 51.0, "sext": 5.0, "bend": 16.0, "rf": 30.0}
+# split-TF32 form: float32 gather from the cached fixed-point weights
+FP64_INST_BASE_F32 = 8.8
+# sliced grids: the slice index (one subtract, one multiply; the floor is integer work) per locate
+FP64_INST_SLICE = 2.0
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -67,6 +66,8 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--cpu-kicks", type=int, default=24, help="oracle sample size in kicks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiling", default=None,
+                    help="force the split-TF32 solve's kernel variant per phase, e.g. 0,1,2,1 (default: tuned)")
     return ap.parse_args()
 
 
@@ -220,7 +221,17 @@ class SingleRun:
         import torch
         from paper_2010_11540_gb300 import sc
         dev = {k: torch.from_numpy(self.parts[k]).cuda() for k in KEYS}
-        return sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices), dev
+        g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
+        if precision == "tf32x3" and self.tiling:
+            sc.set_solver_tiling(g, self.tiling)
+        return g, dev
+
+    def tiling_desc(self, h):
+        from paper_2010_11540_gb300 import sc
+        if h[0].precision != "tf32x3":
+            return None
+        v, d = sc.get_solver_tiling(h[0])
+        return {"variants": v, "grid": d}
 
     def turns(self, h, n):
         from paper_2010_11540_gb300 import sc
@@ -244,6 +255,34 @@ class SingleRun:
 
     def close(self, h):
         h[0].close()
+
+    def deposit_roofline(self, h, flush, atom_peak, atom_conflict_free, reps=20):
+        """sc_deposit alone (the deposit kernel) on the workload's particles:
+        4 shared-memory u64 atomic adds per particle inside the grid, against
+        the probed rate of such atomics on random words of a 128 KB tile."""
+        import torch
+        from paper_2010_11540_gb300 import sc
+        g, dev = h
+        with torch.cuda.stream(self.stream):
+            out0 = sc.grid_read(g)[3]
+            sc.deposit(g, dev)
+            n_in = self.n - (sc.grid_read(g)[3] - out0)  # particles inside the grid (one deposit)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, c in ev:
+                flush.zero_()
+                a.record(self.stream)
+                sc.deposit(g, dev)
+                c.record(self.stream)
+            torch.cuda.synchronize()
+        ms = sorted(a.elapsed_time(c) for a, c in ev)[reps // 2]
+        atomics = 4 * n_in
+        return {"bound": "shared-atomics", "kernel": "deposit_kernel (stand-alone sc_deposit)",
+                "achieved": atomics / (ms * 1e-3) / 1e9, "peak": atom_peak / 1e9, "unit": "G shared-u64-atomics/s",
+                "frac": atomics / (ms * 1e-3) / atom_peak, "avg_launch_ms": ms, "atomics_per_launch": atomics,
+                "peak_source": "sc_probe_peaks: shared u64 atomicAdd on random words of a 128 KB table, "
+                               "measured in this run",
+                "peak_conflict_free": atom_conflict_free / 1e9,
+                "frac_of_conflict_free": atomics / (ms * 1e-3) / atom_conflict_free}
 
     def grid_desc(self):
         d = {"grid": [self.grid[0], self.grid[1]]}
@@ -272,7 +311,21 @@ class BatchRun:
         import torch
         from paper_2010_11540_gb300 import sc
         devs = [{k: torch.from_numpy(p[k]).cuda() for k in KEYS} for p, _, _, _ in self.bunches]
-        return sc.create_batch(self.grids, precision=precision, stream=self.stream), devs
+        B = sc.create_batch(self.grids, precision=precision, stream=self.stream)
+        if precision == "tf32x3" and self.tiling:
+            sc.batch_set_solver_tiling(B, self.tiling)
+        return B, devs
+
+    def tiling_desc(self, h):
+        from paper_2010_11540_gb300 import sc
+        if h[0].precision != "tf32x3":
+            return None
+        out = {}
+        for i, g in enumerate(self.grids):
+            key = f"{g[0]}x{g[1]}"
+            if key not in out:
+                out[key] = sc.batch_get_solver_tiling(h[0], i)[1]
+        return out
 
     def turns(self, h, n):
         from paper_2010_11540_gb300 import sc
@@ -318,6 +371,7 @@ def run_ours(args):
     sc.load()
     stream = torch.cuda.Stream()
     W = (BatchRun if args.config == "c4" else SingleRun)(args.config, rank, stream)
+    W.tiling = [int(v) for v in args.tiling.split(",")] if args.tiling else None
     n = W.n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
@@ -388,6 +442,11 @@ def run_ours(args):
                 "avg_launch_ms": kp_avg_ms, "fp64_inst_per_particle_kick": inst_per_kick,
                 "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
 
+    # ---------------- live machine probes and the stand-alone deposit (shared-atomic roofline)
+    atom_cf, atom_rand, fp64_probe = sc.probe_peaks(stream)
+    roofline["peak_probe_fp64_tinst"] = fp64_probe / 1e12
+    deposit = W.deposit_roofline(h, flush, atom_rand, atom_cf) if hasattr(W, "deposit_roofline") else None
+
     # ---------------- end to end: host buffers through the public API
     pinned = W.pinned()
     e2e_steps = max(2, args.steps // 2)
@@ -408,11 +467,12 @@ def run_ours(args):
                       f"{'sc_batch_track_turns' if args.config == 'c4' else 'sc_track_turns'} (CUDA graph)",
               "solve": "fp64 FFT convolution" if args.precision == "fp64" else "tf32x3 DFT GEMMs on tcgen05",
               "particles": n, **W.grid_desc(),
+              "solve_tiling": W.tiling_desc(h),
               "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-            "roofline": roofline, "e2e": e2e, "clocks": clk, "compare_form": compare,
+            "roofline": roofline, "roofline_deposit": deposit, "e2e": e2e, "clocks": clk, "compare_form": compare,
             "gpu_launches": args.steps * n_kicks * (W.n_classes * solve_kernels + 1),
             "wall_s_timed": wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -257,7 +257,9 @@ sc_status sc_batch_read(sc_batch *B, int b, uint64_t *Q, double *Ex, double *Ey,
  * time is the batched launch covering every bunch; solve time covers every
  * grid class). */
 sc_status sc_batch_trace_enable(sc_batch *B, int enable);
-/* sc_set_solver_tiling for every grid class of the batch (split-TF32 batches). */
+/* sc_get_solver_tiling of bunch b's grid class; sc_set_solver_tiling for
+ * every grid class of the batch (split-TF32 batches). */
+sc_status sc_batch_get_solver_tiling(sc_batch *B, int b, int *choice, char *desc, size_t n);
 sc_status sc_batch_set_solver_tiling(sc_batch *B, const int *choice);
 sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
@@ -282,6 +284,16 @@ sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_m
  * Errors: SC_ERR_ARG (NULL, n <= 0), SC_ERR_OVERFLOW (n > SC_MOMENTS_NOALLOC_MAX_N),
  * SC_ERR_CUDA. */
 sc_status sc_moments_noalloc(const sc_particles *p, double *out, void *stream);
+
+/* Machine probes (no counterpart in the paper): the throughput of
+ * shared-memory 64-bit atomic adds (the CIC deposit's unit of work), once
+ * conflict-free (each warp on 32 consecutive words) and once on random words
+ * of a 128 KB table (the access pattern of a deposit into a 128 x 128 tile),
+ * and of FP64 fused multiply-adds (the pipe that bounds the push), on the
+ * current device, each timed over five launches on `stream` (synchronous).
+ * Outputs may be NULL (not all).  Used as live roofline denominators. */
+sc_status sc_probe_peaks(double *shared_atomics_per_s, double *random_atomics_per_s, double *fp64_inst_per_s,
+                         void *stream);
 
 /* Text of the last error on the calling thread (always NUL-terminated). */
 sc_status sc_last_error(char *buf, size_t n);

@@ -498,6 +498,12 @@ sc_status sc_batch_read(sc_batch* B, int b, uint64_t* Q, double* Ex, double* Ey,
   return SC_OK;
 }
 
+sc_status sc_batch_get_solver_tiling(sc_batch* B, int b, int* choice, char* desc, size_t n) {
+  if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
+  if (b < 0 || b >= B->n_bunches) return set_error(SC_ERR_ARG, "bunch index out of range");
+  return sc_get_solver_tiling(B->cls[B->cls_of[b]], choice, desc, n);
+}
+
 sc_status sc_batch_set_solver_tiling(sc_batch* B, const int* choice) {
   if (!B || !choice) return set_error(SC_ERR_ARG, "batch or choice is NULL");
   SC_CUDA(cudaStreamSynchronize(B->stream));

@@ -6,7 +6,9 @@ namespace sc {
 
 namespace {
 
-constexpr int kDepThreads = 512;
+// 1024 threads: the shared-memory atomics of random cells are latency-bound
+// (bank conflicts), more warps per SM hide more of it (measured).
+constexpr int kDepThreads = 1024;
 
 template <bool TILE>
 __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __restrict__ x,
@@ -26,15 +28,32 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __re
   // one contiguous chunk per block (a sigma-sorted bunch keeps a block in one slice)
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t p_end = min(n, (int64_t)(blockIdx.x + 1) * chunk);
-  for (int64_t p = (int64_t)blockIdx.x * chunk + threadIdx.x; p < p_end; p += blockDim.x) {
+  const bool sliced = g.nz > 1;
+  // the next particle's coordinates are loaded before this one's atomics
+  int64_t p = (int64_t)blockIdx.x * chunk + threadIdx.x;
+  double xn = 0.0, yn = 0.0, sn = 0.0;
+  if (p < p_end) {
+    xn = __ldg(x + p);
+    yn = __ldg(y + p);
+    if (sliced) sn = __ldg(sg + p);
+  }
+  for (; p < p_end; p += blockDim.x) {
+    const double xc = xn, yc = yn, sc_ = sn;
+    const int64_t q = p + blockDim.x;
+    if (q < p_end) {
+      xn = __ldg(x + q);
+      yn = __ldg(y + q);
+      if (sliced) sn = __ldg(sg + q);
+    }
     double fx, fy;
-    const int cell = locate(g, __ldg(x + p), __ldg(y + p), __ldg(sg + p), fx, fy);
+    int2 a;
+    const int cell = locate<false>(g, xc, yc, sc_, a, fx, fy);
     if (cell < 0)
       ++out;
     else if (TILE)
-      deposit_tiled(tile, &tile_k, Q, g, cell, fx, fy);
+      deposit_tiled(tile, &tile_k, Q, g, cell, a);
     else
-      deposit4(Q, g.nx, cell, fx, fy);
+      deposit4(Q, g.nx, cell, a);
   }
   count_out(out, n_out);
   if (TILE) {

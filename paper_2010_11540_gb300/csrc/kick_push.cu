@@ -48,9 +48,10 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           fy = (float)a.y * (1.0f / 1048576.0f);
         } else {
           double dx, dy;
-          cell = locate(P.gk, s.x, s.y, s.sg, dx, dy);
-          fx = (float)dx;
-          fy = (float)dy;
+          int2 a;
+          cell = locate<false>(P.gk, s.x, s.y, s.sg, a, dx, dy);
+          fx = (float)a.x * (1.0f / 1048576.0f);
+          fy = (float)a.y * (1.0f / 1048576.0f);
         }
         if (cell >= 0) {
           const float2* e = P.E32 + cell;
@@ -69,7 +70,8 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           fx = f.x;
           fy = f.y;
         } else {
-          cell = locate(P.gk, s.x, s.y, s.sg, fx, fy);
+          int2 a;
+          cell = locate<true>(P.gk, s.x, s.y, s.sg, a, fx, fy);
         }
         if (cell >= 0) {
           const double2* e = P.E + cell;
@@ -105,13 +107,18 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
       P.psc[4 * n + p] = k.qi;
     }
     if (P.do_deposit) {
-      double fx, fy;
-      const int cell = locate(P.gd, s.x, s.y, s.sg, fx, fy);
+      double fx = 0.0, fy = 0.0;
       int2 a = make_int2(0, 0);
-      if (cell >= 0)
-        a = use_tile ? deposit_tiled(tile, tile_k, P.Q, P.gd, cell, fx, fy) : deposit4(P.Q, P.gd.nx, cell, fx, fy);
-      else
+      const int cell = locate<!F32>(P.gd, s.x, s.y, s.sg, a, fx, fy);
+      if (cell >= 0) {
+        if (use_tile)
+          deposit_tiled(tile, tile_k, P.Q, P.gd, cell, a);
+        else
+          deposit4(P.Q, P.gd.nx, cell, a);
+      } else {
         ++out;
+        a = make_int2(0, 0);
+      }
       if (CACHE) {
         P.cell[p] = cell;
         if (F32)

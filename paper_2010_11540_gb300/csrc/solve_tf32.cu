@@ -778,7 +778,7 @@ sc_status tf32_tune(sc_grid* g) {
       r.a.scale = 1.f;
       cudaError_t e = launch_run(ph, r, g->stream, false);  // warm-up
       float ms = 0.f;
-      constexpr int reps = 3;
+      constexpr int reps = 8;
       if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
       for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch_run(ph, r, g->stream, false);
       if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);

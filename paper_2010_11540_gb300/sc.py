@@ -28,7 +28,7 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
-           "sc_batch_set_solver_tiling",
+           "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks",
            "sc_last_error")
 
 
@@ -96,6 +96,9 @@ def load():
     L.sc_get_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p, ctypes.c_size_t]
     L.sc_set_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.sc_batch_set_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.sc_batch_get_solver_tiling.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p,
+                                             ctypes.c_size_t]
+    L.sc_probe_peaks.argtypes = [dp, dp, dp, vp]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -258,6 +261,14 @@ def set_solver_tiling(grid: Grid, choice):
     _check(load().sc_set_solver_tiling(grid.handle, (ctypes.c_int * 4)(*[int(v) for v in choice])))
 
 
+def probe_peaks(stream=None):
+    """-> (conflict-free shared u64 atomics/s, random-word shared u64 atomics/s,
+    FP64 FMA instructions/s) measured on the current device."""
+    a, r, f = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().sc_probe_peaks(ctypes.byref(a), ctypes.byref(r), ctypes.byref(f), _stream_handle(stream)))
+    return a.value, r.value, f.value
+
+
 def moments_noalloc(state, out, stream=None):
     """Beam moments into the 14-element CUDA float64 tensor `out`, through the
     entry point that allocates no device memory (sc_moments_noalloc)."""
@@ -378,6 +389,14 @@ def batch_read(batch: Batch, b: int):
     _check(load().sc_batch_read(batch.handle, int(b), Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data,
                                 ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
+
+
+def batch_get_solver_tiling(batch: Batch, b: int):
+    """-> ([variant index per phase], description) of bunch b's grid class."""
+    c = (ctypes.c_int * 4)()
+    buf = ctypes.create_string_buffer(1024)
+    _check(load().sc_batch_get_solver_tiling(batch.handle, int(b), c, buf, 1024))
+    return list(c), buf.value.decode()
 
 
 def batch_set_solver_tiling(batch: Batch, choice):
