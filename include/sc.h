@@ -38,7 +38,7 @@ typedef int sc_status;
 #define SC_ERR_ARG (-1)         /* bad argument (null, size, geometry)        */
 #define SC_ERR_CUDA (-2)        /* a CUDA runtime call failed                 */
 #define SC_ERR_OOM (-3)         /* device allocation failed                   */
-#define SC_ERR_OVERFLOW (-4)    /* more particles than the int64 charge grid can hold */
+#define SC_ERR_OVERFLOW (-4)    /* more particles than the 64-bit charge grid can hold */
 #define SC_ERR_TIMEOUT (-5)     /* a bounded device wait ran out              */
 #define SC_ERR_NAN (-6)         /* non-finite particle state seen             */
 #define SC_ERR_UNSUPPORTED (-7) /* grid size / precision not supported        */

@@ -1,5 +1,5 @@
 // Stand-alone CIC charge deposition (Sec. IV-A): per-block shared-memory
-// int64 tile, flushed once per block into the global grid.
+// uint64 tile, flushed once per block into the global grid.
 #include "cic.cuh"
 
 namespace sc {

@@ -1,7 +1,7 @@
 // Fused space-charge step for one location: bilinear field gather + kick
 // (Sec. IV kick equation), push through the segment's elements (Sec. III),
 // and CIC deposit of the new positions (Sec. IV-A) into a per-block
-// shared-memory int64 tile flushed once per block.  One thread per particle,
+// shared-memory uint64 tile flushed once per block.  One thread per particle,
 // persistent grid-stride loop over SoA float64 state.
 #include <cmath>
 

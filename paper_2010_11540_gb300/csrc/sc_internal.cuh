@@ -94,7 +94,7 @@ struct KPParams {
   // deposit
   int do_deposit;
   GridGeom gd;
-  unsigned long long* Q;      // int64 charge of the deposit grid
+  unsigned long long* Q;      // uint64 charge of the deposit grid
   unsigned long long* n_out;  // running count of particles outside the deposit grid
   // beam constants
   double beta0_sq, inv_gamma0_sq;
