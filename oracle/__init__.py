@@ -141,10 +141,10 @@ def kick_sliced(g: Geometry, zs: Slices, st, Ex, Ey, kl):
                           _d(np.ascontiguousarray(Ex)), _d(np.ascontiguousarray(Ey)), kl)
 
 
-def solve_sliced(g: Geometry, Q, n_total, method="fft"):
+def solve_sliced(g: Geometry, Q, n_total, method="fft", boundary="open"):
     """Per-slice fields (Ex, Ey) [nz, ny, nx], each slice's charge normalised by
     the total macroparticle count."""
-    out = [solve(g, Q[k], n_total, method) for k in range(Q.shape[0])]
+    out = [solve(g, Q[k], n_total, method, boundary) for k in range(Q.shape[0])]
     return np.stack([e[0] for e in out]), np.stack([e[1] for e in out])
 
 
@@ -201,9 +201,58 @@ def fields(g: Geometry, phi_ext):
     return Ex, Ey
 
 
-def solve(g: Geometry, Q, n_total, method="fft"):
-    """Charge grid -> node fields (Ex, Ey), normalised per unit line charge."""
+def potential_pipe(g: Geometry, q):
+    """Potential inside a rectangular conducting pipe whose walls are the
+    grid's outer nodes (Sec. IV-B: Eqs. poisson2D, boundary, disc, extension,
+    solution), on nodes i = -1..nx, j = -1..ny.
+
+    The 5-point discretisation (Eq. disc) holds on the m_x x m_y interior
+    nodes (m = n - 2), with phi = 0 on the walls (Eq. boundary).  Its right-hand
+    side is the density of the normalised line charge with the sign and 2 pi
+    of the free-space Green function -ln r that the open solve uses
+    (lap(-ln r) = -2 pi delta): f = -2 pi q / (hx hy).  The paper's steps:
+    F = odd extension of f to period 2(m+1) along both axes (Eq. extension);
+    2-D DFT of F (numpy FFT, the library step); division by
+    -4 (sin^2(p pi / 2(m+1)) / hx^2 + sin^2(q pi / 2(m+1)) / hy^2), indices
+    p, q = 0 .. 2m+1 (the paper prints 1..N: a garble; the p = q = 0 term of an
+    odd extension is 0 and stays 0); inverse 2-D DFT; V at the interior nodes
+    is phi.  The ring of nodes just outside the walls takes the odd extension
+    (phi(-1) = -phi(1)), so centred differences give the field at the walls."""
+    mx, my = g.nx - 2, g.ny - 2
+    f = -2.0 * np.pi * np.asarray(q, dtype=np.float64)[1:-1, 1:-1] / (g.hx * g.hy)
+
+    def odd(a, axis):
+        z = np.zeros_like(np.take(a, [0], axis=axis))
+        return np.concatenate([z, a, z, -np.flip(a, axis=axis)], axis=axis)
+
+    F = odd(odd(f, 1), 0)  # [2(my+1), 2(mx+1)]
+    P = 2 * (mx + 1)
+    Qn = 2 * (my + 1)
+    sp = np.sin(np.arange(P) * np.pi / P) ** 2 / g.hx ** 2
+    sq = np.sin(np.arange(Qn) * np.pi / Qn) ** 2 / g.hy ** 2
+    den = -4.0 * (sq[:, None] + sp[None, :])
+    Fh = np.fft.fft2(F)
+    Vh = np.zeros_like(Fh)
+    nz = den != 0.0
+    Vh[nz] = Fh[nz] / den[nz]
+    V = np.fft.ifft2(Vh).real
+    phi = np.zeros((g.ny + 2, g.nx + 2))
+    phi[2:-2, 2:-2] = V[1:my + 1, 1:mx + 1]
+    # odd extension across the walls (rows/columns 1 and n hold the walls, 0 and n+1 the ring)
+    phi[:, 0] = -phi[:, 2]
+    phi[:, -1] = -phi[:, -3]
+    phi[0, :] = -phi[2, :]
+    phi[-1, :] = -phi[-3, :]
+    return phi
+
+
+def solve(g: Geometry, Q, n_total, method="fft", boundary="open"):
+    """Charge grid -> node fields (Ex, Ey), normalised per unit line charge.
+    boundary "open": free space (Hockney); "pipe": conducting rectangular pipe
+    on the grid's outer nodes (Sec. IV-B)."""
     q = normalise(Q, n_total)
+    if boundary == "pipe":
+        return fields(g, potential_pipe(g, q))
     phi = potential_fft(g, q) if method == "fft" else potential_direct(g, q)
     return fields(g, phi)
 
@@ -269,13 +318,15 @@ def segments(lattice):
     return head, kicks
 
 
-def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None, slices=None):
+def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None, slices=None,
+          boundary="open"):
     """Track `st` (modified in place) for n_turns with the PIC loop of Sec. I.
     Each space-charge location: deposit -> solve -> kick (L since the previous
     location) -> push to the next location.  Returns the number of kicks done.
     `diag(turn, st)` is called at the start of every turn.  With `slices`
     (a Slices), every slice has its own grid and b["n_lambda"] is the line
-    density of a slice that held the whole bunch (N / dz)."""
+    density of a slice that held the whole bunch (N / dz).  boundary "pipe":
+    the conducting-pipe solve of Sec. IV-B on the grid's outer nodes."""
     head, kicks = segments(lattice)
     K = kick_strength(b)
     n = len(st["x"])
@@ -289,11 +340,11 @@ def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kic
                 return done
             if slices is None:
                 Q, _ = deposit(g, st["x"], st["y"])
-                Ex, Ey = solve(g, Q, n, method)
+                Ex, Ey = solve(g, Q, n, method, boundary)
                 kick(g, st, Ex, Ey, K * L)
             else:
                 Q, _ = deposit_sliced(g, slices, st["x"], st["y"], st["sigma"])
-                Ex, Ey = solve_sliced(g, Q, n, method)
+                Ex, Ey = solve_sliced(g, Q, n, method, boundary)
                 kick_sliced(g, slices, st, Ex, Ey, K * L)
             push(st, seg, b)
             done += 1
