@@ -46,6 +46,10 @@ typedef int sc_status;
 /* Poisson-solve arithmetic (sc_create_grid `precision`). */
 #define SC_SOLVE_FP64 0   /* float64 FFT convolution (the plain form)           */
 #define SC_SOLVE_TF32X3 1 /* DFT as tcgen05 GEMMs, 3-term split TF32, FP32 acc. */
+/* Conducting rectangular pipe (Sec. IV-B, Dirichlet walls on the grid's outer
+ * nodes), float64 sine transforms by FFT; nx - 1, ny - 1 powers of two in
+ * 8..512.  The potential is kept (sc_grid_read_potential). */
+#define SC_SOLVE_PIPE_FP64 2
 
 /* Element types (sc_element.type). */
 #define SC_DRIFT 0 /* exact drift, Sec. III-A                                  */
@@ -92,7 +96,8 @@ typedef struct {
  * (Hockney zero-padded) Poisson solver of the given precision.  Builds the
  * Green's-function spectra on the device (synchronous on `stream`).
  * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {64, 128, 256}
- * for SC_SOLVE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
+ * for SC_SOLVE_TF32X3; nx - 1, ny - 1 powers of two in 8..512 for
+ * SC_SOLVE_PIPE_FP64.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
  * SC_ERR_OOM, SC_ERR_CUDA.  *out is set only on success. */
 sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
                          double ymax, int precision, void *stream);
@@ -166,6 +171,13 @@ sc_status sc_grid_read(sc_grid *g, uint64_t *Q, double *Ex, double *Ey, int64_t 
 /* Synchronous upload of a charge grid Q (host, n_slices*ny*nx uint64) and the
  * particle count N used to normalise it, e.g. to solve a given charge. */
 sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particles);
+
+/* Synchronous copy-out of a pipe grid's potential (n_slices*ny*nx float64,
+ * row-major, 0 on the walls): normalised like the fields (per unit line
+ * charge, -ln r normalisation), i.e. phi solves lap phi = -2 pi q / (hx hy).
+ * Errors: SC_ERR_ARG (NULL), SC_ERR_UNSUPPORTED (not a SC_SOLVE_PIPE_FP64
+ * grid), SC_ERR_CUDA. */
+sc_status sc_grid_read_potential(sc_grid *g, double *phi);
 
 /* Per-particle tunes, Sec. V (the betatron tune of a particle is its one-turn
  * phase advance).  Arms grid g: every turn sc_track_turns then runs ends with

@@ -158,6 +158,7 @@ void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, 
 
 sc_status solve_dispatch(sc_grid* g, bool zero_q) {
   if (g->precision == SC_SOLVE_TF32X3) return tf32_solve(g, zero_q);
+  if (g->precision == SC_SOLVE_PIPE_FP64) return pipe_solve(g, zero_q);
   return fft64_solve(g, zero_q);
 }
 
@@ -174,7 +175,7 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   if (!(xmax > xmin) || !(ymax > ymin) || !std::isfinite(xmin) || !std::isfinite(xmax) || !std::isfinite(ymin) ||
       !std::isfinite(ymax))
     return set_error(SC_ERR_ARG, "grid extent must be finite with xmax > xmin, ymax > ymin");
-  if (precision != SC_SOLVE_FP64 && precision != SC_SOLVE_TF32X3)
+  if (precision != SC_SOLVE_FP64 && precision != SC_SOLVE_TF32X3 && precision != SC_SOLVE_PIPE_FP64)
     return set_error(SC_ERR_UNSUPPORTED, "unknown solve precision");
   sc_grid* g = new (std::nothrow) sc_grid();
   if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
@@ -237,7 +238,8 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   g->dep_blocks = deposit_blocks_for(tile ? tile_bytes : 0, tile);
   g->kp_blocks = kick_push_blocks_for(tile ? tile_bytes : 0, tile);
   g->kp_blocks_plain = kick_push_blocks_for(0, false);
-  st = (precision == SC_SOLVE_TF32X3) ? tf32_create(g) : fft64_create(g);
+  st = (precision == SC_SOLVE_TF32X3) ? tf32_create(g) : (precision == SC_SOLVE_PIPE_FP64) ? pipe_create(g)
+                                                                                             : fft64_create(g);
   if (st == SC_OK) {
     e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) st = cuda_error(e, "sc_create_grid");
@@ -279,6 +281,8 @@ sc_status sc_destroy_grid(sc_grid* g) {
   destroy_plan(g->track);
   if (g->precision == SC_SOLVE_TF32X3)
     tf32_destroy(g);
+  else if (g->precision == SC_SOLVE_PIPE_FP64)
+    pipe_destroy(g);
   else
     fft64_destroy(g);
   cudaFree(g->Q);
@@ -364,6 +368,14 @@ sc_status sc_grid_read(sc_grid* g, uint64_t* Q, double* Ex, double* Ey, int64_t*
     *n_out = (int64_t)v;
   }
   if (tf32_error(g)) return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
+  return SC_OK;
+}
+
+sc_status sc_grid_read_potential(sc_grid* g, double* phi) {
+  if (!g || !phi) return set_error(SC_ERR_ARG, "grid or phi is NULL");
+  if (g->precision != SC_SOLVE_PIPE_FP64) return set_error(SC_ERR_UNSUPPORTED, "only pipe grids keep the potential");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  SC_CUDA(cudaMemcpy(phi, g->pipe.phi, (size_t)g->nx * g->ny * g->nstack * sizeof(double), cudaMemcpyDeviceToHost));
   return SC_OK;
 }
 

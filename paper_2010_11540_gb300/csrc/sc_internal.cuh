@@ -124,6 +124,16 @@ struct Fft64Plan {
   double* Sy;            // imaginary part of the Ey kernel spectrum [My][nx+1]
 };
 
+// Solve scratch for the conducting-pipe form (solve_pipe64.cu).
+struct PipePlan {
+  double2* twx;      // (nx-1) twiddles exp(-2 pi i t / 2(nx-1))
+  double2* twy;      // (ny-1) twiddles
+  double* inv_lam;   // [ny][nx]: 1 / lambda_pq at (q, p), interior indices
+  double* T1;        // [nstack][ny][nx] row sine transforms
+  double* T2;        // [nstack][ny][nx] after the column transforms
+  double* phi;       // [nstack][ny][nx] potential (0 on the walls)
+};
+
 struct Tf32Plan;  // tensor-core DFT-GEMM form (solve_tf32.cu)
 
 struct TrackPlan;  // captured turn graph (api.cu)
@@ -151,6 +161,7 @@ struct sc_grid {
   unsigned long long* n_out;  // device counter (one per stacked grid in a batch class)
   int64_t n_particles;        // particle count of the last deposit (normalises Q)
   sc::Fft64Plan fft;
+  sc::PipePlan pipe;
   sc::Tf32Plan* tf32;
   sc::TrackPlan* track;
   int trace;                   // record per-phase events in captured turns
@@ -184,6 +195,10 @@ sc_status fft64_create(sc_grid* g);
 void fft64_destroy(sc_grid* g);
 // zero_q: also clear the charge grid once it has been read (for the next deposit)
 sc_status fft64_solve(sc_grid* g, bool zero_q);
+// solve_pipe64.cu
+sc_status pipe_create(sc_grid* g);
+void pipe_destroy(sc_grid* g);
+sc_status pipe_solve(sc_grid* g, bool zero_q);
 // solve_tf32.cu
 sc_status tf32_create(sc_grid* g);
 void tf32_destroy(sc_grid* g);

@@ -23,12 +23,12 @@ LIB_PATH = os.path.join(_PKG, "libsc.so")
 SC_OK = 0
 ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVERFLOW",
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "tf32x3": 1}
+PRECISION = {"fp64": 0, "tf32x3": 1, "pipe_fp64": 2}
 EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
-           "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks",
+           "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
            "sc_last_error")
 
 
@@ -99,6 +99,7 @@ def load():
     L.sc_batch_get_solver_tiling.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p,
                                              ctypes.c_size_t]
     L.sc_probe_peaks.argtypes = [dp, dp, dp, vp]
+    L.sc_grid_read_potential.argtypes = [vp, vp]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -220,6 +221,14 @@ def grid_read(grid: Grid):
     n_out = ctypes.c_int64(0)
     _check(load().sc_grid_read(grid.handle, Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data, ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
+
+
+def grid_read_potential(grid: Grid):
+    """-> phi [ny, nx] (or [n_slices, ny, nx]) of a conducting-pipe grid."""
+    shape = (grid.ny, grid.nx) if grid.nz == 1 else (grid.nz, grid.ny, grid.nx)
+    phi = np.zeros(shape)
+    _check(load().sc_grid_read_potential(grid.handle, phi.ctypes.data))
+    return phi
 
 
 def tune_setup(grid: Grid, state, twiss, acc):

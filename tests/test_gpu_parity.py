@@ -513,3 +513,60 @@ def test_sliced_deposit_edges():
         sc.create_grid(8, 8, 0.0, 1.0, 0.0, 1.0, slices=(4, 1.0, 1.0))
     with pytest.raises(sc.ScError):
         sc.create_grid(4096, 4096, 0.0, 1.0, 0.0, 1.0, slices=(32, -1.0, 1.0))
+
+
+# ------------------------------------------------------------------ conducting pipe (Sec. IV-B)
+@pytest.mark.parametrize("grid", [(129, 129, -0.02, 0.02, -0.015, 0.015), (65, 33, -0.012, 0.009, -0.007, 0.008),
+                                  (17, 17, -0.01, 0.01, -0.01, 0.01)])
+def test_solve_pipe_matches_oracle(grid):
+    parts = synth.gaussian_bunch(300000, 17 + grid[0], 3e-3, 2.5e-3, 1e-4, 1e-4)
+    parts["x"] += 1.5e-3  # off centre: the walls act unevenly
+    g = sc.create_grid(*grid, precision="pipe_fp64")
+    og = oracle.Geometry(*grid)
+    Qo, _ = oracle.deposit(og, parts["x"], parts["y"])
+    sc.grid_write_charge(g, Qo, len(parts["x"]))
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    phi = sc.grid_read_potential(g)
+    Exo, Eyo = oracle.solve(og, Qo, len(parts["x"]), boundary="pipe")
+    phio = oracle.potential_pipe(og, oracle.normalise(Qo, len(parts["x"])))[1:-1, 1:-1]
+    assert rel_l2(Ex, Exo) < 1e-12 and rel_l2(Ey, Eyo) < 1e-12, (rel_l2(Ex, Exo), rel_l2(Ey, Eyo))
+    assert rel_l2(phi, phio) < 1e-12
+    assert not phi[0].any() and not phi[-1].any() and not phi[:, 0].any() and not phi[:, -1].any()
+
+
+def test_solve_pipe_sliced():
+    parts, b, _, lat = synth.workload("c5", n=400000)
+    grid = (129, 129) + synth.grid_extent(4e-3, 3e-3)
+    sl = (5, -60.0, 60.0)
+    g = sc.create_grid(*grid, precision="pipe_fp64", slices=sl)
+    og, zs = oracle.Geometry(*grid), oracle.Slices(*sl)
+    Qo, _ = oracle.deposit_sliced(og, zs, parts["x"], parts["y"], parts["sigma"])
+    sc.grid_write_charge(g, Qo, len(parts["x"]))
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    Exo, Eyo = oracle.solve_sliced(og, Qo, len(parts["x"]), boundary="pipe")
+    for k in range(5):
+        assert rel_l2(Ex[k], Exo[k]) < 1e-12 and rel_l2(Ey[k], Eyo[k]) < 1e-12, k
+
+
+def test_track_pipe_one_turn():
+    """2e5 particles, one turn of the c2 ring, fields of a conducting pipe at
+    +-5 sigma on a 129 x 129 grid, against the oracle."""
+    parts, b, _, lat = synth.workload("c2", n=200000)
+    grid = (129, 129) + synth.grid_extent(4e-3, 3e-3)
+    g = sc.create_grid(*grid, precision="pipe_fp64")
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(oracle.Geometry(*grid), ref, b, lat, 1, boundary="pipe")
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+
+
+@pytest.mark.parametrize("n", [128, 7, 1025])
+def test_pipe_unsupported_size(n):
+    with pytest.raises(sc.ScError) as e:
+        sc.create_grid(n, 129, -1.0, 1.0, -1.0, 1.0, precision="pipe_fp64")
+    assert e.value.code in (-7, -1)
