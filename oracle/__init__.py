@@ -65,6 +65,10 @@ def lib():
         L.orc_kick_sliced.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, ctypes.c_double]
+        L.orc_kick_long.restype = None
+        L.orc_kick_long.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double]
         L.orc_green_self.restype = ctypes.c_double
         L.orc_green_self.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_green_cyclic.restype = None
@@ -139,6 +143,20 @@ def kick_sliced(g: Geometry, zs: Slices, st, Ex, Ey, kl):
     lib().orc_kick_sliced(len(st["x"]), _d(st["x"]), _d(st["y"]), _d(st["sigma"]), _d(st["px"]), _d(st["py"]),
                           g.nx, g.ny, g.xmin, g.ymin, g.inv_hx, g.inv_hy, zs.nz, zs.zmin, zs.inv_dz,
                           _d(np.ascontiguousarray(Ex)), _d(np.ascontiguousarray(Ey)), kl)
+
+
+def potential_sliced_pipe(g: Geometry, Q, n_total):
+    """Node potentials [nz, ny, nx] of every slice in the conducting pipe
+    (each slice's charge normalised by the total count)."""
+    return np.stack([potential_pipe(g, normalise(Q[k], n_total))[1:-1, 1:-1] for k in range(Q.shape[0])])
+
+
+def kick_long(g: Geometry, zs: Slices, st, phi, klz):
+    """Longitudinal kick of Sec. IV on sliced potentials (see orc_kick_long);
+    klz = K gamma0 L / (2 dz)."""
+    lib().orc_kick_long(len(st["x"]), _d(st["x"]), _d(st["y"]), _d(st["sigma"]), _d(st["psigma"]), g.nx, g.ny,
+                        g.xmin, g.ymin, g.inv_hx, g.inv_hy, zs.nz, zs.zmin, zs.inv_dz,
+                        _d(np.ascontiguousarray(phi, dtype=np.float64)), klz)
 
 
 def solve_sliced(g: Geometry, Q, n_total, method="fft", boundary="open"):
@@ -319,14 +337,18 @@ def segments(lattice):
 
 
 def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None, slices=None,
-          boundary="open"):
+          boundary="open", longitudinal=False):
     """Track `st` (modified in place) for n_turns with the PIC loop of Sec. I.
     Each space-charge location: deposit -> solve -> kick (L since the previous
     location) -> push to the next location.  Returns the number of kicks done.
     `diag(turn, st)` is called at the start of every turn.  With `slices`
     (a Slices), every slice has its own grid and b["n_lambda"] is the line
     density of a slice that held the whole bunch (N / dz).  boundary "pipe":
-    the conducting-pipe solve of Sec. IV-B on the grid's outer nodes."""
+    the conducting-pipe solve of Sec. IV-B on the grid's outer nodes.
+    longitudinal (sliced pipe grids): also the longitudinal kick of Sec. IV,
+    after the transverse one, from the same positions."""
+    if longitudinal and (slices is None or boundary != "pipe"):
+        raise ValueError("the longitudinal kick needs sliced grids in a conducting pipe")
     head, kicks = segments(lattice)
     K = kick_strength(b)
     n = len(st["x"])
@@ -345,7 +367,12 @@ def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kic
             else:
                 Q, _ = deposit_sliced(g, slices, st["x"], st["y"], st["sigma"])
                 Ex, Ey = solve_sliced(g, Q, n, method, boundary)
+                if longitudinal:
+                    phi = potential_sliced_pipe(g, Q, n)
+                    klz = K * b["gamma0"] * L / (2.0 * slices.dz)
                 kick_sliced(g, slices, st, Ex, Ey, K * L)
+                if longitudinal:
+                    kick_long(g, slices, st, phi, klz)
             push(st, seg, b)
             done += 1
     return done

@@ -204,6 +204,49 @@ void orc_kick_sliced(int64_t n, const double *x, const double *y, const double *
   }
 }
 
+/* ---------------------------------------------------------------------
+ * Longitudinal space-charge kick, Sec. IV (longitudinal kick equation):
+ *   dps = -(e / (m gamma0^2 beta0^2 c^2)) u dlambda/dz L.
+ * In the normalisation of the transverse kick, lambda(z) u(x, y) is
+ * N_lambda Phi_k(x, y), Phi_k the potential of slice k (its charge n_k/N
+ * of a slice holding the whole bunch, -ln r normalisation), so
+ *   dps = -(K gamma0) L dPhi/dz,   K gamma0 = 2 r_p N_lambda / (beta0^2 gamma0^2).
+ * dPhi/dz is the centred difference of the neighbouring slices at the
+ * particle's (x, y): (Phi_{k+1} - Phi_{k-1}) / (2 dz), Phi = 0 beyond the
+ * first and the last slice (no charge there).  For a bunch whose transverse
+ * shape does not change along z (the paper's assumption) Phi_k = lambda_k u and
+ * this is the paper's u dlambda/dz.  Phi at the particle: bilinear, with the
+ * cell and float64 fractions of the transverse kick.  klz = K gamma0 L / (2 dz).
+ * phi holds nz grids [k][j][i] of node potentials.
+ * ------------------------------------------------------------------- */
+void orc_kick_long(int64_t n, const double *x, const double *y, const double *sg, double *ps, int nx, int ny,
+                   double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin, double inv_dz,
+                   const double *phi, double klz) {
+  int64_t cells = (int64_t)nx * ny;
+  for (int64_t p = 0; p < n; ++p) {
+    int k = orc_slice(sg[p], nz, zmin, inv_dz);
+    double xi = (x[p] - xmin) * inv_hx;
+    double eta = (y[p] - ymin) * inv_hy;
+    if (k < 0 || !(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) continue;
+    double fi = floor(xi), fj = floor(eta);
+    int i = (int)fi, j = (int)fj;
+    double fx = xi - fi, fy = eta - fj;
+    double w00 = (1.0 - fx) * (1.0 - fy), w10 = fx * (1.0 - fy);
+    double w01 = (1.0 - fx) * fy, w11 = fx * fy;
+    int64_t c = (int64_t)j * nx + i;
+    double up = 0.0, dn = 0.0;
+    if (k + 1 < nz) {
+      const double *f = phi + (int64_t)(k + 1) * cells + c;
+      up = w00 * f[0] + w10 * f[1] + w01 * f[nx] + w11 * f[nx + 1];
+    }
+    if (k > 0) {
+      const double *f = phi + (int64_t)(k - 1) * cells + c;
+      dn = w00 * f[0] + w10 * f[1] + w01 * f[nx] + w11 * f[nx + 1];
+    }
+    ps[p] -= klz * (up - dn);
+  }
+}
+
 void orc_kick(int64_t n, const double *x, const double *y, double *px, double *py, int nx, int ny, double xmin,
               double ymin, double inv_hx, double inv_hy, const double *Ex, const double *Ey, double kl) {
   orc_kick_sliced(n, x, y, 0, px, py, nx, ny, xmin, ymin, inv_hx, inv_hy, 1, 0.0, 0.0, Ex, Ey, kl);
