@@ -172,6 +172,15 @@ sc_status sc_grid_read(sc_grid *g, uint64_t *Q, double *Ex, double *Ey, int64_t 
  * particle count N used to normalise it, e.g. to solve a given charge. */
 sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particles);
 
+/* Longitudinal space-charge kick, Sec. IV (dps = -(e/(m gamma0^2 beta0^2
+ * c^2)) u dlambda/dz L), on a sliced SC_SOLVE_PIPE_FP64 grid: every kick on
+ * this grid then also applies dps = -(K gamma0) L (Phi_{k+1} - Phi_{k-1}) /
+ * (2 dz) at the particle's (x, y), Phi_k the potential of slice k (0 beyond
+ * the first and last slice), K the transverse kick strength.  For a bunch
+ * whose transverse shape is the same in every slice this is the paper's
+ * u dlambda/dz.  Errors: SC_ERR_UNSUPPORTED (not a sliced pipe grid). */
+sc_status sc_set_longitudinal_kick(sc_grid *g, int enable);
+
 /* Synchronous copy-out of a pipe grid's potential (n_slices*ny*nx float64,
  * row-major, 0 on the walls): normalised like the fields (per unit line
  * charge, -ln r normalisation), i.e. phi solves lap phi = -2 pi q / (hx hy).

@@ -125,13 +125,18 @@ KPParams base_params(const sc_particles* p, const sc_beam* b) {
   return P;
 }
 
-void set_kick(KPParams& P, const sc_grid* g, double kl) {
+void set_kick(KPParams& P, const sc_grid* g, double kl, double gamma0) {
   P.do_kick = (kl != 0.0);
   P.gk = g->geom;
   P.E = g->E;
   P.E32 = (const float2*)g->E;
   P.field32 = g->field32;
   P.kl = kl;
+  if (g->lon) {  // K gamma0 L / (2 dz)
+    P.lon = 1;
+    P.phi = g->pipe.phi;
+    P.klz = kl * gamma0 / (2.0 * (g->zmax - g->zmin) / (double)g->nz);
+  }
 }
 
 // The cell cache a deposit writes follows the deposit grid's field precision.
@@ -322,7 +327,7 @@ sc_status sc_kick_push(sc_grid* g, const sc_particles* p, const sc_beam* b, doub
   }
   if (p->n == 0) return SC_OK;
   KPParams P = base_params(p, b);
-  set_kick(P, g, kick_strength(b) * L_sc);
+  set_kick(P, g, kick_strength(b) * L_sc, b->gamma0);
   if (next) set_deposit(P, next);
   if (n_elems > KP_INLINE) {
     // long segment: compiled copy in device memory (synchronous upload)
@@ -368,6 +373,15 @@ sc_status sc_grid_read(sc_grid* g, uint64_t* Q, double* Ex, double* Ey, int64_t*
     *n_out = (int64_t)v;
   }
   if (tf32_error(g)) return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
+  return SC_OK;
+}
+
+sc_status sc_set_longitudinal_kick(sc_grid* g, int enable) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (enable && (g->precision != SC_SOLVE_PIPE_FP64 || g->nz < 2))
+    return set_error(SC_ERR_UNSUPPORTED, "the longitudinal kick needs a sliced SC_SOLVE_PIPE_FP64 grid");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  g->lon = enable ? 1 : 0;
   return SC_OK;
 }
 
@@ -466,6 +480,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
   put(&g->trace, sizeof g->trace);
+  put(&g->lon, sizeof g->lon);
   put(&g->tune_acc, sizeof g->tune_acc);
   put(g->tune_twiss, sizeof g->tune_twiss);
 
@@ -558,7 +573,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       KPParams P = base_params(p, b);
       P.psc = T->psc;
       P.psc_mode = 1;
-      set_kick(P, g, K * (s[m] - prev));
+      set_kick(P, g, K * (s[m] - prev), b->gamma0);
       set_elements(P, lattice + m + 1, end - m - 1, b, T->d_elems + m + 1);
       // the cell cache is valid at every marker: the previous launch deposited on this grid
       P.cell = T->cell;

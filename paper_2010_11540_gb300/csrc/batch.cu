@@ -96,7 +96,7 @@ size_t cells_of(const sc_grid* g) { return (size_t)g->nx * g->ny; }
 // its own stacked grid.
 void bunch_kick(const sc_batch* B, int b, KPParams& P, double kl) {
   const sc_grid* g = B->cls[B->cls_of[b]];
-  set_kick(P, g, kl);
+  set_kick(P, g, kl, 1.0);  // batch grids are not sliced: no longitudinal kick
   const size_t off = (size_t)B->idx[b] * cells_of(g);
   P.E = g->E + off;
   P.E32 = (const float2*)g->E + off;

@@ -82,11 +82,31 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           const double ay = fma(fx, e10.y - e00.y, e00.y), by = fma(fx, e11.y - e01.y, e01.y);
           s.px = fma(P.kl, fma(fy, bx - ax, ax), s.px);
           s.py = fma(P.kl, fma(fy, by - ay, ay), s.py);
+          if (P.lon) {
+            // longitudinal kick: centred z-difference of the neighbouring slices' potentials
+            const int cells = P.gk.nx * P.gk.ny, k = cell / cells, nxk = P.gk.nx;
+            double up = 0.0, dn = 0.0;
+            if (k + 1 < P.gk.nz) {
+              const double* f = P.phi + cell + cells;
+              const double a0 = fma(fx, __ldg(f + 1) - __ldg(f), __ldg(f));
+              const double a1 = fma(fx, __ldg(f + nxk + 1) - __ldg(f + nxk), __ldg(f + nxk));
+              up = fma(fy, a1 - a0, a0);
+            }
+            if (k > 0) {
+              const double* f = P.phi + cell - cells;
+              const double a0 = fma(fx, __ldg(f + 1) - __ldg(f), __ldg(f));
+              const double a1 = fma(fx, __ldg(f + nxk + 1) - __ldg(f + nxk), __ldg(f + nxk));
+              dn = fma(fy, a1 - a0, a0);
+            }
+            s.ps = fma(-P.klz, up - dn, s.ps);
+          }
         }
       }
     }
     PsConst k;
-    if (psc_mode == 1) {
+    // the longitudinal kick changed psigma: its dependent quantities are recomputed and stored
+    const bool fresh = psc_mode == 2 || (psc_mode == 1 && !F32 && P.lon);
+    if (psc_mode == 1 && !fresh) {
       k.opd2 = P.psc[p];
       k.opb = P.psc[n + p];
       k.s1 = P.psc[2 * n + p];
@@ -94,12 +114,12 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
       k.qi = P.psc[4 * n + p];
       k.opm = 1.0 - s.ps;
     } else {
-      ps_const(k, s.ps, P.beta0_sq, psc_mode == 2 || P.has_quad != 0);
+      ps_const(k, s.ps, P.beta0_sq, fresh || P.has_quad != 0);
     }
     const bool quads = psc_mode != 0 || P.has_quad != 0;
     const bool changed = P.el ? push_elements(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads)
                               : push_elements(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads);
-    if (psc_mode == 2 || (psc_mode == 1 && changed)) {
+    if (fresh || (psc_mode == 1 && changed)) {
       P.psc[p] = k.opd2;
       P.psc[n + p] = k.opb;
       P.psc[2 * n + p] = k.s1;

@@ -106,6 +106,12 @@ struct KPParams {
   // (computed in registers), 1: read (rewritten after an RF cavity), 2: compute and write.
   double* psc;
   int psc_mode;
+  // Longitudinal kick (sliced pipe grids, float64 form): psigma -= klz *
+  // (Phi_{k+1} - Phi_{k-1}) at the particle, phi the slices' node potentials
+  // of the kick grid, klz = K gamma0 L / (2 dz).
+  int lon;
+  const double* phi;
+  double klz;
   DevElem inl[KP_INLINE];
 };
 
@@ -169,6 +175,7 @@ struct sc_grid {
   double tune_twiss[4];        // bare beta_x, alpha_x, beta_y, alpha_y at the turn start
   double trace_kp_ms, trace_solve_ms;
   int64_t trace_kicks;
+  int lon;                     // longitudinal kick on (sliced pipe grids)
   int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
   int kp_blocks_plain;         // kick/push without a deposit
   sc::DevElem* el_stage;       // device copy of sc_kick_push's last long segment
@@ -221,7 +228,7 @@ sc_status check_beam(const sc_beam* b);
 sc_status check_elements(const sc_element* e, int n);
 double kick_strength(const sc_beam* b);
 KPParams base_params(const sc_particles* p, const sc_beam* b);
-void set_kick(KPParams& P, const sc_grid* g, double kl);
+void set_kick(KPParams& P, const sc_grid* g, double kl, double gamma0);
 void set_deposit(KPParams& P, sc_grid* d);
 void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, const DevElem* dev);
 sc_status solve_dispatch(sc_grid* g, bool zero_q);

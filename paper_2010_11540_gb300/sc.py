@@ -29,6 +29,7 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
+           "sc_set_longitudinal_kick",
            "sc_last_error")
 
 
@@ -100,6 +101,7 @@ def load():
                                              ctypes.c_size_t]
     L.sc_probe_peaks.argtypes = [dp, dp, dp, vp]
     L.sc_grid_read_potential.argtypes = [vp, vp]
+    L.sc_set_longitudinal_kick.argtypes = [vp, ctypes.c_int]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -221,6 +223,11 @@ def grid_read(grid: Grid):
     n_out = ctypes.c_int64(0)
     _check(load().sc_grid_read(grid.handle, Q.ctypes.data, Ex.ctypes.data, Ey.ctypes.data, ctypes.byref(n_out)))
     return Q, Ex, Ey, int(n_out.value)
+
+
+def set_longitudinal_kick(grid: Grid, enable: bool = True):
+    """Longitudinal space-charge kick on a sliced conducting-pipe grid."""
+    _check(load().sc_set_longitudinal_kick(grid.handle, 1 if enable else 0))
 
 
 def grid_read_potential(grid: Grid):

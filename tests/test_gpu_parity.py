@@ -570,3 +570,67 @@ def test_pipe_unsupported_size(n):
     with pytest.raises(sc.ScError) as e:
         sc.create_grid(n, 129, -1.0, 1.0, -1.0, 1.0, precision="pipe_fp64")
     assert e.value.code in (-7, -1)
+
+
+# ------------------------------------------------------------------ longitudinal kick (Sec. IV)
+def test_longitudinal_kick_single_step():
+    """One kick (no elements) on a sliced pipe grid: transverse and longitudinal
+    momentum changes against the oracle."""
+    parts, _, _, _ = synth.workload("c5", n=300000)
+    grid = (65, 65) + synth.grid_extent(4e-3, 3e-3)
+    sl = (12, -60.0, 60.0)
+    zs = oracle.Slices(*sl)
+    b = synth.beam(n_lambda=1e13 / zs.dz, circumference=1728.0)
+    g = sc.create_grid(*grid, precision="pipe_fp64", slices=sl)
+    sc.set_longitudinal_kick(g)
+    st = to_gpu(parts)
+    sc.deposit(g, st)
+    sc.solve(g)
+    L = 8.0
+    sc.kick_push(g, st, b, L, None)
+    got = to_host(st)
+    og = oracle.Geometry(*grid)
+    ref = oracle.copy_state(parts)
+    n = len(ref["x"])
+    Q, _ = oracle.deposit_sliced(og, zs, ref["x"], ref["y"], ref["sigma"])
+    Ex, Ey = oracle.solve_sliced(og, Q, n, boundary="pipe")
+    K = oracle.kick_strength(b)
+    oracle.kick_sliced(og, zs, ref, Ex, Ey, K * L)
+    oracle.kick_long(og, zs, ref, oracle.potential_sliced_pipe(og, Q, n), K * b["gamma0"] * L / (2 * zs.dz))
+    for k in ("px", "py", "psigma"):
+        d_got, d_ref = got[k] - parts[k], ref[k] - parts[k]
+        assert np.abs(d_ref).max() > 0
+        assert np.abs(d_got - d_ref).max() < 1e-10 * np.abs(d_ref).max(), k
+
+
+def test_longitudinal_kick_rejected_without_pipe_slices():
+    g = sc.create_grid(64, 64, -1.0, 1.0, -1.0, 1.0)
+    with pytest.raises(sc.ScError) as e:
+        sc.set_longitudinal_kick(g)
+    assert e.value.code == -7
+    g2 = sc.create_grid(65, 65, -1.0, 1.0, -1.0, 1.0, precision="pipe_fp64")
+    with pytest.raises(sc.ScError):
+        sc.set_longitudinal_kick(g2)
+
+
+def test_track_longitudinal_one_turn():
+    """2e5 particles in 8 slices of 65 x 65 pipe grids, transverse and
+    longitudinal kicks, one turn of the c2 ring, against the oracle."""
+    parts, _, _, lat = synth.workload("c5", n=200000)
+    grid = (65, 65) + synth.grid_extent(4e-3, 3e-3)
+    sl = (8, -60.0, 60.0)
+    zs = oracle.Slices(*sl)
+    b = synth.beam(n_lambda=1e12 / zs.dz, circumference=float(lat["length"].sum()))
+    g = sc.create_grid(*grid, precision="pipe_fp64", slices=sl)
+    sc.set_longitudinal_kick(g)
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(oracle.Geometry(*grid), ref, b, lat, 1, slices=zs, boundary="pipe", longitudinal=True)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+    # the longitudinal kick did act: without it psigma ends elsewhere
+    ref0 = oracle.copy_state(parts)
+    oracle.track(oracle.Geometry(*grid), ref0, b, lat, 1, slices=zs, boundary="pipe")
+    assert np.abs(ref0["psigma"] - ref["psigma"]).max() > 1e3 * np.abs(got["psigma"] - ref["psigma"]).max()
