@@ -29,7 +29,7 @@ _LIB = os.path.join(_HERE, "libsc_oracle.so")
 ONE_FX = 1 << 20  # fixed-point unit per axis
 Q_UNIT = float(1 << 40)  # one particle's total deposited charge
 
-DRIFT, QUAD, SEXT, BEND, RF, MARK = 0, 1, 2, 3, 4, 5
+DRIFT, QUAD, SEXT, BEND, RF, MARK, EXACT_BEND = 0, 1, 2, 3, 4, 5, 6
 
 
 def build(force=False):

@@ -45,7 +45,7 @@ typedef struct {
   double gamma0, beta0, n_lambda, r_p, circumference, mass_ev;
 } orc_beam;
 
-enum { ORC_DRIFT = 0, ORC_QUAD = 1, ORC_SEXT = 2, ORC_BEND = 3, ORC_RF = 4, ORC_MARK = 5 };
+enum { ORC_DRIFT = 0, ORC_QUAD = 1, ORC_SEXT = 2, ORC_BEND = 3, ORC_RF = 4, ORC_MARK = 5, ORC_EXACT_BEND = 6 };
 
 static const double ORC_ONE_FX = 1048576.0; /* 2^20 */
 
@@ -332,6 +332,49 @@ static void orc_sext(double *s, double k2l) {
   s[3] += k2l * x * y;
 }
 
+/* Thick sextupole, Sec. III-C: H_approx = H0 + V with
+ * H0 = (px^2+py^2)/2 (1-ps) + ps^2/(2 gamma0^2) and V = k2 (x^3 - 3 x y^2)/6,
+ * k2 = k2l / L, integrated by the symplectic split of Eq. Sym2,
+ *   exp(H0 a L) exp(V b L) exp(H0 c L) exp(V b L) exp(H0 a L),
+ * a = (1 - 1/sqrt 3)/2, b = 1/2, c = 1/sqrt 3 (the V steps are kicks of
+ * integrated strength k2 b L = k2l/2). */
+static void orc_thick_sext(double *s, double L, double k2l, double gamma0) {
+  const double a = 0.5 * (1.0 - 1.0 / sqrt(3.0)), c = 1.0 / sqrt(3.0);
+  orc_h0_drift(s, a * L, gamma0);
+  orc_sext(s, 0.5 * k2l);
+  orc_h0_drift(s, c * L, gamma0);
+  orc_sext(s, 0.5 * k2l);
+  orc_h0_drift(s, a * L, gamma0);
+}
+
+/* Exact sector dipole (Sec. III-A: uniform field solved without H_approx,
+ * Eqs. BEND1, BEND2 and the transformation to (x, sg) at the exit face, with
+ * the printed sqrt(x~ + z~) read as sqrt(x~^2 + z~^2)).  Worked out in the
+ * bending plane: the particle circles with radius rho P, P^2 = (1+delta)^2 -
+ * py^2, about C = (rho + x0 - rho pz0, rho px0) (rho = L/angle, origin at the
+ * reference orbit's centre); the exit face is the ray at `angle`.  With
+ * pz0 = sqrt(P^2 - px0^2), C = cos(angle), S = sin(angle):
+ *   px = px0 C + (pz0 - 1 - x0/rho) S,         pz = sqrt(P^2 - px^2),
+ *   x  = (x0 + rho (1 - pz0)) C + rho px0 S + rho (pz - 1),
+ *   alpha = angle + asin(px0/P) - asin(px/P)   (turn of the momentum),
+ *   y += py rho alpha,  sg += L - (1 + beta0^2 ps) rho alpha,  py, ps const.
+ * Zero angle: the exact drift. */
+static void orc_exact_bend(double *s, double L, double angle, double beta0) {
+  if (angle == 0.0) { orc_drift(s, L, beta0); return; }
+  double rho = L / angle, C = cos(angle), S = sin(angle);
+  double x0 = s[0], px0 = s[1], py = s[3], ps = s[5];
+  double P2 = 1.0 + 2.0 * ps + beta0 * beta0 * ps * ps - py * py;
+  double pz0 = sqrt(P2 - px0 * px0);
+  double px = px0 * C + (pz0 - 1.0 - x0 / rho) * S;
+  double pz = sqrt(P2 - px * px);
+  double P = sqrt(P2);
+  double alpha = angle + asin(px0 / P) - asin(px / P);
+  s[0] = (x0 + rho * (1.0 - pz0)) * C + rho * px0 * S + rho * (pz - 1.0);
+  s[1] = px;
+  s[2] += py * rho * alpha;
+  s[4] += L - (1.0 + beta0 * beta0 * ps) * rho * alpha;
+}
+
 /* Linear sector dipole from H_approx with curvature h = angle/L and the
  * bending field's h^2 x^2/2 term (Sec. III, Eq. H):
  *   H = (px^2+py^2)/2 + ps^2/(2 gamma0^2) - h x ps + h^2 x^2 / 2.
@@ -368,7 +411,13 @@ void orc_push(int64_t n, double *x, double *px, double *y, double *py, double *s
       switch (e->type) {
         case ORC_DRIFT: orc_drift(s, e->length, bm->beta0); break;
         case ORC_QUAD: orc_quad(s, e->length, e->k1, bm->gamma0); break;
-        case ORC_SEXT: orc_sext(s, e->k2l); break;
+        case ORC_SEXT:
+          if (e->length > 0.0)
+            orc_thick_sext(s, e->length, e->k2l, bm->gamma0);
+          else
+            orc_sext(s, e->k2l);
+          break;
+        case ORC_EXACT_BEND: orc_exact_bend(s, e->length, e->angle, bm->beta0); break;
         case ORC_BEND: orc_bend(s, e->length, e->angle, bm->gamma0); break;
         case ORC_RF: orc_rf(s, e, bm); break;
         default: break; /* markers: no-op */

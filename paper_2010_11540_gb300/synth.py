@@ -20,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 
 # ---- element table -------------------------------------------------------
-DRIFT, QUAD, SEXT, BEND, RF, MARK = 0, 1, 2, 3, 4, 5
+DRIFT, QUAD, SEXT, BEND, RF, MARK, EXACT_BEND = 0, 1, 2, 3, 4, 5, 6
 
 ELEMENT_DTYPE = np.dtype(
     [

@@ -167,3 +167,74 @@ def test_rms_size_gives_beta():
     eps_meas = oracle.emittances(st)[0]
     assert np.var(st["x"]) / eps_meas == pytest.approx(b1, rel=0.01)  # sampling error ~ 1/sqrt(n)
     assert eps_meas == pytest.approx(eps, rel=0.01)
+
+
+# ------------------------------------------------------------------ exact sector dipole, thick sextupole
+def h_exact_bend(h):
+    """Exact sector-dipole Hamiltonian in curvilinear coordinates: the uniform
+    field's A_s with (1+hx) A_s = -B0 (x + h x^2/2):
+    H = ps - (1 + h x) sqrt((1+delta)^2 - px^2 - py^2) + h x + h^2 x^2 / 2."""
+    def H(z):
+        x, px, y, py, sg, ps = z
+        return ps - (1 + h * x) * np.sqrt(1 + 2 * ps + B0**2 * ps**2 - px**2 - py**2) + h * x + h * h * x * x / 2
+    return H
+
+
+def h_sext(k2):
+    def H(z):
+        x, px, y, py, sg, ps = z
+        return ((px**2 + py**2) / 2 * (1 - ps) + ps**2 / (2 * G0**2) + k2 / 6 * (x**3 - 3 * x * y**2))
+    return H
+
+
+@pytest.mark.parametrize("angle,L", [(0.2, 1.3), (-0.35, 2.0), (0.05, 0.5)])
+def test_exact_bend_equals_hamiltonian_flow(angle, L):
+    got = apply([synth.elem(synth.EXACT_BEND, L, angle=angle)], Z0)
+    want = rk4(h_exact_bend(angle / L), Z0.copy(), L)
+    scale = np.array([1e-3, 1e-4, 1e-3, 1e-4, 1e-3, 1e-3])
+    assert np.max(np.abs(got - want) / scale) < 1e-9
+
+
+def test_exact_bend_linearises_to_the_linear_bend():
+    """The Jacobian of the exact map at the reference orbit is the linear
+    sector-dipole matrix (H_approx is the exact H to second order)."""
+    e_exact = synth.elem(synth.EXACT_BEND, 1.5, angle=0.12)
+    e_lin = synth.elem(synth.BEND, 1.5, angle=0.12)
+    z = np.zeros(6)
+    assert np.max(np.abs(jacobian([e_exact], z, 1e-7) - jacobian([e_lin], z, 1e-7))) < 1e-7
+    # and zero angle is the exact drift
+    a = apply([synth.elem(synth.EXACT_BEND, 1.5, angle=0.0)], Z0)
+    b = apply([synth.elem(synth.DRIFT, 1.5)], Z0)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("e", [synth.elem(synth.EXACT_BEND, 1.5, angle=0.1),
+                               synth.elem(synth.SEXT, 0.4, k2l=4.0)])
+def test_symplectic_new_elements(e):
+    M = jacobian([e], Z0)
+    assert np.max(np.abs(M.T @ J @ M - J)) < 1e-7
+
+
+def test_thick_sextupole_is_the_papers_split():
+    """Eq. Sym2 with a, b, c of the paper (SABA2): zero strength is the H0
+    flow; against the exact flow of H0 + V its error is second order in the
+    step and quadratic in the strength (O(eps^2 tau^2 + eps tau^4): the
+    linear-in-strength part of a plain second-order split cancels); a very
+    short element is the thin kick."""
+    L = 0.6
+    zero = apply([synth.elem(synth.SEXT, L, k2l=0.0)], Z0)
+    h0 = apply([synth.elem(synth.QUAD, L, k1=0.0)], Z0)
+    assert np.max(np.abs(zero - h0)) < 1e-15
+    z = np.array([8e-3, -6e-4, -5e-3, 4e-4, 0.3, 2.5e-3])
+
+    def err(k2l, pieces):
+        exact = rk4(h_sext(k2l / L), z.copy(), L, n=4000)
+        got = apply([synth.elem(synth.SEXT, L / pieces, k2l=k2l / pieces)] * pieces, z)
+        return np.abs(got - exact).max()
+
+    e30, e30h, e3 = err(30.0, 1), err(30.0, 2), err(3.0, 1)
+    assert 3.5 < e30 / e30h < 4.5, (e30, e30h)  # second order in the step
+    assert e30 / e3 > 50, (e30, e3)  # quadratic in the strength
+    thin = apply([synth.elem(synth.SEXT, 1e-7, k2l=30.0)], z)
+    kick = apply([synth.elem(synth.SEXT, 0.0, k2l=30.0)], z)
+    assert np.max(np.abs(thin - kick)) < 1e-9
