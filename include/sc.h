@@ -54,10 +54,11 @@ typedef int sc_status;
 /* Element types (sc_element.type). */
 #define SC_DRIFT 0 /* exact drift, Sec. III-A                                  */
 #define SC_QUAD 1  /* thick quadrupole with chromatic factor, Sec. III-B       */
-#define SC_SEXT 2  /* thin sextupole kick (V-step of Eq. Sym2), Sec. III-C     */
+#define SC_SEXT 2  /* sextupole, Sec. III-C: thin kick, or Eq. Sym2 if thick  */
 #define SC_BEND 3  /* linear sector dipole from H_approx, Sec. III             */
 #define SC_RF 4    /* thin RF cavity                                           */
 #define SC_MARK 5  /* space-charge location (kick point), Sec. V               */
+#define SC_EXACT_BEND 6 /* exact sector dipole (uniform field, Sec. III-A)  */
 
 /* Largest macroparticle count per call: each particle deposits exactly 2^40
  * fixed-point units into an unsigned 64-bit grid, which holds fewer than 2^24
@@ -82,7 +83,10 @@ typedef struct {
 
 /* One lattice element, 64 bytes.
  * length [m] (0 for thin elements); k1 [m^-2] (SC_QUAD; >0 focuses x);
- * k2l [m^-2] integrated sextupole strength (SC_SEXT); angle [rad] (SC_BEND);
+ * k2l [m^-2] integrated sextupole strength (SC_SEXT: length 0 is one thin
+ * kick, length > 0 the split exp(H0 aL) exp(V bL) exp(H0 cL) exp(V bL)
+ * exp(H0 aL) of Eq. Sym2 with k2 = k2l/length); angle [rad] (SC_BEND: linear
+ * map of H_approx; SC_EXACT_BEND: exact uniform-field sector dipole);
  * volt [V], harmonic, lag [rad] (SC_RF: dpsigma = volt/(beta0^2 E0) *
  * sin(lag - 2 pi harmonic sigma / circumference)). */
 typedef struct {

@@ -92,7 +92,7 @@ sc_status check_beam(const sc_beam* b) {
 sc_status check_elements(const sc_element* e, int n) {
   if (n < 0 || (n > 0 && !e)) return set_error(SC_ERR_ARG, "bad element list");
   for (int k = 0; k < n; ++k) {
-    if (e[k].type < SC_DRIFT || e[k].type > SC_MARK) return set_error(SC_ERR_ARG, "unknown element type");
+    if (e[k].type < SC_DRIFT || e[k].type > SC_EXACT_BEND) return set_error(SC_ERR_ARG, "unknown element type");
     if (!std::isfinite(e[k].length) || e[k].length < 0.0) return set_error(SC_ERR_ARG, "bad element length");
   }
   return SC_OK;

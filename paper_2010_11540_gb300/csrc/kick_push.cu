@@ -326,9 +326,30 @@ void compile_elements(const sc_element* in, int n, const sc_beam* b, DevElem* ou
         break;
       }
       case SC_SEXT:
-        d.p[0] = 0.5 * e.k2l;
-        d.p[1] = e.k2l;
+        if (e.length > 0.0) {  // Eq. Sym2: kicks of k2 b L = k2l/2 between H0 flows of a L, c L, a L
+          d.flags = 1;
+          d.p[0] = 0.25 * e.k2l;
+          d.p[1] = 0.5 * e.k2l;
+          d.p[2] = 0.5 * (1.0 - 1.0 / std::sqrt(3.0)) * e.length;
+          d.p[3] = e.length / std::sqrt(3.0);
+        } else {
+          d.p[0] = 0.5 * e.k2l;
+          d.p[1] = e.k2l;
+        }
         break;
+      case SC_EXACT_BEND: {
+        d.p[0] = e.length;
+        if (e.angle == 0.0 || e.length == 0.0) {
+          d.flags = 1;  // exact drift
+          break;
+        }
+        d.p[1] = e.angle;
+        d.p[2] = std::cos(e.angle);
+        d.p[3] = std::sin(e.angle);
+        d.p[4] = e.length / e.angle;  // rho
+        d.p[5] = e.angle / e.length;  // 1 / rho
+        break;
+      }
       case SC_BEND: {
         d.p[0] = e.length;
         if (e.angle == 0.0 || e.length == 0.0) {

@@ -125,11 +125,61 @@ __device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsCon
   s.sg = fma(-fma(L, S2, D), k.qi, fma(s.ps, L * inv_gamma0_sq, s.sg));
 }
 
-// Thin sextupole (the V step of Eq. Sym2): px -= k2l/2 (x^2 - y^2), py += k2l x y.
-// e.p = {k2l/2, k2l}.
-__device__ __forceinline__ void map_sext(State& s, const DevElem& e) {
-  s.px = fma(-e.p[0], (s.x - s.y) * (s.x + s.y), s.px);
-  s.py = fma(e.p[1] * s.x, s.y, s.py);
+// Flow of H0 = (px^2+py^2)/2 (1-ps) + ps^2/(2 gamma0^2) over l.
+__device__ __forceinline__ void h0_flow(State& s, const PsConst& k, double l, double inv_gamma0_sq) {
+  const double f = k.opm * l;
+  const double pp = fma(s.px, s.px, s.py * s.py);
+  s.x = fma(f, s.px, s.x);
+  s.y = fma(f, s.py, s.y);
+  s.sg = fma(-0.5 * l, pp, fma(s.ps, l * inv_gamma0_sq, s.sg));
+}
+
+// Sextupole (Sec. III-C).  Thin: the V step of Eq. Sym2 as one kick,
+// px -= k2l/2 (x^2 - y^2), py += k2l x y; e.p = {k2l/2, k2l}.  Thick
+// (e.flags = 1): Eq. Sym2, H0 flows of a L, c L, a L around two kicks of
+// integrated strength k2l/2; e.p = {k2l/4, k2l/2, a L, c L}.
+__device__ __forceinline__ void sext_kick(State& s, double half, double full) {
+  s.px = fma(-half, (s.x - s.y) * (s.x + s.y), s.px);
+  s.py = fma(full * s.x, s.y, s.py);
+}
+
+__device__ __forceinline__ void map_sext(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
+  if (e.flags != 1) {
+    sext_kick(s, e.p[0], e.p[1]);
+    return;
+  }
+  h0_flow(s, k, e.p[2], inv_gamma0_sq);
+  sext_kick(s, e.p[0], e.p[1]);
+  h0_flow(s, k, e.p[3], inv_gamma0_sq);
+  sext_kick(s, e.p[0], e.p[1]);
+  h0_flow(s, k, e.p[2], inv_gamma0_sq);
+}
+
+// Exact sector dipole (Sec. III-A, uniform field without H_approx): the
+// particle's circle in the bending plane carried to the exit face.  With
+// P^2 = (1+delta)^2 - py^2, pz0 = sqrt(P^2 - px0^2), C = cos(angle), S = sin(angle):
+//   px = px0 C + (pz0 - 1 - x0/rho) S,  pz = sqrt(P^2 - px^2),
+//   x = (x0 + rho (1 - pz0)) C + rho px0 S + rho (pz - 1),
+//   alpha = angle + asin(px0/P) - asin(px/P),
+//   y += py rho alpha,  sg += L - (1 + beta0^2 ps) rho alpha.
+// e.p = {L, angle, C, S, rho, 1/rho}; zero angle (e.flags = 1): the exact drift.
+__device__ __forceinline__ void map_exact_bend(State& s, const DevElem& e, const PsConst& k) {
+  if (e.flags == 1) {
+    map_drift(s, e, k);
+    return;
+  }
+  const double L = e.p[0], angle = e.p[1], C = e.p[2], S = e.p[3], rho = e.p[4], h = e.p[5];
+  const double x0 = s.x, px0 = s.px;
+  const double P2 = fma(-s.py, s.py, k.opd2);
+  const double pz0 = sqrt(fma(-px0, px0, P2));
+  const double px = fma(px0, C, (pz0 - 1.0 - x0 * h) * S);
+  const double pz = sqrt(fma(-px, px, P2));
+  const double rP = rsqrt(P2);
+  const double alpha = angle + (asin(px0 * rP) - asin(px * rP));
+  s.x = fma(x0 + rho * (1.0 - pz0), C, fma(rho * px0, S, rho * (pz - 1.0)));
+  s.px = px;
+  s.y = fma(s.py * rho, alpha, s.y);
+  s.sg += fma(-k.opb * rho, alpha, L);
 }
 
 // Linear sector dipole from H_approx with curvature h (Sec. III, Eq. H plus
@@ -173,7 +223,8 @@ __device__ __forceinline__ bool push_elements(State& s, PsConst& k, const DevEle
     switch (e.type) {
       case SC_DRIFT: map_drift(s, e, k); break;
       case SC_QUAD: map_quad(s, e, k, inv_gamma0_sq); break;
-      case SC_SEXT: map_sext(s, e); break;
+      case SC_SEXT: map_sext(s, e, k, inv_gamma0_sq); break;
+      case SC_EXACT_BEND: map_exact_bend(s, e, k); break;
       case SC_BEND: map_bend(s, e, k, inv_gamma0_sq); break;
       case SC_RF:
         map_rf(s, e);

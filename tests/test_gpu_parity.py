@@ -146,6 +146,23 @@ def test_kick_push_every_element_type():
     assert max(err.values()) < 1e-10, err
 
 
+def test_kick_push_exact_bend_and_thick_sextupole():
+    """The exact sector dipole (both signs, zero angle) and the thick Eq. Sym2
+    sextupole, with an RF cavity between them (psigma-dependent quantities
+    refreshed mid-segment), against the oracle."""
+    parts, b, grid, lat = synth.workload("c1", n=5000)
+    b = dict(b, circumference=264.0)
+    elems = synth.table([
+        synth.elem(synth.EXACT_BEND, 1.5, angle=0.1), synth.elem(synth.SEXT, 0.4, k2l=4.0),
+        synth.elem(synth.RF, volt=2e5, harmonic=9.0, lag=0.3), synth.elem(synth.EXACT_BEND, 2.0, angle=-0.05),
+        synth.elem(synth.EXACT_BEND, 1.0, angle=0.0), synth.elem(synth.SEXT, 0.25, k2l=-6.0),
+        synth.elem(synth.DRIFT, 1.0),
+    ])
+    got, ref, _, _ = _one_step(parts, b, grid, elems, 5.5)
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
+
+
 # ------------------------------------------------------------------ tracking
 def test_track_c1_full():
     """Config c1 in full: 2e4 particles, 64x64, 48 kicks/turn, 10 turns."""
