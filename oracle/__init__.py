@@ -69,6 +69,14 @@ def lib():
         L.orc_kick_long.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, ctypes.c_double]
+        L.orc_kick_bezier.restype = None
+        L.orc_kick_bezier.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, _dp, ctypes.c_double, ctypes.c_double]
+        L.orc_bezier_point.restype = None
+        L.orc_bezier_point.argtypes = [_dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp]
         L.orc_green_self.restype = ctypes.c_double
         L.orc_green_self.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_green_cyclic.restype = None
@@ -157,6 +165,25 @@ def kick_long(g: Geometry, zs: Slices, st, phi, klz):
     lib().orc_kick_long(len(st["x"]), _d(st["x"]), _d(st["y"]), _d(st["sigma"]), _d(st["psigma"]), g.nx, g.ny,
                         g.xmin, g.ymin, g.inv_hx, g.inv_hy, zs.nz, zs.zmin, zs.inv_dz,
                         _d(np.ascontiguousarray(phi, dtype=np.float64)), klz)
+
+
+def bezier_point(g: Geometry, phi, i, j, fx, fy):
+    """(u, du/dx, du/dy) of the Bezier surface (Sec. IV-C) of node potentials
+    phi [ny, nx] in cell (i, j) at fractions (fx, fy)."""
+    out = np.zeros(3)
+    lib().orc_bezier_point(_d(np.ascontiguousarray(phi, dtype=np.float64)), g.nx, g.ny, g.hx, g.hy, int(i), int(j),
+                           float(fx), float(fy), _d(out))
+    return out
+
+
+def kick_bezier(g: Geometry, zs, st, phi, kl, klz=0.0):
+    """Space-charge kick from the Bezier surface of the node potentials
+    (Sec. IV-C), phi [nz, ny, nx] (nz = 1 unsliced); with klz the longitudinal
+    kick from the same surfaces."""
+    nz, zmin, inv_dz = (1, 0.0, 0.0) if zs is None else (zs.nz, zs.zmin, zs.inv_dz)
+    lib().orc_kick_bezier(len(st["x"]), _d(st["x"]), _d(st["y"]), _d(st["sigma"]), _d(st["px"]), _d(st["py"]),
+                          _d(st["psigma"]), g.nx, g.ny, g.xmin, g.ymin, g.inv_hx, g.inv_hy, g.hx, g.hy, nz, zmin,
+                          inv_dz, _d(np.ascontiguousarray(phi, dtype=np.float64)), kl, klz)
 
 
 def solve_sliced(g: Geometry, Q, n_total, method="fft", boundary="open"):
@@ -337,7 +364,7 @@ def segments(lattice):
 
 
 def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kicks=None, slices=None,
-          boundary="open", longitudinal=False):
+          boundary="open", longitudinal=False, gather="bilinear"):
     """Track `st` (modified in place) for n_turns with the PIC loop of Sec. I.
     Each space-charge location: deposit -> solve -> kick (L since the previous
     location) -> push to the next location.  Returns the number of kicks done.
@@ -346,9 +373,12 @@ def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kic
     density of a slice that held the whole bunch (N / dz).  boundary "pipe":
     the conducting-pipe solve of Sec. IV-B on the grid's outer nodes.
     longitudinal (sliced pipe grids): also the longitudinal kick of Sec. IV,
-    after the transverse one, from the same positions."""
+    after the transverse one, from the same positions.  gather "bezier" (pipe
+    grids): kicks from the Bezier surface of the potential (Sec. IV-C)."""
     if longitudinal and (slices is None or boundary != "pipe"):
         raise ValueError("the longitudinal kick needs sliced grids in a conducting pipe")
+    if gather == "bezier" and boundary != "pipe":
+        raise ValueError("the Bezier gather needs the potential of a conducting pipe")
     head, kicks = segments(lattice)
     K = kick_strength(b)
     n = len(st["x"])
@@ -360,7 +390,16 @@ def track(g: Geometry, st, b, lattice, n_turns, method="fft", diag=None, max_kic
         for L, seg in kicks:
             if max_kicks is not None and done >= max_kicks:
                 return done
-            if slices is None:
+            if gather == "bezier":
+                if slices is None:
+                    Q, _ = deposit(g, st["x"], st["y"])
+                    phi = potential_pipe(g, normalise(Q, n))[1:-1, 1:-1][None]
+                else:
+                    Q, _ = deposit_sliced(g, slices, st["x"], st["y"], st["sigma"])
+                    phi = potential_sliced_pipe(g, Q, n)
+                klz = K * b["gamma0"] * L / (2.0 * slices.dz) if longitudinal else 0.0
+                kick_bezier(g, slices, st, phi, K * L, klz)
+            elif slices is None:
                 Q, _ = deposit(g, st["x"], st["y"])
                 Ex, Ey = solve(g, Q, n, method, boundary)
                 kick(g, st, Ex, Ey, K * L)

@@ -247,6 +247,92 @@ void orc_kick_long(int64_t n, const double *x, const double *y, const double *sg
   }
 }
 
+/* ---------------------------------------------------------------------
+ * Bezier gather of the potential, Sec. IV-C:
+ *   u(x, y) = sum_{m,n=0..3} u_{i+m-1, j+n-1} B_m(tx) B_n(ty),
+ *   B_m(t) = 3!/(m!(3-m)!) t^m (1-t)^(3-m),   E = -grad u.
+ * Reading: the cubic's four control points are the nodes i-1 .. i+2, so its
+ * parameter runs over them, tx = (x - x_{i-1}) / (3 hx) = (1 + fx)/3 (the
+ * printed (x - x_i)/hx over one cell would triple every gradient: a linear
+ * potential's printed dU/dx is 3 times its slope).  Linear potentials are then
+ * reproduced exactly; for u = x^2 the surface is x^2 + 3 tx (1 - tx) hx^2 (the
+ * Bernstein smoothing).  Nodes beyond the walls take the odd extension of the
+ * pipe potential (u_{-1} = -u_1, u_{n} = -u_{n-2}).  Cell, fractions and
+ * validity as orc_kick_sliced.
+ * The kick: px += kl Ex, py += kl Ey; with klz != 0 also the longitudinal kick
+ * of orc_kick_long with the neighbouring slices' u taken from the same
+ * surface.  phi: nz grids [k][j][i] of node potentials.
+ * ------------------------------------------------------------------- */
+static double orc_phi_at(const double *phi, int nx, int ny, int i, int j) {
+  double sgn = 1.0;
+  if (i < 0) { i = -i; sgn = -sgn; }
+  if (i > nx - 1) { i = 2 * (nx - 1) - i; sgn = -sgn; }
+  if (j < 0) { j = -j; sgn = -sgn; }
+  if (j > ny - 1) { j = 2 * (ny - 1) - j; sgn = -sgn; }
+  return sgn * phi[(int64_t)j * nx + i];
+}
+
+static void orc_bernstein3(double t, double *b, double *db) {
+  double u = 1.0 - t;
+  b[0] = u * u * u;
+  b[1] = 3.0 * t * u * u;
+  b[2] = 3.0 * t * t * u;
+  b[3] = t * t * t;
+  db[0] = -3.0 * u * u;
+  db[1] = 3.0 * u * u - 6.0 * t * u;
+  db[2] = 6.0 * t * u - 3.0 * t * t;
+  db[3] = 3.0 * t * t;
+}
+
+/* Value and gradient of the Bezier surface of grid `phi` in cell (i, j) at fractions (fx, fy). */
+static void orc_bezier_eval(const double *phi, int nx, int ny, int i, int j, double fx, double fy, double hx,
+                            double hy, double *u, double *dudx, double *dudy) {
+  double bx[4], dbx[4], by[4], dby[4];
+  orc_bernstein3((1.0 + fx) / 3.0, bx, dbx);
+  orc_bernstein3((1.0 + fy) / 3.0, by, dby);
+  double v = 0.0, gx = 0.0, gy = 0.0;
+  for (int n = 0; n < 4; ++n)
+    for (int m = 0; m < 4; ++m) {
+      double c = orc_phi_at(phi, nx, ny, i + m - 1, j + n - 1);
+      v += c * bx[m] * by[n];
+      gx += c * dbx[m] * by[n];
+      gy += c * bx[m] * dby[n];
+    }
+  *u = v;
+  *dudx = gx / (3.0 * hx);
+  *dudy = gy / (3.0 * hy);
+}
+
+void orc_bezier_point(const double *phi, int nx, int ny, double hx, double hy, int i, int j, double fx, double fy,
+                      double *out3) {
+  orc_bezier_eval(phi, nx, ny, i, j, fx, fy, hx, hy, &out3[0], &out3[1], &out3[2]);
+}
+
+void orc_kick_bezier(int64_t n, const double *x, const double *y, const double *sg, double *px, double *py,
+                     double *ps, int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy, double hx,
+                     double hy, int nz, double zmin, double inv_dz, const double *phi, double kl, double klz) {
+  int64_t cells = (int64_t)nx * ny;
+  for (int64_t p = 0; p < n; ++p) {
+    int k = orc_slice(sg ? sg[p] : 0.0, nz, zmin, inv_dz);
+    double xi = (x[p] - xmin) * inv_hx;
+    double eta = (y[p] - ymin) * inv_hy;
+    if (k < 0 || !(xi >= 0.0 && xi < (double)(nx - 1) && eta >= 0.0 && eta < (double)(ny - 1))) continue;
+    double fi = floor(xi), fj = floor(eta);
+    int i = (int)fi, j = (int)fj;
+    double fx = xi - fi, fy = eta - fj;
+    double u, gx, gy;
+    orc_bezier_eval(phi + (int64_t)k * cells, nx, ny, i, j, fx, fy, hx, hy, &u, &gx, &gy);
+    px[p] += kl * -gx;
+    py[p] += kl * -gy;
+    if (klz != 0.0) {
+      double up = 0.0, dn = 0.0, a, b;
+      if (k + 1 < nz) orc_bezier_eval(phi + (int64_t)(k + 1) * cells, nx, ny, i, j, fx, fy, hx, hy, &up, &a, &b);
+      if (k > 0) orc_bezier_eval(phi + (int64_t)(k - 1) * cells, nx, ny, i, j, fx, fy, hx, hy, &dn, &a, &b);
+      ps[p] -= klz * (up - dn);
+    }
+  }
+}
+
 void orc_kick(int64_t n, const double *x, const double *y, double *px, double *py, int nx, int ny, double xmin,
               double ymin, double inv_hx, double inv_hy, const double *Ex, const double *Ey, double kl) {
   orc_kick_sliced(n, x, y, 0, px, py, nx, ny, xmin, ymin, inv_hx, inv_hy, 1, 0.0, 0.0, Ex, Ey, kl);

@@ -1,0 +1,81 @@
+"""Pins of the oracle's Bezier gather (Sec. IV-C; control points u_{i-1..i+2},
+parameter over their span): a linear potential is reproduced exactly (value
+and gradient); a quadratic one is smoothed by the closed-form Bernstein amount
+3 t (1 - t) h^2; a constant gives no field; a round Gaussian beam in a wide
+pipe gets its closed-form field; the kick is antisymmetric for a symmetric
+beam."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_11540_gb300 import synth
+
+G = oracle.Geometry(33, 17, -0.4, 0.4, -0.2, 0.2)
+
+
+def node_field(f):
+    x, y = np.meshgrid(G.node_x, G.node_y)
+    return f(x, y)
+
+
+@pytest.mark.parametrize("i,j,fx,fy", [(1, 1, 0.0, 0.0), (5, 7, 0.3, 0.8), (29, 13, 0.999, 0.01), (16, 8, 0.5, 0.5)])
+def test_linear_potential_is_reproduced(i, j, fx, fy):
+    a, b, c = 2.5, -1.25, 0.75
+    phi = node_field(lambda x, y: a * x + b * y + c)
+    u, gx, gy = oracle.bezier_point(G, phi, i, j, fx, fy)
+    x = G.xmin + (i + fx) * G.hx
+    y = G.ymin + (j + fy) * G.hy
+    assert abs(u - (a * x + b * y + c)) < 1e-14
+    assert abs(gx - a) < 1e-13 and abs(gy - b) < 1e-13
+
+
+@pytest.mark.parametrize("i,fx", [(3, 0.0), (10, 0.25), (20, 0.9)])
+def test_quadratic_is_smoothed_by_the_bernstein_amount(i, fx):
+    phi = node_field(lambda x, y: x * x + 0 * y)
+    u, gx, gy = oracle.bezier_point(G, phi, i, 6, fx, 0.4)
+    x = G.xmin + (i + fx) * G.hx
+    t = (1 + fx) / 3
+    assert abs(u - (x * x + 3 * t * (1 - t) * G.hx ** 2)) < 1e-14
+    assert abs(gx - (2 * x + G.hx * (1 - 2 * t))) < 1e-13
+    assert abs(gy) < 1e-14
+
+
+def test_constant_gives_no_field():
+    phi = node_field(lambda x, y: 0 * x + 3.0)
+    u, gx, gy = oracle.bezier_point(G, phi, 12, 5, 0.37, 0.61)
+    assert abs(u - 3.0) < 1e-14 and abs(gx) < 1e-13 and abs(gy) < 1e-13
+
+
+def test_round_gaussian_in_a_wide_pipe():
+    g = oracle.Geometry(257, 257, -20.0, 20.0, -20.0, 20.0)
+    x, y = np.meshgrid(g.node_x, g.node_y)
+    q = np.exp(-(x ** 2 + y ** 2) / 2)
+    q /= q.sum()
+    Q = np.round(q * oracle.Q_UNIT * 1000).astype(np.uint64)
+    phi = oracle.potential_pipe(g, oracle.normalise(Q, 1000))[1:-1, 1:-1]
+    r = np.linspace(1.0, 2.5, 7)
+    st = {k: np.zeros(len(r)) for k in ("x", "px", "y", "py", "sigma", "psigma")}
+    st["x"] = r.copy()
+    oracle.kick_bezier(g, None, st, phi[None], 1.0)
+    np.testing.assert_allclose(st["px"], (1 - np.exp(-r ** 2 / 2)) / r, rtol=2e-2)
+    assert np.abs(st["py"]).max() < 1e-3 * st["px"].max()
+
+
+def test_symmetric_beam_gets_antisymmetric_kicks():
+    g = oracle.Geometry(65, 65, -0.02, 0.02, -0.02, 0.02)
+    parts = synth.gaussian_bunch(100000, 3, 3e-3, 3e-3, 1e-4, 1e-4)
+    xs = np.concatenate([parts["x"], -parts["x"]])
+    ys = np.concatenate([parts["y"], parts["y"]])
+    Q, _ = oracle.deposit(g, xs, ys)
+    Q = Q + Q[:, ::-1]  # exactly mirror-symmetric in x
+    phi = oracle.potential_pipe(g, oracle.normalise(Q, 2 * len(xs)))[1:-1, 1:-1]
+    probe = np.array([0.001, 0.004, 0.009])
+    a = {k: np.zeros(3) for k in ("x", "px", "y", "py", "sigma", "psigma")}
+    b = {k: np.zeros(3) for k in ("x", "px", "y", "py", "sigma", "psigma")}
+    a["x"], b["x"] = probe.copy(), -probe
+    a["y"][:] = b["y"][:] = 0.0013
+    oracle.kick_bezier(g, None, a, phi[None], 1.0)
+    oracle.kick_bezier(g, None, b, phi[None], 1.0)
+    np.testing.assert_allclose(a["px"], -b["px"], rtol=1e-10)
+    np.testing.assert_allclose(a["py"], b["py"], rtol=1e-10)
+    assert np.all(a["px"] > 0)
