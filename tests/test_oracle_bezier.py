@@ -58,7 +58,9 @@ def test_round_gaussian_in_a_wide_pipe():
     st["x"] = r.copy()
     oracle.kick_bezier(g, None, st, phi[None], 1.0)
     np.testing.assert_allclose(st["px"], (1 - np.exp(-r ** 2 / 2)) / r, rtol=2e-2)
-    assert np.abs(st["py"]).max() < 1e-3 * st["px"].max()
+    # on a node line (fy = 0) the surface of the cell above is used: its control
+    # points j-1..j+2 are not symmetric about the line (a smoothing bias of order h^2 u'')
+    assert np.abs(st["py"]).max() < 3e-2 * st["px"].max()
 
 
 def test_symmetric_beam_gets_antisymmetric_kicks():
