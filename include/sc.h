@@ -185,6 +185,18 @@ sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particle
  * u dlambda/dz.  Errors: SC_ERR_UNSUPPORTED (not a sliced pipe grid). */
 sc_status sc_set_longitudinal_kick(sc_grid *g, int enable);
 
+/* Field gather of the kick (sc_set_gather).  BILINEAR: the node fields
+ * interpolated with the CIC weights (Sec. IV-A).  BEZIER: E = -grad of the
+ * Bezier surface of the potential over the 4 x 4 nodes i-1..i+2, j-1..j+2
+ * (Sec. IV-C), the cubic's parameter running over those nodes,
+ * t = (x - x_{i-1}) / (3 hx); nodes beyond the walls take the odd extension;
+ * on a sliced grid with the longitudinal kick the neighbouring slices'
+ * potentials come from the same surfaces.  BEZIER needs a SC_SOLVE_PIPE_FP64
+ * grid (SC_ERR_UNSUPPORTED otherwise). */
+#define SC_GATHER_BILINEAR 0
+#define SC_GATHER_BEZIER 1
+sc_status sc_set_gather(sc_grid *g, int mode);
+
 /* Synchronous copy-out of a pipe grid's potential (n_slices*ny*nx float64,
  * row-major, 0 on the walls): normalised like the fields (per unit line
  * charge, -ln r normalisation), i.e. phi solves lap phi = -2 pi q / (hx hy).

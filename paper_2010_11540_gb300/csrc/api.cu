@@ -104,6 +104,13 @@ static bool any_quad(const sc_element* e, int n) {
   return false;
 }
 
+// thick sextupoles and exact dipoles need the extended kernels
+static bool any_xe(const sc_element* e, int n) {
+  for (int k = 0; k < n; ++k)
+    if (e[k].type == SC_EXACT_BEND || (e[k].type == SC_SEXT && e[k].length > 0.0)) return true;
+  return false;
+}
+
 // K = 2 r_p N_lambda / (beta0^2 gamma0^3): the transverse kick of Sec. IV per
 // unit length and unit normalised field.
 double kick_strength(const sc_beam* b) {
@@ -137,6 +144,10 @@ void set_kick(KPParams& P, const sc_grid* g, double kl, double gamma0) {
     P.phi = g->pipe.phi;
     P.klz = kl * gamma0 / (2.0 * (g->zmax - g->zmin) / (double)g->nz);
   }
+  if (g->gather == SC_GATHER_BEZIER) {
+    P.bezier = 1;
+    P.phi = g->pipe.phi;
+  }
 }
 
 // The cell cache a deposit writes follows the deposit grid's field precision.
@@ -153,6 +164,7 @@ void set_deposit(KPParams& P, sc_grid* d) {
 void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, const DevElem* dev) {
   P.n_elem = n;
   P.has_quad = any_quad(host, n);
+  P.has_xe = any_xe(host, n);
   if (n <= KP_INLINE) {
     compile_elements(host, n, b, P.inl);
     P.el = nullptr;
@@ -385,6 +397,16 @@ sc_status sc_set_longitudinal_kick(sc_grid* g, int enable) {
   return SC_OK;
 }
 
+sc_status sc_set_gather(sc_grid* g, int mode) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (mode != SC_GATHER_BILINEAR && mode != SC_GATHER_BEZIER) return set_error(SC_ERR_ARG, "unknown gather mode");
+  if (mode == SC_GATHER_BEZIER && g->precision != SC_SOLVE_PIPE_FP64)
+    return set_error(SC_ERR_UNSUPPORTED, "the Bezier gather needs the potential of a SC_SOLVE_PIPE_FP64 grid");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  g->gather = mode;
+  return SC_OK;
+}
+
 sc_status sc_grid_read_potential(sc_grid* g, double* phi) {
   if (!g || !phi) return set_error(SC_ERR_ARG, "grid or phi is NULL");
   if (g->precision != SC_SOLVE_PIPE_FP64) return set_error(SC_ERR_UNSUPPORTED, "only pipe grids keep the potential");
@@ -481,6 +503,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   put(&want_diag, sizeof want_diag);
   put(&g->trace, sizeof g->trace);
   put(&g->lon, sizeof g->lon);
+  put(&g->gather, sizeof g->gather);
   put(&g->tune_acc, sizeof g->tune_acc);
   put(g->tune_twiss, sizeof g->tune_twiss);
 

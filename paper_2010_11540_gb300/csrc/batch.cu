@@ -34,6 +34,7 @@ struct BatchPlan {
   KPParams* d_descs = nullptr;
   int n_launches = 0;
   std::vector<char> launch_cache;  // CACHE flag per launch
+  std::vector<char> launch_xe;     // extended-element kernels per launch (any bunch's segment needs them)
   int4* d_blocks = nullptr;
   int n_blocks = 0;
   int tile_cells = 0;
@@ -307,6 +308,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     T->n_launches = 1 + (T->has_head ? 1 : 0) + n_marks;
     std::vector<KPParams> descs((size_t)T->n_launches * nb);
     T->launch_cache.assign(T->n_launches, 0);
+    T->launch_xe.assign(T->n_launches, 0);
     for (int b = 0; b < nb; ++b) {
       const sc_bunch& u = bunches[b];
       const sc_particles* p = &u.particles;
@@ -363,6 +365,9 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         T->launch_cache[L] = 1;
       }
     }
+    for (int L = 0; L < T->n_launches; ++L)
+      for (int b = 0; b < nb; ++b)
+        if (descs[(size_t)L * nb + b].has_xe || descs[(size_t)L * nb + b].bezier) T->launch_xe[L] = 1;
     SC_CUDA(cudaMalloc(&T->d_descs, descs.size() * sizeof(KPParams)));
     SC_CUDA(cudaMemcpy(T->d_descs, descs.data(), descs.size() * sizeof(KPParams), cudaMemcpyHostToDevice));
     if (B->trace) {
@@ -389,7 +394,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     if (T->has_head) {
       if (!cst && any)
         cst = launch_kick_push_batched(T->d_descs + (size_t)L * nb, T->d_blocks, T->n_blocks, T->tile_cells, f32,
-                                       T->launch_cache[L] != 0, S);
+                                       T->launch_cache[L] != 0, T->launch_xe[L] != 0, S);
       ++L;
     }
     for (int k = 0; !cst && k < n_marks; ++k, ++L) {
@@ -401,7 +406,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         cst = set_error(SC_ERR_CUDA, "event");
       if (!cst && any)
         cst = launch_kick_push_batched(T->d_descs + (size_t)L * nb, T->d_blocks, T->n_blocks, T->tile_cells, f32,
-                                       T->launch_cache[L] != 0, S);
+                                       T->launch_cache[L] != 0, T->launch_xe[L] != 0, S);
       if (!cst && B->trace && cudaEventRecordWithFlags(T->ev[3 * k + 2], S, cudaEventRecordExternal) != cudaSuccess)
         cst = set_error(SC_ERR_CUDA, "event");
     }
@@ -442,7 +447,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     if (!T->has_head && T->n_kicks > 0)
       for (sc_grid* g : B->cls) SC_CUDA(cudaMemsetAsync(g->Q, 0, cells_of(g) * g->nstack * 8, S));
     if ((st = launch_kick_push_batched(T->d_descs, T->d_blocks, T->n_blocks, T->tile_cells, f32,
-                                       T->launch_cache[0] != 0, S)))
+                                       T->launch_cache[0] != 0, T->launch_xe[0] != 0, S)))
       return st;
   }
   for (int t = 0; t < n_turns; ++t) {

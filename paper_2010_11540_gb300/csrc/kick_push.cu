@@ -21,6 +21,25 @@ constexpr int kp_max_threads() {
   return F32 ? 768 : 640;
 }
 
+// Kick from the Bezier surface of the potential (Sec. IV-C): E = -grad u, and
+// with the longitudinal kick the neighbouring slices' u from the same
+// surfaces.  Not inlined: its registers stay out of the bilinear path.
+__device__ __noinline__ void bezier_kick(State& s, const KPParams& P, int cell, double fx, double fy) {
+  const int nxk = P.gk.nx, nyk = P.gk.ny, cells = nxk * nyk;
+  const int k = cell / cells, rem = cell - k * cells, j = rem / nxk, i = rem - j * nxk;
+  const double* ph = P.phi + (size_t)k * cells;
+  double u, gx, gy;
+  bezier_eval<false, true>(ph, nxk, nyk, i, j, fx, fy, u, gx, gy);
+  s.px = fma(-P.kl * (1.0 / 3.0) * P.gk.inv_hx, gx, s.px);
+  s.py = fma(-P.kl * (1.0 / 3.0) * P.gk.inv_hy, gy, s.py);
+  if (P.lon) {
+    double up = 0.0, dn = 0.0, a, b;
+    if (k + 1 < P.gk.nz) bezier_eval<true, false>(ph + cells, nxk, nyk, i, j, fx, fy, up, a, b);
+    if (k > 0) bezier_eval<true, false>(ph - cells, nxk, nyk, i, j, fx, fy, dn, a, b);
+    s.ps = fma(-P.klz, up - dn, s.ps);
+  }
+}
+
 // One block's share of a space-charge location: particles p_begin, p_begin +
 // p_step, ... below p_end.  use_tile: deposit into the block's shared-memory
 // tile (zeroed by the caller), flushed at the end; CACHE: the cell cache of
@@ -28,7 +47,7 @@ constexpr int kp_max_threads() {
 // deposit; F32: float32 fields and gather (the split-precision solve's fields
 // carry float32 accuracy; the fractions are then the deposit's own fixed-point
 // weights), else float64 fields and fractions.
-template <bool CACHE, bool F32>
+template <bool CACHE, bool F32, bool XE>
 __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile, unsigned long long* tile,
                                                 int* tile_k, int64_t p_begin, int64_t p_end, int64_t p_step) {
   const int cells = P.gd.nx * P.gd.ny;
@@ -73,7 +92,9 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           int2 a;
           cell = locate<true>(P.gk, s.x, s.y, s.sg, a, fx, fy);
         }
-        if (cell >= 0) {
+        if (XE && cell >= 0 && P.bezier) {
+          bezier_kick(s, P, cell, fx, fy);
+        } else if (cell >= 0) {
           const double2* e = P.E + cell;
           const double2 e00 = __ldg(e), e10 = __ldg(e + 1);
           const double2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
@@ -117,8 +138,8 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
       ps_const(k, s.ps, P.beta0_sq, fresh || P.has_quad != 0);
     }
     const bool quads = psc_mode != 0 || P.has_quad != 0;
-    const bool changed = P.el ? push_elements(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads)
-                              : push_elements(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads);
+    const bool changed = P.el ? push_elements<XE>(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads)
+                              : push_elements<XE>(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads);
     if (fresh || (psc_mode == 1 && changed)) {
       P.psc[p] = k.opd2;
       P.psc[n + p] = k.opb;
@@ -164,8 +185,9 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
   }
 }
 
-// One grid, one location.  TILE: the deposit grid fits the shared-memory tile.
-template <bool TILE, bool CACHE, bool F32>
+// One grid, one location.  TILE: the deposit grid fits the shared-memory tile;
+// XE: thick sextupoles, exact dipoles or the Bezier gather may occur.
+template <bool TILE, bool CACHE, bool F32, bool XE>
 __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
   __shared__ int tile_k;  // slice held by the tile (-1: not yet claimed)
@@ -187,14 +209,14 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
   const int64_t p_begin = chunked ? (int64_t)blockIdx.x * chunk : (int64_t)blockIdx.x * blockDim.x;
   const int64_t p_end = chunked ? min(P.n, (int64_t)(blockIdx.x + 1) * chunk) : P.n;
   const int64_t p_step = chunked ? (int64_t)blockDim.x : (int64_t)gridDim.x * blockDim.x;
-  kick_push_range<CACHE, F32>(P, TILE, tile, &tile_k, p_begin, p_end, p_step);
+  kick_push_range<CACHE, F32, XE>(P, TILE, tile, &tile_k, p_begin, p_end, p_step);
 }
 
 // Many bunches, one location each, one launch.  Block b works for bunch
 // blocks[b].x (its descriptor descs[bunch], copied to shared memory) on the
 // contiguous chunk blocks[b].y of blocks[b].z equal chunks of that bunch.
 // The bunch's deposit uses the tile when its grid fits tile_cells.
-template <bool CACHE, bool F32>
+template <bool CACHE, bool F32, bool XE>
 __global__ void __launch_bounds__(kp_max_threads<F32>())
     kick_push_batched(const KPParams* __restrict__ descs, const int4* __restrict__ blocks, int tile_cells) {
   extern __shared__ unsigned long long tile[];
@@ -218,77 +240,97 @@ __global__ void __launch_bounds__(kp_max_threads<F32>())
   const int64_t chunk = (sP.n + bt.z - 1) / bt.z;
   const int64_t p_begin = (int64_t)bt.y * chunk;
   const int64_t p_end = min(sP.n, p_begin + chunk);
-  kick_push_range<CACHE, F32>(sP, use_tile, tile, &tile_k, p_begin, p_end, blockDim.x);
+  kick_push_range<CACHE, F32, XE>(sP, use_tile, tile, &tile_k, p_begin, p_end, blockDim.x);
 }
 
-template <bool TILE, bool CACHE, bool F32>
-int blocks_for(int smem) {
-  int dev = 0, sms = 0, per = 0;
+using KPKernel = void (*)(KPParams);
+using KPBatched = void (*)(const KPParams*, const int4*, int);
+
+// kick_push_kernel<TILE, CACHE, F32, XE> indexed by the four flags
+KPKernel kp_kernel(bool tile, bool cache, bool f32, bool xe) {
+  static const KPKernel k[16] = {
+      kick_push_kernel<false, false, false, false>, kick_push_kernel<false, false, false, true>,
+      kick_push_kernel<false, false, true, false>,  kick_push_kernel<false, false, true, true>,
+      kick_push_kernel<false, true, false, false>,  kick_push_kernel<false, true, false, true>,
+      kick_push_kernel<false, true, true, false>,   kick_push_kernel<false, true, true, true>,
+      kick_push_kernel<true, false, false, false>,  kick_push_kernel<true, false, false, true>,
+      kick_push_kernel<true, false, true, false>,   kick_push_kernel<true, false, true, true>,
+      kick_push_kernel<true, true, false, false>,   kick_push_kernel<true, true, false, true>,
+      kick_push_kernel<true, true, true, false>,    kick_push_kernel<true, true, true, true>};
+  return k[(tile ? 8 : 0) + (cache ? 4 : 0) + (f32 ? 2 : 0) + (xe ? 1 : 0)];
+}
+
+KPBatched kp_batched(bool cache, bool f32, bool xe) {
+  static const KPBatched k[8] = {kick_push_batched<false, false, false>, kick_push_batched<false, false, true>,
+                                 kick_push_batched<false, true, false>,  kick_push_batched<false, true, true>,
+                                 kick_push_batched<true, false, false>,  kick_push_batched<true, false, true>,
+                                 kick_push_batched<true, true, false>,   kick_push_batched<true, true, true>};
+  return k[(cache ? 4 : 0) + (f32 ? 2 : 0) + (xe ? 1 : 0)];
+}
+
+// Resident blocks per SM of the smallest-occupancy variant for this tile size.
+int min_blocks(int smem, bool tile) {
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (TILE)
-    cudaFuncSetAttribute(kick_push_kernel<TILE, CACHE, F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kick_push_kernel<TILE, CACHE, F32>, kp_max_threads<F32>(), smem);
-  return sms * (per < 1 ? 1 : per);
-}
-
-template <bool TILE>
-int min_blocks(int smem) {
-  const int c[4] = {blocks_for<TILE, false, false>(smem), blocks_for<TILE, false, true>(smem),
-                    blocks_for<TILE, true, false>(smem), blocks_for<TILE, true, true>(smem)};
-  int b = c[0];
-  for (int v : c) b = v < b ? v : b;
-  return b;
+  int best = 1 << 30;
+  for (int v = 0; v < 8; ++v) {
+    const bool cache = v & 4, f32 = v & 2, xe = v & 1;
+    const KPKernel k = kp_kernel(tile, cache, f32, xe);
+    if (tile) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, f32 ? kp_max_threads<true>() : kp_max_threads<false>(),
+                                                  tile ? smem : 0);
+    best = per < best ? per : best;
+  }
+  return sms * (best < 1 ? 1 : best);
 }
 
 }  // namespace
 
 int kick_push_blocks_for(int smem_bytes, bool tile) {
   // all variants share the shared memory size; size the grid on the largest register count
-  return tile ? min_blocks<true>(smem_bytes) : min_blocks<false>(0);
+  return min_blocks(smem_bytes, tile);
 }
 
 sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s) {
   const bool tile = P.do_deposit && dep && deposit_uses_tile(dep);
   const bool cache = P.cell != nullptr;
   const bool f32 = P.field32 != 0;
+  const bool xe = P.has_xe != 0 || P.bezier != 0;
   // the variant's largest block: measured, the extra warps outweigh a partly empty last round
   const int threads = f32 ? kp_max_threads<true>() : kp_max_threads<false>();
   const int64_t need = (P.n + threads - 1) / threads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
   const int smem = tile ? dep->nx * dep->ny * 8 : 0;
-  decltype(&kick_push_kernel<true, true, true>) k;
-  if (tile)
-    k = cache ? (f32 ? kick_push_kernel<true, true, true> : kick_push_kernel<true, true, false>)
-              : (f32 ? kick_push_kernel<true, false, true> : kick_push_kernel<true, false, false>);
-  else
-    k = cache ? (f32 ? kick_push_kernel<false, true, true> : kick_push_kernel<false, true, false>)
-              : (f32 ? kick_push_kernel<false, false, true> : kick_push_kernel<false, false, false>);
-  SC_CUDA(launch_pdl(k, dim3(blocks), dim3(threads), (size_t)smem, s, P));
+  SC_CUDA(launch_pdl(kp_kernel(tile, cache, f32, xe), dim3(blocks), dim3(threads), (size_t)smem, s, P));
   return SC_OK;
 }
 
 int kick_push_batched_threads(bool f32) { return f32 ? kp_max_threads<true>() : kp_max_threads<false>(); }
 
 int kick_push_batched_resident(int smem_bytes, bool f32, bool cache) {
-  int dev = 0, sms = 0, per = 0;
+  int dev = 0, sms = 0, per = 1 << 30;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  decltype(&kick_push_batched<true, true>) ks[4] = {kick_push_batched<false, false>, kick_push_batched<false, true>,
-                                                     kick_push_batched<true, false>, kick_push_batched<true, true>};
-  for (auto k : ks) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  auto k = ks[(cache ? 2 : 0) + (f32 ? 1 : 0)];
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kick_push_batched_threads(f32), smem_bytes);
+  for (int v = 0; v < 8; ++v) {
+    const KPBatched k = kp_batched(v & 4, v & 2, v & 1);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  }
+  for (int xe = 0; xe < 2; ++xe) {
+    int p = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kp_batched(cache, f32, xe), kick_push_batched_threads(f32),
+                                                  smem_bytes);
+    per = p < per ? p : per;
+  }
   return sms * (per < 1 ? 1 : per);
 }
 
 sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
-                                   bool cache, cudaStream_t s) {
-  auto k = cache ? (f32 ? kick_push_batched<true, true> : kick_push_batched<true, false>)
-                 : (f32 ? kick_push_batched<false, true> : kick_push_batched<false, false>);
+                                   bool cache, bool xe, cudaStream_t s) {
   // (the shared-memory limit was raised by kick_push_batched_resident, called before any launch)
-  SC_CUDA(launch_pdl(k, dim3(n_blocks), dim3(kick_push_batched_threads(f32)), (size_t)tile_cells * 8, s, descs,
-                     blocks, tile_cells));
+  SC_CUDA(launch_pdl(kp_batched(cache, f32, xe), dim3(n_blocks), dim3(kick_push_batched_threads(f32)),
+                     (size_t)tile_cells * 8, s, descs, blocks, tile_cells));
   return SC_OK;
 }
 

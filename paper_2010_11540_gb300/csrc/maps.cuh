@@ -143,16 +143,21 @@ __device__ __forceinline__ void sext_kick(State& s, double half, double full) {
   s.py = fma(full * s.x, s.y, s.py);
 }
 
-__device__ __forceinline__ void map_sext(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
-  if (e.flags != 1) {
-    sext_kick(s, e.p[0], e.p[1]);
-    return;
-  }
+// (Thick elements and the exact dipole are not inlined: their registers stay
+// out of the hot kernels' allocation.)
+__device__ __noinline__ void map_sext_thick(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
   h0_flow(s, k, e.p[2], inv_gamma0_sq);
   sext_kick(s, e.p[0], e.p[1]);
   h0_flow(s, k, e.p[3], inv_gamma0_sq);
   sext_kick(s, e.p[0], e.p[1]);
   h0_flow(s, k, e.p[2], inv_gamma0_sq);
+}
+
+__device__ __forceinline__ void map_sext(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
+  if (e.flags != 1)
+    sext_kick(s, e.p[0], e.p[1]);
+  else
+    map_sext_thick(s, e, k, inv_gamma0_sq);
 }
 
 // Exact sector dipole (Sec. III-A, uniform field without H_approx): the
@@ -163,7 +168,7 @@ __device__ __forceinline__ void map_sext(State& s, const DevElem& e, const PsCon
 //   alpha = angle + asin(px0/P) - asin(px/P),
 //   y += py rho alpha,  sg += L - (1 + beta0^2 ps) rho alpha.
 // e.p = {L, angle, C, S, rho, 1/rho}; zero angle (e.flags = 1): the exact drift.
-__device__ __forceinline__ void map_exact_bend(State& s, const DevElem& e, const PsConst& k) {
+__device__ __noinline__ void map_exact_bend(State& s, const DevElem& e, const PsConst& k) {
   if (e.flags == 1) {
     map_drift(s, e, k);
     return;
@@ -213,7 +218,10 @@ __device__ __forceinline__ void map_rf(State& s, const DevElem& e) {
 
 // Push through n_elem elements with the ps-dependent quantities k (valid on
 // entry).  quads: refresh k's square roots after an RF cavity.  Returns true
-// when an RF cavity changed ps (k then holds the new values).
+// when an RF cavity changed ps (k then holds the new values).  XE: the
+// segment may hold thick sextupoles or exact dipoles (their code is compiled
+// only into the kernels that need it, keeping the common kernels' registers).
+template <bool XE>
 __device__ __forceinline__ bool push_elements(State& s, PsConst& k, const DevElem* __restrict__ el, int n_elem,
                                               double beta0_sq, double inv_gamma0_sq, bool quads) {
   bool changed = false;
@@ -223,9 +231,16 @@ __device__ __forceinline__ bool push_elements(State& s, PsConst& k, const DevEle
     switch (e.type) {
       case SC_DRIFT: map_drift(s, e, k); break;
       case SC_QUAD: map_quad(s, e, k, inv_gamma0_sq); break;
-      case SC_SEXT: map_sext(s, e, k, inv_gamma0_sq); break;
-      case SC_EXACT_BEND: map_exact_bend(s, e, k); break;
+      case SC_SEXT:
+        if (XE)
+          map_sext(s, e, k, inv_gamma0_sq);
+        else
+          sext_kick(s, e.p[0], e.p[1]);
+        break;
       case SC_BEND: map_bend(s, e, k, inv_gamma0_sq); break;
+      case SC_EXACT_BEND:
+        if (XE) map_exact_bend(s, e, k);
+        break;
       case SC_RF:
         map_rf(s, e);
         ps_const(k, s.ps, beta0_sq, quads);

@@ -101,6 +101,7 @@ struct KPParams {
   const DevElem* el;  // device array of the segment's compiled elements, or NULL: use inl
   int n_elem;
   int has_quad;       // the segment holds an SC_QUAD
+  int has_xe;         // the segment holds a thick SC_SEXT or an SC_EXACT_BEND
   // Per-particle ps-dependent quantities, 5 arrays of n: (1+delta)^2,
   // 1 + beta0^2 ps, sqrt(1-ps), 1/sqrt(1-ps), 1/(4(1-ps)).  psc_mode 0: none
   // (computed in registers), 1: read (rewritten after an RF cavity), 2: compute and write.
@@ -112,6 +113,10 @@ struct KPParams {
   int lon;
   const double* phi;
   double klz;
+  // Bezier gather (pipe grids, float64 form): E = -grad of the Bezier surface
+  // of phi (Sec. IV-C) instead of bilinear node fields; with lon the
+  // neighbouring slices' potentials come from the same surfaces.
+  int bezier;
   DevElem inl[KP_INLINE];
 };
 
@@ -176,6 +181,7 @@ struct sc_grid {
   double trace_kp_ms, trace_solve_ms;
   int64_t trace_kicks;
   int lon;                     // longitudinal kick on (sliced pipe grids)
+  int gather;                  // SC_GATHER_BILINEAR or SC_GATHER_BEZIER (pipe grids)
   int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
   int kp_blocks_plain;         // kick/push without a deposit
   sc::DevElem* el_stage;       // device copy of sc_kick_push's last long segment
@@ -192,7 +198,7 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
 // Batched form: descs[bunch] per bunch, blocks[b] = (bunch, chunk, chunks of that bunch, 0) per block;
 // deposits of grids with at most tile_cells nodes go through the shared-memory tile.
 sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
-                                   bool cache, cudaStream_t s);
+                                   bool cache, bool xe, cudaStream_t s);
 int kick_push_batched_resident(int smem_bytes, bool f32, bool cache);  // resident blocks on the device
 bool deposit_uses_tile(const sc_grid* g);
 int deposit_blocks_for(int smem_bytes, bool tile);

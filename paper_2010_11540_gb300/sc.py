@@ -29,7 +29,7 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
-           "sc_set_longitudinal_kick",
+           "sc_set_longitudinal_kick", "sc_set_gather",
            "sc_last_error")
 
 
@@ -102,6 +102,7 @@ def load():
     L.sc_probe_peaks.argtypes = [dp, dp, dp, vp]
     L.sc_grid_read_potential.argtypes = [vp, vp]
     L.sc_set_longitudinal_kick.argtypes = [vp, ctypes.c_int]
+    L.sc_set_gather.argtypes = [vp, ctypes.c_int]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -228,6 +229,14 @@ def grid_read(grid: Grid):
 def set_longitudinal_kick(grid: Grid, enable: bool = True):
     """Longitudinal space-charge kick on a sliced conducting-pipe grid."""
     _check(load().sc_set_longitudinal_kick(grid.handle, 1 if enable else 0))
+
+
+GATHER = {"bilinear": 0, "bezier": 1}
+
+
+def set_gather(grid: Grid, mode: str):
+    """Field gather of the kick: "bilinear" node fields, or "bezier" (Sec. IV-C, pipe grids)."""
+    _check(load().sc_set_gather(grid.handle, GATHER[mode]))
 
 
 def grid_read_potential(grid: Grid):

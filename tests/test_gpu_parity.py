@@ -651,3 +651,56 @@ def test_track_longitudinal_one_turn():
     ref0 = oracle.copy_state(parts)
     oracle.track(oracle.Geometry(*grid), ref0, b, lat, 1, slices=zs, boundary="pipe")
     assert np.abs(ref0["psigma"] - ref["psigma"]).max() > 1e3 * np.abs(got["psigma"] - ref["psigma"]).max()
+
+
+# ------------------------------------------------------------------ Bezier gather (Sec. IV-C)
+def test_bezier_kick_single_step():
+    parts, b, _, _ = synth.workload("c2", n=300000)
+    grid = (129, 129) + synth.grid_extent(4e-3, 3e-3)
+    b = dict(b, n_lambda=5e11)
+    g = sc.create_grid(*grid, precision="pipe_fp64")
+    sc.set_gather(g, "bezier")
+    st = to_gpu(parts)
+    sc.deposit(g, st)
+    sc.solve(g)
+    L = 8.0
+    sc.kick_push(g, st, b, L, None)
+    got = to_host(st)
+    og = oracle.Geometry(*grid)
+    ref = oracle.copy_state(parts)
+    Q, _ = oracle.deposit(og, ref["x"], ref["y"])
+    phi = oracle.potential_pipe(og, oracle.normalise(Q, len(ref["x"])))[1:-1, 1:-1]
+    oracle.kick_bezier(og, None, ref, phi[None], oracle.kick_strength(b) * L)
+    for k in ("px", "py"):
+        d_got, d_ref = got[k] - parts[k], ref[k] - parts[k]
+        assert np.abs(d_ref).max() > 0
+        assert np.abs(d_got - d_ref).max() < 1e-10 * np.abs(d_ref).max(), k
+    assert np.array_equal(got["psigma"], parts["psigma"])
+
+
+def test_bezier_needs_a_pipe_grid():
+    g = sc.create_grid(64, 64, -1.0, 1.0, -1.0, 1.0)
+    with pytest.raises(sc.ScError) as e:
+        sc.set_gather(g, "bezier")
+    assert e.value.code == -7
+
+
+def test_track_bezier_longitudinal_one_turn():
+    """Sliced pipe grids, Bezier gather for the transverse and the
+    longitudinal kick, one turn of the c2 ring, against the oracle."""
+    parts, _, _, lat = synth.workload("c5", n=150000)
+    grid = (65, 65) + synth.grid_extent(4e-3, 3e-3)
+    sl = (8, -60.0, 60.0)
+    zs = oracle.Slices(*sl)
+    b = synth.beam(n_lambda=1e12 / zs.dz, circumference=float(lat["length"].sum()))
+    g = sc.create_grid(*grid, precision="pipe_fp64", slices=sl)
+    sc.set_longitudinal_kick(g)
+    sc.set_gather(g, "bezier")
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(oracle.Geometry(*grid), ref, b, lat, 1, slices=zs, boundary="pipe", longitudinal=True,
+                 gather="bezier")
+    err = rel_state_err(got, ref)
+    assert max(err.values()) < 1e-10, err
