@@ -51,6 +51,12 @@ FP64_INST = {"base": 18.1, "drift": 12.1, "quad": 51.0, "sext": 5.0, "bend": 16.
 FP64_INST_BASE_F32 = 8.8
 # sliced grids: the slice index (one subtract, one multiply; the floor is integer work) per locate
 FP64_INST_SLICE = 2.0
+# Bezier gather instead of bilinear fields (extra per particle-kick), and the
+# longitudinal kick (bilinear / Bezier potentials of two slices plus the
+# psigma-dependent quantities recomputed): measured with ncu like FP64_INST
+FP64_INST_BEZIER = 103.7
+FP64_INST_LON = 25.6
+FP64_INST_LON_BEZIER = 83.7
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -66,6 +72,13 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--cpu-kicks", type=int, default=24, help="oracle sample size in kicks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--boundary", default="open", choices=["open", "pipe"],
+                    help="pipe: conducting rectangular pipe on the grid's outer nodes (Sec. IV-B), one more node "
+                         "per axis over the same extent, float64 sine-transform solve")
+    ap.add_argument("--gather", default="bilinear", choices=["bilinear", "bezier"],
+                    help="bezier: Bezier surface of the potential (Sec. IV-C), pipe grids only")
+    ap.add_argument("--longitudinal", action="store_true",
+                    help="longitudinal space-charge kick (Sec. IV), sliced pipe grids (c5 --boundary pipe)")
     ap.add_argument("--tiling", default=None,
                     help="force the split-TF32 solve's kernel variant per phase, e.g. 0,1,2,1 (default: tuned)")
     return ap.parse_args()
@@ -146,7 +159,7 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(config, n_kicks):
+def cpu_baseline(config, n_kicks, boundary="open", gather="bilinear", longitudinal=False):
     """The FP64 oracle as it stands, single-threaded, on a bounded sample:
     the full particle set (c4: its largest bunch) through the first n_kicks
     kicks of turn 1."""
@@ -162,11 +175,15 @@ def cpu_baseline(config, n_kicks):
         what = f"{config} full particle set"
         if "n_slices" in synth.CONFIGS[config]:
             slices = oracle.Slices(*synth.slices(config))
+    if boundary == "pipe":
+        grid = (grid[0] + 1, grid[1] + 1) + tuple(grid[2:])
+        what += f", conducting pipe, {gather} gather" + (", longitudinal kick" if longitudinal else "")
     g = oracle.Geometry(*grid)
     st = oracle.copy_state(parts)
     oracle.lib()
     t0 = time.perf_counter()
-    done = oracle.track(g, st, b, lat, 1, max_kicks=n_kicks, slices=slices)
+    done = oracle.track(g, st, b, lat, 1, max_kicks=n_kicks, slices=slices, boundary=boundary, gather=gather,
+                        longitudinal=longitudinal)
     dt = time.perf_counter() - t0
     n = len(parts["x"])
     return {"value": n * done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -209,10 +226,15 @@ class SingleRun:
 
     kernel = "kick_push_kernel (gather+kick, push, fused CIC deposit)"
 
-    def __init__(self, config, rank, stream):
+    def __init__(self, config, rank, stream, args=None):
         from paper_2010_11540_gb300 import synth
         self.parts, self.b, self.grid, self.lat = synth.workload(config, seed=12345 + rank)
         self.slices = synth.slices(config) if "n_slices" in synth.CONFIGS[config] else None
+        self.pipe = args is not None and args.boundary == "pipe"
+        self.gather = args.gather if args is not None else "bilinear"
+        self.longitudinal = args is not None and args.longitudinal
+        if self.pipe:  # walls on the outer nodes: n - 1 a power of two
+            self.grid = (self.grid[0] + 1, self.grid[1] + 1) + tuple(self.grid[2:])
         self.n = len(self.parts["x"])
         self.stream = stream
         self.n_classes = 1
@@ -224,6 +246,11 @@ class SingleRun:
         g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
         if precision == "tf32x3" and self.tiling:
             sc.set_solver_tiling(g, self.tiling)
+        if precision == "pipe_fp64":
+            if self.gather == "bezier":
+                sc.set_gather(g, "bezier")
+            if self.longitudinal:
+                sc.set_longitudinal_kick(g)
         return g, dev
 
     def tiling_desc(self, h):
@@ -288,6 +315,10 @@ class SingleRun:
         d = {"grid": [self.grid[0], self.grid[1]]}
         if self.slices:
             d["slices"] = list(self.slices)
+        if self.pipe:
+            d["boundary"] = "conducting rectangular pipe on the outer nodes"
+            d["gather"] = self.gather
+            d["longitudinal_kick"] = self.longitudinal
         return d
 
 
@@ -370,7 +401,11 @@ def run_ours(args):
     build.build()
     sc.load()
     stream = torch.cuda.Stream()
-    W = (BatchRun if args.config == "c4" else SingleRun)(args.config, rank, stream)
+    W = BatchRun(args.config, rank, stream) if args.config == "c4" else SingleRun(args.config, rank, stream, args)
+    if args.boundary == "pipe":
+        if args.config == "c4":
+            raise SystemExit("--boundary pipe: single-bunch configs only")
+        args.precision, args.no_compare = "pipe_fp64", True
     W.tiling = [int(v) for v in args.tiling.split(",")] if args.tiling else None
     n = W.n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -409,9 +444,13 @@ def run_ours(args):
             ms = float(t.item())
         return h, ms, wall, clk
 
-    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, args.precision)
+    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, "fp64" if args.precision == "pipe_fp64" else args.precision)
     if getattr(W, "slices", None):
         inst_turn += n_kicks * FP64_INST_SLICE
+    if args.gather == "bezier":
+        inst_turn += n_kicks * FP64_INST_BEZIER
+    if args.longitudinal:
+        inst_turn += n_kicks * (FP64_INST_LON_BEZIER if args.gather == "bezier" else FP64_INST_LON)
     h, ms, wall, clk = timed_turns(args.precision)
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
     compare = None
@@ -461,11 +500,12 @@ def run_ours(args):
     e2e = {"value": world * n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
            "d2h_bytes_per_step": 6 * 8 * n}
 
-    solve_kernels = 3 if args.precision == "fp64" else 4
+    solve_kernels = {"fp64": 3, "tf32x3": 4, "pipe_fp64": 4}[args.precision]
     config = {"workload": WORKLOADS.get(args.config, args.config),
               "step": f"one turn = {n_kicks} SC kicks via "
                       f"{'sc_batch_track_turns' if args.config == 'c4' else 'sc_track_turns'} (CUDA graph)",
-              "solve": "fp64 FFT convolution" if args.precision == "fp64" else "tf32x3 DFT GEMMs on tcgen05",
+              "solve": {"fp64": "fp64 FFT convolution", "tf32x3": "tf32x3 DFT GEMMs on tcgen05",
+                        "pipe_fp64": "fp64 sine transforms (conducting pipe)"}[args.precision],
               "particles": n, **W.grid_desc(),
               "solve_tiling": W.tiling_desc(h),
               "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"}
@@ -476,7 +516,7 @@ def run_ours(args):
             "gpu_launches": args.steps * n_kicks * (W.n_classes * solve_kernels + 1),
             "wall_s_timed": wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_kicks)
+        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_kicks, args.boundary, args.gather, args.longitudinal)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
