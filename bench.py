@@ -57,6 +57,10 @@ FP64_INST_SLICE = 2.0
 FP64_INST_BEZIER = 103.7
 FP64_INST_LON = 25.6
 FP64_INST_LON_BEZIER = 83.7
+# DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
+# from ncu --set full (cold cache, mean of the three segment types): the
+# roofline's "traffic" for that workload; other workloads report null.
+KP_TRAFFIC_C2_TF32 = 109.1e6
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -476,7 +480,10 @@ def run_ours(args):
     achieved = inst_per_kick * n / (kp_avg_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "kernel": W.kernel,
                 "achieved": achieved, "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
-                "frac": achieved / FP64_PIPE_PEAK_TINST, "traffic": None,
+                "frac": achieved / FP64_PIPE_PEAK_TINST,
+                "traffic": (KP_TRAFFIC_C2_TF32 if (args.config == "c2" and args.precision == "tf32x3"
+                                                   and args.gather == "bilinear") else None),
+                "traffic_unit": "DRAM bytes per launch (ncu, cold cache; algorithmic 160 B/particle)",
                 "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (probe: 2.0/clk/SM)",
                 "avg_launch_ms": kp_avg_ms, "fp64_inst_per_particle_kick": inst_per_kick,
                 "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
