@@ -248,7 +248,7 @@ class SingleRun:
         from paper_2010_11540_gb300 import sc
         dev = {k: torch.from_numpy(self.parts[k]).cuda() for k in KEYS}
         g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
-        if precision == "tf32x3" and self.tiling:
+        if precision in ("tf32x3", "pipe_tf32x3") and self.tiling:
             sc.set_solver_tiling(g, self.tiling)
         if precision == "pipe_fp64":
             if self.gather == "bezier":
@@ -259,7 +259,7 @@ class SingleRun:
 
     def tiling_desc(self, h):
         from paper_2010_11540_gb300 import sc
-        if h[0].precision != "tf32x3":
+        if h[0].precision not in ("tf32x3", "pipe_tf32x3"):
             return None
         v, d = sc.get_solver_tiling(h[0])
         return {"variants": v, "grid": d}
@@ -409,7 +409,11 @@ def run_ours(args):
     if args.boundary == "pipe":
         if args.config == "c4":
             raise SystemExit("--boundary pipe: single-bunch configs only")
-        args.precision, args.no_compare = "pipe_fp64", True
+        if args.gather == "bezier" or args.longitudinal or args.precision == "fp64":
+            args.precision = "pipe_fp64"  # the potential-based kicks are float64-form features
+            args.no_compare = True
+        else:
+            args.precision = "pipe_tf32x3"
     W.tiling = [int(v) for v in args.tiling.split(",")] if args.tiling else None
     n = W.n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -448,7 +452,8 @@ def run_ours(args):
             ms = float(t.item())
         return h, ms, wall, clk
 
-    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, "fp64" if args.precision == "pipe_fp64" else args.precision)
+    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, {"pipe_fp64": "fp64", "pipe_tf32x3": "tf32x3"}.get(args.precision,
+                                                                                                 args.precision))
     if getattr(W, "slices", None):
         inst_turn += n_kicks * FP64_INST_SLICE
     if args.gather == "bezier":
@@ -459,7 +464,7 @@ def run_ours(args):
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
     compare = None
     if not args.no_compare:
-        other = "fp64" if args.precision == "tf32x3" else "tf32x3"
+        other = {"tf32x3": "fp64", "fp64": "tf32x3", "pipe_tf32x3": "pipe_fp64"}[args.precision]
         h2, ms2, _, clk2 = timed_turns(other)
         compare = {"precision": other, "value": world * n * n_kicks * args.steps / (ms2 * 1e-3),
                    "ms_per_step": ms2 / args.steps, "clocks": clk2}
@@ -507,12 +512,13 @@ def run_ours(args):
     e2e = {"value": world * n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
            "d2h_bytes_per_step": 6 * 8 * n}
 
-    solve_kernels = {"fp64": 3, "tf32x3": 4, "pipe_fp64": 4}[args.precision]
+    solve_kernels = {"fp64": 3, "tf32x3": 4, "pipe_fp64": 4, "pipe_tf32x3": 5}[args.precision]
     config = {"workload": WORKLOADS.get(args.config, args.config),
               "step": f"one turn = {n_kicks} SC kicks via "
                       f"{'sc_batch_track_turns' if args.config == 'c4' else 'sc_track_turns'} (CUDA graph)",
               "solve": {"fp64": "fp64 FFT convolution", "tf32x3": "tf32x3 DFT GEMMs on tcgen05",
-                        "pipe_fp64": "fp64 sine transforms (conducting pipe)"}[args.precision],
+                        "pipe_fp64": "fp64 sine transforms (conducting pipe)",
+                        "pipe_tf32x3": "tf32x3 sine-transform GEMMs on tcgen05 (conducting pipe)"}[args.precision],
               "particles": n, **W.grid_desc(),
               "solve_tiling": W.tiling_desc(h),
               "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"}

@@ -50,6 +50,10 @@ typedef int sc_status;
  * nodes), float64 sine transforms by FFT; nx - 1, ny - 1 powers of two in
  * 8..512.  The potential is kept (sc_grid_read_potential). */
 #define SC_SOLVE_PIPE_FP64 2
+/* The same conducting pipe with the sine transforms as dense GEMMs on the
+ * tensor cores (3-term split TF32, FP32 accumulate; tiling tuned as for
+ * SC_SOLVE_TF32X3), float32 fields; nx = ny in 10..258. */
+#define SC_SOLVE_PIPE_TF32X3 3
 
 /* Element types (sc_element.type). */
 #define SC_DRIFT 0 /* exact drift, Sec. III-A                                  */
@@ -101,7 +105,7 @@ typedef struct {
  * Green's-function spectra on the device (synchronous on `stream`).
  * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {64, 128, 256}
  * for SC_SOLVE_TF32X3; nx - 1, ny - 1 powers of two in 8..512 for
- * SC_SOLVE_PIPE_FP64.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
+ * SC_SOLVE_PIPE_FP64; nx = ny in 10..258 for SC_SOLVE_PIPE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
  * SC_ERR_OOM, SC_ERR_CUDA.  *out is set only on success. */
 sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
                          double ymax, int precision, void *stream);
@@ -200,8 +204,8 @@ sc_status sc_set_gather(sc_grid *g, int mode);
 /* Synchronous copy-out of a pipe grid's potential (n_slices*ny*nx float64,
  * row-major, 0 on the walls): normalised like the fields (per unit line
  * charge, -ln r normalisation), i.e. phi solves lap phi = -2 pi q / (hx hy).
- * Errors: SC_ERR_ARG (NULL), SC_ERR_UNSUPPORTED (not a SC_SOLVE_PIPE_FP64
- * grid), SC_ERR_CUDA. */
+ * Errors: SC_ERR_ARG (NULL), SC_ERR_UNSUPPORTED (not a pipe grid),
+ * SC_ERR_CUDA. */
 sc_status sc_grid_read_potential(sc_grid *g, double *phi);
 
 /* Per-particle tunes, Sec. V (the betatron tune of a particle is its one-turn

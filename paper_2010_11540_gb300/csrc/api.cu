@@ -174,7 +174,7 @@ void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, 
 }
 
 sc_status solve_dispatch(sc_grid* g, bool zero_q) {
-  if (g->precision == SC_SOLVE_TF32X3) return tf32_solve(g, zero_q);
+  if (g->precision == SC_SOLVE_TF32X3 || g->precision == SC_SOLVE_PIPE_TF32X3) return tf32_solve(g, zero_q);
   if (g->precision == SC_SOLVE_PIPE_FP64) return pipe_solve(g, zero_q);
   return fft64_solve(g, zero_q);
 }
@@ -192,7 +192,8 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   if (!(xmax > xmin) || !(ymax > ymin) || !std::isfinite(xmin) || !std::isfinite(xmax) || !std::isfinite(ymin) ||
       !std::isfinite(ymax))
     return set_error(SC_ERR_ARG, "grid extent must be finite with xmax > xmin, ymax > ymin");
-  if (precision != SC_SOLVE_FP64 && precision != SC_SOLVE_TF32X3 && precision != SC_SOLVE_PIPE_FP64)
+  if (precision != SC_SOLVE_FP64 && precision != SC_SOLVE_TF32X3 && precision != SC_SOLVE_PIPE_FP64 &&
+      precision != SC_SOLVE_PIPE_TF32X3)
     return set_error(SC_ERR_UNSUPPORTED, "unknown solve precision");
   sc_grid* g = new (std::nothrow) sc_grid();
   if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
@@ -203,7 +204,7 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   g->zmin = zmin;
   g->zmax = zmax;
   g->precision = precision;
-  g->field32 = (precision == SC_SOLVE_TF32X3);
+  g->field32 = (precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3);
   g->xmin = xmin;
   g->xmax = xmax;
   g->ymin = ymin;
@@ -255,8 +256,9 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   g->dep_blocks = deposit_blocks_for(tile ? tile_bytes : 0, tile);
   g->kp_blocks = kick_push_blocks_for(tile ? tile_bytes : 0, tile);
   g->kp_blocks_plain = kick_push_blocks_for(0, false);
-  st = (precision == SC_SOLVE_TF32X3) ? tf32_create(g) : (precision == SC_SOLVE_PIPE_FP64) ? pipe_create(g)
-                                                                                             : fft64_create(g);
+  st = (precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3) ? tf32_create(g)
+       : (precision == SC_SOLVE_PIPE_FP64)                                    ? pipe_create(g)
+                                                                              : fft64_create(g);
   if (st == SC_OK) {
     e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) st = cuda_error(e, "sc_create_grid");
@@ -296,7 +298,7 @@ sc_status sc_destroy_grid(sc_grid* g) {
   if (!g) return SC_OK;
   if (g->stream) cudaStreamSynchronize(g->stream);
   destroy_plan(g->track);
-  if (g->precision == SC_SOLVE_TF32X3)
+  if (g->precision == SC_SOLVE_TF32X3 || g->precision == SC_SOLVE_PIPE_TF32X3)
     tf32_destroy(g);
   else if (g->precision == SC_SOLVE_PIPE_FP64)
     pipe_destroy(g);
@@ -409,6 +411,10 @@ sc_status sc_set_gather(sc_grid* g, int mode) {
 
 sc_status sc_grid_read_potential(sc_grid* g, double* phi) {
   if (!g || !phi) return set_error(SC_ERR_ARG, "grid or phi is NULL");
+  if (g->precision == SC_SOLVE_PIPE_TF32X3) {
+    SC_CUDA(cudaStreamSynchronize(g->stream));
+    return tf32_read_potential(g, phi);
+  }
   if (g->precision != SC_SOLVE_PIPE_FP64) return set_error(SC_ERR_UNSUPPORTED, "only pipe grids keep the potential");
   SC_CUDA(cudaStreamSynchronize(g->stream));
   SC_CUDA(cudaMemcpy(phi, g->pipe.phi, (size_t)g->nx * g->ny * g->nstack * sizeof(double), cudaMemcpyDeviceToHost));

@@ -178,7 +178,8 @@ sc_status sc_create_batch(sc_batch** out, const sc_grid_spec* grids, int n_bunch
     sc_status st = create_grid(&g, s.nx, s.ny, s.xmin, s.xmax, s.ymin, s.ymax, 1, 0.0, 0.0, count[c], precision,
                                B->stream);
     if (st == SC_OK) {
-      const size_t bytes = (size_t)count[c] * (precision == SC_SOLVE_TF32X3 ? sizeof(float) : sizeof(double));
+      const bool f32 = precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3;
+      const size_t bytes = (size_t)count[c] * (f32 ? sizeof(float) : sizeof(double));
       cudaError_t e = cudaMalloc(&g->stack_scale, bytes);
       if (e != cudaSuccess) {
         sc_destroy_grid(g);
@@ -242,7 +243,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
   put(&want_diag, sizeof want_diag);
   put(&B->trace, sizeof B->trace);
 
-  const bool f32 = B->precision == SC_SOLVE_TF32X3;
+  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
   BatchPlan* T = B->plan;
   if (!T || T->key != key) {
     destroy_batch_plan(T);

@@ -220,6 +220,7 @@ int tf32_error(sc_grid* g);  // 1 when a tensor-core solve gave up on a bounded 
 // kernel variant per phase (4 entries) chosen by the tuner, with a description
 sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc);
 sc_status tf32_set_tiling(sc_grid* g, const int* choice);  // -1 entries keep the current variant
+sc_status tf32_read_potential(const sc_grid* g, double* out);  // pipe grids of the split form
 // diag.cu
 // out = *base_ptr + stride * (*turn) receives the 14 moments; bumps *turn
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,

@@ -22,6 +22,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -38,7 +39,8 @@ constexpr int TM = 128;         // rows per MMA / M tile
 constexpr int kThreads = 128;   // 4 warps: TMA producer, MMA issuer, TMEM owner, all do the epilogue
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier waits (~2 s of SM clock), then error + bail out
 
-enum Phase { P1 = 0, P2A = 1, P2B = 2, P3 = 3 };
+// P1..P3: open-boundary convolution; D1..D4: conducting-pipe sine transforms
+enum Phase { P1 = 0, P2A = 1, P2B = 2, P3 = 3, D1 = 4, D2 = 5, D3 = 6, D4 = 7 };
 
 // ------------------------------------------------------------------ PTX wrappers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -147,6 +149,7 @@ struct GemmArgs {
   const unsigned long long* Q;
   float scale;
   const float* stack_scale;  // per stacked grid (bunches of a batch), or NULL: scale
+  float qfac;                // D1: extra factor of the charge (-2 pi / (hx hy)); P1: 1
   // P2A: charge grid to clear for the next deposit (NULL: leave it)
   unsigned long long* Qzero;
   long long qcells;
@@ -158,14 +161,19 @@ struct GemmArgs {
   float2* E;               // P3: fields, float32 (Ex, Ey) per node
   long long e_slice;       // P3: nodes per stacked grid
   int* err;                // set to 1 when a bounded wait ran out
+  // conducting pipe (D phases): m interior nodes per axis, mp = m padded to whole M tiles
+  int m, mp;
+  const float* inv_lam;    // D2: 1 / lambda at (q, p), [mp][mp], 0 in the padding
+  float norm;              // D4: 4 / (m+1)^2
+  float* phi;              // D4: potential [stacked grid][ny][nx] (walls stay 0)
 };
 
 // Which operand is a constant DFT matrix (loadable before the grid dependency
 // resolves) and which is the previous kernel's output.
 template <int PH>
 struct Roles {
-  static constexpr bool CONST_A = (PH != P3);
-  static constexpr bool TMA_B = (PH != P1);
+  static constexpr bool CONST_A = (PH != P3 && PH != D4);
+  static constexpr bool TMA_B = (PH != P1 && PH != D1);
 };
 
 template <int PH, int NT, int STAGES_>
@@ -175,7 +183,7 @@ struct Smem {
   static constexpr int STAGE = 2 * A_TILE + (Roles<PH>::TMA_B ? 2 * B_TILE : 0);
   static constexpr int STAGES = STAGES_;
   static constexpr int B_RESIDENT_MAX_CHUNKS = 8;  // P1: charge tiles for K up to 256
-  static constexpr int RESIDENT = (PH == P1) ? 2 * B_RESIDENT_MAX_CHUNKS * B_TILE : 0;
+  static constexpr int RESIDENT = (PH == P1 || PH == D1) ? 2 * B_RESIDENT_MAX_CHUNKS * B_TILE : 0;
   static constexpr int BYTES = STAGES * STAGE + RESIDENT + 1024 /*align slack*/;
   static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
@@ -264,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     }
   }
   pdl_wait();
-  if (PH == P2A && g.Qzero) {
+  if ((PH == P2A || PH == D2) && g.Qzero) {
     // every reader of the charge (the row transform) has finished: clear it for the next deposit
     for (long long c = (long long)blockIdx.x * kThreads + threadIdx.x; c < g.qcells;
          c += (long long)gridDim.x * kThreads)
@@ -275,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     // tile), all K = nx, split hi/lo, swizzled; 16-byte loads, issued in groups of 8.
     const int pairs = NT * g.nx / 2;
     const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx);
-    const float qscale = g.stack_scale ? g.stack_scale[n0 / g.ny] : g.scale;
+    const float qscale = g.qfac * (g.stack_scale ? g.stack_scale[n0 / g.ny] : g.scale);
     constexpr int G = 8;
     for (int e0 = threadIdx.x; e0 < pairs; e0 += G * kThreads) {
       longlong2 v[G];
@@ -301,6 +309,40 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
             *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
             *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
           }
+        }
+      }
+    }
+    fence_proxy_async();
+  }
+  if (PH == D1) {
+    // B operand = interior charge rows of the pipe grid: GEMM row n0 + r = (stacked grid s, interior
+    // row j) <- charge row j+1, K = i <- column i+1, zero beyond the m interior nodes (mp divides
+    // by NT: one stacked grid per tile); scaled to the right-hand side -2 pi q / (hx hy).
+    const int s0 = n0 / g.mp, j0 = n0 - s0 * g.mp;
+    const unsigned long long* q = g.Q + (size_t)s0 * g.nx * g.ny;
+    const float qscale = g.qfac * (g.stack_scale ? g.stack_scale[s0] : g.scale);
+    const int elems = NT * g.mp;
+    constexpr int G = 8;
+    for (int e0 = threadIdx.x; e0 < elems; e0 += G * kThreads) {
+      unsigned long long v[G];
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int e = e0 + u * kThreads;
+        const int r = e / g.mp, i = e - r * g.mp, j = j0 + r;
+        v[u] = (e < elems && i < g.m && j < g.m) ? q[(size_t)(j + 1) * g.nx + (i + 1)] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < G; ++u) {
+        const int e = e0 + u * kThreads;
+        if (e < elems) {
+          const int r = e / g.mp, i = e - r * g.mp;
+          const float qv =
+              fmaf(__uint2float_rn((unsigned)(v[u] >> 32)), 4294967296.f, __uint2float_rn((unsigned)v[u])) * qscale;
+          float hi, lo;
+          split(qv, hi, lo);
+          const int kc = i / KC, k = i % KC;
+          *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
+          *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
         }
       }
     }
@@ -337,7 +379,8 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       }
       tc_fence_after();
       unsigned char* sb = stage_base + st * L::STAGE;
-      const unsigned char* bh = (PH == P1) ? resident + (2 * (kc0 + kc)) * L::B_TILE : sb + 2 * L::A_TILE;
+      const unsigned char* bh =
+          (PH == P1 || PH == D1) ? resident + (2 * (kc0 + kc)) * L::B_TILE : sb + 2 * L::A_TILE;
       const unsigned char* bl = bh + L::B_TILE;
       const uint64_t dbh = desc_sw128(smem_u32(bh)), dbl = desc_sw128(smem_u32(bl));
       const uint64_t dah = desc_sw128(smem_u32(sb)), dal = desc_sw128(smem_u32(sb + L::A_TILE));
@@ -435,7 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
         *(float4*)(g.out_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
         *(float4*)(g.out_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
       }
-    } else {
+    } else if (PH == P3) {
       // stacked row r: grid r / (2 ny); within it field f = (r % 2ny) / ny (Ex, Ey) at j;
       // columns i = n0 + cb + u; float32 (Ex, Ey) pairs
       const int slice = r / (2 * g.ny), rr = r - slice * 2 * g.ny;
@@ -443,6 +486,55 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       float* e = (float*)g.E + 2 * ((size_t)slice * g.e_slice + (size_t)j * g.nx + n0 + cb) + f;
 #pragma unroll
       for (int u = 0; u < CH; ++u) e[2 * u] = acc[u];
+    } else if (PH == D1 || PH == D3) {
+      // D1: row p, columns (s, j) -> T1[s][p][j];  D3: row j, columns (s, p) -> T3[s][j][p]
+      // (one stacked grid per tile, consecutive columns contiguous)
+      const int s0 = n0 / g.mp, c = n0 - s0 * g.mp + cb;
+      const size_t ob = (size_t)s0 * g.out_slice + (size_t)r * g.out_ld + c;
+      float4* dh = (float4*)(g.out_hi + ob);
+      float4* dl = (float4*)(g.out_lo + ob);
+#pragma unroll
+      for (int q4 = 0; q4 < CH / 4; ++q4) {
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) split(acc[4 * q4 + u], h[u], l[u]);
+        dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
+        dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
+      }
+    } else if (PH == D2) {
+      // row q, columns (s, p): U = W / lambda_pq, stored transposed UT[s][p][q] (K = q of D3)
+      float il[CH];
+      int sl[CH], pp[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        const int n = n0 + cb + u;
+        sl[u] = n / g.mp;
+        pp[u] = n - sl[u] * g.mp;
+        il[u] = n < g.n_total ? __ldg(g.inv_lam + (size_t)r * g.mp + pp[u]) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) {
+        if (n0 + cb + u >= g.n_total) continue;
+        const size_t o = (size_t)sl[u] * g.out_slice + (size_t)pp[u] * g.out_ld + r;
+        split(acc[u] * il[u], g.out_hi[o], g.out_lo[o]);
+      }
+    } else {
+      // D4: stacked row (s, f, j) with f = 0: T3 (potential part), 1: its y-derivative; columns
+      // (h, i) with h = 0: S, 1: the x-derivative matrix (one h per tile).  Blocks (0,0) phi,
+      // (0,1) Ex, (1,0) Ey at interior node (i+1, j+1) of grid s; (1,1) is not used.
+      const int s0 = r / (2 * g.mp), rr = r - s0 * 2 * g.mp;
+      const int f = rr / g.mp, j = rr - f * g.mp;
+      const int hblk = n0 / g.mp, i0 = n0 - hblk * g.mp + cb;
+      if (j < g.m && !(f == 1 && hblk == 1)) {
+        const size_t node = (size_t)s0 * g.e_slice + (size_t)(j + 1) * g.nx + 1;
+        float* out = (f == 0 && hblk == 0) ? g.phi + node : (float*)g.E + 2 * node + (f == 0 ? 0 : 1);
+        const int step = (f == 0 && hblk == 0) ? 1 : 2;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+          const int i = i0 + u;
+          if (i < g.m) out[(size_t)step * i] = acc[u] * g.norm;
+        }
+      }
     }
   };
 
@@ -494,6 +586,40 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   if (warp == 2) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// Fields of the conducting-pipe form on the walls (the interior comes from the
+// derivative GEMMs): centred differences with the odd extension across the
+// walls reduce to the first interior potential over h for the normal
+// component; the tangential component vanishes (phi = 0 along a wall).
+__global__ void pipe_walls32(const float* __restrict__ phi, int nx, int ny, int nstack, float inv_hx, float inv_hy,
+                             float2* __restrict__ E) {
+  pdl_wait();
+  const int per = 2 * nx + 2 * (ny - 2);  // perimeter nodes of one grid
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nstack * per; c += gridDim.x * blockDim.x) {
+    const int s = c / per, k = c - s * per;
+    int i, j;
+    if (k < nx) {
+      i = k;
+      j = 0;
+    } else if (k < 2 * nx) {
+      i = k - nx;
+      j = ny - 1;
+    } else if (k < 2 * nx + ny - 2) {
+      i = 0;
+      j = k - 2 * nx + 1;
+    } else {
+      i = nx - 1;
+      j = k - 2 * nx - (ny - 2) + 1;
+    }
+    const float* p = phi + (size_t)s * nx * ny;
+    float ex = 0.f, ey = 0.f;
+    if (i == 0 && j > 0 && j < ny - 1) ex = -p[(size_t)j * nx + 1] * inv_hx;
+    if (i == nx - 1 && j > 0 && j < ny - 1) ex = p[(size_t)j * nx + nx - 2] * inv_hx;
+    if (j == 0 && i > 0 && i < nx - 1) ey = -p[(size_t)nx + i] * inv_hy;
+    if (j == ny - 1 && i > 0 && i < nx - 1) ey = p[(size_t)(ny - 2) * nx + i] * inv_hy;
+    E[(size_t)s * nx * ny + (size_t)j * nx + i] = make_float2(ex, ey);
   }
 }
 
@@ -564,8 +690,15 @@ struct Tf32Plan {
   float *Sx, *Sy;            // [Npad][My]
   int K3;                    // row length of A3 and B4 (2 Npad rounded up to whole split-K chunks)
   int* err;
-  PhaseRun run[4];           // P1, P2A, P2B, P3
+  // conducting pipe (phases D1..D4): sine matrix, intermediates, 1/lambda, potential
+  bool pipe = false;
+  int m = 0, mp = 0;
+  Mat S, SCy, SCx, T1, UT, T3;  // S; [S; Cy] (rows of D3); [S; Cx] (rows of D4's B)
+  float* inv_lam = nullptr;  // [mp][mp]
+  float* phi = nullptr;      // [nstack][ny][nx]
+  PhaseRun run[4];           // the chain's four phases (P1..P3 or D1..D4)
   float tuned_us[4];         // time of the chosen variant when tuned (0: forced)
+  int base() const { return pipe ? D1 : P1; }
 };
 
 namespace {
@@ -614,13 +747,19 @@ Variant variant() {
 // each constant-operand tile once for many columns (stacked grids); narrow,
 // K-split tiles give a single small grid enough CTAs.
 const std::vector<Variant>& variants(int ph) {
-  static const std::vector<Variant> v[4] = {
+  static const std::vector<Variant> v[8] = {
       {variant<P1, 1, 16, 4>(), variant<P1, 1, 32, 4>(), variant<P1, 1, 64, 2>()},
       {variant<P2A, 2, 16, 5>(), variant<P2A, 1, 32, 4>(), variant<P2A, 2, 32, 4>(), variant<P2A, 1, 64, 4>(),
        variant<P2A, 1, 128, 3>()},
       {variant<P2B, 4, 16, 5>(), variant<P2B, 2, 32, 4>(), variant<P2B, 1, 64, 4>(), variant<P2B, 2, 64, 4>(),
        variant<P2B, 1, 128, 3>()},
-      {variant<P3, 2, 16, 5>(), variant<P3, 1, 32, 4>(), variant<P3, 2, 32, 4>(), variant<P3, 1, 64, 4>()}};
+      {variant<P3, 2, 16, 5>(), variant<P3, 1, 32, 4>(), variant<P3, 2, 32, 4>(), variant<P3, 1, 64, 4>()},
+      {variant<D1, 1, 16, 4>(), variant<D1, 1, 32, 4>(), variant<D1, 1, 64, 2>()},
+      {variant<D2, 2, 16, 5>(), variant<D2, 1, 32, 4>(), variant<D2, 2, 32, 4>(), variant<D2, 1, 64, 4>(),
+       variant<D2, 1, 128, 3>()},
+      {variant<D3, 2, 16, 5>(), variant<D3, 1, 32, 4>(), variant<D3, 2, 32, 4>(), variant<D3, 1, 64, 4>(),
+       variant<D3, 1, 128, 3>()},
+      {variant<D4, 2, 16, 5>(), variant<D4, 1, 32, 4>(), variant<D4, 2, 32, 4>(), variant<D4, 1, 64, 4>()}};
   return v[ph];
 }
 
@@ -703,6 +842,7 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
       a.k_chunks = nx / KC;
       a.n_total = nz * ny;
       a.Q = g->Q;
+      a.qfac = 1.f;
       a.out_hi = T->B2.hi;
       a.out_lo = T->B2.lo;
       a.out_ld = 2 * ny;
@@ -739,6 +879,57 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
       a.out_ld = K3;
       a.out_slice = (long long)2 * ny * K3;
       break;
+    case D1:  // T1[p][(s,j)] = S F^T: M = mp (p), N = nz mp (interior rows j of every grid), K = mp (i)
+    case D2:  // W[q][(s,p)] = S T1^T, / lambda -> UT: M = mp (q), N = nz mp, K = mp (j)
+    case D3:  // T3[j][(s,p)] = S UT^T: M = mp (j), N = nz mp, K = mp (q)
+    case D4: {  // u[(s,j)][i] = T3 S^T: M = nz mp, N = mp (i), K = mp (p)
+      const int mp = T->mp;
+      if (mp % v.nt) return set_error(SC_ERR_ARG, "tile width does not divide the padded interior");
+      a.m = T->m;
+      a.mp = mp;
+      a.k_chunks = mp / KC;
+      a.out_ld = mp;
+      a.out_slice = (long long)mp * mp;
+      if (ph == D1 || ph == D2) {
+        if ((st = make_map(&a.tA_hi, T->S.hi, mp, mp, TM)) || (st = make_map(&a.tA_lo, T->S.lo, mp, mp, TM))) return st;
+        M = mp;
+        a.n_total = nz * mp;
+      }
+      if (ph == D1) {
+        a.Q = g->Q;
+        a.qfac = (float)(-2.0 * M_PI / (g->hx * g->hy));
+        a.out_hi = T->T1.hi;
+        a.out_lo = T->T1.lo;
+      } else if (ph == D2) {
+        if ((st = make_map(&a.tB_hi, T->T1.hi, nz * mp, mp, v.nt)) || (st = make_map(&a.tB_lo, T->T1.lo, nz * mp, mp, v.nt)))
+          return st;
+        a.inv_lam = T->inv_lam;
+        a.qcells = (long long)nz * nx * ny;
+        a.out_hi = T->UT.hi;
+        a.out_lo = T->UT.lo;
+      } else if (ph == D3) {  // A = [S; Cy]: rows (f, j), the potential part and its y-derivative
+        if ((st = make_map(&a.tA_hi, T->SCy.hi, 2 * mp, mp, TM)) || (st = make_map(&a.tA_lo, T->SCy.lo, 2 * mp, mp, TM)) ||
+            (st = make_map(&a.tB_hi, T->UT.hi, nz * mp, mp, v.nt)) || (st = make_map(&a.tB_lo, T->UT.lo, nz * mp, mp, v.nt)))
+          return st;
+        M = 2 * mp;
+        a.n_total = nz * mp;
+        a.out_hi = T->T3.hi;
+        a.out_lo = T->T3.lo;
+        a.out_slice = (long long)2 * mp * mp;
+      } else {  // D4: A = T3 rows (s, f, j), B = [S; Cx]: columns (h, i)
+        if ((st = make_map(&a.tA_hi, T->T3.hi, nz * 2 * mp, mp, TM)) ||
+            (st = make_map(&a.tA_lo, T->T3.lo, nz * 2 * mp, mp, TM)) ||
+            (st = make_map(&a.tB_hi, T->SCx.hi, 2 * mp, mp, v.nt)) || (st = make_map(&a.tB_lo, T->SCx.lo, 2 * mp, mp, v.nt)))
+          return st;
+        M = nz * 2 * mp;
+        a.n_total = 2 * mp;
+        a.phi = T->phi;
+        a.E = (float2*)g->E;
+        a.norm = (float)(4.0 / ((double)(T->m + 1) * (double)(T->m + 1)));
+        a.e_slice = (long long)nx * ny;
+      }
+      break;
+    }
     default:  // P3: C[(s,f,j)][i] = A3 B4^T: M = nz 2ny as (Ex, Ey) halves per grid, N = nx, K = K3
       if (nx % v.nt) return set_error(SC_ERR_ARG, "tile wider than a grid's columns");
       if ((st = make_map(&a.tA_hi, T->A3.hi, nz * 2 * ny, K3, TM)) ||
@@ -770,7 +961,8 @@ sc_status tf32_tune(sc_grid* g) {
   SC_CUDA(cudaEventCreate(&e0));
   SC_CUDA(cudaEventCreate(&e1));
   sc_status st = SC_OK;
-  for (int ph = 0; ph < 4 && !st; ++ph) {
+  for (int c = 0; c < 4 && !st; ++c) {
+    const int ph = T->base() + c;
     float best = 1e30f;
     for (int k = 0; k < (int)variants(ph).size() && !st; ++k) {
       PhaseRun r;
@@ -791,11 +983,11 @@ sc_status tf32_tune(sc_grid* g) {
       const float us = 1e3f * ms / reps;
       if (us < best) {
         best = us;
-        T->run[ph] = r;
-        T->tuned_us[ph] = us;
+        T->run[c] = r;
+        T->tuned_us[c] = us;
       }
     }
-    if (!st && T->run[ph].variant < 0) st = set_error(SC_ERR_UNSUPPORTED, "no solve tiling fits this grid");
+    if (!st && T->run[c].variant < 0) st = set_error(SC_ERR_UNSUPPORTED, "no solve tiling fits this grid");
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -803,7 +995,60 @@ sc_status tf32_tune(sc_grid* g) {
   return st;
 }
 
+// Conducting-pipe form (Sec. IV-B) as four dense GEMMs with the real sine
+// matrix S[p][i] = sin(pi (p+1)(i+1) / (m+1)) of the m interior nodes
+// (padded to mp = whole 128-row tiles): T1 = S F^T (rows), W = S T1^T (columns),
+// U = W / lambda, [T3; T3y] = [S; Cy] U^T, and from [T3; T3y] [S; Cx]^T the
+// potential (T3 S^T), Ex (T3 Cx^T) and Ey (T3y S^T), times 4/(m+1)^2.  Cx, Cy
+// are the centred differences of the sine modes (cosine series), so the fields
+// equal the centred differences of phi without forming them (no cancellation).
+sc_status tf32_pipe_create(sc_grid* g) {
+  const int nx = g->nx, ny = g->ny, nz = g->nstack;
+  if (nx != ny || nx < 10 || nx > 258)
+    return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_PIPE_TF32X3 needs nx = ny in 10..258");
+  sc_status st = get_encoder();
+  if (st) return st;
+  Tf32Plan* T = new (std::nothrow) Tf32Plan();
+  if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
+  g->tf32 = T;
+  T->pipe = true;
+  const int m = nx - 2, mp = ((m + TM - 1) / TM) * TM;
+  T->m = m;
+  T->mp = mp;
+  std::vector<double> S((size_t)mp * mp, 0.0);
+  for (int p = 0; p < m; ++p)
+    for (int i = 0; i < m; ++i) S[(size_t)p * mp + i] = std::sin(M_PI * (double)(p + 1) * (double)(i + 1) / (m + 1));
+  // derivative matrices: the centred difference of sin(th (i+1)) is sin(th) cos(th (i+1)) / h, so
+  // -d/dx of the sine series is the series with C[i][p] = -sin(th_p) cos(th_p (i+1)) / hx
+  std::vector<double> SCy((size_t)2 * mp * mp, 0.0), SCx((size_t)2 * mp * mp, 0.0);
+  for (int r = 0; r < m; ++r)
+    for (int k = 0; k < m; ++k) {
+      const double th = M_PI * (double)(k + 1) / (m + 1);
+      SCy[(size_t)r * mp + k] = SCx[(size_t)r * mp + k] = S[(size_t)r * mp + k];
+      SCy[(size_t)(mp + r) * mp + k] = -std::sin(th) * std::cos(th * (r + 1)) / g->hy;
+      SCx[(size_t)(mp + r) * mp + k] = -std::sin(th) * std::cos(th * (r + 1)) / g->hx;
+    }
+  std::vector<float> il((size_t)mp * mp, 0.f);
+  for (int q = 0; q < m; ++q)
+    for (int p = 0; p < m; ++p) {
+      const double sp = std::sin(M_PI * (p + 1) / (2.0 * (m + 1))), sq = std::sin(M_PI * (q + 1) / (2.0 * (m + 1)));
+      il[(size_t)q * mp + p] = (float)(1.0 / (-4.0 * (sp * sp / (g->hx * g->hx) + sq * sq / (g->hy * g->hy))));
+    }
+  if ((st = upload(T->S, S, mp, mp)) || (st = upload(T->SCy, SCy, 2 * mp, mp)) || (st = upload(T->SCx, SCx, 2 * mp, mp)) ||
+      (st = alloc_zero(T->T1, nz * mp, mp)) || (st = alloc_zero(T->UT, nz * mp, mp)) ||
+      (st = alloc_zero(T->T3, nz * 2 * mp, mp)))
+    return st;
+  SC_CUDA(cudaMalloc(&T->inv_lam, il.size() * sizeof(float)));
+  SC_CUDA(cudaMemcpy(T->inv_lam, il.data(), il.size() * sizeof(float), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMalloc(&T->phi, (size_t)nz * nx * ny * sizeof(float)));
+  SC_CUDA(cudaMemset(T->phi, 0, (size_t)nz * nx * ny * sizeof(float)));
+  SC_CUDA(cudaMalloc(&T->err, sizeof(int)));
+  SC_CUDA(cudaMemset(T->err, 0, sizeof(int)));
+  return tf32_tune(g);
+}
+
 sc_status tf32_create(sc_grid* g) {
+  if (g->precision == SC_SOLVE_PIPE_TF32X3) return tf32_pipe_create(g);
   const int nx = g->nx, ny = g->ny, nz = g->nstack;
   if (nx != ny || (nx != 64 && nx != 128 && nx != 256))
     return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_TF32X3 needs nx = ny in {64, 128, 256}");
@@ -901,6 +1146,14 @@ void tf32_destroy(sc_grid* g) {
   free_mat(T->A3);
   cudaFree(T->Sx);
   cudaFree(T->Sy);
+  free_mat(T->S);
+  free_mat(T->SCy);
+  free_mat(T->SCx);
+  free_mat(T->T1);
+  free_mat(T->UT);
+  free_mat(T->T3);
+  cudaFree(T->inv_lam);
+  cudaFree(T->phi);
   cudaFree(T->err);
   delete T;
   g->tf32 = nullptr;
@@ -909,11 +1162,20 @@ void tf32_destroy(sc_grid* g) {
 sc_status tf32_solve(sc_grid* g, bool zero_q) {
   Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_ARG, "grid has no TF32 solver");
-  PhaseRun& r1 = T->run[P1];
+  PhaseRun& r1 = T->run[0];
   r1.a.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
   r1.a.stack_scale = (const float*)g->stack_scale;
-  T->run[P2A].a.Qzero = zero_q ? g->Q : nullptr;
-  for (int ph = P1; ph <= P3; ++ph) SC_CUDA(launch_run(ph, T->run[ph], g->stream, true));
+  T->run[1].a.Qzero = zero_q ? g->Q : nullptr;  // P2A / D2: the charge has been read
+  for (int c = 0; c < 4; ++c) SC_CUDA(launch_run(T->base() + c, T->run[c], g->stream, true));
+  if (T->pipe) {
+    int dev = 0, sms = 0;
+    SC_CUDA(cudaGetDevice(&dev));
+    SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t total = (int64_t)g->nstack * (2 * g->nx + 2 * (g->ny - 2));
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms * 4);
+    SC_CUDA(launch_pdl(pipe_walls32, dim3(blocks), dim3(256), 0, g->stream, (const float*)T->phi, g->nx, g->ny,
+                       g->nstack, (float)(1.0 / g->hx), (float)(1.0 / g->hy), (float2*)g->E));
+  }
   return SC_OK;
 }
 
@@ -926,18 +1188,30 @@ int tf32_error(sc_grid* g) {
 
 int tf32_variant_count(int ph) { return (int)variants(ph).size(); }
 
+sc_status tf32_read_potential(const sc_grid* g, double* out) {
+  const Tf32Plan* T = g->tf32;
+  if (!T || !T->pipe) return set_error(SC_ERR_UNSUPPORTED, "only pipe grids keep the potential");
+  const size_t cells = (size_t)g->nstack * g->nx * g->ny;
+  std::vector<float> v(cells);
+  SC_CUDA(cudaMemcpy(v.data(), T->phi, cells * sizeof(float), cudaMemcpyDeviceToHost));
+  for (size_t c = 0; c < cells; ++c) out[c] = v[c];
+  return SC_OK;
+}
+
 sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc) {
   const Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_UNSUPPORTED, "the grid has no split-TF32 solve");
-  static const char* names[4] = {"row DFT", "column DFT", "inverse column DFT", "inverse row DFT"};
-  for (int ph = 0; ph < 4; ++ph) {
-    const int k = T->run[ph].variant;
-    if (choice) choice[ph] = k;
+  static const char* names[8] = {"row DFT", "column DFT", "inverse column DFT", "inverse row DFT",
+                                 "row sine transform", "column sine transform / lambda", "inverse column sine transform",
+                                 "inverse row sine transform"};
+  for (int c = 0; c < 4; ++c) {
+    const int k = T->run[c].variant, ph = T->base() + c;
+    if (choice) choice[c] = k;
     if (desc) {
       const Variant& v = variants(ph)[k];
-      char b[160];
-      std::snprintf(b, sizeof b, "%s%s: %d columns x split-K %d, %d stages, %d CTAs (%.1f us)", ph ? "; " : "",
-                    names[ph], v.nt, v.sk, v.stages, T->run[ph].grid, T->tuned_us[ph]);
+      char b[200];
+      std::snprintf(b, sizeof b, "%s%s: %d columns x split-K %d, %d stages, %d CTAs (%.1f us)", c ? "; " : "",
+                    names[ph], v.nt, v.sk, v.stages, T->run[c].grid, T->tuned_us[c]);
       *desc += b;
     }
   }
@@ -947,14 +1221,15 @@ sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc) {
 sc_status tf32_set_tiling(sc_grid* g, const int* choice) {
   Tf32Plan* T = g->tf32;
   if (!T) return set_error(SC_ERR_UNSUPPORTED, "the grid has no split-TF32 solve");
-  for (int ph = 0; ph < 4; ++ph) {
-    if (choice[ph] < 0) continue;
-    if (choice[ph] >= (int)variants(ph).size()) return set_error(SC_ERR_ARG, "tiling variant index out of range");
+  for (int c = 0; c < 4; ++c) {
+    if (choice[c] < 0) continue;
+    const int ph = T->base() + c;
+    if (choice[c] >= (int)variants(ph).size()) return set_error(SC_ERR_ARG, "tiling variant index out of range");
     PhaseRun r;
-    sc_status st = make_run(g, ph, choice[ph], r);
+    sc_status st = make_run(g, ph, choice[c], r);
     if (st) return st;
-    T->run[ph] = r;
-    T->tuned_us[ph] = 0.f;
+    T->run[c] = r;
+    T->tuned_us[c] = 0.f;
   }
   return SC_OK;
 }

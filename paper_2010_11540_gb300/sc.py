@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_PKG, "libsc.so")
 SC_OK = 0
 ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVERFLOW",
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "tf32x3": 1, "pipe_fp64": 2}
+PRECISION = {"fp64": 0, "tf32x3": 1, "pipe_fp64": 2, "pipe_tf32x3": 3}
 EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",

@@ -704,3 +704,74 @@ def test_track_bezier_longitudinal_one_turn():
                  gather="bezier")
     err = rel_state_err(got, ref)
     assert max(err.values()) < 1e-10, err
+
+
+# ------------------------------------------------------------------ conducting pipe, split-TF32 sine GEMMs
+@pytest.mark.parametrize("n,nz", [(129, 1), (65, 1), (257, 1), (129, 4)])
+def test_solve_pipe_tf32_every_tiling(n, nz):
+    """The pipe solve as split-TF32 sine-transform GEMMs: fields within 1e-5
+    (relative L2) of the float64 oracle for every kernel variant of every phase,
+    single and stacked grids; the potential too."""
+    parts = synth.gaussian_bunch(200000, 3 + n + nz, 4e-3, 3e-3, 1e-4, 1e-4, sig_z=15.0)
+    parts["x"] += 1e-3
+    grid = (n, n, -0.02, 0.02, -0.015, 0.015)
+    sl = None if nz == 1 else (nz, -60.0, 60.0)
+    g = sc.create_grid(*grid, precision="pipe_tf32x3", slices=sl)
+    og = oracle.Geometry(*grid)
+    N = len(parts["x"])
+    if sl is None:
+        Qo, _ = oracle.deposit(og, parts["x"], parts["y"])
+        Exo, Eyo = oracle.solve(og, Qo, N, boundary="pipe")
+        phio = oracle.potential_pipe(og, oracle.normalise(Qo, N))[1:-1, 1:-1]
+    else:
+        Qo, _ = oracle.deposit_sliced(og, oracle.Slices(*sl), parts["x"], parts["y"], parts["sigma"])
+        Exo, Eyo = oracle.solve_sliced(og, Qo, N, boundary="pipe")
+        phio = oracle.potential_sliced_pipe(og, Qo, N)
+    tuned, desc = sc.get_solver_tiling(g)
+    assert "sine" in desc
+    tried = 0
+    for ph in range(4):
+        for k in range(TILING_VARIANTS[ph]):
+            choice = list(tuned)
+            choice[ph] = k
+            try:
+                sc.set_solver_tiling(g, choice)
+            except sc.ScError as e:
+                assert e.code == -1
+                continue
+            tried += 1
+            sc.grid_write_charge(g, Qo, N)
+            sc.solve(g)
+            _, Ex, Ey, _ = sc.grid_read(g)
+            assert rel_l2(Ex, Exo) < 1e-5 and rel_l2(Ey, Eyo) < 1e-5, (ph, k, rel_l2(Ex, Exo), rel_l2(Ey, Eyo))
+    assert tried >= 12
+    phi = sc.grid_read_potential(g)
+    assert rel_l2(phi, phio) < 1e-5
+
+
+def test_track_pipe_tf32_statistics():
+    """One c2 turn with the split-TF32 pipe solve: rms coordinate differences
+    from the float64 oracle within 1e-5 of each coordinate's rms."""
+    parts, b, _, lat = synth.workload("c2", n=200000)
+    grid = (129, 129) + synth.grid_extent(4e-3, 3e-3)
+    g = sc.create_grid(*grid, precision="pipe_tf32x3")
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    got = to_host(st)
+    ref = oracle.copy_state(parts)
+    oracle.track(oracle.Geometry(*grid), ref, b, lat, 1, boundary="pipe")
+    for k in KEYS:
+        scale = np.sqrt(np.mean(ref[k] ** 2))
+        d = got[k] - ref[k]
+        assert np.sqrt(np.mean(d * d)) < 1e-5 * scale, k
+
+
+def test_pipe_tf32_limits():
+    with pytest.raises(sc.ScError) as e:
+        sc.create_grid(129, 65, -1.0, 1.0, -1.0, 1.0, precision="pipe_tf32x3")
+    assert e.value.code == -7
+    g = sc.create_grid(33, 33, -1.0, 1.0, -1.0, 1.0, precision="pipe_tf32x3", slices=(3, -1.0, 1.0))
+    with pytest.raises(sc.ScError):
+        sc.set_longitudinal_kick(g)  # float64 form only
+    with pytest.raises(sc.ScError):
+        sc.set_gather(g, "bezier")
