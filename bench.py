@@ -57,6 +57,10 @@ FP64_INST_SLICE = 2.0
 FP64_INST_BEZIER = 103.7
 FP64_INST_LON = 25.6
 FP64_INST_LON_BEZIER = 83.7
+# the same in the split form (float32 potential and Bezier surface)
+FP64_INST_BEZIER_F32 = 3.85
+FP64_INST_LON_F32 = 13.95
+FP64_INST_LON_BEZIER_F32 = 13.95
 # DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
 # from ncu --set full (cold cache, mean of the three segment types): the
 # roofline's "traffic" for that workload; other workloads report null.
@@ -250,7 +254,7 @@ class SingleRun:
         g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
         if precision in ("tf32x3", "pipe_tf32x3") and self.tiling:
             sc.set_solver_tiling(g, self.tiling)
-        if precision == "pipe_fp64":
+        if precision in ("pipe_fp64", "pipe_tf32x3"):
             if self.gather == "bezier":
                 sc.set_gather(g, "bezier")
             if self.longitudinal:
@@ -409,11 +413,7 @@ def run_ours(args):
     if args.boundary == "pipe":
         if args.config == "c4":
             raise SystemExit("--boundary pipe: single-bunch configs only")
-        if args.gather == "bezier" or args.longitudinal or args.precision == "fp64":
-            args.precision = "pipe_fp64"  # the potential-based kicks are float64-form features
-            args.no_compare = True
-        else:
-            args.precision = "pipe_tf32x3"
+        args.precision = "pipe_fp64" if args.precision == "fp64" else "pipe_tf32x3"
     W.tiling = [int(v) for v in args.tiling.split(",")] if args.tiling else None
     n = W.n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -456,10 +456,12 @@ def run_ours(args):
                                                                                                  args.precision))
     if getattr(W, "slices", None):
         inst_turn += n_kicks * FP64_INST_SLICE
+    f32 = args.precision in ("tf32x3", "pipe_tf32x3")
     if args.gather == "bezier":
-        inst_turn += n_kicks * FP64_INST_BEZIER
+        inst_turn += n_kicks * (FP64_INST_BEZIER_F32 if f32 else FP64_INST_BEZIER)
     if args.longitudinal:
-        inst_turn += n_kicks * (FP64_INST_LON_BEZIER if args.gather == "bezier" else FP64_INST_LON)
+        inst_turn += n_kicks * ((FP64_INST_LON_BEZIER_F32 if f32 else FP64_INST_LON_BEZIER) if args.gather == "bezier"
+                                else (FP64_INST_LON_F32 if f32 else FP64_INST_LON))
     h, ms, wall, clk = timed_turns(args.precision)
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
     compare = None

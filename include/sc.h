@@ -181,7 +181,8 @@ sc_status sc_grid_read(sc_grid *g, uint64_t *Q, double *Ex, double *Ey, int64_t 
 sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particles);
 
 /* Longitudinal space-charge kick, Sec. IV (dps = -(e/(m gamma0^2 beta0^2
- * c^2)) u dlambda/dz L), on a sliced SC_SOLVE_PIPE_FP64 grid: every kick on
+ * c^2)) u dlambda/dz L), on a sliced pipe grid (SC_SOLVE_PIPE_FP64, or
+ * SC_SOLVE_PIPE_TF32X3 with the float32 potential): every kick on
  * this grid then also applies dps = -(K gamma0) L (Phi_{k+1} - Phi_{k-1}) /
  * (2 dz) at the particle's (x, y), Phi_k the potential of slice k (0 beyond
  * the first and last slice), K the transverse kick strength.  For a bunch
@@ -195,8 +196,9 @@ sc_status sc_set_longitudinal_kick(sc_grid *g, int enable);
  * (Sec. IV-C), the cubic's parameter running over those nodes,
  * t = (x - x_{i-1}) / (3 hx); nodes beyond the walls take the odd extension;
  * on a sliced grid with the longitudinal kick the neighbouring slices'
- * potentials come from the same surfaces.  BEZIER needs a SC_SOLVE_PIPE_FP64
- * grid (SC_ERR_UNSUPPORTED otherwise). */
+ * potentials come from the same surfaces.  BEZIER needs a pipe grid
+ * (SC_SOLVE_PIPE_FP64; SC_SOLVE_PIPE_TF32X3 evaluates the surface of its
+ * float32 potential in float32), SC_ERR_UNSUPPORTED otherwise. */
 #define SC_GATHER_BILINEAR 0
 #define SC_GATHER_BEZIER 1
 sc_status sc_set_gather(sc_grid *g, int mode);

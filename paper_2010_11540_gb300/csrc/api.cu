@@ -139,15 +139,15 @@ void set_kick(KPParams& P, const sc_grid* g, double kl, double gamma0) {
   P.E32 = (const float2*)g->E;
   P.field32 = g->field32;
   P.kl = kl;
+  if (g->lon || g->gather == SC_GATHER_BEZIER) {
+    P.phi = g->pipe.phi;         // float64 form
+    P.phi32 = tf32_potential(g);  // split form
+  }
   if (g->lon) {  // K gamma0 L / (2 dz)
     P.lon = 1;
-    P.phi = g->pipe.phi;
     P.klz = kl * gamma0 / (2.0 * (g->zmax - g->zmin) / (double)g->nz);
   }
-  if (g->gather == SC_GATHER_BEZIER) {
-    P.bezier = 1;
-    P.phi = g->pipe.phi;
-  }
+  if (g->gather == SC_GATHER_BEZIER) P.bezier = 1;
 }
 
 // The cell cache a deposit writes follows the deposit grid's field precision.
@@ -392,8 +392,9 @@ sc_status sc_grid_read(sc_grid* g, uint64_t* Q, double* Ex, double* Ey, int64_t*
 
 sc_status sc_set_longitudinal_kick(sc_grid* g, int enable) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
-  if (enable && (g->precision != SC_SOLVE_PIPE_FP64 || g->nz < 2))
-    return set_error(SC_ERR_UNSUPPORTED, "the longitudinal kick needs a sliced SC_SOLVE_PIPE_FP64 grid");
+  const bool pipe = g->precision == SC_SOLVE_PIPE_FP64 || g->precision == SC_SOLVE_PIPE_TF32X3;
+  if (enable && (!pipe || g->nz < 2))
+    return set_error(SC_ERR_UNSUPPORTED, "the longitudinal kick needs a sliced pipe grid");
   SC_CUDA(cudaStreamSynchronize(g->stream));
   g->lon = enable ? 1 : 0;
   return SC_OK;
@@ -402,8 +403,8 @@ sc_status sc_set_longitudinal_kick(sc_grid* g, int enable) {
 sc_status sc_set_gather(sc_grid* g, int mode) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   if (mode != SC_GATHER_BILINEAR && mode != SC_GATHER_BEZIER) return set_error(SC_ERR_ARG, "unknown gather mode");
-  if (mode == SC_GATHER_BEZIER && g->precision != SC_SOLVE_PIPE_FP64)
-    return set_error(SC_ERR_UNSUPPORTED, "the Bezier gather needs the potential of a SC_SOLVE_PIPE_FP64 grid");
+  if (mode == SC_GATHER_BEZIER && g->precision != SC_SOLVE_PIPE_FP64 && g->precision != SC_SOLVE_PIPE_TF32X3)
+    return set_error(SC_ERR_UNSUPPORTED, "the Bezier gather needs the potential of a pipe grid");
   SC_CUDA(cudaStreamSynchronize(g->stream));
   g->gather = mode;
   return SC_OK;

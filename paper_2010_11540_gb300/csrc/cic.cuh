@@ -60,23 +60,26 @@ __device__ __forceinline__ void deposit_tiled(unsigned long long* tile, int* til
     deposit4(Q, g.nx, cell, a);
 }
 
-// Cubic Bernstein weights b_m(t) and their derivatives.
-__device__ __forceinline__ void bernstein3(double t, double (&b)[4], double (&db)[4]) {
-  const double u = 1.0 - t, uu = u * u, tt = t * t, tu = t * u;
+// Cubic Bernstein weights b_m(t) and their derivatives (R = double for the
+// float64 form, float for the split form whose potential is float32).
+template <typename R>
+__device__ __forceinline__ void bernstein3(R t, R (&b)[4], R (&db)[4]) {
+  const R u = R(1) - t, uu = u * u, tt = t * t, tu = t * u;
   b[0] = uu * u;
-  b[1] = 3.0 * tu * u;
-  b[2] = 3.0 * tu * t;
+  b[1] = R(3) * tu * u;
+  b[2] = R(3) * tu * t;
   b[3] = tt * t;
-  db[0] = -3.0 * uu;
-  db[1] = fma(3.0, uu, -6.0 * tu);
-  db[2] = fma(6.0, tu, -3.0 * tt);
-  db[3] = 3.0 * tt;
+  db[0] = R(-3) * uu;
+  db[1] = fma(R(3), uu, R(-6) * tu);
+  db[2] = fma(R(6), tu, R(-3) * tt);
+  db[3] = R(3) * tt;
 }
 
 // Potential of node (i, j) of one grid, i in -1..nx, j in -1..ny: beyond the
 // walls the odd extension (u_{-1} = -u_1, u_n = -u_{n-2}).
-__device__ __forceinline__ double phi_node(const double* __restrict__ phi, int nx, int ny, int i, int j) {
-  double sgn = 1.0;
+template <typename R>
+__device__ __forceinline__ R phi_node(const R* __restrict__ phi, int nx, int ny, int i, int j) {
+  R sgn = R(1);
   if (i < 0) { i = -i; sgn = -sgn; }
   if (i > nx - 1) { i = 2 * (nx - 1) - i; sgn = -sgn; }
   if (j < 0) { j = -j; sgn = -sgn; }
@@ -87,19 +90,19 @@ __device__ __forceinline__ double phi_node(const double* __restrict__ phi, int n
 // Bezier surface (Sec. IV-C) of grid phi in cell (i, j) at fractions (fx, fy):
 // value u and the derivatives with respect to the cell fractions' span
 // parameters (d/dx = gx / (3 hx), d/dy = gy / (3 hy)).
-template <bool VALUE, bool GRAD>
-__device__ __forceinline__ void bezier_eval(const double* __restrict__ phi, int nx, int ny, int i, int j, double fx,
-                                            double fy, double& u, double& gx, double& gy) {
-  double bx[4], dbx[4], by[4], dby[4];
-  bernstein3((1.0 + fx) * (1.0 / 3.0), bx, dbx);
-  bernstein3((1.0 + fy) * (1.0 / 3.0), by, dby);
-  u = gx = gy = 0.0;
+template <typename R, bool VALUE, bool GRAD>
+__device__ __forceinline__ void bezier_eval(const R* __restrict__ phi, int nx, int ny, int i, int j, R fx, R fy,
+                                            R& u, R& gx, R& gy) {
+  R bx[4], dbx[4], by[4], dby[4];
+  bernstein3<R>((R(1) + fx) * (R(1) / R(3)), bx, dbx);
+  bernstein3<R>((R(1) + fy) * (R(1) / R(3)), by, dby);
+  u = gx = gy = R(0);
 #pragma unroll
   for (int n = 0; n < 4; ++n) {
-    double rv = 0.0, rx = 0.0;
+    R rv = R(0), rx = R(0);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      const double c = phi_node(phi, nx, ny, i + m - 1, j + n - 1);
+      const R c = phi_node<R>(phi, nx, ny, i + m - 1, j + n - 1);
       rv = fma(c, bx[m], rv);
       if (GRAD) rx = fma(c, dbx[m], rx);
     }

@@ -29,14 +29,32 @@ __device__ __noinline__ void bezier_kick(State& s, const KPParams& P, int cell, 
   const int k = cell / cells, rem = cell - k * cells, j = rem / nxk, i = rem - j * nxk;
   const double* ph = P.phi + (size_t)k * cells;
   double u, gx, gy;
-  bezier_eval<false, true>(ph, nxk, nyk, i, j, fx, fy, u, gx, gy);
+  bezier_eval<double, false, true>(ph, nxk, nyk, i, j, fx, fy, u, gx, gy);
   s.px = fma(-P.kl * (1.0 / 3.0) * P.gk.inv_hx, gx, s.px);
   s.py = fma(-P.kl * (1.0 / 3.0) * P.gk.inv_hy, gy, s.py);
   if (P.lon) {
     double up = 0.0, dn = 0.0, a, b;
-    if (k + 1 < P.gk.nz) bezier_eval<true, false>(ph + cells, nxk, nyk, i, j, fx, fy, up, a, b);
-    if (k > 0) bezier_eval<true, false>(ph - cells, nxk, nyk, i, j, fx, fy, dn, a, b);
+    if (k + 1 < P.gk.nz) bezier_eval<double, true, false>(ph + cells, nxk, nyk, i, j, fx, fy, up, a, b);
+    if (k > 0) bezier_eval<double, true, false>(ph - cells, nxk, nyk, i, j, fx, fy, dn, a, b);
     s.ps = fma(-P.klz, up - dn, s.ps);
+  }
+}
+
+// The same from the split form's float32 potential, in float32 arithmetic
+// (its fields carry float32 accuracy); the momentum updates in float64.
+__device__ __noinline__ void bezier_kick32(State& s, const KPParams& P, int cell, float fx, float fy) {
+  const int nxk = P.gk.nx, nyk = P.gk.ny, cells = nxk * nyk;
+  const int k = cell / cells, rem = cell - k * cells, j = rem / nxk, i = rem - j * nxk;
+  const float* ph = P.phi32 + (size_t)k * cells;
+  float u, gx, gy;
+  bezier_eval<float, false, true>(ph, nxk, nyk, i, j, fx, fy, u, gx, gy);
+  s.px = fma(-P.kl * (1.0 / 3.0) * P.gk.inv_hx, (double)gx, s.px);
+  s.py = fma(-P.kl * (1.0 / 3.0) * P.gk.inv_hy, (double)gy, s.py);
+  if (P.lon) {
+    float up = 0.f, dn = 0.f, a, b;
+    if (k + 1 < P.gk.nz) bezier_eval<float, true, false>(ph + cells, nxk, nyk, i, j, fx, fy, up, a, b);
+    if (k > 0) bezier_eval<float, true, false>(ph - cells, nxk, nyk, i, j, fx, fy, dn, a, b);
+    s.ps = fma(-P.klz, (double)(up - dn), s.ps);
   }
 }
 
@@ -72,7 +90,9 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           fx = (float)a.x * (1.0f / 1048576.0f);
           fy = (float)a.y * (1.0f / 1048576.0f);
         }
-        if (cell >= 0) {
+        if (XE && cell >= 0 && P.bezier) {
+          bezier_kick32(s, P, cell, fx, fy);
+        } else if (cell >= 0) {
           const float2* e = P.E32 + cell;
           const float2 e00 = __ldg(e), e10 = __ldg(e + 1);
           const float2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
@@ -80,6 +100,24 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           const float ay = fmaf(fx, e10.y - e00.y, e00.y), by = fmaf(fx, e11.y - e01.y, e01.y);
           s.px = fma(P.kl, (double)fmaf(fy, bx - ax, ax), s.px);
           s.py = fma(P.kl, (double)fmaf(fy, by - ay, ay), s.py);
+          if (P.lon) {
+            // longitudinal kick from the float32 potentials of the neighbouring slices
+            const int cells = P.gk.nx * P.gk.ny, k = cell / cells, nxk = P.gk.nx;
+            float up = 0.f, dn = 0.f;
+            if (k + 1 < P.gk.nz) {
+              const float* f = P.phi32 + cell + cells;
+              const float a0 = fmaf(fx, __ldg(f + 1) - __ldg(f), __ldg(f));
+              const float a1 = fmaf(fx, __ldg(f + nxk + 1) - __ldg(f + nxk), __ldg(f + nxk));
+              up = fmaf(fy, a1 - a0, a0);
+            }
+            if (k > 0) {
+              const float* f = P.phi32 + cell - cells;
+              const float a0 = fmaf(fx, __ldg(f + 1) - __ldg(f), __ldg(f));
+              const float a1 = fmaf(fx, __ldg(f + nxk + 1) - __ldg(f + nxk), __ldg(f + nxk));
+              dn = fmaf(fy, a1 - a0, a0);
+            }
+            s.ps = fma(-P.klz, (double)(up - dn), s.ps);
+          }
         }
       } else {
         double fx, fy;
@@ -126,7 +164,7 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
     }
     PsConst k;
     // the longitudinal kick changed psigma: its dependent quantities are recomputed and stored
-    const bool fresh = psc_mode == 2 || (psc_mode == 1 && !F32 && P.lon);
+    const bool fresh = psc_mode == 2 || (psc_mode == 1 && P.lon);
     if (psc_mode == 1 && !fresh) {
       k.opd2 = P.psc[p];
       k.opb = P.psc[n + p];

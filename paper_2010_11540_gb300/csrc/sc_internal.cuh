@@ -112,6 +112,7 @@ struct KPParams {
   // of the kick grid, klz = K gamma0 L / (2 dz).
   int lon;
   const double* phi;
+  const float* phi32;  // the split form's float32 potential (lon / Bezier with float32 fields)
   double klz;
   // Bezier gather (pipe grids, float64 form): E = -grad of the Bezier surface
   // of phi (Sec. IV-C) instead of bilinear node fields; with lon the
@@ -221,6 +222,7 @@ int tf32_error(sc_grid* g);  // 1 when a tensor-core solve gave up on a bounded 
 sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc);
 sc_status tf32_set_tiling(sc_grid* g, const int* choice);  // -1 entries keep the current variant
 sc_status tf32_read_potential(const sc_grid* g, double* out);  // pipe grids of the split form
+const float* tf32_potential(const sc_grid* g);                 // device potential of a split-form pipe grid
 // diag.cu
 // out = *base_ptr + stride * (*turn) receives the 14 moments; bumps *turn
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,

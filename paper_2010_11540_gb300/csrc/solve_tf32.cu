@@ -1188,6 +1188,8 @@ int tf32_error(sc_grid* g) {
 
 int tf32_variant_count(int ph) { return (int)variants(ph).size(); }
 
+const float* tf32_potential(const sc_grid* g) { return (g->tf32 && g->tf32->pipe) ? g->tf32->phi : nullptr; }
+
 sc_status tf32_read_potential(const sc_grid* g, double* out) {
   const Tf32Plan* T = g->tf32;
   if (!T || !T->pipe) return set_error(SC_ERR_UNSUPPORTED, "only pipe grids keep the potential");
