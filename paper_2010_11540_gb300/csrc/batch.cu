@@ -75,6 +75,11 @@ struct sc_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<sc_grid*> cls;   // grid classes (stacked grids)
+  // classes after the first solve on side streams forked from the batch's
+  // stream inside the captured turn (independent solves overlap)
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
   std::vector<int> cls_of;     // bunch -> class
   std::vector<int> idx;        // bunch -> stacked grid within its class
   sc::BatchPlan* plan = nullptr;
@@ -192,6 +197,21 @@ sc_status sc_create_batch(sc_batch** out, const sc_grid_spec* grids, int n_bunch
     }
     B->cls.push_back(g);
   }
+  if (B->cls.size() > 1) {
+    cudaError_t e = cudaEventCreateWithFlags(&B->fork_ev, cudaEventDisableTiming);
+    for (size_t c = 1; c < B->cls.size() && e == cudaSuccess; ++c) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) B->side.push_back(st);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) B->join_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+      sc_destroy_batch(B);
+      return cuda_error(e, "side streams of a batch");
+    }
+  }
   *out = B;
   return SC_OK;
 }
@@ -201,6 +221,9 @@ sc_status sc_destroy_batch(sc_batch* B) {
   if (B->stream) cudaStreamSynchronize(B->stream);
   destroy_batch_plan(B->plan);
   for (sc_grid* g : B->cls) sc_destroy_grid(g);
+  for (cudaStream_t st : B->side) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : B->join_ev) cudaEventDestroy(ev);
+  if (B->fork_ev) cudaEventDestroy(B->fork_ev);
   if (B->own_stream) cudaStreamDestroy(B->stream);
   delete B;
   return SC_OK;
@@ -401,8 +424,25 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     for (int k = 0; !cst && k < n_marks; ++k, ++L) {
       if (B->trace && cudaEventRecordWithFlags(T->ev[3 * k], S, cudaEventRecordExternal) != cudaSuccess)
         cst = set_error(SC_ERR_CUDA, "event");
-      // every class: solve, then clear the charge for this marker's deposit
-      for (size_t c = 0; !cst && c < B->cls.size(); ++c) cst = solve_dispatch(B->cls[c], true);
+      // every class: solve, then clear the charge for this marker's deposit; classes after the
+      // first on their side streams (forked after the previous kick/push, joined before the next)
+      if (!cst && B->cls.size() > 1 && cudaEventRecord(B->fork_ev, S) != cudaSuccess)
+        cst = set_error(SC_ERR_CUDA, "fork event");
+      for (size_t c = 1; !cst && c < B->cls.size(); ++c) {
+        sc_grid* g = B->cls[c];
+        if (cudaStreamWaitEvent(B->side[c - 1], B->fork_ev, 0) != cudaSuccess) {
+          cst = set_error(SC_ERR_CUDA, "fork wait");
+          break;
+        }
+        g->stream = B->side[c - 1];
+        cst = solve_dispatch(g, true);
+        g->stream = S;
+        if (!cst && cudaEventRecord(B->join_ev[c - 1], B->side[c - 1]) != cudaSuccess)
+          cst = set_error(SC_ERR_CUDA, "join event");
+      }
+      if (!cst) cst = solve_dispatch(B->cls[0], true);
+      for (size_t c = 1; !cst && c < B->cls.size(); ++c)
+        if (cudaStreamWaitEvent(S, B->join_ev[c - 1], 0) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "join wait");
       if (!cst && B->trace && cudaEventRecordWithFlags(T->ev[3 * k + 1], S, cudaEventRecordExternal) != cudaSuccess)
         cst = set_error(SC_ERR_CUDA, "event");
       if (!cst && any)
