@@ -247,6 +247,17 @@ sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int6
 sc_status sc_get_solver_tiling(sc_grid *g, int *choice, char *desc, size_t n);
 sc_status sc_set_solver_tiling(sc_grid *g, const int *choice);
 
+/* Failure-detection test hook (no counterpart in the paper).  The tensor-core
+ * solve's waits on its copy and MMA barriers are bounded (~2 s of SM clock);
+ * when one runs out the kernel records an error word, lets its issued work
+ * drain, frees its tensor memory and returns, and sc_grid_read reports
+ * SC_ERR_TIMEOUT (the word stays set for this grid).  While enabled, the
+ * split-TF32 solve announces its data-operand copies to the pipeline barriers
+ * without issuing them, so those waits run out (≈ 2 s per phase); no copy,
+ * MMA or memory access is left in flight and the context stays usable.
+ * Errors: SC_ERR_UNSUPPORTED (no split-TF32 solve). */
+sc_status sc_test_bounded_waits(sc_grid *g, int enable);
+
 /* ---- Batches of independent bunches --------------------------------------
  * Many bunches (working points of a tune scan, bunches of a train, intensity
  * scans), each with its own particles, beam, lattice and transverse grid,

@@ -461,6 +461,16 @@ sc_status sc_set_solver_tiling(sc_grid* g, const int* choice) {
   return tf32_set_tiling(g, choice);
 }
 
+sc_status sc_test_bounded_waits(sc_grid* g, int enable) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  if (g->track) {  // captured turns hold the old launch arguments
+    destroy_plan(g->track);
+    g->track = nullptr;
+  }
+  return tf32_test_bounded_waits(g, enable);
+}
+
 sc_status sc_trace_enable(sc_grid* g, int enable) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   g->trace = enable ? 1 : 0;

@@ -223,6 +223,7 @@ sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc);
 sc_status tf32_set_tiling(sc_grid* g, const int* choice);  // -1 entries keep the current variant
 sc_status tf32_read_potential(const sc_grid* g, double* out);  // pipe grids of the split form
 const float* tf32_potential(const sc_grid* g);                 // device potential of a split-form pipe grid
+sc_status tf32_test_bounded_waits(sc_grid* g, int enable);     // failure-detection test hook
 // diag.cu
 // out = *base_ptr + stride * (*turn) receives the 14 moments; bumps *turn
 sc_status launch_moments(const sc_particles* p, double* partial, int n_blocks, double* const* base_ptr, int* turn,

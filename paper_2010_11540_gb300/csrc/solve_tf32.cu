@@ -166,6 +166,9 @@ struct GemmArgs {
   const float* inv_lam;    // D2: 1 / lambda at (q, p), [mp][mp], 0 in the padding
   float norm;              // D4: 4 / (m+1)^2
   float* phi;              // D4: potential [stacked grid][ny][nx] (walls stay 0)
+  // failure-detection test: announce the data operand's copies to the stage
+  // barriers without issuing them, so every bounded wait runs out
+  int drop_data_loads;
 };
 
 // Which operand is a constant DFT matrix (loadable before the grid dependency
@@ -352,7 +355,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 
   if (warp == 0 && lane == 0) {
     // ---- TMA producer: the data operand of the prefetched stages, then whole stages
-    for (int kc = 0; kc < pre; ++kc) {
+    for (int kc = 0; kc < pre && !g.drop_data_loads; ++kc) {
       if (R::CONST_A) {
         if (R::TMA_B) load_b(kc, kc);
       } else {
@@ -697,6 +700,7 @@ struct Tf32Plan {
   float* inv_lam = nullptr;  // [mp][mp]
   float* phi = nullptr;      // [nstack][ny][nx]
   PhaseRun run[4];           // the chain's four phases (P1..P3 or D1..D4)
+  int drop_data_loads = 0;   // failure-detection test (sc_test_bounded_waits)
   float tuned_us[4];         // time of the chosen variant when tuned (0: forced)
   int base() const { return pipe ? D1 : P1; }
 };
@@ -1166,6 +1170,7 @@ sc_status tf32_solve(sc_grid* g, bool zero_q) {
   r1.a.scale = (float)(1.0 / 1099511627776.0 / (double)(g->n_particles > 0 ? g->n_particles : 1));
   r1.a.stack_scale = (const float*)g->stack_scale;
   T->run[1].a.Qzero = zero_q ? g->Q : nullptr;  // P2A / D2: the charge has been read
+  for (int c = 0; c < 4; ++c) T->run[c].a.drop_data_loads = T->drop_data_loads;
   for (int c = 0; c < 4; ++c) SC_CUDA(launch_run(T->base() + c, T->run[c], g->stream, true));
   if (T->pipe) {
     int dev = 0, sms = 0;
@@ -1187,6 +1192,12 @@ int tf32_error(sc_grid* g) {
 }
 
 int tf32_variant_count(int ph) { return (int)variants(ph).size(); }
+
+sc_status tf32_test_bounded_waits(sc_grid* g, int enable) {
+  if (!g->tf32) return set_error(SC_ERR_UNSUPPORTED, "the grid has no split-TF32 solve");
+  g->tf32->drop_data_loads = enable ? 1 : 0;
+  return SC_OK;
+}
 
 const float* tf32_potential(const sc_grid* g) { return (g->tf32 && g->tf32->pipe) ? g->tf32->phi : nullptr; }
 

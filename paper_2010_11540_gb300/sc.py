@@ -29,7 +29,7 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
-           "sc_set_longitudinal_kick", "sc_set_gather",
+           "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits",
            "sc_last_error")
 
 
@@ -103,6 +103,7 @@ def load():
     L.sc_grid_read_potential.argtypes = [vp, vp]
     L.sc_set_longitudinal_kick.argtypes = [vp, ctypes.c_int]
     L.sc_set_gather.argtypes = [vp, ctypes.c_int]
+    L.sc_test_bounded_waits.argtypes = [vp, ctypes.c_int]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
