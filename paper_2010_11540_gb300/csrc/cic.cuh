@@ -19,43 +19,49 @@ namespace sc {
 // grid and the cell index is k*nx*ny + j*nx + i.
 template <bool FRAC>
 __device__ __forceinline__ int locate(const GridGeom& g, double x, double y, double sg, int2& a, double& fx,
-                                      double& fy) {
+                                      double& fy, int& k) {
   const double xi = __dmul_rn(__dsub_rn(x, g.xmin), g.inv_hx);
   const double eta = __dmul_rn(__dsub_rn(y, g.ymin), g.inv_hy);
-  int i = 0, j = 0, k = 0;
+  int i = 0, j = 0;
+  k = 0;
   bool in = cic_split(xi, g.nx - 1, i, a.x, FRAC ? &fx : nullptr);
   in = cic_split(eta, g.ny - 1, j, a.y, FRAC ? &fy : nullptr) && in;
   if (g.nz > 1) in = floor_index(__dmul_rn(__dsub_rn(sg, g.zmin), g.inv_dz), g.nz, k) && in;
   return in ? (k * g.ny + j) * g.nx + i : -1;
 }
 
-// The four CIC weights in 2^-20 fixed point per axis: a (from locate), b =
-// 2^20 - a; the products sum to exactly 2^40.  dst is either a shared-memory
-// tile or the global grid (same [j][i] layout).
-__device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int cell, int2 a) {
-  const long long ax = a.x, ay = a.y;
-  const long long bx = 1048576LL - ax, by = 1048576LL - ay;
-  unsigned long long* q = dst + cell;
-  atomicAdd(q, (unsigned long long)(bx * by));
-  atomicAdd(q + 1, (unsigned long long)(ax * by));
-  atomicAdd(q + nx, (unsigned long long)(bx * ay));
-  atomicAdd(q + nx + 1, (unsigned long long)(ax * ay));
+template <bool FRAC>
+__device__ __forceinline__ int locate(const GridGeom& g, double x, double y, double sg, int2& a, double& fx,
+                                      double& fy) {
+  int k;
+  return locate<FRAC>(g, x, y, sg, a, fx, fy, k);
 }
 
-// Deposit into a block's shared tile when the cell's slice is the tile's,
-// else straight into the global grid.  The tile takes the slice of the first
-// particle that reaches this (tile_k, shared, starts at -1).
+// The four CIC weights in 2^-20 fixed point per axis: a (from locate), b =
+// 2^20 - a; the products sum to exactly 2^40 (32 x 32 -> 64-bit multiplies).
+// dst is either a shared-memory tile or the global grid (same [j][i] layout).
+__device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int cell, int2 a) {
+  const unsigned ax = (unsigned)a.x, ay = (unsigned)a.y;
+  const unsigned bx = 1048576u - ax, by = 1048576u - ay;
+  unsigned long long* q = dst + cell;
+  atomicAdd(q, (unsigned long long)bx * by);
+  atomicAdd(q + 1, (unsigned long long)ax * by);
+  atomicAdd(q + nx, (unsigned long long)bx * ay);
+  atomicAdd(q + nx + 1, (unsigned long long)ax * ay);
+}
+
+// Deposit into a block's shared tile when the particle's slice k is the
+// tile's, else straight into the global grid.  The tile takes the slice of the
+// first particle that reaches this (tile_k, shared, starts at -1).
 __device__ __forceinline__ void deposit_tiled(unsigned long long* tile, int* tile_k, unsigned long long* Q,
-                                              const GridGeom& g, int cell, int2 a) {
-  const int cells = g.nx * g.ny;
-  const int k = cell / cells;
+                                              const GridGeom& g, int cell, int k, int2 a) {
   int tk = *(volatile int*)tile_k;
   if (tk < 0) {
     const int prev = atomicCAS(tile_k, -1, k);
     tk = prev < 0 ? k : prev;
   }
   if (tk == k)
-    deposit4(tile, g.nx, cell - k * cells, a);
+    deposit4(tile, g.nx, cell - k * g.nx * g.ny, a);
   else
     deposit4(Q, g.nx, cell, a);
 }

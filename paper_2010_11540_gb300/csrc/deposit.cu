@@ -47,11 +47,12 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __re
     }
     double fx, fy;
     int2 a;
-    const int cell = locate<false>(g, xc, yc, sc_, a, fx, fy);
+    int k;
+    const int cell = locate<false>(g, xc, yc, sc_, a, fx, fy, k);
     if (cell < 0)
       ++out;
     else if (TILE)
-      deposit_tiled(tile, &tile_k, Q, g, cell, a);
+      deposit_tiled(tile, &tile_k, Q, g, cell, k, a);
     else
       deposit4(Q, g.nx, cell, a);
   }

@@ -188,10 +188,11 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
     if (P.do_deposit) {
       double fx = 0.0, fy = 0.0;
       int2 a = make_int2(0, 0);
-      const int cell = locate<!F32>(P.gd, s.x, s.y, s.sg, a, fx, fy);
+      int kz;
+      const int cell = locate<!F32>(P.gd, s.x, s.y, s.sg, a, fx, fy, kz);
       if (cell >= 0) {
         if (use_tile)
-          deposit_tiled(tile, tile_k, P.Q, P.gd, cell, a);
+          deposit_tiled(tile, tile_k, P.Q, P.gd, cell, kz, a);
         else
           deposit4(P.Q, P.gd.nx, cell, a);
       } else {
