@@ -1,8 +1,10 @@
-// Fused space-charge step for one location: bilinear field gather + kick
-// (Sec. IV kick equation), push through the segment's elements (Sec. III),
-// and CIC deposit of the new positions (Sec. IV-A) into a per-block
-// shared-memory uint64 tile flushed once per block.  One thread per particle,
-// persistent grid-stride loop over SoA float64 state.
+// Fused space-charge step for one location: field gather + kick (Sec. IV kick
+// equation; bilinear node fields, or the Bezier surface of the potential, plus
+// the longitudinal kick on sliced pipe grids), push through the segment's
+// elements (Sec. III), and CIC deposit of the new positions (Sec. IV-A) into a
+// per-block shared-memory uint64 tile flushed once per block.  One thread per
+// particle, persistent grid over SoA float64 state; one launch serves one grid
+// (kick_push_kernel) or every bunch of a batch (kick_push_batched).
 #include <cmath>
 
 #include "cic.cuh"

@@ -1,4 +1,4 @@
-// Open-boundary field solve as dense DFT GEMMs on the 5th-generation tensor
+// Field solves as dense DFT / sine-transform GEMMs on the 5th-generation tensor
 // cores (tcgen05, kind::tf32), operands staged by TMA into 128-byte-swizzled
 // shared memory, accumulators in TMEM, 3-term split precision:
 //   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,   a_hi = tf32(a), a_lo = tf32(a - a_hi),
@@ -15,9 +15,23 @@
 //       DFT, kept for j' < ny: r < ny: Re G_f(j', p), r = ny+j': Im G_f
 //   P3  E[(f,j)][i] = A3[(f,j)][(re|im, p)] B4[i][(re|im, p)]   Hermitian
 //       inverse row DFT with weights 1 (p = 0, nx) or 2 and 1/(Mx My).
-// Supported: nx = ny in {64, 128, 256} (M tiles of 128 rows).  Tile width
-// (N columns per CTA), split-K cluster size and pipeline depth are chosen per
-// phase by timing the candidates when a grid is created.
+// Supported: nx = ny in {64, 128, 256} (M tiles of 128 rows).
+//
+// The conducting pipe of Sec. IV-B (walls on the outer nodes) uses the same
+// kernel with four more phases and the real sine matrix S of the m interior
+// nodes (padded to mp, whole 128-row tiles), F the right-hand side
+// -2 pi q / (hx hy) on the interior:
+//   D1  T1[p][j]  = S[p][i] F[j][i]               row sine transform
+//   D2  UT[p][q]  = (S[q][j] T1[p][j]) / lambda_pq column transform, division
+//   D3  T3[(f,j)][p] = [S; Cy][(f,j)][q] UT[p][q]  inverse columns, f = 1: d/dy
+//   D4  [(f,j)][(h,i)] = T3[(f,j)][p] [S; Cx][(h,i)][p] x 4/(m+1)^2:
+//       (0,0) potential, (0,1) Ex, (1,0) Ey at interior node (i+1, j+1)
+// with Cx, Cy the centred differences of the sine modes (cosine series).
+//
+// Stacked grids (slices, bunches of a batch) extend the data operand, so one
+// launch per phase covers them.  Tile width (N columns per CTA), split-K
+// cluster size and pipeline depth are chosen per phase by timing the
+// candidates when a grid is created.
 #include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
