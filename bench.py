@@ -89,6 +89,9 @@ def parse():
                     help="longitudinal space-charge kick (Sec. IV), sliced pipe grids (c5 --boundary pipe)")
     ap.add_argument("--tiling", default=None,
                     help="force the split-TF32 solve's kernel variant per phase, e.g. 0,1,2,1 (default: tuned)")
+    ap.add_argument("--kp-shape", default=None,
+                    help="force the kick/push block size and traversal (0 grid stride, 1 chunks), e.g. 768,1 "
+                         "(default: tuned; single-bunch configs)")
     return ap.parse_args()
 
 
@@ -254,6 +257,8 @@ class SingleRun:
         g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
         if precision in ("tf32x3", "pipe_tf32x3") and self.tiling:
             sc.set_solver_tiling(g, self.tiling)
+        if self.kp_shape:
+            sc.set_kick_push_shape(g, *self.kp_shape)
         if precision in ("pipe_fp64", "pipe_tf32x3"):
             if self.gather == "bezier":
                 sc.set_gather(g, "bezier")
@@ -267,6 +272,13 @@ class SingleRun:
             return None
         v, d = sc.get_solver_tiling(h[0])
         return {"variants": v, "grid": d}
+
+    def shape_desc(self, h):
+        from paper_2010_11540_gb300 import sc
+        t, v, us = sc.get_kick_push_shape(h[0])
+        return {"threads": t, "traversal": ("grid stride", "chunks")[v],
+                "trial_us_first_16_sc_steps": round(us, 1) or None,
+                "chosen": "fixed" if self.kp_shape else ("tuned" if us > 0 else "default")}
 
     def turns(self, h, n):
         from paper_2010_11540_gb300 import sc
@@ -366,6 +378,9 @@ class BatchRun:
                 out[key] = sc.batch_get_solver_tiling(h[0], i)[1]
         return out
 
+    def shape_desc(self, h):
+        return None
+
     def turns(self, h, n):
         from paper_2010_11540_gb300 import sc
         sc.batch_track_turns(h[0], h[1], self.beams, self.lats, n)
@@ -415,6 +430,7 @@ def run_ours(args):
             raise SystemExit("--boundary pipe: single-bunch configs only")
         args.precision = "pipe_fp64" if args.precision == "fp64" else "pipe_tf32x3"
     W.tiling = [int(v) for v in args.tiling.split(",")] if args.tiling else None
+    W.kp_shape = [int(v) for v in args.kp_shape.split(",")] if args.kp_shape else None
     n = W.n
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
@@ -522,7 +538,7 @@ def run_ours(args):
                         "pipe_fp64": "fp64 sine transforms (conducting pipe)",
                         "pipe_tf32x3": "tf32x3 sine-transform GEMMs on tcgen05 (conducting pipe)"}[args.precision],
               "particles": n, **W.grid_desc(),
-              "solve_tiling": W.tiling_desc(h),
+              "solve_tiling": W.tiling_desc(h), "kick_push_shape": W.shape_desc(h),
               "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -247,6 +247,26 @@ sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int6
 sc_status sc_get_solver_tiling(sc_grid *g, int *choice, char *desc, size_t n);
 sc_status sc_set_solver_tiling(sc_grid *g, const int *choice);
 
+/* Launch shape of sc_track_turns' fused kick/push (Sec. IV-A, IV-B): block
+ * size (threads, a multiple of 32 up to 768 for split-TF32 grids and 640 for
+ * float64 fields) and particle traversal (0: all blocks sweep a common window,
+ * grid stride; 1: each block takes one contiguous chunk; sliced grids always
+ * use chunks).  Every shape gives bit-identical results.  Left free (threads
+ * 0, traversal -1: the default), the shape is chosen when a turn is captured
+ * for a bunch of 2^18 particles or more: each candidate runs the turn's first
+ * 16 space-charge steps (solve, then kick/push with its deposit), captured as
+ * a graph, on a scratch copy of the bunch, and the fastest is kept (the
+ * particles, the charge grid and the out-of-grid counter are left as they
+ * were); smaller bunches take the largest block and the field type's default
+ * traversal.  A re-capture for the same particles, beam, lattice and options
+ * (tracing or diagnostics switched) reuses the choice.
+ * sc_set_kick_push_shape fixes either part (the next sc_track_turns
+ * re-captures); sc_get_kick_push_shape reads the shape of the captured turn
+ * and, in trial_us, the timed trial of the chosen shape (0 when not timed).
+ * Errors: SC_ERR_ARG (NULL grid, a value out of range, or no captured turn). */
+sc_status sc_set_kick_push_shape(sc_grid *g, int threads, int traversal);
+sc_status sc_get_kick_push_shape(sc_grid *g, int *threads, int *traversal, double *trial_us);
+
 /* Failure-detection test hook (no counterpart in the paper).  The tensor-core
  * solve's waits on its copy and MMA barriers are bounded (~2 s of SM clock);
  * when one runs out the kernel records an error word, lets its issued work

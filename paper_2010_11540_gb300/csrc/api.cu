@@ -48,6 +48,11 @@ struct TrackPlan {
   double* d_diag = nullptr;   // [cap][14]
   int diag_cap = 0;
   std::vector<cudaEvent_t> ev;  // tracing: per kick (solve start, kick/push start, kick/push end)
+  int kp_threads = 0;           // kick/push block size (0: the variant's largest)
+  int kp_trav = -1;             // kick/push traversal (-1: the variant's default, 0 grid stride, 1 chunks)
+  int kp_blocks_dep = 0;        // resident grid sizes at kp_threads: with the deposit tile
+  int kp_blocks_plain = 0;      //   and without a deposit
+  double kp_trial_us = 0.0;     // timed trial of the chosen shape (0: not timed)
 };
 
 namespace {
@@ -67,6 +72,126 @@ void destroy_plan(TrackPlan* t) {
   cudaFree(t->d_diag);
   for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
   delete t;
+}
+
+}  // namespace
+
+namespace {
+
+// Bunches from this size up have their kick/push launch shape timed at plan build.
+constexpr int64_t kShapeTuneMinParticles = int64_t(1) << 18;
+
+// Launch shape of a captured turn's kick/push: block size and particle
+// traversal.  Every shape gives bit-identical results (the charge is an
+// integer sum, the particles are independent), so the choice changes only the
+// time.  Each candidate (of the parts the caller left free) is captured as a
+// graph of the turn's first kShapeTuneKicks space-charge steps (solve, then
+// kick/push with its deposit, as in the turn itself) on a scratch copy of the
+// particles and timed: one untimed launch, then the best of three.  The charge
+// grid and the out-of-grid counters are put back afterwards; the fields and
+// the psc, cell and fraction caches the trials overwrite are rebuilt by every
+// call before they are read.
+constexpr int kShapeTuneKicks = 16;
+
+template <class Head, class Mark, class Launch, class Blocks>
+sc_status tune_shape(sc_grid* g, TrackPlan* T, const sc_particles* p, Head&& head_params, Mark&& mark_params,
+                     Launch&& launch, Blocks&& set_blocks) {
+  const int64_t n = p->n;
+  const size_t qbytes = (size_t)g->nx * g->ny * g->nstack * 8, obytes = 8 * (size_t)g->nstack;
+  const int kicks = T->n_kicks < kShapeTuneKicks ? T->n_kicks : kShapeTuneKicks;
+  double* scratch = nullptr;
+  unsigned char* saved = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  sc_status st = SC_OK;
+  auto cu = [&st](cudaError_t e, const char* what) {
+    if (!st && e != cudaSuccess) st = cuda_error(e, what);
+    return st == SC_OK;
+  };
+  cu(cudaMalloc(&scratch, (size_t)n * 6 * sizeof(double)), "cudaMalloc(shape trial)");
+  cu(cudaMalloc(&saved, qbytes + obytes), "cudaMalloc(shape trial)");
+  cu(cudaEventCreate(&e0), "cudaEventCreate");
+  cu(cudaEventCreate(&e1), "cudaEventCreate");
+  sc_particles q = {scratch, scratch + n, scratch + 2 * n, scratch + 3 * n, scratch + 4 * n, scratch + 5 * n, n};
+  const double* src[6] = {p->x, p->px, p->y, p->py, p->sigma, p->psigma};
+  double* dst[6] = {q.x, q.px, q.y, q.py, q.sigma, q.psigma};
+  cu(cudaMemcpyAsync(saved, g->Q, qbytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
+  cu(cudaMemcpyAsync(saved + qbytes, g->n_out, obytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
+  for (int a = 0; a < 6 && st == SC_OK; ++a)
+    cu(cudaMemcpyAsync(dst[a], src[a], (size_t)n * 8, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
+  // the psc cache of the scratch bunch, and its charge (and cell cache) at the
+  // first marker when the lattice opens with one; otherwise each trial opens
+  // with the head segment's deposit into a cleared grid
+  if (st == SC_OK && cu(cudaMemsetAsync(g->Q, 0, qbytes, g->stream), "cudaMemsetAsync")) {
+    KPParams pro = T->prologue;
+    pro.x = q.x, pro.px = q.px, pro.y = q.y, pro.py = q.py, pro.sg = q.sigma, pro.ps = q.psigma;
+    st = launch(pro, !T->has_head);
+  }
+  auto capture = [&](cudaGraphExec_t* exec) -> sc_status {
+    SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    sc_status r = SC_OK;
+    if (T->has_head) r = launch(head_params(&q), true);
+    for (int k = 0; !r && k < kicks; ++k) {
+      r = solve_dispatch(g, true);
+      bool dep = false;
+      if (!r) r = launch(mark_params(&q, (size_t)k, dep), dep);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+    if (!r && ce != cudaSuccess) r = cuda_error(ce, "cudaStreamEndCapture(shape trial)");
+    if (!r) {
+      const cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+      if (ie != cudaSuccess) r = cuda_error(ie, "cudaGraphInstantiate(shape trial)");
+    }
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  };
+  const int th_set = g->kp_threads_set, tr_set = g->nz > 1 ? -1 : g->kp_trav_set;
+  const int f32_max = kick_push_max_threads(g->field32);
+  int best_th = T->kp_threads, best_tr = T->kp_trav;
+  float best = 0.f;
+  for (int th : {384, 512, 640, 768}) {
+    if (th > f32_max || (th_set > 0 && th != th_set)) continue;
+    for (int tr = 0; tr < 2 && st == SC_OK; ++tr) {
+      if (g->nz > 1 ? tr != 0 : (tr_set >= 0 && tr != tr_set)) continue;
+      T->kp_threads = th;
+      T->kp_trav = g->nz > 1 ? -1 : tr;
+      set_blocks();
+      cudaGraphExec_t exec = nullptr;
+      st = capture(&exec);
+      float t_min = 0.f;
+      for (int r = 0; r < 4 && st == SC_OK; ++r) {
+        if (T->has_head && !cu(cudaMemsetAsync(g->Q, 0, qbytes, g->stream), "cudaMemsetAsync")) break;
+        cu(cudaEventRecord(e0, g->stream), "cudaEventRecord");
+        cu(cudaGraphLaunch(exec, g->stream), "cudaGraphLaunch(shape trial)");
+        cu(cudaEventRecord(e1, g->stream), "cudaEventRecord");
+        cu(cudaEventSynchronize(e1), "shape trial");
+        float ms = 0.f;
+        cu(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (r > 0 && (t_min == 0.f || ms < t_min)) t_min = ms;
+      }
+      if (exec) cudaGraphExecDestroy(exec);
+      if (st == SC_OK && (best == 0.f || t_min < best)) {
+        best = t_min;
+        best_th = th;
+        best_tr = T->kp_trav;
+      }
+    }
+  }
+  T->kp_threads = best_th;
+  T->kp_trav = best_tr;
+  T->kp_trial_us = 1e3 * (double)best;
+  set_blocks();
+  // the charge grid and the counters as the caller left them
+  if (saved) {
+    cu(cudaMemcpyAsync(g->Q, saved, qbytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
+    cu(cudaMemcpyAsync(g->n_out, saved + qbytes, obytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
+  }
+  cu(cudaStreamSynchronize(g->stream), "shape trial");
+  cudaFree(scratch);
+  cudaFree(saved);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
 }
 
 }  // namespace
@@ -129,6 +254,7 @@ KPParams base_params(const sc_particles* p, const sc_beam* b) {
   P.n = p->n;
   P.beta0_sq = b->beta0 * b->beta0;
   P.inv_gamma0_sq = 1.0 / (b->gamma0 * b->gamma0);
+  P.traversal = -1;
   return P;
 }
 
@@ -197,6 +323,7 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
     return set_error(SC_ERR_UNSUPPORTED, "unknown solve precision");
   sc_grid* g = new (std::nothrow) sc_grid();
   if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
+  g->kp_trav_set = -1;
   g->nx = nx;
   g->ny = ny;
   g->nz = n_slices;
@@ -489,6 +616,27 @@ sc_status sc_trace_read(sc_grid* g, double* kick_push_ms, double* solve_ms, int6
   return SC_OK;
 }
 
+sc_status sc_set_kick_push_shape(sc_grid* g, int threads, int traversal) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  const int max = kick_push_max_threads(g->field32);
+  if (threads < 0 || threads % 32 != 0 || threads > max)
+    return set_error(SC_ERR_ARG, "kick/push block size must be 0 or a multiple of 32 up to the variant's maximum");
+  if (traversal < -1 || traversal > 1) return set_error(SC_ERR_ARG, "traversal must be -1, 0 or 1");
+  g->kp_threads_set = threads;
+  g->kp_trav_set = traversal;
+  return SC_OK;
+}
+
+sc_status sc_get_kick_push_shape(sc_grid* g, int* threads, int* traversal, double* trial_us) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  const TrackPlan* T = g->track;
+  if (!T) return set_error(SC_ERR_ARG, "no captured turn on this grid");
+  if (threads) *threads = T->kp_threads > 0 ? T->kp_threads : kick_push_max_threads(g->field32);
+  if (traversal) *traversal = g->nz > 1 ? 1 : T->kp_trav >= 0 ? T->kp_trav : (g->field32 ? 1 : 0);
+  if (trial_us) *trial_us = T->kp_trial_us;
+  return SC_OK;
+}
+
 sc_status sc_grid_write_charge(sc_grid* g, const uint64_t* Q, int64_t n_particles) {
   if (!g || !Q) return set_error(SC_ERR_ARG, "grid or Q is NULL");
   if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
@@ -516,11 +664,14 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   put(b, sizeof *b);
   put(&n_elems, sizeof n_elems);
   if (n_elems) put(lattice, (size_t)n_elems * sizeof(sc_element));
+  put(&g->lon, sizeof g->lon);
+  put(&g->gather, sizeof g->gather);
+  put(&g->kp_threads_set, sizeof g->kp_threads_set);
+  put(&g->kp_trav_set, sizeof g->kp_trav_set);
+  const std::vector<unsigned char> shape_key = key;  // what the kick/push shape depends on
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
   put(&g->trace, sizeof g->trace);
-  put(&g->lon, sizeof g->lon);
-  put(&g->gather, sizeof g->gather);
   put(&g->tune_acc, sizeof g->tune_acc);
   put(g->tune_twiss, sizeof g->tune_twiss);
 
@@ -571,21 +722,19 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     T->prologue = base_params(p, b);
     T->prologue.psc = T->psc;
     T->prologue.psc_mode = 2;
+    T->prologue.field32 = g->field32;  // every launch of the plan takes the grid's kernel family (and block size)
     if (!T->has_head && T->n_kicks > 0) {
       set_deposit(T->prologue, g);
       T->prologue.cell = T->cell;
       T->prologue.frac = T->frac;
       T->prologue.fix = T->fix;
     }
-    // ---- capture one turn ------------------------------------------------------
-    SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-    sc_status cst = SC_OK;
-    if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, 14, g->stream);
-    if (!cst && T->has_head) {
-      KPParams P = base_params(p, b);
+    // ---- kick/push launches of one turn, for particles q ------------------------
+    const int nh = marks.empty() ? n_elems : marks[0];
+    auto head_params = [&](const sc_particles* q) {
+      KPParams P = base_params(q, b);
       P.psc = T->psc;
       P.psc_mode = 1;
-      const int nh = marks.empty() ? n_elems : marks[0];
       set_elements(P, lattice, nh, b, T->d_elems);
       if (!marks.empty()) {
         // the turn's last solve cleared the charge (and the prologue did before the first turn)
@@ -594,23 +743,14 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
         P.frac = T->frac;
         P.fix = T->fix;
       }
-      if (!cst)
-        cst = launch_kick_push(P, marks.empty() ? nullptr : g, marks.empty() ? g->kp_blocks_plain : g->kp_blocks,
-                               g->stream);
-    }
-    for (size_t k = 0; !cst && k < marks.size(); ++k) {
+      return P;
+    };
+    // marker k: kick, the segment up to the next marker, and (dep) the next deposit
+    auto mark_params = [&](const sc_particles* q, size_t k, bool& dep) {
       const int m = marks[k];
       const int end = (k + 1 < marks.size()) ? marks[k + 1] : n_elems;
       const double prev = (k > 0) ? s[marks[k - 1]] : s[marks.back()] - circ;
-      if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k], g->stream, cudaEventRecordExternal) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "event");
-      // the solve clears the charge after reading it, ready for this marker's deposit
-      if (!cst) cst = solve_dispatch(g, true);
-      if (cst) break;
-      if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k + 1], g->stream, cudaEventRecordExternal) != cudaSuccess) {
-        cst = set_error(SC_ERR_CUDA, "event");
-        break;
-      }
-      KPParams P = base_params(p, b);
+      KPParams P = base_params(q, b);
       P.psc = T->psc;
       P.psc_mode = 1;
       set_kick(P, g, K * (s[m] - prev), b->gamma0);
@@ -619,9 +759,62 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       P.cell = T->cell;
       P.frac = T->frac;
       P.fix = T->fix;
-      const bool dep = (k + 1 < marks.size()) || !T->has_head;
+      dep = (k + 1 < marks.size()) || !T->has_head;
       if (dep) set_deposit(P, g);
-      cst = launch_kick_push(P, dep ? g : nullptr, dep ? g->kp_blocks : g->kp_blocks_plain, g->stream);
+      return P;
+    };
+    auto launch = [&](KPParams P, bool dep) {
+      P.field32 = g->field32;
+      P.traversal = T->kp_trav;
+      return launch_kick_push(P, dep ? g : nullptr, dep ? T->kp_blocks_dep : T->kp_blocks_plain, g->stream,
+                              T->kp_threads);
+    };
+    // ---- launch shape (block size, traversal) ----------------------------------
+    T->kp_threads = g->kp_threads_set;
+    T->kp_trav = g->nz > 1 ? -1 : g->kp_trav_set;  // sliced grids always use chunks
+    auto set_blocks = [&] {
+      const int th = T->kp_threads > 0 ? T->kp_threads : kick_push_max_threads(g->field32);
+      T->kp_blocks_dep = kick_push_blocks_at(g->nx * g->ny * 8, deposit_uses_tile(g), g->field32, th);
+      T->kp_blocks_plain = kick_push_blocks_at(0, false, g->field32, th);
+    };
+    set_blocks();
+    const bool free_shape = T->kp_threads == 0 || (T->kp_trav < 0 && g->nz == 1);
+    if (T->n_kicks > 0 && p->n >= kShapeTuneMinParticles && free_shape) {
+      if (g->kp_tuned_key == shape_key) {
+        T->kp_threads = g->kp_tuned_threads;
+        T->kp_trav = g->kp_tuned_trav;
+        T->kp_trial_us = g->kp_tuned_us;
+        set_blocks();
+      } else {
+        sc_status tst = tune_shape(g, T, p, head_params, mark_params, launch, set_blocks);
+        if (tst) {
+          destroy_plan(T);
+          g->track = nullptr;
+          return tst;
+        }
+        g->kp_tuned_key = shape_key;
+        g->kp_tuned_threads = T->kp_threads;
+        g->kp_tuned_trav = T->kp_trav;
+        g->kp_tuned_us = T->kp_trial_us;
+      }
+    }
+    // ---- capture one turn ------------------------------------------------------
+    SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+    sc_status cst = SC_OK;
+    if (want_diag) cst = launch_moments(p, T->partial, moments_blocks(), T->d_base, T->d_turn, 14, g->stream);
+    if (!cst && T->has_head) cst = launch(head_params(p), !marks.empty());
+    for (size_t k = 0; !cst && k < marks.size(); ++k) {
+      if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k], g->stream, cudaEventRecordExternal) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "event");
+      // the solve clears the charge after reading it, ready for this marker's deposit
+      if (!cst) cst = solve_dispatch(g, true);
+      if (cst) break;
+      if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k + 1], g->stream, cudaEventRecordExternal) != cudaSuccess) {
+        cst = set_error(SC_ERR_CUDA, "event");
+        break;
+      }
+      bool dep = false;
+      const KPParams P = mark_params(p, k, dep);
+      cst = launch(P, dep);
       if (!cst && g->trace && cudaEventRecordWithFlags(T->ev[3 * k + 2], g->stream, cudaEventRecordExternal) != cudaSuccess)
         cst = set_error(SC_ERR_CUDA, "event");
     }
@@ -662,12 +855,16 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     SC_CUDA(cudaMemsetAsync(T->d_turn, 0, sizeof(int), g->stream));
   }
   g->n_particles = p->n;
-  if (!T->has_head && T->n_kicks > 0) {
-    // charge at the first space-charge location of the first turn
-    SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nstack * 8, g->stream));
-    if ((st = launch_kick_push(T->prologue, g, g->kp_blocks, g->stream))) return st;
-  } else {
-    if ((st = launch_kick_push(T->prologue, nullptr, g->kp_blocks_plain, g->stream))) return st;
+  {
+    KPParams P = T->prologue;
+    P.traversal = T->kp_trav;
+    if (!T->has_head && T->n_kicks > 0) {
+      // charge at the first space-charge location of the first turn
+      SC_CUDA(cudaMemsetAsync(g->Q, 0, (size_t)g->nx * g->ny * g->nstack * 8, g->stream));
+      if ((st = launch_kick_push(P, g, T->kp_blocks_dep, g->stream, T->kp_threads))) return st;
+    } else {
+      if ((st = launch_kick_push(P, nullptr, T->kp_blocks_plain, g->stream, T->kp_threads))) return st;
+    }
   }
   for (int t = 0; t < n_turns; ++t) {
     SC_CUDA(cudaGraphLaunch(T->exec, g->stream));

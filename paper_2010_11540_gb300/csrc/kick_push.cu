@@ -238,14 +238,14 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
   }
   pdl_wait();  // fields, charge grid and particles of the previous kernels
   if (TILE) __syncthreads();
-  // Traversal (measured on the c2 workload): the float32-field variant gives
-  // each block one contiguous, equal chunk (every SM finishes together); the
-  // float64-field variant, whose plan arrays take more of L2, sweeps all
-  // blocks over a common window (grid stride);
-  // consecutive threads take consecutive particles either way.  Sliced grids
-  // always use chunks, so that a block's particles (sorted by sigma) stay in
-  // the slice its tile holds.
-  const bool chunked = F32 || P.gd.nz > 1;
+  // Traversal: each block one contiguous, equal chunk, or all blocks sweeping a
+  // common window (grid stride); consecutive threads take consecutive particles
+  // either way.  Default (measured on the c2 workload): chunks for the
+  // float32-field variant (every SM finishes together), grid stride for the
+  // float64-field variant (whose plan arrays take more of L2); the launch-shape
+  // tuner may choose (P.traversal).  Sliced grids always use chunks, so that a
+  // block's particles (sorted by sigma) stay in the slice its tile holds.
+  const bool chunked = P.gd.nz > 1 || (P.traversal < 0 ? F32 : P.traversal == 1);
   const int64_t chunk = chunked ? (P.n + gridDim.x - 1) / gridDim.x : 0;
   const int64_t p_begin = chunked ? (int64_t)blockIdx.x * chunk : (int64_t)blockIdx.x * blockDim.x;
   const int64_t p_end = chunked ? min(P.n, (int64_t)(blockIdx.x + 1) * chunk) : P.n;
@@ -334,13 +334,31 @@ int kick_push_blocks_for(int smem_bytes, bool tile) {
   return min_blocks(smem_bytes, tile);
 }
 
-sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s) {
+int kick_push_max_threads(bool f32) { return f32 ? kp_max_threads<true>() : kp_max_threads<false>(); }
+
+int kick_push_blocks_at(int smem_bytes, bool tile, bool f32, int threads) {
+  // the smallest occupancy over the gather variants (cell cache, XE) of this field type
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int best = 1 << 30;
+  for (int v = 0; v < 4; ++v) {
+    const KPKernel k = kp_kernel(tile, v & 2, f32, v & 1);
+    if (tile) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, tile ? smem_bytes : 0);
+    best = per < best ? per : best;
+  }
+  return sms * (best < 1 ? 1 : best);
+}
+
+sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s, int threads) {
   const bool tile = P.do_deposit && dep && deposit_uses_tile(dep);
   const bool cache = P.cell != nullptr;
   const bool f32 = P.field32 != 0;
   const bool xe = P.has_xe != 0 || P.bezier != 0;
-  // the variant's largest block: measured, the extra warps outweigh a partly empty last round
-  const int threads = f32 ? kp_max_threads<true>() : kp_max_threads<false>();
+  // default: the variant's largest block (measured: the extra warps outweigh a partly empty last round)
+  if (threads <= 0) threads = kick_push_max_threads(f32);
   const int64_t need = (P.n + threads - 1) / threads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
   const int smem = tile ? dep->nx * dep->ny * 8 : 0;

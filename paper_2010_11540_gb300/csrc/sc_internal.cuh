@@ -118,6 +118,8 @@ struct KPParams {
   // of phi (Sec. IV-C) instead of bilinear node fields; with lon the
   // neighbouring slices' potentials come from the same surfaces.
   int bezier;
+  // particle traversal of the blocks: -1 default, 0 grid stride, 1 contiguous chunks
+  int traversal;
   DevElem inl[KP_INLINE];
 };
 
@@ -185,6 +187,12 @@ struct sc_grid {
   int gather;                  // SC_GATHER_BILINEAR or SC_GATHER_BEZIER (pipe grids)
   int kp_blocks, dep_blocks;   // persistent grid sizes for this grid's tile size
   int kp_blocks_plain;         // kick/push without a deposit
+  int kp_threads_set, kp_trav_set;  // kick/push shape forced by the caller (0 / -1: tuned)
+  // last tuned kick/push shape and what it was timed on (particles, beam, lattice, options),
+  // reused by re-captures that differ only in tracing or diagnostics
+  std::vector<unsigned char> kp_tuned_key;
+  int kp_tuned_threads, kp_tuned_trav;
+  double kp_tuned_us;
   sc::DevElem* el_stage;       // device copy of sc_kick_push's last long segment
   int el_stage_cap;
 };
@@ -195,7 +203,12 @@ namespace sc {
 sc_status launch_deposit(sc_grid* g, const sc_particles* p);
 // kick_push.cu
 // blocks: dep->kp_blocks when depositing into dep, else the kick grid's kp_blocks_plain.
-sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s);
+// threads: block size (0: the variant's largest); blocks as above.
+sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s, int threads = 0);
+int kick_push_max_threads(bool f32);
+// resident blocks on the device at the given block size (smallest over the
+// variants of this field type; smem_bytes: the deposit tile when tile)
+int kick_push_blocks_at(int smem_bytes, bool tile, bool f32, int threads);
 // Batched form: descs[bunch] per bunch, blocks[b] = (bunch, chunk, chunks of that bunch, 0) per block;
 // deposits of grids with at most tile_cells nodes go through the shared-memory tile.
 sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,

@@ -29,8 +29,8 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
-           "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits",
-           "sc_last_error")
+           "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
+           "sc_get_kick_push_shape", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -104,6 +104,8 @@ def load():
     L.sc_set_longitudinal_kick.argtypes = [vp, ctypes.c_int]
     L.sc_set_gather.argtypes = [vp, ctypes.c_int]
     L.sc_test_bounded_waits.argtypes = [vp, ctypes.c_int]
+    L.sc_set_kick_push_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.sc_get_kick_push_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -285,6 +287,20 @@ def get_solver_tiling(grid: Grid):
 def set_solver_tiling(grid: Grid, choice):
     """Force the split-TF32 solve's kernel variant per phase (-1 keeps one)."""
     _check(load().sc_set_solver_tiling(grid.handle, (ctypes.c_int * 4)(*[int(v) for v in choice])))
+
+
+def set_kick_push_shape(grid: Grid, threads: int = 0, traversal: int = -1):
+    """Fix the kick/push block size (0: chosen at capture) and traversal
+    (-1: chosen, 0: grid stride, 1: contiguous chunks) of tracked turns."""
+    _check(load().sc_set_kick_push_shape(grid.handle, int(threads), int(traversal)))
+
+
+def get_kick_push_shape(grid: Grid):
+    """-> (threads, traversal, trial_us) of the grid's captured turn (trial_us:
+    the timed trial of the chosen shape, 0 when the shape was not timed)."""
+    t, v, us = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+    _check(load().sc_get_kick_push_shape(grid.handle, ctypes.byref(t), ctypes.byref(v), ctypes.byref(us)))
+    return int(t.value), int(v.value), us.value
 
 
 def probe_peaks(stream=None):
