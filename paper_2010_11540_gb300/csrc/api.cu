@@ -53,6 +53,9 @@ struct TrackPlan {
   int kp_blocks_dep = 0;        // resident grid sizes at kp_threads: with the deposit tile
   int kp_blocks_plain = 0;      //   and without a deposit
   double kp_trial_us = 0.0;     // timed trial of the chosen shape (0: not timed)
+  std::vector<DevElem> qfam;    // quadrupole families with cached per-particle coefficients
+  DevElem* d_qfam = nullptr;    // their device copy
+  double* qcache = nullptr;     // [qfam][6][n]
 };
 
 namespace {
@@ -70,6 +73,8 @@ void destroy_plan(TrackPlan* t) {
   cudaFree(t->d_base);
   cudaFree(t->d_turn);
   cudaFree(t->d_diag);
+  cudaFree(t->d_qfam);
+  cudaFree(t->qcache);
   for (cudaEvent_t e : t->ev) cudaEventDestroy(e);
   delete t;
 }
@@ -696,6 +701,26 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     T->has_head = marks.empty() ? true : marks[0] > 0;
     std::vector<DevElem> dev(n_elems > 0 ? n_elems : 1);
     compile_elements(lattice, n_elems, b, dev.data());
+    // Quadrupole families whose per-particle coefficients the turn keeps: ps
+    // changes only in RF cavities (after which they are recomputed); with the
+    // longitudinal kick it changes at every kick, and each map computes its own.
+    if (!g->lon) {
+      T->qfam.resize(KP_QFAM_MAX);
+      T->qfam.resize(quad_families(dev.data(), n_elems, T->qfam.data(), KP_QFAM_MAX));
+      tag_quad_families(dev.data(), n_elems, T->qfam.data(), (int)T->qfam.size());
+    }
+    if (!T->qfam.empty()) {
+      SC_CUDA(cudaMalloc(&T->qcache, T->qfam.size() * 6 * (size_t)p->n * sizeof(double)));
+      SC_CUDA(cudaMalloc(&T->d_qfam, T->qfam.size() * sizeof(DevElem)));
+      SC_CUDA(cudaMemcpy(T->d_qfam, T->qfam.data(), T->qfam.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
+    }
+    auto with_qcache = [T](KPParams& P) {
+      if (T->qfam.empty()) return;
+      P.qcache = T->qcache;
+      P.qfam = T->d_qfam;
+      P.qfam_n = (int)T->qfam.size();
+      if (!P.el) tag_quad_families(P.inl, P.n_elem, T->qfam.data(), P.qfam_n);
+    };
     SC_CUDA(cudaMalloc(&T->d_elems, dev.size() * sizeof(DevElem)));
     SC_CUDA(cudaMemcpy(T->d_elems, dev.data(), dev.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
     if (!marks.empty()) {
@@ -723,6 +748,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     T->prologue.psc = T->psc;
     T->prologue.psc_mode = 2;
     T->prologue.field32 = g->field32;  // every launch of the plan takes the grid's kernel family (and block size)
+    with_qcache(T->prologue);
     if (!T->has_head && T->n_kicks > 0) {
       set_deposit(T->prologue, g);
       T->prologue.cell = T->cell;
@@ -736,6 +762,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       P.psc = T->psc;
       P.psc_mode = 1;
       set_elements(P, lattice, nh, b, T->d_elems);
+      with_qcache(P);
       if (!marks.empty()) {
         // the turn's last solve cleared the charge (and the prologue did before the first turn)
         set_deposit(P, g);
@@ -755,6 +782,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       P.psc_mode = 1;
       set_kick(P, g, K * (s[m] - prev), b->gamma0);
       set_elements(P, lattice + m + 1, end - m - 1, b, T->d_elems + m + 1);
+      with_qcache(P);
       // the cell cache is valid at every marker: the previous launch deposited on this grid
       P.cell = T->cell;
       P.frac = T->frac;

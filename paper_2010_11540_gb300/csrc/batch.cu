@@ -30,6 +30,11 @@ struct BatchPlan {
   std::vector<double2*> frac;
   std::vector<int2*> fix;
   std::vector<double*> psc;
+  // quadrupole families with cached per-particle coefficients (batch grids are
+  // not sliced: ps changes only in RF cavities)
+  std::vector<std::vector<DevElem>> qfam;
+  std::vector<DevElem*> d_qfam;
+  std::vector<double*> qcache;  // [qfam][6][n]
   // launch descriptors: [launch][bunch]; launch 0 = prologue, 1 = head (if any), then one per marker
   KPParams* d_descs = nullptr;
   int n_launches = 0;
@@ -57,6 +62,8 @@ void destroy_batch_plan(BatchPlan* t) {
   for (auto* p : t->frac) cudaFree(p);
   for (auto* p : t->fix) cudaFree(p);
   for (auto* p : t->psc) cudaFree(p);
+  for (auto* p : t->d_qfam) cudaFree(p);
+  for (auto* p : t->qcache) cudaFree(p);
   cudaFree(t->d_descs);
   cudaFree(t->d_blocks);
   cudaFree(t->partial);
@@ -285,6 +292,9 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     T->frac.assign(nb, nullptr);
     T->fix.assign(nb, nullptr);
     T->psc.assign(nb, nullptr);
+    T->qfam.assign(nb, {});
+    T->d_qfam.assign(nb, nullptr);
+    T->qcache.assign(nb, nullptr);
     std::vector<int64_t> counts(nb);
     for (int b = 0; b < nb; ++b) {
       const sc_bunch& u = bunches[b];
@@ -292,6 +302,15 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
       counts[b] = n;
       std::vector<DevElem> dev(u.n_elems > 0 ? u.n_elems : 1);
       compile_elements(u.lattice, u.n_elems, &u.beam, dev.data());
+      std::vector<DevElem>& fam = T->qfam[b];
+      fam.resize(KP_QFAM_MAX);
+      fam.resize(quad_families(dev.data(), u.n_elems, fam.data(), KP_QFAM_MAX));
+      tag_quad_families(dev.data(), u.n_elems, fam.data(), (int)fam.size());
+      if (!fam.empty() && n > 0) {
+        SC_CUDA(cudaMalloc(&T->qcache[b], fam.size() * 6 * (size_t)n * sizeof(double)));
+        SC_CUDA(cudaMalloc(&T->d_qfam[b], fam.size() * sizeof(DevElem)));
+        SC_CUDA(cudaMemcpy(T->d_qfam[b], fam.data(), fam.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
+      }
       SC_CUDA(cudaMalloc(&T->d_elems[b], dev.size() * sizeof(DevElem)));
       SC_CUDA(cudaMemcpy(T->d_elems[b], dev.data(), dev.size() * sizeof(DevElem), cudaMemcpyHostToDevice));
       const size_t m = (size_t)(n > 0 ? n : 1);
@@ -342,12 +361,20 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
       for (int k = 0; k < u.n_elems; ++k) s[k + 1] = s[k] + u.lattice[k].length;
       const double circ = s[u.n_elems];
       const double K = kick_strength(bm);
+      auto with_qcache = [&](KPParams& P) {
+        if (!T->qcache[b]) return;
+        P.qcache = T->qcache[b];
+        P.qfam = T->d_qfam[b];
+        P.qfam_n = (int)T->qfam[b].size();
+        if (!P.el) tag_quad_families(P.inl, P.n_elem, T->qfam[b].data(), P.qfam_n);
+      };
       int L = 0;
       // prologue: the ps-dependent quantities, and the first deposit for lattices opening with a marker
       KPParams& P0 = descs[(size_t)L * nb + b];
       P0 = base_params(p, bm);
       P0.psc = T->psc[b];
       P0.psc_mode = 2;
+      with_qcache(P0);
       if (!T->has_head && n_marks > 0) {
         bunch_deposit(B, b, P0);
         P0.cell = T->cell[b];
@@ -363,6 +390,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         P.psc_mode = 1;
         const int nh = mk.empty() ? u.n_elems : mk[0];
         set_elements(P, u.lattice, nh, bm, T->d_elems[b]);
+        with_qcache(P);
         if (!mk.empty()) {
           bunch_deposit(B, b, P);
           P.cell = T->cell[b];
@@ -382,6 +410,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         P.psc_mode = 1;
         bunch_kick(B, b, P, K * (s[m] - prev));
         set_elements(P, u.lattice + m + 1, end - m - 1, bm, T->d_elems[b] + m + 1);
+        with_qcache(P);
         P.cell = T->cell[b];
         P.frac = T->frac[b];
         P.fix = T->fix[b];

@@ -6,6 +6,7 @@
 // particle, persistent grid over SoA float64 state; one launch serves one grid
 // (kick_push_kernel) or every bunch of a batch (kick_push_batched).
 #include <cmath>
+#include <cstring>
 
 #include "cic.cuh"
 #include "maps.cuh"
@@ -57,6 +58,22 @@ __device__ __noinline__ void bezier_kick32(State& s, const KPParams& P, int cell
     if (k + 1 < P.gk.nz) bezier_eval<float, true, false>(ph + cells, nxk, nyk, i, j, fx, fy, up, a, b);
     if (k > 0) bezier_eval<float, true, false>(ph - cells, nxk, nyk, i, j, fx, fy, dn, a, b);
     s.ps = fma(-P.klz, (double)(up - dn), s.ps);
+  }
+}
+
+// The particle's coefficients of every quadrupole family, from its current ps
+// (k), into the cache.  Not inlined: it runs once per call and after RF cavities.
+__device__ __noinline__ void store_quad_cache(const KPParams& P, const PsConst& k, int64_t p) {
+  const size_t n = (size_t)P.n;
+  for (int f = 0; f < P.qfam_n; ++f) {
+    const QuadCoef q = quad_coef(P.qfam[f], k);
+    double* c = P.qcache + (size_t)f * 6 * n + p;
+    c[0] = q.cx;
+    c[n] = q.sxa;
+    c[2 * n] = q.sxb;
+    c[3 * n] = q.cy;
+    c[4 * n] = q.sya;
+    c[5 * n] = q.syb;
   }
 }
 
@@ -178,14 +195,17 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
       ps_const(k, s.ps, P.beta0_sq, fresh || P.has_quad != 0);
     }
     const bool quads = psc_mode != 0 || P.has_quad != 0;
-    const bool changed = P.el ? push_elements<XE>(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads)
-                              : push_elements<XE>(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads);
+    // the quadrupole coefficient cache holds this particle's values unless ps changed in this launch
+    const double* qc = (P.qcache && psc_mode == 1 && !fresh) ? P.qcache + p : nullptr;
+    const bool changed = P.el ? push_elements<XE>(s, k, P.el, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads, qc, n)
+                              : push_elements<XE>(s, k, P.inl, P.n_elem, P.beta0_sq, P.inv_gamma0_sq, quads, qc, n);
     if (fresh || (psc_mode == 1 && changed)) {
       P.psc[p] = k.opd2;
       P.psc[n + p] = k.opb;
       P.psc[2 * n + p] = k.s1;
       P.psc[3 * n + p] = k.r;
       P.psc[4 * n + p] = k.qi;
+      if (P.qcache) store_quad_cache(P, k, p);
     }
     if (P.do_deposit) {
       double fx = 0.0, fy = 0.0;
@@ -474,6 +494,36 @@ void compile_elements(const sc_element* in, int n, const sc_beam* b, DevElem* ou
       default:
         break;
     }
+  }
+}
+
+int quad_families(const DevElem* el, int n, DevElem* fam, int max) {
+  int nf = 0;
+  for (int i = 0; i < n; ++i) {
+    const DevElem& e = el[i];
+    if (e.type != SC_QUAD || (e.flags & QF_KIND) == QF_ZERO) continue;
+    bool seen = false;
+    for (int f = 0; f < nf && !seen; ++f)
+      seen = (fam[f].flags & QF_KIND) == (e.flags & QF_KIND) && std::memcmp(fam[f].p, e.p, sizeof e.p) == 0;
+    if (!seen && nf < max) {
+      fam[nf] = e;
+      fam[nf].flags = e.flags & QF_KIND;
+      ++nf;
+    }
+  }
+  return nf;
+}
+
+void tag_quad_families(DevElem* el, int n, const DevElem* fam, int nf) {
+  for (int i = 0; i < n; ++i) {
+    DevElem& e = el[i];
+    if (e.type != SC_QUAD) continue;
+    e.flags &= QF_KIND;
+    for (int f = 0; f < nf; ++f)
+      if (fam[f].flags == e.flags && std::memcmp(fam[f].p, e.p, sizeof e.p) == 0) {
+        e.flags |= (f + 1) << QF_FAM_SHIFT;
+        break;
+      }
   }
 }
 

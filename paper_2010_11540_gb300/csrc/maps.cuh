@@ -12,7 +12,10 @@
 
 namespace sc {
 
-enum : int { QF_ZERO = 0, QF_FOCUS_X = 1, QF_FOCUS_Y = 2 };
+// Quadrupole flags: the kind (QF_KIND bits) and, from bit QF_FAM_SHIFT, 1 +
+// the index of the quadrupole's family in the per-particle coefficient cache
+// (0: the map computes its own coefficients).
+enum : int { QF_ZERO = 0, QF_FOCUS_X = 1, QF_FOCUS_Y = 2, QF_KIND = 3, QF_FAM_SHIFT = 4 };
 
 // Largest chromatic phase shift |Delta| = |theta0 (sqrt(1-ps) - 1)| handled by
 // the angle-addition series: with terms up to Delta^5 (sin) and Delta^4 (cos),
@@ -72,17 +75,16 @@ __device__ __forceinline__ void map_drift(State& s, const DevElem& e, const PsCo
 // which gives sg += ps L/gamma0^2 - (L S2 + D) / (4 (1-ps)) with
 // S2 = (1-ps)(px0^2+py0^2) + k1 (x0^2 - y0^2), D = [x px + y py]_0^L.
 // e.p = {L, theta0, cos theta0, sin theta0, cosh theta0, sinh theta0, sqk, 1/sqk, k1},
-// e.flags = QF_*; the L/gamma0^2 term is e.p[0] * inv_gamma0_sq.
-__device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
-  const double L = e.p[0];
-  if (e.flags == QF_ZERO) {  // flow of H0: straight line with the chromatic factor
-    const double f = k.opm * L;
-    const double pp = fma(s.px, s.px, s.py * s.py);
-    s.x = fma(f, s.px, s.x);
-    s.y = fma(f, s.py, s.y);
-    s.sg = fma(-0.5 * L, pp, fma(s.ps, L * inv_gamma0_sq, s.sg));
-    return;
-  }
+// e.flags = QF_* (plus the family bits); the L/gamma0^2 term is e.p[0] * inv_gamma0_sq.
+//
+// The entries of the two planes' 2x2 matrices depend on ps alone (QuadCoef:
+// u = cu u0 + sua pu0, pu = cu pu0 + sub u0), so a turn's tracking keeps them
+// per particle and quadrupole family (computed where psc is, read by the map).
+struct QuadCoef {
+  double cx, sxa, sxb, cy, sya, syb;
+};
+
+__device__ __forceinline__ QuadCoef quad_coef(const DevElem& e, const PsConst& k) {
   const double th0 = e.p[1];
   const double delta = fma(th0, k.s1, -th0);
   double c, sn, ch, sh;
@@ -105,24 +107,44 @@ __device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsCon
   }
   const double a = k.s1 * e.p[7];
   const double bq = e.p[6] * k.r;
+  // focusing plane on trig (c, sn), defocusing on hyperbolic (ch, sh)
+  if ((e.flags & QF_KIND) == QF_FOCUS_X) return QuadCoef{c, a * sn, -bq * sn, ch, a * sh, bq * sh};
+  return QuadCoef{ch, a * sh, bq * sh, c, a * sn, -bq * sn};
+}
+
+__device__ __forceinline__ void quad_apply(State& s, const DevElem& e, const QuadCoef& q, const PsConst& k,
+                                           double inv_gamma0_sq) {
+  const double L = e.p[0];
   const double x0 = s.x, px0 = s.px, y0 = s.y, py0 = s.py;
   const double S2 = fma(e.p[8], fma(x0, x0, -y0 * y0), k.opm * fma(px0, px0, py0 * py0));
   const double D0 = fma(x0, px0, y0 * py0);
-  // focusing plane on trig (c, sn), defocusing on hyperbolic (ch, sh)
-  double cx, sx_a, sx_b, cy, sy_a, sy_b;
-  if (e.flags == QF_FOCUS_X) {
-    cx = c;  sx_a = a * sn;  sx_b = -bq * sn;
-    cy = ch; sy_a = a * sh;  sy_b = bq * sh;
-  } else {
-    cx = ch; sx_a = a * sh;  sx_b = bq * sh;
-    cy = c;  sy_a = a * sn;  sy_b = -bq * sn;
-  }
-  s.x = fma(cx, x0, sx_a * px0);
-  s.px = fma(cx, px0, sx_b * x0);
-  s.y = fma(cy, y0, sy_a * py0);
-  s.py = fma(cy, py0, sy_b * y0);
+  s.x = fma(q.cx, x0, q.sxa * px0);
+  s.px = fma(q.cx, px0, q.sxb * x0);
+  s.y = fma(q.cy, y0, q.sya * py0);
+  s.py = fma(q.cy, py0, q.syb * y0);
   const double D = fma(s.x, s.px, s.y * s.py) - D0;
   s.sg = fma(-fma(L, S2, D), k.qi, fma(s.ps, L * inv_gamma0_sq, s.sg));
+}
+
+__device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
+  if ((e.flags & QF_KIND) == QF_ZERO) {  // flow of H0: straight line with the chromatic factor
+    const double L = e.p[0];
+    const double f = k.opm * L;
+    const double pp = fma(s.px, s.px, s.py * s.py);
+    s.x = fma(f, s.px, s.x);
+    s.y = fma(f, s.py, s.y);
+    s.sg = fma(-0.5 * L, pp, fma(s.ps, L * inv_gamma0_sq, s.sg));
+    return;
+  }
+  quad_apply(s, e, quad_coef(e, k), k, inv_gamma0_sq);
+}
+
+// The map with the particle's cached coefficients: qc points at its entry of
+// the family's six arrays of n (cx, sxa, sxb, cy, sya, syb).
+__device__ __forceinline__ void map_quad_cached(State& s, const DevElem& e, const double* __restrict__ qc, size_t n,
+                                                const PsConst& k, double inv_gamma0_sq) {
+  const QuadCoef q{qc[0], qc[n], qc[2 * n], qc[3 * n], qc[4 * n], qc[5 * n]};
+  quad_apply(s, e, q, k, inv_gamma0_sq);
 }
 
 // Flow of H0 = (px^2+py^2)/2 (1-ps) + ps^2/(2 gamma0^2) over l.
@@ -218,19 +240,29 @@ __device__ __forceinline__ void map_rf(State& s, const DevElem& e) {
 
 // Push through n_elem elements with the ps-dependent quantities k (valid on
 // entry).  quads: refresh k's square roots after an RF cavity.  Returns true
-// when an RF cavity changed ps (k then holds the new values).  XE: the
-// segment may hold thick sextupoles or exact dipoles (their code is compiled
-// only into the kernels that need it, keeping the common kernels' registers).
+// when an RF cavity changed ps (k then holds the new values).  qc: the
+// particle's entry in the quadrupole coefficient cache (arrays of n), valid
+// until an RF cavity; NULL: none.  XE: the segment may hold thick sextupoles
+// or exact dipoles (their code is compiled only into the kernels that need
+// it, keeping the common kernels' registers).
 template <bool XE>
 __device__ __forceinline__ bool push_elements(State& s, PsConst& k, const DevElem* __restrict__ el, int n_elem,
-                                              double beta0_sq, double inv_gamma0_sq, bool quads) {
+                                              double beta0_sq, double inv_gamma0_sq, bool quads,
+                                              const double* __restrict__ qc, size_t n) {
   bool changed = false;
 #pragma unroll 1
   for (int i = 0; i < n_elem; ++i) {
     const DevElem e = el[i];
     switch (e.type) {
       case SC_DRIFT: map_drift(s, e, k); break;
-      case SC_QUAD: map_quad(s, e, k, inv_gamma0_sq); break;
+      case SC_QUAD: {
+        const int fam = e.flags >> QF_FAM_SHIFT;
+        if (qc && fam && !changed)
+          map_quad_cached(s, e, qc + (size_t)(fam - 1) * 6 * n, n, k, inv_gamma0_sq);
+        else
+          map_quad(s, e, k, inv_gamma0_sq);
+        break;
+      }
       case SC_SEXT:
         if (XE)
           map_sext(s, e, k, inv_gamma0_sq);

@@ -107,6 +107,13 @@ struct KPParams {
   // (computed in registers), 1: read (rewritten after an RF cavity), 2: compute and write.
   double* psc;
   int psc_mode;
+  // Per-particle coefficients of the lattice's quadrupole families (they
+  // depend on ps alone), qfam_n x 6 arrays of n: written with psc (psc_mode 2,
+  // and after an RF cavity), read by the quadrupoles tagged with a family while
+  // ps is unchanged.  NULL: every quadrupole computes its own.
+  double* qcache;
+  const DevElem* qfam;  // the families' compiled elements (device)
+  int qfam_n;
   // Longitudinal kick (sliced pipe grids, float64 form): psigma -= klz *
   // (Phi_{k+1} - Phi_{k-1}) at the particle, phi the slices' node potentials
   // of the kick grid, klz = K gamma0 L / (2 dz).
@@ -125,6 +132,12 @@ struct KPParams {
 
 // Host: compile n user elements into out (float64 constants per element).
 void compile_elements(const sc_element* in, int n, const sc_beam* b, DevElem* out);
+// Host: the distinct (thick, non-zero) quadrupoles of compiled elements, up to
+// max, copied into fam; returns their count.
+constexpr int KP_QFAM_MAX = 8;
+int quad_families(const DevElem* el, int n, DevElem* fam, int max);
+// Host: tag each quadrupole of el equal to a family with its index.
+void tag_quad_families(DevElem* el, int n, const DevElem* fam, int nf);
 
 // Solve scratch and spectra for the float64 FFT form.
 struct Fft64Plan {

@@ -360,6 +360,33 @@ def test_track_with_rf_and_head():
     assert np.abs(got["psigma"] - parts["psigma"]).max() > 1e-6  # the cavity did act
 
 
+def test_quad_coefficient_cache_bit_identical():
+    """Tracked turns keep each particle's quadrupole matrix entries per
+    quadrupole family (computed once per call and again after an RF cavity);
+    the stand-alone kick/push computes them in every map.  Two turns of a
+    lattice with a head segment and an RF cavity give the same bits both ways."""
+    parts, b, grid, lat = synth.workload("c1", n=5000)
+    rows = list(lat)
+    rf = synth.table([synth.elem(synth.RF, volt=4e6, harmonic=4.0, lag=0.0)])[0]
+    lat2 = synth.table([tuple(rows[0]), tuple(rf)] + [tuple(r) for r in rows[1:]])
+    b = dict(b, circumference=float(lat2["length"].sum()))
+    g = sc.create_grid(*grid)
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat2, 2)
+    g2 = sc.create_grid(*grid)
+    st2 = to_gpu(parts)
+    head, kicks = oracle.segments(lat2)
+    assert len(head) == 3 and len(kicks) > 1  # quad, cavity, drift
+    for _ in range(2):
+        sc.kick_push(g2, st2, b, 0.0, head)
+        for L, seg in kicks:
+            sc.deposit(g2, st2)
+            sc.solve(g2)
+            sc.kick_push(g2, st2, b, L, seg)
+    for k in KEYS:
+        assert np.array_equal(st[k].cpu().numpy(), st2[k].cpu().numpy()), k
+
+
 def test_track_without_space_charge_markers():
     parts, b, grid, lat = synth.workload("c1", n=3000)
     lat2 = lat[lat["type"] != synth.MARK]
