@@ -301,7 +301,7 @@ class SingleRun:
 
     def host_turn(self, h, pinned):
         from paper_2010_11540_gb300 import sc
-        sc.track_turns_host(h[0], pinned, self.b, self.lat, 1, device_state=h[1])
+        sc.track_turns_host(h[0], pinned, self.b, self.lat, 1)
 
     def close(self, h):
         h[0].close()
@@ -402,7 +402,7 @@ class BatchRun:
 
     def host_turn(self, h, pinned):
         from paper_2010_11540_gb300 import sc
-        sc.batch_track_turns_host(h[0], pinned, self.beams, self.lats, 1, device_states=h[1])
+        sc.batch_track_turns_host(h[0], pinned, self.beams, self.lats, 1)
 
     def close(self, h):
         pass

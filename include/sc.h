@@ -160,8 +160,10 @@ sc_status sc_kick_push(sc_grid *g, const sc_particles *p, const sc_beam *b, doub
  * pushed; elements before the first marker are pushed without a kick.  One
  * turn is captured once as a CUDA graph and replayed (re-captured when any
  * argument changes).  The grid keeps per-particle working arrays for the run
- * (cell/fraction cache of the last deposit, psigma-dependent quantities; 60
- * bytes per particle), recomputed at the start of every call.  When diag != NULL
+ * (cell/fraction cache of the last deposit, psigma-dependent quantities, and
+ * the 2x2 matrix entries of each distinct thick quadrupole, up to 8, as long
+ * as psigma is unchanged; 60 + 48 per quadrupole bytes per particle),
+ * recomputed at the start of every call.  When diag != NULL
  * (host, n_turns x 14 doubles) the beam moments at the start of every turn
  * are written there: means of (x, px, y, py, sigma, psigma), then central
  * <xx>, <x px>, <px px>, <yy>, <y py>, <py py>, <sigma sigma>,
@@ -169,6 +171,16 @@ sc_status sc_kick_push(sc_grid *g, const sc_particles *p, const sc_beam *b, doub
  * Errors: SC_ERR_ARG, SC_ERR_OVERFLOW, SC_ERR_CUDA. */
 sc_status sc_track_turns(sc_grid *g, const sc_particles *p, const sc_beam *b,
                          const sc_element *lattice, int n_elems, int n_turns, double *diag);
+
+/* sc_track_turns on a bunch held in HOST memory: host->x .. host->psigma are
+ * host arrays of host->n doubles (page-locked memory copies fastest), read at
+ * the call and overwritten with the tracked state before it returns.  The
+ * grid owns device copies (grown on demand, reused across calls, so the
+ * captured turn is reused too); the copies run on the grid's stream around
+ * the turns and the call is synchronous.  Errors: as sc_track_turns, and
+ * SC_ERR_OOM when the device copies cannot be allocated. */
+sc_status sc_track_turns_host(sc_grid *g, const sc_particles *host, const sc_beam *b,
+                              const sc_element *lattice, int n_elems, int n_turns, double *diag);
 
 /* Synchronous copy-out of a grid's state into host arrays (each may be NULL):
  * Q (n_slices*ny*nx uint64, row-major [k][j][i]), Ex and Ey (same layout,
@@ -248,8 +260,7 @@ sc_status sc_get_solver_tiling(sc_grid *g, int *choice, char *desc, size_t n);
 sc_status sc_set_solver_tiling(sc_grid *g, const int *choice);
 
 /* Launch shape of sc_track_turns' fused kick/push (Sec. IV-A, IV-B): block
- * size (threads, a multiple of 32 up to 768 for split-TF32 grids and 640 for
- * float64 fields) and particle traversal (0: all blocks sweep a common window,
+ * size (threads, a multiple of 32 up to 768) and particle traversal (0: all blocks sweep a common window,
  * grid stride; 1: each block takes one contiguous chunk; sliced grids always
  * use chunks).  Every shape gives bit-identical results.  Left free (threads
  * 0, traversal -1: the default), the shape is chosen when a turn is captured
@@ -323,6 +334,13 @@ sc_status sc_destroy_batch(sc_batch *B);
  * Errors: SC_ERR_ARG (NULL, mismatched markers), SC_ERR_OVERFLOW (a bunch over
  * SC_MAX_PARTICLES_PER_GRID), SC_ERR_CUDA, SC_ERR_OOM. */
 sc_status sc_batch_track_turns(sc_batch *B, const sc_bunch *bunches, int n_turns, double *diag);
+
+/* sc_batch_track_turns on bunches held in HOST memory (each bunch's
+ * particles.x .. psigma host arrays, read at the call and overwritten with
+ * the tracked state), with device copies owned by the batch as in
+ * sc_track_turns_host.  Synchronous.  Errors: as sc_batch_track_turns, and
+ * SC_ERR_OOM. */
+sc_status sc_batch_track_turns_host(sc_batch *B, const sc_bunch *bunches, int n_turns, double *diag);
 
 /* Synchronous copy-out of bunch b's grid state, as sc_grid_read. */
 sc_status sc_batch_read(sc_batch *B, int b, uint64_t *Q, double *Ex, double *Ey, int64_t *n_out);

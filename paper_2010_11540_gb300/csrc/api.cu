@@ -438,6 +438,7 @@ sc_status sc_destroy_grid(sc_grid* g) {
     fft64_destroy(g);
   cudaFree(g->Q);
   cudaFree(g->E);
+  cudaFree(g->host_stage);
   cudaFree(g->n_out);
   cudaFree(g->stack_scale);
   cudaFree(g->el_stage);
@@ -618,6 +619,36 @@ sc_status sc_trace_read(sc_grid* g, double* kick_push_ms, double* solve_ms, int6
   if (n_kicks) *n_kicks = g->trace_kicks;
   g->trace_kp_ms = g->trace_solve_ms = 0.0;
   g->trace_kicks = 0;
+  return SC_OK;
+}
+
+sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_beam* b, const sc_element* lattice,
+                              int n_elems, int n_turns, double* diag) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  sc_status st;
+  if ((st = check_particles(host))) return st;
+  if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
+  const int64_t n = host->n;
+  if (n_turns == 0 || n == 0) return SC_OK;
+  if (n > g->host_stage_cap) {
+    SC_CUDA(cudaStreamSynchronize(g->stream));
+    cudaFree(g->host_stage);
+    g->host_stage = nullptr;
+    g->host_stage_cap = 0;
+    SC_CUDA(cudaMalloc(&g->host_stage, (size_t)n * 6 * sizeof(double)));
+    g->host_stage_cap = n;
+  }
+  const size_t cap = (size_t)g->host_stage_cap;
+  double* src[6] = {host->x, host->px, host->y, host->py, host->sigma, host->psigma};
+  sc_particles dev = {g->host_stage, g->host_stage + cap, g->host_stage + 2 * cap, g->host_stage + 3 * cap,
+                      g->host_stage + 4 * cap, g->host_stage + 5 * cap, n};
+  double* dst[6] = {dev.x, dev.px, dev.y, dev.py, dev.sigma, dev.psigma};
+  for (int a = 0; a < 6; ++a)
+    SC_CUDA(cudaMemcpyAsync(dst[a], src[a], (size_t)n * 8, cudaMemcpyHostToDevice, g->stream));
+  if ((st = sc_track_turns(g, &dev, b, lattice, n_elems, n_turns, diag))) return st;
+  for (int a = 0; a < 6; ++a)
+    SC_CUDA(cudaMemcpyAsync(src[a], dst[a], (size_t)n * 8, cudaMemcpyDeviceToHost, g->stream));
+  SC_CUDA(cudaStreamSynchronize(g->stream));
   return SC_OK;
 }
 

@@ -93,6 +93,8 @@ struct sc_batch {
   int trace = 0;
   double trace_kp_ms = 0.0, trace_solve_ms = 0.0;
   int64_t trace_kicks = 0;
+  double* host_stage = nullptr;  // device copies for sc_batch_track_turns_host: bunch after bunch, [6][n_b] each
+  int64_t host_stage_cap = 0;    // particles
 };
 
 using namespace sc;
@@ -231,8 +233,56 @@ sc_status sc_destroy_batch(sc_batch* B) {
   for (cudaStream_t st : B->side) cudaStreamDestroy(st);
   for (cudaEvent_t ev : B->join_ev) cudaEventDestroy(ev);
   if (B->fork_ev) cudaEventDestroy(B->fork_ev);
+  cudaFree(B->host_stage);
   if (B->own_stream) cudaStreamDestroy(B->stream);
   delete B;
+  return SC_OK;
+}
+
+sc_status sc_batch_track_turns_host(sc_batch* B, const sc_bunch* bunches, int n_turns, double* diag) {
+  if (!B || !bunches) return set_error(SC_ERR_ARG, "batch or bunches is NULL");
+  if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
+  const int nb = B->n_bunches;
+  sc_status st;
+  int64_t total = 0;
+  for (int b = 0; b < nb; ++b) {
+    if ((st = check_particles(&bunches[b].particles))) return st;
+    total += bunches[b].particles.n;
+  }
+  if (n_turns == 0) return SC_OK;
+  if (total > B->host_stage_cap) {
+    SC_CUDA(cudaStreamSynchronize(B->stream));
+    cudaFree(B->host_stage);
+    B->host_stage = nullptr;
+    B->host_stage_cap = 0;
+    SC_CUDA(cudaMalloc(&B->host_stage, (size_t)(total > 0 ? total : 1) * 6 * sizeof(double)));
+    B->host_stage_cap = total;
+  }
+  std::vector<sc_bunch> dev(bunches, bunches + nb);
+  size_t off = 0;
+  for (int b = 0; b < nb; ++b) {
+    const sc_particles& h = bunches[b].particles;
+    const size_t n = (size_t)h.n;
+    sc_particles& d = dev[b].particles;
+    double* base = B->host_stage + 6 * off;
+    d.x = base, d.px = base + n, d.y = base + 2 * n, d.py = base + 3 * n, d.sigma = base + 4 * n,
+    d.psigma = base + 5 * n;
+    const double* src[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
+    for (int a = 0; a < 6 && n > 0; ++a)
+      SC_CUDA(cudaMemcpyAsync(base + a * n, src[a], n * 8, cudaMemcpyHostToDevice, B->stream));
+    off += n;
+  }
+  if ((st = sc_batch_track_turns(B, dev.data(), n_turns, diag))) return st;
+  for (int b = 0; b < nb; ++b) {
+    const sc_particles& h = bunches[b].particles;
+    const sc_particles& d = dev[b].particles;
+    const size_t n = (size_t)h.n;
+    double* dst[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
+    const double* src[6] = {d.x, d.px, d.y, d.py, d.sigma, d.psigma};
+    for (int a = 0; a < 6 && n > 0; ++a)
+      SC_CUDA(cudaMemcpyAsync(dst[a], src[a], n * 8, cudaMemcpyDeviceToHost, B->stream));
+  }
+  SC_CUDA(cudaStreamSynchronize(B->stream));
   return SC_OK;
 }
 

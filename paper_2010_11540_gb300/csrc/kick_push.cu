@@ -17,10 +17,17 @@ namespace {
 
 // Block sizes are multiples of 4 warps so that the four SM sub-partitions,
 // each with its own FP64 unit, carry the same number of warps.  Largest block
-// per variant (measured on the c2 workload): float32-field gather 768 threads
-// (80 registers), float64-field gather 640 threads (96 registers).
+// per variant (measured on the c2 workload): 768 threads (80 registers) for
+// the single-grid kernels (bounding the float32-field kernel at 1024 threads,
+// 64 registers, spilled and ran 1% slower; the float64-field kernel gained 3%
+// over 640 threads with 96 registers); the batched float64-field kernel,
+// whose per-bunch descriptor costs registers, keeps 640 (96 registers).
 template <bool F32>
 constexpr int kp_max_threads() {
+  return 768;
+}
+template <bool F32>
+constexpr int kpb_max_threads() {
   return F32 ? 768 : 640;
 }
 
@@ -278,7 +285,7 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
 // contiguous chunk blocks[b].y of blocks[b].z equal chunks of that bunch.
 // The bunch's deposit uses the tile when its grid fits tile_cells.
 template <bool CACHE, bool F32, bool XE>
-__global__ void __launch_bounds__(kp_max_threads<F32>())
+__global__ void __launch_bounds__(kpb_max_threads<F32>())
     kick_push_batched(const KPParams* __restrict__ descs, const int4* __restrict__ blocks, int tile_cells) {
   extern __shared__ unsigned long long tile[];
   __shared__ int tile_k;
@@ -386,7 +393,7 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
   return SC_OK;
 }
 
-int kick_push_batched_threads(bool f32) { return f32 ? kp_max_threads<true>() : kp_max_threads<false>(); }
+int kick_push_batched_threads(bool f32) { return f32 ? kpb_max_threads<true>() : kpb_max_threads<false>(); }
 
 int kick_push_batched_resident(int smem_bytes, bool f32, bool cache) {
   int dev = 0, sms = 0, per = 1 << 30;

@@ -208,6 +208,8 @@ struct sc_grid {
   double kp_tuned_us;
   sc::DevElem* el_stage;       // device copy of sc_kick_push's last long segment
   int el_stage_cap;
+  double* host_stage;          // device copy of sc_track_turns_host's particles [6][cap]
+  int64_t host_stage_cap;
 };
 
 namespace sc {

@@ -30,7 +30,7 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
            "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
-           "sc_get_kick_push_shape", "sc_last_error")
+           "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -105,6 +105,9 @@ def load():
     L.sc_set_gather.argtypes = [vp, ctypes.c_int]
     L.sc_test_bounded_waits.argtypes = [vp, ctypes.c_int]
     L.sc_set_kick_push_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.sc_track_turns_host.argtypes = [vp, ctypes.POINTER(Particles), ctypes.POINTER(Beam), vp, ctypes.c_int,
+                                      ctypes.c_int, dp]
+    L.sc_batch_track_turns_host.argtypes = [vp, ctypes.POINTER(Bunch), ctypes.c_int, dp]
     L.sc_get_kick_push_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
@@ -325,27 +328,41 @@ def grid_write_charge(grid: Grid, Q, n_particles: int):
     _check(load().sc_grid_write_charge(grid.handle, Q.ctypes.data, int(n_particles)))
 
 
-def track_turns_host(grid: Grid, host_state, b: dict, lattice, n_turns: int, device_state=None, stream=None):
-    """Track a bunch held in host memory: copy the six arrays to the device,
-    run sc_track_turns, copy them back (in place).  `host_state` values are
-    numpy float64 arrays (pinned torch CPU tensors also accepted);
-    `device_state` may hold preallocated CUDA tensors to reuse."""
-    import torch
-
+def host_particles(state) -> Particles:
+    """sc_particles from a dict of six host float64 arrays of equal length:
+    contiguous writable numpy arrays or CPU torch tensors (pinned memory copies
+    fastest)."""
     keys = ("x", "px", "y", "py", "sigma", "psigma")
-    if device_state is None:
-        device_state = {k: torch.empty(len(host_state[k]), dtype=torch.float64, device="cuda") for k in keys}
+    ptrs, n = [], None
     for k in keys:
-        src = host_state[k]
-        src = torch.from_numpy(src) if isinstance(src, np.ndarray) else src
-        device_state[k].copy_(src, non_blocking=True)
-    track_turns(grid, device_state, b, lattice, n_turns)
-    for k in keys:
-        dst = host_state[k]
-        dst = torch.from_numpy(dst) if isinstance(dst, np.ndarray) else dst
-        dst.copy_(device_state[k], non_blocking=True)
-    torch.cuda.current_stream().synchronize()
-    return host_state
+        a = state[k]
+        if isinstance(a, np.ndarray):
+            if a.dtype != np.float64 or not a.flags.c_contiguous or not a.flags.writeable:
+                raise ValueError("host particle arrays must be contiguous writable float64")
+            ptrs.append(a.ctypes.data)
+            m = a.size
+        else:
+            if a.is_cuda or a.element_size() != 8 or not a.dtype.is_floating_point or not a.is_contiguous():
+                raise ValueError("host particle tensors must be contiguous CPU float64")
+            ptrs.append(a.data_ptr())
+            m = a.numel()
+        if n is not None and m != n:
+            raise ValueError("particle arrays differ in length")
+        n = m
+    return Particles(*ptrs, n)
+
+
+def track_turns_host(grid: Grid, host_state, b: dict, lattice, n_turns: int, diag: bool = False):
+    """sc_track_turns_host: track a bunch held in host memory (the library
+    copies it to its own device buffers and back); host_state is updated in
+    place.  diag -> [n_turns, 14] moments as in track_turns."""
+    p = host_particles(host_state)
+    bb = beam(b)
+    ptr, n, keep = _elements(lattice)
+    out = np.zeros((n_turns, 14)) if diag else None
+    _check(load().sc_track_turns_host(grid.handle, ctypes.byref(p), ctypes.byref(bb), ptr, n, int(n_turns),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if diag else None))
+    return out
 
 
 # ---------------------------------------------------------------- batches of bunches
@@ -399,26 +416,22 @@ def batch_track_turns(batch: Batch, states, beams, lattices, n_turns: int, diag:
     return out
 
 
-def batch_track_turns_host(batch: Batch, host_states, beams, lattices, n_turns: int, device_states=None):
-    """Track bunches held in host memory: copy each bunch's six arrays to the
-    device, run sc_batch_track_turns, copy them back (in place)."""
-    import torch
-
-    keys = ("x", "px", "y", "py", "sigma", "psigma")
-    if device_states is None:
-        device_states = [{k: torch.empty(len(h[k]), dtype=torch.float64, device="cuda") for k in keys}
-                         for h in host_states]
-    for h, d in zip(host_states, device_states):
-        for k in keys:
-            src = torch.from_numpy(h[k]) if isinstance(h[k], np.ndarray) else h[k]
-            d[k].copy_(src, non_blocking=True)
-    batch_track_turns(batch, device_states, beams, lattices, n_turns)
-    for h, d in zip(host_states, device_states):
-        for k in keys:
-            dst = torch.from_numpy(h[k]) if isinstance(h[k], np.ndarray) else h[k]
-            dst.copy_(d[k], non_blocking=True)
-    torch.cuda.current_stream().synchronize()
-    return host_states
+def batch_track_turns_host(batch: Batch, host_states, beams, lattices, n_turns: int, diag: bool = False):
+    """sc_batch_track_turns_host: bunches held in host memory (numpy arrays or
+    CPU torch tensors, updated in place); diag -> [n_turns, n_bunches, 14]."""
+    nb = len(batch)
+    if not (len(host_states) == len(beams) == len(lattices) == nb):
+        raise ValueError("one state, beam and lattice per bunch")
+    keep = []
+    arr = (Bunch * nb)()
+    for b in range(nb):
+        ptr, n, k = _elements(lattices[b])
+        keep.append(k)
+        arr[b] = Bunch(host_particles(host_states[b]), beam(beams[b]), ptr, n)
+    out = np.zeros((n_turns, nb, 14)) if diag else None
+    _check(load().sc_batch_track_turns_host(batch.handle, arr, int(n_turns),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if diag else None))
+    return out
 
 
 def batch_read(batch: Batch, b: int):

@@ -156,3 +156,27 @@ def test_batch_c4_full_size_sampled():
         scale = np.sqrt(np.mean(ref[k] ** 2))
         d = got[k] - ref[k]
         assert np.sqrt(np.mean(d * d)) < 1e-5 * scale, k
+
+
+def test_batch_host_buffers_equal_device_buffers():
+    """sc_batch_track_turns_host (host arrays, copies inside the library) gives
+    the bits of sc_batch_track_turns on device arrays; an empty bunch included."""
+    bunches = mixed_bunches()
+    bunches[4] = (synth.gaussian_bunch(0, 1, 1e-3, 1e-3, 1e-4, 1e-4),) + bunches[4][1:]
+    grids = [g for _, _, g, _ in bunches]
+    beams = [b for _, b, _, _ in bunches]
+    lats = [l for _, _, _, l in bunches]
+    B1 = sc.create_batch(grids, precision="tf32x3")
+    sc.batch_set_solver_tiling(B1, FIXED_TILING)
+    dev = [to_gpu(p) for p, _, _, _ in bunches]
+    d1 = sc.batch_track_turns(B1, dev, beams, lats, 2, diag=True)
+    B2 = sc.create_batch(grids, precision="tf32x3")
+    sc.batch_set_solver_tiling(B2, FIXED_TILING)
+    host = [{k: p[k].copy() for k in KEYS} for p, _, _, _ in bunches]
+    d2 = sc.batch_track_turns_host(B2, host, beams, lats, 1, diag=True)
+    d3 = sc.batch_track_turns_host(B2, host, beams, lats, 1, diag=True)  # device copies and plan reused
+    for i in range(len(bunches)):
+        got = to_host(dev[i])
+        for k in KEYS:
+            assert np.array_equal(host[i][k], got[k]), (i, k)
+    assert np.array_equal(d1[0], d2[0], equal_nan=True) and np.array_equal(d1[1], d3[0], equal_nan=True)

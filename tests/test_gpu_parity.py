@@ -387,6 +387,26 @@ def test_quad_coefficient_cache_bit_identical():
         assert np.array_equal(st[k].cpu().numpy(), st2[k].cpu().numpy()), k
 
 
+def test_track_host_buffers_equal_device_buffers():
+    """sc_track_turns_host (host numpy arrays, copies inside the library) gives
+    the bits of sc_track_turns on device arrays; repeated calls reuse the
+    library's device copies and captured turn."""
+    parts, b, grid, lat = synth.workload("c1", n=7001)
+    g = sc.create_grid(*grid)
+    st = to_gpu(parts)
+    d1 = sc.track_turns(g, st, b, lat, 3, diag=True)
+    g2 = sc.create_grid(*grid)
+    host = {k: parts[k].copy() for k in KEYS}
+    d2 = sc.track_turns_host(g2, host, b, lat, 2, diag=True)
+    d3 = sc.track_turns_host(g2, host, b, lat, 1, diag=True)
+    got = to_host(st)
+    for k in KEYS:
+        assert np.array_equal(host[k], got[k]), k
+    assert np.array_equal(d1[:2], d2) and np.array_equal(d1[2:], d3)
+    with pytest.raises(ValueError):
+        sc.track_turns_host(g2, {k: v.astype(np.float32) for k, v in host.items()}, b, lat, 1)
+
+
 def test_track_without_space_charge_markers():
     parts, b, grid, lat = synth.workload("c1", n=3000)
     lat2 = lat[lat["type"] != synth.MARK]

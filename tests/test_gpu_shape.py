@@ -42,8 +42,7 @@ def test_every_shape_bit_identical(precision):
     tuned = run(parts, b, grid, lat, 2, precision)
     th, tr, us = tuned[3]
     assert us > 0 and th in (384, 512, 640, 768) and tr in (0, 1)
-    top = 768 if precision == "tf32x3" else 640
-    for shape in [(128, 0), (384, 1), (top, 0), (top, 1)]:
+    for shape in [(128, 0), (384, 1), (640, 0), (768, 0), (768, 1)]:
         got = run(parts, b, grid, lat, 2, precision, shape)
         assert got[3][:2] == shape and got[3][2] == 0.0  # fixed: not timed
         assert_same(got, tuned)
@@ -76,7 +75,7 @@ def test_sliced_grid_shapes():
 def test_small_bunch_takes_default_shape():
     parts, b, grid, lat = synth.workload("c2", n=5000)
     got = run(parts, b, grid, lat, 1, "fp64")
-    assert got[3] == (640, 0, 0.0)
+    assert got[3] == (768, 0, 0.0)
     got = run(parts, b, grid, lat, 1, "tf32x3")
     assert got[3] == (768, 1, 0.0)
 
@@ -85,7 +84,7 @@ def test_shape_arguments():
     g = sc.create_grid(16, 16, -1.0, 1.0, -1.0, 1.0)
     with pytest.raises(sc.ScError):
         sc.get_kick_push_shape(g)  # nothing captured yet
-    for th, tr in [(48, -1), (-32, -1), (768, -1), (1024, 0), (256, 2), (256, -2)]:
+    for th, tr in [(48, -1), (-32, -1), (800, -1), (1024, 0), (256, 2), (256, -2)]:
         with pytest.raises(sc.ScError):
             sc.set_kick_push_shape(g, th, tr)
     sc.set_kick_push_shape(g, 640, 0)
