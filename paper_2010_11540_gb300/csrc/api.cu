@@ -201,6 +201,52 @@ sc_status tune_shape(sc_grid* g, TrackPlan* T, const sc_particles* p, Head&& hea
 
 }  // namespace
 
+sc_status copy_spread(CopyStreams** csp, cudaStream_t s, cudaMemcpyKind kind, const std::vector<CopyJob>& jobs) {
+  if (!*csp) {
+    CopyStreams* cs = new (std::nothrow) CopyStreams();
+    if (!cs) return set_error(SC_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaEventCreateWithFlags(&cs->fork, cudaEventDisableTiming);
+    for (int k = 0; k < CopyStreams::kStreams && e == cudaSuccess; ++k) {
+      e = cudaStreamCreateWithFlags(&cs->s[k], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cs->join[k], cudaEventDisableTiming);
+    }
+    if (e != cudaSuccess) {
+      copy_streams_destroy(cs);
+      return cuda_error(e, "copy streams");
+    }
+    *csp = cs;
+  }
+  CopyStreams* cs = *csp;
+  constexpr size_t kChunk = size_t(8) << 20;
+  SC_CUDA(cudaEventRecord(cs->fork, s));
+  for (int k = 0; k < CopyStreams::kStreams; ++k) SC_CUDA(cudaStreamWaitEvent(cs->s[k], cs->fork, 0));
+  int next = 0;
+  for (const CopyJob& j : jobs)
+    for (size_t o = 0; o < j.bytes; o += kChunk) {
+      const size_t b = j.bytes - o < kChunk ? j.bytes - o : kChunk;
+      SC_CUDA(cudaMemcpyAsync((char*)j.dst + o, (const char*)j.src + o, b, kind, cs->s[next]));
+      next = (next + 1) % CopyStreams::kStreams;
+    }
+  for (int k = 0; k < CopyStreams::kStreams; ++k) {
+    SC_CUDA(cudaEventRecord(cs->join[k], cs->s[k]));
+    SC_CUDA(cudaStreamWaitEvent(s, cs->join[k], 0));
+  }
+  return SC_OK;
+}
+
+void copy_streams_destroy(CopyStreams* cs) {
+  if (!cs) return;
+  for (int k = 0; k < CopyStreams::kStreams; ++k) {
+    if (cs->s[k]) {
+      cudaStreamSynchronize(cs->s[k]);
+      cudaStreamDestroy(cs->s[k]);
+    }
+    if (cs->join[k]) cudaEventDestroy(cs->join[k]);
+  }
+  if (cs->fork) cudaEventDestroy(cs->fork);
+  delete cs;
+}
+
 sc_status check_particles(const sc_particles* p) {
   if (!p) return set_error(SC_ERR_ARG, "particles is NULL");
   if (p->n < 0) return set_error(SC_ERR_ARG, "negative particle count");
@@ -439,6 +485,7 @@ sc_status sc_destroy_grid(sc_grid* g) {
   cudaFree(g->Q);
   cudaFree(g->E);
   cudaFree(g->host_stage);
+  copy_streams_destroy(g->copies);
   cudaFree(g->n_out);
   cudaFree(g->stack_scale);
   cudaFree(g->el_stage);
@@ -643,11 +690,14 @@ sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_bea
   sc_particles dev = {g->host_stage, g->host_stage + cap, g->host_stage + 2 * cap, g->host_stage + 3 * cap,
                       g->host_stage + 4 * cap, g->host_stage + 5 * cap, n};
   double* dst[6] = {dev.x, dev.px, dev.y, dev.py, dev.sigma, dev.psigma};
-  for (int a = 0; a < 6; ++a)
-    SC_CUDA(cudaMemcpyAsync(dst[a], src[a], (size_t)n * 8, cudaMemcpyHostToDevice, g->stream));
+  std::vector<CopyJob> in(6), out(6);
+  for (int a = 0; a < 6; ++a) {
+    in[a] = CopyJob{dst[a], src[a], (size_t)n * 8};
+    out[a] = CopyJob{src[a], dst[a], (size_t)n * 8};
+  }
+  if ((st = copy_spread(&g->copies, g->stream, cudaMemcpyHostToDevice, in))) return st;
   if ((st = sc_track_turns(g, &dev, b, lattice, n_elems, n_turns, diag))) return st;
-  for (int a = 0; a < 6; ++a)
-    SC_CUDA(cudaMemcpyAsync(src[a], dst[a], (size_t)n * 8, cudaMemcpyDeviceToHost, g->stream));
+  if ((st = copy_spread(&g->copies, g->stream, cudaMemcpyDeviceToHost, out))) return st;
   SC_CUDA(cudaStreamSynchronize(g->stream));
   return SC_OK;
 }

@@ -95,6 +95,7 @@ struct sc_batch {
   int64_t trace_kicks = 0;
   double* host_stage = nullptr;  // device copies for sc_batch_track_turns_host: bunch after bunch, [6][n_b] each
   int64_t host_stage_cap = 0;    // particles
+  sc::CopyStreams* copies = nullptr;
 };
 
 using namespace sc;
@@ -234,6 +235,7 @@ sc_status sc_destroy_batch(sc_batch* B) {
   for (cudaEvent_t ev : B->join_ev) cudaEventDestroy(ev);
   if (B->fork_ev) cudaEventDestroy(B->fork_ev);
   cudaFree(B->host_stage);
+  copy_streams_destroy(B->copies);
   if (B->own_stream) cudaStreamDestroy(B->stream);
   delete B;
   return SC_OK;
@@ -259,6 +261,7 @@ sc_status sc_batch_track_turns_host(sc_batch* B, const sc_bunch* bunches, int n_
     B->host_stage_cap = total;
   }
   std::vector<sc_bunch> dev(bunches, bunches + nb);
+  std::vector<CopyJob> in, out;
   size_t off = 0;
   for (int b = 0; b < nb; ++b) {
     const sc_particles& h = bunches[b].particles;
@@ -267,21 +270,16 @@ sc_status sc_batch_track_turns_host(sc_batch* B, const sc_bunch* bunches, int n_
     double* base = B->host_stage + 6 * off;
     d.x = base, d.px = base + n, d.y = base + 2 * n, d.py = base + 3 * n, d.sigma = base + 4 * n,
     d.psigma = base + 5 * n;
-    const double* src[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
-    for (int a = 0; a < 6 && n > 0; ++a)
-      SC_CUDA(cudaMemcpyAsync(base + a * n, src[a], n * 8, cudaMemcpyHostToDevice, B->stream));
+    double* host[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
+    for (int a = 0; a < 6 && n > 0; ++a) {
+      in.push_back(CopyJob{base + a * n, host[a], n * 8});
+      out.push_back(CopyJob{host[a], base + a * n, n * 8});
+    }
     off += n;
   }
+  if ((st = copy_spread(&B->copies, B->stream, cudaMemcpyHostToDevice, in))) return st;
   if ((st = sc_batch_track_turns(B, dev.data(), n_turns, diag))) return st;
-  for (int b = 0; b < nb; ++b) {
-    const sc_particles& h = bunches[b].particles;
-    const sc_particles& d = dev[b].particles;
-    const size_t n = (size_t)h.n;
-    double* dst[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
-    const double* src[6] = {d.x, d.px, d.y, d.py, d.sigma, d.psigma};
-    for (int a = 0; a < 6 && n > 0; ++a)
-      SC_CUDA(cudaMemcpyAsync(dst[a], src[a], n * 8, cudaMemcpyDeviceToHost, B->stream));
-  }
+  if ((st = copy_spread(&B->copies, B->stream, cudaMemcpyDeviceToHost, out))) return st;
   SC_CUDA(cudaStreamSynchronize(B->stream));
   return SC_OK;
 }

@@ -165,6 +165,21 @@ struct Tf32Plan;  // tensor-core DFT-GEMM form (solve_tf32.cu)
 
 struct TrackPlan;  // captured turn graph (api.cu)
 
+// Host<->device copies spread over a few streams (forked from and joined back
+// to the caller's stream), so that several copy engines share a large transfer.
+struct CopyJob {
+  void* dst;
+  const void* src;
+  size_t bytes;
+};
+struct CopyStreams {
+  static constexpr int kStreams = 4;
+  cudaStream_t s[kStreams] = {};
+  cudaEvent_t fork = nullptr, join[kStreams] = {};
+};
+sc_status copy_spread(CopyStreams** cs, cudaStream_t s, cudaMemcpyKind kind, const std::vector<CopyJob>& jobs);
+void copy_streams_destroy(CopyStreams* cs);
+
 }  // namespace sc
 
 struct sc_grid {
@@ -210,6 +225,7 @@ struct sc_grid {
   int el_stage_cap;
   double* host_stage;          // device copy of sc_track_turns_host's particles [6][cap]
   int64_t host_stage_cap;
+  sc::CopyStreams* copies;     // streams the host copies are spread over (created on first use)
 };
 
 namespace sc {
