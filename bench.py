@@ -93,8 +93,9 @@ def parse():
     ap.add_argument("--tiling", default=None,
                     help="force the split-TF32 solve's kernel variant per phase, e.g. 0,1,2,1 (default: tuned)")
     ap.add_argument("--kp-shape", default=None,
-                    help="force the kick/push block size and traversal (0 grid stride, 1 chunks), e.g. 768,1 "
-                         "(default: tuned; single-bunch configs)")
+                    help="force the kick/push launch shape (default: tuned): block size and traversal "
+                         "(0 grid stride, 1 chunks) for single-bunch configs, e.g. 768,1; block size and "
+                         "waves per launch for c4, e.g. 768,4")
     return ap.parse_args()
 
 
@@ -368,6 +369,8 @@ class BatchRun:
         B = sc.create_batch(self.grids, precision=precision, stream=self.stream)
         if precision == "tf32x3" and self.tiling:
             sc.batch_set_solver_tiling(B, self.tiling)
+        if self.kp_shape:
+            sc.batch_set_kick_push_shape(B, *self.kp_shape)
         return B, devs
 
     def tiling_desc(self, h):
@@ -382,7 +385,10 @@ class BatchRun:
         return out
 
     def shape_desc(self, h):
-        return None
+        from paper_2010_11540_gb300 import sc
+        t, w, us = sc.batch_get_kick_push_shape(h[0])
+        return {"threads": t, "waves": w, "trial_us_first_16_sc_steps": round(us, 1) or None,
+                "chosen": "fixed" if self.kp_shape else ("tuned" if us > 0 else "default")}
 
     def turns(self, h, n):
         from paper_2010_11540_gb300 import sc

@@ -349,6 +349,22 @@ sc_status sc_batch_read(sc_batch *B, int b, uint64_t *Q, double *Ex, double *Ey,
  * time is the batched launch covering every bunch; solve time covers every
  * grid class). */
 sc_status sc_batch_trace_enable(sc_batch *B, int enable);
+/* Launch shape of the batched kick/push: block size (a multiple of 32 up to
+ * 768 for split-TF32 batches, 640 for float64 fields) and the number of waves
+ * of resident blocks each launch's bunch chunks are cut into (more waves
+ * balance bunches of uneven size, fewer flush fewer deposit tiles).  Every
+ * shape gives bit-identical results.  Left free (0), the shape is chosen when
+ * a turn is captured for batches of 2^18 particles or more, by timing the
+ * candidates (512 or the largest block; 1, 2, 4 or 8 waves) over the turn's
+ * first 16 space-charge steps on scratch copies of the bunches (the bunches,
+ * charge grids and out-of-grid counters are left as they were); else 4 waves
+ * of the largest block.  sc_batch_set_kick_push_shape fixes either part (the
+ * next turn re-captures); sc_batch_get_kick_push_shape reads the captured
+ * turn's shape and the timed trial (0 when not timed).  Errors: SC_ERR_ARG
+ * (NULL batch, value out of range, or no captured turn). */
+sc_status sc_batch_set_kick_push_shape(sc_batch *B, int threads, int waves);
+sc_status sc_batch_get_kick_push_shape(sc_batch *B, int *threads, int *waves, double *trial_us);
+
 /* sc_get_solver_tiling of bunch b's grid class; sc_set_solver_tiling for
  * every grid class of the batch (split-TF32 batches). */
 sc_status sc_batch_get_solver_tiling(sc_batch *B, int b, int *choice, char *desc, size_t n);

@@ -716,7 +716,7 @@ sc_status sc_set_kick_push_shape(sc_grid* g, int threads, int traversal) {
 sc_status sc_get_kick_push_shape(sc_grid* g, int* threads, int* traversal, double* trial_us) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   const TrackPlan* T = g->track;
-  if (!T) return set_error(SC_ERR_ARG, "no captured turn on this grid");
+  if (!T || !T->exec) return set_error(SC_ERR_ARG, "no captured turn on this grid");
   if (threads) *threads = T->kp_threads > 0 ? T->kp_threads : kick_push_max_threads(g->field32);
   if (traversal) *traversal = g->nz > 1 ? 1 : T->kp_trav >= 0 ? T->kp_trav : (g->field32 ? 1 : 0);
   if (trial_us) *trial_us = T->kp_trial_us;
@@ -767,7 +767,6 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     g->track = nullptr;
     T = new (std::nothrow) TrackPlan();
     if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
-    T->key = key;
     T->diag = want_diag;
     g->track = T;
     // ---- segments: head (before the first marker) and one per marker -----------
@@ -949,6 +948,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       g->track = nullptr;
       return cuda_error(ce, "cudaGraphInstantiate");
     }
+    T->key = key;  // complete: a plan left half-built by an error is rebuilt by the next call
   }
 
   // ---- run -------------------------------------------------------------------------

@@ -15,9 +15,13 @@
 namespace sc {
 namespace {
 
-// Waves of resident blocks a batched launch is cut into: more waves balance
-// bunches of uneven size better, fewer flush fewer deposit tiles.
+// Waves of resident blocks a batched launch is cut into by default: more
+// waves balance bunches of uneven size better, fewer flush fewer deposit
+// tiles.  Batches of kShapeTuneMin particles or more time the candidates
+// (waves x block size) at capture instead.
 constexpr int kWaves = 4;
+constexpr int64_t kShapeTuneMin = int64_t(1) << 18;
+constexpr int kShapeTuneKicks = 16;
 
 struct BatchPlan {
   std::vector<unsigned char> key;
@@ -43,6 +47,9 @@ struct BatchPlan {
   int4* d_blocks = nullptr;
   int n_blocks = 0;
   int tile_cells = 0;
+  int kp_threads = 0;     // batched kick/push block size (0: the field type's largest)
+  int kp_waves = kWaves;  // waves of resident blocks per launch
+  double trial_us = 0.0;  // timed trial of the chosen shape (0: not timed)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double* partial = nullptr;
@@ -93,6 +100,12 @@ struct sc_batch {
   int trace = 0;
   double trace_kp_ms = 0.0, trace_solve_ms = 0.0;
   int64_t trace_kicks = 0;
+  int kp_threads_set = 0, kp_waves_set = 0;  // batched kick/push shape fixed by the caller (0: tuned)
+  // last tuned shape and what it was timed on, reused by re-captures that
+  // differ only in tracing or diagnostics
+  std::vector<unsigned char> tuned_key;
+  int tuned_threads = 0, tuned_waves = 0;
+  double tuned_us = 0.0;
   double* host_stage = nullptr;  // device copies for sc_batch_track_turns_host: bunch after bunch, [6][n_b] each
   int64_t host_stage_cap = 0;    // particles
   sc::CopyStreams* copies = nullptr;
@@ -126,9 +139,9 @@ void bunch_deposit(const sc_batch* B, int b, KPParams& P) {
 }
 
 // Blocks of one batched launch: the smallest chunk for which the bunches'
-// chunks fit kWaves waves of resident blocks; bunch by bunch, chunk by chunk.
-std::vector<int4> partition(const std::vector<int64_t>& n, int resident) {
-  const int target = kWaves * (resident > 0 ? resident : 1);
+// chunks fit `waves` waves of resident blocks; bunch by bunch, chunk by chunk.
+std::vector<int4> partition(const std::vector<int64_t>& n, int resident, int waves) {
+  const int target = waves * (resident > 0 ? resident : 1);
   int64_t total = 0;
   for (int64_t v : n) total += v;
   auto count = [&](int64_t chunk) {
@@ -150,6 +163,157 @@ std::vector<int4> partition(const std::vector<int64_t>& n, int resident) {
     for (int c = 0; c < k; ++c) blocks.push_back(make_int4((int)b, c, k, 0));
   }
   return blocks;
+}
+
+// Launch shape of the batched kick/push: block size and the waves of resident
+// blocks each launch is cut into.  Every shape gives bit-identical results
+// (integer charge, independent particles).  Each candidate (of the parts the
+// caller left free) is captured as a graph of the turn's first
+// kShapeTuneKicks space-charge steps (every class's solve, then the batched
+// kick/push) on scratch copies of the bunches and timed: one untimed launch,
+// then the best of three.  The classes' charge grids and out-of-grid counters
+// are put back afterwards; the fields and per-particle caches the trials
+// overwrite are rebuilt by every call before they are read.
+template <class Capture, class Blocks>
+sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, const std::vector<int64_t>& counts,
+                           const std::vector<KPParams>& descs, Capture&& capture, Blocks&& set_blocks) {
+  const int nb = B->n_bunches;
+  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  cudaStream_t S = B->stream;
+  const int kicks = T->n_kicks < kShapeTuneKicks ? T->n_kicks : kShapeTuneKicks;
+  int64_t total = 0;
+  for (int64_t v : counts) total += v;
+  // candidates
+  std::vector<int> ths, ws;
+  const int th_max = kick_push_batched_threads(f32);
+  for (int th : {512, th_max})
+    if ((B->kp_threads_set == 0 || th == B->kp_threads_set) &&
+        std::find(ths.begin(), ths.end(), th) == ths.end())
+      ths.push_back(th);
+  if (ths.empty()) ths.push_back(B->kp_threads_set);
+  for (int w : {1, 2, 4, 8})
+    if (B->kp_waves_set == 0 || w == B->kp_waves_set) ws.push_back(w);
+  if (ws.empty()) ws.push_back(B->kp_waves_set);
+  size_t max_blocks = 0;
+  for (int th : ths) {
+    T->kp_threads = th;
+    for (int w : ws) {
+      std::vector<int4> bl;
+      set_blocks(w, bl);
+      max_blocks = std::max(max_blocks, bl.size());
+    }
+  }
+  size_t saved_bytes = 0;
+  for (sc_grid* g : B->cls) saved_bytes += cells_of(g) * g->nstack * 8 + 8 * (size_t)g->nstack;
+  double* scratch = nullptr;
+  KPParams* d_sdescs = nullptr;
+  int4* d_blk = nullptr;
+  unsigned char* saved = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  sc_status st = SC_OK;
+  auto cu = [&st](cudaError_t e, const char* what) {
+    if (!st && e != cudaSuccess) st = cuda_error(e, what);
+    return st == SC_OK;
+  };
+  cu(cudaMalloc(&scratch, (size_t)(total > 0 ? total : 1) * 6 * sizeof(double)), "cudaMalloc(shape trial)");
+  cu(cudaMalloc(&d_sdescs, descs.size() * sizeof(KPParams)), "cudaMalloc(shape trial)");
+  cu(cudaMalloc(&d_blk, (max_blocks > 0 ? max_blocks : 1) * sizeof(int4)), "cudaMalloc(shape trial)");
+  cu(cudaMalloc(&saved, saved_bytes), "cudaMalloc(shape trial)");
+  cu(cudaEventCreate(&e0), "cudaEventCreate");
+  cu(cudaEventCreate(&e1), "cudaEventCreate");
+  // scratch copies of the bunches and descriptors that point at them
+  std::vector<KPParams> sd = descs;
+  size_t off = 0;
+  for (int b = 0; b < nb && st == SC_OK; ++b) {
+    const sc_particles& h = bunches[b].particles;
+    const size_t n = (size_t)h.n;
+    double* base = scratch + 6 * off;
+    const double* src[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
+    for (int a = 0; a < 6 && n > 0; ++a)
+      cu(cudaMemcpyAsync(base + a * n, src[a], n * 8, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
+    for (int L = 0; L < T->n_launches; ++L) {
+      KPParams& P = sd[(size_t)L * nb + b];
+      P.x = base, P.px = base + n, P.y = base + 2 * n, P.py = base + 3 * n, P.sg = base + 4 * n,
+      P.ps = base + 5 * n;
+    }
+    off += n;
+  }
+  cu(cudaMemcpyAsync(d_sdescs, sd.data(), sd.size() * sizeof(KPParams), cudaMemcpyHostToDevice, S),
+     "cudaMemcpyAsync");
+  auto grids = [&](bool save) {
+    size_t o = 0;
+    for (sc_grid* g : B->cls) {
+      const size_t qb = cells_of(g) * g->nstack * 8, ob = 8 * (size_t)g->nstack;
+      if (save) {
+        cu(cudaMemcpyAsync(saved + o, g->Q, qb, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
+        cu(cudaMemcpyAsync(saved + o + qb, g->n_out, ob, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
+      } else {
+        cu(cudaMemcpyAsync(g->Q, saved + o, qb, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
+        cu(cudaMemcpyAsync(g->n_out, saved + o + qb, ob, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
+      }
+      o += qb + ob;
+    }
+  };
+  auto clear_q = [&] {
+    for (sc_grid* g : B->cls) cu(cudaMemsetAsync(g->Q, 0, cells_of(g) * g->nstack * 8, S), "cudaMemsetAsync");
+  };
+  if (st == SC_OK) grids(true);
+  int best_th = ths[0], best_w = ws[0];
+  float best = 0.f;
+  bool first = true;
+  for (int th : ths) {
+    for (int w : ws) {
+      if (st != SC_OK) break;
+      T->kp_threads = th;
+      std::vector<int4> bl;
+      set_blocks(w, bl);
+      if (bl.empty()) continue;
+      cu(cudaMemcpyAsync(d_blk, bl.data(), bl.size() * sizeof(int4), cudaMemcpyHostToDevice, S), "cudaMemcpyAsync");
+      if (first) {
+        // the psc and quadrupole caches of the scratch bunches, and their charge at the first
+        // marker when the lattices open with one (else each trial opens with the head's deposit)
+        clear_q();
+        if (st == SC_OK)
+          st = launch_kick_push_batched(d_sdescs, d_blk, (int)bl.size(), T->tile_cells, f32, T->launch_cache[0] != 0,
+                                        T->launch_xe[0] != 0, S, th);
+        first = false;
+      }
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (st == SC_OK) st = capture(d_sdescs, d_blk, (int)bl.size(), kicks, false, &graph);
+      if (st == SC_OK) cu(cudaGraphInstantiate(&exec, graph, 0), "cudaGraphInstantiate(shape trial)");
+      if (graph) cudaGraphDestroy(graph);
+      float t_min = 0.f;
+      for (int r = 0; r < 4 && st == SC_OK; ++r) {
+        if (T->has_head) clear_q();
+        cu(cudaEventRecord(e0, S), "cudaEventRecord");
+        cu(cudaGraphLaunch(exec, S), "cudaGraphLaunch(shape trial)");
+        cu(cudaEventRecord(e1, S), "cudaEventRecord");
+        cu(cudaEventSynchronize(e1), "shape trial");
+        float ms = 0.f;
+        cu(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+        if (r > 0 && (t_min == 0.f || ms < t_min)) t_min = ms;
+      }
+      if (exec) cudaGraphExecDestroy(exec);
+      if (st == SC_OK && (best == 0.f || t_min < best)) {
+        best = t_min;
+        best_th = th;
+        best_w = w;
+      }
+    }
+  }
+  T->kp_threads = best_th;
+  T->kp_waves = best_w;
+  T->trial_us = 1e3 * (double)best;
+  if (saved) grids(false);
+  cu(cudaStreamSynchronize(S), "shape trial");
+  cudaFree(scratch);
+  cudaFree(d_sdescs);
+  cudaFree(d_blk);
+  cudaFree(saved);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
 }
 
 }  // namespace
@@ -241,6 +405,28 @@ sc_status sc_destroy_batch(sc_batch* B) {
   return SC_OK;
 }
 
+sc_status sc_batch_set_kick_push_shape(sc_batch* B, int threads, int waves) {
+  if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
+  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  if (threads < 0 || threads % 32 != 0 || threads > kick_push_batched_threads(f32))
+    return set_error(SC_ERR_ARG, "batched kick/push block size must be 0 or a multiple of 32 up to the maximum");
+  if (waves < 0 || waves > 64) return set_error(SC_ERR_ARG, "waves must be in 0..64");
+  B->kp_threads_set = threads;
+  B->kp_waves_set = waves;
+  return SC_OK;
+}
+
+sc_status sc_batch_get_kick_push_shape(sc_batch* B, int* threads, int* waves, double* trial_us) {
+  if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
+  const BatchPlan* T = B->plan;
+  if (!T || !T->exec) return set_error(SC_ERR_ARG, "no captured turn on this batch");
+  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  if (threads) *threads = T->kp_threads > 0 ? T->kp_threads : kick_push_batched_threads(f32);
+  if (waves) *waves = T->kp_waves;
+  if (trial_us) *trial_us = T->trial_us;
+  return SC_OK;
+}
+
 sc_status sc_batch_track_turns_host(sc_batch* B, const sc_bunch* bunches, int n_turns, double* diag) {
   if (!B || !bunches) return set_error(SC_ERR_ARG, "batch or bunches is NULL");
   if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
@@ -317,6 +503,9 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     put(&bunches[b].n_elems, sizeof(int));
     if (bunches[b].n_elems) put(bunches[b].lattice, (size_t)bunches[b].n_elems * sizeof(sc_element));
   }
+  put(&B->kp_threads_set, sizeof B->kp_threads_set);
+  put(&B->kp_waves_set, sizeof B->kp_waves_set);
+  const std::vector<unsigned char> shape_key = key;  // what the kick/push shape depends on
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
   put(&B->trace, sizeof B->trace);
@@ -329,7 +518,6 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     T = new (std::nothrow) BatchPlan();
     if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
     B->plan = T;
-    T->key = key;
     T->diag = want_diag;
     T->n_bunches = nb;
     const int n_marks = (int)marks[0].size();
@@ -389,12 +577,6 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     for (sc_grid* g : B->cls)
       if (deposit_uses_tile(g)) tile_cells = std::max(tile_cells, (int)cells_of(g));
     T->tile_cells = tile_cells;
-    const std::vector<int4> blocks = partition(counts, kick_push_batched_resident(tile_cells * 8, f32, true));
-    T->n_blocks = (int)blocks.size();
-    if (T->n_blocks > 0) {
-      SC_CUDA(cudaMalloc(&T->d_blocks, blocks.size() * sizeof(int4)));
-      SC_CUDA(cudaMemcpy(T->d_blocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    }
     // ---- descriptors: prologue, head, one per marker ------------------------------
     T->n_launches = 1 + (T->has_head ? 1 : 0) + n_marks;
     std::vector<KPParams> descs((size_t)T->n_launches * nb);
@@ -482,67 +664,111 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     }
     for (sc_grid* g : B->cls) g->n_particles = 1;  // normalisation comes from stack_scale
 
-    // ---- capture one turn of every bunch -----------------------------------------
+    // ---- the turn (or its first `kicks` space-charge steps) as a graph -----------
     cudaStream_t S = B->stream;
-    SC_CUDA(cudaStreamBeginCapture(S, cudaStreamCaptureModeThreadLocal));
-    sc_status cst = SC_OK;
-    for (int b = 0; !cst && want_diag && b < nb; ++b)
-      if (bunches[b].particles.n > 0)
-        cst = launch_moments(&bunches[b].particles, T->partial, moments_blocks(), T->d_base + b, T->d_turn + b,
-                             14 * nb, S);
-    int L = 1;
-    const bool any = T->n_blocks > 0;  // some bunch holds particles
-    if (T->has_head) {
-      if (!cst && any)
-        cst = launch_kick_push_batched(T->d_descs + (size_t)L * nb, T->d_blocks, T->n_blocks, T->tile_cells, f32,
-                                       T->launch_cache[L] != 0, T->launch_xe[L] != 0, S);
-      ++L;
-    }
-    for (int k = 0; !cst && k < n_marks; ++k, ++L) {
-      if (B->trace && cudaEventRecordWithFlags(T->ev[3 * k], S, cudaEventRecordExternal) != cudaSuccess)
-        cst = set_error(SC_ERR_CUDA, "event");
-      // every class: solve, then clear the charge for this marker's deposit; classes after the
-      // first on their side streams (forked after the previous kick/push, joined before the next)
-      if (!cst && B->cls.size() > 1 && cudaEventRecord(B->fork_ev, S) != cudaSuccess)
-        cst = set_error(SC_ERR_CUDA, "fork event");
-      for (size_t c = 1; !cst && c < B->cls.size(); ++c) {
-        sc_grid* g = B->cls[c];
-        if (cudaStreamWaitEvent(B->side[c - 1], B->fork_ev, 0) != cudaSuccess) {
-          cst = set_error(SC_ERR_CUDA, "fork wait");
-          break;
-        }
-        g->stream = B->side[c - 1];
-        cst = solve_dispatch(g, true);
-        g->stream = S;
-        if (!cst && cudaEventRecord(B->join_ev[c - 1], B->side[c - 1]) != cudaSuccess)
-          cst = set_error(SC_ERR_CUDA, "join event");
+    auto capture = [&](const KPParams* d_descs, const int4* d_blocks, int n_blocks, int kicks, bool full,
+                       cudaGraph_t* graph) -> sc_status {
+      SC_CUDA(cudaStreamBeginCapture(S, cudaStreamCaptureModeThreadLocal));
+      sc_status cst = SC_OK;
+      const bool diag_on = full && want_diag, trace_on = full && B->trace;
+      for (int b = 0; !cst && diag_on && b < nb; ++b)
+        if (bunches[b].particles.n > 0)
+          cst = launch_moments(&bunches[b].particles, T->partial, moments_blocks(), T->d_base + b, T->d_turn + b,
+                               14 * nb, S);
+      int L = 1;
+      const bool any = n_blocks > 0;  // some bunch holds particles
+      if (T->has_head) {
+        if (!cst && any)
+          cst = launch_kick_push_batched(d_descs + (size_t)L * nb, d_blocks, n_blocks, T->tile_cells, f32,
+                                         T->launch_cache[L] != 0, T->launch_xe[L] != 0, S, T->kp_threads);
+        ++L;
       }
-      if (!cst) cst = solve_dispatch(B->cls[0], true);
-      for (size_t c = 1; !cst && c < B->cls.size(); ++c)
-        if (cudaStreamWaitEvent(S, B->join_ev[c - 1], 0) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "join wait");
-      if (!cst && B->trace && cudaEventRecordWithFlags(T->ev[3 * k + 1], S, cudaEventRecordExternal) != cudaSuccess)
-        cst = set_error(SC_ERR_CUDA, "event");
-      if (!cst && any)
-        cst = launch_kick_push_batched(T->d_descs + (size_t)L * nb, T->d_blocks, T->n_blocks, T->tile_cells, f32,
-                                       T->launch_cache[L] != 0, T->launch_xe[L] != 0, S);
-      if (!cst && B->trace && cudaEventRecordWithFlags(T->ev[3 * k + 2], S, cudaEventRecordExternal) != cudaSuccess)
-        cst = set_error(SC_ERR_CUDA, "event");
+      for (int k = 0; !cst && k < kicks; ++k, ++L) {
+        if (trace_on && cudaEventRecordWithFlags(T->ev[3 * k], S, cudaEventRecordExternal) != cudaSuccess)
+          cst = set_error(SC_ERR_CUDA, "event");
+        // every class: solve, then clear the charge for this marker's deposit; classes after the
+        // first on their side streams (forked after the previous kick/push, joined before the next)
+        if (!cst && B->cls.size() > 1 && cudaEventRecord(B->fork_ev, S) != cudaSuccess)
+          cst = set_error(SC_ERR_CUDA, "fork event");
+        for (size_t c = 1; !cst && c < B->cls.size(); ++c) {
+          sc_grid* g = B->cls[c];
+          if (cudaStreamWaitEvent(B->side[c - 1], B->fork_ev, 0) != cudaSuccess) {
+            cst = set_error(SC_ERR_CUDA, "fork wait");
+            break;
+          }
+          g->stream = B->side[c - 1];
+          cst = solve_dispatch(g, true);
+          g->stream = S;
+          if (!cst && cudaEventRecord(B->join_ev[c - 1], B->side[c - 1]) != cudaSuccess)
+            cst = set_error(SC_ERR_CUDA, "join event");
+        }
+        if (!cst) cst = solve_dispatch(B->cls[0], true);
+        for (size_t c = 1; !cst && c < B->cls.size(); ++c)
+          if (cudaStreamWaitEvent(S, B->join_ev[c - 1], 0) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "join wait");
+        if (!cst && trace_on && cudaEventRecordWithFlags(T->ev[3 * k + 1], S, cudaEventRecordExternal) != cudaSuccess)
+          cst = set_error(SC_ERR_CUDA, "event");
+        if (!cst && any)
+          cst = launch_kick_push_batched(d_descs + (size_t)L * nb, d_blocks, n_blocks, T->tile_cells, f32,
+                                         T->launch_cache[L] != 0, T->launch_xe[L] != 0, S, T->kp_threads);
+        if (!cst && trace_on && cudaEventRecordWithFlags(T->ev[3 * k + 2], S, cudaEventRecordExternal) != cudaSuccess)
+          cst = set_error(SC_ERR_CUDA, "event");
+      }
+      cudaGraph_t gr = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(S, &gr);
+      if (!cst && ce != cudaSuccess) cst = cuda_error(ce, "cudaStreamEndCapture");
+      if (cst) {
+        if (gr) cudaGraphDestroy(gr);
+        return cst;
+      }
+      *graph = gr;
+      return SC_OK;
+    };
+    auto set_blocks = [&](int waves, std::vector<int4>& blocks) {
+      blocks = partition(counts, kick_push_batched_resident(T->tile_cells * 8, f32, true, T->kp_threads), waves);
+    };
+    auto fail = [&](sc_status e) {
+      destroy_batch_plan(T);
+      B->plan = nullptr;
+      return e;
+    };
+    // ---- launch shape of the batched kick/push (block size, waves) -----------------
+    int64_t total = 0;
+    for (int64_t v : counts) total += v;
+    T->kp_threads = B->kp_threads_set;
+    T->kp_waves = B->kp_waves_set > 0 ? B->kp_waves_set : kWaves;
+    const bool free_shape = B->kp_threads_set == 0 || B->kp_waves_set == 0;
+    if (n_marks > 0 && total >= kShapeTuneMin && free_shape) {
+      if (B->tuned_key == shape_key) {
+        T->kp_threads = B->tuned_threads;
+        T->kp_waves = B->tuned_waves;
+        T->trial_us = B->tuned_us;
+      } else {
+        const sc_status tst = tune_batch_shape(B, T, bunches, counts, descs, capture, set_blocks);
+        if (tst) return fail(tst);
+        B->tuned_key = shape_key;
+        B->tuned_threads = T->kp_threads;
+        B->tuned_waves = T->kp_waves;
+        B->tuned_us = T->trial_us;
+      }
     }
+    {
+      std::vector<int4> blocks;
+      set_blocks(T->kp_waves, blocks);
+      T->n_blocks = (int)blocks.size();
+      if (T->n_blocks > 0) {
+        cudaError_t e = cudaMalloc(&T->d_blocks, blocks.size() * sizeof(int4));
+        if (e == cudaSuccess)
+          e = cudaMemcpy(T->d_blocks, blocks.data(), blocks.size() * sizeof(int4), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(cuda_error(e, "block table"));
+      }
+    }
+    // ---- capture one turn of every bunch -----------------------------------------
     cudaGraph_t graph = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(S, &graph);
-    if (cst || ce != cudaSuccess) {
-      if (graph) cudaGraphDestroy(graph);
-      destroy_batch_plan(T);
-      B->plan = nullptr;
-      return cst ? cst : cuda_error(ce, "cudaStreamEndCapture");
-    }
+    if ((st = capture(T->d_descs, T->d_blocks, T->n_blocks, n_marks, true, &graph))) return fail(st);
     T->graph = graph;
-    ce = cudaGraphInstantiate(&T->exec, graph, 0);
-    if (ce != cudaSuccess) {
-      destroy_batch_plan(T);
-      B->plan = nullptr;
-      return cuda_error(ce, "cudaGraphInstantiate");
-    }
+    const cudaError_t ce = cudaGraphInstantiate(&T->exec, graph, 0);
+    if (ce != cudaSuccess) return fail(cuda_error(ce, "cudaGraphInstantiate"));
+    T->key = key;  // complete: a plan left half-built by an error is rebuilt by the next call
   }
 
   // ---- run -------------------------------------------------------------------------
@@ -565,7 +791,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     if (!T->has_head && T->n_kicks > 0)
       for (sc_grid* g : B->cls) SC_CUDA(cudaMemsetAsync(g->Q, 0, cells_of(g) * g->nstack * 8, S));
     if ((st = launch_kick_push_batched(T->d_descs, T->d_blocks, T->n_blocks, T->tile_cells, f32,
-                                       T->launch_cache[0] != 0, T->launch_xe[0] != 0, S)))
+                                       T->launch_cache[0] != 0, T->launch_xe[0] != 0, S, T->kp_threads)))
       return st;
   }
   for (int t = 0; t < n_turns; ++t) {

@@ -395,7 +395,8 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
 
 int kick_push_batched_threads(bool f32) { return f32 ? kpb_max_threads<true>() : kpb_max_threads<false>(); }
 
-int kick_push_batched_resident(int smem_bytes, bool f32, bool cache) {
+int kick_push_batched_resident(int smem_bytes, bool f32, bool cache, int threads) {
+  if (threads <= 0) threads = kick_push_batched_threads(f32);
   int dev = 0, sms = 0, per = 1 << 30;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -405,18 +406,18 @@ int kick_push_batched_resident(int smem_bytes, bool f32, bool cache) {
   }
   for (int xe = 0; xe < 2; ++xe) {
     int p = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kp_batched(cache, f32, xe), kick_push_batched_threads(f32),
-                                                  smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, kp_batched(cache, f32, xe), threads, smem_bytes);
     per = p < per ? p : per;
   }
   return sms * (per < 1 ? 1 : per);
 }
 
 sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
-                                   bool cache, bool xe, cudaStream_t s) {
+                                   bool cache, bool xe, cudaStream_t s, int threads) {
   // (the shared-memory limit was raised by kick_push_batched_resident, called before any launch)
-  SC_CUDA(launch_pdl(kp_batched(cache, f32, xe), dim3(n_blocks), dim3(kick_push_batched_threads(f32)),
-                     (size_t)tile_cells * 8, s, descs, blocks, tile_cells));
+  if (threads <= 0) threads = kick_push_batched_threads(f32);
+  SC_CUDA(launch_pdl(kp_batched(cache, f32, xe), dim3(n_blocks), dim3(threads), (size_t)tile_cells * 8, s, descs,
+                     blocks, tile_cells));
   return SC_OK;
 }
 

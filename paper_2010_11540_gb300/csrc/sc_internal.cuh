@@ -242,9 +242,12 @@ int kick_push_max_threads(bool f32);
 int kick_push_blocks_at(int smem_bytes, bool tile, bool f32, int threads);
 // Batched form: descs[bunch] per bunch, blocks[b] = (bunch, chunk, chunks of that bunch, 0) per block;
 // deposits of grids with at most tile_cells nodes go through the shared-memory tile.
+// threads: block size (0: the field type's largest, kick_push_batched_threads)
 sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
-                                   bool cache, bool xe, cudaStream_t s);
-int kick_push_batched_resident(int smem_bytes, bool f32, bool cache);  // resident blocks on the device
+                                   bool cache, bool xe, cudaStream_t s, int threads = 0);
+int kick_push_batched_threads(bool f32);
+// resident blocks on the device at this block size (0: the largest)
+int kick_push_batched_resident(int smem_bytes, bool f32, bool cache, int threads = 0);
 bool deposit_uses_tile(const sc_grid* g);
 int deposit_blocks_for(int smem_bytes, bool tile);
 int kick_push_blocks_for(int smem_bytes, bool tile);

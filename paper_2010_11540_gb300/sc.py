@@ -30,7 +30,8 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
            "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
-           "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_last_error")
+           "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_batch_set_kick_push_shape",
+           "sc_batch_get_kick_push_shape", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -108,6 +109,8 @@ def load():
     L.sc_track_turns_host.argtypes = [vp, ctypes.POINTER(Particles), ctypes.POINTER(Beam), vp, ctypes.c_int,
                                       ctypes.c_int, dp]
     L.sc_batch_track_turns_host.argtypes = [vp, ctypes.POINTER(Bunch), ctypes.c_int, dp]
+    L.sc_batch_set_kick_push_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.sc_batch_get_kick_push_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.sc_get_kick_push_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
@@ -432,6 +435,18 @@ def batch_track_turns_host(batch: Batch, host_states, beams, lattices, n_turns: 
     _check(load().sc_batch_track_turns_host(batch.handle, arr, int(n_turns),
                                             out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if diag else None))
     return out
+
+
+def batch_set_kick_push_shape(batch: Batch, threads: int = 0, waves: int = 0):
+    """Fix the batched kick/push block size and waves per launch (0: chosen at capture)."""
+    _check(load().sc_batch_set_kick_push_shape(batch.handle, int(threads), int(waves)))
+
+
+def batch_get_kick_push_shape(batch: Batch):
+    """-> (threads, waves, trial_us) of the batch's captured turn."""
+    t, w, us = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
+    _check(load().sc_batch_get_kick_push_shape(batch.handle, ctypes.byref(t), ctypes.byref(w), ctypes.byref(us)))
+    return int(t.value), int(w.value), us.value
 
 
 def batch_read(batch: Batch, b: int):

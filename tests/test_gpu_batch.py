@@ -180,3 +180,47 @@ def test_batch_host_buffers_equal_device_buffers():
         for k in KEYS:
             assert np.array_equal(host[i][k], got[k]), (i, k)
     assert np.array_equal(d1[0], d2[0], equal_nan=True) and np.array_equal(d1[1], d3[0], equal_nan=True)
+
+
+def test_batch_kick_push_shapes_bit_identical():
+    """The batched kick/push's block size and waves per launch change only the
+    time: the shape timed at capture (a batch above 2^18 particles), and fixed
+    shapes, track to the same bits; the tuner leaves the bunches as they were."""
+    bunches = synth.c4_bunches(seed=99, n_bunches=8, n_min=2e4, n_max=1.2e5)
+    assert sum(len(p["x"]) for p, _, _, _ in bunches) >= 1 << 18
+    grids = [g for _, _, g, _ in bunches]
+    beams = [b for _, b, _, _ in bunches]
+    lats = [l for _, _, _, l in bunches]
+
+    def run(shape):
+        B = sc.create_batch(grids, precision="tf32x3")
+        sc.batch_set_solver_tiling(B, FIXED_TILING)
+        if shape is not None:
+            sc.batch_set_kick_push_shape(B, *shape)
+        st = [to_gpu(p) for p, _, _, _ in bunches]
+        sc.batch_track_turns(B, st, beams, lats, 2)
+        return [to_host(x) for x in st], sc.batch_get_kick_push_shape(B)
+
+    tuned, (th, w, us) = run(None)
+    assert us > 0 and th in (512, 768) and w in (1, 2, 4, 8)
+    for shape in [(768, 4), (512, 1), (256, 8), (768, 2)]:
+        got, sh = run(shape)
+        assert sh[:2] == shape and sh[2] == 0.0
+        for i in range(len(bunches)):
+            for k in KEYS:
+                assert np.array_equal(got[i][k], tuned[i][k]), (shape, i, k)
+
+
+def test_batch_shape_arguments():
+    bunches = mixed_bunches()[:2]
+    B = sc.create_batch([g for _, _, g, _ in bunches], precision="tf32x3")
+    with pytest.raises(sc.ScError):
+        sc.batch_get_kick_push_shape(B)  # nothing captured yet
+    for th, w in [(48, 0), (800, 0), (-32, 0), (256, 65), (256, -1)]:
+        with pytest.raises(sc.ScError):
+            sc.batch_set_kick_push_shape(B, th, w)
+    sc.batch_set_kick_push_shape(B, 768, 3)
+    B64 = sc.create_batch([g for _, _, g, _ in bunches], precision="fp64")
+    with pytest.raises(sc.ScError):
+        sc.batch_set_kick_push_shape(B64, 768, 0)  # the float64 batched kernel stops at 640
+    sc.batch_set_kick_push_shape(B64, 640, 0)
