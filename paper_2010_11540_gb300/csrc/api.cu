@@ -112,8 +112,13 @@ sc_status tune_shape(sc_grid* g, TrackPlan* T, const sc_particles* p, Head&& hea
     if (!st && e != cudaSuccess) st = cuda_error(e, what);
     return st == SC_OK;
   };
-  cu(cudaMalloc(&scratch, (size_t)n * 6 * sizeof(double)), "cudaMalloc(shape trial)");
-  cu(cudaMalloc(&saved, qbytes + obytes), "cudaMalloc(shape trial)");
+  // no room for the scratch copy: keep the default shape rather than fail the call
+  if (cudaMalloc(&scratch, (size_t)n * 6 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&saved, qbytes + obytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(scratch);
+    return SC_OK;
+  }
   cu(cudaEventCreate(&e0), "cudaEventCreate");
   cu(cudaEventCreate(&e1), "cudaEventCreate");
   sc_particles q = {scratch, scratch + n, scratch + 2 * n, scratch + 3 * n, scratch + 4 * n, scratch + 5 * n, n};

@@ -215,10 +215,19 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
     if (!st && e != cudaSuccess) st = cuda_error(e, what);
     return st == SC_OK;
   };
-  cu(cudaMalloc(&scratch, (size_t)(total > 0 ? total : 1) * 6 * sizeof(double)), "cudaMalloc(shape trial)");
-  cu(cudaMalloc(&d_sdescs, descs.size() * sizeof(KPParams)), "cudaMalloc(shape trial)");
-  cu(cudaMalloc(&d_blk, (max_blocks > 0 ? max_blocks : 1) * sizeof(int4)), "cudaMalloc(shape trial)");
-  cu(cudaMalloc(&saved, saved_bytes), "cudaMalloc(shape trial)");
+  // no room for the scratch copies: keep the default shape rather than fail the call
+  if (cudaMalloc(&scratch, (size_t)(total > 0 ? total : 1) * 6 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&d_sdescs, descs.size() * sizeof(KPParams)) != cudaSuccess ||
+      cudaMalloc(&d_blk, (max_blocks > 0 ? max_blocks : 1) * sizeof(int4)) != cudaSuccess ||
+      cudaMalloc(&saved, saved_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(scratch);
+    cudaFree(d_sdescs);
+    cudaFree(d_blk);
+    T->kp_threads = B->kp_threads_set;
+    T->kp_waves = B->kp_waves_set > 0 ? B->kp_waves_set : kWaves;
+    return SC_OK;
+  }
   cu(cudaEventCreate(&e0), "cudaEventCreate");
   cu(cudaEventCreate(&e1), "cudaEventCreate");
   // scratch copies of the bunches and descriptors that point at them
