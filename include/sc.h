@@ -278,6 +278,14 @@ sc_status sc_set_solver_tiling(sc_grid *g, const int *choice);
 sc_status sc_set_kick_push_shape(sc_grid *g, int threads, int traversal);
 sc_status sc_get_kick_push_shape(sc_grid *g, int *threads, int *traversal, double *trial_us);
 
+/* Work of one sc_solve on this grid (all stacked grids), for rooflines:
+ * tensor_flops = the split-TF32 DFT GEMMs' 2 M N K per phase times the three
+ * split products (0 for the float64 forms); fft_flops = the FFT-equivalent
+ * count 2 x 5 N log2 N of a forward and an inverse complex 2-D transform of
+ * N points (the zero-padded 2nx x 2ny grid, or the pipe's odd extension
+ * 2(nx-1) x 2(ny-1)) per stacked grid.  Errors: SC_ERR_ARG (NULL grid). */
+sc_status sc_get_solver_work(sc_grid *g, double *tensor_flops, double *fft_flops);
+
 /* Failure-detection test hook (no counterpart in the paper).  The tensor-core
  * solve's waits on its copy and MMA barriers are bounded (~2 s of SM clock);
  * when one runs out the kernel records an error word, lets its issued work

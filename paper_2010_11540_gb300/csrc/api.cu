@@ -707,6 +707,17 @@ sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_bea
   return SC_OK;
 }
 
+sc_status sc_get_solver_work(sc_grid* g, double* tensor_flops, double* fft_flops) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  const bool pipe = g->precision == SC_SOLVE_PIPE_FP64 || g->precision == SC_SOLVE_PIPE_TF32X3;
+  // transform lengths: the zero-padded 2nx x 2ny grid (open), the odd extension 2(nx-1) x 2(ny-1) (pipe)
+  const double lx = pipe ? 2.0 * (g->nx - 1) : 2.0 * g->nx, ly = pipe ? 2.0 * (g->ny - 1) : 2.0 * g->ny;
+  const double n = lx * ly;
+  if (fft_flops) *fft_flops = 2.0 * 5.0 * n * std::log2(n) * g->nstack;
+  if (tensor_flops) *tensor_flops = g->tf32 ? tf32_tensor_flops(g) : 0.0;
+  return SC_OK;
+}
+
 sc_status sc_set_kick_push_shape(sc_grid* g, int threads, int traversal) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   const int max = kick_push_max_threads(g->field32);

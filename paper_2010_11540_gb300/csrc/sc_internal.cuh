@@ -261,6 +261,7 @@ sc_status pipe_create(sc_grid* g);
 void pipe_destroy(sc_grid* g);
 sc_status pipe_solve(sc_grid* g, bool zero_q);
 // solve_tf32.cu
+double tf32_tensor_flops(const sc_grid* g);  // tensor-core flops of one solve (all stacked grids)
 sc_status tf32_create(sc_grid* g);
 void tf32_destroy(sc_grid* g);
 sc_status tf32_solve(sc_grid* g, bool zero_q);

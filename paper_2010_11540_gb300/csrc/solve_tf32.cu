@@ -1205,6 +1205,15 @@ int tf32_error(sc_grid* g) {
   return e;
 }
 
+double tf32_tensor_flops(const sc_grid* g) {
+  // 2 M N K per GEMM (the chosen runs' logical sizes), three split products each
+  const Tf32Plan* T = g->tf32;
+  double f = 0.0;
+  for (const PhaseRun& r : T->run)
+    f += 2.0 * (double)r.a.m_tiles * TM * (double)r.a.n_total * (double)r.a.k_chunks * KC * 3.0;
+  return f;
+}
+
 int tf32_variant_count(int ph) { return (int)variants(ph).size(); }
 
 sc_status tf32_test_bounded_waits(sc_grid* g, int enable) {

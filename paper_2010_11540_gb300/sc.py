@@ -31,7 +31,7 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
            "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
            "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_batch_set_kick_push_shape",
-           "sc_batch_get_kick_push_shape", "sc_last_error")
+           "sc_batch_get_kick_push_shape", "sc_get_solver_work", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -106,6 +106,7 @@ def load():
     L.sc_set_gather.argtypes = [vp, ctypes.c_int]
     L.sc_test_bounded_waits.argtypes = [vp, ctypes.c_int]
     L.sc_set_kick_push_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.sc_get_solver_work.argtypes = [vp, dp, dp]
     L.sc_track_turns_host.argtypes = [vp, ctypes.POINTER(Particles), ctypes.POINTER(Beam), vp, ctypes.c_int,
                                       ctypes.c_int, dp]
     L.sc_batch_track_turns_host.argtypes = [vp, ctypes.POINTER(Bunch), ctypes.c_int, dp]
@@ -293,6 +294,13 @@ def get_solver_tiling(grid: Grid):
 def set_solver_tiling(grid: Grid, choice):
     """Force the split-TF32 solve's kernel variant per phase (-1 keeps one)."""
     _check(load().sc_set_solver_tiling(grid.handle, (ctypes.c_int * 4)(*[int(v) for v in choice])))
+
+
+def solver_work(grid: Grid):
+    """-> (tensor-core flops, FFT-equivalent flops) of one solve on the grid."""
+    t, f = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().sc_get_solver_work(grid.handle, ctypes.byref(t), ctypes.byref(f)))
+    return t.value, f.value
 
 
 def set_kick_push_shape(grid: Grid, threads: int = 0, traversal: int = -1):

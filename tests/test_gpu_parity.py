@@ -853,3 +853,20 @@ def test_track_pipe_tf32_longitudinal_statistics(gather):
     d_lon = ref["psigma"] - ref0["psigma"]
     d_err = got["psigma"] - ref["psigma"]
     assert np.sqrt(np.mean(d_lon ** 2)) > 100 * np.sqrt(np.mean(d_err ** 2))
+
+
+def test_solver_work_counts():
+    """sc_get_solver_work: the FFT-equivalent count of the zero-padded 256²
+    transform pair is exact; the split-TF32 GEMMs' count covers the four DFT
+    phases (about 1.3e8 real flops, three split products), stacked grids
+    scale it; the float64 forms report no tensor work."""
+    ext = (-1.0, 1.0, -1.0, 1.0)
+    g64 = sc.create_grid(128, 128, *ext)
+    t, f = sc.solver_work(g64)
+    assert t == 0.0 and f == 2 * 5 * 256 * 256 * 16
+    g32 = sc.create_grid(128, 128, *ext, precision="tf32x3")
+    t32, f32 = sc.solver_work(g32)
+    assert f32 == f and 3 * 1.2e8 < t32 < 3 * 2.5e8
+    gs = sc.create_grid(128, 128, *ext, precision="tf32x3", slices=(4, -1.0, 1.0))
+    ts, fs = sc.solver_work(gs)
+    assert fs == 4 * f and abs(ts / t32 - 4) < 0.5
