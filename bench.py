@@ -311,6 +311,35 @@ class SingleRun:
     def close(self, h):
         h[0].close()
 
+    def cufft_reference(self, flush, reps=20):
+        """Context line: the open-boundary solve as the paper does it, with cuFFT
+        (through torch.fft, float64): forward real 2-D transform of the
+        zero-padded charge, times two field spectra, two inverse transforms;
+        median of `reps`, L2 flushed.  Not on the product path."""
+        import torch
+        if self.pipe or self.slices:
+            return None
+        nx, ny = self.grid[0], self.grid[1]
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        q = torch.zeros(2 * ny, 2 * nx, dtype=torch.float64, device="cuda")
+        q[:ny, :nx] = torch.rand(ny, nx, generator=gen, dtype=torch.float64, device="cuda")
+        gx = torch.randn(2 * ny, nx + 1, generator=gen, dtype=torch.complex128, device="cuda")
+        gy = torch.randn(2 * ny, nx + 1, generator=gen, dtype=torch.complex128, device="cuda")
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps + 3)]
+        with torch.cuda.stream(self.stream):
+            for i, (a, c) in enumerate(ev):
+                flush.zero_()
+                a.record(self.stream)
+                f = torch.fft.rfft2(q)
+                ex = torch.fft.irfft2(f * gx, s=q.shape)
+                ey = torch.fft.irfft2(f * gy, s=q.shape)
+                c.record(self.stream)
+            torch.cuda.synchronize()
+        del ex, ey
+        ms = sorted(a.elapsed_time(c) for a, c in ev[3:])[reps // 2]
+        return {"solve_us": ms * 1e3, "what": f"cuFFT (torch.fft, float64) rfft2 of the {2 * nx}x{2 * ny} "
+                                             "zero-padded charge, x2 spectra, 2 irfft2; context only"}
+
     def deposit_roofline(self, h, flush, atom_peak, atom_conflict_free, reps=20):
         """sc_deposit alone (the deposit kernel) on the workload's particles:
         4 shared-memory u64 atomic adds per particle inside the grid, against
@@ -550,6 +579,7 @@ def run_ours(args):
     atom_cf, atom_rand, fp64_probe = sc.probe_peaks(stream)
     roofline["peak_probe_fp64_tinst"] = fp64_probe / 1e12
     deposit = W.deposit_roofline(h, flush, atom_rand, atom_cf) if hasattr(W, "deposit_roofline") else None
+    cufft = W.cufft_reference(flush) if hasattr(W, "cufft_reference") else None
 
     # ---------------- end to end: host buffers through the public API
     pinned = W.pinned()
@@ -578,7 +608,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-            "roofline": roofline, "roofline_deposit": deposit, "roofline_solve": roofline_solve, "e2e": e2e,
+            "roofline": roofline, "roofline_deposit": deposit, "roofline_solve": roofline_solve,
+            "reference_cufft_solve": cufft, "e2e": e2e,
             "clocks": clk, "compare_form": compare,
             "gpu_launches": args.steps * n_kicks * (W.n_classes * solve_kernels + 1),
             "wall_s_timed": wall}
