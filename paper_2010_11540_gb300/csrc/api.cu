@@ -859,6 +859,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       P.psc_mode = 1;
       set_elements(P, lattice, nh, b, T->d_elems);
       with_qcache(P);
+      P.psc_skip = psc_skip_mask(lattice, nh, b, T->qfam.data(), (int)T->qfam.size());
       if (!marks.empty()) {
         // the turn's last solve cleared the charge (and the prologue did before the first turn)
         set_deposit(P, g);
@@ -879,6 +880,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       set_kick(P, g, K * (s[m] - prev), b->gamma0);
       set_elements(P, lattice + m + 1, end - m - 1, b, T->d_elems + m + 1);
       with_qcache(P);
+      P.psc_skip = psc_skip_mask(lattice + m + 1, end - m - 1, b, T->qfam.data(), (int)T->qfam.size());
       // the cell cache is valid at every marker: the previous launch deposited on this grid
       P.cell = T->cell;
       P.frac = T->frac;

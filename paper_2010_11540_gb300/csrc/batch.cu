@@ -630,6 +630,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         const int nh = mk.empty() ? u.n_elems : mk[0];
         set_elements(P, u.lattice, nh, bm, T->d_elems[b]);
         with_qcache(P);
+        P.psc_skip = psc_skip_mask(u.lattice, nh, bm, T->qfam[b].data(), (int)T->qfam[b].size());
         if (!mk.empty()) {
           bunch_deposit(B, b, P);
           P.cell = T->cell[b];
@@ -650,6 +651,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         bunch_kick(B, b, P, K * (s[m] - prev));
         set_elements(P, u.lattice + m + 1, end - m - 1, bm, T->d_elems[b] + m + 1);
         with_qcache(P);
+        P.psc_skip = psc_skip_mask(u.lattice + m + 1, end - m - 1, bm, T->qfam[b].data(), (int)T->qfam[b].size());
         P.cell = T->cell[b];
         P.frac = T->frac[b];
         P.fix = T->fix[b];

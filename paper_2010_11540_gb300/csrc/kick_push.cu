@@ -7,6 +7,7 @@
 // (kick_push_kernel) or every bunch of a batch (kick_push_batched).
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "cic.cuh"
 #include "maps.cuh"
@@ -194,9 +195,9 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
     if (psc_mode == 1 && !fresh) {
       k.opd2 = P.psc[p];
       k.opb = P.psc[n + p];
-      k.s1 = P.psc[2 * n + p];
-      k.r = P.psc[3 * n + p];
-      k.qi = P.psc[4 * n + p];
+      k.s1 = (P.psc_skip & 1) ? 0.0 : P.psc[2 * n + p];
+      k.r = (P.psc_skip & 1) ? 0.0 : P.psc[3 * n + p];
+      k.qi = (P.psc_skip & 2) ? 0.0 : P.psc[4 * n + p];
       k.opm = 1.0 - s.ps;
     } else {
       ps_const(k, s.ps, P.beta0_sq, fresh || P.has_quad != 0);
@@ -520,6 +521,19 @@ int quad_families(const DevElem* el, int n, DevElem* fam, int max) {
     }
   }
   return nf;
+}
+
+int psc_skip_mask(const sc_element* host, int n, const sc_beam* b, const DevElem* fam, int nf) {
+  std::vector<DevElem> d(n > 0 ? n : 1);
+  compile_elements(host, n, b, d.data());
+  tag_quad_families(d.data(), n, fam, nf);
+  bool thick = false, own = false;
+  for (int i = 0; i < n; ++i)
+    if (d[i].type == SC_QUAD && (d[i].flags & QF_KIND) != QF_ZERO) {
+      thick = true;
+      own = own || (d[i].flags >> QF_FAM_SHIFT) == 0;
+    }
+  return (own ? 0 : 1) | (thick ? 0 : 2);
 }
 
 void tag_quad_families(DevElem* el, int n, const DevElem* fam, int nf) {

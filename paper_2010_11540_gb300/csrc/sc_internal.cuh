@@ -114,6 +114,10 @@ struct KPParams {
   double* qcache;
   const DevElem* qfam;  // the families' compiled elements (device)
   int qfam_n;
+  // psc arrays the segment does not read (psc_mode 1): bit 0 sqrt(1-ps) and
+  // 1/sqrt(1-ps) (only quadrupoles computing their own matrix entries use
+  // them), bit 1 1/(4(1-ps)) (only thick quadrupoles)
+  int psc_skip;
   // Longitudinal kick (sliced pipe grids, float64 form): psigma -= klz *
   // (Phi_{k+1} - Phi_{k-1}) at the particle, phi the slices' node potentials
   // of the kick grid, klz = K gamma0 L / (2 dz).
@@ -138,6 +142,9 @@ constexpr int KP_QFAM_MAX = 8;
 int quad_families(const DevElem* el, int n, DevElem* fam, int max);
 // Host: tag each quadrupole of el equal to a family with its index.
 void tag_quad_families(DevElem* el, int n, const DevElem* fam, int nf);
+// Host: KPParams::psc_skip for a segment of n user elements whose
+// quadrupoles are tagged against the nf families fam.
+int psc_skip_mask(const sc_element* host, int n, const sc_beam* b, const DevElem* fam, int nf);
 
 // Solve scratch and spectra for the float64 FFT form.
 struct Fft64Plan {
