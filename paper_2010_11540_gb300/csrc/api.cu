@@ -860,6 +860,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       set_elements(P, lattice, nh, b, T->d_elems);
       with_qcache(P);
       P.psc_skip = psc_skip_mask(lattice, nh, b, T->qfam.data(), (int)T->qfam.size());
+      P.ps_mode = ps_mode_mask(lattice, nh, false);
       if (!marks.empty()) {
         // the turn's last solve cleared the charge (and the prologue did before the first turn)
         set_deposit(P, g);
@@ -881,6 +882,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       set_elements(P, lattice + m + 1, end - m - 1, b, T->d_elems + m + 1);
       with_qcache(P);
       P.psc_skip = psc_skip_mask(lattice + m + 1, end - m - 1, b, T->qfam.data(), (int)T->qfam.size());
+      P.ps_mode = ps_mode_mask(lattice + m + 1, end - m - 1, P.lon != 0);
       // the cell cache is valid at every marker: the previous launch deposited on this grid
       P.cell = T->cell;
       P.frac = T->frac;

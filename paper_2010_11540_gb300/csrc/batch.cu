@@ -631,6 +631,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         set_elements(P, u.lattice, nh, bm, T->d_elems[b]);
         with_qcache(P);
         P.psc_skip = psc_skip_mask(u.lattice, nh, bm, T->qfam[b].data(), (int)T->qfam[b].size());
+        P.ps_mode = ps_mode_mask(u.lattice, nh, false);
         if (!mk.empty()) {
           bunch_deposit(B, b, P);
           P.cell = T->cell[b];
@@ -652,6 +653,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         set_elements(P, u.lattice + m + 1, end - m - 1, bm, T->d_elems[b] + m + 1);
         with_qcache(P);
         P.psc_skip = psc_skip_mask(u.lattice + m + 1, end - m - 1, bm, T->qfam[b].data(), (int)T->qfam[b].size());
+        P.ps_mode = ps_mode_mask(u.lattice + m + 1, end - m - 1, P.lon != 0);
         P.cell = T->cell[b];
         P.frac = T->frac[b];
         P.fix = T->fix[b];

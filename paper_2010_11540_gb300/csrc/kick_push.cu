@@ -100,7 +100,7 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
   const size_t n = (size_t)P.n;
   unsigned int out = 0;
   for (int64_t p = p_begin + threadIdx.x; p < p_end; p += p_step) {
-    State s{P.x[p], P.px[p], P.y[p], P.py[p], P.sg[p], P.ps[p]};
+    State s{P.x[p], P.px[p], P.y[p], P.py[p], P.sg[p], (P.ps_mode & 2) ? 0.0 : P.ps[p]};
     if (P.do_kick) {
       int cell;
       if (F32) {
@@ -242,7 +242,7 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
     P.y[p] = s.y;
     P.py[p] = s.py;
     P.sg[p] = s.sg;
-    P.ps[p] = s.ps;
+    if (!(P.ps_mode & 1)) P.ps[p] = s.ps;
   }
   pdl_allow();
   if (P.do_deposit) {
@@ -534,6 +534,17 @@ int psc_skip_mask(const sc_element* host, int n, const sc_beam* b, const DevElem
       own = own || (d[i].flags >> QF_FAM_SHIFT) == 0;
     }
   return (own ? 0 : 1) | (thick ? 0 : 2);
+}
+
+int ps_mode_mask(const sc_element* host, int n, bool lon) {
+  bool reads = lon, writes = lon;
+  for (int i = 0; i < n; ++i) {
+    const sc_element& e = host[i];
+    if (e.type == SC_QUAD || e.type == SC_BEND || e.type == SC_RF || (e.type == SC_SEXT && e.length > 0.0))
+      reads = true;
+    if (e.type == SC_RF) writes = true;
+  }
+  return (writes ? 0 : 1) | (reads || writes ? 0 : 2);
 }
 
 void tag_quad_families(DevElem* el, int n, const DevElem* fam, int nf) {

@@ -118,6 +118,10 @@ struct KPParams {
   // 1/sqrt(1-ps) (only quadrupoles computing their own matrix entries use
   // them), bit 1 1/(4(1-ps)) (only thick quadrupoles)
   int psc_skip;
+  // psigma traffic of the segment (psc_mode 1): bit 0 psigma is not changed
+  // (no RF cavity, no longitudinal kick: not stored), bit 1 not read either
+  // (drifts and thin sextupoles only: not loaded)
+  int ps_mode;
   // Longitudinal kick (sliced pipe grids, float64 form): psigma -= klz *
   // (Phi_{k+1} - Phi_{k-1}) at the particle, phi the slices' node potentials
   // of the kick grid, klz = K gamma0 L / (2 dz).
@@ -145,6 +149,8 @@ void tag_quad_families(DevElem* el, int n, const DevElem* fam, int nf);
 // Host: KPParams::psc_skip for a segment of n user elements whose
 // quadrupoles are tagged against the nf families fam.
 int psc_skip_mask(const sc_element* host, int n, const sc_beam* b, const DevElem* fam, int nf);
+// Host: KPParams::ps_mode for a segment of n user elements (lon: the launch's longitudinal kick).
+int ps_mode_mask(const sc_element* host, int n, bool lon);
 
 // Solve scratch and spectra for the float64 FFT form.
 struct Fft64Plan {
