@@ -973,32 +973,51 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
 
 // Time every candidate of every phase on this grid (zero inputs; the time of a
 // dense contraction does not depend on the values) and keep the fastest.
+// Tiling choice, in two stages.  (1) Each phase alone: every variant that fits
+// the grid, 8 back-to-back launches, best of three rounds.  (2) The whole
+// solve as the turn runs it (the four phases chained by programmatic
+// dependent launch): one phase at a time, each of its variants with the other
+// phases' current choices, 4 chained solves per timing, best of three rounds,
+// keeping the fastest (coordinate descent from the stage-1 choice).  Variants
+// of a phase differ only in the FP32 summation order of split-K partial tiles.
 sc_status tf32_tune(sc_grid* g) {
   Tf32Plan* T = g->tf32;
   cudaEvent_t e0, e1;
   SC_CUDA(cudaEventCreate(&e0));
   SC_CUDA(cudaEventCreate(&e1));
   sc_status st = SC_OK;
-  for (int c = 0; c < 4 && !st; ++c) {
-    const int ph = T->base() + c;
+  // best of three rounds of `reps` calls of launch(), in microseconds per call
+  auto timed = [&](auto&& launch, int reps, float* us) -> cudaError_t {
+    cudaError_t e = launch();  // warm-up
     float best = 1e30f;
-    for (int k = 0; k < (int)variants(ph).size() && !st; ++k) {
-      PhaseRun r;
-      if (make_run(g, ph, k, r) != SC_OK) continue;  // does not fit this grid
-      r.a.scale = 1.f;
-      cudaError_t e = launch_run(ph, r, g->stream, false);  // warm-up
+    for (int round = 0; round < 3 && e == cudaSuccess; ++round) {
       float ms = 0.f;
-      constexpr int reps = 8;
-      if (e == cudaSuccess) e = cudaEventRecord(e0, g->stream);
-      for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch_run(ph, r, g->stream, false);
+      e = cudaEventRecord(e0, g->stream);
+      for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
       if (e == cudaSuccess) e = cudaEventRecord(e1, g->stream);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      best = std::min(best, 1e3f * ms / reps);
+    }
+    *us = best;
+    return e;
+  };
+  constexpr int kMaxVariants = 8;
+  float iso[4][kMaxVariants] = {};  // stage-1 time of each variant
+  for (int c = 0; c < 4 && !st; ++c) {
+    const int ph = T->base() + c;
+    float best = 1e30f;
+    for (int k = 0; k < (int)variants(ph).size() && k < kMaxVariants && !st; ++k) {
+      PhaseRun r;
+      if (make_run(g, ph, k, r) != SC_OK) continue;  // does not fit this grid
+      r.a.scale = 1.f;
+      float us = 0.f;
+      const cudaError_t e = timed([&] { return launch_run(ph, r, g->stream, false); }, 8, &us);
       if (e != cudaSuccess) {
         st = cuda_error(e, "tuning the split-TF32 solve");
         break;
       }
-      const float us = 1e3f * ms / reps;
+      iso[c][k] = us;
       if (us < best) {
         best = us;
         T->run[c] = r;
@@ -1006,6 +1025,39 @@ sc_status tf32_tune(sc_grid* g) {
       }
     }
     if (!st && T->run[c].variant < 0) st = set_error(SC_ERR_UNSUPPORTED, "no solve tiling fits this grid");
+  }
+  // stage 2: the chained solve
+  auto chain = [&] {
+    const sc_status s2 = tf32_solve(g, false);
+    return s2 == SC_OK ? cudaSuccess : cudaErrorUnknown;
+  };
+  float chain_best = 0.f;
+  if (!st) {
+    const cudaError_t e = timed(chain, 4, &chain_best);
+    if (e != cudaSuccess) st = cuda_error(e, "tuning the split-TF32 solve");
+  }
+  for (int c = 0; c < 4 && !st; ++c) {
+    const int ph = T->base() + c;
+    const PhaseRun keep = T->run[c];
+    PhaseRun best_run = keep;
+    for (int k = 0; k < (int)variants(ph).size() && k < kMaxVariants && !st; ++k) {
+      if (k == keep.variant || iso[c][k] == 0.f) continue;  // the current choice, or does not fit
+      PhaseRun r;
+      if (make_run(g, ph, k, r) != SC_OK) continue;
+      T->run[c] = r;
+      float us = 0.f;
+      const cudaError_t e = timed(chain, 4, &us);
+      if (e != cudaSuccess) {
+        st = cuda_error(e, "tuning the split-TF32 solve");
+        break;
+      }
+      if (us < chain_best) {
+        chain_best = us;
+        best_run = r;
+      }
+    }
+    T->run[c] = best_run;
+    T->tuned_us[c] = iso[c][best_run.variant];
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
