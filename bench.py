@@ -67,7 +67,7 @@ FP64_INST_LON_BEZIER_F32 = 13.95
 # DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
 # from ncu --set full (cold cache, mean of the three segment types): the
 # roofline's "traffic" for that workload; other workloads report null.
-KP_TRAFFIC_C2_TF32 = 151.1e6
+KP_TRAFFIC_C2_TF32 = 122.5e6
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -553,7 +553,7 @@ def run_ours(args):
                 "frac": achieved / FP64_PIPE_PEAK_TINST,
                 "traffic": (KP_TRAFFIC_C2_TF32 if (args.config == "c2" and args.precision == "tf32x3"
                                                    and args.gather == "bilinear") else None),
-                "traffic_unit": "DRAM bytes per launch (ncu, cold cache; algorithmic 192 B/particle)",
+                "traffic_unit": "DRAM bytes per launch (ncu, cold cache; algorithmic 163 B/particle, c2 mean)",
                 "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (probe: 2.0/clk/SM)",
                 "avg_launch_ms": kp_avg_ms, "fp64_inst_per_particle_kick": inst_per_kick,
                 "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
