@@ -559,6 +559,46 @@ def test_sliced_track_one_turn(precision):
             assert np.sqrt(np.mean(d * d)) < 1e-5 * scale, k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_c5_full_size_sampled(precision):
+    """The c5 workload at full size (1e7 particles sorted by sigma, 32 slices of
+    128x128): the sliced deposit bit for bit; the solve (float64 1e-12, split
+    form 1e-5); one space-charge step (kick, the segment up to the next
+    location, the fused deposit into a second sliced grid) on every particle:
+    its deposit bit for bit against the oracle's deposit of the pushed
+    coordinates, and, in the float64 form, 20000 sampled particles against the
+    oracle's kick and push (1e-10 of each coordinate's rms)."""
+    parts, b, grid, lat = synth.workload("c5")
+    n = len(parts["x"])
+    sl = synth.slices("c5")
+    g, og, zs = sliced_pair(grid, sl, precision)
+    st = to_gpu(parts)
+    sc.deposit(g, st)
+    Q = sc.grid_read(g)[0]
+    Qo, _ = oracle.deposit_sliced(og, zs, parts["x"], parts["y"], parts["sigma"])
+    assert np.array_equal(Q, Qo)
+    sc.solve(g)
+    _, Ex, Ey, _ = sc.grid_read(g)
+    Exo, Eyo = oracle.solve_sliced(og, Qo, n)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert rel_l2(Ex, Exo) < tol and rel_l2(Ey, Eyo) < tol, (rel_l2(Ex, Exo), rel_l2(Ey, Eyo))
+    _, kicks = oracle.segments(lat)
+    L, seg = kicks[0]
+    g2 = sc.create_grid(*grid, precision=precision, slices=sl)
+    sc.kick_push(g, st, b, L, seg, next_grid=g2)
+    got = to_host(st)
+    Q2 = sc.grid_read(g2)[0]
+    Q2o, _ = oracle.deposit_sliced(og, zs, got["x"], got["y"], got["sigma"])
+    assert np.array_equal(Q2, Q2o)
+    if precision == "fp64":
+        idx = np.sort(np.random.default_rng(5).choice(n, 20000, replace=False))
+        ref = {k: np.ascontiguousarray(parts[k][idx]) for k in KEYS}
+        oracle.kick_sliced(og, zs, ref, Exo, Eyo, oracle.kick_strength(b) * L)
+        oracle.push(ref, seg, b)
+        err = rel_state_err({k: got[k][idx] for k in KEYS}, ref)
+        assert max(err.values()) < 1e-10, err
+
+
 def test_sliced_deposit_edges():
     """sigma on the slice edges, outside the range, non-finite; rejected shapes."""
     grid, sl = (8, 8, 0.0, 7.0, 0.0, 7.0), (4, -2.0, 2.0)
