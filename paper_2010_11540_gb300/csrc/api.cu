@@ -1,6 +1,9 @@
 // C-ABI of libsc (include/sc.h): grid lifecycle, the PIC-loop calls of
 // Sec. I (deposit, solve, kick + push) and the turn driver that captures one
-// turn of the ring as a CUDA graph and replays it.
+// turn of the ring as a CUDA graph and replays it: the per-particle plan
+// arrays (cell cache, psigma quantities, quadrupole matrix entries), the
+// kick/push launch shape timed on a scratch copy of the bunch, and the
+// host-buffer entry point with its device copies.
 #include <cmath>
 #include <cstdio>
 #include <cstring>

@@ -4,8 +4,10 @@
 // conversion takes one of its two issue slots per SM clock).
 //
 // State: (x, px, y, py, sg, ps) with px = Px/p0, sg = s - c beta0 t.
-// Per-particle quantities that depend on ps alone are computed once per
-// launch (ps changes only in RF cavities, after which they are refreshed).
+// Per-particle quantities that depend on ps alone (the chromatic factors of
+// PsConst, the thick quadrupoles' matrix entries QuadCoef) are computed once
+// per call of a tracked turn and kept per particle (ps changes only in RF
+// cavities, after which they are refreshed).
 #pragma once
 
 #include "sc_internal.cuh"
