@@ -192,6 +192,23 @@ sc_status sc_grid_read(sc_grid *g, uint64_t *Q, double *Ex, double *Ey, int64_t 
  * particle count N used to normalise it, e.g. to solve a given charge. */
 sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particles);
 
+/* Device view of the charge grid, for a reduction across ranks of a bunch
+ * whose particles are sharded (the Sec. IV-A charge is a sum over particles):
+ * *Q receives the device pointer of the grid's uint64 charge ([nstack][ny][nx],
+ * owned by the grid, valid until sc_destroy_grid) and *cells its element
+ * count.  Each rank deposits its share with sc_deposit (or a fused
+ * sc_kick_push deposit), the ranks sum their grids in place on the grid's
+ * stream (an integer sum all-reduce; uint64 sums wrap modulo 2^64, so an int64
+ * reduction gives the same bits), sc_set_particle_count gives the bunch's
+ * total count, and sc_solve then yields on every rank the fields of the whole
+ * bunch, bit for bit those of one GPU.  Errors: SC_ERR_ARG. */
+sc_status sc_grid_charge_device(sc_grid *g, uint64_t **Q, int64_t *cells);
+
+/* The particle count N that normalises the next sc_solve (q = Q 2^-40 / N);
+ * every deposit sets it to the count it deposited.  Errors: SC_ERR_ARG (NULL
+ * grid, negative count). */
+sc_status sc_set_particle_count(sc_grid *g, int64_t n_particles);
+
 /* Longitudinal space-charge kick, Sec. IV (dps = -(e/(m gamma0^2 beta0^2
  * c^2)) u dlambda/dz L), on a sliced pipe grid (SC_SOLVE_PIPE_FP64, or
  * SC_SOLVE_PIPE_TF32X3 with the float32 potential): every kick on

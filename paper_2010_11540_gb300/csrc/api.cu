@@ -677,6 +677,20 @@ sc_status sc_trace_read(sc_grid* g, double* kick_push_ms, double* solve_ms, int6
   return SC_OK;
 }
 
+sc_status sc_grid_charge_device(sc_grid* g, uint64_t** Q, int64_t* cells) {
+  if (!g || !Q) return set_error(SC_ERR_ARG, "grid or Q is NULL");
+  *Q = (uint64_t*)g->Q;
+  if (cells) *cells = (int64_t)g->nx * g->ny * g->nstack;
+  return SC_OK;
+}
+
+sc_status sc_set_particle_count(sc_grid* g, int64_t n_particles) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
+  g->n_particles = n_particles;
+  return SC_OK;
+}
+
 sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_beam* b, const sc_element* lattice,
                               int n_elems, int n_turns, double* diag) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");

@@ -31,7 +31,8 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
            "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
            "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_batch_set_kick_push_shape",
-           "sc_batch_get_kick_push_shape", "sc_get_solver_work", "sc_last_error")
+           "sc_batch_get_kick_push_shape", "sc_get_solver_work", "sc_grid_charge_device",
+           "sc_set_particle_count", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -107,6 +108,8 @@ def load():
     L.sc_test_bounded_waits.argtypes = [vp, ctypes.c_int]
     L.sc_set_kick_push_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.sc_get_solver_work.argtypes = [vp, dp, dp]
+    L.sc_grid_charge_device.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(i64)]
+    L.sc_set_particle_count.argtypes = [vp, i64]
     L.sc_track_turns_host.argtypes = [vp, ctypes.POINTER(Particles), ctypes.POINTER(Beam), vp, ctypes.c_int,
                                       ctypes.c_int, dp]
     L.sc_batch_track_turns_host.argtypes = [vp, ctypes.POINTER(Bunch), ctypes.c_int, dp]
@@ -294,6 +297,29 @@ def get_solver_tiling(grid: Grid):
 def set_solver_tiling(grid: Grid, choice):
     """Force the split-TF32 solve's kernel variant per phase (-1 keeps one)."""
     _check(load().sc_set_solver_tiling(grid.handle, (ctypes.c_int * 4)(*[int(v) for v in choice])))
+
+
+class _DeviceArray:
+    """A raw device buffer described through __cuda_array_interface__ (no copy)."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr, "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+def charge_tensor(grid: Grid):
+    """The grid's uint64 charge as a CUDA int64 tensor sharing its memory
+    ([nstack * ny * nx], sc_grid_charge_device): sum it across ranks in place
+    (e.g. torch.distributed.all_reduce) between the deposit and the solve."""
+    import torch
+    q, cells = ctypes.c_void_p(), ctypes.c_int64(0)
+    _check(load().sc_grid_charge_device(grid.handle, ctypes.byref(q), ctypes.byref(cells)))
+    return torch.as_tensor(_DeviceArray(q.value, int(cells.value), "<i8"), device="cuda")
+
+
+def set_particle_count(grid: Grid, n: int):
+    """The count that normalises the next solve (the whole bunch's, after a cross-rank sum)."""
+    _check(load().sc_set_particle_count(grid.handle, int(n)))
 
 
 def solver_work(grid: Grid):

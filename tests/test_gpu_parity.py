@@ -910,3 +910,57 @@ def test_solver_work_counts():
     gs = sc.create_grid(128, 128, *ext, precision="tf32x3", slices=(4, -1.0, 1.0))
     ts, fs = sc.solver_work(gs)
     assert fs == 4 * f and abs(ts / t32 - 4) < 0.5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_sharded_bunch_through_the_charge_view(precision):
+    """A bunch split in two shards, each deposited on its own grid, the grids
+    summed in place through their device views (the cross-rank integer
+    all-reduce, done here between two grids of one GPU) and normalised by the
+    whole count: every shard grid then holds the whole bunch's charge and
+    fields bit for bit, and one kick/push of each shard gives the bits of the
+    unsharded kick/push."""
+    import torch
+
+    parts, b, grid, lat = synth.workload("c2", n=300001)
+    n, split = len(parts["x"]), 123457
+    _, kicks = oracle.segments(lat)
+    L, seg = kicks[0]
+
+    def make():
+        g = sc.create_grid(*grid, precision=precision)
+        if precision == "tf32x3":
+            sc.set_solver_tiling(g, (0, 0, 0, 0))  # one summation order for every grid
+        return g
+
+    g_all = make()
+    st_all = to_gpu(parts)
+    sc.deposit(g_all, st_all)
+    sc.solve(g_all)
+    Q_all, Ex_all, Ey_all, _ = sc.grid_read(g_all)
+    shards = [{k: v[:split].copy() for k, v in parts.items()}, {k: v[split:].copy() for k, v in parts.items()}]
+    gs = [make(), make()]
+    sts = [to_gpu(s) for s in shards]
+    for g, st in zip(gs, sts):
+        sc.deposit(g, st)
+    torch.cuda.synchronize()
+    views = [sc.charge_tensor(g) for g in gs]
+    assert views[0].numel() == 128 * 128 and views[0].dtype == torch.int64
+    total = views[0] + views[1]
+    for v in views:
+        v.copy_(total)
+    torch.cuda.synchronize()
+    for g in gs:
+        sc.set_particle_count(g, n)
+        sc.solve(g)
+        Q, Ex, Ey, _ = sc.grid_read(g)
+        assert np.array_equal(Q, Q_all) and np.array_equal(Ex, Ex_all) and np.array_equal(Ey, Ey_all)
+    sc.kick_push(g_all, st_all, b, L, seg)
+    for g, st in zip(gs, sts):
+        sc.kick_push(g, st, b, L, seg)
+    got_all = to_host(st_all)
+    got = [to_host(st) for st in sts]
+    for k in KEYS:
+        assert np.array_equal(np.concatenate([got[0][k], got[1][k]]), got_all[k]), k
+    with pytest.raises(sc.ScError):
+        sc.set_particle_count(gs[0], -1)
