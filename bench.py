@@ -67,7 +67,9 @@ FP64_INST_LON_BEZIER_F32 = 13.95
 # DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
 # from ncu --set full (cold cache, mean of the three segment types): the
 # roofline's "traffic" for that workload; other workloads report null.
-KP_TRAFFIC_C2_TF32 = 122.5e6
+KP_TRAFFIC_TF32 = {"c2": 122.5e6,   # 1e6 particles (the 200 MB working set partly stays in L2)
+                   "c4": 3859.8e6,  # the batched launch over 2.37e7 particles
+                   "c5": 1594.1e6}  # 1e7 particles, 32 slices
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 
@@ -563,9 +565,10 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": W.kernel,
                 "achieved": achieved, "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
                 "frac": achieved / FP64_PIPE_PEAK_TINST,
-                "traffic": (KP_TRAFFIC_C2_TF32 if (args.config == "c2" and args.precision == "tf32x3"
-                                                   and args.gather == "bilinear") else None),
-                "traffic_unit": "DRAM bytes per launch (ncu, cold cache; algorithmic 163 B/particle, c2 mean)",
+                "traffic": (KP_TRAFFIC_TF32.get(args.config) if (args.precision == "tf32x3" and args.gather == "bilinear"
+                                                                  and args.boundary == "open") else None),
+                "traffic_unit": "DRAM bytes per launch (ncu, cold cache, mean of the ring's three segment types; "
+                                "algorithmic 163 B/particle)",
                 "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (probe: 2.0/clk/SM)",
                 "avg_launch_ms": kp_avg_ms, "fp64_inst_per_particle_kick": inst_per_kick,
                 "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
