@@ -15,10 +15,13 @@
  *    own their device buffers (charge, fields, Green's-function spectra,
  *    scratch, captured graphs) and release them in sc_destroy_grid().
  *  - All work on a grid is enqueued on the CUDA stream given to
- *    sc_create_grid() (NULL = legacy default stream) and is asynchronous,
- *    except the calls documented as synchronous (sc_grid_read,
- *    sc_grid_write_charge, sc_track_turns when diag != NULL).  Errors raised
- *    inside kernels surface at the next synchronous call.
+ *    sc_create_grid() (NULL: a stream the grid creates, which orders with
+ *    the legacy default stream; graph capture needs a non-legacy stream) and
+ *    is asynchronous, except the calls documented as synchronous
+ *    (sc_grid_read, sc_grid_write_charge, the *_host tracking calls,
+ *    sc_track_turns when diag != NULL, and the first call that captures a
+ *    turn, which times the candidate launch shapes).  Errors raised inside
+ *    kernels surface at the next synchronous call.
  *  - Particle state is SoA float64: x [m], px = Px/p0, y [m], py = Py/p0,
  *    sigma = s - c beta0 t [m], psigma (Sec. III, Eq. H).
  */
