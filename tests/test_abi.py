@@ -91,3 +91,37 @@ def test_last_error_without_gpu(lib):
     buf = ctypes.create_string_buffer(64)
     assert lib.sc_last_error(buf, 64) == 0
     assert lib.sc_last_error(None, 0) != 0
+
+
+def test_new_entry_points_reject_null_without_gpu(lib):
+    """The launch-shape, host-buffer, solve-work and charge-view calls reject a
+    NULL grid or batch before touching the device."""
+    i, d, v, n = ctypes.c_int(), ctypes.c_double(), ctypes.c_void_p(), ctypes.c_int64()
+    assert lib.sc_set_kick_push_shape(None, 0, -1) == -1
+    assert lib.sc_get_kick_push_shape(None, ctypes.byref(i), ctypes.byref(i), ctypes.byref(d)) == -1
+    assert lib.sc_batch_set_kick_push_shape(None, 0, 0) == -1
+    assert lib.sc_batch_get_kick_push_shape(None, ctypes.byref(i), ctypes.byref(i), ctypes.byref(d)) == -1
+    assert lib.sc_track_turns_host(None, None, None, None, 0, 1, None) == -1
+    assert lib.sc_batch_track_turns_host(None, None, 1, None) == -1
+    assert lib.sc_get_solver_work(None, ctypes.byref(d), ctypes.byref(d)) == -1
+    assert lib.sc_grid_charge_device(None, ctypes.byref(v), ctypes.byref(n)) == -1
+    assert lib.sc_set_particle_count(None, 10) == -1
+
+
+def test_host_particle_marshalling():
+    """The binding's host-array view: contiguous float64 numpy arrays or CPU
+    tensors of one length; anything else is refused before the library."""
+    import numpy as np
+    import torch
+    keys = ("x", "px", "y", "py", "sigma", "psigma")
+    good = {k: np.zeros(5) for k in keys}
+    p = sc.host_particles(good)
+    assert p.n == 5 and p.x == good["x"].ctypes.data
+    t = {k: torch.zeros(5, dtype=torch.float64) for k in keys}
+    assert sc.host_particles(t).n == 5
+    with pytest.raises(ValueError):
+        sc.host_particles(dict(good, y=np.zeros(5, dtype=np.float32)))
+    with pytest.raises(ValueError):
+        sc.host_particles(dict(good, y=np.zeros(6)))
+    with pytest.raises(ValueError):
+        sc.host_particles(dict(good, y=np.zeros(10)[::2]))
