@@ -5,11 +5,13 @@ cpu_baseline / reference legs of bench.py, never by the product package.  It
 shares no code with the CUDA path; the seeded inputs come from
 paper_2010_11540_gb300.synth, which the caller passes in as plain arrays.
 
-The particle loops are plain C (sc_oracle.c, built with -ffp-contract=off);
-the open-boundary convolution uses numpy's FFT as the library primitive
-(Hockney's zero-padded method, Sec. I reference [Hockney]); the tracking loop
-follows the PIC loop of Sec. I (deposit -> Poisson -> kick/push) with the kick
-of Sec. IV.
+The particle loops are plain C (sc_oracle.c, built with -ffp-contract=off
+and OpenMP: set_threads(n) splits them over n threads, bit-identically to one
+thread); the open-boundary convolution uses a library FFT (pocketfft, through
+scipy.fft with one worker per thread when scipy is present, else numpy.fft)
+as the primitive of Hockney's zero-padded method (Sec. I reference
+[Hockney]); the tracking loop follows the PIC loop of Sec. I (deposit ->
+Poisson -> kick/push) with the kick of Sec. IV.
 
 Functions whose parity is pinned only against the oracle itself are marked
 "parity unpinned" in their docstrings (long-run statistics).
@@ -33,10 +35,12 @@ DRIFT, QUAD, SEXT, BEND, RF, MARK, EXACT_BEND = 0, 1, 2, 3, 4, 5, 6
 
 
 def build(force=False):
-    """Compile the C oracle (gcc, -O2 -ffp-contract=off)."""
+    """Compile the C oracle (gcc, -O2 -ffp-contract=off, OpenMP)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                               "-std=c11", "-D_DEFAULT_SOURCE", _SRC, "-o", _LIB, "-lm"])
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+                               "-std=c11", "-D_DEFAULT_SOURCE", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
     return _LIB
 
 
@@ -95,8 +99,44 @@ def lib():
                                ctypes.POINTER(_Beam)]
         L.orc_moments.restype = None
         L.orc_moments.argtypes = [ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+        L.orc_set_threads.restype = ctypes.c_int
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_max_threads.restype = ctypes.c_int
+        L.orc_max_threads.argtypes = []
         _lib = L
     return _lib
+
+
+_threads = 1
+
+
+def set_threads(n=None):
+    """Threads of the particle loops and FFT workers (None: every core);
+    returns the count in use.  Results are bit-identical for any count."""
+    global _threads
+    L = lib()
+    _threads = int(L.orc_set_threads(int(L.orc_max_threads() if n is None else n)))
+    return _threads
+
+
+def threads():
+    return _threads
+
+
+try:  # the library FFT of the convolution: pocketfft through scipy (threaded) or numpy
+    import scipy.fft as _sfft
+
+    def _rfft2(a):
+        return _sfft.rfft2(a, workers=_threads)
+
+    def _irfft2(a, s):
+        return _sfft.irfft2(a, s=s, workers=_threads)
+except ImportError:  # pragma: no cover
+    def _rfft2(a):
+        return np.fft.rfft2(a)
+
+    def _irfft2(a, s):
+        return np.fft.irfft2(a, s=s)
 
 
 def _d(a):
@@ -201,6 +241,18 @@ def deposit(g: Geometry, x, y):
     return Q, int(n_out)
 
 
+def deposit_cells(g: Geometry, x, y):
+    """Cell index j*nx + i of each particle by the deposit's rule (Sec. IV-A:
+    xi = (x - xmin) / hx, inside iff 0 <= xi < nx-1, likewise eta), -1 outside."""
+    xi = (np.asarray(x, dtype=np.float64) - g.xmin) * g.inv_hx
+    eta = (np.asarray(y, dtype=np.float64) - g.ymin) * g.inv_hy
+    with np.errstate(invalid="ignore"):
+        inside = (xi >= 0.0) & (xi < g.nx - 1) & (eta >= 0.0) & (eta < g.ny - 1)
+    cell = np.full(len(xi), -1, dtype=np.int64)
+    cell[inside] = np.floor(eta[inside]).astype(np.int64) * g.nx + np.floor(xi[inside]).astype(np.int64)
+    return cell
+
+
 def green_self(hx, hy):
     return lib().orc_green_self(hx, hy)
 
@@ -224,14 +276,26 @@ def potential_direct(g: Geometry, q):
     return phi
 
 
+_green_spectra = {}
+
+
+def green_spectrum(g: Geometry):
+    """rfft2 of green_cyclic(g), kept per geometry (it depends on nx, ny, hx, hy only)."""
+    key = (g.nx, g.ny, g.hx, g.hy)
+    if key not in _green_spectra:
+        if len(_green_spectra) > 16:
+            _green_spectra.clear()
+        _green_spectra[key] = _rfft2(green_cyclic(g))
+    return _green_spectra[key]
+
+
 def potential_fft(g: Geometry, q):
     """phi on nodes i=-1..nx, j=-1..ny: Hockney's method, q zero-padded to the
-    doubled grid and cyclically convolved with G by FFT (numpy, float64)."""
+    doubled grid and cyclically convolved with G by FFT (pocketfft, float64)."""
     Mx, My = 2 * g.nx, 2 * g.ny
     qp = np.zeros((My, Mx))
     qp[: g.ny, : g.nx] = q
-    G = green_cyclic(g)
-    phi = np.fft.irfft2(np.fft.rfft2(qp) * np.fft.rfft2(G), s=(My, Mx))
+    phi = _irfft2(_rfft2(qp) * green_spectrum(g), s=(My, Mx))
     iy = np.r_[My - 1, np.arange(0, g.ny + 1)]
     ix = np.r_[Mx - 1, np.arange(0, g.nx + 1)]
     return np.ascontiguousarray(phi[np.ix_(iy, ix)])

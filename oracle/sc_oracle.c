@@ -9,6 +9,14 @@
  * -ffp-contract=off so that every product and sum below is rounded exactly as
  * written (no fused multiply-add).
  *
+ * Threads (orc_set_threads, default 1): with OpenMP the particle loops of the
+ * deposit, kicks and push are split over threads.  Each particle's arithmetic
+ * is the same whatever the split, and the deposit's integer sums do not depend
+ * on their order (each thread fills its own zeroed grid over a contiguous
+ * range of particles, and the grids are added afterwards), so the results are
+ * bit-identical to one thread.  Moments stay sequential (floating-point sums
+ * in particle order).
+ *
  * Contents, each following the passage cited at the function:
  *   orc_deposit        Sec. IV-A, CIC charge-assignment equation (4 weights),
  *                      in 2^-20 fixed point per axis, uint64 accumulation;
@@ -16,7 +24,7 @@
  *                      (the line density lambda(z) of Sec. IV as a histogram
  *                      of sigma, each bin with its own transverse grid).
  *   orc_green_self     cell-averaged -ln r (self term of the open-boundary
- *                      Green's function; the paper is silent, see DESIGN).
+ *                      Green's function; the paper is silent on it).
  *   orc_green_cyclic   Hockney's zero-padded free-space Green's function
  *                      G = -ln r laid out on the doubled (2nx x 2ny) grid.
  *   orc_potential_direct  direct pairwise sum phi = sum G q (definition).
@@ -34,7 +42,11 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int32_t type, pad;
@@ -48,6 +60,27 @@ typedef struct {
 enum { ORC_DRIFT = 0, ORC_QUAD = 1, ORC_SEXT = 2, ORC_BEND = 3, ORC_RF = 4, ORC_MARK = 5, ORC_EXACT_BEND = 6 };
 
 static const double ORC_ONE_FX = 1048576.0; /* 2^20 */
+
+/* Threads of the particle loops (1 without OpenMP). */
+static int orc_threads = 1;
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  orc_threads = n < 1 ? 1 : n;
+#else
+  (void)n;
+  orc_threads = 1;
+#endif
+  return orc_threads;
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_num_procs();
+#else
+  return 1;
+#endif
+}
 
 /* ---------------------------------------------------------------------
  * Charge deposition, Sec. IV-A (CIC equation).  Grid nodes are
@@ -71,11 +104,11 @@ static int orc_slice(double sg, int nz, double zmin, double inv_dz) {
   return (int)floor(zeta);
 }
 
-uint64_t orc_deposit_sliced(int64_t n, const double *x, const double *y, const double *sg, int nx, int ny,
-                            double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin,
-                            double inv_dz, uint64_t *Q) {
+static uint64_t orc_deposit_range(int64_t p0, int64_t p1, const double *x, const double *y, const double *sg,
+                                  int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy, int nz,
+                                  double zmin, double inv_dz, uint64_t *Q) {
   uint64_t n_out = 0;
-  for (int64_t p = 0; p < n; ++p) {
+  for (int64_t p = p0; p < p1; ++p) {
     int k = orc_slice(sg ? sg[p] : 0.0, nz, zmin, inv_dz);
     double xi = (x[p] - xmin) * inv_hx;
     double eta = (y[p] - ymin) * inv_hy;
@@ -96,6 +129,29 @@ uint64_t orc_deposit_sliced(int64_t n, const double *x, const double *y, const d
     q[(int64_t)(j + 1) * nx + i] += bx * ay;
     q[(int64_t)(j + 1) * nx + i + 1] += ax * ay;
   }
+  return n_out;
+}
+
+uint64_t orc_deposit_sliced(int64_t n, const double *x, const double *y, const double *sg, int nx, int ny,
+                            double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin,
+                            double inv_dz, uint64_t *Q) {
+  int nt = orc_threads;
+  if (n < 4096) nt = 1;
+  uint64_t *priv = 0;
+  size_t cells = (size_t)nx * ny * nz;
+  if (nt > 1) priv = (uint64_t *)calloc((size_t)(nt - 1) * cells, sizeof(uint64_t));
+  if (!priv) return orc_deposit_range(0, n, x, y, sg, nx, ny, xmin, ymin, inv_hx, inv_hy, nz, zmin, inv_dz, Q);
+  uint64_t n_out = 0;
+#pragma omp parallel for num_threads(nt) schedule(static, 1) reduction(+ : n_out)
+  for (int t = 0; t < nt; ++t) {
+    /* thread t: particles [n t / nt, n (t+1) / nt) into Q (t = 0) or its own zeroed grid */
+    uint64_t *dst = t == 0 ? Q : priv + (size_t)(t - 1) * cells;
+    n_out += orc_deposit_range(n * t / nt, n * (t + 1) / nt, x, y, sg, nx, ny, xmin, ymin, inv_hx, inv_hy, nz, zmin,
+                               inv_dz, dst);
+  }
+  for (int t = 1; t < nt; ++t)
+    for (size_t c = 0; c < cells; ++c) Q[c] += priv[(size_t)(t - 1) * cells + c];
+  free(priv);
   return n_out;
 }
 
@@ -186,6 +242,7 @@ void orc_fields(int nx, int ny, double hx, double hy, const double *phi_ext, dou
 void orc_kick_sliced(int64_t n, const double *x, const double *y, const double *sg, double *px, double *py,
                      int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin,
                      double inv_dz, const double *Ex, const double *Ey, double kl) {
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
   for (int64_t p = 0; p < n; ++p) {
     int k = orc_slice(sg ? sg[p] : 0.0, nz, zmin, inv_dz);
     double xi = (x[p] - xmin) * inv_hx;
@@ -223,6 +280,7 @@ void orc_kick_long(int64_t n, const double *x, const double *y, const double *sg
                    double xmin, double ymin, double inv_hx, double inv_hy, int nz, double zmin, double inv_dz,
                    const double *phi, double klz) {
   int64_t cells = (int64_t)nx * ny;
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
   for (int64_t p = 0; p < n; ++p) {
     int k = orc_slice(sg[p], nz, zmin, inv_dz);
     double xi = (x[p] - xmin) * inv_hx;
@@ -312,6 +370,7 @@ void orc_kick_bezier(int64_t n, const double *x, const double *y, const double *
                      double *ps, int nx, int ny, double xmin, double ymin, double inv_hx, double inv_hy, double hx,
                      double hy, int nz, double zmin, double inv_dz, const double *phi, double kl, double klz) {
   int64_t cells = (int64_t)nx * ny;
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
   for (int64_t p = 0; p < n; ++p) {
     int k = orc_slice(sg ? sg[p] : 0.0, nz, zmin, inv_dz);
     double xi = (x[p] - xmin) * inv_hx;
@@ -490,6 +549,7 @@ static void orc_rf(double *s, const orc_elem *e, const orc_beam *bm) {
 /* Push every particle through elements[0..n_elems) in order. */
 void orc_push(int64_t n, double *x, double *px, double *y, double *py, double *sg, double *ps,
               const orc_elem *el, int n_elems, const orc_beam *bm) {
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
   for (int64_t p = 0; p < n; ++p) {
     double s[6] = {x[p], px[p], y[p], py[p], sg[p], ps[p]};
     for (int k = 0; k < n_elems; ++k) {

@@ -94,3 +94,25 @@ def test_first_moment():
     my = (Q.sum(axis=1) / UNIT * g.node_y).sum()
     tol = len(x) * 2.0 ** -21 * max(g.hx, g.hy) * 1.01
     assert abs(mx - x.sum()) < tol and abs(my - y.sum()) < tol
+
+
+def test_deposit_cells_follow_the_deposit():
+    """deposit_cells names the cell each particle's four weights go to: a
+    single particle's deposit lands on that cell's four nodes; outside and
+    non-finite particles get -1."""
+    g = oracle.Geometry(8, 6, -1.0, 1.0, -0.5, 0.7)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.2, 1.2, 300)
+    y = rng.uniform(-0.7, 0.9, 300)
+    x[:3] = [np.nan, 1.0, -1.0]
+    cells = oracle.deposit_cells(g, x, y)
+    assert cells[0] == -1 and cells[1] == -1
+    for p in range(300):
+        Q, n_out = oracle.deposit(g, x[p:p + 1], y[p:p + 1])
+        if cells[p] < 0:
+            assert n_out == 1 and not Q.any()
+        else:
+            j, i = divmod(int(cells[p]), g.nx)
+            nz = np.argwhere(Q.reshape(g.ny, g.nx) > 0)
+            assert set(map(tuple, nz)) <= {(j, i), (j, i + 1), (j + 1, i), (j + 1, i + 1)}
+            assert Q[j, i] > 0 or Q[j, i + 1] > 0 or Q[j + 1, i] > 0 or Q[j + 1, i + 1] > 0

@@ -42,3 +42,26 @@ def test_deterministic():
     oracle.track(g, a, b, lat, 1)
     oracle.track(g, c, b, lat, 1)
     assert all(np.array_equal(a[k], c[k]) for k in a)
+
+
+def test_threads_bit_identical():
+    """The OpenMP oracle (particle loops split over threads, each thread's
+    deposit into its own grid, the integer grids added afterwards) gives the
+    same bits as one thread: deposit, fields and three kicks of tracking, on
+    plain and sliced grids."""
+    parts, b, grid, lat = synth.workload("c2", n=20011)
+    g = oracle.Geometry(*grid)
+    zs = oracle.Slices(4, -10.0, 10.0)
+    out = []
+    for n in (1, 4):
+        assert oracle.set_threads(n) == n or oracle.lib().orc_max_threads() == 1
+        st = oracle.copy_state(parts)
+        oracle.track(g, st, b, lat, 1, max_kicks=3)
+        Q, n_out = oracle.deposit(g, st["x"], st["y"])
+        Qs, n_out_s = oracle.deposit_sliced(g, zs, st["x"], st["y"], st["sigma"])
+        out.append((st, Q, n_out, Qs, n_out_s, oracle.solve(g, Q, len(st["x"]))))
+    oracle.set_threads(1)
+    (a, Qa, na, Qsa, nsa, Ea), (c, Qc, nc, Qsc, nsc, Ec) = out
+    assert all(np.array_equal(a[k], c[k]) for k in a)
+    assert np.array_equal(Qa, Qc) and na == nc and np.array_equal(Qsa, Qsc) and nsa == nsc
+    assert np.array_equal(Ea[0], Ec[0]) and np.array_equal(Ea[1], Ec[1])
