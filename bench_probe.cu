@@ -1,11 +1,11 @@
-// Machine probes for roofline denominators, measured on the device in use:
+// Machine probes for bench.py's roofline denominators (not part of libsc):
 // the throughput of shared-memory 64-bit atomic adds (the unit of work of the
 // CIC deposit, Sec. IV-A) and of FP64 fused multiply-adds (the FP64 pipe that
-// bounds the transfer-map push, Sec. III).  Both kernels touch only their own
-// shared memory / registers and one output word per block.
-#include "sc_internal.cuh"
+// bounds the transfer-map push, Sec. III), measured on the device in use.
+// The kernels touch only their own shared memory / registers and one output
+// word per block.  Built into libsc_probe.so beside bench.py.
+#include <cuda_runtime.h>
 
-namespace sc {
 namespace {
 
 constexpr int kProbeThreads = 1024;
@@ -65,10 +65,9 @@ __global__ void __launch_bounds__(256) probe_fp64_kernel(int iters, double* sink
 }
 
 template <class F>
-sc_status time_launches(F launch, cudaStream_t s, float* ms) {
+int time_launches(F launch, cudaStream_t s, float* ms) {
   cudaEvent_t e0, e1;
-  SC_CUDA(cudaEventCreate(&e0));
-  SC_CUDA(cudaEventCreate(&e1));
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -2;
   launch();  // warm-up
   cudaEventRecord(e0, s);
   for (int r = 0; r < 5; ++r) launch();
@@ -78,28 +77,29 @@ sc_status time_launches(F launch, cudaStream_t s, float* ms) {
   if (e == cudaSuccess) e = cudaGetLastError();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (e != cudaSuccess) return cuda_error(e, "probe");
+  if (e != cudaSuccess) return -2;
   *ms /= 5.f;
-  return SC_OK;
+  return 0;
 }
 
 }  // namespace
-}  // namespace sc
 
-using namespace sc;
-
-extern "C" sc_status sc_probe_peaks(double* shared_atomics_per_s, double* random_atomics_per_s,
-                                    double* fp64_inst_per_s, void* stream) {
-  if (!shared_atomics_per_s && !random_atomics_per_s && !fp64_inst_per_s)
-    return set_error(SC_ERR_ARG, "nothing to probe");
+// Throughput of conflict-free shared u64 atomics (each warp on 32 consecutive
+// words), of shared u64 atomics on random words of a 128 KB table, and of FP64
+// FMA instructions, per second on the current device, each timed over five
+// launches on `stream` (synchronous).  Outputs may be NULL (not all).
+// Returns 0, -1 (nothing asked) or -2 (a CUDA call failed).
+extern "C" int scb_probe_peaks(double* shared_atomics_per_s, double* random_atomics_per_s, double* fp64_inst_per_s,
+                               void* stream) {
+  if (!shared_atomics_per_s && !random_atomics_per_s && !fp64_inst_per_s) return -1;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0;
-  SC_CUDA(cudaGetDevice(&dev));
-  SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -2;
   const int blocks = 2 * sms;
   unsigned long long* sink = nullptr;
-  SC_CUDA(cudaMalloc(&sink, (size_t)blocks * 8 * sizeof(unsigned long long)));
-  sc_status st = SC_OK;
+  if (cudaMalloc(&sink, (size_t)blocks * 8 * sizeof(unsigned long long)) != cudaSuccess) return -2;
+  int st = 0;
   if (shared_atomics_per_s) {
     const int iters = 4096;
     float ms = 0.f;
@@ -109,9 +109,11 @@ extern "C" sc_status sc_probe_peaks(double* shared_atomics_per_s, double* random
   if (!st && random_atomics_per_s) {
     const int iters = 1024;
     float ms = 0.f;
-    SC_CUDA(cudaFuncSetAttribute(probe_atomics_random_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kRandTable * 8));
-    st = time_launches(
+    if (cudaFuncSetAttribute(probe_atomics_random_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kRandTable * 8) != cudaSuccess)
+      st = -2;
+    if (!st)
+      st = time_launches(
         [&] { probe_atomics_random_kernel<<<sms, kProbeThreads, kRandTable * 8, s>>>(iters, sink); }, s, &ms);
     if (!st) *random_atomics_per_s = (double)sms * kProbeThreads * iters * 4 / (ms * 1e-3);
   }

@@ -21,7 +21,14 @@
  *    (sc_grid_read, sc_grid_write_charge, the *_host tracking calls,
  *    sc_track_turns when diag != NULL, and the first call that captures a
  *    turn, which times the candidate launch shapes).  Errors raised inside
- *    kernels surface at the next synchronous call.
+ *    kernels surface at the next synchronous call of that grid:
+ *    SC_ERR_TIMEOUT when a tensor-core solve gave up on a bounded wait (the
+ *    grid then refuses further solves, sc_solve and sc_track_turns return
+ *    SC_ERR_TIMEOUT; destroy it and create a new one), else SC_ERR_NAN when
+ *    deposits met particles whose x or y (or sigma, on a sliced grid) is NaN
+ *    or infinite (such particles are outside the grid: no charge, no kick;
+ *    the count is cleared by the call that reports it, whose outputs are
+ *    still written).
  *  - Particle state is SoA float64: x [m], px = Px/p0, y [m], py = Py/p0,
  *    sigma = s - c beta0 t [m], psigma (Sec. III, Eq. H).
  */
@@ -43,7 +50,7 @@ typedef int sc_status;
 #define SC_ERR_OOM (-3)         /* device allocation failed                   */
 #define SC_ERR_OVERFLOW (-4)    /* more particles than the 64-bit charge grid can hold */
 #define SC_ERR_TIMEOUT (-5)     /* a bounded device wait ran out              */
-#define SC_ERR_NAN (-6)         /* non-finite particle state seen             */
+#define SC_ERR_NAN (-6)         /* deposits met particles whose position is not finite */
 #define SC_ERR_UNSUPPORTED (-7) /* grid size / precision not supported        */
 
 /* Poisson-solve arithmetic (sc_create_grid `precision`). */
@@ -57,6 +64,12 @@ typedef int sc_status;
  * tensor cores (3-term split TF32, FP32 accumulate; tiling tuned as for
  * SC_SOLVE_TF32X3), float32 fields; nx = ny in 10..258. */
 #define SC_SOLVE_PIPE_TF32X3 3
+/* The open-boundary solve of SC_SOLVE_TF32X3 with BF16 operands instead:
+ * tcgen05 kind::f16 MMAs on bf16 hi/lo splits (8 significant bits each, ~16
+ * together), FP32 accumulate, float32 fields; half the operand bytes of the
+ * TF32 form, and fields about 1e-5 (relative L2) from the float64 solution
+ * rather than 1e-7.  nx = ny in {64, 128, 256}. */
+#define SC_SOLVE_BF16X3 4
 
 /* Element types (sc_element.type). */
 #define SC_DRIFT 0 /* exact drift, Sec. III-A                                  */
@@ -107,7 +120,7 @@ typedef struct {
  * (Hockney zero-padded) Poisson solver of the given precision.  Builds the
  * Green's-function spectra on the device (synchronous on `stream`).
  * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {64, 128, 256}
- * for SC_SOLVE_TF32X3; nx - 1, ny - 1 powers of two in 8..512 for
+ * for SC_SOLVE_TF32X3 and SC_SOLVE_BF16X3; nx - 1, ny - 1 powers of two in 8..512 for
  * SC_SOLVE_PIPE_FP64; nx = ny in 10..258 for SC_SOLVE_PIPE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
  * SC_ERR_OOM, SC_ERR_CUDA.  *out is set only on success. */
 sc_status sc_create_grid(sc_grid **out, int nx, int ny, double xmin, double xmax, double ymin,
@@ -139,6 +152,24 @@ sc_status sc_destroy_grid(sc_grid *g);
  * ones) deposit nothing and are counted (sc_grid_read's n_out).
  * Errors: SC_ERR_ARG, SC_ERR_OVERFLOW (n > SC_MAX_PARTICLES_PER_GRID). */
 sc_status sc_deposit(sc_grid *g, const sc_particles *p);
+
+/* Reorder a bunch by its cell on grid g (an option; the paper has no
+ * counterpart): the six arrays of p are permuted in place, all by the same
+ * permutation -- particles sorted by cell index (slice, then row j, then
+ * column i), those outside the grid last, equal cells in their old order
+ * (stable) -- and, when perm != NULL (device, caller-owned, p->n int32), perm[k]
+ * receives the old index of the particle now at k.  Physics results do not
+ * depend on the order (particles are independent and the charge is an
+ * integer sum).  sc_deposit on this grid of the bunch it last ordered (same
+ * x array and count) runs faster: each warp combines the weights of
+ * neighbouring particles in the same cell before its atomic adds, which only
+ * pays on an ordered bunch.  Per-particle arrays the caller keeps elsewhere (e.g. tune
+ * accumulators) are not permuted; sc_track_turns rebuilds its own at every
+ * call.  The grid keeps a scratch buffer for the sort (20 bytes per particle
+ * plus the radix sort's storage, grown on demand: the call then synchronises
+ * and allocates); asynchronous on the grid's stream otherwise.
+ * Errors: SC_ERR_ARG, SC_ERR_OVERFLOW, SC_ERR_OOM, SC_ERR_CUDA. */
+sc_status sc_sort_particles(sc_grid *g, const sc_particles *p, int32_t *perm);
 
 /* Open-boundary Poisson solve (Sec. IV, Eq. poisson3D, free-space part):
  * phi = G * q with G = -ln r, q = Q 2^-40 / N (N = particle count of the last
@@ -188,7 +219,8 @@ sc_status sc_track_turns_host(sc_grid *g, const sc_particles *host, const sc_bea
 /* Synchronous copy-out of a grid's state into host arrays (each may be NULL):
  * Q (n_slices*ny*nx uint64, row-major [k][j][i]), Ex and Ey (same layout,
  * float64), and n_out = particles found outside the grid by deposits since
- * the grid was created. */
+ * the grid was created.  Errors: SC_ERR_ARG; after the copies, SC_ERR_TIMEOUT
+ * or SC_ERR_NAN as described under Conventions. */
 sc_status sc_grid_read(sc_grid *g, uint64_t *Q, double *Ex, double *Ey, int64_t *n_out);
 
 /* Synchronous upload of a charge grid Q (host, n_slices*ny*nx uint64) and the
@@ -206,6 +238,26 @@ sc_status sc_grid_write_charge(sc_grid *g, const uint64_t *Q, int64_t n_particle
  * total count, and sc_solve then yields on every rank the fields of the whole
  * bunch, bit for bit those of one GPU.  Errors: SC_ERR_ARG. */
 sc_status sc_grid_charge_device(sc_grid *g, uint64_t **Q, int64_t *cells);
+
+/* The sharded bunch inside sc_track_turns (no counterpart in the paper; the
+ * charge of Sec. IV-A is a sum over particles, so ranks holding parts of one
+ * bunch add their grids).  fn is a caller function that enqueues, on the CUDA
+ * stream it is given, an in-place sum of `cells` uint64 charge values at the
+ * device pointer `charge` over every rank of the bunch (e.g. an NCCL uint64
+ * sum all-reduce; uint64 sums wrap modulo 2^64, so an int64 reduction gives
+ * the same bits) and returns 0 (non-zero: the capture fails with
+ * SC_ERR_CUDA).  sc_track_turns calls it while it captures a turn, once per
+ * space-charge location, between that location's deposit and its solve, so
+ * the reduction is part of the replayed turn graph; every rank must track the
+ * same lattice for the same turns.  The solve then normalises by
+ * total_particles (the whole bunch) instead of the local count; fields and
+ * kicks on every rank equal those of the whole bunch on one GPU, bit for bit.
+ * Per-turn moments and tunes stay per rank (local particles).  The launch-
+ * shape trials of a first capture do not call fn.  fn == NULL switches the
+ * reduction off.  Synchronises the grid's stream; the next sc_track_turns
+ * re-captures.  Errors: SC_ERR_ARG (NULL grid; fn with total_particles < 1). */
+typedef int (*sc_charge_reduce_fn)(uint64_t *charge, int64_t cells, void *stream, void *user);
+sc_status sc_set_charge_reduce(sc_grid *g, sc_charge_reduce_fn fn, void *user, int64_t total_particles);
 
 /* The particle count N that normalises the next sc_solve (q = Q 2^-40 / N);
  * every deposit sets it to the count it deposited.  Errors: SC_ERR_ARG (NULL
@@ -399,6 +451,13 @@ sc_status sc_batch_get_solver_tiling(sc_batch *B, int b, int *choice, char *desc
 sc_status sc_batch_set_solver_tiling(sc_batch *B, const int *choice);
 sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
+/* Fractional tunes from a tune accumulator (sc_tune_setup) after n_turns
+ * tracked turns: q (device, caller-owned, 2 n doubles) receives acc's summed
+ * advances / (2 pi n_turns), x for particles 0..n-1, then y.  Asynchronous on
+ * `stream` (NULL: the legacy default stream); acc and q are device pointers.
+ * Errors: SC_ERR_ARG (NULL pointer, n < 0, n_turns < 1), SC_ERR_CUDA. */
+sc_status sc_tunes(const double *acc, int64_t n, int n_turns, double *q, void *stream);
+
 /* Largest particle count sc_moments_noalloc accepts (its partial sums are
  * reduced in float64 by a fixed 304-block grid; counts are bounded like a
  * grid's). */
@@ -410,26 +469,18 @@ sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_m
  * re-entered, a real-time loop where cudaMalloc/cudaFree may synchronise).
  * Writes 14 doubles to the device pointer `out` on `stream` (asynchronous):
  * means of (x, px, y, py, sigma, psigma), then the central moments <xx>,
- * <x px>, <px px>, <yy>, <y py>, <py py>, <sigma sigma>, <psigma psigma> — the
+ * <x px>, <px px>, <yy>, <y py>, <py py>, <sigma sigma>, <psigma psigma>
+ * (two passes: the means, then the moments of the offsets from them) — the
  * same numbers as sc_track_turns' per-turn diagnostics.  Scratch: a
  * file-scope device array of 304 x 14 doubles (34 KB), held by every GPU that
  * loads the library until the process exits.  The first call on a device
- * looks up that array's address (make it before any stream capture); calls
- * that overlap on the GPU share the array and race.  Calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * looks up that array's address (make it before any stream capture), and so
+ * does the first call after the device's context was reset (cudaDeviceReset);
+ * calls that overlap on the GPU share the array and race.  Calls no
+ * cudaMalloc, cudaFree or other allocating routine.
  * Errors: SC_ERR_ARG (NULL, n <= 0), SC_ERR_OVERFLOW (n > SC_MOMENTS_NOALLOC_MAX_N),
  * SC_ERR_CUDA. */
 sc_status sc_moments_noalloc(const sc_particles *p, double *out, void *stream);
-
-/* Machine probes (no counterpart in the paper): the throughput of
- * shared-memory 64-bit atomic adds (the CIC deposit's unit of work), once
- * conflict-free (each warp on 32 consecutive words) and once on random words
- * of a 128 KB table (the access pattern of a deposit into a 128 x 128 tile),
- * and of FP64 fused multiply-adds (the pipe that bounds the push), on the
- * current device, each timed over five launches on `stream` (synchronous).
- * Outputs may be NULL (not all).  Used as live roofline denominators. */
-sc_status sc_probe_peaks(double *shared_atomics_per_s, double *random_atomics_per_s, double *fp64_inst_per_s,
-                         void *stream);
 
 /* Text of the last error on the calling thread (always NUL-terminated). */
 sc_status sc_last_error(char *buf, size_t n);

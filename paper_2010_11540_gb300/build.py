@@ -2,7 +2,9 @@
 
 Each translation unit under csrc/ is compiled in parallel, then linked into
 paper_2010_11540_gb300/libsc.so with the static CUDA runtime.  Rebuilds only
-when a source or header is newer than the library.
+when a source or header is newer than the library.  build_probe() builds the
+bench's machine probes (bench_probe.cu at the repository root) into their own
+libsc_probe.so there; they are not part of libsc.
 """
 from __future__ import annotations
 
@@ -63,6 +65,25 @@ def build(force=False, verbose=False, extra=()):
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+PROBE_SRC = os.path.join(ROOT, "bench_probe.cu")
+PROBE_LIB = os.path.join(ROOT, "libsc_probe.so")
+
+
+def build_probe(force=False):
+    """Compile the bench-only machine probes into libsc_probe.so (repository root)."""
+    if not os.path.exists(PROBE_SRC):
+        return None
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= os.path.getmtime(PROBE_SRC):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp"
+    cmd = [NVCC, *ARCH, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

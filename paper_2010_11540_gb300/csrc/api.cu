@@ -105,7 +105,8 @@ template <class Head, class Mark, class Launch, class Blocks>
 sc_status tune_shape(sc_grid* g, TrackPlan* T, const sc_particles* p, Head&& head_params, Mark&& mark_params,
                      Launch&& launch, Blocks&& set_blocks) {
   const int64_t n = p->n;
-  const size_t qbytes = (size_t)g->nx * g->ny * g->nstack * 8, obytes = 8 * (size_t)g->nstack;
+  // the charge grid and its counters (out-of-grid per stacked grid, then the non-finite count)
+  const size_t qbytes = (size_t)g->nx * g->ny * g->nstack * 8, obytes = 8 * (size_t)(g->nstack + 1);
   const int kicks = T->n_kicks < kShapeTuneKicks ? T->n_kicks : kShapeTuneKicks;
   double* scratch = nullptr;
   unsigned char* saved = nullptr;
@@ -129,16 +130,21 @@ sc_status tune_shape(sc_grid* g, TrackPlan* T, const sc_particles* p, Head&& hea
   double* dst[6] = {q.x, q.px, q.y, q.py, q.sigma, q.psigma};
   cu(cudaMemcpyAsync(saved, g->Q, qbytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
   cu(cudaMemcpyAsync(saved + qbytes, g->n_out, obytes, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
-  for (int a = 0; a < 6 && st == SC_OK; ++a)
-    cu(cudaMemcpyAsync(dst[a], src[a], (size_t)n * 8, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
-  // the psc cache of the scratch bunch, and its charge (and cell cache) at the
-  // first marker when the lattice opens with one; otherwise each trial opens
-  // with the head segment's deposit into a cleared grid
-  if (st == SC_OK && cu(cudaMemsetAsync(g->Q, 0, qbytes, g->stream), "cudaMemsetAsync")) {
-    KPParams pro = T->prologue;
-    pro.x = q.x, pro.px = q.px, pro.y = q.y, pro.py = q.py, pro.sg = q.sigma, pro.ps = q.psigma;
-    st = launch(pro, !T->has_head);
-  }
+  // Before every timed trial: the scratch bunch as the caller's, its psc cache,
+  // and its charge (and cell cache) at the first marker when the lattice opens
+  // with one (otherwise the trial opens with the head segment's deposit into a
+  // cleared grid).  Every trial then runs the same first steps of the turn (a
+  // bunch tracked again and again through a part of the ring would not stay
+  // the workload: its optics need not be stable).
+  auto reset = [&]() {
+    for (int a = 0; a < 6 && st == SC_OK; ++a)
+      cu(cudaMemcpyAsync(dst[a], src[a], (size_t)n * 8, cudaMemcpyDeviceToDevice, g->stream), "cudaMemcpyAsync");
+    if (st == SC_OK && cu(cudaMemsetAsync(g->Q, 0, qbytes, g->stream), "cudaMemsetAsync")) {
+      KPParams pro = T->prologue;
+      pro.x = q.x, pro.px = q.px, pro.y = q.y, pro.py = q.py, pro.sg = q.sigma, pro.ps = q.psigma;
+      st = launch(pro, !T->has_head);
+    }
+  };
   auto capture = [&](cudaGraphExec_t* exec) -> sc_status {
     SC_CUDA(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
     sc_status r = SC_OK;
@@ -173,7 +179,7 @@ sc_status tune_shape(sc_grid* g, TrackPlan* T, const sc_particles* p, Head&& hea
       st = capture(&exec);
       float t_min = 0.f;
       for (int r = 0; r < 4 && st == SC_OK; ++r) {
-        if (T->has_head && !cu(cudaMemsetAsync(g->Q, 0, qbytes, g->stream), "cudaMemsetAsync")) break;
+        reset();
         cu(cudaEventRecord(e0, g->stream), "cudaEventRecord");
         cu(cudaGraphLaunch(exec, g->stream), "cudaGraphLaunch(shape trial)");
         cu(cudaEventRecord(e1, g->stream), "cudaEventRecord");
@@ -342,6 +348,7 @@ void set_deposit(KPParams& P, sc_grid* d) {
   P.gd = d->geom;
   P.Q = d->Q;
   P.n_out = d->n_out;
+  P.n_nan = d->n_nan;
 }
 
 // Elements of a segment: inline in the launch parameters when they fit,
@@ -358,8 +365,23 @@ void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, 
   }
 }
 
+sc_status check_grid_errors(sc_grid* g) {
+  if (tf32_error(g)) {
+    g->poisoned = 1;
+    return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait; the grid takes no more solves");
+  }
+  unsigned long long v = 0;
+  SC_CUDA(cudaMemcpy(&v, g->n_nan, 8, cudaMemcpyDeviceToHost));
+  if (v) {
+    SC_CUDA(cudaMemset(g->n_nan, 0, 8));
+    return set_error(SC_ERR_NAN, std::to_string(v) + " particle(s) with a non-finite position reached a deposit");
+  }
+  return SC_OK;
+}
+
 sc_status solve_dispatch(sc_grid* g, bool zero_q) {
-  if (g->precision == SC_SOLVE_TF32X3 || g->precision == SC_SOLVE_PIPE_TF32X3) return tf32_solve(g, zero_q);
+  if (g->poisoned) return set_error(SC_ERR_TIMEOUT, "a tensor-core solve on this grid gave up on a bounded wait");
+  if (split_solve(g->precision)) return tf32_solve(g, zero_q);
   if (g->precision == SC_SOLVE_PIPE_FP64) return pipe_solve(g, zero_q);
   return fft64_solve(g, zero_q);
 }
@@ -378,7 +400,7 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
       !std::isfinite(ymax))
     return set_error(SC_ERR_ARG, "grid extent must be finite with xmax > xmin, ymax > ymin");
   if (precision != SC_SOLVE_FP64 && precision != SC_SOLVE_TF32X3 && precision != SC_SOLVE_PIPE_FP64 &&
-      precision != SC_SOLVE_PIPE_TF32X3)
+      precision != SC_SOLVE_PIPE_TF32X3 && precision != SC_SOLVE_BF16X3)
     return set_error(SC_ERR_UNSUPPORTED, "unknown solve precision");
   sc_grid* g = new (std::nothrow) sc_grid();
   if (!g) return set_error(SC_ERR_OOM, "host allocation failed");
@@ -390,7 +412,7 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   g->zmin = zmin;
   g->zmax = zmax;
   g->precision = precision;
-  g->field32 = (precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3);
+  g->field32 = split_solve(precision);
   g->xmin = xmin;
   g->xmax = xmax;
   g->ymin = ymin;
@@ -408,6 +430,7 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   g->geom.nz = n_slices;
   g->geom.zmin = zmin;
   g->geom.inv_dz = n_slices > 1 ? 1.0 / ((zmax - zmin) / (double)n_slices) : 0.0;  // 1 / dz
+  tile_window(nx, ny, &g->geom.wx0, &g->geom.wy0, &g->geom.wnx, &g->geom.wny);
   sc_status st = SC_OK;
   cudaError_t e = cudaGetDevice(&g->device);
   if (e != cudaSuccess) {
@@ -429,20 +452,19 @@ sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, d
   }
   const size_t cells = (size_t)nx * ny * nstack;  // all stacked grids
   if ((e = cudaMalloc(&g->Q, cells * 8)) != cudaSuccess || (e = cudaMalloc(&g->E, cells * sizeof(double2))) != cudaSuccess ||
-      (e = cudaMalloc(&g->n_out, 8 * (size_t)nstack)) != cudaSuccess) {
+      (e = cudaMalloc(&g->n_out, 8 * (size_t)(nstack + 1))) != cudaSuccess) {
     st = cuda_error(e, "cudaMalloc(grid)");
     sc_destroy_grid(g);
     return st;
   }
   cudaMemsetAsync(g->Q, 0, cells * 8, g->stream);
   cudaMemsetAsync(g->E, 0, cells * sizeof(double2), g->stream);
-  cudaMemsetAsync(g->n_out, 0, 8 * (size_t)nstack, g->stream);
-  const bool tile = deposit_uses_tile(g);
-  const int tile_bytes = nx * ny * 8;  // one slice
-  g->dep_blocks = deposit_blocks_for(tile ? tile_bytes : 0, tile);
-  g->kp_blocks = kick_push_blocks_for(tile ? tile_bytes : 0, tile);
+  g->n_nan = g->n_out + nstack;
+  cudaMemsetAsync(g->n_out, 0, 8 * (size_t)(nstack + 1), g->stream);
+  g->dep_blocks = deposit_blocks_for(tile_bytes(g));
+  g->kp_blocks = kick_push_blocks_for(tile_bytes(g), true);
   g->kp_blocks_plain = kick_push_blocks_for(0, false);
-  st = (precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3) ? tf32_create(g)
+  st = split_solve(precision)                                                ? tf32_create(g)
        : (precision == SC_SOLVE_PIPE_FP64)                                    ? pipe_create(g)
                                                                               : fft64_create(g);
   if (st == SC_OK) {
@@ -484,7 +506,7 @@ sc_status sc_destroy_grid(sc_grid* g) {
   if (!g) return SC_OK;
   if (g->stream) cudaStreamSynchronize(g->stream);
   destroy_plan(g->track);
-  if (g->precision == SC_SOLVE_TF32X3 || g->precision == SC_SOLVE_PIPE_TF32X3)
+  if (split_solve(g->precision))
     tf32_destroy(g);
   else if (g->precision == SC_SOLVE_PIPE_FP64)
     pipe_destroy(g);
@@ -497,6 +519,7 @@ sc_status sc_destroy_grid(sc_grid* g) {
   cudaFree(g->n_out);
   cudaFree(g->stack_scale);
   cudaFree(g->el_stage);
+  cudaFree(g->sort_scratch);
   if (g->own_stream) cudaStreamDestroy(g->stream);
   delete g;
   return SC_OK;
@@ -510,6 +533,14 @@ sc_status sc_deposit(sc_grid* g, const sc_particles* p) {
   g->n_particles = p->n;
   if (p->n == 0) return SC_OK;
   return launch_deposit(g, p);
+}
+
+sc_status sc_sort_particles(sc_grid* g, const sc_particles* p, int32_t* perm) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  sc_status st = check_particles(p);
+  if (st) return st;
+  if (p->n == 0) return SC_OK;
+  return sort_particles(g, p, perm);
 }
 
 sc_status sc_solve(sc_grid* g) {
@@ -574,8 +605,7 @@ sc_status sc_grid_read(sc_grid* g, uint64_t* Q, double* Ex, double* Ey, int64_t*
     SC_CUDA(cudaMemcpy(&v, g->n_out, 8, cudaMemcpyDeviceToHost));
     *n_out = (int64_t)v;
   }
-  if (tf32_error(g)) return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
-  return SC_OK;
+  return check_grid_errors(g);
 }
 
 sc_status sc_set_longitudinal_kick(sc_grid* g, int enable) {
@@ -684,6 +714,17 @@ sc_status sc_grid_charge_device(sc_grid* g, uint64_t** Q, int64_t* cells) {
   return SC_OK;
 }
 
+sc_status sc_set_charge_reduce(sc_grid* g, sc_charge_reduce_fn fn, void* user, int64_t total_particles) {
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if (fn && (total_particles < 1 || total_particles > ((int64_t)1 << 62)))
+    return set_error(SC_ERR_ARG, "total_particles must be positive");
+  SC_CUDA(cudaStreamSynchronize(g->stream));
+  g->reduce_fn = fn;
+  g->reduce_user = fn ? user : nullptr;
+  g->reduce_total = fn ? total_particles : 0;
+  return SC_OK;
+}
+
 sc_status sc_set_particle_count(sc_grid* g, int64_t n_particles) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   if (n_particles < 0) return set_error(SC_ERR_ARG, "negative particle count");
@@ -695,7 +736,7 @@ sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_bea
                               int n_elems, int n_turns, double* diag) {
   if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
   sc_status st;
-  if ((st = check_particles(host))) return st;
+  if ((st = check_particles(host)) || (st = check_beam(b)) || (st = check_elements(lattice, n_elems))) return st;
   if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
   const int64_t n = host->n;
   if (n_turns == 0 || n == 0) return SC_OK;
@@ -721,7 +762,7 @@ sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_bea
   if ((st = sc_track_turns(g, &dev, b, lattice, n_elems, n_turns, diag))) return st;
   if ((st = copy_spread(&g->copies, g->stream, cudaMemcpyDeviceToHost, out))) return st;
   SC_CUDA(cudaStreamSynchronize(g->stream));
-  return SC_OK;
+  return check_grid_errors(g);
 }
 
 sc_status sc_get_solver_work(sc_grid* g, double* tensor_flops, double* fft_flops) {
@@ -788,6 +829,11 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   put(&g->kp_threads_set, sizeof g->kp_threads_set);
   put(&g->kp_trav_set, sizeof g->kp_trav_set);
   const std::vector<unsigned char> shape_key = key;  // what the kick/push shape depends on
+  put(&g->reduce_fn, sizeof g->reduce_fn);
+  put(&g->reduce_user, sizeof g->reduce_user);
+  put(&g->reduce_total, sizeof g->reduce_total);
+  // the solve's normalisation: the whole bunch when its particles are sharded over ranks
+  const int64_t n_norm = g->reduce_fn ? g->reduce_total : p->n;
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
   put(&g->trace, sizeof g->trace);
@@ -853,7 +899,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
       SC_CUDA(cudaMalloc(&T->d_base, sizeof(double*)));
       SC_CUDA(cudaMalloc(&T->d_turn, sizeof(int)));
     }
-    g->n_particles = p->n;
+    g->n_particles = n_norm;
     const double K = kick_strength(b);
     // prologue of every call: the ps-dependent quantities of each particle, and
     // for lattices that open with a marker the charge (and cell cache) there
@@ -919,7 +965,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     T->kp_trav = g->nz > 1 ? -1 : g->kp_trav_set;  // sliced grids always use chunks
     auto set_blocks = [&] {
       const int th = T->kp_threads > 0 ? T->kp_threads : kick_push_max_threads(g->field32);
-      T->kp_blocks_dep = kick_push_blocks_at(g->nx * g->ny * 8, deposit_uses_tile(g), g->field32, th);
+      T->kp_blocks_dep = kick_push_blocks_at(tile_bytes(g), true, g->field32, th);
       T->kp_blocks_plain = kick_push_blocks_at(0, false, g->field32, th);
     };
     set_blocks();
@@ -950,6 +996,10 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     if (!cst && T->has_head) cst = launch(head_params(p), !marks.empty());
     for (size_t k = 0; !cst && k < marks.size(); ++k) {
       if (g->trace && cudaEventRecordWithFlags(T->ev[3 * k], g->stream, cudaEventRecordExternal) != cudaSuccess) cst = set_error(SC_ERR_CUDA, "event");
+      // a sharded bunch: the ranks' charges summed in place (the callback enqueues the reduction)
+      if (!cst && g->reduce_fn &&
+          g->reduce_fn((uint64_t*)g->Q, (int64_t)g->nx * g->ny * g->nstack, (void*)g->stream, g->reduce_user) != 0)
+        cst = set_error(SC_ERR_CUDA, "the charge reduction callback failed");
       // the solve clears the charge after reading it, ready for this marker's deposit
       if (!cst) cst = solve_dispatch(g, true);
       if (cst) break;
@@ -1000,7 +1050,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     SC_CUDA(cudaMemcpyAsync(T->d_base, &T->d_diag, sizeof(double*), cudaMemcpyHostToDevice, g->stream));
     SC_CUDA(cudaMemsetAsync(T->d_turn, 0, sizeof(int), g->stream));
   }
-  g->n_particles = p->n;
+  g->n_particles = n_norm;
   {
     KPParams P = T->prologue;
     P.traversal = T->kp_trav;
@@ -1030,6 +1080,7 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     SC_CUDA(cudaMemcpyAsync(diag, T->d_diag, (size_t)n_turns * 14 * sizeof(double), cudaMemcpyDeviceToHost,
                             g->stream));
     SC_CUDA(cudaStreamSynchronize(g->stream));
+    return check_grid_errors(g);
   }
   return SC_OK;
 }

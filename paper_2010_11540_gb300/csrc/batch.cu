@@ -178,7 +178,7 @@ template <class Capture, class Blocks>
 sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, const std::vector<int64_t>& counts,
                            const std::vector<KPParams>& descs, Capture&& capture, Blocks&& set_blocks) {
   const int nb = B->n_bunches;
-  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  const bool f32 = split_solve(B->precision);
   cudaStream_t S = B->stream;
   const int kicks = T->n_kicks < kShapeTuneKicks ? T->n_kicks : kShapeTuneKicks;
   int64_t total = 0;
@@ -204,7 +204,7 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
     }
   }
   size_t saved_bytes = 0;
-  for (sc_grid* g : B->cls) saved_bytes += cells_of(g) * g->nstack * 8 + 8 * (size_t)g->nstack;
+  for (sc_grid* g : B->cls) saved_bytes += cells_of(g) * g->nstack * 8 + 8 * (size_t)(g->nstack + 1);
   double* scratch = nullptr;
   KPParams* d_sdescs = nullptr;
   int4* d_blk = nullptr;
@@ -230,16 +230,24 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
   }
   cu(cudaEventCreate(&e0), "cudaEventCreate");
   cu(cudaEventCreate(&e1), "cudaEventCreate");
-  // scratch copies of the bunches and descriptors that point at them
+  // scratch copies of the bunches (refreshed before every trial) and descriptors that point at them
   std::vector<KPParams> sd = descs;
+  auto copy_bunches = [&]() {
+    size_t o = 0;
+    for (int b = 0; b < nb && st == SC_OK; ++b) {
+      const sc_particles& h = bunches[b].particles;
+      const size_t n = (size_t)h.n;
+      double* base = scratch + 6 * o;
+      const double* src[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
+      for (int a = 0; a < 6 && n > 0; ++a)
+        cu(cudaMemcpyAsync(base + a * n, src[a], n * 8, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
+      o += n;
+    }
+  };
   size_t off = 0;
   for (int b = 0; b < nb && st == SC_OK; ++b) {
-    const sc_particles& h = bunches[b].particles;
-    const size_t n = (size_t)h.n;
+    const size_t n = (size_t)bunches[b].particles.n;
     double* base = scratch + 6 * off;
-    const double* src[6] = {h.x, h.px, h.y, h.py, h.sigma, h.psigma};
-    for (int a = 0; a < 6 && n > 0; ++a)
-      cu(cudaMemcpyAsync(base + a * n, src[a], n * 8, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
     for (int L = 0; L < T->n_launches; ++L) {
       KPParams& P = sd[(size_t)L * nb + b];
       P.x = base, P.px = base + n, P.y = base + 2 * n, P.py = base + 3 * n, P.sg = base + 4 * n,
@@ -252,7 +260,7 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
   auto grids = [&](bool save) {
     size_t o = 0;
     for (sc_grid* g : B->cls) {
-      const size_t qb = cells_of(g) * g->nstack * 8, ob = 8 * (size_t)g->nstack;
+      const size_t qb = cells_of(g) * g->nstack * 8, ob = 8 * (size_t)(g->nstack + 1);
       if (save) {
         cu(cudaMemcpyAsync(saved + o, g->Q, qb, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
         cu(cudaMemcpyAsync(saved + o + qb, g->n_out, ob, cudaMemcpyDeviceToDevice, S), "cudaMemcpyAsync");
@@ -269,7 +277,6 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
   if (st == SC_OK) grids(true);
   int best_th = ths[0], best_w = ws[0];
   float best = 0.f;
-  bool first = true;
   for (int th : ths) {
     for (int w : ws) {
       if (st != SC_OK) break;
@@ -278,15 +285,6 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
       set_blocks(w, bl);
       if (bl.empty()) continue;
       cu(cudaMemcpyAsync(d_blk, bl.data(), bl.size() * sizeof(int4), cudaMemcpyHostToDevice, S), "cudaMemcpyAsync");
-      if (first) {
-        // the psc and quadrupole caches of the scratch bunches, and their charge at the first
-        // marker when the lattices open with one (else each trial opens with the head's deposit)
-        clear_q();
-        if (st == SC_OK)
-          st = launch_kick_push_batched(d_sdescs, d_blk, (int)bl.size(), T->tile_cells, f32, T->launch_cache[0] != 0,
-                                        T->launch_xe[0] != 0, S, th);
-        first = false;
-      }
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
       if (st == SC_OK) st = capture(d_sdescs, d_blk, (int)bl.size(), kicks, false, &graph);
@@ -294,7 +292,14 @@ sc_status tune_batch_shape(sc_batch* B, BatchPlan* T, const sc_bunch* bunches, c
       if (graph) cudaGraphDestroy(graph);
       float t_min = 0.f;
       for (int r = 0; r < 4 && st == SC_OK; ++r) {
-        if (T->has_head) clear_q();
+        // every trial from the bunches as the caller's: their psc and quadrupole caches, and
+        // their charge at the first marker when the lattices open with one (else the trial
+        // opens with the head's deposit into cleared grids)
+        copy_bunches();
+        clear_q();
+        if (st == SC_OK)
+          st = launch_kick_push_batched(d_sdescs, d_blk, (int)bl.size(), T->tile_cells, f32, T->launch_cache[0] != 0,
+                                        T->launch_xe[0] != 0, S, th);
         cu(cudaEventRecord(e0, S), "cudaEventRecord");
         cu(cudaGraphLaunch(exec, S), "cudaGraphLaunch(shape trial)");
         cu(cudaEventRecord(e1, S), "cudaEventRecord");
@@ -366,7 +371,7 @@ sc_status sc_create_batch(sc_batch** out, const sc_grid_spec* grids, int n_bunch
     sc_status st = create_grid(&g, s.nx, s.ny, s.xmin, s.xmax, s.ymin, s.ymax, 1, 0.0, 0.0, count[c], precision,
                                B->stream);
     if (st == SC_OK) {
-      const bool f32 = precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3;
+      const bool f32 = split_solve(precision);
       const size_t bytes = (size_t)count[c] * (f32 ? sizeof(float) : sizeof(double));
       cudaError_t e = cudaMalloc(&g->stack_scale, bytes);
       if (e != cudaSuccess) {
@@ -416,7 +421,7 @@ sc_status sc_destroy_batch(sc_batch* B) {
 
 sc_status sc_batch_set_kick_push_shape(sc_batch* B, int threads, int waves) {
   if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
-  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  const bool f32 = split_solve(B->precision);
   if (threads < 0 || threads % 32 != 0 || threads > kick_push_batched_threads(f32))
     return set_error(SC_ERR_ARG, "batched kick/push block size must be 0 or a multiple of 32 up to the maximum");
   if (waves < 0 || waves > 64) return set_error(SC_ERR_ARG, "waves must be in 0..64");
@@ -429,7 +434,7 @@ sc_status sc_batch_get_kick_push_shape(sc_batch* B, int* threads, int* waves, do
   if (!B) return set_error(SC_ERR_ARG, "batch is NULL");
   const BatchPlan* T = B->plan;
   if (!T || !T->exec) return set_error(SC_ERR_ARG, "no captured turn on this batch");
-  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  const bool f32 = split_solve(B->precision);
   if (threads) *threads = T->kp_threads > 0 ? T->kp_threads : kick_push_batched_threads(f32);
   if (waves) *waves = T->kp_waves;
   if (trial_us) *trial_us = T->trial_us;
@@ -519,7 +524,7 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
   put(&want_diag, sizeof want_diag);
   put(&B->trace, sizeof B->trace);
 
-  const bool f32 = B->precision == SC_SOLVE_TF32X3 || B->precision == SC_SOLVE_PIPE_TF32X3;
+  const bool f32 = split_solve(B->precision);
   BatchPlan* T = B->plan;
   if (!T || T->key != key) {
     destroy_batch_plan(T);
@@ -581,10 +586,10 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
         SC_CUDA(cudaMemcpy(g->stack_scale, sd.data(), sd.size() * sizeof(double), cudaMemcpyHostToDevice));
       }
     }
-    // blocks of the batched launch: the shared-memory tile holds the largest class grid that fits
+    // blocks of the batched launch: the shared-memory tile holds the largest tile window of the classes
     int tile_cells = 0;
     for (sc_grid* g : B->cls)
-      if (deposit_uses_tile(g)) tile_cells = std::max(tile_cells, (int)cells_of(g));
+      tile_cells = std::max(tile_cells, g->geom.wnx * g->geom.wny);
     T->tile_cells = tile_cells;
     // ---- descriptors: prologue, head, one per marker ------------------------------
     T->n_launches = 1 + (T->has_head ? 1 : 0) + n_marks;
@@ -855,9 +860,12 @@ sc_status sc_batch_read(sc_batch* B, int b, uint64_t* Q, double* Ex, double* Ey,
     SC_CUDA(cudaMemcpy(&v, g->n_out + B->idx[b], 8, cudaMemcpyDeviceToHost));
     *n_out = (int64_t)v;
   }
-  for (sc_grid* c : B->cls)
-    if (tf32_error(c)) return set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
-  return SC_OK;
+  sc_status first = SC_OK;
+  for (sc_grid* c : B->cls) {
+    const sc_status st = check_grid_errors(c);
+    if (st && (!first || st == SC_ERR_TIMEOUT)) first = st;
+  }
+  return first;
 }
 
 sc_status sc_batch_get_solver_tiling(sc_batch* B, int b, int* choice, char* desc, size_t n) {

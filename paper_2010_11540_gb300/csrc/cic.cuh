@@ -19,15 +19,23 @@ namespace sc {
 // grid and the cell index is k*nx*ny + j*nx + i.
 template <bool FRAC>
 __device__ __forceinline__ int locate(const GridGeom& g, double x, double y, double sg, int2& a, double& fx,
-                                      double& fy, int& k) {
+                                      double& fy, int& i, int& j, int& k) {
   const double xi = __dmul_rn(__dsub_rn(x, g.xmin), g.inv_hx);
   const double eta = __dmul_rn(__dsub_rn(y, g.ymin), g.inv_hy);
-  int i = 0, j = 0;
+  i = 0;
+  j = 0;
   k = 0;
   bool in = cic_split(xi, g.nx - 1, i, a.x, FRAC ? &fx : nullptr);
   in = cic_split(eta, g.ny - 1, j, a.y, FRAC ? &fy : nullptr) && in;
   if (g.nz > 1) in = floor_index(__dmul_rn(__dsub_rn(sg, g.zmin), g.inv_dz), g.nz, k) && in;
   return in ? (k * g.ny + j) * g.nx + i : -1;
+}
+
+template <bool FRAC>
+__device__ __forceinline__ int locate(const GridGeom& g, double x, double y, double sg, int2& a, double& fx,
+                                      double& fy, int& k) {
+  int i, j;
+  return locate<FRAC>(g, x, y, sg, a, fx, fy, i, j, k);
 }
 
 template <bool FRAC>
@@ -39,7 +47,8 @@ __device__ __forceinline__ int locate(const GridGeom& g, double x, double y, dou
 
 // The four CIC weights in 2^-20 fixed point per axis: a (from locate), b =
 // 2^20 - a; the products sum to exactly 2^40 (32 x 32 -> 64-bit multiplies).
-// dst is either a shared-memory tile or the global grid (same [j][i] layout).
+// dst is either a shared-memory tile or the global grid (same [j][i] layout,
+// row length nx).
 __device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int cell, int2 a) {
   const unsigned ax = (unsigned)a.x, ay = (unsigned)a.y;
   const unsigned bx = 1048576u - ax, by = 1048576u - ay;
@@ -50,20 +59,93 @@ __device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int ce
   atomicAdd(q + nx + 1, (unsigned long long)ax * ay);
 }
 
-// Deposit into a block's shared tile when the particle's slice k is the
-// tile's, else straight into the global grid.  The tile takes the slice of the
-// first particle that reaches this (tile_k, shared, starts at -1).
-__device__ __forceinline__ void deposit_tiled(unsigned long long* tile, int* tile_k, unsigned long long* Q,
-                                              const GridGeom& g, int cell, int k, int2 a) {
-  int tk = *(volatile int*)tile_k;
-  if (tk < 0) {
-    const int prev = atomicCAS(tile_k, -1, k);
-    tk = prev < 0 ? k : prev;
+// Deposit target of a particle in cell (i, j) of slice k (`cell` its global
+// index, -1 outside): the block's tile when it holds slice k (the tile takes
+// the slice of the first particle that asks, tile_k starting at -1) and the
+// tile's window holds the cell's four nodes -- key = the cell's lower-left
+// node in the tile -- else the global grid -- key = kGlobalKey | cell.  -1:
+// nothing to deposit.
+constexpr int kGlobalKey = 1 << 29;
+__device__ __forceinline__ int deposit_key(bool use_tile, int* tile_k, const GridGeom& g, int cell, int i, int j,
+                                           int k) {
+  if (cell < 0) return -1;
+  if (use_tile) {
+    int tk = *(volatile int*)tile_k;
+    if (tk < 0) {
+      const int prev = atomicCAS(tile_k, -1, k);
+      tk = prev < 0 ? k : prev;
+    }
+    const int li = i - g.wx0, lj = j - g.wy0;
+    if (tk == k && (unsigned)li < (unsigned)(g.wnx - 1) && (unsigned)lj < (unsigned)(g.wny - 1))
+      return lj * g.wnx + li;
   }
-  if (tk == k)
-    deposit4(tile, g.nx, cell - k * g.nx * g.ny, a);
+  return kGlobalKey | cell;
+}
+
+// The four CIC adds of one particle at its target key (deposit_key; -1: none).
+__device__ __forceinline__ void deposit_at(int key, int2 a, unsigned long long* tile, int wnx, unsigned long long* Q,
+                                           int nx) {
+  if (key < 0) return;
+  if (key & kGlobalKey)
+    deposit4(Q, nx, key & (kGlobalKey - 1), a);
   else
-    deposit4(Q, g.nx, cell, a);
+    deposit4(tile, wnx, key, a);
+}
+
+// One warp's CIC deposits (Sec. IV-A), the lanes of `mask` calling together,
+// each with its target key (deposit_key) and fixed-point weights a.  Lanes
+// next to each other with the same key form a run (a bunch ordered by cell
+// puts a warp's particles in one or two runs); a run's four node sums are
+// formed in registers -- over the run, sum bx by = n 2^40 - 2^20 (Sax + Say)
+// + Saxay, sum ax by = 2^20 Sax - Saxay, sum bx ay = 2^20 Say - Saxay, sum
+// ax ay = Saxay, exact in 64-bit integers -- and its first lane issues the
+// four atomic adds.  Integer sums do not depend on their order, so the grid
+// gets the same bits as with one atomic per weight.  When no two neighbouring
+// lanes share a key each lane adds its own.  (For particles in random order
+// the test itself costs more than it saves: callers use deposit_at there.)
+__device__ __forceinline__ void deposit_warp(unsigned mask, int key, int2 a, unsigned long long* tile, int wnx,
+                                             unsigned long long* Q, int nx) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(mask, key, 1);
+  const bool head = lane == 0 || !((mask >> (lane - 1)) & 1u) || prev != key;
+  const unsigned heads = __ballot_sync(mask, head);
+  if (heads == mask) {
+    deposit_at(key, a, tile, wnx, Q, nx);
+    return;
+  }
+  // suffix sums over each run by doubling: after the step of offset d, a lane
+  // holds the sums of its run's lanes [lane, lane + 2d)
+  unsigned sx = (unsigned)a.x, sy = (unsigned)a.y;
+  unsigned long long sxy = (unsigned long long)sx * sy;
+  const int rid = __popc(heads & ((2u << lane) - 1u));  // runs that start at or below this lane
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned ox = __shfl_down_sync(mask, sx, d);
+    const unsigned oy = __shfl_down_sync(mask, sy, d);
+    const unsigned long long oxy = __shfl_down_sync(mask, sxy, d);
+    const int src = lane + d;
+    if (src < 32 && ((mask >> src) & 1u) && __popc(heads & ((2u << src) - 1u)) == rid) {
+      sx += ox;
+      sy += oy;
+      sxy += oxy;
+    }
+  }
+  if (head && key >= 0) {
+    // run length: the lanes of the mask from this one up to the next run's head
+    const unsigned above = heads & ~((2u << lane) - 1u);
+    const unsigned span = above ? ((1u << (__ffs(above) - 1)) - 1u) : 0xffffffffu;
+    const unsigned long long n = (unsigned long long)__popc(mask & span & ~((1u << lane) - 1u));
+    const unsigned long long one = 1048576ull;
+    const unsigned long long w11 = sxy, w10 = one * sx - sxy, w01 = one * sy - sxy;
+    const unsigned long long w00 = (n << 40) - one * ((unsigned long long)sx + sy) + sxy;
+    const bool global = key & kGlobalKey;
+    const int stride = global ? nx : wnx;
+    unsigned long long* q = global ? Q + (key & (kGlobalKey - 1)) : tile + key;
+    atomicAdd(q, w00);
+    atomicAdd(q + 1, w10);
+    atomicAdd(q + stride, w01);
+    atomicAdd(q + stride + 1, w11);
+  }
 }
 
 // Cubic Bernstein weights b_m(t) and their derivatives (R = double for the
@@ -125,14 +207,31 @@ __device__ __forceinline__ void tile_zero(unsigned long long* tile, int cells) {
   for (int c = threadIdx.x; c < cells; c += blockDim.x) tile[c] = 0ull;
 }
 
-// Add the non-zero bins of a block's tile into the global grid (whole block;
-// caller synchronises before).  This is the only cross-block reduction of the
-// deposit.
-__device__ __forceinline__ void tile_flush(const unsigned long long* tile, unsigned long long* Q, int cells) {
+// Add the non-zero bins of a block's tile into the global grid Q (one
+// slice; whole block; caller synchronises before): bin (li, lj) of the window
+// is node (wx0 + li, wy0 + lj).  This is the only cross-block reduction of
+// the deposit.
+__device__ __forceinline__ void tile_flush(const unsigned long long* tile, unsigned long long* Q, const GridGeom& g) {
+  const int cells = g.wnx * g.wny;
   for (int c = threadIdx.x; c < cells; c += blockDim.x) {
     const unsigned long long v = tile[c];
-    if (v) atomicAdd(Q + c, v);
+    if (v) {
+      const int lj = c / g.wnx, li = c - lj * g.wnx;
+      atomicAdd(Q + (size_t)(g.wy0 + lj) * g.nx + g.wx0 + li, v);
+    }
   }
+}
+
+// A non-finite coordinate (NaN or infinity), tested on the bits: no FP64 instruction.
+__device__ __forceinline__ bool nonfinite(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
+}
+
+// A particle the deposit found outside grid g: count it as non-finite when its
+// position (or, on a sliced grid, its sigma) is (rare path, one atomic).
+__device__ __forceinline__ void count_nonfinite(const GridGeom& g, double x, double y, double sg,
+                                                unsigned long long* n_nan) {
+  if (n_nan && (nonfinite(x) || nonfinite(y) || (g.nz > 1 && nonfinite(sg)))) atomicAdd(n_nan, 1ull);
 }
 
 // Block-wide sum of per-thread out-of-grid counts into a global counter.

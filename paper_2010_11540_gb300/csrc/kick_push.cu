@@ -1,8 +1,9 @@
 // Fused space-charge step for one location: field gather + kick (Sec. IV kick
 // equation; bilinear node fields, or the Bezier surface of the potential, plus
 // the longitudinal kick on sliced pipe grids), push through the segment's
-// elements (Sec. III), and CIC deposit of the new positions (Sec. IV-A) into a
-// per-block shared-memory uint64 tile flushed once per block.  One thread per
+// elements (Sec. III), and CIC deposit of the new positions (Sec. IV-A) into
+// a per-block shared-memory uint64 tile (the grid, or its centred window)
+// flushed once per block.  One thread per
 // particle, persistent grid over SoA float64 state; one launch serves one grid
 // (kick_push_kernel) or every bunch of a batch (kick_push_batched).
 #include <cmath>
@@ -218,17 +219,14 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
     if (P.do_deposit) {
       double fx = 0.0, fy = 0.0;
       int2 a = make_int2(0, 0);
-      int kz;
-      const int cell = locate<!F32>(P.gd, s.x, s.y, s.sg, a, fx, fy, kz);
-      if (cell >= 0) {
-        if (use_tile)
-          deposit_tiled(tile, tile_k, P.Q, P.gd, cell, kz, a);
-        else
-          deposit4(P.Q, P.gd.nx, cell, a);
-      } else {
+      int i, j, kz;
+      const int cell = locate<!F32>(P.gd, s.x, s.y, s.sg, a, fx, fy, i, j, kz);
+      if (cell < 0) {
         ++out;
+        count_nonfinite(P.gd, s.x, s.y, s.sg, P.n_nan);
         a = make_int2(0, 0);
       }
+      deposit_at(deposit_key(use_tile, tile_k, P.gd, cell, i, j, kz), a, tile, P.gd.wnx, P.Q, P.gd.nx);
       if (CACHE) {
         P.cell[p] = cell;
         if (F32)
@@ -249,19 +247,19 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
     count_out(out, P.n_out);
     if (use_tile) {
       __syncthreads();
-      if (*tile_k >= 0) tile_flush(tile, P.Q + (size_t)*tile_k * cells, cells);
+      if (*tile_k >= 0) tile_flush(tile, P.Q + (size_t)*tile_k * cells, P.gd);
     }
   }
 }
 
-// One grid, one location.  TILE: the deposit grid fits the shared-memory tile;
+// One grid, one location.  TILE: the launch deposits (through the block's tile);
 // XE: thick sextupoles, exact dipoles or the Bezier gather may occur.
 template <bool TILE, bool CACHE, bool F32, bool XE>
 __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const __grid_constant__ KPParams P) {
   extern __shared__ unsigned long long tile[];
   __shared__ int tile_k;  // slice held by the tile (-1: not yet claimed)
   if (TILE) {
-    tile_zero(tile, P.gd.nx * P.gd.ny);
+    tile_zero(tile, P.gd.wnx * P.gd.wny);
     if (threadIdx.x == 0) tile_k = P.gd.nz > 1 ? -1 : 0;
   }
   pdl_wait();  // fields, charge grid and particles of the previous kernels
@@ -284,7 +282,7 @@ __global__ void __launch_bounds__(kp_max_threads<F32>()) kick_push_kernel(const 
 // Many bunches, one location each, one launch.  Block b works for bunch
 // blocks[b].x (its descriptor descs[bunch], copied to shared memory) on the
 // contiguous chunk blocks[b].y of blocks[b].z equal chunks of that bunch.
-// The bunch's deposit uses the tile when its grid fits tile_cells.
+// The bunch's deposit uses the tile when its grid's tile window fits tile_cells.
 template <bool CACHE, bool F32, bool XE>
 __global__ void __launch_bounds__(kpb_max_threads<F32>())
     kick_push_batched(const KPParams* __restrict__ descs, const int4* __restrict__ blocks, int tile_cells) {
@@ -299,9 +297,9 @@ __global__ void __launch_bounds__(kpb_max_threads<F32>())
     for (int w = threadIdx.x; w < (int)(sizeof(KPParams) / 8); w += blockDim.x) dst[w] = src[w];
   }
   __syncthreads();
-  const bool use_tile = sP.do_deposit && sP.gd.nx * sP.gd.ny <= tile_cells;
+  const bool use_tile = sP.do_deposit && sP.gd.wnx * sP.gd.wny <= tile_cells;
   if (use_tile) {
-    tile_zero(tile, sP.gd.nx * sP.gd.ny);
+    tile_zero(tile, sP.gd.wnx * sP.gd.wny);
     if (threadIdx.x == 0) tile_k = sP.gd.nz > 1 ? -1 : 0;
   }
   pdl_wait();
@@ -346,7 +344,7 @@ int min_blocks(int smem, bool tile) {
   for (int v = 0; v < 8; ++v) {
     const bool cache = v & 4, f32 = v & 2, xe = v & 1;
     const KPKernel k = kp_kernel(tile, cache, f32, xe);
-    if (tile) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (tile) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, f32 ? kp_max_threads<true>() : kp_max_threads<false>(),
                                                   tile ? smem : 0);
@@ -372,7 +370,7 @@ int kick_push_blocks_at(int smem_bytes, bool tile, bool f32, int threads) {
   int best = 1 << 30;
   for (int v = 0; v < 4; ++v) {
     const KPKernel k = kp_kernel(tile, v & 2, f32, v & 1);
-    if (tile) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (tile) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, tile ? smem_bytes : 0);
     best = per < best ? per : best;
@@ -381,7 +379,7 @@ int kick_push_blocks_at(int smem_bytes, bool tile, bool f32, int threads) {
 }
 
 sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cudaStream_t s, int threads) {
-  const bool tile = P.do_deposit && dep && deposit_uses_tile(dep);
+  const bool tile = P.do_deposit && dep;
   const bool cache = P.cell != nullptr;
   const bool f32 = P.field32 != 0;
   const bool xe = P.has_xe != 0 || P.bezier != 0;
@@ -389,7 +387,7 @@ sc_status launch_kick_push(const KPParams& P, const sc_grid* dep, int blocks, cu
   if (threads <= 0) threads = kick_push_max_threads(f32);
   const int64_t need = (P.n + threads - 1) / threads;
   if (need < blocks) blocks = (int)(need > 0 ? need : 1);
-  const int smem = tile ? dep->nx * dep->ny * 8 : 0;
+  const int smem = tile ? tile_bytes(dep) : 0;
   SC_CUDA(launch_pdl(kp_kernel(tile, cache, f32, xe), dim3(blocks), dim3(threads), (size_t)smem, s, P));
   return SC_OK;
 }
@@ -403,7 +401,7 @@ int kick_push_batched_resident(int smem_bytes, bool f32, bool cache, int threads
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   for (int v = 0; v < 8; ++v) {
     const KPBatched k = kp_batched(v & 4, v & 2, v & 1);
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes);
   }
   for (int xe = 0; xe < 2; ++xe) {
     int p = 0;

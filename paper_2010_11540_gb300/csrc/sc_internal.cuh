@@ -12,6 +12,11 @@
 
 namespace sc {
 
+// Solve forms whose fields are float32 (tensor-core split-precision GEMMs).
+inline bool split_solve(int precision) {
+  return precision == SC_SOLVE_TF32X3 || precision == SC_SOLVE_PIPE_TF32X3 || precision == SC_SOLVE_BF16X3;
+}
+
 // ---------------------------------------------------------------------------
 // Error reporting (thread-local last error, status codes of sc.h)
 // ---------------------------------------------------------------------------
@@ -60,7 +65,14 @@ struct GridGeom {
   // cell indices then carry the slice offset k * nx * ny
   int nz;
   double zmin, inv_dz;
+  // deposit tile window: nodes [wx0, wx0 + wnx) x [wy0, wy0 + wny) of one
+  // slice, held in a block's shared memory (the whole slice when it fits in
+  // kTileBytes, else the centred window that does)
+  int wx0, wy0, wnx, wny;
 };
+
+// Shared memory of a block's deposit tile (uint64 per node of its window).
+constexpr int kTileBytes = 200 * 1024;
 
 // Element compiled for the kernels: the user's sc_element plus per-element
 // constants precomputed on the host in float64 (see compile_elements).
@@ -96,6 +108,7 @@ struct KPParams {
   GridGeom gd;
   unsigned long long* Q;      // uint64 charge of the deposit grid
   unsigned long long* n_out;  // running count of particles outside the deposit grid
+  unsigned long long* n_nan;  // running count of those with a non-finite x, y (or sigma on sliced grids)
   // beam constants
   double beta0_sq, inv_gamma0_sq;
   const DevElem* el;  // device array of the segment's compiled elements, or NULL: use inl
@@ -214,6 +227,8 @@ struct sc_grid {
   double2* E;                 // [nstack][ny][nx] (Ex, Ey); float32 pairs in the first half when field32
   int field32;                // the solve writes float32 fields (SC_SOLVE_TF32X3)
   unsigned long long* n_out;  // device counter (one per stacked grid in a batch class)
+  unsigned long long* n_nan;  // device counter of non-finite particles seen by deposits (n_out + nstack)
+  int poisoned;               // a tensor-core solve gave up on a bounded wait: no further solves
   int64_t n_particles;        // particle count of the last deposit (normalises Q)
   sc::Fft64Plan fft;
   sc::PipePlan pipe;
@@ -239,12 +254,22 @@ struct sc_grid {
   double* host_stage;          // device copy of sc_track_turns_host's particles [6][cap]
   int64_t host_stage_cap;
   sc::CopyStreams* copies;     // streams the host copies are spread over (created on first use)
+  void* sort_scratch;          // sc_sort_particles' keys, indices, gather buffer and sort storage
+  size_t sort_cap;
+  const double* sorted_x;      // the bunch (x array, count) this grid last ordered by cell
+  int64_t sorted_n;
+  // charge reduction across the ranks of a sharded bunch (sc_set_charge_reduce)
+  sc_charge_reduce_fn reduce_fn;
+  void* reduce_user;
+  int64_t reduce_total;        // particles of the whole bunch (normalises the solve)
 };
 
 namespace sc {
 
 // deposit.cu
 sc_status launch_deposit(sc_grid* g, const sc_particles* p);
+// reorder the particles by their cell on g (stable); perm_out (device, n, or NULL) gets the old indices
+sc_status sort_particles(sc_grid* g, const sc_particles* p, int32_t* perm_out);
 // kick_push.cu
 // blocks: dep->kp_blocks when depositing into dep, else the kick grid's kp_blocks_plain.
 // threads: block size (0: the variant's largest); blocks as above.
@@ -254,15 +279,17 @@ int kick_push_max_threads(bool f32);
 // variants of this field type; smem_bytes: the deposit tile when tile)
 int kick_push_blocks_at(int smem_bytes, bool tile, bool f32, int threads);
 // Batched form: descs[bunch] per bunch, blocks[b] = (bunch, chunk, chunks of that bunch, 0) per block;
-// deposits of grids with at most tile_cells nodes go through the shared-memory tile.
+// deposits of grids whose tile window has at most tile_cells nodes go through the shared-memory tile.
 // threads: block size (0: the field type's largest, kick_push_batched_threads)
 sc_status launch_kick_push_batched(const KPParams* descs, const int4* blocks, int n_blocks, int tile_cells, bool f32,
                                    bool cache, bool xe, cudaStream_t s, int threads = 0);
 int kick_push_batched_threads(bool f32);
 // resident blocks on the device at this block size (0: the largest)
 int kick_push_batched_resident(int smem_bytes, bool f32, bool cache, int threads = 0);
-bool deposit_uses_tile(const sc_grid* g);
-int deposit_blocks_for(int smem_bytes, bool tile);
+// shared memory of a grid's deposit tile; the tile window of an nx x ny grid
+int tile_bytes(const sc_grid* g);
+void tile_window(int nx, int ny, int* wx0, int* wy0, int* wnx, int* wny);
+int deposit_blocks_for(int smem_bytes);
 int kick_push_blocks_for(int smem_bytes, bool tile);
 // solve_fft64.cu
 sc_status fft64_create(sc_grid* g);
@@ -303,6 +330,10 @@ void set_kick(KPParams& P, const sc_grid* g, double kl, double gamma0);
 void set_deposit(KPParams& P, sc_grid* d);
 void set_elements(KPParams& P, const sc_element* host, int n, const sc_beam* b, const DevElem* dev);
 sc_status solve_dispatch(sc_grid* g, bool zero_q);
+// After a synchronisation: SC_ERR_TIMEOUT (and the grid refuses further solves)
+// when a tensor-core solve gave up on a bounded wait, else SC_ERR_NAN (and the
+// count is cleared) when deposits met particles with a non-finite position.
+sc_status check_grid_errors(sc_grid* g);
 // Grid construction shared by sc_create_grid_sliced and batches: nstack stacked
 // grids; n_slices > 1 slices them by sigma (then nstack == n_slices).
 sc_status create_grid(sc_grid** out, int nx, int ny, double xmin, double xmax, double ymin, double ymax,

@@ -1,8 +1,10 @@
 // Field solves as dense DFT / sine-transform GEMMs on the 5th-generation tensor
-// cores (tcgen05, kind::tf32), operands staged by TMA into 128-byte-swizzled
-// shared memory, accumulators in TMEM, 3-term split precision:
-//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,   a_hi = tf32(a), a_lo = tf32(a - a_hi),
-// accumulated in FP32.
+// cores (tcgen05), operands staged by TMA into 128-byte-swizzled shared
+// memory, accumulators in TMEM, 3-term split precision:
+//   a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,   a_hi = r(a), a_lo = r(a - a_hi),
+// accumulated in FP32, with r the rounding to TF32 (kind::tf32, operands kept
+// as fp32) or, for the open-boundary solve only, to BF16 (kind::f16 with bf16
+// operands, half the operand bytes; 8 + 8 significant bits per split value).
 //
 // The convolution of Hockney's method (zero-padded doubled grid, Mx = 2nx,
 // My = 2ny) with the centred-difference field kernels Dx, Dy (spectra i Sx,
@@ -34,6 +36,7 @@
 // candidates when a grid is created.
 #include <cooperative_groups.h>
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -48,7 +51,23 @@ namespace sc {
 
 namespace {
 
-constexpr int KC = 32;          // fp32 elements per K chunk (one 128-byte swizzle row)
+// Operand element of the split products.  A K chunk is one 128-byte swizzle
+// row either way: 32 fp32 (TF32) or 64 bf16 elements; each MMA takes 32 bytes
+// of K (8 TF32 or 16 BF16 elements), four per chunk.
+enum Elem { E_TF32 = 0, E_BF16 = 1 };
+template <int EL>
+struct Op;
+template <>
+struct Op<E_TF32> {
+  using T = float;
+  static constexpr int KC = 32;
+};
+template <>
+struct Op<E_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr int KC = 64;
+};
+__host__ __device__ constexpr int kc_of(int el) { return el == E_BF16 ? 64 : 32; }
 constexpr int TM = 128;         // rows per MMA / M tile
 constexpr int kThreads = 128;   // 4 warps: TMA producer, MMA issuer, TMEM owner, all do the epilogue
 constexpr long long kWaitCycles = 4000000000LL;  // bounded mbarrier waits (~2 s of SM clock), then error + bail out
@@ -100,11 +119,18 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
-__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+template <int EL>
+__device__ __forceinline__ void mma_split(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (EL == E_BF16)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -141,20 +167,41 @@ __device__ __forceinline__ float tf32_round(float x) {
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
-// hi/lo split of a value for the 3-term products
+// hi/lo split of a value for the 3-term products (TF32 values kept as fp32, or bf16)
 __device__ __forceinline__ void split(float x, float& hi, float& lo) {
   hi = tf32_round(x);
   lo = tf32_round(x - hi);
 }
+__device__ __forceinline__ void split(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
 
-// byte offset of element (r, k), k < 32, in a K-major SW128 tile of 128-byte rows
-__device__ __forceinline__ uint32_t sw128_offset(int r, int k) {
-  return (uint32_t)(r * 128 + ((((k >> 2) ^ (r & 7)) << 4) | ((k & 3) << 2)));
+// Split four consecutive values and store hi and lo as one vector each (16 B
+// of fp32, or 8 B of bf16; the destinations are aligned to 4 elements).
+__device__ __forceinline__ void store_split4(float* dh, float* dl, const float* v) {
+  float h[4], l[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) split(v[u], h[u], l[u]);
+  *(float4*)dh = make_float4(h[0], h[1], h[2], h[3]);
+  *(float4*)dl = make_float4(l[0], l[1], l[2], l[3]);
+}
+__device__ __forceinline__ void store_split4(__nv_bfloat16* dh, __nv_bfloat16* dl, const float* v) {
+  __align__(8) __nv_bfloat16 h[4], l[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) split(v[u], h[u], l[u]);
+  *(uint2*)dh = *(const uint2*)h;
+  *(uint2*)dl = *(const uint2*)l;
+}
+
+// byte offset of the element at byte kb < 128 of row r in a K-major SW128 tile of 128-byte rows
+__device__ __forceinline__ uint32_t sw128_offset_bytes(int r, int kb) {
+  return (uint32_t)(r * 128 + ((((kb >> 4) ^ (r & 7)) << 4) | (kb & 15)));
 }
 
 struct GemmArgs {
   CUtensorMap tA_hi, tA_lo, tB_hi, tB_lo;  // tB_* unused for P1
-  int k_chunks;   // K / KC
+  int k_chunks;   // K / (elements per K chunk)
   int m_tiles;    // M tiles (TM rows each) of the whole, possibly stacked, GEMM
   int n_tiles;    // N tiles (NT columns each)
   int n_total;    // valid columns (the last tile may run past them)
@@ -168,7 +215,7 @@ struct GemmArgs {
   unsigned long long* Qzero;
   long long qcells;
   // outputs / epilogue inputs
-  float *out_hi, *out_lo;  // next phase's operand (P1: B2, P2A: B3, P2B: A3)
+  void *out_hi, *out_lo;   // next phase's operand (P1: B2, P2A: B3, P2B: A3), fp32 or bf16
   int out_ld;              // its row length (K of the next phase)
   long long out_slice;     // its elements per stacked grid
   const float *Sx, *Sy;    // P2A: spectra [Npad][My]
@@ -205,10 +252,12 @@ struct Smem {
   static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
 
-// Instruction descriptor: D f32, A = B = tf32, both K-major, M = 128, N = NT.
-template <int NT>
+// Instruction descriptor: D f32, A = B = tf32 (kind::tf32: format 2) or bf16
+// (kind::f16: format 1), both K-major, M = 128, N = NT.
+template <int NT, int EL>
 __host__ __device__ constexpr uint32_t idesc() {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  return (1u << 4) | ((EL == E_BF16 ? 1u : 2u) << 7) | ((EL == E_BF16 ? 1u : 2u) << 10) |
+         ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
 namespace cg = cooperative_groups;
@@ -223,10 +272,14 @@ __device__ __forceinline__ void prefetch_map(const CUtensorMap* m) {
 // bunches of a batch) extend the data operand: their rows follow one another,
 // so one launch covers all of them; tiles are ordered so that consecutive
 // CTAs share the data operand's tile (the constant one stays in L2).
-template <int PH, int SK, int NT, int STAGES>
+template <int PH, int SK, int NT, int STAGES, int EL>
 __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ GemmArgs g) {
   using L = Smem<PH, NT, STAGES>;
   using R = Roles<PH>;
+  using T = typename Op<EL>::T;
+  constexpr int KC = Op<EL>::KC;
+  T* const out_hi = (T*)g.out_hi;
+  T* const out_lo = (T*)g.out_lo;
   constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -320,11 +373,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
             // uint64 -> float through its 32-bit halves (no FP64 instruction)
             const float qv =
                 fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * qscale;
-            float hi, lo;
+            T hi, lo;
             split(qv, hi, lo);
-            const int kc = i / KC, k = i % KC;
-            *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
-            *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+            const int kc = i / KC, kb = (i % KC) * (int)sizeof(T);
+            *(T*)(resident + (2 * kc) * L::B_TILE + sw128_offset_bytes(r, kb)) = hi;
+            *(T*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset_bytes(r, kb)) = lo;
           }
         }
       }
@@ -355,11 +408,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
           const int r = e / g.mp, i = e - r * g.mp;
           const float qv =
               fmaf(__uint2float_rn((unsigned)(v[u] >> 32)), 4294967296.f, __uint2float_rn((unsigned)v[u])) * qscale;
-          float hi, lo;
+          T hi, lo;
           split(qv, hi, lo);
-          const int kc = i / KC, k = i % KC;
-          *(float*)(resident + (2 * kc) * L::B_TILE + sw128_offset(r, k)) = hi;
-          *(float*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset(r, k)) = lo;
+          const int kc = i / KC, kb = (i % KC) * (int)sizeof(T);
+          *(T*)(resident + (2 * kc) * L::B_TILE + sw128_offset_bytes(r, kb)) = hi;
+          *(T*)(resident + (2 * kc + 1) * L::B_TILE + sw128_offset_bytes(r, kb)) = lo;
         }
       }
     }
@@ -402,11 +455,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const uint64_t dbh = desc_sw128(smem_u32(bh)), dbl = desc_sw128(smem_u32(bl));
       const uint64_t dah = desc_sw128(smem_u32(sb)), dal = desc_sw128(smem_u32(sb + L::A_TILE));
 #pragma unroll
-      for (int kk = 0; kk < KC / 8; ++kk) {
+      for (int kk = 0; kk < 4; ++kk) {
         const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
-        mma_tf32(tmem, dah + o, dbh + o, idesc<NT>(), (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah + o, dbl + o, idesc<NT>(), 1u);
-        mma_tf32(tmem, dal + o, dbh + o, idesc<NT>(), 1u);
+        mma_split<EL>(tmem, dah + o, dbh + o, idesc<NT, EL>(), (kc > 0 || kk > 0) ? 1u : 0u);
+        mma_split<EL>(tmem, dah + o, dbl + o, idesc<NT, EL>(), 1u);
+        mma_split<EL>(tmem, dal + o, dbh + o, idesc<NT, EL>(), 1u);
       }
       mma_commit(&empty_bar[st]);
     }
@@ -439,16 +492,8 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const int half = (r <= g.nx) ? 0 : 1;
       const int slice = n0 / g.ny, j = n0 - slice * g.ny + cb;
       const size_t ob = (size_t)slice * g.out_slice + (size_t)p * g.out_ld + half * g.ny + j;
-      float4* dh = (float4*)(g.out_hi + ob);
-      float4* dl = (float4*)(g.out_lo + ob);
 #pragma unroll
-      for (int q4 = 0; q4 < CH / 4; ++q4) {
-        float h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) split(acc[4 * q4 + u], h[u], l[u]);
-        dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
-        dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
-      }
+      for (int q4 = 0; q4 < CH / 4; ++q4) store_split4(out_hi + ob + 4 * q4, out_lo + ob + 4 * q4, acc + 4 * q4);
     } else if (PH == P2A) {
       // row r < My: Re F(k = r, p) -> Im H_f = S_f Re F (column My + k of B3)
       // row r >= My: Im F(k = r - My, p) -> Re H_f = -S_f Im F (column k)
@@ -475,8 +520,8 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
         const size_t base = (size_t)sl[u] * g.out_slice;
         const size_t rx = base + (size_t)pp[u] * g.out_ld + col;
         const size_t ry = base + (size_t)(g.Npad + pp[u]) * g.out_ld + col;
-        split(sx[u] * f, g.out_hi[rx], g.out_lo[rx]);
-        split(sy[u] * f, g.out_hi[ry], g.out_lo[ry]);
+        split(sx[u] * f, out_hi[rx], out_lo[rx]);
+        split(sy[u] * f, out_hi[ry], out_lo[ry]);
       }
     } else if (PH == P2B) {
       // row r: part (Re G, Im G) = r / ny at j' = r % ny; stacked column n: grid n / (2 Npad),
@@ -489,11 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
         const int slice = n / (2 * g.Npad), rem = n - slice * 2 * g.Npad;
         const int f = rem / g.Npad, p = rem - f * g.Npad;
         const size_t o = (size_t)slice * g.out_slice + (size_t)(f * g.ny + jr) * g.out_ld + part * g.Npad + p;
-        float h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) split(acc[4 * q4 + u], h[u], l[u]);
-        *(float4*)(g.out_hi + o) = make_float4(h[0], h[1], h[2], h[3]);
-        *(float4*)(g.out_lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+        store_split4(out_hi + o, out_lo + o, acc + 4 * q4);
       }
     } else if (PH == P3) {
       // stacked row r: grid r / (2 ny); within it field f = (r % 2ny) / ny (Ex, Ey) at j;
@@ -508,16 +549,8 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       // (one stacked grid per tile, consecutive columns contiguous)
       const int s0 = n0 / g.mp, c = n0 - s0 * g.mp + cb;
       const size_t ob = (size_t)s0 * g.out_slice + (size_t)r * g.out_ld + c;
-      float4* dh = (float4*)(g.out_hi + ob);
-      float4* dl = (float4*)(g.out_lo + ob);
 #pragma unroll
-      for (int q4 = 0; q4 < CH / 4; ++q4) {
-        float h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) split(acc[4 * q4 + u], h[u], l[u]);
-        dh[q4] = make_float4(h[0], h[1], h[2], h[3]);
-        dl[q4] = make_float4(l[0], l[1], l[2], l[3]);
-      }
+      for (int q4 = 0; q4 < CH / 4; ++q4) store_split4(out_hi + ob + 4 * q4, out_lo + ob + 4 * q4, acc + 4 * q4);
     } else if (PH == D2) {
       // row q, columns (s, p): U = W / lambda_pq, stored transposed UT[s][p][q] (K = q of D3)
       float il[CH];
@@ -533,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       for (int u = 0; u < CH; ++u) {
         if (n0 + cb + u >= g.n_total) continue;
         const size_t o = (size_t)sl[u] * g.out_slice + (size_t)pp[u] * g.out_ld + r;
-        split(acc[u] * il[u], g.out_hi[o], g.out_lo[o]);
+        split(acc[u] * il[u], out_hi[o], out_lo[o]);
       }
     } else {
       // D4: stacked row (s, f, j) with f = 0: T3 (potential part), 1: its y-derivative; columns
@@ -556,18 +589,22 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   };
 
   if (SK > 1) {
-    // partial tiles -> shared memory (the stages are idle now), summed across the cluster
+    // partial tiles -> shared memory (the stages are idle now), summed across the cluster.
+    // After a timed-out wait copies or MMAs may still use the stages: nothing is
+    // written there, the cluster barriers are still taken (every CTA of the
+    // cluster reaches them), and the error word marks the results invalid.
     static_assert(SK == 1 || kThreads * NT * 4 <= L::STAGES * L::STAGE, "reduction buffer fits the stages");
     cg::cluster_group cl = cg::this_cluster();
     float4* red = (float4*)stage_base;
+    if (have) {
 #pragma unroll
-    for (int c16 = 0; c16 < NT / 16; ++c16) {
-      float v[16];
-      if (have) tmem_ld16(trow + c16 * 16, v);
+      for (int c16 = 0; c16 < NT / 16; ++c16) {
+        float v[16];
+        tmem_ld16(trow + c16 * 16, v);
 #pragma unroll
-      for (int q4 = 0; q4 < 4; ++q4)
-        red[t * (NT / 4) + c16 * 4 + q4] =
-            have ? make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q4 = 0; q4 < 4; ++q4)
+          red[t * (NT / 4) + c16 * 4 + q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+      }
     }
     cl.sync();
 #pragma unroll
@@ -601,6 +638,9 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   tc_fence_before();
   __syncthreads();
   if (warp == 2) {
+    // after a timed-out wait, issued MMAs get a second bounded wait to finish
+    // before their tensor memory is released
+    if (!have) (void)__all_sync(0xffffffffu, mbar_wait(&accum_bar, 0));
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
@@ -654,13 +694,16 @@ sc_status get_encoder() {
   return SC_OK;
 }
 
-// 2-D fp32 row-major [rows][cols] tensor map with boxes of 32 x box_rows, 128-byte swizzle.
-sc_status make_map(CUtensorMap* tm, const float* base, int rows, int cols, int box_rows) {
+// 2-D row-major [rows][cols] tensor map of fp32 (TF32 operands) or bf16
+// elements with boxes of one K chunk (128 bytes) x box_rows, 128-byte swizzle.
+sc_status make_map(CUtensorMap* tm, const void* base, int rows, int cols, int box_rows, int el) {
+  const size_t esz = el == E_BF16 ? 2 : 4;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)KC, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
+  cuuint32_t box[2] = {(cuuint32_t)kc_of(el), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)base, dims, strides, box, es,
+  CUresult r = g_encode(tm, el == E_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        (void*)base, dims, strides, box, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(SC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -676,18 +719,43 @@ float tf32_host(float x) {
   return r;
 }
 
-void split_host(const std::vector<double>& a, std::vector<float>& hi, std::vector<float>& lo) {
-  hi.resize(a.size());
-  lo.resize(a.size());
+// bf16 bits of a float, rounded to nearest, ties to even (finite inputs)
+uint16_t bf16_bits_host(float x) {
+  uint32_t b;
+  std::memcpy(&b, &x, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+float bf16_value_host(uint16_t h) {
+  const uint32_t b = (uint32_t)h << 16;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
+// hi/lo split of constant matrices on the host, as raw operand bytes (fp32 or bf16)
+void split_host(const std::vector<double>& a, int el, std::vector<unsigned char>& hi, std::vector<unsigned char>& lo) {
+  const size_t esz = el == E_BF16 ? 2 : 4;
+  hi.resize(a.size() * esz);
+  lo.resize(a.size() * esz);
   for (size_t i = 0; i < a.size(); ++i) {
-    hi[i] = tf32_host((float)a[i]);
-    lo[i] = tf32_host((float)(a[i] - (double)hi[i]));
+    if (el == E_BF16) {
+      const uint16_t h = bf16_bits_host((float)a[i]);
+      const uint16_t l = bf16_bits_host((float)(a[i] - (double)bf16_value_host(h)));
+      std::memcpy(&hi[i * 2], &h, 2);
+      std::memcpy(&lo[i * 2], &l, 2);
+    } else {
+      const float h = tf32_host((float)a[i]);
+      const float l = tf32_host((float)(a[i] - (double)h));
+      std::memcpy(&hi[i * 4], &h, 4);
+      std::memcpy(&lo[i * 4], &l, 4);
+    }
   }
 }
 
 struct Mat {
-  float* hi = nullptr;
-  float* lo = nullptr;
+  void* hi = nullptr;
+  void* lo = nullptr;
   int rows = 0, cols = 0;
 };
 
@@ -696,11 +764,13 @@ struct Mat {
 // One phase of the solve as launched: kernel variant, its arguments, its grid.
 struct PhaseRun {
   int variant = -1;  // index into the phase's candidate list
+  int el = 0;        // operand element (E_TF32 or E_BF16)
   GemmArgs a;
   int grid = 0;
 };
 
 struct Tf32Plan {
+  int el = E_TF32;           // operand element: E_TF32 or E_BF16 (open boundary only)
   int Mx, My, Npad;
   Mat B1, W2f, W2i, B4;      // constants
   Mat B2, B3, A3;            // intermediates (next phase operands)
@@ -721,25 +791,26 @@ struct Tf32Plan {
 
 namespace {
 
-sc_status upload(Mat& m, const std::vector<double>& v, int rows, int cols) {
-  std::vector<float> hi, lo;
-  split_host(v, hi, lo);
+sc_status upload(Mat& m, const std::vector<double>& v, int rows, int cols, int el) {
+  std::vector<unsigned char> hi, lo;
+  split_host(v, el, hi, lo);
   m.rows = rows;
   m.cols = cols;
-  SC_CUDA(cudaMalloc(&m.hi, hi.size() * 4));
-  SC_CUDA(cudaMalloc(&m.lo, lo.size() * 4));
-  SC_CUDA(cudaMemcpy(m.hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice));
-  SC_CUDA(cudaMemcpy(m.lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMalloc(&m.hi, hi.size()));
+  SC_CUDA(cudaMalloc(&m.lo, lo.size()));
+  SC_CUDA(cudaMemcpy(m.hi, hi.data(), hi.size(), cudaMemcpyHostToDevice));
+  SC_CUDA(cudaMemcpy(m.lo, lo.data(), lo.size(), cudaMemcpyHostToDevice));
   return SC_OK;
 }
 
-sc_status alloc_zero(Mat& m, int rows, int cols) {
+sc_status alloc_zero(Mat& m, int rows, int cols, int el) {
+  const size_t bytes = (size_t)rows * cols * (el == E_BF16 ? 2 : 4);
   m.rows = rows;
   m.cols = cols;
-  SC_CUDA(cudaMalloc(&m.hi, (size_t)rows * cols * 4));
-  SC_CUDA(cudaMalloc(&m.lo, (size_t)rows * cols * 4));
-  SC_CUDA(cudaMemset(m.hi, 0, (size_t)rows * cols * 4));
-  SC_CUDA(cudaMemset(m.lo, 0, (size_t)rows * cols * 4));
+  SC_CUDA(cudaMalloc(&m.hi, bytes));
+  SC_CUDA(cudaMalloc(&m.lo, bytes));
+  SC_CUDA(cudaMemset(m.hi, 0, bytes));
+  SC_CUDA(cudaMemset(m.lo, 0, bytes));
   return SC_OK;
 }
 
@@ -755,16 +826,16 @@ struct Variant {
   const void* fn;
 };
 
-template <int PH, int SK, int NT, int ST>
+template <int PH, int SK, int NT, int ST, int EL = E_TF32>
 Variant variant() {
-  return Variant{SK, NT, ST, Smem<PH, NT, ST>::BYTES, (const void*)dft_gemm<PH, SK, NT, ST>};
+  return Variant{SK, NT, ST, Smem<PH, NT, ST>::BYTES, (const void*)dft_gemm<PH, SK, NT, ST, EL>};
 }
 
 // Candidates per phase (split-K cluster size SK, tile width NT, pipeline
 // stages), timed against each other when a grid is created.  Wide tiles load
 // each constant-operand tile once for many columns (stacked grids); narrow,
 // K-split tiles give a single small grid enough CTAs.
-const std::vector<Variant>& variants(int ph) {
+const std::vector<Variant>& variants(int ph, int el = E_TF32) {
   static const std::vector<Variant> v[8] = {
       {variant<P1, 1, 16, 4>(), variant<P1, 1, 32, 4>(), variant<P1, 1, 64, 2>()},
       {variant<P2A, 2, 16, 5>(), variant<P2A, 1, 32, 4>(), variant<P2A, 2, 32, 4>(), variant<P2A, 1, 64, 4>(),
@@ -778,7 +849,16 @@ const std::vector<Variant>& variants(int ph) {
       {variant<D3, 2, 16, 5>(), variant<D3, 1, 32, 4>(), variant<D3, 2, 32, 4>(), variant<D3, 1, 64, 4>(),
        variant<D3, 1, 128, 3>()},
       {variant<D4, 2, 16, 5>(), variant<D4, 1, 32, 4>(), variant<D4, 2, 32, 4>(), variant<D4, 1, 64, 4>()}};
-  return v[ph];
+  // BF16 operands (open boundary): the same tilings; a K chunk holds 64 elements
+  static const std::vector<Variant> b[4] = {
+      {variant<P1, 1, 16, 4, E_BF16>(), variant<P1, 1, 32, 4, E_BF16>(), variant<P1, 1, 64, 2, E_BF16>()},
+      {variant<P2A, 2, 16, 5, E_BF16>(), variant<P2A, 1, 32, 4, E_BF16>(), variant<P2A, 2, 32, 4, E_BF16>(),
+       variant<P2A, 1, 64, 4, E_BF16>(), variant<P2A, 1, 128, 3, E_BF16>()},
+      {variant<P2B, 4, 16, 5, E_BF16>(), variant<P2B, 2, 32, 4, E_BF16>(), variant<P2B, 1, 64, 4, E_BF16>(),
+       variant<P2B, 2, 64, 4, E_BF16>(), variant<P2B, 1, 128, 3, E_BF16>()},
+      {variant<P3, 2, 16, 5, E_BF16>(), variant<P3, 1, 32, 4, E_BF16>(), variant<P3, 2, 32, 4, E_BF16>(),
+       variant<P3, 1, 64, 4, E_BF16>()}};
+  return (el == E_BF16 && ph <= P3) ? b[ph] : v[ph];
 }
 
 sc_status set_attrs(const Variant& v) {
@@ -789,7 +869,7 @@ sc_status set_attrs(const Variant& v) {
 
 // CTAs (tiles x SK), clusters of SK along x, optionally programmatic dependent launch.
 cudaError_t launch_run(int ph, const PhaseRun& r, cudaStream_t s, bool pdl) {
-  const Variant& v = variants(ph)[r.variant];
+  const Variant& v = variants(ph, r.el)[r.variant];
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(r.grid);
   cfg.blockDim = dim3(kThreads);
@@ -840,7 +920,8 @@ void host_fft(std::complex<double>* a, int n, int stride) {
 // variant's tile width); SC_ERR_ARG when the variant does not fit the grid.
 sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
   Tf32Plan* T = g->tf32;
-  const Variant& v = variants(ph)[k];
+  const int el = T->el, kc = kc_of(el);
+  const Variant& v = variants(ph, el)[k];
   const int nx = g->nx, ny = g->ny, nz = g->nstack, My = T->My, Npad = T->Npad, K3 = T->K3;
   GemmArgs& a = out.a;
   std::memset(&a, 0, sizeof a);
@@ -854,10 +935,10 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
   switch (ph) {
     case P1:  // C[c][(s,j)] = B1 q^T: M = 2nx (c), N = nz ny (j of every stacked grid), K = nx
       if (ny % v.nt) return set_error(SC_ERR_ARG, "tile wider than a grid's rows");
-      if ((st = make_map(&a.tA_hi, T->B1.hi, 2 * nx, nx, TM)) || (st = make_map(&a.tA_lo, T->B1.lo, 2 * nx, nx, TM)))
+      if ((st = make_map(&a.tA_hi, T->B1.hi, 2 * nx, nx, TM, el)) || (st = make_map(&a.tA_lo, T->B1.lo, 2 * nx, nx, TM, el)))
         return st;
       M = 2 * nx;
-      a.k_chunks = nx / KC;
+      a.k_chunks = nx / kc;
       a.n_total = nz * ny;
       a.Q = g->Q;
       a.qfac = 1.f;
@@ -867,13 +948,13 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
       a.out_slice = (long long)Npad * 2 * ny;
       break;
     case P2A:  // C[r][(s,p)] = W2f B2^T: M = 2My as (Re, Im) halves, N = nz Npad, K = 2ny
-      if ((st = make_map(&a.tA_hi, T->W2f.hi, 2 * My, 2 * ny, TM)) ||
-          (st = make_map(&a.tA_lo, T->W2f.lo, 2 * My, 2 * ny, TM)) ||
-          (st = make_map(&a.tB_hi, T->B2.hi, nz * Npad, 2 * ny, v.nt)) ||
-          (st = make_map(&a.tB_lo, T->B2.lo, nz * Npad, 2 * ny, v.nt)))
+      if ((st = make_map(&a.tA_hi, T->W2f.hi, 2 * My, 2 * ny, TM, el)) ||
+          (st = make_map(&a.tA_lo, T->W2f.lo, 2 * My, 2 * ny, TM, el)) ||
+          (st = make_map(&a.tB_hi, T->B2.hi, nz * Npad, 2 * ny, v.nt, el)) ||
+          (st = make_map(&a.tB_lo, T->B2.lo, nz * Npad, 2 * ny, v.nt, el)))
         return st;
       M = 2 * My;
-      a.k_chunks = 2 * ny / KC;
+      a.k_chunks = 2 * ny / kc;
       a.n_total = nz * Npad;
       a.qcells = (long long)nz * nx * ny;
       a.Sx = T->Sx;
@@ -884,13 +965,13 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
       a.out_slice = (long long)2 * Npad * 2 * My;
       break;
     case P2B:  // C[r][(s,f,p)] = W2i B3^T: M = 2ny as (Re, Im) halves, N = nz 2 Npad, K = 2My
-      if ((st = make_map(&a.tA_hi, T->W2i.hi, 2 * ny, 2 * My, TM)) ||
-          (st = make_map(&a.tA_lo, T->W2i.lo, 2 * ny, 2 * My, TM)) ||
-          (st = make_map(&a.tB_hi, T->B3.hi, nz * 2 * Npad, 2 * My, v.nt)) ||
-          (st = make_map(&a.tB_lo, T->B3.lo, nz * 2 * Npad, 2 * My, v.nt)))
+      if ((st = make_map(&a.tA_hi, T->W2i.hi, 2 * ny, 2 * My, TM, el)) ||
+          (st = make_map(&a.tA_lo, T->W2i.lo, 2 * ny, 2 * My, TM, el)) ||
+          (st = make_map(&a.tB_hi, T->B3.hi, nz * 2 * Npad, 2 * My, v.nt, el)) ||
+          (st = make_map(&a.tB_lo, T->B3.lo, nz * 2 * Npad, 2 * My, v.nt, el)))
         return st;
       M = 2 * ny;
-      a.k_chunks = 2 * My / KC;
+      a.k_chunks = 2 * My / kc;
       a.n_total = nz * 2 * Npad;
       a.out_hi = T->A3.hi;
       a.out_lo = T->A3.lo;
@@ -905,11 +986,11 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
       if (mp % v.nt) return set_error(SC_ERR_ARG, "tile width does not divide the padded interior");
       a.m = T->m;
       a.mp = mp;
-      a.k_chunks = mp / KC;
+      a.k_chunks = mp / kc;
       a.out_ld = mp;
       a.out_slice = (long long)mp * mp;
       if (ph == D1 || ph == D2) {
-        if ((st = make_map(&a.tA_hi, T->S.hi, mp, mp, TM)) || (st = make_map(&a.tA_lo, T->S.lo, mp, mp, TM))) return st;
+        if ((st = make_map(&a.tA_hi, T->S.hi, mp, mp, TM, el)) || (st = make_map(&a.tA_lo, T->S.lo, mp, mp, TM, el))) return st;
         M = mp;
         a.n_total = nz * mp;
       }
@@ -919,15 +1000,15 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
         a.out_hi = T->T1.hi;
         a.out_lo = T->T1.lo;
       } else if (ph == D2) {
-        if ((st = make_map(&a.tB_hi, T->T1.hi, nz * mp, mp, v.nt)) || (st = make_map(&a.tB_lo, T->T1.lo, nz * mp, mp, v.nt)))
+        if ((st = make_map(&a.tB_hi, T->T1.hi, nz * mp, mp, v.nt, el)) || (st = make_map(&a.tB_lo, T->T1.lo, nz * mp, mp, v.nt, el)))
           return st;
         a.inv_lam = T->inv_lam;
         a.qcells = (long long)nz * nx * ny;
         a.out_hi = T->UT.hi;
         a.out_lo = T->UT.lo;
       } else if (ph == D3) {  // A = [S; Cy]: rows (f, j), the potential part and its y-derivative
-        if ((st = make_map(&a.tA_hi, T->SCy.hi, 2 * mp, mp, TM)) || (st = make_map(&a.tA_lo, T->SCy.lo, 2 * mp, mp, TM)) ||
-            (st = make_map(&a.tB_hi, T->UT.hi, nz * mp, mp, v.nt)) || (st = make_map(&a.tB_lo, T->UT.lo, nz * mp, mp, v.nt)))
+        if ((st = make_map(&a.tA_hi, T->SCy.hi, 2 * mp, mp, TM, el)) || (st = make_map(&a.tA_lo, T->SCy.lo, 2 * mp, mp, TM, el)) ||
+            (st = make_map(&a.tB_hi, T->UT.hi, nz * mp, mp, v.nt, el)) || (st = make_map(&a.tB_lo, T->UT.lo, nz * mp, mp, v.nt, el)))
           return st;
         M = 2 * mp;
         a.n_total = nz * mp;
@@ -935,9 +1016,9 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
         a.out_lo = T->T3.lo;
         a.out_slice = (long long)2 * mp * mp;
       } else {  // D4: A = T3 rows (s, f, j), B = [S; Cx]: columns (h, i)
-        if ((st = make_map(&a.tA_hi, T->T3.hi, nz * 2 * mp, mp, TM)) ||
-            (st = make_map(&a.tA_lo, T->T3.lo, nz * 2 * mp, mp, TM)) ||
-            (st = make_map(&a.tB_hi, T->SCx.hi, 2 * mp, mp, v.nt)) || (st = make_map(&a.tB_lo, T->SCx.lo, 2 * mp, mp, v.nt)))
+        if ((st = make_map(&a.tA_hi, T->T3.hi, nz * 2 * mp, mp, TM, el)) ||
+            (st = make_map(&a.tA_lo, T->T3.lo, nz * 2 * mp, mp, TM, el)) ||
+            (st = make_map(&a.tB_hi, T->SCx.hi, 2 * mp, mp, v.nt, el)) || (st = make_map(&a.tB_lo, T->SCx.lo, 2 * mp, mp, v.nt, el)))
           return st;
         M = nz * 2 * mp;
         a.n_total = 2 * mp;
@@ -950,12 +1031,12 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
     }
     default:  // P3: C[(s,f,j)][i] = A3 B4^T: M = nz 2ny as (Ex, Ey) halves per grid, N = nx, K = K3
       if (nx % v.nt) return set_error(SC_ERR_ARG, "tile wider than a grid's columns");
-      if ((st = make_map(&a.tA_hi, T->A3.hi, nz * 2 * ny, K3, TM)) ||
-          (st = make_map(&a.tA_lo, T->A3.lo, nz * 2 * ny, K3, TM)) ||
-          (st = make_map(&a.tB_hi, T->B4.hi, nx, K3, v.nt)) || (st = make_map(&a.tB_lo, T->B4.lo, nx, K3, v.nt)))
+      if ((st = make_map(&a.tA_hi, T->A3.hi, nz * 2 * ny, K3, TM, el)) ||
+          (st = make_map(&a.tA_lo, T->A3.lo, nz * 2 * ny, K3, TM, el)) ||
+          (st = make_map(&a.tB_hi, T->B4.hi, nx, K3, v.nt, el)) || (st = make_map(&a.tB_lo, T->B4.lo, nx, K3, v.nt, el)))
         return st;
       M = nz * 2 * ny;
-      a.k_chunks = K3 / KC;
+      a.k_chunks = K3 / kc;
       a.n_total = nx;
       a.E = (float2*)g->E;
       a.e_slice = (long long)nx * ny;
@@ -968,6 +1049,7 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
   if (grid > (1LL << 30)) return set_error(SC_ERR_ARG, "too many tiles");
   out.grid = (int)grid;
   out.variant = k;
+  out.el = el;
   return set_attrs(v);
 }
 
@@ -1007,7 +1089,7 @@ sc_status tf32_tune(sc_grid* g) {
   for (int c = 0; c < 4 && !st; ++c) {
     const int ph = T->base() + c;
     float best = 1e30f;
-    for (int k = 0; k < (int)variants(ph).size() && k < kMaxVariants && !st; ++k) {
+    for (int k = 0; k < (int)variants(ph, T->el).size() && k < kMaxVariants && !st; ++k) {
       PhaseRun r;
       if (make_run(g, ph, k, r) != SC_OK) continue;  // does not fit this grid
       r.a.scale = 1.f;
@@ -1040,7 +1122,7 @@ sc_status tf32_tune(sc_grid* g) {
     const int ph = T->base() + c;
     const PhaseRun keep = T->run[c];
     PhaseRun best_run = keep;
-    for (int k = 0; k < (int)variants(ph).size() && k < kMaxVariants && !st; ++k) {
+    for (int k = 0; k < (int)variants(ph, T->el).size() && k < kMaxVariants && !st; ++k) {
       if (k == keep.variant || iso[c][k] == 0.f) continue;  // the current choice, or does not fit
       PhaseRun r;
       if (make_run(g, ph, k, r) != SC_OK) continue;
@@ -1104,9 +1186,10 @@ sc_status tf32_pipe_create(sc_grid* g) {
       const double sp = std::sin(M_PI * (p + 1) / (2.0 * (m + 1))), sq = std::sin(M_PI * (q + 1) / (2.0 * (m + 1)));
       il[(size_t)q * mp + p] = (float)(1.0 / (-4.0 * (sp * sp / (g->hx * g->hx) + sq * sq / (g->hy * g->hy))));
     }
-  if ((st = upload(T->S, S, mp, mp)) || (st = upload(T->SCy, SCy, 2 * mp, mp)) || (st = upload(T->SCx, SCx, 2 * mp, mp)) ||
-      (st = alloc_zero(T->T1, nz * mp, mp)) || (st = alloc_zero(T->UT, nz * mp, mp)) ||
-      (st = alloc_zero(T->T3, nz * 2 * mp, mp)))
+  const int el = T->el;
+  if ((st = upload(T->S, S, mp, mp, el)) || (st = upload(T->SCy, SCy, 2 * mp, mp, el)) ||
+      (st = upload(T->SCx, SCx, 2 * mp, mp, el)) || (st = alloc_zero(T->T1, nz * mp, mp, el)) ||
+      (st = alloc_zero(T->UT, nz * mp, mp, el)) || (st = alloc_zero(T->T3, nz * 2 * mp, mp, el)))
     return st;
   SC_CUDA(cudaMalloc(&T->inv_lam, il.size() * sizeof(float)));
   SC_CUDA(cudaMemcpy(T->inv_lam, il.data(), il.size() * sizeof(float), cudaMemcpyHostToDevice));
@@ -1121,15 +1204,17 @@ sc_status tf32_create(sc_grid* g) {
   if (g->precision == SC_SOLVE_PIPE_TF32X3) return tf32_pipe_create(g);
   const int nx = g->nx, ny = g->ny, nz = g->nstack;
   if (nx != ny || (nx != 64 && nx != 128 && nx != 256))
-    return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_TF32X3 needs nx = ny in {64, 128, 256}");
+    return set_error(SC_ERR_UNSUPPORTED, "SC_SOLVE_TF32X3 and SC_SOLVE_BF16X3 need nx = ny in {64, 128, 256}");
   sc_status st = get_encoder();
   if (st) return st;
   Tf32Plan* T = new (std::nothrow) Tf32Plan();
   if (!T) return set_error(SC_ERR_OOM, "host allocation failed");
   g->tf32 = T;
+  T->el = g->precision == SC_SOLVE_BF16X3 ? E_BF16 : E_TF32;
+  const int el = T->el, kc = kc_of(el);
   // half-spectrum columns p = 0..nx, padded to a multiple of 16 (whole float4 groups per field)
   const int Mx = 2 * nx, My = 2 * ny, Npad = ((nx + 1 + 15) / 16) * 16;
-  const int K3 = ((2 * Npad + 2 * KC - 1) / (2 * KC)) * (2 * KC);  // whole chunks for split-K up to 2
+  const int K3 = ((2 * Npad + 2 * kc - 1) / (2 * kc)) * (2 * kc);  // whole chunks for split-K up to 2
   T->Mx = Mx;
   T->My = My;
   T->Npad = Npad;
@@ -1188,10 +1273,10 @@ sc_status tf32_create(sc_grid* g) {
       Sy[(size_t)p * My + k] = (float)cy[(size_t)k * Mx + p].imag();
     }
 
-  if ((st = upload(T->B1, B1, 2 * nx, nx)) || (st = upload(T->W2f, W2f, 2 * My, 2 * ny)) ||
-      (st = upload(T->W2i, W2i, 2 * ny, 2 * My)) || (st = upload(T->B4, B4, nx, K3)) ||
-      (st = alloc_zero(T->B2, nz * Npad, 2 * ny)) || (st = alloc_zero(T->B3, nz * 2 * Npad, 2 * My)) ||
-      (st = alloc_zero(T->A3, nz * 2 * ny, K3)))
+  if ((st = upload(T->B1, B1, 2 * nx, nx, el)) || (st = upload(T->W2f, W2f, 2 * My, 2 * ny, el)) ||
+      (st = upload(T->W2i, W2i, 2 * ny, 2 * My, el)) || (st = upload(T->B4, B4, nx, K3, el)) ||
+      (st = alloc_zero(T->B2, nz * Npad, 2 * ny, el)) || (st = alloc_zero(T->B3, nz * 2 * Npad, 2 * My, el)) ||
+      (st = alloc_zero(T->A3, nz * 2 * ny, K3, el)))
     return st;
   SC_CUDA(cudaMalloc(&T->Sx, Sx.size() * 4));
   SC_CUDA(cudaMalloc(&T->Sy, Sy.size() * 4));
@@ -1262,7 +1347,7 @@ double tf32_tensor_flops(const sc_grid* g) {
   const Tf32Plan* T = g->tf32;
   double f = 0.0;
   for (const PhaseRun& r : T->run)
-    f += 2.0 * (double)r.a.m_tiles * TM * (double)r.a.n_total * (double)r.a.k_chunks * KC * 3.0;
+    f += 2.0 * (double)r.a.m_tiles * TM * (double)r.a.n_total * (double)r.a.k_chunks * kc_of(r.el) * 3.0;
   return f;
 }
 
@@ -1296,7 +1381,7 @@ sc_status tf32_get_tiling(const sc_grid* g, int* choice, std::string* desc) {
     const int k = T->run[c].variant, ph = T->base() + c;
     if (choice) choice[c] = k;
     if (desc) {
-      const Variant& v = variants(ph)[k];
+      const Variant& v = variants(ph, T->el)[k];
       char b[200];
       std::snprintf(b, sizeof b, "%s%s: %d columns x split-K %d, %d stages, %d CTAs (%.1f us)", c ? "; " : "",
                     names[ph], v.nt, v.sk, v.stages, T->run[c].grid, T->tuned_us[c]);
@@ -1312,7 +1397,7 @@ sc_status tf32_set_tiling(sc_grid* g, const int* choice) {
   for (int c = 0; c < 4; ++c) {
     if (choice[c] < 0) continue;
     const int ph = T->base() + c;
-    if (choice[c] >= (int)variants(ph).size()) return set_error(SC_ERR_ARG, "tiling variant index out of range");
+    if (choice[c] >= (int)variants(ph, T->el).size()) return set_error(SC_ERR_ARG, "tiling variant index out of range");
     PhaseRun r;
     sc_status st = make_run(g, ph, choice[c], r);
     if (st) return st;

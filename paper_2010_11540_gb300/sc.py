@@ -23,16 +23,16 @@ LIB_PATH = os.path.join(_PKG, "libsc.so")
 SC_OK = 0
 ERRORS = {-1: "SC_ERR_ARG", -2: "SC_ERR_CUDA", -3: "SC_ERR_OOM", -4: "SC_ERR_OVERFLOW",
           -5: "SC_ERR_TIMEOUT", -6: "SC_ERR_NAN", -7: "SC_ERR_UNSUPPORTED"}
-PRECISION = {"fp64": 0, "tf32x3": 1, "pipe_fp64": 2, "pipe_tf32x3": 3}
+PRECISION = {"fp64": 0, "tf32x3": 1, "pipe_fp64": 2, "pipe_tf32x3": 3, "bf16x3": 4}
 EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_deposit", "sc_solve", "sc_kick_push", "sc_track_turns",
            "sc_grid_read", "sc_grid_write_charge", "sc_tune_setup", "sc_trace_enable", "sc_trace_read",
            "sc_moments_noalloc", "sc_create_batch", "sc_destroy_batch", "sc_batch_track_turns", "sc_batch_read",
            "sc_batch_trace_enable", "sc_batch_trace_read", "sc_get_solver_tiling", "sc_set_solver_tiling",
-           "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_probe_peaks", "sc_grid_read_potential",
+           "sc_batch_set_solver_tiling", "sc_batch_get_solver_tiling", "sc_tunes", "sc_grid_read_potential",
            "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
            "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_batch_set_kick_push_shape",
            "sc_batch_get_kick_push_shape", "sc_get_solver_work", "sc_grid_charge_device",
-           "sc_set_particle_count", "sc_last_error")
+           "sc_set_particle_count", "sc_sort_particles", "sc_set_charge_reduce", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -59,6 +59,9 @@ class GridSpec(ctypes.Structure):
 class Bunch(ctypes.Structure):
     _fields_ = [("particles", Particles), ("beam", Beam), ("lattice", ctypes.c_void_p), ("n_elems", ctypes.c_int)]
 
+
+# int (*)(uint64_t* charge, int64_t cells, void* stream, void* user)
+REDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p)
 
 _lib = None
 
@@ -101,7 +104,9 @@ def load():
     L.sc_batch_set_solver_tiling.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.sc_batch_get_solver_tiling.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_char_p,
                                              ctypes.c_size_t]
-    L.sc_probe_peaks.argtypes = [dp, dp, dp, vp]
+    L.sc_tunes.argtypes = [vp, i64, ctypes.c_int, vp, vp]
+    L.sc_sort_particles.argtypes = [vp, ctypes.POINTER(Particles), vp]
+    L.sc_set_charge_reduce.argtypes = [vp, REDUCE_FN, vp, i64]
     L.sc_grid_read_potential.argtypes = [vp, vp]
     L.sc_set_longitudinal_kick.argtypes = [vp, ctypes.c_int]
     L.sc_set_gather.argtypes = [vp, ctypes.c_int]
@@ -206,6 +211,14 @@ def deposit(grid: Grid, state):
     _check(load().sc_deposit(grid.handle, ctypes.byref(p)))
 
 
+def sort_particles(grid: Grid, state, perm=None):
+    """Reorder the bunch (CUDA float64 tensors) in place by its cell on `grid`
+    (sc_sort_particles); perm: optional CUDA int32 tensor of n receiving the
+    old index of each new position."""
+    p = particles(state)
+    _check(load().sc_sort_particles(grid.handle, ctypes.byref(p), perm.data_ptr() if perm is not None else None))
+
+
 def solve(grid: Grid):
     _check(load().sc_solve(grid.handle))
 
@@ -268,11 +281,16 @@ def tune_setup(grid: Grid, state, twiss, acc):
     _check(load().sc_tune_setup(grid.handle, ctypes.byref(p), tw, acc.data_ptr() if acc is not None else None))
 
 
-def tunes(acc, n, turns):
-    """Fractional tunes (qx, qy) per particle from a tune accumulator after `turns` turns."""
-    import math
-    a = acc.view(4, n)
-    return (a[2] / (2 * math.pi * turns)).cpu().numpy(), (a[3] / (2 * math.pi * turns)).cpu().numpy()
+def tunes(acc, n, turns, stream=None):
+    """Fractional tunes (qx, qy) per particle from a tune accumulator after
+    `turns` turns (sc_tunes on the device), as host arrays."""
+    import torch
+    q = torch.empty(2 * n, dtype=torch.float64, device=acc.device)
+    _check(load().sc_tunes(acc.data_ptr(), n, int(turns), q.data_ptr(), _stream_handle(stream)))
+    if stream is not None:
+        stream.synchronize()
+    q = q.cpu().numpy()
+    return q[:n], q[n:]
 
 
 def trace_enable(grid: Grid, enable: bool = True):
@@ -317,6 +335,32 @@ def charge_tensor(grid: Grid):
     return torch.as_tensor(_DeviceArray(q.value, int(cells.value), "<i8"), device="cuda")
 
 
+def set_charge_reduce(grid: Grid, reduce, total_particles: int):
+    """Sharded bunch inside track_turns (sc_set_charge_reduce): reduce(charge,
+    stream) gets the grid's charge as a CUDA int64 tensor and the grid's stream
+    (a torch.cuda.ExternalStream) while a turn is captured, and must enqueue
+    on that stream an in-place sum of the tensor over the ranks; None switches
+    it off.  The callback object is kept on the grid."""
+    if reduce is None:
+        grid._reduce_cb = None
+        _check(load().sc_set_charge_reduce(grid.handle, REDUCE_FN(), None, 0))
+        return
+    import torch
+    q = charge_tensor(grid)
+
+    def cb(ptr, cells, stream, user):
+        try:
+            reduce(q, torch.cuda.ExternalStream(stream))
+            return 0
+        except Exception:  # noqa: BLE001 -- a failure becomes the capture's error code
+            import traceback
+            traceback.print_exc()
+            return 1
+
+    grid._reduce_cb = REDUCE_FN(cb)
+    _check(load().sc_set_charge_reduce(grid.handle, grid._reduce_cb, None, int(total_particles)))
+
+
 def set_particle_count(grid: Grid, n: int):
     """The count that normalises the next solve (the whole bunch's, after a cross-rank sum)."""
     _check(load().sc_set_particle_count(grid.handle, int(n)))
@@ -341,14 +385,6 @@ def get_kick_push_shape(grid: Grid):
     t, v, us = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0)
     _check(load().sc_get_kick_push_shape(grid.handle, ctypes.byref(t), ctypes.byref(v), ctypes.byref(us)))
     return int(t.value), int(v.value), us.value
-
-
-def probe_peaks(stream=None):
-    """-> (conflict-free shared u64 atomics/s, random-word shared u64 atomics/s,
-    FP64 FMA instructions/s) measured on the current device."""
-    a, r, f = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
-    _check(load().sc_probe_peaks(ctypes.byref(a), ctypes.byref(r), ctypes.byref(f), _stream_handle(stream)))
-    return a.value, r.value, f.value
 
 
 def moments_noalloc(state, out, stream=None):

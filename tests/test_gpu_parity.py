@@ -56,6 +56,9 @@ def test_deposit_edge_cases():
     st = {k: np.zeros(len(x)) for k in KEYS}
     st["x"], st["y"] = x, y
     sc.deposit(g, to_gpu(st))
+    # the NaN and the infinity are reported once (SC_ERR_NAN), then the count is clear
+    with pytest.raises(sc.ScError, match="SC_ERR_NAN"):
+        sc.grid_read(g)
     Q, _, _, n_out = sc.grid_read(g)
     Qo, n_out_o = oracle.deposit(og, x, y)
     assert np.array_equal(Q, Qo) and n_out == n_out_o == 5
@@ -291,6 +294,55 @@ def test_solve_tf32_every_tiling(n, nz):
     assert tried >= 12
     with pytest.raises(sc.ScError):
         sc.set_solver_tiling(g, [99, -1, -1, -1])
+
+
+# The split-precision tolerance: the BF16 hi + lo split keeps 16 significant
+# bits of each operand, but the products' 2^-16 errors are random and the
+# FP32 accumulation of long sums dominates in both split forms (measured
+# 4-6e-6 for BF16 and 2-5e-6 for TF32 on these grids).
+BF16_FIELD_TOL = 1e-5
+
+
+@pytest.mark.parametrize("n,nz", [(64, 1), (128, 1), (256, 1), (128, 3)])
+def test_solve_bf16_every_tiling(n, nz):
+    """The open-boundary solve with BF16 split operands (kind::f16 MMAs),
+    every tiling variant phase by phase, single and stacked grids: fields
+    within 1e-5 of the oracle (relative L2), as the TF32 form's on the same
+    charge (the measured errors of both are printed)."""
+    parts = synth.gaussian_bunch(200000, 9 + n + nz, 4e-3, 3e-3, 1e-4, 1e-4, sig_z=15.0)
+    grid = (n, n, -0.02, 0.02, -0.015, 0.015)
+    sl = None if nz == 1 else (nz, -60.0, 60.0)
+    g = sc.create_grid(*grid, precision="bf16x3", slices=sl)
+    og = oracle.Geometry(*grid)
+    if sl is None:
+        Qo, _ = oracle.deposit(og, parts["x"], parts["y"])
+        Exo, Eyo = oracle.solve(og, Qo, len(parts["x"]))
+    else:
+        Qo, _ = oracle.deposit_sliced(og, oracle.Slices(*sl), parts["x"], parts["y"], parts["sigma"])
+        Exo, Eyo = oracle.solve_sliced(og, Qo, len(parts["x"]))
+    tuned, desc = sc.get_solver_tiling(g)
+    errs = []
+    for ph in range(4):
+        for k in range(TILING_VARIANTS[ph]):
+            choice = list(tuned)
+            choice[ph] = k
+            try:
+                sc.set_solver_tiling(g, choice)
+            except sc.ScError as e:
+                assert e.code == -1
+                continue
+            sc.grid_write_charge(g, Qo, len(parts["x"]))
+            sc.solve(g)
+            _, Ex, Ey, _ = sc.grid_read(g)
+            errs.append(max(rel_l2(Ex, Exo), rel_l2(Ey, Eyo)))
+            assert errs[-1] < BF16_FIELD_TOL, (ph, k, errs[-1])
+    g32 = sc.create_grid(*grid, precision="tf32x3", slices=sl)
+    sc.grid_write_charge(g32, Qo, len(parts["x"]))
+    sc.solve(g32)
+    _, Ex32, Ey32, _ = sc.grid_read(g32)
+    e32 = max(rel_l2(Ex32, Exo), rel_l2(Ey32, Eyo))
+    print(f"bf16x3 {n}x{n}x{nz}: field rel L2 {min(errs):.3e} .. {max(errs):.3e}; tf32x3 {e32:.3e}")
+    assert len(errs) >= 12 and e32 < BF16_FIELD_TOL
 
 
 def test_solve_tf32_point_charges():
@@ -607,6 +659,8 @@ def test_sliced_deposit_edges():
     st = {k: np.zeros(len(sg)) for k in KEYS}
     st["x"], st["y"], st["sigma"] = np.full(len(sg), 3.25), np.full(len(sg), 2.5), sg
     sc.deposit(g, to_gpu(st))
+    with pytest.raises(sc.ScError, match="SC_ERR_NAN: 2 "):  # the NaN and the infinite sigma
+        sc.grid_read(g)
     Q, _, _, n_out = sc.grid_read(g)
     Qo, n_out_o = oracle.deposit_sliced(og, zs, st["x"], st["y"], sg)
     assert np.array_equal(Q, Qo) and n_out == n_out_o == 4
@@ -964,3 +1018,164 @@ def test_sharded_bunch_through_the_charge_view(precision):
         assert np.array_equal(np.concatenate([got[0][k], got[1][k]]), got_all[k]), k
     with pytest.raises(sc.ScError):
         sc.set_particle_count(gs[0], -1)
+
+
+def test_moments_off_centre_bunch():
+    """Per-turn moments of a bunch whose centre sits 1e4 rms sizes off the axis
+    in x and y (50 rms in px, py): computed in two passes (the means, then the
+    moments of the offsets from them), they equal the oracle's within 1e-12 of
+    each moment's scale (a one-pass E[x^2] - E[x]^2 would lose 8 digits here);
+    so do those of the allocation-free entry point."""
+    import torch
+    parts, b, grid, lat = synth.workload("c1", n=20000)
+    shift = {"x": 1e4, "y": 1e4, "px": 50.0, "py": 50.0}
+    off = {k: np.ascontiguousarray(v + shift.get(k, 0.0) * np.std(v)) for k, v in parts.items()}
+    ref = oracle.moments(off)
+    # scale of each moment: |mean| for the means, sqrt(<aa><bb>) for <ab>
+    pairs = [(6, 6), (6, 8), (8, 8), (9, 9), (9, 11), (11, 11), (12, 12), (13, 13)]
+    scale = np.concatenate([np.abs(ref[:6]), [np.sqrt(ref[a] * ref[c]) for a, c in pairs]])
+    g = sc.create_grid(*grid)
+    # a marker and a drift: the moments are taken at the start of the turn (the
+    # ring's quadrupoles would throw a bunch 20 m off axis out of the paraxial range)
+    short = synth.table([synth.elem(synth.MARK), synth.elem(synth.DRIFT, 1.0)])
+    got = sc.track_turns(g, to_gpu(off), dict(b, n_lambda=0.0), short, 1, diag=True)[0]
+    assert np.all(np.abs(got - ref) <= 1e-12 * scale), (got - ref) / scale
+    out = torch.full((14,), np.nan, dtype=torch.float64, device="cuda")
+    sc.moments_noalloc(to_gpu(off), out)
+    got2 = out.cpu().numpy()
+    assert np.all(np.abs(got2 - ref) <= 1e-12 * scale), (got2 - ref) / scale
+
+
+def test_nonfinite_state_reported_by_tracking():
+    """A particle whose px is NaN drifts to a NaN position, which the next
+    deposit finds: sc_track_turns with diagnostics (a synchronous call)
+    returns SC_ERR_NAN; the other particles are tracked as without it."""
+    parts, b, grid, lat = synth.workload("c1", n=2000)
+    bad = oracle.copy_state(parts)
+    bad["px"][7] = np.nan
+    g = sc.create_grid(*grid)
+    st = to_gpu(bad)
+    with pytest.raises(sc.ScError, match="SC_ERR_NAN"):
+        sc.track_turns(g, st, b, lat, 1, diag=True)
+    got = to_host(st)
+    assert np.isnan(got["x"][7]) and np.all(np.isfinite(np.delete(got["x"], 7)))
+
+
+# ------------------------------------------------------------------ cell ordering and warp-combined deposits
+def test_sorted_bunch_deposit_bit_exact():
+    """sc_sort_particles orders the c2 bunch by cell (stable, outside last) and
+    reports the permutation; the deposit of the ordered bunch -- whose warps
+    combine the weights of neighbouring particles in one cell -- equals the
+    oracle's deposit of the original bunch bit for bit."""
+    import torch
+    parts, b, grid, lat = synth.workload("c2")
+    g, og = grid_pair(grid)
+    st = to_gpu(parts)
+    perm = torch.empty(len(parts["x"]), dtype=torch.int32, device="cuda")
+    sc.sort_particles(g, st, perm)
+    got = to_host(st)
+    pm = perm.cpu().numpy()
+    assert np.array_equal(np.sort(pm), np.arange(len(pm)))
+    for k in KEYS:
+        assert np.array_equal(got[k], parts[k][pm]), k
+    cell = oracle.deposit_cells(og, got["x"], got["y"])
+    key = np.where(cell < 0, grid[0] * grid[1], cell)
+    assert np.all(np.diff(key) >= 0)
+    same = np.diff(key) == 0
+    assert np.all(np.diff(pm)[same] > 0)  # stable
+    sc.deposit(g, st)
+    Q, _, _, n_out = sc.grid_read(g)
+    Qo, n_out_o = oracle.deposit(og, parts["x"], parts["y"])
+    assert np.array_equal(Q, Qo) and n_out == n_out_o
+
+
+@pytest.mark.parametrize("n,grid,centre", [
+    (12345, (256, 256) + synth.grid_extent(4e-3, 3e-3), (0.0, 0.0)),     # window of the 256x256 grid
+    (200003, (256, 256) + synth.grid_extent(4e-3, 3e-3), (0.012, -0.009)),  # beam mostly outside the window
+    (4099, (64, 32, -0.01, 0.01, -0.01, 0.01), (0.0, 0.0)),
+])
+@pytest.mark.parametrize("ordered", [False, True])
+def test_deposit_windows_and_runs_bit_exact(n, grid, centre, ordered):
+    """Grids beyond the 200 KB tile deposit through a centred window of it plus
+    global atomics for the rest; ordered or not, ragged counts, beams off the
+    window: the charge is the oracle's bit for bit."""
+    parts = synth.gaussian_bunch(n, 777 + n, 4e-3, 3e-3, 2e-4, 2e-4)
+    parts["x"] += centre[0]
+    parts["y"] += centre[1]
+    g, og = grid_pair(grid)
+    st = to_gpu(parts)
+    if ordered:
+        sc.sort_particles(g, st)
+    sc.deposit(g, st)
+    Q, _, _, n_out = sc.grid_read(g)
+    Qo, n_out_o = oracle.deposit(og, parts["x"], parts["y"])
+    assert np.array_equal(Q, Qo) and n_out == n_out_o
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_sorted_bunch_tracks_like_unsorted(precision):
+    """A turn of the ordered bunch gives, particle by particle (through the
+    permutation), the same bits as a turn of the original order: the charge is
+    an integer sum and every particle's arithmetic is its own."""
+    import torch
+    parts, b, grid, lat = synth.workload("c2", n=200000)
+    g = sc.create_grid(*grid, precision=precision)
+    a = to_gpu(parts)
+    sc.track_turns(g, a, b, lat, 1)
+    ref = to_host(a)
+    c = to_gpu(parts)
+    perm = torch.empty(len(parts["x"]), dtype=torch.int32, device="cuda")
+    sc.sort_particles(g, c, perm)
+    sc.track_turns(g, c, b, lat, 1)
+    got = to_host(c)
+    pm = perm.cpu().numpy()
+    for k in KEYS:
+        assert np.array_equal(got[k], ref[k][pm]), k
+
+
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+def test_sharded_turn_through_the_reduce_hook(precision):
+    """The charge reduction of a sharded bunch inside the captured turn
+    (sc_set_charge_reduce), on one GPU with two identical shards: the callback
+    stands in for the all-reduce by doubling the grid's charge (the other rank
+    holds the same particles) and the solve normalises by both shards'
+    count, so the fields -- and, in the float64 form, every particle after two
+    turns -- are those of the unsharded bunch.  The callback runs once per
+    space-charge location, while the turn is captured."""
+    import torch
+    parts, b, grid, lat = synth.workload("c2", n=100000)
+    n = len(parts["x"])
+    g0 = sc.create_grid(*grid, precision=precision)
+    a = to_gpu(parts)
+    sc.track_turns(g0, a, b, lat, 2)
+    ref = to_host(a)
+    g1 = sc.create_grid(*grid, precision=precision)
+    if precision != "fp64":  # the same GEMM tiling (summation order) on both grids
+        sc.set_solver_tiling(g1, sc.get_solver_tiling(g0)[0])
+    calls = []
+
+    def reduce(q, stream):
+        calls.append(q.numel())
+        with torch.cuda.stream(stream):
+            q.mul_(2)
+
+    sc.set_charge_reduce(g1, reduce, 2 * n)
+    c = to_gpu(parts)
+    sc.track_turns(g1, c, b, lat, 2)
+    got = to_host(c)
+    assert calls == [grid[0] * grid[1]] * 216
+    if precision == "fp64":
+        for k in KEYS:
+            assert np.array_equal(got[k], ref[k]), k
+    else:
+        for k in KEYS:
+            scale = np.sqrt(np.mean(ref[k] ** 2))
+            d = got[k] - ref[k]
+            assert np.sqrt(np.mean(d * d)) < 1e-5 * scale, k
+    # switched off: the local count normalises again (the same turn as the unsharded grid)
+    sc.set_charge_reduce(g1, None, 0)
+    e = to_gpu(parts)
+    sc.track_turns(g1, e, b, lat, 1)
+    f = to_gpu(parts)
+    sc.track_turns(g0, f, b, lat, 1)
+    assert all(np.array_equal(to_host(e)[k], to_host(f)[k]) for k in KEYS)

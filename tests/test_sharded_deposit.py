@@ -52,3 +52,45 @@ def test_two_rank_deposit_equals_single_rank(tmp_path, split):
     Q, n_out = oracle.deposit(g, parts["x"], parts["y"])
     assert np.array_equal(res[:-1].reshape(Q.shape), Q)
     assert res[-1] == n_out
+
+
+def _track_worker(rank, world, port, out_path):
+    """The sharded turn as the tracked turn runs it (the charge reduction
+    between each location's deposit and its solve, the solve normalised by the
+    whole bunch), on gloo ranks with the oracle's steps: rank r holds the
+    particles r, r + world, ... of the bunch."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    parts, b, grid, lat = synth.workload("c1", n=6000)
+    g = oracle.Geometry(*grid)
+    st = {k: np.ascontiguousarray(v[rank::world]) for k, v in parts.items()}
+    n_total = len(parts["x"])
+    head, kicks = oracle.segments(lat)
+    K = oracle.kick_strength(b)
+    oracle.push(st, head, b)
+    for L, seg in kicks[:20]:
+        Q, _ = oracle.deposit(g, st["x"], st["y"])
+        t = torch.from_numpy(Q.view(np.int64).copy())
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        Ex, Ey = oracle.solve(g, t.numpy().view(np.uint64).reshape(Q.shape), n_total)
+        oracle.kick(g, st, Ex, Ey, K * L)
+        oracle.push(st, seg, b)
+    np.save(out_path + f".{rank}.npy", np.stack([st[k] for k in ("x", "px", "y", "py", "sigma", "psigma")]))
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharded_turn_equals_single_rank(tmp_path):
+    """Twenty space-charge steps of a bunch sharded over two gloo ranks, with
+    one charge all-reduce per step, give every particle the same bits as the
+    whole bunch tracked on one rank (the reduction point of the sharded
+    tracked turn)."""
+    out = str(tmp_path / "st")
+    mp.start_processes(_track_worker, args=(2, _free_port(), out), nprocs=2, join=True, start_method="spawn")
+    parts, b, grid, lat = synth.workload("c1", n=6000)
+    ref = oracle.copy_state(parts)
+    oracle.track(oracle.Geometry(*grid), ref, b, lat, 1, max_kicks=20)
+    for rank in range(2):
+        got = np.load(out + f".{rank}.npy")
+        for i, k in enumerate(("x", "px", "y", "py", "sigma", "psigma")):
+            assert np.array_equal(got[i], ref[k][rank::2]), (rank, k)

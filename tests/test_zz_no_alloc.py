@@ -38,6 +38,23 @@ def test_noalloc_moments_match_track_diagnostics_twice():
     assert np.max(np.abs(got - oracle.moments(parts)) / np.abs(oracle.moments(parts))) < 1e-9
 
 
+def test_noalloc_moments_allocate_nothing():
+    """After the first call (which looks up the scratch array), further calls
+    leave the device's free memory unchanged: no allocation on any path."""
+    import torch
+
+    parts, _, _, _ = synth.workload("c1", n=20000)
+    st = to_gpu(parts)
+    out = torch.zeros(14, dtype=torch.float64, device="cuda")
+    sc.moments_noalloc(st, out)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(8):
+        sc.moments_noalloc(st, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+
+
 def test_noalloc_moments_rejects_bad_sizes():
     import torch
 
