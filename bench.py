@@ -45,9 +45,12 @@ WORKLOADS = {
 # FP64-pipe thread instructions per particle in kick_push_kernel (the turn
 # graph's variant), by segment content, from ncu's
 # sm__thread_inst_executed_pipe_fp64_pred_on per launch on the three segment
-# types of the bench ring (1e6 particles); base = gather + kick + fused deposit.
-# The quadrupole reads its matrix entries from the per-particle family cache
-# (51.0 when it computes them).
+# types of the bench ring (1e6 particles), fitted to the segments' element mix
+# (profiles/kick_push_c2.md gives the per-segment counts and the commands);
+# base = gather + kick + fused deposit.  The quadrupole reads its matrix
+# entries from the per-particle family cache (51.0 when it computes them).
+# The counts belong to the kernel sources whose SHA-256 (first 16 hex digits)
+# is FP64_INST_SOURCES_SHA; the bench reports whether the sources still match.
 FP64_INST = {"base": 18.1, "drift": 12.1, "quad": 24.0, "sext": 5.0, "bend": 16.0, "rf": 30.0}
 FP64_INST_QUAD_UNCACHED = 51.0  # with the longitudinal kick (psigma changes at every kick: no cache)
 # split-TF32 form: float32 gather from the cached fixed-point weights
@@ -72,6 +75,29 @@ KP_TRAFFIC_TF32 = {"c2": 122.5e6,   # 1e6 particles (the 200 MB working set part
                    "c5": 1594.1e6}  # 1e7 particles, 32 slices
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
+KP_SOURCES = ("kick_push.cu", "maps.cuh", "cic.cuh", "fixpt.h")
+FP64_INST_SOURCES_SHA = "ca5be54ef7c53b49"
+# HBM bytes per particle-kick that the fused kick/push must move (algorithmic):
+# the six float64 coordinates read (48 B) and the five a kick and a push
+# change written back (40 B: psigma changes only in RF cavities); 96 B when
+# psigma is written too.
+KP_ALGORITHMIC_BYTES = 88
+KP_ALGORITHMIC_BYTES_RF = 96
+
+
+def kp_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KP_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_11540_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+# arithmetic of each form: particle state and push, solve
+DTYPE_LABEL = {"fp64": "f64", "tf32x3": "f64 state and push / tf32x3 solve (fp32 accumulate, fp32 fields)",
+               "bf16x3": "f64 state and push / bf16x3 solve (fp32 accumulate, fp32 fields)",
+               "pipe_fp64": "f64", "pipe_tf32x3": "f64 state and push / tf32x3 solve (fp32 accumulate, fp32 fields)"}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -79,9 +105,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3"],
-                    help="solve form of the headline number; the other form is timed beside it")
-    ap.add_argument("--no-compare", action="store_true", help="skip timing the other solve form")
+    ap.add_argument("--precision", default="tf32x3", choices=["fp64", "tf32x3", "bf16x3"],
+                    help="solve form of the headline number; the other forms are timed beside it")
+    ap.add_argument("--compare", default=None,
+                    help="comma-separated solve forms timed beside the headline one (default: the plain FP64 form, "
+                         "or split-TF32 when the headline is FP64; c3: both other forms)")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other solve forms")
     ap.add_argument("--config", default="c2")
     ap.add_argument("--cpu-kicks", type=int, default=0,
                     help="oracle sample size in kicks (0: as many as take about 10 s, from a 2-kick probe)")
@@ -158,16 +187,39 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- helpers
-def fp64_inst_per_turn(lat, precision):
-    """FP64-pipe instructions per particle per turn from the element mix, and kicks/turn."""
+def element_mix(lat):
+    """Elements per turn by kind (space-charge locations as "kicks")."""
     from paper_2010_11540_gb300 import synth
     t = lat["type"]
-    n_k = int((t == synth.MARK).sum())
     per = {synth.DRIFT: "drift", synth.QUAD: "quad", synth.SEXT: "sext", synth.BEND: "bend", synth.RF: "rf"}
-    f = n_k * (FP64_INST["base"] if precision == "fp64" else FP64_INST_BASE_F32)
-    for code, name in per.items():
-        f += int((t == code).sum()) * FP64_INST[name]
-    return f, n_k
+    mix = {name: int((t == code).sum()) for code, name in per.items()}
+    mix["kicks"] = int((t == synth.MARK).sum())
+    return mix
+
+
+def fp64_inst_per_turn(lat, precision):
+    """FP64-pipe instructions per particle per turn from the element mix, and kicks/turn."""
+    mix = element_mix(lat)
+    f = mix["kicks"] * (FP64_INST["base"] if precision == "fp64" else FP64_INST_BASE_F32)
+    for name in ("drift", "quad", "sext", "bend", "rf"):
+        f += mix[name] * FP64_INST[name]
+    return f, mix["kicks"]
+
+
+def probe_peaks(stream):
+    """Live machine probes from libsc_probe.so (bench_probe.cu, built beside
+    this file; not part of libsc): conflict-free and random-word shared u64
+    atomics per second, FP64 FMA instructions per second."""
+    import ctypes
+    from paper_2010_11540_gb300 import build
+    L = ctypes.CDLL(build.build_probe())
+    L.scb_probe_peaks.argtypes = [ctypes.POINTER(ctypes.c_double)] * 3 + [ctypes.c_void_p]
+    L.scb_probe_peaks.restype = ctypes.c_int
+    a, r, f = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    code = L.scb_probe_peaks(ctypes.byref(a), ctypes.byref(r), ctypes.byref(f), int(stream.cuda_stream))
+    if code != 0:
+        raise RuntimeError(f"machine probes failed ({code})")
+    return a.value, r.value, f.value
 
 
 def measured_peaks():
@@ -177,12 +229,14 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(config, n_kicks, boundary="open", gather="bilinear", longitudinal=False):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample:
-    the full particle set (c4: its largest bunch) through the first n_kicks
-    kicks of turn 1."""
+def cpu_baseline(config, n_kicks, boundary="open", gather="bilinear", longitudinal=False, threads=1):
+    """The FP64 oracle as it stands on `threads` host threads (None: every
+    core; its OpenMP particle loops give the same bits for any count), on a
+    bounded sample: the full particle set (c4: its largest bunch) through the
+    first n_kicks kicks of turn 1."""
     import oracle
     from paper_2010_11540_gb300 import synth
+    oracle.set_threads(threads)
     slices = None
     if config == "c4":
         bunches = synth.c4_bunches()
@@ -215,8 +269,20 @@ def cpu_baseline(config, n_kicks, boundary="open", gather="bilinear", longitudin
     dt = time.perf_counter() - t0
     n = len(parts["x"])
     span = "of turn 1" if turns == 1 else f"over {turns} turns"
-    return {"value": n * done / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{what} ({n}), first {done} SC kicks {span}, {dt:.1f} s"}
+    cores = oracle.threads()
+    oracle.set_threads(1)
+    return {"value": n * done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{what} ({n}), first {done} SC kicks {span}, {dt:.1f} s on {cores} thread(s)"}
+
+
+def cpu_baselines(config, n_kicks, boundary="open", gather="bilinear", longitudinal=False):
+    """The oracle on every host core (the reported baseline) and on one."""
+    allc = cpu_baseline(config, n_kicks, boundary, gather, longitudinal, threads=None)
+    one = cpu_baseline(config, n_kicks, boundary, gather, longitudinal, threads=1)
+    allc["single_thread"] = {"value": one["value"], "cores": 1, "sample": one["sample"]}
+    allc["threads_note"] = ("OpenMP particle loops and per-thread integer charge grids: bit-identical to one thread "
+                            "(tests/test_oracle_track.py::test_threads_bit_identical)")
+    return allc
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -226,11 +292,11 @@ def run_reference(args):
         return
     kicks = max(1, args.cpu_kicks // 4) if args.cpu_kicks > 0 else 6  # a bounded sample per step
     for _ in range(args.warmup):
-        cpu_baseline(args.config, 1)
+        cpu_baseline(args.config, 1, threads=None)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(args.config, kicks))
+        vals.append(cpu_baseline(args.config, kicks, threads=None))
     wall = time.perf_counter() - t0
     value = statistics.mean(v["value"] for v in vals)
     cb = dict(vals[0])
@@ -267,13 +333,25 @@ class SingleRun:
         self.n = len(self.parts["x"])
         self.stream = stream
         self.n_classes = 1
+        # several ranks: each holds its own seeded share of one bunch of world x n particles, and the
+        # ranks' charges are summed by an NCCL all-reduce captured in the turn (sc_set_charge_reduce)
+        self.world = int(os.environ.get("WORLD_SIZE", 1))
+
+    @staticmethod
+    def allreduce(q, stream):
+        import torch
+        import torch.distributed as dist
+        with torch.cuda.stream(stream):
+            dist.all_reduce(q)
 
     def make(self, precision):
         import torch
         from paper_2010_11540_gb300 import sc
         dev = {k: torch.from_numpy(self.parts[k]).cuda() for k in KEYS}
         g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
-        if precision in ("tf32x3", "pipe_tf32x3") and self.tiling:
+        if self.world > 1:
+            sc.set_charge_reduce(g, self.allreduce, self.world * self.n)
+        if precision in ("tf32x3", "pipe_tf32x3", "bf16x3") and self.tiling:
             sc.set_solver_tiling(g, self.tiling)
         if self.kp_shape:
             sc.set_kick_push_shape(g, *self.kp_shape)
@@ -286,7 +364,7 @@ class SingleRun:
 
     def tiling_desc(self, h):
         from paper_2010_11540_gb300 import sc
-        if h[0].precision not in ("tf32x3", "pipe_tf32x3"):
+        if h[0].precision not in ("tf32x3", "pipe_tf32x3", "bf16x3"):
             return None
         v, d = sc.get_solver_tiling(h[0])
         return {"variants": v, "grid": d}
@@ -354,10 +432,11 @@ class SingleRun:
         return {"solve_us": ms * 1e3, "what": f"cuFFT (torch.fft, float64) rfft2 of the {2 * nx}x{2 * ny} "
                                              "zero-padded charge, x2 spectra, 2 irfft2; context only"}
 
-    def deposit_roofline(self, h, flush, atom_peak, atom_conflict_free, reps=20):
+    def deposit_roofline(self, h, flush, atom_random, atom_conflict_free, reps=20):
         """sc_deposit alone (the deposit kernel) on the workload's particles:
         4 shared-memory u64 atomic adds per particle inside the grid, against
-        the probed rate of such atomics on random words of a 128 KB tile."""
+        the probed conflict-free rate of such atomics (the random-word rate of
+        a 128 KB table as context)."""
         import torch
         from paper_2010_11540_gb300 import sc
         g, dev = h
@@ -374,13 +453,33 @@ class SingleRun:
             torch.cuda.synchronize()
         ms = sorted(a.elapsed_time(c) for a, c in ev)[reps // 2]
         atomics = 4 * n_in
+        rate = atomics / (ms * 1e-3)
+        # the same bunch ordered by cell (sc_sort_particles, on a copy): warps combine equal cells
+        with torch.cuda.stream(self.stream):
+            od = {k: v.clone() for k, v in dev.items()}
+            sc.sort_particles(g, od)
+            sc.deposit(g, od)
+            ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, c in ev2:
+                flush.zero_()
+                a.record(self.stream)
+                sc.deposit(g, od)
+                c.record(self.stream)
+            torch.cuda.synchronize()
+        ms_o = sorted(a.elapsed_time(c) for a, c in ev2)[reps // 2]
+        del od
+        ordered = {"avg_launch_ms": ms_o, "achieved": atomics / (ms_o * 1e-3) / 1e9,
+                   "frac": atomics / (ms_o * 1e-3) / atom_conflict_free,
+                   "what": "the same particles ordered by cell (sc_sort_particles): each warp combines the weights "
+                           "of neighbouring particles in one cell before its atomic adds; achieved counts the "
+                           "4 algorithmic atomics per particle"}
         return {"bound": "shared-atomics", "kernel": "deposit_kernel (stand-alone sc_deposit)",
-                "achieved": atomics / (ms * 1e-3) / 1e9, "peak": atom_peak / 1e9, "unit": "G shared-u64-atomics/s",
-                "frac": atomics / (ms * 1e-3) / atom_peak, "avg_launch_ms": ms, "atomics_per_launch": atomics,
-                "peak_source": "sc_probe_peaks: shared u64 atomicAdd on random words of a 128 KB table, "
-                               "measured in this run",
-                "peak_conflict_free": atom_conflict_free / 1e9,
-                "frac_of_conflict_free": atomics / (ms * 1e-3) / atom_conflict_free}
+                "achieved": rate / 1e9, "peak": atom_conflict_free / 1e9, "unit": "G shared-u64-atomics/s",
+                "frac": rate / atom_conflict_free, "avg_launch_ms": ms, "atomics_per_launch": atomics,
+                "peak_source": "live probe (libsc_probe.so): conflict-free shared u64 atomicAdd, each warp on 32 "
+                               "consecutive words, measured in this run",
+                "context_peak_random_words": atom_random / 1e9,
+                "frac_of_random_words": rate / atom_random, "ordered_bunch": ordered}
 
     def grid_desc(self):
         d = {"grid": [self.grid[0], self.grid[1]]}
@@ -414,7 +513,7 @@ class BatchRun:
         from paper_2010_11540_gb300 import sc
         devs = [{k: torch.from_numpy(p[k]).cuda() for k in KEYS} for p, _, _, _ in self.bunches]
         B = sc.create_batch(self.grids, precision=precision, stream=self.stream)
-        if precision == "tf32x3" and self.tiling:
+        if precision in ("tf32x3", "bf16x3") and self.tiling:
             sc.batch_set_solver_tiling(B, self.tiling)
         if self.kp_shape:
             sc.batch_set_kick_push_shape(B, *self.kp_shape)
@@ -422,7 +521,7 @@ class BatchRun:
 
     def tiling_desc(self, h):
         from paper_2010_11540_gb300 import sc
-        if h[0].precision != "tf32x3":
+        if h[0].precision not in ("tf32x3", "bf16x3"):
             return None
         out = {}
         for i, g in enumerate(self.grids):
@@ -527,11 +626,12 @@ def run_ours(args):
             ms = float(t.item())
         return h, ms, wall, clk
 
-    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, {"pipe_fp64": "fp64", "pipe_tf32x3": "tf32x3"}.get(args.precision,
+    inst_turn, n_kicks = fp64_inst_per_turn(W.lat, {"pipe_fp64": "fp64", "pipe_tf32x3": "tf32x3",
+                                                    "bf16x3": "tf32x3"}.get(args.precision,
                                                                                                  args.precision))
     if getattr(W, "slices", None):
         inst_turn += n_kicks * FP64_INST_SLICE
-    f32 = args.precision in ("tf32x3", "pipe_tf32x3")
+    f32 = args.precision in ("tf32x3", "pipe_tf32x3", "bf16x3")
     if args.gather == "bezier":
         inst_turn += n_kicks * (FP64_INST_BEZIER_F32 if f32 else FP64_INST_BEZIER)
     if args.longitudinal:
@@ -543,12 +643,20 @@ def run_ours(args):
     value = world * n * n_kicks * args.steps / (ms * 1e-3)
     compare = None
     if not args.no_compare:
-        other = {"tf32x3": "fp64", "fp64": "tf32x3", "pipe_tf32x3": "pipe_fp64"}[args.precision]
-        h2, ms2, _, clk2 = timed_turns(other)
-        compare = {"precision": other, "value": world * n * n_kicks * args.steps / (ms2 * 1e-3),
-                   "ms_per_step": ms2 / args.steps, "clocks": clk2}
-        W.close(h2)
-        del h2
+        if args.compare:
+            others = args.compare.split(",")
+        elif args.config == "c3":
+            others = [f for f in ("fp64", "tf32x3", "bf16x3") if f != args.precision]
+        else:
+            others = [{"tf32x3": "fp64", "fp64": "tf32x3", "bf16x3": "fp64", "pipe_tf32x3": "pipe_fp64"}[args.precision]]
+        forms = []
+        for other in others:
+            h2, ms2, _, clk2 = timed_turns(other)
+            forms.append({"precision": other, "value": world * n * n_kicks * args.steps / (ms2 * 1e-3),
+                          "ms_per_step": ms2 / args.steps, "clocks": clk2})
+            W.close(h2)
+            del h2
+        compare = forms[0] if len(forms) == 1 else forms
 
     # ---------------- dominant kernel, timed inside the turn graph (library tracing:
     # CUDA events on the grid's stream around every solve and kick/push launch)
@@ -562,15 +670,31 @@ def run_ours(args):
     kp_avg_ms = kp_ms / traced
     inst_per_kick = inst_turn / n_kicks
     achieved = inst_per_kick * n / (kp_avg_ms * 1e-3) / 1e12
+    sha = kp_sources_sha()
+    mix = element_mix(W.lat)
+    rf = mix["rf"] > 0 or args.longitudinal
+    kp_bytes = KP_ALGORITHMIC_BYTES_RF if rf else KP_ALGORITHMIC_BYTES
+    hbm_peak = measured_peaks().get("hbm_gbs", 6800.0)
+    hbm_achieved = kp_bytes * n / (kp_avg_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "kernel": W.kernel,
                 "achieved": achieved, "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
                 "frac": achieved / FP64_PIPE_PEAK_TINST,
                 "traffic": (KP_TRAFFIC_TF32.get(args.config) if (args.precision == "tf32x3" and args.gather == "bilinear"
-                                                                  and args.boundary == "open") else None),
-                "traffic_unit": "DRAM bytes per launch (ncu, cold cache, mean of the ring's three segment types; "
-                                "algorithmic 163 B/particle)",
-                "peak_source": "derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz (probe: 2.0/clk/SM)",
-                "avg_launch_ms": kp_avg_ms, "fp64_inst_per_particle_kick": inst_per_kick,
+                                                                  and args.boundary == "open"
+                                                                  and sha == FP64_INST_SOURCES_SHA) else None),
+                "traffic_unit": "DRAM bytes per launch (ncu, cold cache, mean of the ring's three segment types)",
+                "peak_source": None,  # after the live probe below
+                "avg_launch_ms": kp_avg_ms,
+                "fp64_inst_per_particle_kick": inst_per_kick,
+                "fp64_inst_model": {"per_element": dict(FP64_INST, base_split_form=FP64_INST_BASE_F32),
+                                    "element_mix_per_turn": mix,
+                                    "source": "ncu sm__thread_inst_executed_pipe_fp64_pred_on per launch, "
+                                              "profiles/kick_push_c2.md",
+                                    "fitted_on_sources_sha": FP64_INST_SOURCES_SHA, "current_sources_sha": sha,
+                                    "current": sha == FP64_INST_SOURCES_SHA},
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                        "algorithmic_bytes_per_particle_kick": kp_bytes,
+                        "peak_source": "of measured: MEASURED_PEAKS.json hbm_gbs"},
                 "solve_avg_ms": solve_ms / traced, "share_kick_push": kp_ms / (kp_ms + solve_ms)}
 
     # ---------------- the solve on the tensor cores (split-TF32 forms): tensor flops per traced solve
@@ -578,21 +702,26 @@ def run_ours(args):
     work = W.solver_work(h)
     if work is not None and work[0] > 0:
         solve_s = solve_ms / traced * 1e-3
-        tf32_peak = measured_peaks().get("bf16_tflops", 1900.0) / 2
+        bf16 = args.precision == "bf16x3"
+        tensor_peak = measured_peaks().get("bf16_tflops", 1900.0) / (1 if bf16 else 2)
         roofline_solve = {
-            "bound": "tensor", "kernel": "dft_gemm (split-TF32 DFT GEMMs on tcgen05, all phases of one solve)",
-            "achieved": work[0] / solve_s / 1e12, "peak": tf32_peak, "unit": "TFLOP/s",
-            "frac": work[0] / solve_s / 1e12 / tf32_peak,
-            "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops (burst) x 1/2, the nominal dense "
-                           "TF32/BF16 ratio",
+            "bound": "tensor",
+            "kernel": "dft_gemm (split-%s DFT GEMMs on tcgen05, all phases of one solve)" % ("BF16" if bf16 else "TF32"),
+            "achieved": work[0] / solve_s / 1e12, "peak": tensor_peak, "unit": "TFLOP/s",
+            "frac": work[0] / solve_s / 1e12 / tensor_peak,
+            "peak_source": ("of measured: MEASURED_PEAKS.json bf16_tflops (burst)" if bf16 else
+                            "of measured: MEASURED_PEAKS.json bf16_tflops (burst) x 1/2, the nominal dense "
+                            "TF32/BF16 ratio"),
             "tensor_flops_per_solve": work[0], "fft_equivalent_flops_per_solve": work[1],
             "fft_equivalent_tflops": work[1] / solve_s / 1e12, "solve_us_traced": solve_s * 1e6,
             "note": "latency-bound: a few microseconds of tensor work per phase; traced solves are serialised "
                     "with events (in the turn graph programmatic dependent launch overlaps the phases)"}
 
     # ---------------- live machine probes and the stand-alone deposit (shared-atomic roofline)
-    atom_cf, atom_rand, fp64_probe = sc.probe_peaks(stream)
+    atom_cf, atom_rand, fp64_probe = probe_peaks(stream)
     roofline["peak_probe_fp64_tinst"] = fp64_probe / 1e12
+    roofline["peak_source"] = ("derived: 152 SMs x 2 FP64 instructions/clk x 2.07 GHz; the FMA probe of this run "
+                               "reaches %.2f/clk/SM at 2.07 GHz" % (fp64_probe / 152 / 2.07e9))
     deposit = W.deposit_roofline(h, flush, atom_rand, atom_cf) if hasattr(W, "deposit_roofline") else None
     cufft = W.cufft_reference(flush) if hasattr(W, "cufft_reference") else None
 
@@ -610,26 +739,31 @@ def run_ours(args):
     e2e = {"value": world * n * n_kicks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 6 * 8 * n,
            "d2h_bytes_per_step": 6 * 8 * n}
 
-    solve_kernels = {"fp64": 3, "tf32x3": 4, "pipe_fp64": 4, "pipe_tf32x3": 5}[args.precision]
+    solve_kernels = {"fp64": 3, "tf32x3": 4, "bf16x3": 4, "pipe_fp64": 4, "pipe_tf32x3": 5}[args.precision]
     config = {"workload": WORKLOADS.get(args.config, args.config),
               "step": f"one turn = {n_kicks} SC kicks via "
                       f"{'sc_batch_track_turns' if args.config == 'c4' else 'sc_track_turns'} (CUDA graph)",
               "solve": {"fp64": "fp64 FFT convolution", "tf32x3": "tf32x3 DFT GEMMs on tcgen05",
+                        "bf16x3": "bf16x3 DFT GEMMs on tcgen05 (kind::f16)",
                         "pipe_fp64": "fp64 sine transforms (conducting pipe)",
                         "pipe_tf32x3": "tf32x3 sine-transform GEMMs on tcgen05 (conducting pipe)"}[args.precision],
               "particles": n, **W.grid_desc(),
               "solve_tiling": W.tiling_desc(h), "kick_push_shape": W.shape_desc(h),
-              "l2": "256 MB buffer written between timed turns", "parallelism": f"replicas x{world}"}
+              "l2": "256 MB buffer written between timed turns",
+              "parallelism": (f"replicas x{world}" if world == 1 or args.config == "c4" else
+                              f"one bunch sharded over {world} ranks ({n} particles each), uint64 charge all-reduce "
+                              "per space-charge kick captured in the turn graph")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "vs_baseline": None, "dtype": DTYPE_LABEL[args.precision], "data": "synthetic", "config": config,
             "roofline": roofline, "roofline_deposit": deposit, "roofline_solve": roofline_solve,
             "reference_cufft_solve": cufft, "e2e": e2e,
             "clocks": clk, "compare_form": compare,
             "gpu_launches": args.steps * n_kicks * (W.n_classes * solve_kernels + 1),
             "wall_s_timed": wall}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.config, args.cpu_kicks, args.boundary, args.gather, args.longitudinal)
+        line["cpu_baseline"] = cpu_baselines(args.config, args.cpu_kicks, args.boundary, args.gather,
+                                             args.longitudinal)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
