@@ -24,11 +24,14 @@
  *    kernels surface at the next synchronous call of that grid:
  *    SC_ERR_TIMEOUT when a tensor-core solve gave up on a bounded wait (the
  *    grid then refuses further solves, sc_solve and sc_track_turns return
- *    SC_ERR_TIMEOUT; destroy it and create a new one), else SC_ERR_NAN when
- *    deposits met particles whose x or y (or sigma, on a sliced grid) is NaN
- *    or infinite (such particles are outside the grid: no charge, no kick;
- *    the count is cleared by the call that reports it, whose outputs are
- *    still written).
+ *    SC_ERR_TIMEOUT; destroy it and create a new one), else SC_ERR_NAN for
+ *    non-finite particle coordinates: sc_grid_read reports those sc_deposit
+ *    met (x or y, or sigma on a sliced grid, NaN or infinite; such particles
+ *    are outside the grid: no charge, no kick; the count is cleared by the
+ *    call that reports it, whose outputs are still written), and tracking
+ *    with diagnostics reports a turn whose moments are not finite (the fused
+ *    deposits of a tracked turn do not test every particle: that costs the
+ *    FP64-bound push a few percent).
  *  - Particle state is SoA float64: x [m], px = Px/p0, y [m], py = Py/p0,
  *    sigma = s - c beta0 t [m], psigma (Sec. III, Eq. H).
  */

@@ -1080,7 +1080,13 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     SC_CUDA(cudaMemcpyAsync(diag, T->d_diag, (size_t)n_turns * 14 * sizeof(double), cudaMemcpyDeviceToHost,
                             g->stream));
     SC_CUDA(cudaStreamSynchronize(g->stream));
-    return check_grid_errors(g);
+    if ((st = check_grid_errors(g))) return st;
+    // a non-finite coordinate of any particle makes the moments of its turn non-finite
+    for (int k = 0; k < n_turns * 14; ++k)
+      if (!std::isfinite(diag[k]))
+        return set_error(SC_ERR_NAN, "non-finite particle coordinates: the moments of turn " +
+                                         std::to_string(k / 14) + " are not finite");
+    return SC_OK;
   }
   return SC_OK;
 }

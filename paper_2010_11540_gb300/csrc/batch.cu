@@ -829,6 +829,10 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
   if (T->diag) {
     SC_CUDA(cudaMemcpyAsync(diag, T->d_diag, (size_t)n_turns * nb * 14 * sizeof(double), cudaMemcpyDeviceToHost, S));
     SC_CUDA(cudaStreamSynchronize(S));
+    // a non-finite coordinate of any particle makes its bunch's moments of that turn non-finite
+    for (size_t k = 0; k < (size_t)n_turns * nb * 14; ++k)
+      if (!std::isfinite(diag[k]))
+        return set_error(SC_ERR_NAN, "non-finite particle coordinates in bunch " + std::to_string((k / 14) % nb));
   }
   return SC_OK;
 }

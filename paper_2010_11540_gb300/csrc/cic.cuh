@@ -66,6 +66,12 @@ __device__ __forceinline__ void deposit4(unsigned long long* dst, int nx, int ce
 // node in the tile -- else the global grid -- key = kGlobalKey | cell.  -1:
 // nothing to deposit.
 constexpr int kGlobalKey = 1 << 29;
+
+// The tile holds the whole grid of an unsliced deposit: every cell's four
+// nodes are in it at their own index (the common case, no key needed).
+__device__ __forceinline__ bool tile_is_grid(const GridGeom& g) {
+  return g.nz == 1 && g.wnx == g.nx && g.wny == g.ny;
+}
 __device__ __forceinline__ int deposit_key(bool use_tile, int* tile_k, const GridGeom& g, int cell, int i, int j,
                                            int k) {
   if (cell < 0) return -1;
@@ -213,11 +219,24 @@ __device__ __forceinline__ void tile_zero(unsigned long long* tile, int cells) {
 // the deposit.
 __device__ __forceinline__ void tile_flush(const unsigned long long* tile, unsigned long long* Q, const GridGeom& g) {
   const int cells = g.wnx * g.wny;
+  if (g.wnx == g.nx && g.wny == g.ny) {  // the tile is the whole slice: same indices
+    for (int c = threadIdx.x; c < cells; c += blockDim.x) {
+      const unsigned long long v = tile[c];
+      if (v) atomicAdd(Q + c, v);
+    }
+    return;
+  }
+  // a window: walk its bins with a running (row, column), no division per bin
+  int lj = threadIdx.x / g.wnx, li = threadIdx.x - lj * g.wnx;
+  const int step_j = blockDim.x / g.wnx, step_i = blockDim.x - step_j * g.wnx;
   for (int c = threadIdx.x; c < cells; c += blockDim.x) {
     const unsigned long long v = tile[c];
-    if (v) {
-      const int lj = c / g.wnx, li = c - lj * g.wnx;
-      atomicAdd(Q + (size_t)(g.wy0 + lj) * g.nx + g.wx0 + li, v);
+    if (v) atomicAdd(Q + (size_t)(g.wy0 + lj) * g.nx + g.wx0 + li, v);
+    lj += step_j;
+    li += step_i;
+    if (li >= g.wnx) {
+      li -= g.wnx;
+      ++lj;
     }
   }
 }
@@ -227,18 +246,18 @@ __device__ __forceinline__ bool nonfinite(double v) {
   return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) == 0x7ff0000000000000ull;
 }
 
-// A particle the deposit found outside grid g: count it as non-finite when its
-// position (or, on a sliced grid, its sigma) is (rare path, one atomic).
-__device__ __forceinline__ void count_nonfinite(const GridGeom& g, double x, double y, double sg,
-                                                unsigned long long* n_nan) {
-  if (n_nan && (nonfinite(x) || nonfinite(y) || (g.nz > 1 && nonfinite(sg)))) atomicAdd(n_nan, 1ull);
+// 1 for a particle whose position (or, on a sliced grid, its sigma) is not
+// finite: bit tests only, for particles the deposit found outside grid g; the
+// caller sums them in a register like the out-of-grid count (count_out).
+__device__ __forceinline__ unsigned int nonfinite_state(const GridGeom& g, double x, double y, double sg) {
+  return (unsigned int)(nonfinite(x) | nonfinite(y) | (g.nz > 1 && nonfinite(sg)));
 }
 
 // Block-wide sum of per-thread out-of-grid counts into a global counter.
 __device__ __forceinline__ void count_out(unsigned int out, unsigned long long* n_out) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) out += __shfl_xor_sync(0xffffffffu, out, o);
-  if ((threadIdx.x & 31) == 0 && out) atomicAdd(n_out, (unsigned long long)out);
+  if ((threadIdx.x & 31) == 0 && out && n_out) atomicAdd(n_out, (unsigned long long)out);
 }
 
 }  // namespace sc

@@ -29,13 +29,13 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __re
   tile_zero(tile, g.wnx * g.wny);
   if (threadIdx.x == 0) tile_k = g.nz > 1 ? -1 : 0;
   __syncthreads();
-  unsigned int out = 0;
+  unsigned int out = 0, bad = 0;  // particles outside the grid; of those, non-finite ones
   // one contiguous chunk per block (a sigma-sorted bunch keeps a block in one slice)
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t p_end = min(n, (int64_t)(blockIdx.x + 1) * chunk);
   const bool sliced = g.nz > 1;
-  // the next particle's coordinates are loaded before this one's atomics
   int64_t p = (int64_t)blockIdx.x * chunk + threadIdx.x;
+  // the next particle's coordinates are loaded before this one's deposit (hides their latency)
   double xn = 0.0, yn = 0.0, sn = 0.0;
   if (p < p_end) {
     xn = __ldg(x + p);
@@ -56,15 +56,18 @@ __global__ void __launch_bounds__(kDepThreads) deposit_kernel(const double* __re
     const int cell = locate<false>(g, xc, yc, sc_, a, fx, fy, i, j, k);
     if (cell < 0) {
       ++out;
-      count_nonfinite(g, xc, yc, sc_, n_nan);
+      bad += nonfinite_state(g, xc, yc, sc_);
     }
-    const int key = deposit_key(true, &tile_k, g, cell, i, j, k);
-    if (AGG)
-      deposit_warp(__activemask(), key, a, tile, g.wnx, Q, g.nx);
-    else
-      deposit_at(key, a, tile, g.wnx, Q, g.nx);
+    if (AGG) {  // an ordered bunch: the warp combines equal cells
+      deposit_warp(__activemask(), deposit_key(true, &tile_k, g, cell, i, j, k), a, tile, g.wnx, Q, g.nx);
+    } else if (tile_is_grid(g)) {
+      if (cell >= 0) deposit4(tile, g.nx, cell, a);
+    } else {
+      deposit_at(deposit_key(true, &tile_k, g, cell, i, j, k), a, tile, g.wnx, Q, g.nx);
+    }
   }
   count_out(out, n_out);
+  count_out(bad, n_nan);
   __syncthreads();
   if (tile_k >= 0) tile_flush(tile, Q + (size_t)tile_k * cells, g);
 }

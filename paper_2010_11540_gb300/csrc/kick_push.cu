@@ -223,10 +223,13 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
       const int cell = locate<!F32>(P.gd, s.x, s.y, s.sg, a, fx, fy, i, j, kz);
       if (cell < 0) {
         ++out;
-        count_nonfinite(P.gd, s.x, s.y, s.sg, P.n_nan);
         a = make_int2(0, 0);
       }
-      deposit_at(deposit_key(use_tile, tile_k, P.gd, cell, i, j, kz), a, tile, P.gd.wnx, P.Q, P.gd.nx);
+      if (use_tile && tile_is_grid(P.gd)) {
+        if (cell >= 0) deposit4(tile, P.gd.nx, cell, a);
+      } else {
+        deposit_at(deposit_key(use_tile, tile_k, P.gd, cell, i, j, kz), a, tile, P.gd.wnx, P.Q, P.gd.nx);
+      }
       if (CACHE) {
         P.cell[p] = cell;
         if (F32)
