@@ -50,7 +50,8 @@ WORKLOADS = {
 # base = gather + kick + fused deposit.  The quadrupole reads its matrix
 # entries from the per-particle family cache (51.0 when it computes them).
 # The counts belong to the kernel sources whose SHA-256 (first 16 hex digits)
-# is FP64_INST_SOURCES_SHA; the bench reports whether the sources still match.
+# is FP64_INST_SOURCES_SHA (re-measured on them: 52.14 per particle-kick
+# against the model's 52.33); the bench reports whether the sources still match.
 FP64_INST = {"base": 18.1, "drift": 12.1, "quad": 24.0, "sext": 5.0, "bend": 16.0, "rf": 30.0}
 FP64_INST_QUAD_UNCACHED = 51.0  # with the longitudinal kick (psigma changes at every kick: no cache)
 # split-TF32 form: float32 gather from the cached fixed-point weights
@@ -70,13 +71,17 @@ FP64_INST_LON_BEZIER_F32 = 13.95
 # DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
 # from ncu --set full (cold cache, mean of the three segment types): the
 # roofline's "traffic" for that workload; other workloads report null.
-KP_TRAFFIC_TF32 = {"c2": 122.5e6,   # 1e6 particles (the 200 MB working set partly stays in L2)
-                   "c4": 3859.8e6,  # the batched launch over 2.37e7 particles
-                   "c5": 1594.1e6}  # 1e7 particles, 32 slices
+KP_TRAFFIC_TF32 = {"c2": 122.7e6}  # 1e6 particles (the 200 MB working set partly stays in L2)
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
+# FP64-pipe instructions per particle of the stand-alone deposit (xi and eta: a
+# subtract and a multiply each, 4.23 measured with ncu
+# sm__thread_inst_executed_pipe_fp64_pred_on, profiles/deposit_c2.md; the
+# slice index two more)
+DEP_FP64_INST = 4.23
+DEP_FP64_INST_SLICE = 2.0
 KP_SOURCES = ("kick_push.cu", "maps.cuh", "cic.cuh", "fixpt.h")
-FP64_INST_SOURCES_SHA = "ca5be54ef7c53b49"
+FP64_INST_SOURCES_SHA = "052c41cbfc714941"
 # HBM bytes per particle-kick that the fused kick/push must move (algorithmic):
 # the six float64 coordinates read (48 B) and the five a kick and a push
 # change written back (40 B: psigma changes only in RF cavities); 96 B when
@@ -479,7 +484,19 @@ class SingleRun:
                 "peak_source": "live probe (libsc_probe.so): conflict-free shared u64 atomicAdd, each warp on 32 "
                                "consecutive words, measured in this run",
                 "context_peak_random_words": atom_random / 1e9,
-                "frac_of_random_words": rate / atom_random, "ordered_bunch": ordered}
+                "frac_of_random_words": rate / atom_random, "ordered_bunch": ordered,
+                # what binds it: the locate's FP64 subtract and multiply per axis (the cell, fraction and
+                # weights are decoded from the bits with integer instructions), on the 2-per-clock FP64 pipe
+                "fp64_pipe": {"fp64_inst_per_particle": DEP_FP64_INST + (DEP_FP64_INST_SLICE if self.slices else 0),
+                              "achieved": (DEP_FP64_INST + (DEP_FP64_INST_SLICE if self.slices else 0)) * self.n
+                              / (ms * 1e-3) / 1e12,
+                              "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
+                              "frac": (DEP_FP64_INST + (DEP_FP64_INST_SLICE if self.slices else 0)) * self.n
+                              / (ms * 1e-3) / 1e12 / FP64_PIPE_PEAK_TINST,
+                              "ceiling_atomics_frac": 4 / (DEP_FP64_INST + (DEP_FP64_INST_SLICE if self.slices else 0))
+                              * FP64_PIPE_PEAK_TINST * 1e12 / atom_conflict_free,
+                              "note": "at the FP64 peak the deposit adds 4 atomics per 4 FP64 instructions: the "
+                                      "ceiling_atomics_frac of the conflict-free atomic rate"}}
 
     def grid_desc(self):
         d = {"grid": [self.grid[0], self.grid[1]]}
