@@ -734,9 +734,11 @@ sc_status sc_set_particle_count(sc_grid* g, int64_t n_particles) {
 
 sc_status sc_track_turns_host(sc_grid* g, const sc_particles* host, const sc_beam* b, const sc_element* lattice,
                               int n_elems, int n_turns, double* diag) {
-  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  // every argument is checked before the device copies are sized
   sc_status st;
-  if ((st = check_particles(host)) || (st = check_beam(b)) || (st = check_elements(lattice, n_elems))) return st;
+  if ((st = check_particles(host))) return st;
+  if (!g) return set_error(SC_ERR_ARG, "grid is NULL");
+  if ((st = check_beam(b)) || (st = check_elements(lattice, n_elems))) return st;
   if (n_turns < 0) return set_error(SC_ERR_ARG, "negative turn count");
   const int64_t n = host->n;
   if (n_turns == 0 || n == 0) return SC_OK;

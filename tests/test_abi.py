@@ -106,6 +106,17 @@ def test_new_entry_points_reject_null_without_gpu(lib):
     assert lib.sc_get_solver_work(None, ctypes.byref(d), ctypes.byref(d)) == -1
     assert lib.sc_grid_charge_device(None, ctypes.byref(v), ctypes.byref(n)) == -1
     assert lib.sc_set_particle_count(None, 10) == -1
+    assert lib.sc_tunes(None, 10, 1, None, None) == -1
+    assert lib.sc_sort_particles(None, None, None) == -1
+    assert lib.sc_set_charge_reduce(None, sc.REDUCE_FN(), None, 0) == -1
+    assert lib.sc_moments_noalloc(None, None, None) == -1
+
+
+def test_oversized_host_bunch_rejected_before_any_allocation(lib):
+    """A host bunch of more particles than a grid's 64-bit charge can hold is
+    refused with SC_ERR_OVERFLOW before anything is sized or copied."""
+    host = sc.Particles(*(ctypes.c_void_p(8).value,) * 6, 1 << 24)
+    assert lib.sc_track_turns_host(None, ctypes.byref(host), None, None, 0, 1, None) == -4
 
 
 def test_host_particle_marshalling():

@@ -39,18 +39,18 @@ FIXED_TILING = (0, 0, 0, 0)
 
 def track_single(parts, b, grid, lat, turns, precision, diag=False):
     g = sc.create_grid(*grid, precision=precision)
-    if precision == "tf32x3":
+    if precision in ("tf32x3", "bf16x3"):
         sc.set_solver_tiling(g, FIXED_TILING)
     st = to_gpu(parts)
     d = sc.track_turns(g, st, b, lat, turns, diag=diag)
     return to_host(st), d
 
 
-@pytest.mark.parametrize("precision", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("precision", ["fp64", "tf32x3", "bf16x3"])
 def test_batch_equals_single_bunch_turns(precision):
     bunches = mixed_bunches()
     batch = sc.create_batch([g for _, _, g, _ in bunches], precision=precision)
-    if precision == "tf32x3":
+    if precision in ("tf32x3", "bf16x3"):
         sc.batch_set_solver_tiling(batch, FIXED_TILING)  # the same summation order as the single grids
     states = [to_gpu(p) for p, _, _, _ in bunches]
     diag = sc.batch_track_turns(batch, states, [b for _, b, _, _ in bunches], [l for _, _, _, l in bunches], 2,
