@@ -744,7 +744,7 @@ def run_ours(args):
 
     # ---------------- end to end: host buffers through the public API
     pinned = W.pinned()
-    e2e_steps = max(2, args.steps // 2)
+    e2e_steps = max(3, args.steps // 2)
     with torch.cuda.stream(stream):
         W.host_turn(h, pinned)
         torch.cuda.synchronize()

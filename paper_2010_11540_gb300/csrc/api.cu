@@ -822,7 +822,10 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
     const unsigned char* c = (const unsigned char*)v;
     key.insert(key.end(), c, c + n);
   };
-  put(p, sizeof *p);
+  // what the kick/push shape depends on: the particle count, beam, lattice and
+  // settings, not where the particles live (the host-buffer call tracks from
+  // the library's own staging copy and keeps the shape chosen for the caller's)
+  put(&p->n, sizeof p->n);
   put(b, sizeof *b);
   put(&n_elems, sizeof n_elems);
   if (n_elems) put(lattice, (size_t)n_elems * sizeof(sc_element));
@@ -830,7 +833,8 @@ sc_status sc_track_turns(sc_grid* g, const sc_particles* p, const sc_beam* b, co
   put(&g->gather, sizeof g->gather);
   put(&g->kp_threads_set, sizeof g->kp_threads_set);
   put(&g->kp_trav_set, sizeof g->kp_trav_set);
-  const std::vector<unsigned char> shape_key = key;  // what the kick/push shape depends on
+  const std::vector<unsigned char> shape_key = key;
+  put(p, sizeof *p);
   put(&g->reduce_fn, sizeof g->reduce_fn);
   put(&g->reduce_user, sizeof g->reduce_user);
   put(&g->reduce_total, sizeof g->reduce_total);

@@ -511,15 +511,19 @@ sc_status sc_batch_track_turns(sc_batch* B, const sc_bunch* bunches, int n_turns
     const unsigned char* c = (const unsigned char*)v;
     key.insert(key.end(), c, c + n);
   };
+  // what the kick/push shape depends on: the bunches' counts, beams and lattices
+  // and the settings, not where the particles live (the host-buffer call tracks
+  // from the library's own staging copies and keeps the shape chosen for the caller's)
   for (int b = 0; b < nb; ++b) {
-    put(&bunches[b].particles, sizeof(sc_particles));
+    put(&bunches[b].particles.n, sizeof(int64_t));
     put(&bunches[b].beam, sizeof(sc_beam));
     put(&bunches[b].n_elems, sizeof(int));
     if (bunches[b].n_elems) put(bunches[b].lattice, (size_t)bunches[b].n_elems * sizeof(sc_element));
   }
   put(&B->kp_threads_set, sizeof B->kp_threads_set);
   put(&B->kp_waves_set, sizeof B->kp_waves_set);
-  const std::vector<unsigned char> shape_key = key;  // what the kick/push shape depends on
+  const std::vector<unsigned char> shape_key = key;
+  for (int b = 0; b < nb; ++b) put(&bunches[b].particles, sizeof(sc_particles));
   const int want_diag = diag != nullptr;
   put(&want_diag, sizeof want_diag);
   put(&B->trace, sizeof B->trace);

@@ -211,6 +211,29 @@ def test_batch_kick_push_shapes_bit_identical():
                 assert np.array_equal(got[i][k], tuned[i][k]), (shape, i, k)
 
 
+def test_batch_host_buffers_keep_the_tuned_shape():
+    """A batch tracked from host buffers (the library's staging copies) keeps
+    the kick/push shape timed for the same bunches in device buffers, and gives
+    the same bits."""
+    bunches = synth.c4_bunches(seed=99, n_bunches=8, n_min=2e4, n_max=1.2e5)
+    grids = [g for _, _, g, _ in bunches]
+    beams = [b for _, b, _, _ in bunches]
+    lats = [l for _, _, _, l in bunches]
+    B = sc.create_batch(grids, precision="tf32x3")
+    sc.batch_set_solver_tiling(B, FIXED_TILING)
+    st = [to_gpu(p) for p, _, _, _ in bunches]
+    sc.batch_track_turns(B, st, beams, lats, 1)
+    shape = sc.batch_get_kick_push_shape(B)
+    assert shape[2] > 0
+    host = [{k: np.array(p[k], copy=True) for k in KEYS} for p, _, _, _ in bunches]
+    sc.batch_track_turns_host(B, host, beams, lats, 1)
+    assert sc.batch_get_kick_push_shape(B) == shape
+    for i, x in enumerate(st):
+        got = to_host(x)
+        for k in KEYS:
+            assert np.array_equal(host[i][k], got[k]), (i, k)
+
+
 def test_batch_shape_arguments():
     bunches = mixed_bunches()[:2]
     B = sc.create_batch([g for _, _, g, _ in bunches], precision="tf32x3")

@@ -72,6 +72,25 @@ def test_sliced_grid_shapes():
     assert_same(fixed, tuned)
 
 
+def test_host_buffers_keep_the_tuned_shape():
+    """The shape is chosen for the bunch's size and lattice, not for where its
+    arrays live: tracking the same bunch from host buffers (through the
+    library's staging copy) reuses the choice -- no second timing -- and both
+    calls give the same bits."""
+    parts, b, grid, lat = synth.workload("c2", n=N_TUNED)
+    g = sc.create_grid(*grid, precision="tf32x3")
+    st = to_gpu(parts)
+    sc.track_turns(g, st, b, lat, 1)
+    shape = sc.get_kick_push_shape(g)
+    assert shape[2] > 0
+    host = {k: np.array(parts[k], copy=True) for k in KEYS}
+    sc.track_turns_host(g, host, b, lat, 1)
+    assert sc.get_kick_push_shape(g) == shape
+    dev = to_host(st)
+    for k in KEYS:
+        assert np.array_equal(host[k], dev[k]), k
+
+
 def test_small_bunch_takes_default_shape():
     parts, b, grid, lat = synth.workload("c2", n=5000)
     got = run(parts, b, grid, lat, 1, "fp64")
