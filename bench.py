@@ -71,7 +71,9 @@ FP64_INST_LON_BEZIER_F32 = 13.95
 # DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
 # from ncu --set full (cold cache, mean of the three segment types): the
 # roofline's "traffic" for that workload; other workloads report null.
-KP_TRAFFIC_TF32 = {"c2": 122.7e6}  # 1e6 particles (the 200 MB working set partly stays in L2)
+KP_TRAFFIC_TF32 = {"c2": 122.7e6,  # 1e6 particles (the 200 MB working set partly stays in L2)
+                   "c4": 3860.0e6,  # 2.37e7 particles, batched launch (profiles/kick_push_traffic_c4_c5.md)
+                   "c5": 1594.1e6}  # 1e7 particles in 32 slices
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 # FP64-pipe instructions per particle of the stand-alone deposit (xi and eta: a
