@@ -280,7 +280,14 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   constexpr int KC = Op<EL>::KC;
   T* const out_hi = (T*)g.out_hi;
   T* const out_lo = (T*)g.out_lo;
-  constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
+  // Narrow tiles (NT <= 32), where an MMA's time goes mostly to reading its A slice:
+  // accumulators [0, 2 NT) = a_hi [b_hi | b_lo] (one MMA of width 2 NT over the two B
+  // tiles, which lie back to back in shared memory: the A slice is read once for both
+  // products) and [2 NT, 3 NT) = a_lo b_hi, summed by the epilogue.  Wider tiles: the
+  // three products in one accumulator of NT columns (a few CTAs' allocations then fit
+  // an SM's tensor memory, so the next phase's CTAs allocate while this one runs).
+  constexpr bool FUSE = NT <= 32;
+  constexpr int TMEM_COLS = FUSE ? (3 * NT <= 64 ? 64 : 128) : (NT < 32 ? 32 : NT);
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) uint64_t full_bar[L::STAGES], empty_bar[L::STAGES], accum_bar;
@@ -355,6 +362,11 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
     const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx);
     const float qscale = g.qfac * (g.stack_scale ? g.stack_scale[n0 / g.ny] : g.scale);
     constexpr int G = 8;
+    // pair e = (row r, columns 2c, 2c+1) with r = e / (nx/2): this thread's pairs are
+    // e = threadIdx.x + m kThreads, walked with a running (r, c) -- no division per pair
+    const int hx = g.nx >> 1;
+    const int step_r = kThreads / hx, step_c = kThreads - step_r * hx;
+    int pr = threadIdx.x / hx, pc = threadIdx.x - pr * hx;
     for (int e0 = threadIdx.x; e0 < pairs; e0 += G * kThreads) {
       longlong2 v[G];
 #pragma unroll
@@ -365,11 +377,19 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 #pragma unroll
       for (int u = 0; u < G; ++u) {
         const int e = e0 + u * kThreads;
+        const int r = pr;
+        const int i0 = 2 * pc;
+        pr += step_r;
+        pc += step_c;
+        if (pc >= hx) {
+          pc -= hx;
+          ++pr;
+        }
         if (e < pairs) {
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const unsigned long long qi = (unsigned long long)(h ? v[u].y : v[u].x);
-            const int el = 2 * e + h, r = el / g.nx, i = el % g.nx;
+            const int i = i0 + h;
             // uint64 -> float through its 32-bit halves (no FP64 instruction)
             const float qv =
                 fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * qscale;
@@ -451,15 +471,21 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       unsigned char* sb = stage_base + st * L::STAGE;
       const unsigned char* bh =
           (PH == P1 || PH == D1) ? resident + (2 * (kc0 + kc)) * L::B_TILE : sb + 2 * L::A_TILE;
-      const unsigned char* bl = bh + L::B_TILE;
-      const uint64_t dbh = desc_sw128(smem_u32(bh)), dbl = desc_sw128(smem_u32(bl));
+      const uint64_t dbh = desc_sw128(smem_u32(bh));  // b_hi; b_lo follows at bh + B_TILE
       const uint64_t dah = desc_sw128(smem_u32(sb)), dal = desc_sw128(smem_u32(sb + L::A_TILE));
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk) {
         const uint64_t o = (uint64_t)(kk * 2);  // 32 bytes per K step, in 16-byte units
-        mma_split<EL>(tmem, dah + o, dbh + o, idesc<NT, EL>(), (kc > 0 || kk > 0) ? 1u : 0u);
-        mma_split<EL>(tmem, dah + o, dbl + o, idesc<NT, EL>(), 1u);
-        mma_split<EL>(tmem, dal + o, dbh + o, idesc<NT, EL>(), 1u);
+        const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+        if (FUSE) {
+          mma_split<EL>(tmem, dah + o, dbh + o, idesc<2 * NT, EL>(), acc);       // a_hi b_hi | a_hi b_lo
+          mma_split<EL>(tmem + 2 * NT, dal + o, dbh + o, idesc<NT, EL>(), acc);  // a_lo b_hi
+        } else {
+          const uint64_t dbl = desc_sw128(smem_u32(bh + L::B_TILE));
+          mma_split<EL>(tmem, dah + o, dbh + o, idesc<NT, EL>(), acc);
+          mma_split<EL>(tmem, dah + o, dbl + o, idesc<NT, EL>(), 1u);
+          mma_split<EL>(tmem, dal + o, dbh + o, idesc<NT, EL>(), 1u);
+        }
       }
       mma_commit(&empty_bar[st]);
     }
@@ -483,6 +509,17 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   static_assert(CW % 4 == 0, "whole float4 column groups");
   const int c0 = rank * CW;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  // 16 columns of C from column ta: the three split products' accumulators summed
+  auto tmem_ld_c16 = [&](uint32_t ta, float (&v)[16]) {
+    tmem_ld16(ta, v);
+    if (FUSE) {
+      float b[16], c[16];
+      tmem_ld16(ta + NT, b);
+      tmem_ld16(ta + 2 * NT, c);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v[q] = (v[q] + b[q]) + c[q];
+    }
+  };
 
   // Finish columns cb .. cb+CH-1 of the tile (values in acc) for this phase.
   auto finish = [&](const float* acc, int cb) {
@@ -600,7 +637,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 #pragma unroll
       for (int c16 = 0; c16 < NT / 16; ++c16) {
         float v[16];
-        tmem_ld16(trow + c16 * 16, v);
+        tmem_ld_c16(trow + c16 * 16, v);
 #pragma unroll
         for (int q4 = 0; q4 < 4; ++q4)
           red[t * (NT / 4) + c16 * 4 + q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
@@ -631,7 +668,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 #pragma unroll
     for (int c16 = 0; c16 < NT / 16; ++c16) {
       float acc[16];
-      tmem_ld16(trow + c16 * 16, acc);
+      tmem_ld_c16(trow + c16 * 16, acc);
       finish(acc, c16 * 16);
     }
   }
