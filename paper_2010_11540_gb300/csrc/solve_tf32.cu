@@ -251,6 +251,12 @@ struct Smem {
   static constexpr int BYTES = STAGES * STAGE + RESIDENT + 1024 /*align slack*/;
   static_assert(BYTES <= 227 * 1024, "shared memory of one CTA");
 };
+// split-K reduction buffer after the stages and resident tiles: SK slots of this
+// CTA's NT / SK columns for all TM rows, float32
+template <int SK, int NT>
+constexpr int red_bytes() {
+  return SK > 1 ? TM * NT * 4 : 0;
+}
 
 // Instruction descriptor: D f32, A = B = tf32 (kind::tf32: format 2) or bf16
 // (kind::f16: format 1), both K-major, M = 128, N = NT.
@@ -276,6 +282,7 @@ template <int PH, int SK, int NT, int STAGES, int EL>
 __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ GemmArgs g) {
   using L = Smem<PH, NT, STAGES>;
   using R = Roles<PH>;
+  static_assert(L::BYTES + red_bytes<SK, NT>() <= 227 * 1024, "shared memory of one CTA");
   using T = typename Op<EL>::T;
   constexpr int KC = Op<EL>::KC;
   T* const out_hi = (T*)g.out_hi;
@@ -626,21 +633,28 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   };
 
   if (SK > 1) {
-    // partial tiles -> shared memory (the stages are idle now), summed across the cluster.
-    // After a timed-out wait copies or MMAs may still use the stages: nothing is
-    // written there, the cluster barriers are still taken (every CTA of the
-    // cluster reaches them), and the error word marks the results invalid.
-    static_assert(SK == 1 || kThreads * NT * 4 <= L::STAGES * L::STAGE, "reduction buffer fits the stages");
+    // Partial tiles summed across the cluster: each CTA stores the columns rank r
+    // finishes (CW of them) into rank r's reduction buffer (shared memory of its
+    // own, not the stages), slot = the storing CTA's rank; one cluster barrier
+    // (release / acquire) makes them visible, and each CTA sums its slots locally.
+    // No CTA touches another's shared memory after the barrier, so none waits for
+    // the others before leaving.  After a timed-out wait nothing is stored, the
+    // barrier is still taken (every CTA of the cluster reaches it), and the error
+    // word marks the results invalid.
     cg::cluster_group cl = cg::this_cluster();
-    float4* red = (float4*)stage_base;
+    float4* red = (float4*)(smem + L::STAGES * L::STAGE + L::RESIDENT);  // [SK][kThreads][CW / 4]
     if (have) {
 #pragma unroll
       for (int c16 = 0; c16 < NT / 16; ++c16) {
         float v[16];
         tmem_ld_c16(trow + c16 * 16, v);
 #pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4)
-          red[t * (NT / 4) + c16 * 4 + q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const int col = c16 * 16 + 4 * q4, owner = col / CW, cc = col - owner * CW;
+          float4* dst = owner == rank ? red : cl.map_shared_rank(red, owner);
+          dst[(rank * kThreads + t) * (CW / 4) + cc / 4] =
+              make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+        }
       }
     }
     cl.sync();
@@ -651,10 +665,9 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       for (int u = 0; u < CH; ++u) acc[u] = 0.f;
 #pragma unroll
       for (int q = 0; q < SK; ++q) {
-        const float4* rem = cl.map_shared_rank(red, q);
 #pragma unroll
         for (int q4 = 0; q4 < CH / 4; ++q4) {
-          const float4 w = rem[t * (NT / 4) + cb / 4 + q4];
+          const float4 w = red[(q * kThreads + t) * (CW / 4) + (cb - c0) / 4 + q4];
           acc[4 * q4] += w.x;
           acc[4 * q4 + 1] += w.y;
           acc[4 * q4 + 2] += w.z;
@@ -663,7 +676,6 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       }
       if (ok) finish(acc, cb);
     }
-    cl.sync();  // keep this CTA's partial tile alive until every rank has read it
   } else if (ok) {
 #pragma unroll
     for (int c16 = 0; c16 < NT / 16; ++c16) {
@@ -865,7 +877,7 @@ struct Variant {
 
 template <int PH, int SK, int NT, int ST, int EL = E_TF32>
 Variant variant() {
-  return Variant{SK, NT, ST, Smem<PH, NT, ST>::BYTES, (const void*)dft_gemm<PH, SK, NT, ST, EL>};
+  return Variant{SK, NT, ST, Smem<PH, NT, ST>::BYTES + red_bytes<SK, NT>(), (const void*)dft_gemm<PH, SK, NT, ST, EL>};
 }
 
 // Candidates per phase (split-K cluster size SK, tile width NT, pipeline
