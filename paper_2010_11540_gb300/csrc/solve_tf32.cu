@@ -345,6 +345,25 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   tc_fence_after();
   const uint32_t tmem = tmem_base_s;
 
+  // P2A: the spectra of this thread's row for the epilogue's first column chunk, loaded
+  // now (constants): left to the epilogue, their latency sat on the solve's critical path
+  constexpr int CW = NT / SK;             // columns finished by this CTA
+  constexpr int CH = CW < 16 ? CW : 16;   // columns per epilogue chunk
+  const int c0 = rank * CW;
+  float pre_sx[CH], pre_sy[CH];
+  if (PH == P2A) {
+    const int rr = a_row + threadIdx.x, kr = rr < g.My ? rr : rr - g.My;
+    const int nb = n0 + c0, s0 = nb / g.Npad, q0 = nb - s0 * g.Npad;
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      const bool wrap = q0 + u >= g.Npad;  // CH <= 16 <= Npad: at most one grid boundary
+      const int pq = q0 + u - (wrap ? g.Npad : 0);
+      const bool in = nb + u < g.n_total;
+      pre_sx[u] = in ? __ldg(g.Sx + (size_t)pq * g.My + kr) : 0.f;
+      pre_sy[u] = in ? __ldg(g.Sy + (size_t)pq * g.My + kr) : 0.f;
+    }
+  }
+
   // constant operand of the first stages: independent of the previous kernel
   if (threadIdx.x == 0) {
     for (int kc = 0; kc < pre; ++kc) {
@@ -511,10 +530,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   const int t = warp * 32 + lane;
   const int r = a_row + t;  // row of C
   const bool ok = __all_sync(0xffffffffu, have && !abort_s);
-  constexpr int CW = NT / SK;             // columns finished by this CTA
-  constexpr int CH = CW < 16 ? CW : 16;   // columns per epilogue chunk
   static_assert(CW % 4 == 0, "whole float4 column groups");
-  const int c0 = rank * CW;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   // 16 columns of C from column ta: the three split products' accumulators summed
   auto tmem_ld_c16 = [&](uint32_t ta, float (&v)[16]) {
@@ -545,17 +561,21 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
       const int k = re ? r : r - g.My;
       const int col = re ? g.My + k : k;
       const float sgn = re ? 1.f : -1.f;
-      // all spectrum loads first (the stores below could alias them for the compiler)
+      // stacked column n = n0 + cb + u: grid n / Npad, p = n % Npad (one division per
+      // chunk); the first chunk's spectra were loaded before the main loop, the
+      // others' are loaded here, all before the stores (which could alias them)
+      const int sl0 = (n0 + cb) / g.Npad, p0 = n0 + cb - sl0 * g.Npad;
       float sx[CH], sy[CH];
       int sl[CH], pp[CH];
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
-        const int n = n0 + cb + u;  // stacked column: grid n / Npad, p = n % Npad
-        sl[u] = n / g.Npad;
-        pp[u] = n - sl[u] * g.Npad;
+        const int n = n0 + cb + u;
+        const bool wrap = p0 + u >= g.Npad;
+        sl[u] = sl0 + (wrap ? 1 : 0);
+        pp[u] = p0 + u - (wrap ? g.Npad : 0);
         const bool in = n < g.n_total;
-        sx[u] = in ? __ldg(g.Sx + (size_t)pp[u] * g.My + k) : 0.f;
-        sy[u] = in ? __ldg(g.Sy + (size_t)pp[u] * g.My + k) : 0.f;
+        sx[u] = cb == c0 ? pre_sx[u] : in ? __ldg(g.Sx + (size_t)pp[u] * g.My + k) : 0.f;
+        sy[u] = cb == c0 ? pre_sy[u] : in ? __ldg(g.Sy + (size_t)pp[u] * g.My + k) : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < CH; ++u) {
