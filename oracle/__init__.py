@@ -13,8 +13,12 @@ as the primitive of Hockney's zero-padded method (Sec. I reference
 [Hockney]); the tracking loop follows the PIC loop of Sec. I (deposit ->
 Poisson -> kick/push) with the kick of Sec. IV.
 
-Functions whose parity is pinned only against the oracle itself are marked
-"parity unpinned" in their docstrings (long-run statistics).
+Every function is pinned by tests/test_oracle_*.py against something other
+than itself (closed forms, invariants, brute force on tiny inputs, values the
+paper prints).  The long-run statistics (100-turn emittances and tune spreads
+of an unmatched beam) have no closed form: track(), which produces them, is
+pinned step by step (one-turn pins, the small-amplitude tune shift, the maps'
+symplecticity, thread bit-identity), not over 100 turns.
 """
 from __future__ import annotations
 
