@@ -383,22 +383,34 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
   }
   if (PH == P1) {
     // B operand = normalised charge rows n0 .. n0+NT-1 (NT divides ny: one stacked grid per
-    // tile), all K = nx, split hi/lo, swizzled; 16-byte loads, issued in groups of 8.
-    const int pairs = NT * g.nx / 2;
-    const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx);
+    // tile), this CTA's K columns kcol0 .. kcol0+kcols-1 (all nx without split-K), split
+    // hi/lo, swizzled; 16-byte loads, issued in groups of 8.
+    const int kcol0 = kc0 * KC, kcols = kpc * KC;
+    const int hx = kcols >> 1;  // column pairs per row
+    const int pairs = NT * hx;
+    const longlong2* q2 = (const longlong2*)(g.Q + (size_t)n0 * g.nx + kcol0);
+    const int row2 = g.nx >> 1;  // a charge row in pairs
     const float qscale = g.qfac * (g.stack_scale ? g.stack_scale[n0 / g.ny] : g.scale);
     constexpr int G = 8;
-    // pair e = (row r, columns 2c, 2c+1) with r = e / (nx/2): this thread's pairs are
+    // pair e = (row r, columns kcol0 + 2c, +1) with r = e / hx: this thread's pairs are
     // e = threadIdx.x + m kThreads, walked with a running (r, c) -- no division per pair
-    const int hx = g.nx >> 1;
     const int step_r = kThreads / hx, step_c = kThreads - step_r * hx;
     int pr = threadIdx.x / hx, pc = threadIdx.x - pr * hx;
     for (int e0 = threadIdx.x; e0 < pairs; e0 += G * kThreads) {
       longlong2 v[G];
+      {
+        int lr = pr, lc = pc;
 #pragma unroll
-      for (int u = 0; u < G; ++u) {
-        const int e = e0 + u * kThreads;
-        v[u] = (e < pairs) ? q2[e] : make_longlong2(0, 0);
+        for (int u = 0; u < G; ++u) {
+          const int e = e0 + u * kThreads;
+          v[u] = (e < pairs) ? q2[lr * row2 + lc] : make_longlong2(0, 0);
+          lr += step_r;
+          lc += step_c;
+          if (lc >= hx) {
+            lc -= hx;
+            ++lr;
+          }
+        }
       }
 #pragma unroll
       for (int u = 0; u < G; ++u) {
@@ -415,7 +427,7 @@ __global__ void __launch_bounds__(kThreads, 1) dft_gemm(const __grid_constant__ 
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const unsigned long long qi = (unsigned long long)(h ? v[u].y : v[u].x);
-            const int i = i0 + h;
+            const int i = kcol0 + i0 + h;
             // uint64 -> float through its 32-bit halves (no FP64 instruction)
             const float qv =
                 fmaf(__uint2float_rn((unsigned)(qi >> 32)), 4294967296.f, __uint2float_rn((unsigned)qi)) * qscale;
@@ -906,7 +918,7 @@ Variant variant() {
 // K-split tiles give a single small grid enough CTAs.
 const std::vector<Variant>& variants(int ph, int el = E_TF32) {
   static const std::vector<Variant> v[8] = {
-      {variant<P1, 1, 16, 4>(), variant<P1, 1, 32, 4>(), variant<P1, 1, 64, 2>()},
+      {variant<P1, 1, 16, 4>(), variant<P1, 1, 32, 4>(), variant<P1, 1, 64, 2>(), variant<P1, 2, 16, 4>()},
       {variant<P2A, 2, 16, 5>(), variant<P2A, 1, 32, 4>(), variant<P2A, 2, 32, 4>(), variant<P2A, 1, 64, 4>(),
        variant<P2A, 1, 128, 3>()},
       {variant<P2B, 4, 16, 5>(), variant<P2B, 2, 32, 4>(), variant<P2B, 1, 64, 4>(), variant<P2B, 2, 64, 4>(),
@@ -920,7 +932,8 @@ const std::vector<Variant>& variants(int ph, int el = E_TF32) {
       {variant<D4, 2, 16, 5>(), variant<D4, 1, 32, 4>(), variant<D4, 2, 32, 4>(), variant<D4, 1, 64, 4>()}};
   // BF16 operands (open boundary): the same tilings; a K chunk holds 64 elements
   static const std::vector<Variant> b[4] = {
-      {variant<P1, 1, 16, 4, E_BF16>(), variant<P1, 1, 32, 4, E_BF16>(), variant<P1, 1, 64, 2, E_BF16>()},
+      {variant<P1, 1, 16, 4, E_BF16>(), variant<P1, 1, 32, 4, E_BF16>(), variant<P1, 1, 64, 2, E_BF16>(),
+       variant<P1, 2, 16, 4, E_BF16>()},
       {variant<P2A, 2, 16, 5, E_BF16>(), variant<P2A, 1, 32, 4, E_BF16>(), variant<P2A, 2, 32, 4, E_BF16>(),
        variant<P2A, 1, 64, 4, E_BF16>(), variant<P2A, 1, 128, 3, E_BF16>()},
       {variant<P2B, 4, 16, 5, E_BF16>(), variant<P2B, 2, 32, 4, E_BF16>(), variant<P2B, 1, 64, 4, E_BF16>(),
