@@ -50,12 +50,13 @@ WORKLOADS = {
 # base = gather + kick + fused deposit.  The quadrupole reads its matrix
 # entries from the per-particle family cache (51.0 when it computes them).
 # The counts belong to the kernel sources whose SHA-256 (first 16 hex digits)
-# is FP64_INST_SOURCES_SHA (re-measured on them: 52.14 per particle-kick
-# against the model's 52.33); the bench reports whether the sources still match.
-FP64_INST = {"base": 18.1, "drift": 12.1, "quad": 24.0, "sext": 5.0, "bend": 16.0, "rf": 30.0}
+# is FP64_INST_SOURCES_SHA (the three segment types measured on them: 56.8,
+# 69.0 and 18.0, mean 47.9 per particle-kick, the model's own figure); the
+# bench reports whether the sources still match.
+FP64_INST = {"base": 17.5, "drift": 12.2, "quad": 21.6, "sext": 5.0, "bend": 16.0, "rf": 30.0}
 FP64_INST_QUAD_UNCACHED = 51.0  # with the longitudinal kick (psigma changes at every kick: no cache)
 # split-TF32 form: float32 gather from the cached fixed-point weights
-FP64_INST_BASE_F32 = 8.8
+FP64_INST_BASE_F32 = 5.8
 # sliced grids: the slice index (one subtract, one multiply; the floor is integer work) per locate
 FP64_INST_SLICE = 2.0
 # Bezier gather instead of bilinear fields (extra per particle-kick), and the
@@ -68,12 +69,13 @@ FP64_INST_LON_BEZIER = 83.7
 FP64_INST_BEZIER_F32 = 3.85
 FP64_INST_LON_F32 = 13.95
 FP64_INST_LON_BEZIER_F32 = 13.95
-# DRAM bytes (read + write) per kick_push launch on the c2 workload, split form,
-# from ncu --set full (cold cache, mean of the three segment types): the
-# roofline's "traffic" for that workload; other workloads report null.
-KP_TRAFFIC_TF32 = {"c2": 122.7e6,  # 1e6 particles (the 200 MB working set partly stays in L2)
-                   "c4": 3860.0e6,  # 2.37e7 particles, batched launch (profiles/kick_push_traffic_c4_c5.md)
-                   "c5": 1594.1e6}  # 1e7 particles in 32 slices
+# DRAM bytes (read + write) per kick_push launch, split form, from ncu (cold
+# cache; c2: mean of the three segment types), with the kernel sources'
+# SHA-256 (first 16 hex digits) they were captured on: the roofline's
+# "traffic" while the sources still match; other workloads report null.
+KP_TRAFFIC_TF32 = {"c2": (122.5e6, "9bbf6421bbb27d3f"),  # 1e6 particles (the working set partly stays in L2)
+                   "c4": (3860.0e6, "052c41cbfc714941"),  # 2.37e7 particles, batched (kick_push_traffic_c4_c5.md)
+                   "c5": (1594.1e6, "052c41cbfc714941")}  # 1e7 particles in 32 slices
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
 FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 # FP64-pipe instructions per particle of the stand-alone deposit (xi and eta: a
@@ -82,8 +84,8 @@ FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 # slice index two more)
 DEP_FP64_INST = 4.23
 DEP_FP64_INST_SLICE = 2.0
-KP_SOURCES = ("kick_push.cu", "maps.cuh", "cic.cuh", "fixpt.h")
-FP64_INST_SOURCES_SHA = "052c41cbfc714941"
+KP_SOURCES = ("kick_push.cu", "maps.cuh", "cic.cuh", "fixpt.h", "sc_internal.cuh")
+FP64_INST_SOURCES_SHA = "9bbf6421bbb27d3f"
 # HBM bytes per particle-kick that the fused kick/push must move (algorithmic):
 # the six float64 coordinates read (48 B) and the five a kick and a push
 # change written back (40 B: psigma changes only in RF cavities); 96 B when
@@ -698,9 +700,10 @@ def run_ours(args):
     roofline = {"bound": "alu", "kernel": W.kernel,
                 "achieved": achieved, "peak": FP64_PIPE_PEAK_TINST, "unit": "T FP64-inst/s",
                 "frac": achieved / FP64_PIPE_PEAK_TINST,
-                "traffic": (KP_TRAFFIC_TF32.get(args.config) if (args.precision == "tf32x3" and args.gather == "bilinear"
-                                                                  and args.boundary == "open"
-                                                                  and sha == FP64_INST_SOURCES_SHA) else None),
+                "traffic": (KP_TRAFFIC_TF32[args.config][0]
+                            if (args.config in KP_TRAFFIC_TF32 and args.precision == "tf32x3"
+                                and args.gather == "bilinear" and args.boundary == "open"
+                                and sha == KP_TRAFFIC_TF32[args.config][1]) else None),
                 "traffic_unit": "DRAM bytes per launch (ncu, cold cache, mean of the ring's three segment types)",
                 "peak_source": None,  # after the live probe below
                 "avg_launch_ms": kp_avg_ms,

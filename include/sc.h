@@ -324,7 +324,9 @@ sc_status sc_trace_read(sc_grid *g, double *kick_push_ms, double *solve_ms, int6
  * phases (row DFT, column DFT, inverse column DFT, inverse row DFT) has a few
  * kernel variants (tile width, split-K cluster size, pipeline depth); the
  * fastest for the grid (and its stacked slices) is chosen by timing them all
- * when the grid is created.  sc_get_solver_tiling reads the four variant
+ * when the first grid of its geometry (size, stack depth, operand type) is
+ * created on a device; later grids of that geometry in the process take the
+ * same choice, so they give the same bits.  sc_get_solver_tiling reads the four variant
  * indices and, if desc != NULL, describes them in desc (n bytes, always
  * NUL-terminated); sc_set_solver_tiling forces them (an entry of -1 keeps
  * that phase's variant), e.g. to compare grids bit for bit.  Variants differ

@@ -29,10 +29,11 @@ struct State {
   double x, px, y, py, sg, ps;
 };
 
+// (The quadrupole's chromatic factor 1 - ps is formed where a map needs it:
+// the cached quadrupole map does not.)
 struct PsConst {
   double opd2;  // (1+delta)^2 = 1 + 2 ps + beta0^2 ps^2        (Eq. BEND2)
   double opb;   // 1 + beta0^2 ps = (1+delta) d(delta)/d(ps)
-  double opm;   // 1 - ps, the quadrupole's chromatic factor     (Sec. III-B)
   double s1;    // sqrt(1 - ps)
   double r;     // 1/sqrt(1 - ps)
   double qi;    // 1/(4 (1 - ps))
@@ -41,10 +42,10 @@ struct PsConst {
 __device__ __forceinline__ void ps_const(PsConst& k, double ps, double beta0_sq, bool quads) {
   k.opd2 = fma(beta0_sq * ps, ps, fma(2.0, ps, 1.0));
   k.opb = fma(beta0_sq, ps, 1.0);
-  k.opm = 1.0 - ps;
   if (quads) {
-    k.r = rsqrt(k.opm);
-    k.s1 = k.opm * k.r;
+    const double opm = 1.0 - ps;
+    k.r = rsqrt(opm);
+    k.s1 = opm * k.r;
     k.qi = 0.25 * k.r * k.r;
   } else {
     k.r = k.s1 = k.qi = 0.0;
@@ -75,9 +76,11 @@ __device__ __forceinline__ void map_drift(State& s, const DevElem& e, const PsCo
 // d(u pu)/ds = (1-ps) pu^2 - k_u u^2, so
 //   int_0^L pu^2 ds = (h_u L + [u pu]_0^L / 2) / (1-ps),
 // which gives sg += ps L/gamma0^2 - (L S2 + D) / (4 (1-ps)) with
-// S2 = (1-ps)(px0^2+py0^2) + k1 (x0^2 - y0^2), D = [x px + y py]_0^L.
-// e.p = {L, theta0, cos theta0, sin theta0, cosh theta0, sinh theta0, sqk, 1/sqk, k1},
-// e.flags = QF_* (plus the family bits); the L/gamma0^2 term is e.p[0] * inv_gamma0_sq.
+// S2 = (1-ps)(px0^2+py0^2) + k1 (x0^2 - y0^2), D = [x px + y py]_0^L, i.e.
+//   sg += ps L/gamma0^2 - (L/4)(px0^2+py0^2) - (L k1 (x0^2-y0^2) + D) / (4 (1-ps)).
+// e.p = {L, theta0, cos theta0, sin theta0, cosh theta0, sinh theta0, sqk, 1/sqk, k1,
+//        L k1, L/gamma0^2, L/4},
+// e.flags = QF_* (plus the family bits).
 //
 // The entries of the two planes' 2x2 matrices depend on ps alone (QuadCoef:
 // u = cu u0 + sua pu0, pu = cu pu0 + sub u0), so a turn's tracking keeps them
@@ -114,44 +117,43 @@ __device__ __forceinline__ QuadCoef quad_coef(const DevElem& e, const PsConst& k
   return QuadCoef{ch, a * sh, bq * sh, c, a * sn, -bq * sn};
 }
 
-__device__ __forceinline__ void quad_apply(State& s, const DevElem& e, const QuadCoef& q, const PsConst& k,
-                                           double inv_gamma0_sq) {
-  const double L = e.p[0];
+__device__ __forceinline__ void quad_apply(State& s, const DevElem& e, const QuadCoef& q, const PsConst& k) {
   const double x0 = s.x, px0 = s.px, y0 = s.y, py0 = s.py;
-  const double S2 = fma(e.p[8], fma(x0, x0, -y0 * y0), k.opm * fma(px0, px0, py0 * py0));
+  const double xy = fma(x0, x0, -y0 * y0);
+  const double pp = fma(px0, px0, py0 * py0);
   const double D0 = fma(x0, px0, y0 * py0);
   s.x = fma(q.cx, x0, q.sxa * px0);
   s.px = fma(q.cx, px0, q.sxb * x0);
   s.y = fma(q.cy, y0, q.sya * py0);
   s.py = fma(q.cy, py0, q.syb * y0);
   const double D = fma(s.x, s.px, s.y * s.py) - D0;
-  s.sg = fma(-fma(L, S2, D), k.qi, fma(s.ps, L * inv_gamma0_sq, s.sg));
+  s.sg = fma(-fma(e.p[9], xy, D), k.qi, fma(-e.p[11], pp, fma(s.ps, e.p[10], s.sg)));
 }
 
 __device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
   if ((e.flags & QF_KIND) == QF_ZERO) {  // flow of H0: straight line with the chromatic factor
     const double L = e.p[0];
-    const double f = k.opm * L;
+    const double f = (1.0 - s.ps) * L;
     const double pp = fma(s.px, s.px, s.py * s.py);
     s.x = fma(f, s.px, s.x);
     s.y = fma(f, s.py, s.y);
     s.sg = fma(-0.5 * L, pp, fma(s.ps, L * inv_gamma0_sq, s.sg));
     return;
   }
-  quad_apply(s, e, quad_coef(e, k), k, inv_gamma0_sq);
+  quad_apply(s, e, quad_coef(e, k), k);
 }
 
 // The map with the particle's cached coefficients: qc points at its entry of
 // the family's six arrays of n (cx, sxa, sxb, cy, sya, syb).
 __device__ __forceinline__ void map_quad_cached(State& s, const DevElem& e, const double* __restrict__ qc, size_t n,
-                                                const PsConst& k, double inv_gamma0_sq) {
+                                                const PsConst& k) {
   const QuadCoef q{qc[0], qc[n], qc[2 * n], qc[3 * n], qc[4 * n], qc[5 * n]};
-  quad_apply(s, e, q, k, inv_gamma0_sq);
+  quad_apply(s, e, q, k);
 }
 
 // Flow of H0 = (px^2+py^2)/2 (1-ps) + ps^2/(2 gamma0^2) over l.
 __device__ __forceinline__ void h0_flow(State& s, const PsConst& k, double l, double inv_gamma0_sq) {
-  const double f = k.opm * l;
+  const double f = (1.0 - s.ps) * l;
   const double pp = fma(s.px, s.px, s.py * s.py);
   s.x = fma(f, s.px, s.x);
   s.y = fma(f, s.py, s.y);
@@ -219,7 +221,7 @@ __device__ __noinline__ void map_exact_bend(State& s, const DevElem& e, const Ps
 __device__ __forceinline__ void map_bend(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {
   const double L = e.p[0];
   if (e.flags == 1) {
-    const double f = k.opm * L;
+    const double f = (1.0 - s.ps) * L;
     const double pp = fma(s.px, s.px, s.py * s.py);
     s.x = fma(f, s.px, s.x);
     s.y = fma(f, s.py, s.y);
@@ -260,7 +262,7 @@ __device__ __forceinline__ bool push_elements(State& s, PsConst& k, const DevEle
       case SC_QUAD: {
         const int fam = e.flags >> QF_FAM_SHIFT;
         if (qc && fam && !changed)
-          map_quad_cached(s, e, qc + (size_t)(fam - 1) * 6 * n, n, k, inv_gamma0_sq);
+          map_quad_cached(s, e, qc + (size_t)(fam - 1) * 6 * n, n, k);
         else
           map_quad(s, e, k, inv_gamma0_sq);
         break;

@@ -43,6 +43,9 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "sc_internal.cuh"
@@ -1143,9 +1146,42 @@ sc_status make_run(sc_grid* g, int ph, int k, PhaseRun& out) {
 // dependent launch): one phase at a time, each of its variants with the other
 // phases' current choices, 4 chained solves per timing, best of three rounds,
 // keeping the fastest (coordinate descent from the stage-1 choice).  Variants
-// of a phase differ only in the FP32 summation order of split-K partial tiles.
+// of a phase differ only in the FP32 summation order of split-K partial tiles,
+// so the choice is made once per device and grid geometry in a process and
+// every later grid of that geometry takes it: grids of one geometry give the
+// same bits (near-equal timings could otherwise tip two grids different ways).
+struct TuneKey {
+  int dev, pipe, el, nx, ny, nstack;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, pipe, el, nx, ny, nstack) < std::tie(o.dev, o.pipe, o.el, o.nx, o.ny, o.nstack);
+  }
+};
+struct TuneChoice {
+  int variant[4];
+  float us[4];
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_choice;
+
 sc_status tf32_tune(sc_grid* g) {
   Tf32Plan* T = g->tf32;
+  int dev = 0;
+  SC_CUDA(cudaGetDevice(&dev));
+  const TuneKey key{dev, T->pipe ? 1 : 0, T->el, g->nx, g->ny, g->nstack};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto it = g_tune_choice.find(key);
+    if (it != g_tune_choice.end()) {
+      for (int c = 0; c < 4; ++c) {
+        PhaseRun r;
+        const sc_status st = make_run(g, T->base() + c, it->second.variant[c], r);
+        if (st) return st;
+        T->run[c] = r;
+        T->tuned_us[c] = it->second.us[c];
+      }
+      return SC_OK;
+    }
+  }
   cudaEvent_t e0, e1;
   SC_CUDA(cudaEventCreate(&e0));
   SC_CUDA(cudaEventCreate(&e1));
@@ -1226,6 +1262,15 @@ sc_status tf32_tune(sc_grid* g) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!st && tf32_error(g)) st = set_error(SC_ERR_TIMEOUT, "tensor-core solve gave up on a bounded wait");
+  if (!st) {
+    TuneChoice ch;
+    for (int c = 0; c < 4; ++c) {
+      ch.variant[c] = T->run[c].variant;
+      ch.us[c] = T->tuned_us[c];
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_choice.emplace(key, ch);  // a grid tuned at the same time by another thread keeps the first entry
+  }
   return st;
 }
 
