@@ -54,7 +54,7 @@ WORKLOADS = {
 # 69.0 and 18.0, mean 47.9 per particle-kick, the model's own figure); the
 # bench reports whether the sources still match.
 FP64_INST = {"base": 17.5, "drift": 12.2, "quad": 21.6, "sext": 5.0, "bend": 16.0, "rf": 30.0}
-FP64_INST_QUAD_UNCACHED = 51.0  # with the longitudinal kick (psigma changes at every kick: no cache)
+FP64_INST_QUAD_UNCACHED = 51.0  # with the longitudinal kick (psigma changes at every kick: no cache); earlier build
 # split-TF32 form: float32 gather from the cached fixed-point weights
 FP64_INST_BASE_F32 = 5.8
 # sliced grids: the slice index (one subtract, one multiply; the floor is integer work) per locate
