@@ -50,10 +50,10 @@ WORKLOADS = {
 # base = gather + kick + fused deposit.  The quadrupole reads its matrix
 # entries from the per-particle family cache (51.0 when it computes them).
 # The counts belong to the kernel sources whose SHA-256 (first 16 hex digits)
-# is FP64_INST_SOURCES_SHA (the three segment types measured on them: 56.8,
-# 69.0 and 18.0, mean 47.9 per particle-kick, the model's own figure); the
+# is FP64_INST_SOURCES_SHA (the three segment types measured on them: 55.8,
+# 68.0 and 18.0, mean 47.2 per particle-kick, the model's own figure); the
 # bench reports whether the sources still match.
-FP64_INST = {"base": 17.5, "drift": 12.2, "quad": 21.6, "sext": 5.0, "bend": 16.0, "rf": 30.0}
+FP64_INST = {"base": 17.5, "drift": 12.2, "quad": 20.6, "sext": 5.0, "bend": 16.0, "rf": 30.0}
 FP64_INST_QUAD_UNCACHED = 51.0  # with the longitudinal kick (psigma changes at every kick: no cache); earlier build
 # split-TF32 form: float32 gather from the cached fixed-point weights
 FP64_INST_BASE_F32 = 5.8
@@ -73,7 +73,7 @@ FP64_INST_LON_BEZIER_F32 = 13.95
 # cache; c2: mean of the three segment types), with the kernel sources'
 # SHA-256 (first 16 hex digits) they were captured on: the roofline's
 # "traffic" while the sources still match; other workloads report null.
-KP_TRAFFIC_TF32 = {"c2": (122.5e6, "9bbf6421bbb27d3f"),  # 1e6 particles (the working set partly stays in L2)
+KP_TRAFFIC_TF32 = {"c2": (122.4e6, "741f33f43b3df3e1"),  # 1e6 particles (the working set partly stays in L2)
                    "c4": (3860.0e6, "052c41cbfc714941"),  # 2.37e7 particles, batched (kick_push_traffic_c4_c5.md)
                    "c5": (1594.1e6, "052c41cbfc714941")}  # 1e7 particles in 32 slices
 # GB300: 152 SMs x 2 FP64 instructions per SM clock x 2.07 GHz maximum clock
@@ -85,7 +85,7 @@ FP64_PIPE_PEAK_TINST = 152 * 2 * 2.07e9 / 1e12
 DEP_FP64_INST = 4.23
 DEP_FP64_INST_SLICE = 2.0
 KP_SOURCES = ("kick_push.cu", "maps.cuh", "cic.cuh", "fixpt.h", "sc_internal.cuh")
-FP64_INST_SOURCES_SHA = "9bbf6421bbb27d3f"
+FP64_INST_SOURCES_SHA = "741f33f43b3df3e1"
 # HBM bytes per particle-kick that the fused kick/push must move (algorithmic):
 # the six float64 coordinates read (48 B) and the five a kick and a push
 # change written back (40 B: psigma changes only in RF cavities); 96 B when

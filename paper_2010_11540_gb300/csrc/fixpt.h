@@ -47,6 +47,25 @@ SC_HD int clz64(uint64_t v) {
 #endif
 }
 
+// float -> double by moving bits (IEEE 754 binary32 -> binary64: sign kept,
+// exponent rebiased by 1023 - 127, significand extended with zeros), so that
+// widening a float32 field value takes integer instructions instead of a
+// conversion on the FP64 pipe.  Equal to (double)f for zero, normal, infinite
+// and NaN values; a subnormal float (below 2^-126) becomes zero of its sign.
+SC_HD double f32_widen(float f) {
+#if defined(__CUDA_ARCH__)
+  const uint32_t u = (uint32_t)__float_as_uint(f);
+#else
+  uint32_t u;
+  memcpy(&u, &f, 4);
+#endif
+  const uint32_t mag = u & 0x7fffffffu;
+  uint32_t hi = (mag >> 3) + 0x38000000u, lo = mag << 29;
+  if (mag < 0x00800000u) hi = lo = 0u;                                  // zero, subnormal
+  if (mag >= 0x7f800000u) hi = 0x7ff00000u | ((mag >> 3) & 0x000fffffu);  // infinity, NaN
+  return bits_f64(((uint64_t)(hi | (u & 0x80000000u)) << 32) | lo);
+}
+
 // 0 <= xi < limit (finite; -0.0 counts as 0): true, with i = floor(xi), the
 // fixed-point weight a = rint((xi - i) * 2^20) in [0, 2^20], and, if f is not
 // NULL, *f = xi - i.  Otherwise false (outputs unspecified).  limit <= 2^30.

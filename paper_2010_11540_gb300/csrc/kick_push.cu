@@ -33,19 +33,6 @@ constexpr int kpb_max_threads() {
   return F32 ? 768 : 640;
 }
 
-// float -> double by moving the bits on the integer pipe (the conversion
-// instruction would take an FP64 issue slot): exact for zero, normal,
-// infinite and NaN values (IEEE 754 binary32 -> binary64: sign kept, exponent
-// rebiased by 1023 - 127, significand extended with zeros); subnormal floats
-// (below 2^-126, never a field value here) become zero of the same sign.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned u = __float_as_uint(f), mag = u & 0x7fffffffu;
-  unsigned hi = (mag >> 3) + 0x38000000u, lo = mag << 29;
-  if (mag < 0x00800000u) hi = lo = 0u;                            // zero, subnormal
-  if (mag >= 0x7f800000u) hi = 0x7ff00000u | ((mag >> 3) & 0x000fffffu);  // inf, NaN
-  return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)lo);
-}
-
 // Kick from the Bezier surface of the potential (Sec. IV-C): E = -grad u, and
 // with the longitudinal kick the neighbouring slices' u from the same
 // surfaces.  Not inlined: its registers stay out of the bilinear path.
@@ -139,8 +126,8 @@ __device__ __forceinline__ void kick_push_range(const KPParams& P, bool use_tile
           const float2 e01 = __ldg(e + P.gk.nx), e11 = __ldg(e + P.gk.nx + 1);
           const float ax = fmaf(fx, e10.x - e00.x, e00.x), bx = fmaf(fx, e11.x - e01.x, e01.x);
           const float ay = fmaf(fx, e10.y - e00.y, e00.y), by = fmaf(fx, e11.y - e01.y, e01.y);
-          s.px = fma(P.kl, widen(fmaf(fy, bx - ax, ax)), s.px);
-          s.py = fma(P.kl, widen(fmaf(fy, by - ay, ay)), s.py);
+          s.px = fma(P.kl, f32_widen(fmaf(fy, bx - ax, ax)), s.px);
+          s.py = fma(P.kl, f32_widen(fmaf(fy, by - ay, ay)), s.py);
           if (P.lon) {
             // longitudinal kick from the float32 potentials of the neighbouring slices
             const int cells = P.gk.nx * P.gk.ny, k = cell / cells, nxk = P.gk.nx;
@@ -458,17 +445,15 @@ void compile_elements(const sc_element* in, int n, const sc_beam* b, DevElem* ou
         const double sqk = std::sqrt(std::fabs(e.k1));
         const double th0 = sqk * e.length;
         d.flags = e.k1 > 0.0 ? QF_FOCUS_X : QF_FOCUS_Y;
-        d.p[1] = th0;
+        d.p[0] = 0.25 * e.length;
+        d.p[1] = e.length / (b->gamma0 * b->gamma0);
         d.p[2] = std::cos(th0);
         d.p[3] = std::sin(th0);
         d.p[4] = std::cosh(th0);
         d.p[5] = std::sinh(th0);
         d.p[6] = sqk;
         d.p[7] = 1.0 / sqk;
-        d.p[8] = e.k1;
-        d.p[9] = e.length * e.k1;
-        d.p[10] = e.length / (b->gamma0 * b->gamma0);
-        d.p[11] = 0.25 * e.length;
+        d.p[8] = e.length * e.k1;
         break;
       }
       case SC_SEXT:

@@ -78,9 +78,10 @@ __device__ __forceinline__ void map_drift(State& s, const DevElem& e, const PsCo
 // which gives sg += ps L/gamma0^2 - (L S2 + D) / (4 (1-ps)) with
 // S2 = (1-ps)(px0^2+py0^2) + k1 (x0^2 - y0^2), D = [x px + y py]_0^L, i.e.
 //   sg += ps L/gamma0^2 - (L/4)(px0^2+py0^2) - (L k1 (x0^2-y0^2) + D) / (4 (1-ps)).
-// e.p = {L, theta0, cos theta0, sin theta0, cosh theta0, sinh theta0, sqk, 1/sqk, k1,
-//        L k1, L/gamma0^2, L/4},
-// e.flags = QF_* (plus the family bits).
+// e.p = {L/4, L/gamma0^2, cos theta0, sin theta0, cosh theta0, sinh theta0, sqk, 1/sqk, L k1}
+// (theta0 = sqk L = sqk (4 e.p[0]), the host's product bit for bit: the
+// record keeps nine words, the size the kernels copy per element), e.flags =
+// QF_* (plus the family bits); a zero-gradient quadrupole (QF_ZERO) has e.p[0] = L.
 //
 // The entries of the two planes' 2x2 matrices depend on ps alone (QuadCoef:
 // u = cu u0 + sua pu0, pu = cu pu0 + sub u0), so a turn's tracking keeps them
@@ -90,7 +91,7 @@ struct QuadCoef {
 };
 
 __device__ __forceinline__ QuadCoef quad_coef(const DevElem& e, const PsConst& k) {
-  const double th0 = e.p[1];
+  const double th0 = e.p[6] * (4.0 * e.p[0]);
   const double delta = fma(th0, k.s1, -th0);
   double c, sn, ch, sh;
   if (fabs(delta) <= kMaxDelta) {
@@ -121,13 +122,13 @@ __device__ __forceinline__ void quad_apply(State& s, const DevElem& e, const Qua
   const double x0 = s.x, px0 = s.px, y0 = s.y, py0 = s.py;
   const double xy = fma(x0, x0, -y0 * y0);
   const double pp = fma(px0, px0, py0 * py0);
-  const double D0 = fma(x0, px0, y0 * py0);
   s.x = fma(q.cx, x0, q.sxa * px0);
   s.px = fma(q.cx, px0, q.sxb * x0);
   s.y = fma(q.cy, y0, q.sya * py0);
   s.py = fma(q.cy, py0, q.syb * y0);
-  const double D = fma(s.x, s.px, s.y * s.py) - D0;
-  s.sg = fma(-fma(e.p[9], xy, D), k.qi, fma(-e.p[11], pp, fma(s.ps, e.p[10], s.sg)));
+  // L k1 (x0^2 - y0^2) + D, D = x px + y py - x0 px0 - y0 py0
+  const double u = fma(e.p[8], xy, fma(-y0, py0, fma(-x0, px0, fma(s.x, s.px, s.y * s.py))));
+  s.sg = fma(-u, k.qi, fma(-e.p[0], pp, fma(s.ps, e.p[1], s.sg)));
 }
 
 __device__ __forceinline__ void map_quad(State& s, const DevElem& e, const PsConst& k, double inv_gamma0_sq) {

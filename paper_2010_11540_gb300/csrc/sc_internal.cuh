@@ -79,7 +79,7 @@ constexpr int kTileBytes = 200 * 1024;
 struct DevElem {
   int type;
   int flags;
-  double p[12];
+  double p[9];
 };
 
 // Segments up to this many elements travel inside the launch parameters.

@@ -110,3 +110,54 @@ def test_exact_ties_and_boundaries(harness):
                         0.5 / 2 ** 20, 1.5 / 2 ** 20, 2.0 ** -21, 2.0 ** -61, 2.0 ** -59])
     bad, inside, out = run(harness, np.concatenate([ties, near, special]), 127)
     assert bad == 0, out
+
+
+WIDEN = r"""
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include "fixpt.h"
+int main() {
+  unsigned long long bad = 0, checked = 0;
+  uint32_t u = 0;
+  do {
+    float f;
+    memcpy(&f, &u, 4);
+    const double w = sc::f32_widen(f);
+    uint64_t wb, rb;
+    memcpy(&wb, &w, 8);
+    const double r = (double)f;
+    memcpy(&rb, &r, 8);
+    const uint32_t mag = u & 0x7fffffffu;
+    bool ok;
+    if (mag > 0x7f800000u)            // NaN: a NaN of the same sign (quieting may differ)
+      ok = std::isnan(w) && ((wb >> 63) == (u >> 31));
+    else if (mag != 0 && mag < 0x00800000u)  // subnormal: zero of the same sign
+      ok = wb == ((uint64_t)(u >> 31) << 63);
+    else                              // zero, normal, infinity: the conversion's bits
+      ok = wb == rb;
+    if (!ok && ++bad < 5) printf("mismatch %08x\n", (unsigned)u);
+    ++checked;
+  } while (++u != 0);
+  printf("%llu %llu\n", bad, checked);
+  return 0;
+}
+"""
+
+
+def test_f32_widen_every_float(tmp_path):
+    """f32_widen (the split form's float32 field values widened to float64 on
+    the integer pipe) against the compiler's float -> double conversion for
+    all 2^32 bit patterns: the same bits for zero, normal and infinite values,
+    a NaN for a NaN, signed zero for the (never used) subnormals."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    src = tmp_path / "w.cpp"
+    src.write_text(WIDEN)
+    exe = tmp_path / "w"
+    subprocess.run([cxx, "-std=c++17", "-O2", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    bad, checked = map(int, out.split()[-2:])
+    assert bad == 0 and checked == 2 ** 32, out
