@@ -1,7 +1,10 @@
 /* The C-ABI from plain C99: a bunch in host memory tracked for three turns of
  * a FODO cell with two space-charge locations (sc_track_turns_host), the
  * moments read back, argument errors reported through sc_last_error.
- * Prints "ok" and exits 0 on success. */
+ * Prints "ok" and exits 0 on success.  With a file name argument it also
+ * writes the tracked state (x, px, y, py, sigma, psigma: n doubles each) and
+ * the three turns' moments (3 x 14 doubles) there, for a comparison with the
+ * oracle. */
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -22,7 +25,7 @@ static int fail(const char *what) {
   return 1;
 }
 
-int main(void) {
+int main(int argc, char **argv) {
   const int64_t n = 20000;
   double *a = malloc((size_t)n * 6 * sizeof(double));
   if (!a) return 1;
@@ -67,6 +70,12 @@ int main(void) {
     if (!isfinite(p.x[i]) || !isfinite(p.px[i]) || !isfinite(p.y[i]) || !isfinite(p.psigma[i]))
       return fail("state not finite");
   if (sc_destroy_grid(g) != SC_OK) return fail("destroy");
+  if (argc > 1) {
+    FILE *fp = fopen(argv[1], "wb");
+    if (!fp || fwrite(a, sizeof(double), (size_t)n * 6, fp) != (size_t)n * 6 ||
+        fwrite(diag, sizeof(double), 3 * 14, fp) != 3 * 14 || fclose(fp) != 0)
+      return fail("writing the state");
+  }
   free(a);
   printf("ok\n");
   return 0;
