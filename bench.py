@@ -359,6 +359,10 @@ class SingleRun:
         dev = {k: torch.from_numpy(self.parts[k]).cuda() for k in KEYS}
         g = sc.create_grid(*self.grid, precision=precision, stream=self.stream, slices=self.slices)
         if self.world > 1:
+            # one eager all-reduce of the (still zero) charge first: the communicator is set up
+            # outside the turn's graph capture, which then records the collective only
+            self.allreduce(sc.charge_tensor(g), self.stream)
+            self.stream.synchronize()
             sc.set_charge_reduce(g, self.allreduce, self.world * self.n)
         if precision in ("tf32x3", "pipe_tf32x3", "bf16x3") and self.tiling:
             sc.set_solver_tiling(g, self.tiling)
