@@ -238,3 +238,35 @@ def test_thick_sextupole_is_the_papers_split():
     thin = apply([synth.elem(synth.SEXT, 1e-7, k2l=30.0)], z)
     kick = apply([synth.elem(synth.SEXT, 0.0, k2l=30.0)], z)
     assert np.max(np.abs(thin - kick)) < 1e-9
+
+
+def test_synchrotron_tune_of_a_small_oscillation():
+    """RF cavity and drift together against small-oscillation theory: a ring of
+    one drift of length C (no bends, so the slip factor is 1/gamma0^2: the
+    exact drift advances sigma by C psigma / gamma0^2 to first order) and one
+    thin cavity (psigma kick V/(beta0^2 E0) sin(-2 pi h sigma / C), the
+    linearised restoring strength k = V/(beta0^2 E0) 2 pi h / C) has the
+    one-turn matrix [[1, C/g^2], [-k, 1 - k C/g^2]], so
+    cos(2 pi Q_s) = 1 - k C / (2 gamma0^2) -- for small Q_s the textbook
+    Q_s^2 = h V eta / (2 pi beta0^2 E0).  The tracked small-amplitude
+    particle's period (from its interpolated zero crossings of sigma) must
+    give that tune: a wrong sign of the kick, a missing beta0^2 or gamma0^2,
+    or a wrong 2 pi h / C fails it."""
+    C, V, h = 100.0, 2e6, 20.0
+    b = synth.beam(circumference=C)
+    g0, b0 = b["gamma0"], b["beta0"]
+    k = V / (b0 * b0 * g0 * b["mass_ev"]) * 2 * np.pi * h / C
+    qs = np.arccos(1 - k * C / (2 * g0 * g0)) / (2 * np.pi)
+    assert 0.005 < qs < 0.02
+    ring = synth.table([synth.elem(synth.DRIFT, C), synth.elem(synth.RF, volt=V, harmonic=h, lag=0.0)])
+    st = {key: np.zeros(1) for key in ("x", "px", "y", "py", "sigma", "psigma")}
+    st["sigma"][0] = 1e-3
+    sg = np.empty(4000)
+    for t in range(sg.size):
+        sg[t] = st["sigma"][0]
+        oracle.push(st, ring, b)
+    assert np.max(np.abs(sg)) < 1.01e-3  # a stable, small oscillation
+    i = np.nonzero(np.sign(sg[:-1]) != np.sign(sg[1:]))[0]
+    z = i + sg[i] / (sg[i] - sg[i + 1])  # interpolated zero crossings (turns)
+    period = 2 * (z[-1] - z[0]) / (len(z) - 1)
+    assert 1 / period == pytest.approx(qs, rel=1e-5)
