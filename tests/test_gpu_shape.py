@@ -109,3 +109,27 @@ def test_shape_arguments():
     sc.set_kick_push_shape(g, 640, 0)
     g32 = sc.create_grid(64, 64, -1.0, 1.0, -1.0, 1.0, precision="tf32x3")
     sc.set_kick_push_shape(g32, 768, 1)
+
+
+@pytest.mark.parametrize("precision", ["tf32x3", "bf16x3"])
+def test_grids_of_one_geometry_share_the_solve_tiling(precision):
+    """The split solve's tiling is timed when the first grid of a geometry is
+    created on the device; later grids of that geometry take the same choice
+    (a forced tiling on one grid changes only that grid), so they solve the
+    same charge to the same bits -- tilings differ in FP32 summation order."""
+    parts, _, grid, _ = synth.workload("c2", n=200_000)
+    a = sc.create_grid(*grid, precision=precision)
+    b = sc.create_grid(*grid, precision=precision)
+    assert sc.get_solver_tiling(a) == sc.get_solver_tiling(b)
+    forced = [1, 1, 1, 1]
+    sc.set_solver_tiling(b, forced)
+    assert sc.get_solver_tiling(b)[0] == forced
+    c = sc.create_grid(*grid, precision=precision)
+    assert sc.get_solver_tiling(c) == sc.get_solver_tiling(a)
+    sc.deposit(a, to_gpu(parts))
+    Q, _, _, _ = sc.grid_read(a)
+    sc.grid_write_charge(c, Q, len(parts["x"]))
+    sc.solve(a)
+    sc.solve(c)
+    Ea, Ec = sc.grid_read(a)[1:3], sc.grid_read(c)[1:3]
+    assert np.array_equal(Ea[0], Ec[0]) and np.array_equal(Ea[1], Ec[1])
