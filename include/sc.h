@@ -487,6 +487,26 @@ sc_status sc_tunes(const double *acc, int64_t n, int n_turns, double *q, void *s
  * SC_ERR_CUDA. */
 sc_status sc_moments_noalloc(const sc_particles *p, double *out, void *stream);
 
+/* Checkpoint and resume of a tracked bunch (host memory; the paper has no
+ * counterpart, but its runs reach ~5e5 turns).  sc_checkpoint_write stores
+ * the bunch's six HOST arrays (host->x .. host->psigma, host->n > 0 doubles
+ * each, e.g. after sc_track_turns_host or a copy from the device) bit for bit
+ * together with the caller's turn counter, the beam constants and a 64-bit
+ * hash of the lattice (element count and records) in the file `path`,
+ * replacing it in one step (written to path".tmp", then renamed), with a
+ * checksum of the contents.  sc_checkpoint_read checks the file (format,
+ * particle count = host->n, the same beam constants bit for bit, the same
+ * lattice, the checksum) before it fills the host arrays and *turn (turn may
+ * be NULL); on any mismatch it returns SC_ERR_ARG and leaves the arrays
+ * untouched.  Tracking is deterministic, so resuming from a checkpoint gives
+ * the bits of the uninterrupted run.  Synchronous host I/O, no GPU work.
+ * Errors: SC_ERR_ARG (NULL or empty bunch, bad element list, I/O failure,
+ * mismatch or damage, with the reason in sc_last_error). */
+sc_status sc_checkpoint_write(const char *path, const sc_particles *host, int64_t turn, const sc_beam *b,
+                              const sc_element *lattice, int n_elems);
+sc_status sc_checkpoint_read(const char *path, const sc_particles *host, int64_t *turn, const sc_beam *b,
+                             const sc_element *lattice, int n_elems);
+
 /* Text of the last error on the calling thread (always NUL-terminated). */
 sc_status sc_last_error(char *buf, size_t n);
 

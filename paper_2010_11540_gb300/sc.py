@@ -32,7 +32,8 @@ EXPORTS = ("sc_create_grid", "sc_create_grid_sliced", "sc_destroy_grid", "sc_dep
            "sc_set_longitudinal_kick", "sc_set_gather", "sc_test_bounded_waits", "sc_set_kick_push_shape",
            "sc_get_kick_push_shape", "sc_track_turns_host", "sc_batch_track_turns_host", "sc_batch_set_kick_push_shape",
            "sc_batch_get_kick_push_shape", "sc_get_solver_work", "sc_grid_charge_device",
-           "sc_set_particle_count", "sc_sort_particles", "sc_set_charge_reduce", "sc_last_error")
+           "sc_set_particle_count", "sc_sort_particles", "sc_set_charge_reduce", "sc_checkpoint_write",
+           "sc_checkpoint_read", "sc_last_error")
 
 
 class ScError(RuntimeError):
@@ -121,6 +122,10 @@ def load():
     L.sc_batch_set_kick_push_shape.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.sc_batch_get_kick_push_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
     L.sc_get_kick_push_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), dp]
+    L.sc_checkpoint_write.argtypes = [ctypes.c_char_p, ctypes.POINTER(Particles), i64, ctypes.POINTER(Beam), vp,
+                                      ctypes.c_int]
+    L.sc_checkpoint_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(Particles), ctypes.POINTER(i64),
+                                     ctypes.POINTER(Beam), vp, ctypes.c_int]
     L.sc_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
     for name in EXPORTS:
         getattr(L, name).restype = ctypes.c_int
@@ -436,6 +441,26 @@ def track_turns_host(grid: Grid, host_state, b: dict, lattice, n_turns: int, dia
     _check(load().sc_track_turns_host(grid.handle, ctypes.byref(p), ctypes.byref(bb), ptr, n, int(n_turns),
                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if diag else None))
     return out
+
+
+def checkpoint_write(path, host_state, turn: int, b: dict, lattice):
+    """sc_checkpoint_write: the bunch's six host arrays, the turn counter, the
+    beam constants and a hash of the lattice into the file `path`."""
+    p = host_particles(host_state)
+    bb = beam(b)
+    ptr, n, keep = _elements(lattice)
+    _check(load().sc_checkpoint_write(os.fsencode(path), ctypes.byref(p), int(turn), ctypes.byref(bb), ptr, n))
+
+
+def checkpoint_read(path, host_state, b: dict, lattice) -> int:
+    """sc_checkpoint_read: fill the six host arrays from `path` after checking
+    that it was written for this bunch size, beam and lattice; -> the turn counter."""
+    p = host_particles(host_state)
+    bb = beam(b)
+    ptr, n, keep = _elements(lattice)
+    t = ctypes.c_int64(0)
+    _check(load().sc_checkpoint_read(os.fsencode(path), ctypes.byref(p), ctypes.byref(t), ctypes.byref(bb), ptr, n))
+    return int(t.value)
 
 
 # ---------------------------------------------------------------- batches of bunches
