@@ -305,3 +305,36 @@ def workload(name, seed=12345, n=None):
     g = c["grid"]
     grid = (g, g) + grid_extent(c["sig_x"], c["sig_y"])
     return parts, b, grid, lat
+
+
+# ---- plain-text description of a ring and its beam -------------------------
+TYPE_NAMES = {DRIFT: "drift", QUAD: "quad", SEXT: "sext", BEND: "bend", RF: "rf", MARK: "mark",
+              EXACT_BEND: "exact_bend"}
+FIELDS = ("length", "k1", "k2l", "angle", "volt", "harmonic", "lag")
+
+
+def config_to_json(b: dict, lattice) -> str:
+    """A beam dict and an element table as JSON: {"beam": {...}, "lattice":
+    [{"type": "quad", "length": 1.0, "k1": 0.14, ...}, ...]} (fields that are
+    zero are left out; float64 values written with all their digits)."""
+    import json
+    elems = []
+    for r in np.asarray(lattice, dtype=ELEMENT_DTYPE):
+        e = {"type": TYPE_NAMES[int(r["type"])]}
+        e.update({f: float(r[f]) for f in FIELDS if float(r[f]) != 0.0})
+        elems.append(e)
+    return json.dumps({"beam": {k: float(v) for k, v in b.items()}, "lattice": elems}, indent=1)
+
+
+def config_from_json(text: str):
+    """-> (beam dict, element table) from config_to_json's format."""
+    import json
+    d = json.loads(text)
+    codes = {v: k for k, v in TYPE_NAMES.items()}
+    rows = []
+    for e in d["lattice"]:
+        unknown = set(e) - set(FIELDS) - {"type"}
+        if unknown or e.get("type") not in codes:
+            raise ValueError(f"bad element {e}")
+        rows.append(elem(codes[e["type"]], **{f: float(e[f]) for f in FIELDS if f in e}))
+    return {k: float(v) for k, v in d["beam"].items()}, table(rows)

@@ -68,3 +68,14 @@ def test_same_seed_same_bits():
     d = synth.workload("c1", n=5000, seed=12346)[0]
     assert all(np.array_equal(a[k], c[k]) for k in a)
     assert not np.array_equal(a["x"], d["x"])
+
+
+def test_ring_and_beam_json_round_trip():
+    """The rings and beams as plain text: every preset comes back bit for bit."""
+    for name in ("c1", "c2", "c5"):
+        _, b, _, lat = synth.workload(name, n=10)
+        b2, lat2 = synth.config_from_json(synth.config_to_json(b, lat))
+        assert b2 == b
+        assert lat2.dtype == lat.dtype and lat2.tobytes() == lat.tobytes()
+    with pytest.raises(ValueError):
+        synth.config_from_json('{"beam": {}, "lattice": [{"type": "quad", "k3": 1.0}]}')
