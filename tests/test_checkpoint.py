@@ -125,3 +125,60 @@ def test_argument_errors(tmp_path):
     assert L.sc_checkpoint_read(str(tmp_path / "b").encode(), ctypes.byref(p), None, ctypes.byref(bb), None, 0) == 0
     assert L.sc_checkpoint_write(str(tmp_path / "no" / "dir").encode(), ctypes.byref(p), 0, ctypes.byref(bb), None,
                                  0) == -1
+
+
+SANITIZED = r"""
+#include <string>
+#include <cstdio>
+#include "sc_internal.cuh"
+namespace sc { std::string g_msg; sc_status set_error(sc_status code, const std::string& msg) { g_msg = msg; return code; } }
+#include <cstdlib>
+#include <cstring>
+int main() {
+  const int64_t n = 1000;
+  double* a = (double*)malloc(6 * n * 8);
+  for (int64_t i = 0; i < 6 * n; ++i) a[i] = (double)i * 0.5;
+  sc_particles p = {a, a + n, a + 2 * n, a + 3 * n, a + 4 * n, a + 5 * n, n};
+  sc_beam b = {4.2, 0.97, 5e9, 1.5e-18, 100, 0.938e9};
+  sc_element lat[2] = {{0, 0, 1.0, 0, 0, 0, 0, 0, 0}, {5, 0, 0, 0, 0, 0, 0, 0, 0}};
+  if (sc_checkpoint_write("c.bin", &p, 7, &b, lat, 2)) return 1;
+  double* c = (double*)calloc(6 * n, 8);
+  sc_particles q = {c, c + n, c + 2 * n, c + 3 * n, c + 4 * n, c + 5 * n, n};
+  int64_t t = 0;
+  if (sc_checkpoint_read("c.bin", &q, &t, &b, lat, 2) || t != 7 || memcmp(a, c, 6 * n * 8)) return 2;
+  FILE* f = fopen("c.bin", "r+b"); fseek(f, 200, SEEK_SET); fputc(0x55, f); fclose(f);
+  if (sc_checkpoint_read("c.bin", &q, &t, &b, lat, 2) != SC_ERR_ARG) return 3;
+  if (sc_checkpoint_read("missing.bin", &q, &t, &b, lat, 2) != SC_ERR_ARG) return 4;
+  sc_particles z = {a, a, a, a, a, a, 0};
+  if (sc_checkpoint_write("d.bin", &z, 0, &b, lat, 2) != SC_ERR_ARG) return 5;
+  free(a); free(c);
+  puts("ok");
+  return 0;
+}
+"""
+
+
+def test_checkpoint_code_under_sanitizers(tmp_path):
+    """The host code of csrc/checkpoint.cu compiled by the system C++ compiler
+    under AddressSanitizer, UndefinedBehaviorSanitizer and LeakSanitizer (a
+    stub stands in for the library's error recorder): a write, a read, a
+    damaged file, a missing file and an empty bunch, with no report."""
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++")
+    cuda_inc = "/usr/local/cuda/include"
+    if cxx is None or not os.path.isdir(cuda_inc):
+        pytest.skip("no g++ or CUDA headers")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    csrc = os.path.join(root, "paper_2010_11540_gb300", "csrc")
+    (tmp_path / "stub.cpp").write_text(SANITIZED)
+    exe = tmp_path / "ck"
+    r = subprocess.run([cxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all",
+                        "-I", os.path.join(root, "include"), "-I", csrc, "-I", cuda_inc,
+                        "-x", "c++", os.path.join(csrc, "checkpoint.cu"), "-x", "c++", str(tmp_path / "stub.cpp"),
+                        "-o", str(exe)], capture_output=True, text=True)
+    if r.returncode != 0:
+        pytest.skip("sanitizer build not available: " + r.stderr[-200:])
+    r = subprocess.run([str(exe)], capture_output=True, text=True, cwd=tmp_path, timeout=120,
+                       env=dict(os.environ, ASAN_OPTIONS="detect_leaks=1"))
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stderr[-3000:])
