@@ -119,9 +119,13 @@ typedef struct {
 } sc_element;
 
 /* Create a transverse grid of nx x ny nodes at x_i = xmin + i hx,
- * hx = (xmax - xmin)/(nx - 1) (same for y), with the open-boundary
- * (Hockney zero-padded) Poisson solver of the given precision.  Builds the
- * Green's-function spectra on the device (synchronous on `stream`).
+ * hx = (xmax - xmin)/(nx - 1) (same for y) -- the mesh of the charge
+ * assignment of Sec. IV-A -- with the Poisson solver of Sec. IV in the given
+ * precision: the open boundary (Hockney's zero-padded convolution, cited in
+ * Sec. I) or, for the SC_SOLVE_PIPE_* forms, the conducting rectangular pipe
+ * of Sec. IV-B.  Builds the Green's-function spectra (or sine-transform
+ * matrices) on the device (synchronous on `stream`); the grid owns them and
+ * every other device buffer it uses (released by sc_destroy_grid).
  * nx, ny: powers of two in 8..512 for SC_SOLVE_FP64; nx = ny in {64, 128, 256}
  * for SC_SOLVE_TF32X3 and SC_SOLVE_BF16X3; nx - 1, ny - 1 powers of two in 8..512 for
  * SC_SOLVE_PIPE_FP64; nx = ny in 10..258 for SC_SOLVE_PIPE_TF32X3.  Errors: SC_ERR_ARG, SC_ERR_UNSUPPORTED,
@@ -190,7 +194,9 @@ sc_status sc_solve(sc_grid *g);
 sc_status sc_kick_push(sc_grid *g, const sc_particles *p, const sc_beam *b, double L_sc,
                        const sc_element *elems, int n_elems, sc_grid *next);
 
-/* Track n_turns turns of the ring `lattice` (host array of n_elems elements;
+/* The PIC loop of Sec. I over whole turns (Sec. V: space-charge kicks at
+ * chosen locations of the ring, each with the path length since the previous
+ * one).  Track n_turns turns of the ring `lattice` (host array of n_elems elements;
  * SC_MARK entries are the space-charge locations, the kick length being the
  * path length since the previous marker, cyclically).  Each marker runs
  * deposit -> solve -> kick, then the elements up to the next marker are
@@ -456,7 +462,8 @@ sc_status sc_batch_get_solver_tiling(sc_batch *B, int b, int *choice, char *desc
 sc_status sc_batch_set_solver_tiling(sc_batch *B, const int *choice);
 sc_status sc_batch_trace_read(sc_batch *B, double *kick_push_ms, double *solve_ms, int64_t *n_kicks);
 
-/* Fractional tunes from a tune accumulator (sc_tune_setup) after n_turns
+/* Per-particle tunes of Sec. V (the mean one-turn phase advance): the
+ * fractional tunes from a tune accumulator (sc_tune_setup) after n_turns
  * tracked turns: q (device, caller-owned, 2 n doubles) receives acc's summed
  * advances / (2 pi n_turns), x for particles 0..n-1, then y.  Asynchronous on
  * `stream` (NULL: the legacy default stream); acc and q are device pointers.
